@@ -1,0 +1,369 @@
+"""FP64 CPU oracle for the PDLP iteration (restarted, diagonally preconditioned PDHG).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  The CUDA product path
+never calls it and shares no code with it (the only common module is the
+seeded input generator ``lpgen``).
+
+What is computed, and from where
+--------------------------------
+The paper (Kempke & Koch, arXiv 2503.10344) solves the LP relaxation of eq. (1)
+(section 1),  min c^T x  s.t.  A x <= b,  l <= x <= u,  with GPU PDLP to a
+*relative* tolerance (section 4, "Hardware and software": relative primal/dual
+tolerances; 1e-4 and 1e-6 in section 4.1 and Table "lp_results").  It runs PDLP
+as a black box and does not restate its internals.  Every internal step below
+is therefore the published PDLP method as this project reads it; the readings
+are listed one by one in the design notes and marked "reading" here:
+
+  A0  canonical form: flip <=-rows to >=, K = S A, q = S b; dual cone Y has
+      y_i >= 0 on inequality rows and y_i free on equality rows.
+  A2  Ruiz equilibration (10 passes, inf-norm) then Pock-Chambolle (alpha = 1)
+      diagonal scaling, K~ = D_r K D_c.
+  A3  x0 = proj_[l~,u~](0), y0 = 0, omega0 = ||c~|| / ||q~|| (if both > 1e-10,
+      else 1), eta0 = 1 / max|K~_ij|.
+  A4/A5  PDHG step  x' = proj_X(x - (eta/omega)(c~ - K~^T y)),
+                    y' = proj_Y(y + eta*omega (q~ - K~ (2x' - x))).
+  A6  adaptive step size: eta_bar = (omega ||dx||^2 + ||dy||^2/omega)
+      / (2 |dy^T K~ dx|); eta_next = min((1-(k+1)^-0.3) eta_bar,
+      (1+(k+1)^-0.6) eta), k = attempt count (1-based); accept iff
+      eta <= eta_bar, else retry from the same point with eta_next.
+  A7  step-size-weighted averages since the last restart.
+  A8  every ``check_period`` accepted iterations: relative KKT of the current
+      and the average iterate on the unscaled data (Part I below).
+  A9  KKT restart (beta_suff 0.2, beta_nec 0.8, beta_art 0.36) on the scaled
+      KKT_omega = sqrt(omega ||r_p~||^2 + ||r_d~||^2 / omega + gap^2).
+  A10 primal weight omega <- exp(0.5 ln(dy/dx) + 0.5 ln omega) on restart.
+  A11 stop when min(relKKT(current), relKKT(average)) <= tol; unscale.
+
+Part I (the definition every result is judged by): for a point x in [l,u] and
+y in Y of the canonical problem,
+  r_p,i = max(0, q_i - (Kx)_i) on >=-rows and q_i - (Kx)_i on =-rows,
+  lambda = c - K^T y,  r_d,j = lambda+_j [l_j = -inf] + lambda-_j [u_j = +inf],
+  primal = c^T x,  dual = q^T y + sum_{l finite} l lambda+ - sum_{u finite} u lambda-,
+  rel_p = ||r_p|| / (1 + ||q||), rel_d = ||r_d|| / (1 + ||c||),
+  rel_gap = |primal - dual| / (1 + |primal| + |dual|),
+  rel_kkt = max(rel_p, rel_d, rel_gap).
+
+Every step is written as its definition: scipy.sparse matrix-vector products
+and numpy elementwise operations, no fusion and no reordering.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+SENSE_LE, SENSE_GE, SENSE_EQ = ord("L"), ord("G"), ord("E")
+
+STATUS_OPTIMAL = 1
+STATUS_ITER_LIMIT = 2
+STATUS_TIME_LIMIT = 3
+
+
+# ---------------------------------------------------------------- A0 -------
+def canonicalize(lp):
+    """A0: K = S A, q = S b with S_ii = -1 on <=-rows and +1 otherwise.
+
+    Returns (K as scipy CSR, q, is_eq mask, S).  Eq. (1) of the paper states
+    the LP with A x <= b; the row senses generalise it (reading).
+    """
+    a = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
+    s = np.where(lp.sense == SENSE_LE, -1.0, 1.0)
+    k = sp.diags(s) @ a
+    return sp.csr_matrix(k), s * lp.b, lp.sense == SENSE_EQ, s
+
+
+def proj_box(x, l, u):
+    """Projection onto [l, u] (infinite bounds allowed)."""
+    return np.minimum(np.maximum(x, l), u)
+
+
+def proj_dual(y, is_eq):
+    """Projection onto Y: y_i >= 0 on inequality rows, free on equality rows."""
+    return np.where(is_eq, y, np.maximum(y, 0.0))
+
+
+# ---------------------------------------------------------------- A2 -------
+def ruiz_pock_chambolle(k, ruiz_iters=10, pc_alpha=1.0):
+    """A2: diagonal preconditioners D_r, D_c with K~ = D_r K D_c (reading).
+
+    Ruiz pass: r_i = sqrt(max_j |K~_ij|), s_j = sqrt(max_i |K~_ij|), both taken
+    from the same K~, a zero row/column gets factor 1, then D_r /= r, D_c /= s.
+    Pock-Chambolle pass (alpha): r_i = sqrt(sum_j |K~_ij|^(2-alpha)),
+    s_j = sqrt(sum_i |K~_ij|^alpha), applied the same way.
+    """
+    m, n = k.shape
+    dr = np.ones(m)
+    dc = np.ones(n)
+    absk = abs(k).tocsr()
+    for _ in range(ruiz_iters):
+        kt = sp.diags(dr) @ absk @ sp.diags(dc)
+        rmax = kt.max(axis=1).toarray().ravel() if m and n else np.zeros(m)
+        cmax = kt.max(axis=0).toarray().ravel() if m and n else np.zeros(n)
+        r = np.where(rmax > 0, np.sqrt(rmax), 1.0)
+        s = np.where(cmax > 0, np.sqrt(cmax), 1.0)
+        dr = dr / r
+        dc = dc / s
+    if pc_alpha is not None:
+        kt = (sp.diags(dr) @ absk @ sp.diags(dc)).tocsr()
+        rs = np.asarray(kt.power(2.0 - pc_alpha).sum(axis=1)).ravel()
+        cs = np.asarray(kt.power(pc_alpha).sum(axis=0)).ravel()
+        r = np.where(rs > 0, np.sqrt(rs), 1.0)
+        s = np.where(cs > 0, np.sqrt(cs), 1.0)
+        dr = dr / r
+        dc = dc / s
+    return dr, dc
+
+
+# ----------------------------------------------------------- Part I --------
+@dataclass
+class KKT:
+    primal_obj: float
+    dual_obj: float
+    r_p: float      # ||r_p||_2 (absolute)
+    r_d: float      # ||r_d||_2 (absolute)
+    gap: float      # |primal - dual| (absolute)
+    rel_p: float
+    rel_d: float
+    rel_gap: float
+
+    @property
+    def rel_kkt(self) -> float:
+        return max(self.rel_p, self.rel_d, self.rel_gap)
+
+    def kkt_omega(self, omega: float) -> float:
+        """A9: sqrt(omega ||r_p||^2 + ||r_d||^2 / omega + gap^2) (reading)."""
+        return math.sqrt(omega * self.r_p ** 2 + self.r_d ** 2 / omega + self.gap ** 2)
+
+
+def kkt_canonical(k, q, is_eq, c, l, u, x, y) -> KKT:
+    """Part I residuals of (x, y) for the canonical LP (K, q, c, l, u)."""
+    kx = k @ x
+    r_p = np.where(is_eq, q - kx, np.maximum(q - kx, 0.0))
+    lam = c - k.T @ y
+    lp_ = np.maximum(lam, 0.0)
+    lm = np.maximum(-lam, 0.0)
+    r_d = np.where(np.isinf(l), lp_, 0.0) + np.where(np.isinf(u), lm, 0.0)
+    primal = float(c @ x)
+    lfin = np.isfinite(l)
+    ufin = np.isfinite(u)
+    dual = float(q @ y + l[lfin] @ lp_[lfin] - u[ufin] @ lm[ufin])
+    nrp = float(np.linalg.norm(r_p))
+    nrd = float(np.linalg.norm(r_d))
+    gap = abs(primal - dual)
+    return KKT(primal, dual, nrp, nrd, gap,
+               nrp / (1.0 + float(np.linalg.norm(q))),
+               nrd / (1.0 + float(np.linalg.norm(c))),
+               gap / (1.0 + abs(primal) + abs(dual)))
+
+
+def kkt_original(lp, x, y_orig) -> KKT:
+    """Part I residuals on the original data, y in the caller's sign convention.
+
+    Convention: y_i <= 0 on <=-rows, y_i >= 0 on >=-rows, free on =-rows,
+    reduced costs lambda = c - A^T y (the signs the Dual / RedCost fixing
+    strategies of section 2 consume).  x is first clipped to [l, u] and y to
+    its cone, as every PDLP iterate already is.
+    """
+    k, q, is_eq, s = canonicalize(lp)
+    x = proj_box(np.asarray(x, dtype=np.float64), lp.l, lp.u)
+    y = proj_dual(s * np.asarray(y_orig, dtype=np.float64), is_eq)
+    return kkt_canonical(k, q, is_eq, lp.c, lp.l, lp.u, x, y)
+
+
+# ---------------------------------------------------------------- solver ---
+@dataclass
+class Params:
+    tol: float = 1e-4
+    iter_limit: int = 100_000
+    time_limit_s: float = float("inf")
+    check_period: int = 64
+    ruiz_iters: int = 10
+    pc_alpha: float | None = 1.0
+    adaptive: bool = True           # A6; False = every step accepted with fixed eta
+    restarts: bool = True           # A9/A10
+    fixed_eta: float | None = None  # overrides eta0 (fixed-step mode)
+    fixed_omega: float | None = None  # overrides omega0
+    terminate: bool = True          # stop at tol (False: run to iter_limit)
+    beta_suff: float = 0.2
+    beta_nec: float = 0.8
+    beta_art: float = 0.36
+    omega_smooth: float = 0.5
+
+
+@dataclass
+class Result:
+    status: int
+    iters: int          # accepted iterations
+    attempts: int       # all step attempts (k)
+    restarts: int
+    x: np.ndarray       # chosen output, unscaled
+    y: np.ndarray       # chosen output, unscaled, caller sign convention
+    kkt: KKT
+    x_cur: np.ndarray   # unscaled current iterate
+    y_cur: np.ndarray
+    x_avg: np.ndarray   # unscaled average iterate (current iterate if the average is empty)
+    y_avg: np.ndarray
+    eta: float
+    omega: float
+    used_average: bool
+    solve_s: float
+    trace: list = field(default_factory=list)
+
+
+def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
+    """PDLP (A0-A11) in FP64, step by step as listed in the module docstring."""
+    p = params or Params()
+    t0 = time.perf_counter()
+    # A0
+    k, q, is_eq, s = canonicalize(lp)
+    # A2
+    dr, dc = ruiz_pock_chambolle(k, p.ruiz_iters, p.pc_alpha)
+    kt = sp.csr_matrix(sp.diags(dr) @ k @ sp.diags(dc))
+    ktt = sp.csr_matrix(kt.T)
+    ct = dc * lp.c
+    qt = dr * q
+    lt = lp.l / dc
+    ut = lp.u / dc
+    # A3
+    if x0 is None:
+        x = proj_box(np.zeros(lp.n), lt, ut)
+    else:
+        x = proj_box(np.asarray(x0, dtype=np.float64) / dc, lt, ut)
+    if y0 is None:
+        y = np.zeros(lp.m)
+    else:
+        y = proj_dual(s * np.asarray(y0, dtype=np.float64) / dr, is_eq)
+    nc, nq = float(np.linalg.norm(ct)), float(np.linalg.norm(qt))
+    omega = nc / nq if (nc > 1e-10 and nq > 1e-10) else 1.0
+    kmax = float(abs(kt).max()) if kt.nnz else 0.0
+    eta = 1.0 / kmax if kmax > 0 else 1.0
+    if p.fixed_eta is not None:
+        eta = p.fixed_eta
+    if p.fixed_omega is not None:
+        omega = p.fixed_omega
+
+    def scaled_kkt(xs, ys):
+        return kkt_canonical(kt, qt, is_eq, ct, lt, ut, xs, ys)
+
+    def unscaled_kkt(xs, ys):
+        return kkt_canonical(k, q, is_eq, lp.c, lp.l, lp.u, dc * xs, dr * ys)
+
+    attempts = 0
+    it = 0
+    restarts = 0
+    sum_x = np.zeros(lp.n)
+    sum_y = np.zeros(lp.m)
+    sum_w = 0.0
+    x_last, y_last = x.copy(), y.copy()
+    kkt_last = scaled_kkt(x, y)          # "last restart" KKT starts at z0
+    kkt_prev_cand = math.inf
+    last_restart_it = 0
+    status = STATUS_ITER_LIMIT
+    trace = []
+    chosen_avg = False
+    chosen_kkt = None
+
+    def average():
+        if sum_w > 0:
+            return sum_x / sum_w, sum_y / sum_w
+        return x, y
+
+    while it < p.iter_limit:
+        attempts += 1
+        # A4: primal step
+        x_new = proj_box(x - (eta / omega) * (ct - ktt @ y), lt, ut)
+        # A5: dual step with extrapolation 2x' - x
+        y_new = proj_dual(y + eta * omega * (qt - kt @ (2.0 * x_new - x)), is_eq)
+        eta_used = eta
+        if p.adaptive:
+            # A6
+            dx = x_new - x
+            dy = y_new - y
+            denom = 2.0 * abs(float(dy @ (kt @ dx)))
+            num = omega * float(dx @ dx) + float(dy @ dy) / omega
+            eta_bar = num / denom if denom > 0 else math.inf
+            eta_next = min((1.0 - (attempts + 1) ** -0.3) * eta_bar,
+                           (1.0 + (attempts + 1) ** -0.6) * eta)
+            if eta > eta_bar:
+                trace.append(("reject", attempts, eta, eta_bar))
+                eta = eta_next
+                continue
+            eta = eta_next
+        # accept; A7 running sums weighted by the step that produced the iterate
+        x, y = x_new, y_new
+        sum_x += eta_used * x
+        sum_y += eta_used * y
+        sum_w += eta_used
+        it += 1
+        last = it >= p.iter_limit
+        if it % p.check_period == 0 or last:
+            # A8
+            xa, ya = average()
+            kc = unscaled_kkt(x, y)
+            ka = unscaled_kkt(xa, ya)
+            chosen_avg = ka.rel_kkt < kc.rel_kkt
+            chosen_kkt = ka if chosen_avg else kc
+            trace.append(("check", it, kc.rel_kkt, ka.rel_kkt, eta, omega))
+            if p.terminate and chosen_kkt.rel_kkt <= p.tol:
+                status = STATUS_OPTIMAL
+                break
+            if time.perf_counter() - t0 > p.time_limit_s:
+                status = STATUS_TIME_LIMIT
+                break
+            if last:
+                break
+            if p.restarts:
+                # A9
+                sc = scaled_kkt(x, y)
+                sa = scaled_kkt(xa, ya)
+                mc, ma = sc.kkt_omega(omega), sa.kkt_omega(omega)
+                use_avg = ma < mc
+                cand_x, cand_y = (xa, ya) if use_avg else (x, y)
+                cand_k = sa if use_avg else sc
+                m_cand = ma if use_avg else mc
+                m_last = kkt_last.kkt_omega(omega)
+                do_restart = (m_cand <= p.beta_suff * m_last
+                              or (m_cand <= p.beta_nec * m_last and m_cand > kkt_prev_cand)
+                              or (it - last_restart_it) >= p.beta_art * it)
+                if do_restart:
+                    # A10
+                    ddx = float(np.linalg.norm(cand_x - x_last))
+                    ddy = float(np.linalg.norm(cand_y - y_last))
+                    if ddx > 1e-10 and ddy > 1e-10:
+                        omega = math.exp(p.omega_smooth * math.log(ddy / ddx)
+                                         + (1.0 - p.omega_smooth) * math.log(omega))
+                    x, y = cand_x.copy(), cand_y.copy()
+                    x_last, y_last = x.copy(), y.copy()
+                    kkt_last = cand_k
+                    kkt_prev_cand = math.inf
+                    last_restart_it = it
+                    sum_x[:] = 0.0
+                    sum_y[:] = 0.0
+                    sum_w = 0.0
+                    restarts += 1
+                    trace.append(("restart", it, bool(use_avg), omega))
+                else:
+                    kkt_prev_cand = m_cand
+    xa, ya = average()
+    if chosen_kkt is None:  # no check ran (iter_limit == 0)
+        chosen_kkt = unscaled_kkt(x, y)
+        chosen_avg = False
+    xo, yo = (xa, ya) if chosen_avg else (x, y)
+
+    def unscale_x(xs):
+        # A11: x = D_c x~, clipped to [l, u] so the rounding of D_c (l / D_c)
+        # cannot leave the box (reading)
+        return proj_box(dc * xs, lp.l, lp.u)
+
+    def unscale_y(ys):
+        # A11: y = D_r y~, then back to the caller's sign convention
+        return s * (dr * ys)
+
+    return Result(status, it, attempts, restarts,
+                  unscale_x(xo), unscale_y(yo), chosen_kkt,
+                  unscale_x(x), unscale_y(y), unscale_x(xa), unscale_y(ya),
+                  eta, omega, chosen_avg, time.perf_counter() - t0, trace)

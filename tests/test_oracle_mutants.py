@@ -1,0 +1,84 @@
+"""Plant plausible mistakes in a copy of the oracle and check that a pin catches each.
+
+Each mutant is the oracle's source with one textual change, executed as a
+fresh module on the CPU; the named pins from ``test_oracle_pins`` are re-run
+against it and at least one of them must fail.  Nothing here touches a GPU.
+"""
+import os
+import sys
+import types
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as P
+
+ORACLE_SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                          "oracle", "pdlp_oracle.py")
+
+MUTANTS = [
+    ("extrapolation 2x'-x dropped", "kt @ (2.0 * x_new - x)", "kt @ x_new",
+     ["test_one_pdhg_step_by_hand"]),
+    ("<=-row sign flip applied to >=-rows", "np.where(lp.sense == SENSE_LE, -1.0, 1.0)",
+     "np.where(lp.sense == SENSE_GE, -1.0, 1.0)", ["test_mip_relaxation_matches_highs"]),
+    ("upper-bound term of the dual objective with the wrong sign",
+     "- u[ufin] @ lm[ufin]", "+ u[ufin] @ lm[ufin]", ["test_kkt_by_hand_with_infinite_bounds"]),
+    ("dual residual charged on the wrong side of an infinite bound",
+     "np.where(np.isinf(l), lp_, 0.0) + np.where(np.isinf(u), lm, 0.0)",
+     "np.where(np.isinf(l), lm, 0.0) + np.where(np.isinf(u), lp_, 0.0)",
+     ["test_kkt_by_hand_with_infinite_bounds"]),
+    ("step-size growth exponent -0.6 replaced by -0.3", "(1.0 + (attempts + 1) ** -0.6)",
+     "(1.0 + (attempts + 1) ** -0.3)", ["test_step_growth_when_eta_bar_is_infinite"]),
+    ("step-size shrink exponent -0.3 replaced by -0.6", "(1.0 - (attempts + 1) ** -0.3)",
+     "(1.0 - (attempts + 1) ** -0.6)", ["test_adaptive_step_rule_by_hand"]),
+    ("Ruiz factor without the square root", "r = np.where(rmax > 0, np.sqrt(rmax), 1.0)",
+     "r = np.where(rmax > 0, rmax, 1.0)", ["test_ruiz_on_powers_of_four_gives_identity_exactly"]),
+    ("primal step with tau = eta * omega", "(eta / omega) * (ct - ktt @ y)",
+     "(eta * omega) * (ct - ktt @ y)", ["test_one_pdhg_step_by_hand"]),
+    ("dual projection clips equality rows", "np.where(is_eq, y, np.maximum(y, 0.0))",
+     "np.maximum(y, 0.0)", ["test_one_pdhg_step_by_hand"]),
+    ("unweighted average", "sum_x += eta_used * x", "sum_x += x",
+     ["test_average_is_step_size_weighted"]),
+    ("primal residual ignores violated >=-rows", "np.maximum(q - kx, 0.0)", "np.minimum(q - kx, 0.0)",
+     ["test_kkt_primal_residual_senses_by_hand"]),
+]
+
+
+def _mutant_module(old, new):
+    src = open(ORACLE_SRC).read()
+    assert src.count(old) >= 1, old
+    name = "pdlp_oracle_mutant"
+    mod = types.ModuleType(name)
+    mod.__file__ = ORACLE_SRC
+    sys.modules[name] = mod  # dataclasses look their module up here
+    try:
+        exec(compile(src.replace(old, new), ORACLE_SRC, "exec"), mod.__dict__)
+    finally:
+        del sys.modules[name]
+    return mod
+
+
+@pytest.mark.parametrize("desc,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(desc, old, new, pins, monkeypatch):
+    mutant = _mutant_module(old, new)
+    monkeypatch.setattr(P, "O", mutant)
+    caught = []
+    for name in pins:
+        fn = getattr(P, name)
+        params = {}
+        if name == "test_mip_relaxation_matches_highs":
+            params = {"seed": 1}
+        try:
+            fn(**params)
+        except Exception:  # an assertion, or the mutant breaking outright
+            caught.append(name)
+    assert caught, f"mutant '{desc}' passed every pin in {pins}"
+
+
+def test_unmutated_copy_passes_the_same_pins(monkeypatch):
+    """Control: the exec'd copy without a change passes the pins used above."""
+    mod = _mutant_module("import math", "import math")
+    monkeypatch.setattr(P, "O", mod)
+    for _, _, _, pins in MUTANTS:
+        for name in pins:
+            getattr(P, name)(**({"seed": 1} if name == "test_mip_relaxation_matches_highs" else {}))

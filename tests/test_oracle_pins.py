@@ -1,0 +1,292 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a hand-computed worked example,
+a closed form, an exact brute-force optimum, an independent library solver
+(HiGHS), or an invariant of the LP.  Together they are chosen so that a
+plausible slip in the oracle (a dropped extrapolation term, a wrong dual sign,
+a transposed operand, a wrong bound term in the dual objective) fails at least
+one of them; ``test_oracle_mutants.py`` plants such slips to show it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import pdlp_oracle as O
+from oracle import reference_lp as R
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _lp_from_dense(a, b, sense, c, l, u):
+    a = np.asarray(a, dtype=np.float64)
+    m, n = a.shape
+    rows, cols = np.nonzero(a)
+    return lpgen._lp(m, n, rows, cols, a[rows, cols], np.asarray(b, float),
+                     np.array([ord(s) for s in sense], dtype=np.uint8), np.asarray(c, float),
+                     np.asarray(l, float), np.asarray(u, float), np.zeros(n, np.uint8), "hand")
+
+
+# ---------------------------------------------------------------- worked example
+def _two_by_two():
+    # row 0: -x0 - 2 x1 <= -1  (canonical: x0 + 2 x1 >= 1)
+    # row 1:  3 x0 + 4 x1  = 2
+    return _lp_from_dense([[-1, -2], [3, 4]], [-1, 2], "LE", [1, -1], [0, 0], [10, 1.2])
+
+
+NOSCALE = dict(ruiz_iters=0, pc_alpha=None, restarts=False, terminate=False)
+
+
+def test_one_pdhg_step_by_hand():
+    """One PDHG step (A4/A5) with eta = 0.1, omega = 2, worked by hand.
+
+    x = (1, 1), y_K = (0.5, 1)  [caller convention y = (-0.5, 1)]; tau = 0.05, sigma = 0.2
+    K^T y = (1*0.5 + 3*1, 2*0.5 + 4*1) = (3.5, 5);  c - K^T y = (-2.5, -6)
+    x - tau g = (1.125, 1.3) -> clip to u = (10, 1.2) -> x' = (1.125, 1.2)
+    2x' - x = (1.25, 1.4);  K(2x' - x) = (1.25 + 2.8, 3.75 + 5.6) = (4.05, 9.35)
+    q - that = (-3.05, -7.35);  y + sigma (...) = (0.5 - 0.61, 1 - 1.47) = (-0.11, -0.47)
+    row 0 is an inequality -> max(-0.11, 0) = 0; row 1 is free -> -0.47
+    y_K' = (0, -0.47) -> caller convention (-0, -0.47)
+    """
+    lp = _two_by_two()
+    r = O.solve(lp, O.Params(iter_limit=1, adaptive=False, fixed_eta=0.1, fixed_omega=2.0,
+                             **NOSCALE), x0=[1.0, 1.0], y0=[-0.5, 1.0])
+    assert r.iters == 1
+    np.testing.assert_allclose(r.x_cur, [1.125, 1.2], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r.y_cur, [0.0, -0.47], rtol=0, atol=1e-15)
+    # the average of a single accepted iterate is that iterate
+    np.testing.assert_allclose(r.x_avg, r.x_cur, rtol=0, atol=1e-15)
+
+
+def test_adaptive_step_rule_by_hand():
+    """A6 on the same step: dx = (0.125, 0.2), dy = (0 - 0.5, -0.47 - 1) = (-0.5, -1.47).
+
+    K dx = (0.125 + 0.4, 0.375 + 0.8) = (0.525, 1.175)
+    dy^T K dx = -0.2625 - 1.72725 = -1.98975 -> denominator 2 * 1.98975 = 3.9795
+    numerator = 2 * (0.015625 + 0.04) + (0.25 + 2.1609) / 2 = 0.11125 + 1.20545 = 1.3167
+    eta_bar = 1.3167 / 3.9795 = 0.33087071240...  >= eta = 0.1  -> accepted
+    eta_next = min((1 - 2^-0.3) eta_bar, (1 + 2^-0.6) 0.1)
+             = min(0.1877476 * 0.3308707, 0.1659754) = 0.0621201833692...
+    """
+    lp = _two_by_two()
+    r = O.solve(lp, O.Params(iter_limit=1, adaptive=True, fixed_eta=0.1, fixed_omega=2.0,
+                             **NOSCALE), x0=[1.0, 1.0], y0=[-0.5, 1.0])
+    assert r.attempts == 1 and r.iters == 1
+    assert r.eta == pytest.approx(0.06212018336920332, rel=1e-13)
+
+
+def test_adaptive_step_rejects_large_eta_and_retries_from_the_same_point():
+    """With eta = 50 (far above 1/||K~||) the first attempt is rejected.  The retry
+    starts from the same (x, y), so the accepted iterate equals the one a run
+    started directly with the retried step size produces (attempt counter aside)."""
+    lp = lpgen.mip_relaxation(1)
+    r = O.solve(lp, O.Params(iter_limit=1, fixed_eta=50.0, terminate=False))
+    assert r.iters == 1 and r.attempts == 2
+    rej = [t for t in r.trace if t[0] == "reject"]
+    assert len(rej) == 1 and rej[0][2] == 50.0 and rej[0][3] < 50.0
+    eta_retry = min((1 - 2 ** -0.3) * rej[0][3], (1 + 2 ** -0.6) * 50.0)
+    r2 = O.solve(lp, O.Params(iter_limit=1, fixed_eta=eta_retry, adaptive=False,
+                              terminate=False))
+    np.testing.assert_array_equal(r.x_cur, r2.x_cur)
+    np.testing.assert_array_equal(r.y_cur, r2.y_cur)
+
+
+# ---------------------------------------------------------------- scaling
+def test_ruiz_on_powers_of_four_gives_identity_exactly():
+    """Ruiz on diag(4, 16, 64): r = s = (2, 4, 8) in the first pass, so K~ = I exactly,
+    and every later pass and the Pock-Chambolle pass (unit row/column sums) keep it."""
+    k = O.sp.csr_matrix(np.diag([4.0, 16.0, 64.0]))
+    dr, dc = O.ruiz_pock_chambolle(k, 10, 1.0)
+    np.testing.assert_array_equal(dr, [0.5, 0.25, 0.125])
+    np.testing.assert_array_equal(dc, [0.5, 0.25, 0.125])
+    kt = (O.sp.diags(dr) @ k @ O.sp.diags(dc)).toarray()
+    np.testing.assert_array_equal(kt, np.eye(3))
+
+
+def test_pock_chambolle_sums_by_hand():
+    """PC (alpha=1) without Ruiz on [[1,0,3],[0,9,0],[2,0,2]]:
+    row sums (4, 9, 4) -> D_r = (1/2, 1/3, 1/2); column sums (3, 9, 5) -> D_c = (1/sqrt3, 1/3, 1/sqrt5)."""
+    k = O.sp.csr_matrix(np.array([[1.0, 0, 3], [0, 9, 0], [2, 0, 2]]))
+    dr, dc = O.ruiz_pock_chambolle(k, 0, 1.0)
+    np.testing.assert_allclose(dr, [0.5, 1 / 3, 0.5], rtol=1e-15)
+    np.testing.assert_allclose(dc, [1 / math.sqrt(3), 1 / 3, 1 / math.sqrt(5)], rtol=1e-15)
+
+
+def test_ruiz_zero_row_and_column_get_factor_one():
+    k = O.sp.csr_matrix(np.array([[0.0, 0, 0], [0, 4, 0], [0, 0, 0]]))
+    dr, dc = O.ruiz_pock_chambolle(k, 3, None)
+    assert dr[0] == 1.0 and dr[2] == 1.0 and dc[0] == 1.0 and dc[2] == 1.0
+    assert dr[1] * 4 * dc[1] == 1.0
+
+
+# ---------------------------------------------------------------- KKT (Part I)
+def test_kkt_by_hand_with_infinite_bounds():
+    """min x0 + 2 x1 - x2  s.t. x0 + x1 + x2 >= 1; x0 free, x1 in [0, inf), x2 in [0, 2].
+    At x = (1, 0, 0), y = 0.5: lambda = c - A^T y = (0.5, 1.5, -1.5).
+    r_d = (|0.5| for the free column, 0, 0) -> ||r_d|| = 0.5, ||c|| = sqrt(6).
+    primal = 1; dual = q y + l1 lambda1+ - u2 lambda2- = 0.5 + 0 - 2*1.5 = -2.5.
+    rel_p = 0, rel_d = 0.5 / (1 + sqrt 6), rel_gap = 3.5 / (1 + 1 + 2.5)."""
+    lp = _lp_from_dense([[1, 1, 1]], [1], "G", [1, 2, -1], [-np.inf, 0, 0], [np.inf, np.inf, 2])
+    k = O.kkt_original(lp, [1.0, 0.0, 0.0], [0.5])
+    assert k.primal_obj == 1.0 and k.dual_obj == -2.5
+    assert k.rel_p == 0.0
+    assert k.rel_d == pytest.approx(0.5 / (1 + math.sqrt(6)), rel=1e-15)
+    assert k.rel_gap == pytest.approx(3.5 / 4.5, rel=1e-15)
+
+
+def test_kkt_primal_residual_senses_by_hand():
+    """x = (1, 1): row L: 2 <= 1 violated by 1; row G: 2 >= 3 violated by 1;
+    row E: 2 = 2.5 off by 0.5 -> ||r_p|| = 1.5, ||q|| = ||(-1, 3, 2.5)||."""
+    lp = _lp_from_dense([[1, 1], [1, 1], [1, 1]], [1, 3, 2.5], "LGE", [0, 0], [0, 0], [5, 5])
+    k = O.kkt_original(lp, [1.0, 1.0], [0.0, 0.0, 0.0])
+    assert k.r_p == pytest.approx(1.5, rel=1e-15)
+    assert k.rel_p == pytest.approx(1.5 / (1 + math.sqrt(1 + 9 + 6.25)), rel=1e-15)
+
+
+@pytest.mark.parametrize("maker", [lambda: lpgen.mip_relaxation(1),
+                                   lambda: lpgen.random_sparse_lp(7, 40, 60),
+                                   lambda: lpgen.random_sparse_lp(8, 30, 50, free_frac=0.2)])
+def test_kkt_vanishes_at_highs_optimum(maker):
+    """At HiGHS's primal-dual optimum all three relative measures are ~0.
+    This pins the dual sign convention and the bound terms of the dual objective."""
+    lp = maker()
+    obj, x, y, lam = R.highs(lp)
+    k = O.kkt_original(lp, x, y)
+    assert k.rel_p < 1e-9 and k.rel_d < 1e-9 and k.rel_gap < 1e-9
+    assert k.primal_obj == pytest.approx(obj, rel=1e-12)
+
+
+# ---------------------------------------------------------------- exact optima
+@pytest.mark.parametrize("seed", range(8))
+def test_tiny_lp_matches_vertex_enumeration(seed):
+    lp = lpgen.tiny_lp(seed, m=5 + seed % 2, n=4 + seed % 2, eq_rows=seed % 2)
+    best, verts = R.vertex_enumeration(lp)
+    r = O.solve(lp, O.Params(tol=1e-10, iter_limit=400_000))
+    assert r.status == O.STATUS_OPTIMAL
+    assert r.kkt.primal_obj == pytest.approx(best, rel=1e-7, abs=1e-7)
+    if len(verts) == 1 or np.ptp(np.array(verts), axis=0).max() < 1e-9:
+        np.testing.assert_allclose(r.x, verts[0], atol=1e-5)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_mip_relaxation_matches_highs(seed):
+    lp = lpgen.mip_relaxation(seed)
+    obj, _, _, _ = R.highs(lp)
+    r = O.solve(lp, O.Params(tol=1e-8))
+    assert r.status == O.STATUS_OPTIMAL
+    assert r.kkt.rel_kkt <= 1e-8
+    assert abs(r.kkt.primal_obj - obj) / (1 + abs(obj)) < 1e-7
+
+
+def test_random_lp_with_free_columns_matches_highs_primal_and_dual():
+    lp = lpgen.random_sparse_lp(11, 30, 45, free_frac=0.15)
+    obj, xh, yh, lamh = R.highs(lp)
+    r = O.solve(lp, O.Params(tol=1e-10, iter_limit=500_000))
+    assert r.status == O.STATUS_OPTIMAL
+    assert abs(r.kkt.primal_obj - obj) / (1 + abs(obj)) < 1e-8
+    # the oracle's dual is a dual optimum: its own KKT and HiGHS's objective agree
+    assert abs(r.kkt.dual_obj - obj) / (1 + abs(obj)) < 1e-8
+
+
+def test_small_energy_system_matches_highs():
+    lp = lpgen.energy_system(hours=24, regions=5, lines=6, techs=3, thermal=2)
+    obj, _, _, _ = R.highs(lp)
+    r = O.solve(lp, O.Params(tol=1e-7, iter_limit=400_000))
+    assert r.status == O.STATUS_OPTIMAL
+    assert abs(r.kkt.primal_obj - obj) / (1 + abs(obj)) < 1e-5
+
+
+# ---------------------------------------------------------------- closed forms
+def test_no_row_lp_closed_form():
+    """With no rows the LP separates: x_j = l_j if c_j > 0, u_j if c_j < 0, proj(0) if c_j = 0."""
+    n = 6
+    c = np.array([1.0, -2.0, 0.0, 3.0, -0.5, 0.0])
+    l = np.array([-1.0, 0.0, 0.5, -3.0, 2.0, -4.0])
+    u = np.array([1.0, 2.0, 1.0, 5.0, 7.0, -1.0])
+    lp = lpgen._lp(0, n, np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), np.zeros(0),
+                   np.zeros(0, np.uint8), c, l, u, np.zeros(n, np.uint8), "norows")
+    r = O.solve(lp, O.Params(tol=1e-12))
+    assert r.status == O.STATUS_OPTIMAL
+    np.testing.assert_array_equal(r.x, [-1.0, 2.0, 0.5, -3.0, 7.0, -1.0])
+
+
+# ---------------------------------------------------------------- invariants
+def test_iterates_stay_in_bounds_and_cone_every_step():
+    lp = lpgen.random_sparse_lp(3, 25, 40)
+    is_eq = lp.sense == ord("E")
+    for it in (1, 2, 3, 17, 64, 65, 200):
+        r = O.solve(lp, O.Params(iter_limit=it, terminate=False))
+        assert np.all(r.x_cur >= lp.l) and np.all(r.x_cur <= lp.u)
+        assert np.all(r.x_avg >= lp.l - 1e-12) and np.all(r.x_avg <= lp.u + 1e-12)
+        yle = r.y_cur[lp.sense == ord("L")]
+        yge = r.y_cur[lp.sense == ord("G")]
+        assert np.all(yle <= 0) and np.all(yge >= 0)
+        assert r.y_cur[is_eq].size == is_eq.sum()
+
+
+def test_weak_duality_at_convergence():
+    lp = lpgen.mip_relaxation(4)
+    r = O.solve(lp, O.Params(tol=1e-6))
+    k = r.kkt
+    # with primal/dual feasibility at 1e-6 the dual bound sits below the primal
+    assert k.dual_obj <= k.primal_obj + 1e-5 * (1 + abs(k.primal_obj))
+
+
+def test_row_and_column_rescaling_keeps_the_solution():
+    """Scaling row i by p_i > 0 and substituting x_j = z_j * t_j leaves the LP optimum unchanged."""
+    lp = lpgen.mip_relaxation(5, m=60, n=120, density=0.06)
+    rng = np.random.default_rng(0)
+    p = rng.uniform(0.1, 10, size=lp.m)
+    t = rng.uniform(0.1, 10, size=lp.n)
+    rows = np.repeat(np.arange(lp.m), np.diff(lp.row_ptr))
+    lp2 = lpgen._lp(lp.m, lp.n, rows, lp.col, lp.val * p[rows] * t[lp.col], lp.b * p, lp.sense,
+                    lp.c * t, lp.l / t, lp.u / t, lp.is_int, "rescaled")
+    r1 = O.solve(lp, O.Params(tol=1e-8))
+    r2 = O.solve(lp2, O.Params(tol=1e-8))
+    assert r1.kkt.primal_obj == pytest.approx(r2.kkt.primal_obj, rel=1e-6)
+
+
+def test_looser_tolerance_never_needs_more_iterations():
+    lp = lpgen.mip_relaxation(6)
+    its = [O.solve(lp, O.Params(tol=t)).iters for t in (1e-2, 1e-4, 1e-6, 1e-8)]
+    assert its == sorted(its)
+
+
+def test_fixed_step_mode_accepts_every_attempt():
+    lp = lpgen.mip_relaxation(1)
+    r = O.solve(lp, O.Params(iter_limit=100, adaptive=False, restarts=False, terminate=False))
+    assert r.iters == r.attempts == 100 and r.restarts == 0
+
+
+def test_average_is_step_size_weighted():
+    """A7: with the adaptive rule the two accepted steps use different step sizes
+    eta_1 (given) and eta_2 (chosen after step 1); the average after two steps
+    is (eta_1 x_1 + eta_2 x_2) / (eta_1 + eta_2), x_1 and x_2 taken from runs
+    stopped after one and two iterations."""
+    lp = lpgen.mip_relaxation(2)
+    p1 = O.Params(iter_limit=1, fixed_eta=0.05, terminate=False, restarts=False)
+    p2 = O.Params(iter_limit=2, fixed_eta=0.05, terminate=False, restarts=False)
+    r1 = O.solve(lp, p1)
+    r2 = O.solve(lp, p2)
+    assert r1.attempts == 1 and r2.attempts == 2  # no rejection in either step
+    eta1, eta2 = 0.05, r1.eta
+    assert abs(eta2 - eta1) > 1e-3 * eta1
+    expect = (eta1 * r1.x_cur + eta2 * r2.x_cur) / (eta1 + eta2)
+    np.testing.assert_allclose(r2.x_avg, expect, rtol=1e-12, atol=1e-12)
+
+
+def test_step_growth_when_eta_bar_is_infinite():
+    """With no rows dy = 0, so dy^T K dx = 0 and eta_bar = inf: every attempt is
+    accepted and eta grows by (1 + (k+1)^-0.6) per step (A6).
+    From eta = 1: after one step 1 + 2^-0.6 = 1.6597539553864471; after two,
+    (1 + 2^-0.6)(1 + 3^-0.6) = 1.6597539553864471 * 1.5172818579717866
+    (3^0.6 = e^(0.6 ln 3) = e^0.6591674 = 1.9331820...)."""
+    n = 3
+    lp = lpgen._lp(0, n, np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), np.zeros(0),
+                   np.zeros(0, np.uint8), np.array([1.0, -1.0, 0.5]), np.full(n, -1e3),
+                   np.full(n, 1e3), np.zeros(n, np.uint8), "norows")
+    r1 = O.solve(lp, O.Params(iter_limit=1, fixed_eta=1.0, terminate=False, restarts=False))
+    r2 = O.solve(lp, O.Params(iter_limit=2, fixed_eta=1.0, terminate=False, restarts=False))
+    assert r1.eta == pytest.approx(1.6597539553864471, rel=1e-15)
+    assert r2.eta == pytest.approx(1.6597539553864471 * 1.5172818579717866, rel=1e-14)
