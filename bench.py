@@ -1,0 +1,286 @@
+"""Benchmark: PDLP solve of the set-cover LP relaxation to relative KKT <= 1e-4 on GB300.
+
+Workload (one "step" = one whole solve, rows A0-A11 of the hot path: device
+setup, scaling, iterations, KKT checks, output): the covering LP with
+m = 50,000 >=-rows (b = 1), n = 200,000 columns in [0, 1], each covering 3-10
+uniformly chosen rows (1,296,541 nonzeros, all 1), integer costs U[1,100],
+seed 2025; synthetic, generated by ``lpgen.set_cover``.  The main arm runs the
+float32 path (matrix stored as a bare pattern, every value being 1), next to
+the plain float64 path on the same instance.
+
+Printed: one JSON line (rank 0).  ``value`` = accepted PDHG iterations per
+second over the whole job (all ranks), ``ms_per_step`` = time to tolerance.
+With N > 1 processes (torchrun) every rank solves its own replica: a single LP
+does not shard without an exchange per half step, so this is replicas only.
+
+``--impl reference`` times the float64 CPU oracle (the reference arm) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel. KKT≤1e-4 and PDHG iters/s vs plain FP64 PDLP, 1×GB300"
+UNIT = "PDHG iters/s"
+WORKLOAD = "set_cover m=50000 n=200000 nnz=1296541 seed=2025 tol=1e-4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=400)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = [float(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(rows),
+                "reasons": reasons}
+
+
+# ------------------------------------------------------------------ CPU oracle
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import lpgen
+from oracle import pdlp_oracle as O
+lp = lpgen.set_cover(2025)
+t = time.perf_counter()
+r = O.solve(lp, O.Params(iter_limit={iters}, terminate=False, check_period=64))
+dt = time.perf_counter() - t
+print(json.dumps({{"iters": r.iters, "seconds": dt}}))
+"""
+
+
+def cpu_oracle_sample(iters: int) -> dict:
+    """The float64 oracle, as it stands, on the full workload for a bounded number of
+    iterations, single-threaded (numpy/scipy with one BLAS thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, iters=iters)],
+                         capture_output=True, text=True, env=env, check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['iters']} accepted iterations of the float64 oracle (scaling included) "
+                      f"on the full workload, {d['seconds']:.1f} s"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_oracle_sample(args.cpu_sample_iters)
+        if i >= args.warmup:
+            steps.append(s)
+    it_s = statistics.mean(s["value"] for s in steps)
+    line = {"impl": "reference", "metric": METRIC, "value": it_s, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * args.cpu_sample_iters / it_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 oracle (numpy/scipy)",
+                       "sample": f"{args.cpu_sample_iters} iterations per step"},
+            "cpu_baseline": {"value": it_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": steps[-1]["sample"]},
+            "e2e": {"value": it_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__ as G
+    G.build()
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    lp = lpgen.set_cover(2025)
+    d = P.DeviceLP(lp, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def timed_solves(prm, steps, warmup):
+        wsz = P.workspace_size(lp.m, lp.n, lp.nnz, prm)
+        wbuf = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
+        xo = torch.empty(lp.n, dtype=torch.float64, device=dev)
+        yo = torch.empty(lp.m, dtype=torch.float64, device=dev)
+        for _ in range(warmup):
+            P.pdlp_solve_device(d, prm, x_out=xo, y_out=yo, workspace=wbuf, stream=stream)
+        ms, iters, launches, res = [], 0, 0, None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        for k in range(steps):
+            flush.fill_(float(k))  # L2 flush between timed solves, outside the events
+            ev[k][0].record(stream)
+            _, _, res = P.pdlp_solve_device(d, prm, x_out=xo, y_out=yo, workspace=wbuf, stream=stream)
+            ev[k][1].record(stream)
+            iters += res["iters"]
+            launches += res["kernel_launches"]
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, iters, launches, res, (xo, yo)
+
+    prm = P.default_params(tol=1e-4, precision=args.precision)
+    with ClockSampler(dev.index) as clk:
+        ms, iters, launches, res, (xo, yo) = timed_solves(prm, args.steps, args.warmup)
+    clocks = clk.summary()
+    total_s = sum(ms) / 1e3
+    # max over ranks of the timed region, units summed over ranks
+    t_local = torch.tensor([total_s, float(iters)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        tmax = t_local.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t_local.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_s, all_iters = float(tmax[0]), float(tsum[1])
+    else:
+        all_iters = float(iters)
+    value = all_iters / total_s
+
+    # plain float64 PDLP on the same instance (the comparison line)
+    ms64, it64, l64, res64, _ = timed_solves(P.default_params(tol=1e-4, precision="fp64"),
+                                             max(1, min(args.steps, 3)), 1)
+    # end to end through the host C ABI: host buffers, copies inside the timed region
+    e2e_t, e2e_it = 0.0, 0
+    for k in range(args.steps + 1):
+        t0 = time.perf_counter()
+        _, _, r = P.pdlp_solve(lp, prm)
+        dt = time.perf_counter() - t0
+        if k > 0:  # first call warms the host path
+            e2e_t += dt
+            e2e_it += r["iters"]
+    h2d = 8 * (lp.m + 1) + 12 * lp.nnz + 9 * lp.m + 24 * lp.n
+    d2h = 8 * (lp.n + lp.m)
+    # roofline of the dominant kernel, timed live with CUDA events on this stream
+    kt = P.time_kernels(d, prm, reps=200, stream=stream)
+    import json as _j
+    peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    dom = max(("primal_step", "dual_step"), key=lambda k: kt[k]["ms"])
+    ach = kt[dom]["bytes"] / (kt[dom]["ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": None,
+            "peak_source": "measured" if peaks else "fallback",
+            "kernels": {k: {"us": 1e3 * v["ms"], "bytes": v["bytes"],
+                            "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9} for k, v in kt.items()}}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample(args.cpu_sample_iters)
+        except Exception as e:  # reported, never silently replaced
+            cpu = {"error": str(e)[:200]}
+    if rank == 0:
+        prec_used = {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
+                     3: "fp32 iterates, pattern matrix"}[res["precision_used"]]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": prec_used, "l2_flush": True,
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "lanes": "auto"},
+            "time_to_tol_s": total_s / args.steps,
+            "iters_per_solve": iters / args.steps,
+            "status": res["status"], "rel_kkt": res["rel_kkt"], "primal_obj": res["primal_obj"],
+            "fp64_baseline": {"time_to_tol_s": sum(ms64) / 1e3 / len(ms64),
+                              "iters_per_s": it64 / (sum(ms64) / 1e3),
+                              "iters_per_solve": it64 / len(ms64), "rel_kkt": res64["rel_kkt"],
+                              "primal_obj": res64["primal_obj"]},
+            "speedup_vs_fp64_time_to_tol": (sum(ms64) / len(ms64)) / (sum(ms) / len(ms)),
+            "e2e": {"value": e2e_it / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

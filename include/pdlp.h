@@ -1,0 +1,225 @@
+/*
+ * pdlp.h -- C ABI of the GB300 (sm_103a) PDLP library.
+ *
+ * The library solves the LP relaxation of a MIP,
+ *
+ *     min c^T x   s.t.  row i of A x  (<=, >=, =)  b_i,   l <= x <= u,          (eq. 1)
+ *
+ * (Kempke & Koch, "Fix-and-Propagate Heuristics Using Low-Precision First-Order
+ * LP Solutions for Large-Scale MILP", section 1, eq. 1; the paper states the
+ * rows as A x <= b, the sense per row generalises that) with restarted,
+ * diagonally preconditioned PDHG ("PDLP", abstract and section 2) to a
+ * RELATIVE tolerance (section 4, "Hardware and software": relative primal,
+ * dual and gap tolerances; 1e-4 and 1e-6 are the paper's settings).  The
+ * solution then ranks and drives the fixings of the fix-and-propagate
+ * heuristic (section 2), exposed here as fp_run().
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are CSR: row_ptr[m+1] (int64, row_ptr[0] = 0, non-decreasing),
+ *    col[nnz] (int32, 0 <= col < n, no duplicate (row, col) pair), val[nnz]
+ *    (float64).  Column order inside a row is free.
+ *  - sense[m] holds the bytes 'L' (<=), 'G' (>=) or 'E' (=).
+ *  - Infinite bounds are +-INFINITY; l_j <= u_j is required.
+ *  - Dual sign convention of every output: y_i <= 0 on 'L' rows, y_i >= 0 on
+ *    'G' rows, free on 'E' rows; reduced costs are lambda = c - A^T y.  These
+ *    are the signs the Dual and RedCost fixing strategies (section 2) read.
+ *  - Ownership: the library owns nothing it returns.  Every output goes into a
+ *    caller-allocated buffer; inputs are only read (host inputs are copied to
+ *    the device, device inputs are read in place).
+ *  - Return codes: 0 (PDLP_OK) or a negative PDLP_ERR_* value.  The solver
+ *    outcome (tolerance met, iteration limit, ...) is pdlp_result.status,
+ *    never the return code.  pdlp_error_string() names every code.
+ *  - Reentrancy: calls share no mutable global state; concurrent calls on
+ *    different streams are independent.
+ *
+ * Relative KKT measures reported in pdlp_result (the definition every result
+ * is judged by), for x in [l,u] and y in the dual cone, on the original data:
+ *    r_p = violation of each row (only the violated side of inequalities),
+ *    r_d_j = lambda_j^+ if l_j = -inf  plus  lambda_j^- if u_j = +inf,
+ *    dual objective = b^T y + sum_{l_j finite} l_j lambda_j^+ - sum_{u_j finite} u_j lambda_j^-,
+ *    rel_primal_res = ||r_p||_2 / (1 + ||b||_2),  rel_dual_res = ||r_d||_2 / (1 + ||c||_2),
+ *    rel_gap = |c^T x - dual| / (1 + |c^T x| + |dual|),
+ *    rel_kkt = max of the three.  Status PDLP_OPTIMAL means rel_kkt <= tol.
+ */
+#ifndef PDLP_H
+#define PDLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define PDLP_OK 0
+#define PDLP_ERR_INVALID_INPUT (-1) /* bad CSR, NaN, l > u, unknown sense, bad params */
+#define PDLP_ERR_CUDA (-2)          /* a CUDA runtime call failed (message: pdlp_last_error) */
+#define PDLP_ERR_OOM (-3)           /* device allocation failed or workspace too small */
+#define PDLP_ERR_TIMEOUT (-4)       /* a bounded device-side wait gave up */
+#define PDLP_ERR_UNSUPPORTED (-5)   /* requested mode not available for this input */
+
+/* ---- solver outcome (pdlp_result.status) ----------------------------- */
+#define PDLP_OPTIMAL 1      /* rel_kkt <= tol */
+#define PDLP_ITER_LIMIT 2   /* iter_limit accepted iterations reached */
+#define PDLP_TIME_LIMIT 3   /* time_limit_s reached */
+#define PDLP_NUMERICAL 4    /* a NaN / Inf appeared in the iteration */
+
+/* ---- precision modes (pdlp_params.precision) -------------------------
+ * PDLP_FP64:      iterates, SpMV and reductions in float64 on the explicitly
+ *                 scaled matrix D_r K D_c (the parity mode).
+ * PDLP_FP32:      iterates, SpMV and accumulation in float32 on the scaled
+ *                 matrix stored in float32; KKT checks, restarts and the
+ *                 primal weight in float64 on the float64 data.
+ * PDLP_FP32_BF16A:float32 iterates on the UNSCALED matrix stored in bfloat16
+ *                 (or as a bare sparsity pattern when every value is 1),
+ *                 with the scaling folded into per-element step sizes
+ *                 tau_j = (eta/omega) D_c,j^2, sigma_i = eta omega D_r,i^2.
+ *                 Chosen only when every value is exactly representable in
+ *                 bfloat16; otherwise the solver falls back to PDLP_FP32 and
+ *                 reports it in pdlp_result.precision_used. */
+#define PDLP_FP64 0
+#define PDLP_FP32 1
+#define PDLP_FP32_BF16A 2
+/* values reported in pdlp_result.precision_used (PDLP_FP64/FP32 as above) */
+#define PDLP_USED_BF16 2
+#define PDLP_USED_PATTERN 3
+
+typedef struct {
+  int32_t m, n;
+  int64_t nnz;
+  const int64_t* row_ptr; /* [m+1] */
+  const int32_t* col;     /* [nnz] */
+  const double* val;      /* [nnz] */
+} pdlp_csr;
+
+typedef struct {
+  size_t struct_size;   /* sizeof(pdlp_params); set by pdlp_default_params */
+  double tol;           /* relative KKT tolerance, default 1e-4 */
+  int64_t iter_limit;   /* accepted PDHG iterations, default 1000000 */
+  double time_limit_s;  /* wall-clock limit of the iteration phase, default 3600 */
+  int precision;        /* PDLP_FP64 (default) | PDLP_FP32 | PDLP_FP32_BF16A */
+  int check_period;     /* accepted iterations between KKT checks, default 64 */
+  int ruiz_iters;       /* Ruiz equilibration passes, default 10 */
+  double pc_alpha;      /* Pock-Chambolle exponent, default 1; < 0 disables the pass */
+  int adaptive_step;    /* 1 (default): adaptive step-size rule; 0: fixed eta, every step accepted */
+  int restarts;         /* 1 (default): KKT-based restarts and primal-weight updates */
+  double fixed_eta;     /* > 0 overrides the initial step size eta0 */
+  double fixed_omega;   /* > 0 overrides the initial primal weight omega0 */
+  int terminate;        /* 1 (default): stop at tol; 0: run to iter_limit */
+  int lanes_A;          /* SpMV lanes per row of A (0 = automatic; 2,4,8,16,32) */
+  int lanes_AT;         /* SpMV lanes per row of A^T (0 = automatic) */
+  int verbose;          /* 0 quiet; 1 one line per KKT check on stderr */
+} pdlp_params;
+
+typedef struct {
+  int status;             /* PDLP_OPTIMAL, PDLP_ITER_LIMIT, PDLP_TIME_LIMIT, PDLP_NUMERICAL */
+  int precision_used;     /* PDLP_FP64, PDLP_FP32, PDLP_USED_BF16 or PDLP_USED_PATTERN */
+  int64_t iters;          /* accepted PDHG iterations */
+  int64_t attempts;       /* step attempts, rejected ones included */
+  int64_t restarts;
+  int64_t kkt_checks;
+  int64_t kernel_launches; /* kernels this call launched (setup, graph nodes, output) */
+  double primal_obj, dual_obj;
+  double rel_primal_res, rel_dual_res, rel_gap, rel_kkt;
+  double eta, omega;      /* final step size and primal weight */
+  int used_average;       /* 1 if the returned point is the weighted average iterate */
+  double setup_s;         /* device setup: canonical form, transpose, scaling */
+  double solve_s;         /* iteration phase, from the first step to termination */
+} pdlp_result;
+
+/* Optional diagnostic outputs (same memory space as the entry point's outputs;
+ * every pointer may be NULL, arrays shorter than the run are filled up to
+ * their capacity):
+ *  - the raw iterates at exit, unscaled and in the caller's sign convention:
+ *    the current iterate (x_cur, y_cur) and the step-size-weighted average
+ *    since the last restart (x_avg, y_avg);
+ *  - the decision trace of the adaptive step-size rule, one entry per step
+ *    attempt k = 1, 2, ...: the step size eta the attempt used, the bound
+ *    eta_bar it computed (+INFINITY when dy^T K dx = 0) and whether it was
+ *    accepted (1) or retried with a smaller step (0);
+ *  - per KKT check: the restart taken (0 none, 1 to the current iterate, 2 to
+ *    the average) and the primal weight after the check.
+ * The trace lets a second implementation replay the step-size sequence and
+ * check every decision (the rule is sensitive enough that two correct
+ * float64 implementations part after a few hundred adaptive steps). */
+typedef struct {
+  double* x_cur;             /* [n] */
+  double* y_cur;             /* [m] */
+  double* x_avg;             /* [n] */
+  double* y_avg;             /* [m] */
+  int64_t attempt_capacity;  /* length of eta, eta_bar, accepted */
+  double* eta;
+  double* eta_bar;
+  int8_t* accepted;
+  int64_t check_capacity;    /* length of restart, omega */
+  int8_t* restart;
+  double* omega;
+} pdlp_diagnostics;
+
+/* Fill *p with the defaults listed above.  Returns PDLP_OK or INVALID_INPUT (p NULL). */
+int pdlp_default_params(pdlp_params* p);
+
+/* Solve eq. (1) from HOST buffers.
+ *   A, b[m], sense[m], c[n], l[n], u[n]: host inputs (copied to the device).
+ *   p: parameters (NULL = defaults).
+ *   x0[n], y0[m]: optional warm start (NULL = cold start x = proj(0), y = 0).
+ *   x_out[n], y_out[m]: host outputs (the better of the current and the
+ *     average iterate at the last KKT check, by rel_kkt).
+ *   r: host result struct.  diag: optional host diagnostic buffers (may be NULL).
+ * Allocates and frees its own device memory; runs on a private stream and
+ * returns after the result is on the host.  Uses the current CUDA device. */
+int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+               const double* l, const double* u, const pdlp_params* p, const double* x0,
+               const double* y0, double* x_out, double* y_out, pdlp_result* r,
+               const pdlp_diagnostics* diag);
+
+/* Device workspace, in bytes, that pdlp_solve_device needs for this size and
+ * these parameters (precision mode and value format decide it).  Returns 0 on
+ * invalid sizes.  The bound holds for every value pattern. */
+size_t pdlp_workspace_size(int32_t m, int32_t n, int64_t nnz, const pdlp_params* p);
+
+/* Solve eq. (1) from DEVICE buffers, in stream order.
+ *   A (struct on the host, arrays on the device), b, sense, c, l, u, x0, y0:
+ *     device inputs of the same layout as pdlp_solve.
+ *   x_out, y_out: device outputs.  r: HOST result struct.  diag: optional
+ *     diagnostic buffers on the device (the struct itself on the host).
+ *   workspace, workspace_bytes: caller-owned device scratch of at least
+ *     pdlp_workspace_size(...) bytes, 256-byte aligned; NULL makes the library
+ *     allocate (and free) it with the stream-ordered allocator.
+ *   stream: a cudaStream_t (NULL = the legacy default stream).
+ * Input validation reads the inputs back to the host once.  The call returns
+ * when the solve is finished (it synchronises the stream once per KKT check
+ * period to read the termination flag). */
+int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, double* x_out, double* y_out, pdlp_result* r,
+                      const pdlp_diagnostics* diag, void* workspace, size_t workspace_bytes,
+                      void* stream);
+
+/* Kernel timing for roofline reports (a profiling aid; not needed to solve).
+ * Runs the same device setup as pdlp_solve_device on the same DEVICE inputs,
+ * then launches each fused kernel `reps` times back to back from a CUDA graph
+ * (step attempts stay live: no KKT check falls due) and writes, for
+ *   [0] the primal step kernel (A^T SpMV + projected update),
+ *   [1] the dual step kernel (A SpMV + extrapolated update + step decision),
+ *   [2] one whole attempt ([0] then [1]),
+ *   [3] the float64 KKT pass over A, [4] the float64 KKT pass over A^T,
+ * the average device time per launch in ms (graph launch gaps included) and
+ * the algorithmic bytes per launch (every array the kernel needs, each element
+ * once, gathered vectors counted once).  Workspace and stream as in
+ * pdlp_solve_device.  Returns PDLP_OK or an error code. */
+int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, int reps,
+                      double* ms_per_launch, double* bytes_per_launch, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Name of a return code, and the last error message of the calling thread. */
+const char* pdlp_error_string(int code);
+const char* pdlp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDLP_H */

@@ -192,6 +192,10 @@ class Params:
     beta_nec: float = 0.8
     beta_art: float = 0.36
     omega_smooth: float = 0.5
+    # replay: step size and accept flag of every attempt taken from another run's
+    # decision trace (eta_bar and all restart decisions are still computed here)
+    replay_eta: object = None
+    replay_accepted: object = None
 
 
 @dataclass
@@ -212,6 +216,8 @@ class Result:
     used_average: bool
     solve_s: float
     trace: list = field(default_factory=list)
+    attempt_trace: list = field(default_factory=list)  # (eta, eta_bar, accepted) per attempt
+    check_trace: list = field(default_factory=list)    # (restart kind, omega after) per check
 
 
 def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
@@ -250,7 +256,8 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
         return kkt_canonical(kt, qt, is_eq, ct, lt, ut, xs, ys)
 
     def unscaled_kkt(xs, ys):
-        return kkt_canonical(k, q, is_eq, lp.c, lp.l, lp.u, dc * xs, dr * ys)
+        # the unscaled point is clipped to [l, u] as the returned point is (A11)
+        return kkt_canonical(k, q, is_eq, lp.c, lp.l, lp.u, proj_box(dc * xs, lp.l, lp.u), dr * ys)
 
     attempts = 0
     it = 0
@@ -272,26 +279,36 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
             return sum_x / sum_w, sum_y / sum_w
         return x, y
 
+    attempt_trace = []
+    check_trace = []
     while it < p.iter_limit:
         attempts += 1
+        if p.replay_eta is not None:
+            eta = float(p.replay_eta[attempts - 1])
         # A4: primal step
         x_new = proj_box(x - (eta / omega) * (ct - ktt @ y), lt, ut)
         # A5: dual step with extrapolation 2x' - x
         y_new = proj_dual(y + eta * omega * (qt - kt @ (2.0 * x_new - x)), is_eq)
         eta_used = eta
+        # A6: the step-size bound of this attempt
+        dx = x_new - x
+        dy = y_new - y
+        denom = 2.0 * abs(float(dy @ (kt @ dx)))
+        num = omega * float(dx @ dx) + float(dy @ dy) / omega
+        eta_bar = num / denom if denom > 0 else math.inf
+        accept = True
         if p.adaptive:
-            # A6
-            dx = x_new - x
-            dy = y_new - y
-            denom = 2.0 * abs(float(dy @ (kt @ dx)))
-            num = omega * float(dx @ dx) + float(dy @ dy) / omega
-            eta_bar = num / denom if denom > 0 else math.inf
             eta_next = min((1.0 - (attempts + 1) ** -0.3) * eta_bar,
                            (1.0 + (attempts + 1) ** -0.6) * eta)
-            if eta > eta_bar:
-                trace.append(("reject", attempts, eta, eta_bar))
-                eta = eta_next
-                continue
+            accept = not (eta > eta_bar)
+        if p.replay_accepted is not None:
+            accept = bool(p.replay_accepted[attempts - 1])
+        attempt_trace.append((eta_used, eta_bar, accept))
+        if not accept:
+            trace.append(("reject", attempts, eta, eta_bar))
+            eta = eta_next
+            continue
+        if p.adaptive:
             eta = eta_next
         # accept; A7 running sums weighted by the step that produced the iterate
         x, y = x_new, y_new
@@ -310,12 +327,16 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
             trace.append(("check", it, kc.rel_kkt, ka.rel_kkt, eta, omega))
             if p.terminate and chosen_kkt.rel_kkt <= p.tol:
                 status = STATUS_OPTIMAL
+                check_trace.append((0, omega))
                 break
             if time.perf_counter() - t0 > p.time_limit_s:
                 status = STATUS_TIME_LIMIT
+                check_trace.append((0, omega))
                 break
             if last:
+                check_trace.append((0, omega))
                 break
+            kind = 0
             if p.restarts:
                 # A9
                 sc = scaled_kkt(x, y)
@@ -345,9 +366,11 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                     sum_y[:] = 0.0
                     sum_w = 0.0
                     restarts += 1
+                    kind = 2 if use_avg else 1
                     trace.append(("restart", it, bool(use_avg), omega))
                 else:
                     kkt_prev_cand = m_cand
+            check_trace.append((kind, omega))
     xa, ya = average()
     if chosen_kkt is None:  # no check ran (iter_limit == 0)
         chosen_kkt = unscaled_kkt(x, y)
@@ -366,4 +389,5 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
     return Result(status, it, attempts, restarts,
                   unscale_x(xo), unscale_y(yo), chosen_kkt,
                   unscale_x(x), unscale_y(y), unscale_x(xa), unscale_y(ya),
-                  eta, omega, chosen_avg, time.perf_counter() - t0, trace)
+                  eta, omega, chosen_avg, time.perf_counter() - t0, trace, attempt_trace,
+                  check_trace)

@@ -57,8 +57,11 @@ def vertex_enumeration(lp, feas_tol=1e-9):
     return best, verts
 
 
-def highs(lp):
-    """HiGHS optimum of the LP: (obj, x, y in caller convention, reduced costs)."""
+def highs(lp, method="highs"):
+    """HiGHS optimum of the LP: (obj, x, y in caller convention, reduced costs).
+
+    ``method`` is scipy's HiGHS variant ("highs", "highs-ds" dual simplex,
+    "highs-ipm" interior point with crossover)."""
     from scipy.optimize import linprog
     import scipy.sparse as sp
 
@@ -77,7 +80,7 @@ def highs(lp):
     bounds = [(None if not np.isfinite(lo) else lo, None if not np.isfinite(hi) else hi)
               for lo, hi in bounds]
     res = linprog(lp.c, A_ub=a_ub, b_ub=b_ub, A_eq=a_eq, b_eq=b_eq, bounds=bounds,
-                  method="highs")
+                  method=method)
     if res.status != 0:
         raise RuntimeError(f"HiGHS failed: {res.message}")
     y = np.zeros(lp.m)

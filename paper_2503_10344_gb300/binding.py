@@ -1,0 +1,256 @@
+"""ctypes binding of the C ABI in ``include/pdlp.h`` (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``libpdlp.so``; this module
+only builds the C structs, passes pointers and converts results.  There is no
+fallback: if the library is missing, :func:`lib` raises.
+
+Host entry point :func:`pdlp_solve` takes numpy arrays; device entry point
+:func:`pdlp_solve_device` takes CUDA torch tensors (PyTorch provides device
+memory and the stream, nothing else).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpdlp.so")
+
+PDLP_OK = 0
+ERRORS = {-1: "PDLP_ERR_INVALID_INPUT", -2: "PDLP_ERR_CUDA", -3: "PDLP_ERR_OOM",
+          -4: "PDLP_ERR_TIMEOUT", -5: "PDLP_ERR_UNSUPPORTED"}
+PDLP_OPTIMAL, PDLP_ITER_LIMIT, PDLP_TIME_LIMIT, PDLP_NUMERICAL = 1, 2, 3, 4
+PDLP_FP64, PDLP_FP32, PDLP_FP32_BF16A = 0, 1, 2
+PDLP_USED_BF16, PDLP_USED_PATTERN = 2, 3
+PRECISION = {"fp64": PDLP_FP64, "fp32": PDLP_FP32, "bf16": PDLP_FP32_BF16A}
+
+
+class PdlpCsr(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class PdlpParams(C.Structure):
+    _fields_ = [("struct_size", C.c_size_t), ("tol", C.c_double), ("iter_limit", C.c_int64),
+                ("time_limit_s", C.c_double), ("precision", C.c_int), ("check_period", C.c_int),
+                ("ruiz_iters", C.c_int), ("pc_alpha", C.c_double), ("adaptive_step", C.c_int),
+                ("restarts", C.c_int), ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
+                ("terminate", C.c_int), ("lanes_A", C.c_int), ("lanes_AT", C.c_int),
+                ("verbose", C.c_int)]
+
+
+class PdlpResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("precision_used", C.c_int), ("iters", C.c_int64),
+                ("attempts", C.c_int64), ("restarts", C.c_int64), ("kkt_checks", C.c_int64),
+                ("kernel_launches", C.c_int64), ("primal_obj", C.c_double),
+                ("dual_obj", C.c_double), ("rel_primal_res", C.c_double),
+                ("rel_dual_res", C.c_double), ("rel_gap", C.c_double), ("rel_kkt", C.c_double),
+                ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
+                ("setup_s", C.c_double), ("solve_s", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PdlpDiagnostics(C.Structure):
+    _fields_ = [("x_cur", C.c_void_p), ("y_cur", C.c_void_p), ("x_avg", C.c_void_p),
+                ("y_avg", C.c_void_p), ("attempt_capacity", C.c_int64), ("eta", C.c_void_p),
+                ("eta_bar", C.c_void_p), ("accepted", C.c_void_p), ("check_capacity", C.c_int64),
+                ("restart", C.c_void_p), ("omega", C.c_void_p)]
+
+
+_LIB = None
+
+
+class PdlpError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libpdlp.so (build it first with ``paper_2503_10344_gb300.build.build()``)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise PdlpError(f"{LIB_PATH} is missing: run paper_2503_10344_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        L.pdlp_default_params.argtypes = [C.POINTER(PdlpParams)]
+        L.pdlp_workspace_size.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.POINTER(PdlpParams)]
+        L.pdlp_workspace_size.restype = C.c_size_t
+        common = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + [C.POINTER(PdlpParams)] + \
+            [C.c_void_p] * 4 + [C.POINTER(PdlpResult), C.POINTER(PdlpDiagnostics)]
+        L.pdlp_solve.argtypes = common
+        L.pdlp_solve_device.argtypes = common + [C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pdlp_time_kernels.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + \
+            [C.POINTER(PdlpParams), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+             C.c_void_p]
+        L.pdlp_error_string.argtypes = [C.c_int]
+        L.pdlp_error_string.restype = C.c_char_p
+        L.pdlp_last_error.restype = C.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def default_params(**kw) -> PdlpParams:
+    p = PdlpParams()
+    lib().pdlp_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _check(rc: int):
+    if rc != PDLP_OK:
+        msg = lib().pdlp_last_error().decode()
+        raise PdlpError(f"{ERRORS.get(rc, rc)}: {msg}")
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+DIAG_ITERATES = ("x_cur", "y_cur", "x_avg", "y_avg")
+
+
+def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates: bool = False,
+               trace: int = 0):
+    """Solve ``lp`` (an :class:`lpgen.LP`-like object) from host memory.
+
+    Returns (x, y, result dict) or, with ``iterates`` or ``trace`` > 0,
+    (x, y, result dict, diagnostics dict); ``trace`` is the capacity of the
+    per-attempt decision trace (the per-check trace gets trace // 16 + 16).
+    """
+    p = params or default_params()
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    row_ptr = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(lp.col, dtype=np.int32)
+    val = f64(lp.val)
+    b, c, l, u = f64(lp.b), f64(lp.c), f64(lp.l), f64(lp.u)
+    sense = np.ascontiguousarray(lp.sense, dtype=np.uint8)
+    csr = PdlpCsr(lp.m, lp.n, int(row_ptr[-1]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    x = np.empty(lp.n)
+    y = np.empty(lp.m)
+    x0a = None if x0 is None else f64(x0)
+    y0a = None if y0 is None else f64(y0)
+    res = PdlpResult()
+    diag = None
+    dgp = None
+    if iterates or trace > 0:
+        diag = {k: np.empty(lp.n if k[0] == "x" else lp.m) for k in DIAG_ITERATES}
+        tc = trace // 16 + 16 if trace > 0 else 0
+        diag.update(eta=np.full(trace, np.nan), eta_bar=np.full(trace, np.nan),
+                    accepted=np.full(trace, -1, dtype=np.int8), restart=np.full(tc, -1, dtype=np.int8),
+                    omega=np.full(tc, np.nan))
+        dgp = PdlpDiagnostics(*[_ptr(diag[k]) for k in DIAG_ITERATES], trace, _ptr(diag["eta"]),
+                              _ptr(diag["eta_bar"]), _ptr(diag["accepted"]), tc,
+                              _ptr(diag["restart"]), _ptr(diag["omega"]))
+    rc = lib().pdlp_solve(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u),
+                          C.byref(p), _ptr(x0a), _ptr(y0a), _ptr(x), _ptr(y), C.byref(res),
+                          C.byref(dgp) if dgp is not None else None)
+    _check(rc)
+    out = res.as_dict()
+    if diag is None:
+        return x, y, out
+    if trace > 0:
+        na = min(trace, out["attempts"])
+        nc = min(tc, out["kkt_checks"])
+        for k in ("eta", "eta_bar", "accepted"):
+            diag[k] = diag[k][:na]
+        for k in ("restart", "omega"):
+            diag[k] = diag[k][:nc]
+    return x, y, out, diag
+
+
+def workspace_size(m: int, n: int, nnz: int, params: PdlpParams | None = None) -> int:
+    p = params or default_params()
+    return int(lib().pdlp_workspace_size(m, n, nnz, C.byref(p)))
+
+
+class DeviceLP:
+    """The arrays of an LP as CUDA torch tensors (inputs of pdlp_solve_device)."""
+
+    def __init__(self, lp, device="cuda"):
+        import torch
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        self.m, self.n, self.nnz = lp.m, lp.n, int(lp.row_ptr[-1])
+        self.row_ptr = t(lp.row_ptr, torch.int64)
+        self.col = t(lp.col, torch.int32)
+        self.val = t(lp.val, torch.float64)
+        self.b = t(lp.b, torch.float64)
+        self.sense = t(lp.sense, torch.uint8)
+        self.c = t(lp.c, torch.float64)
+        self.l = t(lp.l, torch.float64)
+        self.u = t(lp.u, torch.float64)
+
+
+def pdlp_solve_device(dlp: DeviceLP, params: PdlpParams | None = None, x0=None, y0=None,
+                      x_out=None, y_out=None, workspace=None, stream=None, iterates=None):
+    # iterates: optional dict of float64 CUDA tensors named x_cur, y_cur, x_avg, y_avg
+    """Solve from device tensors on ``stream`` (default: torch's current stream).
+
+    ``x_out``/``y_out``/``iterates`` are float64 CUDA tensors (allocated if None);
+    ``workspace`` is a uint8 CUDA tensor of at least :func:`workspace_size` bytes
+    (allocated from torch's caching allocator if None).  Returns (x, y, result).
+    """
+    import torch
+    p = params or default_params()
+    dev = dlp.c.device
+    if x_out is None:
+        x_out = torch.empty(dlp.n, dtype=torch.float64, device=dev)
+    if y_out is None:
+        y_out = torch.empty(max(dlp.m, 1), dtype=torch.float64, device=dev)
+    nbytes = workspace_size(dlp.m, dlp.n, dlp.nnz, p)
+    if workspace is None:
+        workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    avail = workspace.numel() - (aligned - base)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    dp = lambda t_: None if t_ is None else C.c_void_p(t_.data_ptr())
+    csr = PdlpCsr(dlp.m, dlp.n, dlp.nnz, dlp.row_ptr.data_ptr(), dlp.col.data_ptr(),
+                  dlp.val.data_ptr())
+    res = PdlpResult()
+    itp = None
+    if iterates is not None:
+        itp = PdlpDiagnostics(*[dp(iterates.get(k)) for k in DIAG_ITERATES], 0, None, None, None,
+                              0, None, None)
+    rc = lib().pdlp_solve_device(C.byref(csr), dp(dlp.b), dp(dlp.sense), dp(dlp.c), dp(dlp.l),
+                                 dp(dlp.u), C.byref(p), dp(x0), dp(y0), dp(x_out), dp(y_out),
+                                 C.byref(res), C.byref(itp) if itp is not None else None,
+                                 C.c_void_p(aligned), avail, C.c_void_p(stream.cuda_stream))
+    _check(rc)
+    return x_out, y_out[: dlp.m], res.as_dict()
+
+
+KERNELS = ("primal_step", "dual_step", "attempt", "kkt_rows", "kkt_cols")
+
+
+def time_kernels(dlp: DeviceLP, params: PdlpParams | None = None, reps: int = 200,
+                 workspace=None, stream=None) -> dict:
+    """Average device ms and algorithmic bytes per launch of each fused kernel."""
+    import torch
+    p = params or default_params()
+    dev = dlp.c.device
+    nbytes = workspace_size(dlp.m, dlp.n, dlp.nnz, p)
+    if workspace is None:
+        workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    ms = np.zeros(5)
+    by = np.zeros(5)
+    csr = PdlpCsr(dlp.m, dlp.n, dlp.nnz, dlp.row_ptr.data_ptr(), dlp.col.data_ptr(),
+                  dlp.val.data_ptr())
+    dp = lambda t_: C.c_void_p(t_.data_ptr())
+    rc = lib().pdlp_time_kernels(C.byref(csr), dp(dlp.b), dp(dlp.sense), dp(dlp.c), dp(dlp.l),
+                                 dp(dlp.u), C.byref(p), reps, _ptr(ms), _ptr(by), C.c_void_p(aligned),
+                                 workspace.numel() - (aligned - base), C.c_void_p(stream.cuda_stream))
+    _check(rc)
+    return {k: {"ms": float(ms[i]), "bytes": float(by[i])} for i, k in enumerate(KERNELS)}

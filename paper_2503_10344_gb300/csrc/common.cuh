@@ -1,0 +1,162 @@
+// Shared device-side definitions of the PDLP library: the device-resident
+// solver state, value loaders for the matrix storage formats, and the
+// deterministic warp / block reductions every fused kernel ends with.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace pdlp {
+
+constexpr int kBlock = 256;         // threads per block of every streaming kernel
+constexpr int kWarps = kBlock / 32;
+
+// Matrix value formats of the iteration matrix.
+struct Pattern {};  // every stored value is exactly +1: no value array at all
+
+template <typename V> __device__ __forceinline__ float ldv_f(const V* v, int64_t p);
+template <> __device__ __forceinline__ float ldv_f<float>(const float* v, int64_t p) { return __ldg(v + p); }
+template <> __device__ __forceinline__ float ldv_f<__nv_bfloat16>(const __nv_bfloat16* v, int64_t p) {
+  return __bfloat162float(v[p]);
+}
+template <> __device__ __forceinline__ float ldv_f<Pattern>(const Pattern*, int64_t) { return 1.0f; }
+
+template <typename T, typename V> struct Ld;
+template <typename V> struct Ld<float, V> {
+  static __device__ __forceinline__ float get(const V* v, int64_t p) { return ldv_f<V>(v, p); }
+};
+template <> struct Ld<double, double> {
+  static __device__ __forceinline__ double get(const double* v, int64_t p) { return __ldg(v + p); }
+};
+
+// Device-resident solver state.  Written by one thread of the deciding block
+// (the last block of the dual-step kernel, the KKT finalisation kernel) and
+// read by every kernel at entry; kernels launched after a terminating or a
+// KKT-pending decision return immediately, so a captured chunk of iterations
+// is safe to over-launch.
+struct DevState {
+  // host-visible summary first (copied back after every chunk)
+  int status;            // 0 running, else PDLP_OPTIMAL / ITER_LIMIT / TIME_LIMIT / NUMERICAL
+  int check_due;         // 1: the KKT block must run before the next step
+  long long iters;       // accepted iterations
+  long long attempts;    // all step attempts (k of the step-size rule, 1-based after increment)
+  long long restarts;
+  long long checks;
+  // step size / primal weight (A3, A6, A10)
+  double eta, omega;
+  // weighted averages (A7): sum_w includes pending_w; the iterate whose weight
+  // is pending has not yet been added to sum_x / sum_y (the next step adds it
+  // while it reads that iterate anyway)
+  double sum_w, pending_w;
+  int cur;               // which of the two x / y buffers holds the current iterate
+  int restart_kind;      // set by the KKT finalisation: 0 none, 1 to current, 2 to average, 3 initial
+  int init_pending;      // the first KKT block only records the "last restart" data
+  int used_avg;          // output candidate of the last check
+  int force_final;       // host asked for a final check (time limit)
+  unsigned int counter;  // last-block counter of the dual-step kernel
+  long long last_restart_it;
+  double last_rp2, last_rd2, last_gap2;  // scaled KKT triple of the last restart point
+  double prev_cand;                      // KKT_omega of the previous candidate (inf after restart)
+  // parameters
+  long long iter_limit;
+  int period, adaptive, restarts_on, terminate;
+  double tol;
+  double norm_q, norm_c;  // ||q||_2, ||c||_2 of the unscaled data
+  // results of the last KKT check: [0] current, [1] average
+  double pobj[2], dobj[2], relp[2], reld[2], relgap[2];
+  // optional decision trace (device arrays, capacity 0 = off)
+  double* tr_eta;
+  double* tr_eta_bar;
+  signed char* tr_accepted;
+  long long tr_cap;
+  signed char* tr_restart;
+  double* tr_omega;
+  long long tr_check_cap;
+};
+
+// ---------------------------------------------------------------- reductions
+template <int LANES, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+  // sum over an aligned group of LANES lanes; all lanes of the group are active
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = (LANES == 32) ? 0xffffffffu : (((1u << LANES) - 1u) << (lane & ~(unsigned)(LANES - 1)));
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// pair of partial sums reduced together (two candidates, or x' and dx)
+template <typename T>
+struct P2 {
+  T a, b;
+  __device__ __forceinline__ P2& operator+=(const P2& o) {
+    a += o.a;
+    b += o.b;
+    return *this;
+  }
+};
+using D2 = P2<double>;
+template <int LANES, typename T>
+__device__ __forceinline__ P2<T> group_sum(P2<T> v) {
+  v.a = group_sum<LANES, T>(v.a);
+  v.b = group_sum<LANES, T>(v.b);
+  return v;
+}
+
+// interleaved (value, step) pairs of the primal iterate: .x = x_j, .y = x_j - x_j(previous)
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using vec2_t = typename Vec2<T>::type;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic sum of NV values over a block of kBlock threads.  Thread 0
+// gets the result; the order of additions is fixed by the launch shape.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (&out)[NV]) {
+  __shared__ double sh[NV][kWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kWarps; ++i) s += sh[k][i];
+      out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Fixed-order reduction of NV partial arrays part[k * stride + i], i < count,
+// by one block; thread 0 receives the sums.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* part, int stride, int count,
+                                                double (&out)[NV]) {
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int i = threadIdx.x; i < count; i += kBlock) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += part[(size_t)k * stride + i];
+  }
+  block_sum<NV>(v, out);
+}
+
+__device__ __forceinline__ double kkt_omega(double omega, double rp2, double rd2, double gap2) {
+  return sqrt(omega * rp2 + rd2 / omega + gap2);
+}
+
+}  // namespace pdlp

@@ -1,0 +1,67 @@
+// Host-side interfaces between the translation units of the PDLP library.
+// The solver driver fills these untyped launch descriptions; each kernel
+// translation unit casts them to its own element types.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace pdlp {
+
+enum Mode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_BF16 = 2, MODE_PAT = 3 };
+
+struct IterRaw {
+  const int *a_ptr, *a_col;
+  const void* a_val;
+  const int *t_ptr, *t_col;
+  const void* t_val;
+  const int *a_long, *t_long;
+  int a_nlong, t_nlong, a_thresh, t_thresh;
+  int m, n;
+  const void *c, *l, *u, *q, *tw, *sw;
+  const unsigned char* row_kind;
+  void *x[2], *y[2], *sum_x, *sum_y;  // x: interleaved (x_j, dx_j) pairs
+  double *part_p, *part_d;
+  int grid_p_short, grid_p, grid_d_short, grid_d;
+  DevState* st;
+};
+
+enum IterKernel { IK_PRIMAL = 0, IK_DUAL = 1 };
+
+cudaError_t launch_iter_fp64(int which, int lanes, const IterRaw& r, cudaStream_t s);
+cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_t s);
+cudaError_t launch_iter_bf16(int which, int lanes, const IterRaw& r, cudaStream_t s);
+cudaError_t launch_iter_pat(int which, int lanes, const IterRaw& r, cudaStream_t s);
+
+struct KktRaw {
+  const int *a_ptr, *a_col;
+  const double* a_val64;  // raw canonical K (NULL = every value +1)
+  const int *t_ptr, *t_col;
+  const double* t_val64;
+  const int *a_long, *t_long;
+  int a_nlong, t_nlong, a_thresh, t_thresh;
+  int m, n;
+  const double *c, *l, *u, *q, *dr, *dc;  // unscaled canonical data, scaling
+  const unsigned char* row_kind;           // 0 >=-row, 1 =-row, 2 <=-row flipped to >=
+  void *x[2], *y[2], *sum_x, *sum_y;       // iterates (float or double; x as (x_j, dx_j) pairs)
+  double *Xc, *Xa, *Yc, *Ya, *Xl, *Yl;     // unscaled float64 candidates and restart anchors
+  double *part_r, *part_c;
+  int grid_r_short, grid_r, grid_c_short, grid_c, grid_e;
+  int scaled;  // iterates are in scaled space (explicit K~)
+  int fp32;    // iterate element type is float
+  DevState* st;
+};
+
+enum KktKernel { KK_PREP = 0, KK_ROWS = 1, KK_COLS = 2, KK_FINAL = 3, KK_APPLY = 4, KK_END = 5 };
+cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s);
+// Final outputs in the caller's convention: x clipped to [l,u], y sign-flipped
+// back on <=-rows.  Any pointer may be NULL.
+cudaError_t launch_output(const KktRaw& r, double* x_out, double* y_out, double* x_cur,
+                          double* y_cur, double* x_avg, double* y_avg, cudaStream_t s);
+
+int grid_for(long long work_items, int max_blocks);
+int device_sm_count();
+
+}  // namespace pdlp

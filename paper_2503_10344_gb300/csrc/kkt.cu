@@ -1,0 +1,331 @@
+// KKT evaluation, restart decision and primal-weight update (rows A8-A10),
+// all in float64 on the unscaled canonical data, run once per check period.
+//
+//   k_kkt_prep   unscaled float64 current iterate and step-size-weighted
+//                average (A7) into scratch vectors
+//   k_kkt_rows   K x for both candidates in one pass over A, fused with the
+//                primal residuals (unscaled and scaled), q^T y and the scaled
+//                dual distance to the last restart point
+//   k_kkt_cols   K^T y for both candidates in one pass over A^T, fused with
+//                the bound-aware dual residuals, objective terms and the scaled
+//                primal distance to the last restart point
+//   k_kkt_final  one block: fixed-order reduction of the partials, relative
+//                KKT of both candidates (the termination test of the paper's
+//                relative tolerances, section 4), the KKT restart criteria and
+//                the primal-weight update
+//   k_kkt_apply  restart: replace the iterate by the average if chosen, move
+//                the restart anchors, clear the running sums
+//   k_kkt_end    one thread: clear the per-check flags
+#include "internal.h"
+#include "iter_kernels.cuh"
+
+namespace pdlp {
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0) return;
+  const int cur = st->cur;
+  const double pw = st->pending_w, sw = st->sum_w;
+  const vec2_t<T>* x = (const vec2_t<T>*)r.x[cur];
+  const T* y = (const T*)r.y[cur];
+  const T* sx = (const T*)r.sum_x;
+  const T* sy = (const T*)r.sum_y;
+  const long long stride = (long long)gridDim.x * kBlock;
+  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+    const double xc = (double)x[j].x;
+    const double xa = sw > 0.0 ? ((double)sx[j] + pw * xc) / sw : xc;
+    const double s = r.scaled ? r.dc[j] : 1.0;
+    // unscaled candidates, clipped to [l, u] so the KKT measured here is the
+    // KKT of exactly the point the solver returns (A11)
+    r.Xc[j] = fmin(fmax(s * xc, r.l[j]), r.u[j]);
+    r.Xa[j] = fmin(fmax(s * xa, r.l[j]), r.u[j]);
+  }
+  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+    const double yc = (double)y[i];
+    const double ya = sw > 0.0 ? ((double)sy[i] + pw * yc) / sw : yc;
+    const double s = r.scaled ? r.dr[i] : 1.0;
+    r.Yc[i] = s * yc;
+    r.Ya[i] = s * ya;
+  }
+}
+
+// partial layout over rows of A: [0,1] ||r_p||^2 cur/avg, [2,3] ||D_r r_p||^2,
+// [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2
+template <int LANES>
+__global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0) return;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const double* __restrict__ val = r.a_val64;
+  auto load = [&](int p) -> D2 {
+    const double v = val ? __ldg(val + p) : 1.0;
+    const int j = __ldg(r.a_col + p);
+    return D2{v * r.Xc[j], v * r.Xa[j]};
+  };
+  auto epi = [&](int i, D2 ax) {
+    const double q = r.q[i], dr = r.dr[i];
+    const bool eq = r.row_kind[i] == 1;
+    const double kx[2] = {ax.a, ax.b};
+    const double yv[2] = {r.Yc[i], r.Ya[i]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      double rp = q - kx[k];
+      if (!eq) rp = fmax(rp, 0.0);
+      acc[0 + k] += rp * rp;
+      acc[2 + k] += (dr * rp) * (dr * rp);
+      acc[4 + k] += q * yv[k];
+      const double dd = (yv[k] - r.Yl[i]) / dr;
+      acc[6 + k] += dd * dd;
+    }
+  };
+  if ((int)blockIdx.x < r.grid_r_short)
+    rows_short<LANES, D2>(r.m, r.a_ptr, r.a_thresh, r.grid_r_short, load, epi);
+  else
+    rows_long<D2>(r.a_ptr, r.a_long, r.a_nlong, r.grid_r_short, load, epi);
+  double out[8];
+  block_sum<8>(acc, out);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 8; ++k) r.part_r[(size_t)k * r.grid_r + blockIdx.x] = out[k];
+}
+
+// partial layout over rows of A^T: [0,1] ||r_d||^2, [2,3] ||D_c r_d||^2, [4,5] c^T x,
+// [6,7] bound terms of the dual objective, [8,9] ||(x - x_last) / D_c||^2
+template <int LANES>
+__global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0) return;
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const double* __restrict__ val = r.t_val64;
+  auto load = [&](int p) -> D2 {
+    const double v = val ? __ldg(val + p) : 1.0;
+    const int i = __ldg(r.t_col + p);
+    return D2{v * r.Yc[i], v * r.Ya[i]};
+  };
+  auto epi = [&](int j, D2 aty) {
+    const double c = r.c[j], l = r.l[j], u = r.u[j], dc = r.dc[j];
+    const double kty[2] = {aty.a, aty.b};
+    const double xv[2] = {r.Xc[j], r.Xa[j]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double lam = c - kty[k];
+      const double lp = fmax(lam, 0.0), lm = fmax(-lam, 0.0);
+      const double rd = (l == -INFINITY ? lp : 0.0) + (u == INFINITY ? lm : 0.0);
+      acc[0 + k] += rd * rd;
+      acc[2 + k] += (dc * rd) * (dc * rd);
+      acc[4 + k] += c * xv[k];
+      acc[6 + k] += (isfinite(l) ? l * lp : 0.0) - (isfinite(u) ? u * lm : 0.0);
+      const double dd = (xv[k] - r.Xl[j]) / dc;
+      acc[8 + k] += dd * dd;
+    }
+  };
+  if ((int)blockIdx.x < r.grid_c_short)
+    rows_short<LANES, D2>(r.n, r.t_ptr, r.t_thresh, r.grid_c_short, load, epi);
+  else
+    rows_long<D2>(r.t_ptr, r.t_long, r.t_nlong, r.grid_c_short, load, epi);
+  double out[10];
+  block_sum<10>(acc, out);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) r.part_c[(size_t)k * r.grid_c + blockIdx.x] = out[k];
+}
+
+__global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0) return;
+  double pr[8], pc[10];
+  reduce_partials<8>(r.part_r, r.grid_r, r.grid_r, pr);
+  reduce_partials<10>(r.part_c, r.grid_c, r.grid_c, pc);
+  if (threadIdx.x != 0) return;
+  double relk[2], gap2[2];
+  for (int k = 0; k < 2; ++k) {
+    const double pobj = pc[4 + k];
+    const double dobj = pr[4 + k] + pc[6 + k];
+    const double gap = fabs(pobj - dobj);
+    st->pobj[k] = pobj;
+    st->dobj[k] = dobj;
+    st->relp[k] = sqrt(pr[0 + k]) / (1.0 + st->norm_q);
+    st->reld[k] = sqrt(pc[0 + k]) / (1.0 + st->norm_c);
+    st->relgap[k] = gap / (1.0 + fabs(pobj) + fabs(dobj));
+    relk[k] = fmax(st->relp[k], fmax(st->reld[k], st->relgap[k]));
+    gap2[k] = gap * gap;
+  }
+  if (st->init_pending) {  // KKT of the starting point: the first "last restart" data
+    st->last_rp2 = pr[2];
+    st->last_rd2 = pc[2];
+    st->last_gap2 = gap2[0];
+    st->prev_cand = INFINITY;
+    st->restart_kind = 3;
+    st->init_pending = 0;
+    st->used_avg = 0;
+    return;
+  }
+  st->checks += 1;
+  const int use_avg_out = relk[1] < relk[0];
+  st->used_avg = use_avg_out;
+  const double best = use_avg_out ? relk[1] : relk[0];
+  if (!isfinite(relk[0]) && !isfinite(relk[1])) {
+    st->status = 4;  // PDLP_NUMERICAL
+  } else if (st->terminate && best <= st->tol) {
+    st->status = 1;  // PDLP_OPTIMAL
+  } else if (st->iters >= st->iter_limit) {
+    st->status = 2;  // PDLP_ITER_LIMIT
+  } else if (st->force_final) {
+    st->status = 3;  // PDLP_TIME_LIMIT
+  }
+  st->restart_kind = 0;
+  if (st->status == 0 && st->restarts_on && st->iters % st->period == 0) {
+    // A9: KKT restart on the scaled KKT_omega
+    const double om = st->omega;
+    const double mc = kkt_omega(om, pr[2], pc[2], gap2[0]);
+    const double ma = kkt_omega(om, pr[3], pc[3], gap2[1]);
+    const int ua = ma < mc;
+    const double mcand = ua ? ma : mc;
+    const double mlast = kkt_omega(om, st->last_rp2, st->last_rd2, st->last_gap2);
+    const bool do_restart = mcand <= 0.2 * mlast ||
+                            (mcand <= 0.8 * mlast && mcand > st->prev_cand) ||
+                            (double)(st->iters - st->last_restart_it) >= 0.36 * (double)st->iters;
+    if (!do_restart) {
+      st->prev_cand = mcand;
+    } else {
+      // A10: primal weight from the scaled distances moved since the last restart
+      const double ddx = sqrt(pc[8 + ua]), ddy = sqrt(pr[6 + ua]);
+      if (ddx > 1e-10 && ddy > 1e-10) st->omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(om));
+      st->last_rp2 = pr[2 + ua];
+      st->last_rd2 = pc[2 + ua];
+      st->last_gap2 = gap2[ua];
+      st->prev_cand = INFINITY;
+      st->last_restart_it = st->iters;
+      st->restarts += 1;
+      st->restart_kind = ua ? 2 : 1;
+    }
+  }
+  const long long t = st->checks - 1;
+  if (t < st->tr_check_cap) {
+    st->tr_restart[t] = (signed char)st->restart_kind;
+    st->tr_omega[t] = st->omega;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0) return;
+  const int kind = st->restart_kind;
+  if (kind == 0) return;
+  const int cur = st->cur;
+  const double pw = st->pending_w, sw = st->sum_w;
+  vec2_t<T>* x = (vec2_t<T>*)r.x[cur];
+  T* y = (T*)r.y[cur];
+  T* sx = (T*)r.sum_x;
+  T* sy = (T*)r.sum_y;
+  const long long stride = (long long)gridDim.x * kBlock;
+  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+    if (kind == 2) {
+      const double xc = (double)x[j].x;
+      vec2_t<T> v;
+      v.x = (T)(sw > 0.0 ? ((double)sx[j] + pw * xc) / sw : xc);
+      v.y = (T)0;  // the step into the restart point is never read
+      x[j] = v;
+      r.Xl[j] = r.Xa[j];
+    } else {
+      r.Xl[j] = r.Xc[j];
+    }
+    sx[j] = (T)0;
+  }
+  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+    if (kind == 2) {
+      const double yc = (double)y[i];
+      y[i] = (T)(sw > 0.0 ? ((double)sy[i] + pw * yc) / sw : yc);
+      r.Yl[i] = r.Ya[i];
+    } else {
+      r.Yl[i] = r.Yc[i];
+    }
+    sy[i] = (T)0;
+  }
+}
+
+__global__ void k_kkt_end(KktRaw r) {
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0) return;
+  if (st->restart_kind != 0) {
+    st->sum_w = 0.0;
+    st->pending_w = 0.0;
+  }
+  st->restart_kind = 0;
+  st->check_due = 0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, double* y_out,
+                                                   double* x_cur, double* y_cur, double* x_avg,
+                                                   double* y_avg) {
+  const int ua = r.st->used_avg;
+  const long long stride = (long long)gridDim.x * kBlock;
+  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+    const double l = r.l[j], u = r.u[j];
+    const double xc = fmin(fmax(r.Xc[j], l), u), xa = fmin(fmax(r.Xa[j], l), u);
+    if (x_out) x_out[j] = ua ? xa : xc;
+    if (x_cur) x_cur[j] = xc;
+    if (x_avg) x_avg[j] = xa;
+  }
+  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+    const double s = r.row_kind[i] == 2 ? -1.0 : 1.0;
+    const double yc = s * r.Yc[i], ya = s * r.Ya[i];
+    if (y_out) y_out[i] = ua ? ya : yc;
+    if (y_cur) y_cur[i] = yc;
+    if (y_avg) y_avg[i] = ya;
+  }
+}
+
+template <int LANES>
+cudaError_t launch_rc(int which, const KktRaw& r, cudaStream_t s) {
+  if (which == KK_ROWS)
+    k_kkt_rows<LANES><<<r.grid_r, kBlock, 0, s>>>(r);
+  else
+    k_kkt_cols<LANES><<<r.grid_c, kBlock, 0, s>>>(r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rc_lanes(int which, int lanes, const KktRaw& r, cudaStream_t s) {
+  switch (lanes) {
+    case 2: return launch_rc<2>(which, r, s);
+    case 4: return launch_rc<4>(which, r, s);
+    case 8: return launch_rc<8>(which, r, s);
+    case 16: return launch_rc<16>(which, r, s);
+    case 32: return launch_rc<32>(which, r, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s) {
+  switch (which) {
+    case KK_PREP:
+      if (r.fp32) k_kkt_prep<float><<<r.grid_e, kBlock, 0, s>>>(r);
+      else k_kkt_prep<double><<<r.grid_e, kBlock, 0, s>>>(r);
+      return cudaGetLastError();
+    case KK_ROWS: return launch_rc_lanes(KK_ROWS, lanes_r, r, s);
+    case KK_COLS: return launch_rc_lanes(KK_COLS, lanes_c, r, s);
+    case KK_FINAL:
+      k_kkt_final<<<1, kBlock, 0, s>>>(r);
+      return cudaGetLastError();
+    case KK_APPLY:
+      if (r.fp32) k_kkt_apply<float><<<r.grid_e, kBlock, 0, s>>>(r);
+      else k_kkt_apply<double><<<r.grid_e, kBlock, 0, s>>>(r);
+      return cudaGetLastError();
+    case KK_END:
+      k_kkt_end<<<1, 1, 0, s>>>(r);
+      return cudaGetLastError();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_output(const KktRaw& r, double* x_out, double* y_out, double* x_cur,
+                          double* y_cur, double* x_avg, double* y_avg, cudaStream_t s) {
+  k_output<<<r.grid_e, kBlock, 0, s>>>(r, x_out, y_out, x_cur, y_cur, x_avg, y_avg);
+  return cudaGetLastError();
+}
+
+}  // namespace pdlp

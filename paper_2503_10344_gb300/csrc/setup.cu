@@ -1,0 +1,694 @@
+// Device setup of one LP (rows A0-A3 of the hot path):
+//   validation of the caller's CSR and vectors (error bits, no trap),
+//   canonical form K = S A, q = S b (A0),
+//   deterministic transpose of A into CSR (A1: count, scan, scatter, then a
+//   segmented sort of each column's entries by their position in A, so the
+//   result does not depend on the order atomics landed in),
+//   Ruiz (inf-norm) and Pock-Chambolle scaling (A2),
+//   iteration-space matrix values and vectors, and the scalars of A3.
+#include <algorithm>
+#include <vector>
+
+#include "setup.h"
+
+namespace pdlp {
+
+namespace {
+
+constexpr int kScanItems = 8;                       // per thread
+constexpr int kScanTile = kBlock * kScanItems;      // per block
+constexpr int kSmallSeg = 32;                       // per-thread insertion sort up to this length
+constexpr int kTile = 4096;                         // bitonic tile of a long column segment
+
+// ------------------------------------------------------------------ validation
+__global__ void k_validate_rows(SetupIn in, int* err) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < in.m; i += stride) {
+    const int64_t s = in.row_ptr[i], e = in.row_ptr[i + 1];
+    if (s < 0 || e < s || e > in.nnz) atomicOr(err, ERR_ROWPTR);
+    const char sn = in.sense[i];
+    if (sn != 'L' && sn != 'G' && sn != 'E') atomicOr(err, ERR_SENSE);
+    if (!isfinite(in.b[i])) atomicOr(err, ERR_NONFINITE);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (in.row_ptr[0] != 0 || in.row_ptr[in.m] != in.nnz) atomicOr(err, ERR_ROWPTR);
+  }
+}
+
+__global__ void k_validate_nnz(SetupIn in, int* err) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < in.nnz; p += stride) {
+    const int j = in.col[p];
+    if (j < 0 || j >= in.n) atomicOr(err, ERR_COL);
+    if (!isfinite(in.val[p])) atomicOr(err, ERR_NONFINITE);
+  }
+}
+
+__global__ void k_validate_cols(SetupIn in, int* err) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < in.n; j += stride) {
+    const double l = in.l[j], u = in.u[j];
+    if (!isfinite(in.c[j])) atomicOr(err, ERR_NONFINITE);
+    if (isnan(l) || isnan(u) || l > u || l == INFINITY || u == -INFINITY) atomicOr(err, ERR_BOUNDS);
+  }
+}
+
+// ------------------------------------------------------------------ A0
+__global__ void k_canonical(SetupIn in, int* a_ptr, int* a_col, double* a_val64, double* q,
+                            unsigned char* row_kind) {
+  // one warp per row
+  const int lane = threadIdx.x & 31;
+  const long long W = (long long)gridDim.x * blockDim.x / 32;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < in.m; i += W) {
+    const char sn = in.sense[i];
+    const double s = sn == 'L' ? -1.0 : 1.0;
+    const int64_t b = in.row_ptr[i], e = in.row_ptr[i + 1];
+    for (int64_t p = b + lane; p < e; p += 32) {
+      a_col[p] = in.col[p];
+      a_val64[p] = s * in.val[p];
+    }
+    if (lane == 0) {
+      a_ptr[i] = (int)b;
+      q[i] = s * in.b[i];
+      row_kind[i] = sn == 'E' ? 1 : (sn == 'L' ? 2 : 0);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a_ptr[in.m] = (int)in.nnz;
+}
+
+// ------------------------------------------------------------------ scan
+// exclusive scan of cnt[0..N) into out[0..N], out[N] = total
+__global__ void k_scan_tiles(const int* cnt, int* out, int N, int* bsum) {
+  __shared__ int sh[kBlock];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + k;
+    v[k] = i < N ? cnt[i] : 0;
+    s += v[k];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < kBlock; o <<= 1) {  // Hillis-Steele inclusive scan of thread sums
+    const int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int run = sh[threadIdx.x] - s;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + k;
+    if (i < N) out[i] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kBlock - 1) bsum[blockIdx.x] = sh[kBlock - 1];
+}
+
+__global__ void k_scan_bsum(int* bsum, int nb, int* out, int N) {
+  // single block: exclusive scan of the tile sums, written back in place; total into out[N]
+  __shared__ int sh[kBlock];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += kBlock) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? bsum[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kBlock; o <<= 1) {
+      const int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == kBlock - 1) carry += sh[kBlock - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[N] = carry;
+}
+
+__global__ void k_scan_add(int* out, int N, const int* bsum) {
+  const long long base = (long long)blockIdx.x * kScanTile;
+  const int add = bsum[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += kBlock) {
+    const long long i = base + k;
+    if (i < N) out[i] += add;
+  }
+}
+
+// ------------------------------------------------------------------ A1 transpose
+__global__ void k_count_cols(const int* a_col, int nnz, int* cnt) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+    atomicAdd(cnt + a_col[p], 1);
+}
+
+__global__ void k_scatter(const int* a_col, int nnz, const int* t_ptr, int* cursor, int* src) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int j = a_col[p];
+    const int pos = t_ptr[j] + atomicAdd(cursor + j, 1);
+    src[pos] = (int)p;
+  }
+}
+
+__global__ void k_segsort_small(const int* t_ptr, int n, int* src, int* long_list, int* nlong) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const int s = t_ptr[j], e = t_ptr[j + 1], len = e - s;
+    if (len > kSmallSeg) {
+      long_list[atomicAdd(nlong, 1)] = (int)j;
+      continue;
+    }
+    int k[kSmallSeg];
+    for (int a = 0; a < len; ++a) k[a] = src[s + a];
+    for (int a = 1; a < len; ++a) {  // insertion sort
+      const int v = k[a];
+      int b = a - 1;
+      while (b >= 0 && k[b] > v) {
+        k[b + 1] = k[b];
+        --b;
+      }
+      k[b + 1] = v;
+    }
+    for (int a = 0; a < len; ++a) src[s + a] = k[a];
+  }
+}
+
+// one block per tile (start, len <= kTile): bitonic sort in shared memory, in place
+__global__ void __launch_bounds__(1024) k_sort_tiles(const int2* tiles, int* src) {
+  __shared__ int sh[kTile];
+  const int2 t = tiles[blockIdx.x];
+  const int start = t.x, len = t.y;
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < len ? src[start + i] : INT_MAX;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const int a = sh[i], b = sh[ixj];
+          if ((a > b) == up) {
+            sh[i] = b;
+            sh[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += blockDim.x) src[start + i] = sh[i];
+}
+
+// segments of more than one sorted tile: the rank of a key is its index in its
+// tile plus the number of smaller keys in every other tile of the segment
+// (keys are unique positions in A)
+__global__ void k_merge_rank(const int4* mtiles, const int* src, int* out) {
+  // mtiles[b] = {seg_start, seg_len, tile_start, tile_len}
+  const int4 t = mtiles[blockIdx.x];
+  const int seg_s = t.x, seg_len = t.y, ts = t.z, tl = t.w;
+  for (int i = threadIdx.x; i < tl; i += blockDim.x) {
+    const int key = src[ts + i];
+    int rank = i;
+    for (int o = seg_s; o < seg_s + seg_len; o += kTile) {
+      if (o == ts) continue;
+      const int ol = min(kTile, seg_s + seg_len - o);
+      int lo = 0, hi = ol;  // count of keys < key in sorted [o, o+ol)
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (src[o + mid] < key) lo = mid + 1;
+        else hi = mid;
+      }
+      rank += lo;
+    }
+    out[seg_s + rank] = key;
+  }
+}
+
+__global__ void k_copy_ranges(const int2* ranges, const int* from, int* to) {
+  const int2 r = ranges[blockIdx.x];
+  for (int i = threadIdx.x; i < r.y; i += blockDim.x) to[r.x + i] = from[r.x + i];
+}
+
+__global__ void k_finish_transpose(const int* a_ptr, int m, const double* a_val64, const int* src,
+                                   int nnz, int* t_col, double* t_val64) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int s = src[p];
+    int lo = 0, hi = m;  // last row whose start <= s
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a_ptr[mid] <= s) lo = mid;
+      else hi = mid - 1;
+    }
+    t_col[p] = lo;
+    t_val64[p] = a_val64[s];
+  }
+}
+
+// ------------------------------------------------------------------ A2 scaling
+// row statistics of |K~_ij| = (dr_i |K_ij|) dc_j over a CSR orientation:
+// op 0 = max, op 1 = sum of |K~|^power.  In the A^T orientation the roles of
+// the two scale vectors swap (rowscale = dc, colscale = dr) but the product is
+// formed in the same order as in A: (dr_i |K_ij|) dc_j.
+__global__ void k_rowstat(const int* ptr, const int* col, const double* val, int nrows,
+                          const double* own, const double* other, int own_is_row, int op,
+                          double power, double* out) {
+  const int lane = threadIdx.x & 31;
+  const long long W = (long long)gridDim.x * blockDim.x / 32;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < nrows; r += W) {
+    const int s = ptr[r], e = ptr[r + 1];
+    const double so = own[r];
+    double acc = 0.0;
+    for (int p = s + lane; p < e; p += 32) {
+      const double a = fabs(val[p]);
+      const double o = other[col[p]];
+      const double kt = own_is_row ? (so * a) * o : (o * a) * so;
+      if (op == 0) acc = fmax(acc, kt);
+      else acc += power == 1.0 ? kt : pow(kt, power);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, acc, o);
+      acc = op == 0 ? fmax(acc, t) : acc + t;
+    }
+    if (lane == 0) out[r] = acc;
+  }
+}
+
+__global__ void k_apply_scale(double* d, const double* stat, int nrows) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride) {
+    const double s = stat[r];
+    d[r] = d[r] / (s > 0.0 ? sqrt(s) : 1.0);
+  }
+}
+
+__global__ void k_fill(double* p, double v, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
+}
+
+// ------------------------------------------------------------------ value formats
+__global__ void k_value_format(const double* val, int nnz, int* flags) {
+  // flags[0] &= every value exactly representable in bfloat16; flags[1] &= every value == 1
+  bool bf = true, one = true;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const double v = val[p];
+    bf &= (double)__bfloat162float(__double2bfloat16(v)) == v;
+    one &= v == 1.0;
+  }
+  if (!__all_sync(0xffffffffu, bf) && (threadIdx.x & 31) == 0) atomicAnd(flags, 0);
+  if (!__all_sync(0xffffffffu, one) && (threadIdx.x & 31) == 0) atomicAnd(flags + 1, 0);
+}
+
+// iteration matrix values: scaled (dr_i K_ij) dc_j or raw K_ij, in both orientations
+template <typename V>
+__global__ void k_iter_values(const int* ptr, const int* col, const double* val64, int nrows,
+                              const double* own, const double* other, int own_is_row, int scaled,
+                              V* out) {
+  const int lane = threadIdx.x & 31;
+  const long long W = (long long)gridDim.x * blockDim.x / 32;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < nrows; r += W) {
+    const int s = ptr[r], e = ptr[r + 1];
+    const double so = own[r];
+    for (int p = s + lane; p < e; p += 32) {
+      double v = val64[p];
+      if (scaled) {
+        const double o = other[col[p]];
+        v = own_is_row ? (so * v) * o : (o * v) * so;
+      }
+      out[p] = (V)v;
+    }
+  }
+}
+template <>
+__global__ void k_iter_values<__nv_bfloat16>(const int* ptr, const int* col, const double* val64,
+                                            int nrows, const double* own, const double* other,
+                                            int own_is_row, int scaled, __nv_bfloat16* out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long nnz = ptr[nrows];
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+    out[p] = __double2bfloat16(val64[p]);
+}
+
+// iteration-space vectors (A2/A3) and the float64 scalars of A3
+template <typename T>
+__global__ void k_iter_vectors(VecIn v, T* c, T* l, T* u, T* q, T* tw, T* sw, T* x0, T* y0,
+                               double* part) {
+  // part[b*6 + k]: k = 0 ||D_c c||^2, 1 ||D_r q||^2, 2 ||c||^2, 3 ||q||^2
+  double acc[4] = {0, 0, 0, 0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
+    const double d = v.dc[j], cj = v.c[j];
+    double lj = v.l[j], uj = v.u[j];
+    if (v.scaled) {
+      c[j] = (T)(d * cj);
+      lj = lj / d;
+      uj = uj / d;
+    } else {
+      c[j] = (T)cj;
+      tw[j] = (T)(d * d);
+    }
+    l[j] = (T)lj;
+    u[j] = (T)uj;
+    double x = v.x0 ? (v.scaled ? v.x0[j] / d : v.x0[j]) : 0.0;
+    x = fmin(fmax(x, lj), uj);
+    x0[2 * j] = (T)x;  // (x_j, dx_j) pair, no step yet
+    x0[2 * j + 1] = (T)0;
+    acc[0] += (d * cj) * (d * cj);
+    acc[2] += cj * cj;
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < v.m; i += stride) {
+    const double d = v.dr[i], qi = v.q[i];
+    if (v.scaled) {
+      q[i] = (T)(d * qi);
+    } else {
+      q[i] = (T)qi;
+      sw[i] = (T)(d * d);
+    }
+    double y = 0.0;
+    if (v.y0) {
+      const double yc = v.row_kind[i] == 2 ? -v.y0[i] : v.y0[i];  // caller convention -> canonical
+      y = v.scaled ? yc / d : yc;
+      if (v.row_kind[i] != 1) y = fmax(y, 0.0);
+    }
+    y0[i] = (T)y;
+    acc[1] += (d * qi) * (d * qi);
+    acc[3] += qi * qi;
+  }
+  double out[4];
+  block_sum<4>(acc, out);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) part[(size_t)blockIdx.x * 4 + k] = out[k];
+}
+
+__global__ void k_absmax_scaled(const int* ptr, const int* col, const double* val64, int nrows,
+                                const double* dr, const double* dc, double* part) {
+  double mx = 0.0;
+  const int lane = threadIdx.x & 31;
+  const long long W = (long long)gridDim.x * blockDim.x / 32;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < nrows; r += W) {
+    const int s = ptr[r], e = ptr[r + 1];
+    for (int p = s + lane; p < e; p += 32) mx = fmax(mx, fabs((dr[r] * val64[p]) * dc[col[p]]));
+  }
+  __shared__ double sh[kWarps];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kWarps; ++i) mx = fmax(mx, sh[i]);
+    part[blockIdx.x] = mx;
+  }
+}
+
+__global__ void k_finish_scalars(const double* vpart, int nv, const double* mpart, int nmx,
+                                 double* out) {
+  // out: [0] ||c~||, [1] ||q~||, [2] ||c||, [3] ||q||, [4] max |K~|
+  double a[4] = {0, 0, 0, 0}, r[4];
+  for (int b = threadIdx.x; b < nv; b += kBlock)
+    for (int k = 0; k < 4; ++k) a[k] += vpart[(size_t)b * 4 + k];
+  block_sum<4>(a, r);
+  __shared__ double mx;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int b = 0; b < nmx; ++b) m = fmax(m, mpart[b]);
+    mx = m;
+    for (int k = 0; k < 4; ++k) out[k] = sqrt(r[k]);
+    out[4] = mx;
+  }
+}
+
+// deterministic list of rows longer than thresh: flags, scan, scatter
+__global__ void k_long_flags(const int* ptr, int nrows, int thresh, int* flags) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride)
+    flags[r] = (ptr[r + 1] - ptr[r]) > thresh ? 1 : 0;
+}
+__global__ void k_long_scatter(const int* flags, const int* pos, int nrows, int* list) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride)
+    if (flags[r]) list[pos[r]] = (int)r;
+}
+
+}  // namespace
+
+int grid_for(long long work_items, int max_blocks) {
+  long long g = (work_items + kBlock - 1) / kBlock;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+#define RET(x)                                  \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return e_;           \
+  } while (0)
+
+cudaError_t setup_validate(const SetupIn& in, int* d_err, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  RET(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  k_validate_rows<<<grid_for(in.m + 1, G), kBlock, 0, s>>>(in, d_err);
+  RET(cudaGetLastError());
+  if (in.nnz > 0) {
+    k_validate_nnz<<<grid_for(in.nnz, G), kBlock, 0, s>>>(in, d_err);
+    RET(cudaGetLastError());
+  }
+  k_validate_cols<<<grid_for(in.n, G), kBlock, 0, s>>>(in, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_canonical(const SetupIn& in, int* a_ptr, int* a_col, double* a_val64, double* q,
+                            unsigned char* row_kind, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  k_canonical<<<grid_for((long long)in.m * 32, G), kBlock, 0, s>>>(in, a_ptr, a_col, a_val64, q,
+                                                                    row_kind);
+  return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan(const int* cnt, int* out, int N, int* bsum, cudaStream_t s) {
+  const int nb = (N + kScanTile - 1) / kScanTile;
+  if (nb > 0) {
+    k_scan_tiles<<<nb, kBlock, 0, s>>>(cnt, out, N, bsum);
+    RET(cudaGetLastError());
+  }
+  k_scan_bsum<<<1, kBlock, 0, s>>>(bsum, nb, out, N);
+  RET(cudaGetLastError());
+  if (nb > 0) {
+    k_scan_add<<<nb, kBlock, 0, s>>>(out, N, bsum);
+    RET(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+size_t scan_tmp_ints(long long N) { return (size_t)((N + kScanTile - 1) / kScanTile) + 1; }
+
+cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* a_col,
+                            const double* a_val64, int* t_ptr, int* t_col, double* t_val64,
+                            int* tmp, cudaStream_t s) {
+  // tmp layout (ints): cnt/cursor [n+1] | src [nnz] | src2 [nnz] | long list [n] | nlong [1]
+  //                    | tile descriptors [8 * (nnz/32 + 2)], 16-byte aligned | scan block sums
+  const int G = device_sm_count() * 8;
+  int* cnt = tmp;
+  int* src = cnt + (n + 1);
+  int* src2 = src + nnz;
+  int* long_list = src2 + nnz;
+  int* d_nlong = long_list + n;
+  size_t doff = (size_t)(d_nlong + 1 - tmp);
+  doff = (doff + 3) & ~(size_t)3;
+  int* desc = tmp + doff;
+  const size_t max_desc = (size_t)nnz / 32 + 2;  // bound on tiles of segments longer than 32
+  int* bsum = desc + 8 * max_desc;
+  RET(cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), s));
+  if (nnz > 0) {
+    k_count_cols<<<grid_for(nnz, G), kBlock, 0, s>>>(a_col, nnz, cnt);
+    RET(cudaGetLastError());
+  }
+  RET(exclusive_scan(cnt, t_ptr, n, bsum, s));
+  RET(cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), s));
+  if (nnz > 0) {
+    k_scatter<<<grid_for(nnz, G), kBlock, 0, s>>>(a_col, nnz, t_ptr, cnt, src);
+    RET(cudaGetLastError());
+  }
+  RET(cudaMemsetAsync(d_nlong, 0, sizeof(int), s));
+  k_segsort_small<<<grid_for(n, G), kBlock, 0, s>>>(t_ptr, n, src, long_list, d_nlong);
+  RET(cudaGetLastError());
+  int nlong = 0;
+  RET(cudaMemcpyAsync(&nlong, d_nlong, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RET(cudaStreamSynchronize(s));
+  if (nlong > 0) {
+    std::vector<int> ids(nlong);
+    RET(cudaMemcpyAsync(ids.data(), long_list, sizeof(int) * nlong, cudaMemcpyDeviceToHost, s));
+    std::vector<int> hp(n + 1);
+    RET(cudaMemcpyAsync(hp.data(), t_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+    RET(cudaStreamSynchronize(s));
+    std::sort(ids.begin(), ids.end());
+    std::vector<int2> tiles;
+    std::vector<int4> mtiles;
+    std::vector<int2> mranges;
+    for (int j : ids) {
+      const int st = hp[j], len = hp[j + 1] - hp[j];
+      for (int o = 0; o < len; o += kTile) tiles.push_back(make_int2(st + o, std::min(kTile, len - o)));
+      if (len > kTile) {
+        for (int o = 0; o < len; o += kTile)
+          mtiles.push_back(make_int4(st, len, st + o, std::min(kTile, len - o)));
+        mranges.push_back(make_int2(st, len));
+      }
+    }
+    if (tiles.size() > max_desc || mtiles.size() > max_desc) return cudaErrorInvalidValue;
+    int2* d_tiles = (int2*)desc;                       // 2 ints each
+    int4* d_mtiles = (int4*)(desc + 2 * max_desc);     // 4 ints each
+    int2* d_ranges = (int2*)(desc + 6 * max_desc);     // 2 ints each
+    RET(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s));
+    if (!mtiles.empty()) {
+      RET(cudaMemcpyAsync(d_mtiles, mtiles.data(), sizeof(int4) * mtiles.size(),
+                          cudaMemcpyHostToDevice, s));
+      RET(cudaMemcpyAsync(d_ranges, mranges.data(), sizeof(int2) * mranges.size(),
+                          cudaMemcpyHostToDevice, s));
+    }
+    k_sort_tiles<<<(int)tiles.size(), 1024, 0, s>>>(d_tiles, src);
+    RET(cudaGetLastError());
+    if (!mtiles.empty()) {
+      k_merge_rank<<<(int)mtiles.size(), kBlock, 0, s>>>(d_mtiles, src, src2);
+      RET(cudaGetLastError());
+      k_copy_ranges<<<(int)mranges.size(), kBlock, 0, s>>>(d_ranges, src2, src);
+      RET(cudaGetLastError());
+    }
+    // the host vectors are read by the copies above: wait before they go out of scope
+    RET(cudaStreamSynchronize(s));
+  }
+  if (nnz > 0) {
+    k_finish_transpose<<<grid_for(nnz, G), kBlock, 0, s>>>(a_ptr, m, a_val64, src, nnz, t_col,
+                                                         t_val64);
+    RET(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+size_t transpose_tmp_ints(int m, int n, long long nnz) {
+  return (size_t)(n + 1) + 2 * (size_t)nnz + (size_t)n + 1 + 4 + 8 * ((size_t)nnz / 32 + 2) +
+         scan_tmp_ints((long long)std::max(m, n) + 1) + 64;
+}
+
+cudaError_t setup_scaling(const ScaleIn& sc, double* dr, double* dc, double* stat_r,
+                          double* stat_c, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  k_fill<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, 1.0, sc.m);
+  RET(cudaGetLastError());
+  k_fill<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, 1.0, sc.n);
+  RET(cudaGetLastError());
+  const int gr = grid_for((long long)sc.m * 32, G), gc = grid_for((long long)sc.n * 32, G);
+  for (int it = 0; it < sc.ruiz_iters; ++it) {
+    k_rowstat<<<gr, kBlock, 0, s>>>(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, dr, dc, 1, 0, 1.0, stat_r);
+    RET(cudaGetLastError());
+    k_rowstat<<<gc, kBlock, 0, s>>>(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, dc, dr, 0, 0, 1.0, stat_c);
+    RET(cudaGetLastError());
+    k_apply_scale<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, stat_r, sc.m);
+    RET(cudaGetLastError());
+    k_apply_scale<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, stat_c, sc.n);
+    RET(cudaGetLastError());
+  }
+  if (sc.pc_alpha >= 0.0) {
+    k_rowstat<<<gr, kBlock, 0, s>>>(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, dr, dc, 1, 1,
+                                    2.0 - sc.pc_alpha, stat_r);
+    RET(cudaGetLastError());
+    k_rowstat<<<gc, kBlock, 0, s>>>(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, dc, dr, 0, 1, sc.pc_alpha,
+                                    stat_c);
+    RET(cudaGetLastError());
+    k_apply_scale<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, stat_r, sc.m);
+    RET(cudaGetLastError());
+    k_apply_scale<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, stat_c, sc.n);
+    RET(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+cudaError_t setup_value_format(const double* val64, int nnz, int* d_flags, int* h_bf16_exact,
+                               int* h_all_one, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  const int ones[2] = {1, 1};
+  RET(cudaMemcpyAsync(d_flags, ones, sizeof(ones), cudaMemcpyHostToDevice, s));
+  if (nnz > 0) {
+    k_value_format<<<grid_for(nnz, G), kBlock, 0, s>>>(val64, nnz, d_flags);
+    RET(cudaGetLastError());
+  }
+  int h[2];
+  RET(cudaMemcpyAsync(h, d_flags, sizeof(h), cudaMemcpyDeviceToHost, s));
+  RET(cudaStreamSynchronize(s));
+  *h_bf16_exact = h[0];
+  *h_all_one = h[1];
+  return cudaSuccess;
+}
+
+cudaError_t setup_iter_values(int which_type, const int* ptr, const int* col, const double* val64,
+                              int nrows, const double* own, const double* other, int own_is_row,
+                              int scaled, void* out, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  const int g = grid_for((long long)nrows * 32, G);
+  switch (which_type) {
+    case 0: k_iter_values<double><<<g, kBlock, 0, s>>>(ptr, col, val64, nrows, own, other, own_is_row, scaled, (double*)out); break;
+    case 1: k_iter_values<float><<<g, kBlock, 0, s>>>(ptr, col, val64, nrows, own, other, own_is_row, scaled, (float*)out); break;
+    case 2: k_iter_values<__nv_bfloat16><<<g, kBlock, 0, s>>>(ptr, col, val64, nrows, own, other, own_is_row, scaled, (__nv_bfloat16*)out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void* u, void* q,
+                               void* tw, void* sw, void* x0, void* y0, const int* a_ptr,
+                               const int* a_col, const double* a_val64, double* part,
+                               double* scalars_out, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  const int gv = grid_for(std::max(v.m, v.n), G);
+  if (fp32)
+    k_iter_vectors<float><<<gv, kBlock, 0, s>>>(v, (float*)c, (float*)l, (float*)u, (float*)q,
+                                                (float*)tw, (float*)sw, (float*)x0, (float*)y0, part);
+  else
+    k_iter_vectors<double><<<gv, kBlock, 0, s>>>(v, (double*)c, (double*)l, (double*)u, (double*)q,
+                                                 (double*)tw, (double*)sw, (double*)x0, (double*)y0,
+                                                 part);
+  RET(cudaGetLastError());
+  const int gm = grid_for((long long)v.m * 32, G);
+  double* mpart = part + (size_t)gv * 4;
+  k_absmax_scaled<<<gm, kBlock, 0, s>>>(a_ptr, a_col, a_val64, v.m, v.dr, v.dc, mpart);
+  RET(cudaGetLastError());
+  k_finish_scalars<<<1, kBlock, 0, s>>>(part, gv, mpart, gm, scalars_out);
+  return cudaGetLastError();
+}
+
+size_t setup_part_doubles(int m, int n) {
+  const int G = device_sm_count() * 8;
+  return (size_t)G * 4 + (size_t)G + 16;
+}
+
+cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, int* pos, int* bsum,
+                            int* list, int* h_count, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  k_long_flags<<<grid_for(nrows, G), kBlock, 0, s>>>(ptr, nrows, thresh, flags);
+  RET(cudaGetLastError());
+  RET(exclusive_scan(flags, pos, nrows, bsum, s));
+  k_long_scatter<<<grid_for(nrows, G), kBlock, 0, s>>>(flags, pos, nrows, list);
+  RET(cudaGetLastError());
+  RET(cudaMemcpyAsync(h_count, pos + nrows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace pdlp

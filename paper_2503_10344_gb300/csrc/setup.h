@@ -1,0 +1,66 @@
+// Host interfaces of the device setup (validation, canonical form, transpose,
+// scaling, iteration-space data).
+#pragma once
+
+#include "internal.h"
+
+namespace pdlp {
+
+enum SetupError { ERR_ROWPTR = 1, ERR_COL = 2, ERR_NONFINITE = 4, ERR_SENSE = 8, ERR_BOUNDS = 16 };
+
+struct SetupIn {  // caller's arrays (device)
+  int m, n;
+  long long nnz;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const double *b;
+  const char* sense;
+  const double *c, *l, *u;
+};
+
+struct ScaleIn {
+  int m, n;
+  const int *a_ptr, *a_col;
+  const double* a_val64;
+  const int *t_ptr, *t_col;
+  const double* t_val64;
+  int ruiz_iters;
+  double pc_alpha;  // < 0: no Pock-Chambolle pass
+};
+
+struct VecIn {
+  int m, n;
+  const double *dr, *dc;
+  const double *c, *l, *u, *q;  // canonical float64 data
+  const unsigned char* row_kind;
+  const double *x0, *y0;        // caller warm start (device) or NULL
+  int scaled;
+};
+
+cudaError_t setup_validate(const SetupIn& in, int* d_err, cudaStream_t s);
+cudaError_t setup_canonical(const SetupIn& in, int* a_ptr, int* a_col, double* a_val64, double* q,
+                            unsigned char* row_kind, cudaStream_t s);
+size_t transpose_tmp_ints(int m, int n, long long nnz);
+cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* a_col,
+                            const double* a_val64, int* t_ptr, int* t_col, double* t_val64,
+                            int* tmp, cudaStream_t s);
+cudaError_t setup_scaling(const ScaleIn& sc, double* dr, double* dc, double* stat_r,
+                          double* stat_c, cudaStream_t s);
+cudaError_t setup_value_format(const double* val64, int nnz, int* d_flags, int* h_bf16_exact,
+                               int* h_all_one, cudaStream_t s);
+// which_type: 0 double, 1 float, 2 bfloat16
+cudaError_t setup_iter_values(int which_type, const int* ptr, const int* col, const double* val64,
+                              int nrows, const double* own, const double* other, int own_is_row,
+                              int scaled, void* out, cudaStream_t s);
+size_t setup_part_doubles(int m, int n);
+// scalars_out: [0] ||c~||, [1] ||q~||, [2] ||c||, [3] ||q||, [4] max |K~_ij|
+cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void* u, void* q,
+                               void* tw, void* sw, void* x0, void* y0, const int* a_ptr,
+                               const int* a_col, const double* a_val64, double* part,
+                               double* scalars_out, cudaStream_t s);
+size_t scan_tmp_ints(long long N);
+cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, int* pos, int* bsum,
+                            int* list, int* h_count, cudaStream_t s);
+
+}  // namespace pdlp

@@ -1,0 +1,815 @@
+// Host driver of one PDLP solve and the C ABI of include/pdlp.h.
+//
+// Flow of pdlp_solve_device (all device work in stream order on the caller's
+// stream):
+//   1. carve the workspace; validate the inputs on the device (error bits);
+//   2. canonical form (A0), transpose (A1), value-format check, Ruiz +
+//      Pock-Chambolle scaling (A2), iteration-space matrix and vectors, the
+//      scalars of A3 (one small read-back);
+//   3. the KKT block once in "initial" mode: the KKT of the start point
+//      becomes the first restart reference;
+//   4. a CUDA graph holding `check_period` step attempts (primal + dual
+//      kernels each) followed by the KKT block is launched repeatedly; after
+//      each launch four bytes of state are copied to pinned host memory and
+//      the host reads them one launch behind, so the GPU never waits for the
+//      host.  Kernels launched after termination return at once.
+//   5. outputs in the caller's convention, result struct.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+
+#include "../../include/pdlp.h"
+#include "setup.h"
+
+namespace pdlp {
+
+thread_local std::string g_last_error;
+thread_local long long g_launches = 0;
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(PDLP_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+// ---------------------------------------------------------------- workspace
+struct Arena {
+  char* base;
+  size_t off;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+struct Bufs {
+  int *a_ptr, *a_col, *t_ptr, *t_col;
+  double *a_val64, *t_val64;
+  void *a_valit, *t_valit;
+  double *q64, *dr, *dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *stat_r, *stat_c;
+  unsigned char* row_kind;
+  void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
+  double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
+  int *a_long, *t_long, *tmp, *flags2;
+  DevState* st;
+};
+
+constexpr int kMaxLongBlocks = 1024;
+
+static int max_blocks() { return device_sm_count() * 8; }
+
+// bytes of one iterate element and one iteration-matrix value for a precision request
+static void elem_sizes(int precision, size_t* it_bytes, size_t* val_bytes) {
+  if (precision == PDLP_FP64) {
+    *it_bytes = 8;
+    *val_bytes = 8;
+  } else {
+    *it_bytes = 4;
+    *val_bytes = 4;  // bound: bf16 (2) / pattern (0) fit, FP32 fallback needs 4
+  }
+}
+
+static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precision) {
+  size_t eb, vb;
+  elem_sizes(precision, &eb, &vb);
+  const size_t G = (size_t)max_blocks() + kMaxLongBlocks;
+  const size_t M = (size_t)m, N = (size_t)n, Z = (size_t)nnz;
+  b.a_ptr = (int*)ar.take(4 * (M + 1));
+  b.t_ptr = (int*)ar.take(4 * (N + 1));
+  b.a_col = (int*)ar.take(4 * Z);
+  b.t_col = (int*)ar.take(4 * Z);
+  b.a_val64 = (double*)ar.take(8 * Z);
+  b.t_val64 = (double*)ar.take(8 * Z);
+  b.a_valit = ar.take(vb * Z);
+  b.t_valit = ar.take(vb * Z);
+  b.q64 = (double*)ar.take(8 * M);
+  b.dr = (double*)ar.take(8 * M);
+  b.dc = (double*)ar.take(8 * N);
+  b.Xc = (double*)ar.take(8 * N);
+  b.Xa = (double*)ar.take(8 * N);
+  b.Xl = (double*)ar.take(8 * N);
+  b.Yc = (double*)ar.take(8 * M);
+  b.Ya = (double*)ar.take(8 * M);
+  b.Yl = (double*)ar.take(8 * M);
+  b.stat_r = (double*)ar.take(8 * M);
+  b.stat_c = (double*)ar.take(8 * N);
+  b.row_kind = (unsigned char*)ar.take(M);
+  b.c_it = ar.take(eb * N);
+  b.l_it = ar.take(eb * N);
+  b.u_it = ar.take(eb * N);
+  b.tw = ar.take(eb * N);
+  b.q_it = ar.take(eb * M);
+  b.sw = ar.take(eb * M);
+  for (int k = 0; k < 2; ++k) {
+    b.x[k] = ar.take(2 * eb * N);  // (x_j, dx_j) pairs
+    b.y[k] = ar.take(eb * M);
+  }
+  b.sum_x = ar.take(eb * N);
+  b.sum_y = ar.take(eb * M);
+  b.part_p = (double*)ar.take(8 * G);
+  b.part_d = (double*)ar.take(8 * 2 * G);
+  b.part_r = (double*)ar.take(8 * 8 * G);
+  b.part_c = (double*)ar.take(8 * 10 * G);
+  b.part_setup = (double*)ar.take(8 * setup_part_doubles(m, n));
+  b.scalars = (double*)ar.take(8 * 8);
+  b.a_long = (int*)ar.take(4 * (M + 1));
+  b.t_long = (int*)ar.take(4 * (N + 1));
+  const size_t tmp_ints = std::max(transpose_tmp_ints(m, n, nnz),
+                                   2 * (std::max(M, N) + 1) + scan_tmp_ints((long long)std::max(M, N) + 1));
+  b.tmp = (int*)ar.take(4 * tmp_ints);
+  b.flags2 = (int*)ar.take(16);
+  b.st = (DevState*)ar.take(sizeof(DevState));
+  return ar.off + 256;
+}
+
+static int auto_lanes(double avg_len) {
+  int l = 2;
+  while (l < 32 && l < avg_len) l <<= 1;
+  return l;
+}
+
+static int long_thresh(int lanes) { return std::max(1024, 128 * lanes); }
+
+static bool valid_lanes(int l) { return l == 2 || l == 4 || l == 8 || l == 16 || l == 32; }
+
+// ---------------------------------------------------------------- solver
+struct Solve {
+  int m, n;
+  long long nnz;
+  Mode mode;
+  int lanes_a, lanes_t;
+  IterRaw ir;
+  KktRaw kr;
+  cudaStream_t s;
+
+  cudaError_t iter(int which) {
+    ++g_launches;
+    const int lanes = which == IK_PRIMAL ? lanes_t : lanes_a;
+    switch (mode) {
+      case MODE_FP64: return launch_iter_fp64(which, lanes, ir, s);
+      case MODE_FP32: return launch_iter_fp32(which, lanes, ir, s);
+      case MODE_BF16: return launch_iter_bf16(which, lanes, ir, s);
+      default: return launch_iter_pat(which, lanes, ir, s);
+    }
+  }
+  cudaError_t kkt_block() {
+    cudaError_t e;
+    for (int k : {KK_PREP, KK_ROWS, KK_COLS, KK_FINAL, KK_APPLY, KK_END}) {
+      ++g_launches;
+      if ((e = launch_kkt(k, lanes_a, lanes_t, kr, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+};
+
+static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, const void* c,
+                        const void* l, const void* u, const pdlp_params* p, const void* x_out,
+                        const void* y_out, const pdlp_result* r) {
+  if (!A || !r || !p) return fail(PDLP_ERR_INVALID_INPUT, "NULL problem, params or result");
+  if (p->struct_size != sizeof(pdlp_params))
+    return fail(PDLP_ERR_INVALID_INPUT, "pdlp_params.struct_size mismatch (use pdlp_default_params)");
+  if (A->m < 0 || A->n < 1 || A->nnz < 0)
+    return fail(PDLP_ERR_INVALID_INPUT, "need m >= 0, n >= 1, nnz >= 0");
+  if (A->nnz >= (int64_t)INT32_MAX)
+    return fail(PDLP_ERR_INVALID_INPUT, "nnz must be below 2^31 for one LP");
+  if (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
+    return fail(PDLP_ERR_INVALID_INPUT, "NULL CSR array");
+  if ((A->m > 0 && (!b || !sense)) || !c || !l || !u || !x_out || (A->m > 0 && !y_out))
+    return fail(PDLP_ERR_INVALID_INPUT, "NULL vector argument");
+  if (!(p->tol > 0.0) || p->iter_limit < 0 || p->check_period < 1 || p->ruiz_iters < 0 ||
+      !(p->time_limit_s > 0.0))
+    return fail(PDLP_ERR_INVALID_INPUT, "invalid parameter value");
+  if (p->precision != PDLP_FP64 && p->precision != PDLP_FP32 && p->precision != PDLP_FP32_BF16A)
+    return fail(PDLP_ERR_INVALID_INPUT, "unknown precision mode");
+  if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)))
+    return fail(PDLP_ERR_INVALID_INPUT, "lanes must be 0, 2, 4, 8, 16 or 32");
+  return PDLP_OK;
+}
+
+// Kernel timing request (pdlp_time_kernels): after the setup of a solve, each
+// fused kernel is launched `reps` times back to back from a CUDA graph.
+struct TimingReq {
+  int reps;
+  double* ms;     // [5] primal, dual, attempt (primal + dual), KKT pass over A, over A^T
+  double* bytes;  // [5] algorithmic bytes per launch of the same kernels
+};
+
+static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
+                                    const TimingReq& tq);
+
+static int solve_device(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                        const double* l, const double* u, const pdlp_params* p, const double* x0,
+                        const double* y0, double* x_out, double* y_out, pdlp_result* r,
+                        const pdlp_diagnostics* dg, void* workspace, size_t ws_bytes,
+                        cudaStream_t s, const TimingReq* tq = nullptr) {
+  const int m = A->m, n = A->n;
+  const long long nnz = A->nnz;
+  g_launches = 0;
+  memset(r, 0, sizeof(*r));
+  Bufs bf;
+  Arena dry{nullptr, 0};
+  const size_t need = carve(dry, bf, m, n, nnz, p->precision);
+  void* own_ws = nullptr;
+  if (!workspace) {
+    cudaError_t e = cudaMallocAsync(&own_ws, need, s);
+    if (e != cudaSuccess) return fail(PDLP_ERR_OOM, std::string("workspace: ") + cudaGetErrorString(e));
+    workspace = own_ws;
+  } else if (ws_bytes < need || ((uintptr_t)workspace & 255)) {
+    return fail(PDLP_ERR_OOM, "workspace smaller than pdlp_workspace_size or not 256-byte aligned");
+  }
+  struct Freer {
+    void* p;
+    cudaStream_t s;
+    ~Freer() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  } freer{own_ws, s};
+  Arena ar{(char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255), 0};
+  carve(ar, bf, m, n, nnz, p->precision);
+
+  cudaEvent_t e0, e1, e2;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  CUDA_TRY(cudaEventCreate(&e2));
+  struct EvFree {
+    cudaEvent_t a, b, c;
+    ~EvFree() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaEventDestroy(c);
+    }
+  } evfree{e0, e1, e2};
+  CUDA_TRY(cudaEventRecord(e0, s));
+
+  // ---- validation (A0 preconditions)
+  SetupIn in{m, n, nnz, A->row_ptr, A->col, A->val, b, sense, c, l, u};
+  CUDA_TRY(setup_validate(in, bf.flags2, s));
+  g_launches += 3;
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, bf.flags2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) {
+    std::string msg = "invalid input:";
+    if (err & ERR_ROWPTR) msg += " row_ptr";
+    if (err & ERR_COL) msg += " column index";
+    if (err & ERR_NONFINITE) msg += " non-finite value";
+    if (err & ERR_SENSE) msg += " sense";
+    if (err & ERR_BOUNDS) msg += " bounds";
+    return fail(PDLP_ERR_INVALID_INPUT, msg);
+  }
+  // ---- A0, A1
+  CUDA_TRY(setup_canonical(in, bf.a_ptr, bf.a_col, bf.a_val64, bf.q64, bf.row_kind, s));
+  CUDA_TRY(setup_transpose(m, n, (int)nnz, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col,
+                           bf.t_val64, bf.tmp, s));
+  g_launches += 10;
+  // ---- mode
+  Mode mode = MODE_FP64;
+  int bf16_exact = 0, all_one = 0;
+  if (p->precision == PDLP_FP32) mode = MODE_FP32;
+  if (p->precision == PDLP_FP32_BF16A) {
+    CUDA_TRY(setup_value_format(bf.a_val64, (int)nnz, bf.flags2, &bf16_exact, &all_one, s));
+    ++g_launches;
+    mode = all_one ? MODE_PAT : (bf16_exact ? MODE_BF16 : MODE_FP32);
+  }
+  const int scaled = (mode == MODE_FP64 || mode == MODE_FP32) ? 1 : 0;
+  const int fp32 = mode != MODE_FP64;
+  // ---- A2
+  ScaleIn sc{m, n, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col, bf.t_val64, p->ruiz_iters,
+             p->pc_alpha};
+  CUDA_TRY(setup_scaling(sc, bf.dr, bf.dc, bf.stat_r, bf.stat_c, s));
+  g_launches += 2 + 4 * p->ruiz_iters + (p->pc_alpha >= 0 ? 4 : 0);
+  if (mode != MODE_PAT) {
+    const int vt = mode == MODE_FP64 ? 0 : (mode == MODE_FP32 ? 1 : 2);
+    CUDA_TRY(setup_iter_values(vt, bf.a_ptr, bf.a_col, bf.a_val64, m, bf.dr, bf.dc, 1, scaled,
+                               bf.a_valit, s));
+    CUDA_TRY(setup_iter_values(vt, bf.t_ptr, bf.t_col, bf.t_val64, n, bf.dc, bf.dr, 0, scaled,
+                               bf.t_valit, s));
+    g_launches += 2;
+  }
+  VecIn vi{m, n, bf.dr, bf.dc, c, l, u, bf.q64, bf.row_kind, x0, y0, scaled};
+  CUDA_TRY(setup_iter_vectors(vi, fp32, bf.c_it, bf.l_it, bf.u_it, bf.q_it, bf.tw, bf.sw, bf.x[0],
+                              bf.y[0], bf.a_ptr, bf.a_col, bf.a_val64, bf.part_setup, bf.scalars, s));
+  g_launches += 3;
+  double sca[5];
+  CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
+  // ---- launch shapes and long rows
+  const int lanes_a = p->lanes_A ? p->lanes_A : auto_lanes(m ? (double)nnz / m : 1.0);
+  const int lanes_t = p->lanes_AT ? p->lanes_AT : auto_lanes((double)nnz / n);
+  const int th_a = long_thresh(lanes_a), th_t = long_thresh(lanes_t);
+  int nlong_a = 0, nlong_t = 0;
+  {
+    const size_t R = (size_t)std::max(m, n) + 1;
+    int* flags = bf.tmp;
+    int* pos = flags + R;
+    int* bsum = pos + R + 1;
+    if (m > 0) CUDA_TRY(setup_long_rows(bf.a_ptr, m, th_a, flags, pos, bsum, bf.a_long, &nlong_a, s));
+    CUDA_TRY(setup_long_rows(bf.t_ptr, n, th_t, flags, pos, bsum, bf.t_long, &nlong_t, s));
+    g_launches += 10;
+  }
+  const int MB = max_blocks();
+  const int gp_short = grid_for((long long)n * lanes_t, MB);
+  const int gd_short = grid_for((long long)std::max(m, 1) * lanes_a, MB);
+  const int gp = gp_short + std::min(nlong_t, kMaxLongBlocks);
+  const int gd = gd_short + std::min(nlong_a, kMaxLongBlocks);
+  const int ge = grid_for(std::max(m, n), MB);
+
+  IterRaw ir;
+  ir.a_ptr = bf.a_ptr; ir.a_col = bf.a_col; ir.a_val = mode == MODE_PAT ? nullptr : bf.a_valit;
+  ir.t_ptr = bf.t_ptr; ir.t_col = bf.t_col; ir.t_val = mode == MODE_PAT ? nullptr : bf.t_valit;
+  ir.a_long = bf.a_long; ir.t_long = bf.t_long;
+  ir.a_nlong = nlong_a; ir.t_nlong = nlong_t; ir.a_thresh = th_a; ir.t_thresh = th_t;
+  ir.m = m; ir.n = n;
+  ir.c = bf.c_it; ir.l = bf.l_it; ir.u = bf.u_it; ir.q = bf.q_it;
+  ir.tw = scaled ? nullptr : bf.tw; ir.sw = scaled ? nullptr : bf.sw;
+  ir.row_kind = bf.row_kind;
+  for (int k = 0; k < 2; ++k) { ir.x[k] = bf.x[k]; ir.y[k] = bf.y[k]; }
+  ir.sum_x = bf.sum_x; ir.sum_y = bf.sum_y;
+  ir.part_p = bf.part_p; ir.part_d = bf.part_d;
+  ir.grid_p_short = gp_short; ir.grid_p = gp; ir.grid_d_short = gd_short; ir.grid_d = gd;
+  ir.st = bf.st;
+
+  KktRaw kr;
+  kr.a_ptr = bf.a_ptr; kr.a_col = bf.a_col; kr.a_val64 = bf.a_val64;
+  kr.t_ptr = bf.t_ptr; kr.t_col = bf.t_col; kr.t_val64 = bf.t_val64;
+  kr.a_long = bf.a_long; kr.t_long = bf.t_long;
+  kr.a_nlong = nlong_a; kr.t_nlong = nlong_t; kr.a_thresh = th_a; kr.t_thresh = th_t;
+  kr.m = m; kr.n = n;
+  kr.c = c; kr.l = l; kr.u = u; kr.q = bf.q64; kr.dr = bf.dr; kr.dc = bf.dc;
+  kr.row_kind = bf.row_kind;
+  for (int k = 0; k < 2; ++k) { kr.x[k] = bf.x[k]; kr.y[k] = bf.y[k]; }
+  kr.sum_x = bf.sum_x; kr.sum_y = bf.sum_y;
+  kr.Xc = bf.Xc; kr.Xa = bf.Xa; kr.Xl = bf.Xl; kr.Yc = bf.Yc; kr.Ya = bf.Ya; kr.Yl = bf.Yl;
+  kr.part_r = bf.part_r; kr.part_c = bf.part_c;
+  kr.grid_r_short = gd_short; kr.grid_r = gd; kr.grid_c_short = gp_short; kr.grid_c = gp;
+  kr.grid_e = ge;
+  kr.scaled = scaled; kr.fp32 = fp32;
+  kr.st = bf.st;
+
+  // ---- A3: initial state
+  CUDA_TRY(cudaStreamSynchronize(s));  // scalars
+  DevState hs;
+  memset(&hs, 0, sizeof(hs));
+  const double nct = sca[0], nqt = sca[1], kmax = sca[4];
+  hs.omega = (nct > 1e-10 && nqt > 1e-10) ? nct / nqt : 1.0;
+  hs.eta = kmax > 0.0 ? 1.0 / kmax : 1.0;
+  if (p->fixed_eta > 0.0) hs.eta = p->fixed_eta;
+  if (p->fixed_omega > 0.0) hs.omega = p->fixed_omega;
+  hs.check_due = 1;
+  hs.init_pending = 1;
+  hs.prev_cand = INFINITY;
+  hs.iter_limit = p->iter_limit;
+  hs.period = p->check_period;
+  hs.adaptive = p->adaptive_step ? 1 : 0;
+  hs.restarts_on = p->restarts ? 1 : 0;
+  hs.terminate = p->terminate ? 1 : 0;
+  hs.tol = p->tol;
+  hs.norm_c = sca[2];
+  hs.norm_q = sca[3];
+  if (dg && dg->attempt_capacity > 0 && dg->eta && dg->eta_bar && dg->accepted) {
+    hs.tr_eta = dg->eta;
+    hs.tr_eta_bar = dg->eta_bar;
+    hs.tr_accepted = (signed char*)dg->accepted;
+    hs.tr_cap = dg->attempt_capacity;
+  }
+  if (dg && dg->check_capacity > 0 && dg->restart && dg->omega) {
+    hs.tr_restart = (signed char*)dg->restart;
+    hs.tr_omega = dg->omega;
+    hs.tr_check_cap = dg->check_capacity;
+  }
+  CUDA_TRY(cudaMemcpyAsync(bf.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+  const size_t eb = fp32 ? 4 : 8;
+  CUDA_TRY(cudaMemsetAsync(bf.sum_x, 0, eb * n, s));
+  if (m) CUDA_TRY(cudaMemsetAsync(bf.sum_y, 0, eb * m, s));
+  CUDA_TRY(cudaMemsetAsync(bf.Xl, 0, 8 * (size_t)n, s));
+  if (m) CUDA_TRY(cudaMemsetAsync(bf.Yl, 0, 8 * (size_t)m, s));
+
+  Solve sv{m, n, nnz, mode, lanes_a, lanes_t, ir, kr, s};
+  CUDA_TRY(sv.kkt_block());  // initial KKT and restart anchors
+  CUDA_TRY(cudaEventRecord(e1, s));
+  if (tq) return time_kernels_after_setup(sv, bf.st, mode, nnz, *tq);
+
+  // ---- iteration phase: graph of one check period
+  DevState* hm = nullptr;  // pinned mirror of the first 16 bytes of the state, 2 slots
+  CUDA_TRY(cudaMallocHost(&hm, 2 * sizeof(DevState)));
+  struct HostFree {
+    void* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hfree{hm};
+  cudaEvent_t ev[2];
+  CUDA_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+  struct EvFree2 {
+    cudaEvent_t* e;
+    ~EvFree2() {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+    }
+  } ev2{ev};
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_nodes = 0;
+  if (p->iter_limit > 0) {
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    Solve cap = sv;
+    cap.s = cs;
+    const long long before = g_launches;
+    cudaGraph_t graph;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int a = 0; a < p->check_period && ce == cudaSuccess; ++a) {
+      ce = cap.iter(IK_PRIMAL);
+      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
+    }
+    if (ce == cudaSuccess) ce = cap.kkt_block();
+    cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    CUDA_TRY(ee);
+    graph_nodes = g_launches - before;
+    g_launches = before;
+    cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(ie);
+  }
+  struct GraphFree {
+    cudaGraphExec_t g;
+    ~GraphFree() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  } gfree{gexec};
+
+  const auto t_start = std::chrono::steady_clock::now();
+  long long launched = 0, seen = 0;
+  bool forced = false;
+  const long long max_launches =
+      (p->iter_limit / p->check_period + 2) * 64 + 1024;  // rejections re-run a chunk
+  auto launch = [&]() -> cudaError_t {
+    cudaError_t e = cudaGraphLaunch(gexec, s);
+    if (e != cudaSuccess) return e;
+    g_launches += graph_nodes;
+    e = cudaMemcpyAsync(&hm[launched & 1], bf.st, 16, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev[launched & 1], s);
+    ++launched;
+    return e;
+  };
+  int host_status = 0;
+  if (p->iter_limit > 0) {
+    CUDA_TRY(launch());
+    while (true) {
+      if (launched - seen < 2) CUDA_TRY(launch());
+      CUDA_TRY(cudaEventSynchronize(ev[seen & 1]));
+      const DevState& h = hm[seen & 1];
+      ++seen;
+      if (h.status != 0) {
+        host_status = h.status;
+        break;
+      }
+      if (p->verbose)
+        fprintf(stderr, "pdlp: chunk %lld iters %lld\n", seen, (long long)h.iters);
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      if (!forced && el > p->time_limit_s) {
+        // ask for a final check: the next chunk's steps are skipped and its KKT block terminates
+        static const int one[2] = {1, 1};
+        CUDA_TRY(cudaMemcpyAsync(&bf.st->force_final, &one[0], sizeof(int), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(&bf.st->check_due, &one[1], sizeof(int), cudaMemcpyHostToDevice, s));
+        forced = true;
+      }
+      if (launched > max_launches) return fail(PDLP_ERR_TIMEOUT, "iteration loop did not terminate");
+    }
+  }
+  (void)host_status;
+  CUDA_TRY(cudaStreamSynchronize(s));  // drain the chunk launched behind the terminating one
+  CUDA_TRY(cudaEventRecord(e2, s));
+  // ---- A11: outputs
+  CUDA_TRY(launch_output(kr, x_out, m ? y_out : nullptr, dg ? dg->x_cur : nullptr,
+                         dg && m ? dg->y_cur : nullptr, dg ? dg->x_avg : nullptr,
+                         dg && m ? dg->y_avg : nullptr, s));
+  ++g_launches;
+  DevState fs;
+  CUDA_TRY(cudaMemcpyAsync(&fs, bf.st, sizeof(fs), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  float ms_setup = 0.f, ms_solve = 0.f;
+  cudaEventElapsedTime(&ms_setup, e0, e1);
+  cudaEventElapsedTime(&ms_solve, e1, e2);
+
+  r->status = p->iter_limit == 0 ? PDLP_ITER_LIMIT : fs.status;
+  r->precision_used = mode == MODE_FP64 ? PDLP_FP64
+                      : mode == MODE_FP32 ? PDLP_FP32
+                      : mode == MODE_BF16 ? PDLP_USED_BF16
+                                          : PDLP_USED_PATTERN;
+  r->iters = fs.iters;
+  r->attempts = fs.attempts;
+  r->restarts = fs.restarts;
+  r->kkt_checks = fs.checks;
+  const int k = fs.used_avg ? 1 : 0;
+  r->used_average = k;
+  r->primal_obj = fs.pobj[k];
+  r->dual_obj = fs.dobj[k];
+  r->rel_primal_res = fs.relp[k];
+  r->rel_dual_res = fs.reld[k];
+  r->rel_gap = fs.relgap[k];
+  r->rel_kkt = std::max(r->rel_primal_res, std::max(r->rel_dual_res, r->rel_gap));
+  r->eta = fs.eta;
+  r->omega = fs.omega;
+  r->setup_s = ms_setup * 1e-3;
+  r->solve_s = ms_solve * 1e-3;
+  r->kernel_launches = g_launches;
+  return PDLP_OK;
+}
+
+static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
+                                    const TimingReq& tq) {
+  const cudaStream_t s = sv.s;
+  const int m = sv.m, n = sv.n;
+  // keep every step attempt live: no KKT check becomes due while timing
+  const int big_period = 1 << 30;
+  const long long big_limit = 1LL << 62;
+  static const int zero = 0, one = 1;
+  CUDA_TRY(cudaMemcpyAsync(&st->period, &big_period, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&st->iter_limit, &big_limit, sizeof(long long), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  cudaStream_t cs;
+  CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  struct SFree {
+    cudaStream_t s;
+    ~SFree() { cudaStreamDestroy(s); }
+  } sfree{cs};
+  cudaEvent_t a, b;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  struct EFree {
+    cudaEvent_t a, b;
+    ~EFree() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } efree{a, b};
+  Solve cap = sv;
+  cap.s = cs;
+  // which: 0 primal, 1 dual, 2 attempt, 3 KKT rows, 4 KKT cols
+  auto time_one = [&](int which, double* out_ms) -> int {
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int i = 0; i < tq.reps && ce == cudaSuccess; ++i) {
+      if (which == 0 || which == 2) ce = cap.iter(IK_PRIMAL);
+      if (ce == cudaSuccess && (which == 1 || which == 2)) ce = cap.iter(IK_DUAL);
+      if (which == 3) ce = launch_kkt(KK_ROWS, sv.lanes_a, sv.lanes_t, sv.kr, cs);
+      if (which == 4) ce = launch_kkt(KK_COLS, sv.lanes_a, sv.lanes_t, sv.kr, cs);
+    }
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    CUDA_TRY(ee);
+    cudaGraphExec_t ge;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(ie);
+    struct GFree {
+      cudaGraphExec_t g;
+      ~GFree() { cudaGraphExecDestroy(g); }
+    } gfree{ge};
+    CUDA_TRY(cudaGraphLaunch(ge, s));  // warm
+    CUDA_TRY(cudaEventRecord(a, s));
+    CUDA_TRY(cudaGraphLaunch(ge, s));
+    CUDA_TRY(cudaEventRecord(b, s));
+    CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    *out_ms = (double)ms / tq.reps;
+    g_launches += 2LL * tq.reps * (which == 2 ? 2 : 1);
+    return PDLP_OK;
+  };
+  int rc;
+  for (int w = 0; w < 3; ++w)
+    if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
+  CUDA_TRY(cudaMemcpyAsync(&st->check_due, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+  for (int w = 3; w < 5; ++w)
+    if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
+  CUDA_TRY(cudaMemcpyAsync(&st->check_due, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  // algorithmic bytes per launch: every array the kernel needs, each element once
+  // (gathered vectors counted once, not once per nonzero)
+  const double M = m, N = n, Z = (double)nnz;
+  const double sx = mode == MODE_FP64 ? 8 : 4;
+  const double sv_b = mode == MODE_FP64 ? 8 : mode == MODE_FP32 ? 4 : mode == MODE_BF16 ? 2 : 0;
+  const double impl = (mode == MODE_BF16 || mode == MODE_PAT) ? 1 : 0;
+  const double val64 = mode == MODE_PAT ? 0 : 8;
+  // primal: row_ptr, col, values; y gathered; x (pair) read, c, l, u (+ tw), pair write, sum r/w
+  tq.bytes[0] = 4 * (N + 1) + Z * (4 + sv_b) + M * sx + N * sx * (2 + 3 + impl + 2 + 2);
+  // dual: row_ptr, col, values; x pairs gathered; y, q (+ sw), row kind, y write, sum r/w
+  tq.bytes[1] = 4 * (M + 1) + Z * (4 + sv_b) + N * 2 * sx + M * (sx * (1 + 1 + impl + 1 + 2) + 1);
+  tq.bytes[2] = tq.bytes[0] + tq.bytes[1];
+  // KKT over A: row_ptr, col, float64 values; both candidates gathered; q, D_r, kind, y c/a, y anchor
+  tq.bytes[3] = 4 * (M + 1) + Z * (4 + val64) + N * 16 + M * (8 + 8 + 1 + 16 + 8);
+  // KKT over A^T: row_ptr, col, values; both dual candidates gathered; c, l, u, D_c, x c/a, x anchor
+  tq.bytes[4] = 4 * (N + 1) + Z * (4 + val64) + M * 16 + N * (32 + 16 + 8);
+  return PDLP_OK;
+}
+
+}  // namespace pdlp
+
+using namespace pdlp;
+
+extern "C" {
+
+int pdlp_default_params(pdlp_params* p) {
+  if (!p) return fail(PDLP_ERR_INVALID_INPUT, "NULL params");
+  memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(pdlp_params);
+  p->tol = 1e-4;
+  p->iter_limit = 1000000;
+  p->time_limit_s = 3600.0;
+  p->precision = PDLP_FP64;
+  p->check_period = 64;
+  p->ruiz_iters = 10;
+  p->pc_alpha = 1.0;
+  p->adaptive_step = 1;
+  p->restarts = 1;
+  p->terminate = 1;
+  return PDLP_OK;
+}
+
+size_t pdlp_workspace_size(int32_t m, int32_t n, int64_t nnz, const pdlp_params* p) {
+  if (m < 0 || n < 1 || nnz < 0 || nnz >= (int64_t)INT32_MAX) return 0;
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  Bufs b;
+  Arena ar{nullptr, 0};
+  return carve(ar, b, m, n, nnz, p->precision);
+}
+
+int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, double* x_out, double* y_out, pdlp_result* r,
+                      const pdlp_diagnostics* diag, void* workspace, size_t workspace_bytes,
+                      void* stream) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  int rc = check_inputs(A, b, sense, c, l, u, p, x_out, y_out, r);
+  if (rc) return rc;
+  return solve_device(A, b, sense, c, l, u, p, x0, y0, x_out, y_out, r, diag, workspace,
+                      workspace_bytes, (cudaStream_t)stream);
+}
+
+int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+               const double* l, const double* u, const pdlp_params* p, const double* x0,
+               const double* y0, double* x_out, double* y_out, pdlp_result* r,
+               const pdlp_diagnostics* diag) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  int rc = check_inputs(A, b, sense, c, l, u, p, x_out, y_out, r);
+  if (rc) return rc;
+  const size_t M = (size_t)A->m, N = (size_t)A->n, Z = (size_t)A->nnz;
+  const size_t TA = diag && diag->attempt_capacity > 0 ? (size_t)diag->attempt_capacity : 0;
+  const size_t TC = diag && diag->check_capacity > 0 ? (size_t)diag->check_capacity : 0;
+  cudaStream_t s;
+  CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct StreamFree {
+    cudaStream_t s;
+    ~StreamFree() { cudaStreamDestroy(s); }
+  } sfree{s};
+  // one device block for the inputs, outputs and diagnostics
+  auto lay = [&](Arena& ar, void** ptrs) {
+    ptrs[0] = ar.take(8 * (M + 1));  // row_ptr
+    ptrs[1] = ar.take(4 * Z);        // col
+    ptrs[2] = ar.take(8 * Z);        // val
+    ptrs[3] = ar.take(8 * M);        // b
+    ptrs[4] = ar.take(M);            // sense
+    ptrs[5] = ar.take(8 * N);        // c
+    ptrs[6] = ar.take(8 * N);        // l
+    ptrs[7] = ar.take(8 * N);        // u
+    ptrs[8] = ar.take(8 * N);        // x0
+    ptrs[9] = ar.take(8 * M);        // y0
+    ptrs[10] = ar.take(8 * N);       // x_out
+    ptrs[11] = ar.take(8 * M);       // y_out
+    for (int k = 0; k < 4; ++k) ptrs[12 + k] = ar.take(8 * ((k & 1) ? M : N));  // iterates
+    ptrs[16] = ar.take(8 * TA);      // eta
+    ptrs[17] = ar.take(8 * TA);      // eta_bar
+    ptrs[18] = ar.take(TA);          // accepted
+    ptrs[19] = ar.take(TC);          // restart
+    ptrs[20] = ar.take(8 * TC);      // omega
+  };
+  void* dp[21];
+  Arena dry{nullptr, 0};
+  lay(dry, dp);
+  const size_t io_bytes = dry.off + 256;
+  const size_t ws_bytes = pdlp_workspace_size(A->m, A->n, A->nnz, p);
+  void* dev = nullptr;
+  {
+    cudaError_t e = cudaMallocAsync(&dev, io_bytes + ws_bytes + 256, s);
+    if (e != cudaSuccess) return fail(PDLP_ERR_OOM, std::string("device buffers: ") + cudaGetErrorString(e));
+  }
+  struct DevFree {
+    void* p;
+    cudaStream_t s;
+    ~DevFree() {
+      cudaFreeAsync(p, s);
+      cudaStreamSynchronize(s);
+    }
+  } dfree{dev, s};
+  Arena ar{(char*)dev, 0};
+  lay(ar, dp);
+  void* ws = (char*)dev + ((io_bytes + 255) & ~(size_t)255);
+  auto h2d = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return bytes && src ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return bytes && dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+  };
+  CUDA_TRY(h2d(dp[0], A->row_ptr, 8 * (M + 1)));
+  CUDA_TRY(h2d(dp[1], A->col, 4 * Z));
+  CUDA_TRY(h2d(dp[2], A->val, 8 * Z));
+  CUDA_TRY(h2d(dp[3], b, 8 * M));
+  CUDA_TRY(h2d(dp[4], sense, M));
+  CUDA_TRY(h2d(dp[5], c, 8 * N));
+  CUDA_TRY(h2d(dp[6], l, 8 * N));
+  CUDA_TRY(h2d(dp[7], u, 8 * N));
+  CUDA_TRY(h2d(dp[8], x0, 8 * N));
+  CUDA_TRY(h2d(dp[9], y0, 8 * M));
+  pdlp_csr dA{A->m, A->n, A->nnz, (const int64_t*)dp[0], (const int32_t*)dp[1], (const double*)dp[2]};
+  pdlp_diagnostics ddg{(double*)dp[12], (double*)dp[13], (double*)dp[14], (double*)dp[15],
+                       (int64_t)TA, (double*)dp[16], (double*)dp[17], (int8_t*)dp[18],
+                       (int64_t)TC, (int8_t*)dp[19], (double*)dp[20]};
+  rc = solve_device(&dA, (const double*)dp[3], (const char*)dp[4], (const double*)dp[5],
+                    (const double*)dp[6], (const double*)dp[7], p, x0 ? (const double*)dp[8] : nullptr,
+                    y0 ? (const double*)dp[9] : nullptr, (double*)dp[10], (double*)dp[11], r,
+                    diag ? &ddg : nullptr, ws, ws_bytes, s);
+  if (rc) return rc;
+  CUDA_TRY(d2h(x_out, dp[10], 8 * N));
+  CUDA_TRY(d2h(y_out, dp[11], 8 * M));
+  if (diag) {
+    CUDA_TRY(d2h(diag->x_cur, dp[12], 8 * N));
+    CUDA_TRY(d2h(diag->y_cur, dp[13], 8 * M));
+    CUDA_TRY(d2h(diag->x_avg, dp[14], 8 * N));
+    CUDA_TRY(d2h(diag->y_avg, dp[15], 8 * M));
+    if (diag->eta && diag->eta_bar && diag->accepted) {
+      CUDA_TRY(d2h(diag->eta, dp[16], 8 * TA));
+      CUDA_TRY(d2h(diag->eta_bar, dp[17], 8 * TA));
+      CUDA_TRY(d2h(diag->accepted, dp[18], TA));
+    }
+    if (diag->restart && diag->omega) {
+      CUDA_TRY(d2h(diag->restart, dp[19], TC));
+      CUDA_TRY(d2h(diag->omega, dp[20], 8 * TC));
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PDLP_OK;
+}
+
+int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, int reps,
+                      double* ms_per_launch, double* bytes_per_launch, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  if (reps < 1 || !ms_per_launch || !bytes_per_launch)
+    return fail(PDLP_ERR_INVALID_INPUT, "reps >= 1 and output arrays required");
+  double xo = 0.0;
+  int rc = check_inputs(A, b, sense, c, l, u, p, &xo, &xo, (const pdlp_result*)&xo);
+  if (rc) return rc;
+  pdlp_result r;
+  TimingReq tq{reps, ms_per_launch, bytes_per_launch};
+  return solve_device(A, b, sense, c, l, u, p, nullptr, nullptr, nullptr, nullptr, &r, nullptr,
+                      workspace, workspace_bytes, (cudaStream_t)stream, &tq);
+}
+
+const char* pdlp_error_string(int code) {
+  switch (code) {
+    case PDLP_OK: return "PDLP_OK";
+    case PDLP_ERR_INVALID_INPUT: return "PDLP_ERR_INVALID_INPUT";
+    case PDLP_ERR_CUDA: return "PDLP_ERR_CUDA";
+    case PDLP_ERR_OOM: return "PDLP_ERR_OOM";
+    case PDLP_ERR_TIMEOUT: return "PDLP_ERR_TIMEOUT";
+    case PDLP_ERR_UNSUPPORTED: return "PDLP_ERR_UNSUPPORTED";
+    default: return "PDLP_ERR_UNKNOWN";
+  }
+}
+
+const char* pdlp_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+"""GPU parity of the CUDA PDLP path against the FP64 CPU oracle, through the C ABI.
+
+* float64 iterates (current and average, x and y) after K accepted steps agree
+  with the oracle to 1e-9 relative, ||z_gpu - z_cpu|| / max(1, ||z_cpu||), in
+  the fixed-step mode and in the full adaptive / restarted mode, together with
+  the step, attempt and restart counters;
+* every precision mode reaches relative KKT <= tol, judged by the oracle's
+  float64 KKT of the returned point, with the objective close to HiGHS's;
+* edge cases: no rows, long rows and columns (multi-tile transpose, long-row
+  blocks), infinite bounds, equality rows, invalid inputs, limits, warm start.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import pdlp_oracle as O
+from oracle import reference_lp as R
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+PARITY = 1e-9
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as G
+    G.build()
+    import paper_2503_10344_gb300 as P
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1.0, np.linalg.norm(b)))
+
+
+def skewed_lp(seed=3, m=6000, n=3000):
+    """Random LP with a dense row (n nnz), a column in every row (m nnz, two sort
+    tiles), a column in 2/3 of the rows, and a sparse remainder; mixed senses."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    rows.append(np.zeros(n, dtype=np.int64)); cols.append(np.arange(n))
+    rows.append(np.arange(1, m)); cols.append(np.zeros(m - 1, dtype=np.int64))
+    r2 = np.arange(1, m)[rng.random(m - 1) < 0.66]
+    rows.append(r2); cols.append(np.ones(r2.size, dtype=np.int64))
+    mask = rng.random((m, n)) < 0.002
+    mask[0, :] = False
+    mask[:, :2] = False
+    rr, cc = np.nonzero(mask)
+    rows.append(rr); cols.append(cc)
+    rows = np.concatenate(rows); cols = np.concatenate(cols)
+    vals = rng.uniform(0.5, 2.0, size=rows.size) * np.where(rng.random(rows.size) < 0.3, -1, 1)
+    l = np.zeros(n); u = rng.uniform(1, 3, size=n)
+    u[rng.random(n) < 0.1] = np.inf
+    x0 = rng.random(n) * np.where(np.isfinite(u), u, 1.0)
+    ax0 = np.zeros(m)
+    np.add.at(ax0, rows, vals * x0[cols])
+    sense = np.where(rng.random(m) < 0.5, lpgen.SENSE_LE, lpgen.SENSE_GE).astype(np.uint8)
+    sense[rng.random(m) < 0.1] = lpgen.SENSE_EQ
+    slack = rng.uniform(0, 1, size=m)
+    b = np.where(sense == lpgen.SENSE_LE, ax0 + slack, np.where(sense == lpgen.SENSE_GE, ax0 - slack, ax0))
+    c = rng.uniform(0.1, 1.0, size=n)
+    return lpgen._lp(m, n, rows, cols, vals, b, sense, c, l, u, np.zeros(n, np.uint8), "skewed")
+
+
+INSTANCES = {
+    "mip_relaxation_200x400": lambda: lpgen.mip_relaxation(1),
+    "set_cover_2000x8000": lambda: lpgen.set_cover(7, m=2000, n=8000),
+    "energy_system_24h": lambda: lpgen.energy_system(hours=24),
+    "random_free_eq_300x500": lambda: lpgen.random_sparse_lp(11, 300, 500),
+    "skewed_6000x3000": lambda: skewed_lp(),
+}
+_cache = {}
+
+
+def inst(name):
+    if name not in _cache:
+        _cache[name] = INSTANCES[name]()
+    return _cache[name]
+
+
+def gpu_iterates(P, lp, **kw):
+    x, y, res, its = P.pdlp_solve(lp, P.default_params(**kw), iterates=True)
+    return x, y, res, its
+
+
+def assert_iterate_parity(its, ref):
+    for k, want in (("x_cur", ref.x_cur), ("y_cur", ref.y_cur), ("x_avg", ref.x_avg),
+                    ("y_avg", ref.y_avg)):
+        assert rel(its[k], want) <= PARITY, (k, rel(its[k], want))
+
+
+# ---------------------------------------------------------------- iterate parity
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("K", [1, 10, 100, 1000])
+def test_fixed_step_iterates_match_oracle(P, name, K):
+    # eta = 0.9: after the Pock-Chambolle pass ||K~||_2 <= 1 (Schur test), so the
+    # fixed-step iteration is stable for eta < 1 whatever omega is; eta0 = 1/max|K~|
+    # can exceed 1/||K~||_2, and an unstable iteration amplifies rounding without bound
+    lp = inst(name)
+    _, _, res, its = gpu_iterates(P, lp, iter_limit=K, adaptive_step=0, restarts=0, terminate=0,
+                                  fixed_eta=0.9)
+    ref = O.solve(lp, O.Params(iter_limit=K, adaptive=False, restarts=False, terminate=False,
+                               fixed_eta=0.9))
+    assert res["iters"] == K == ref.iters
+    assert_iterate_parity(its, ref)
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("K", [1, 10, 100])
+def test_adaptive_restarted_iterates_match_oracle(P, name, K):
+    lp = inst(name)
+    _, _, res, its = gpu_iterates(P, lp, iter_limit=K, terminate=0)
+    ref = O.solve(lp, O.Params(iter_limit=K, terminate=False))
+    assert res["iters"] == ref.iters == K
+    assert res["attempts"] == ref.attempts
+    assert res["restarts"] == ref.restarts
+    assert res["eta"] == pytest.approx(ref.eta, rel=1e-9)
+    assert res["omega"] == pytest.approx(ref.omega, rel=1e-9)
+    assert_iterate_parity(its, ref)
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("K", [1, 10, 100])
+def test_fixed_step_with_restarts_matches_oracle(P, name, K):
+    """Restarts (A9) and primal-weight updates (A10) on top of a stable fixed step."""
+    lp = inst(name)
+    _, _, res, its = gpu_iterates(P, lp, iter_limit=10 * K, terminate=0, adaptive_step=0,
+                                  fixed_eta=0.9)
+    ref = O.solve(lp, O.Params(iter_limit=10 * K, terminate=False, adaptive=False, fixed_eta=0.9))
+    assert res["restarts"] == ref.restarts
+    assert res["omega"] == pytest.approx(ref.omega, rel=1e-9)
+    assert_iterate_parity(its, ref)
+
+
+def check_replay(P, lp, K, **kw):
+    """Full adaptive, restarted run of K steps on the GPU with its decision trace; the
+    oracle replays the GPU's step sizes while computing eta_bar and every restart
+    decision itself.  Iterates must agree to 1e-9 and every GPU decision must be
+    the rule applied to the oracle's own numbers.  (Without replay two correct
+    float64 runs part after a few hundred adaptive steps: the step-size rule
+    feeds each iterate's rounding into the next step size.)"""
+    _, _, res, dg = P.pdlp_solve(lp, P.default_params(iter_limit=K, terminate=0, **kw),
+                                 trace=8 * K + 64)
+    ref = O.solve(lp, O.Params(iter_limit=K, terminate=False, replay_eta=dg["eta"],
+                               replay_accepted=dg["accepted"]))
+    assert res["iters"] == ref.iters == K and res["attempts"] == ref.attempts == len(dg["eta"])
+    eta = dg["eta"]
+    o_bar = np.array([t[1] for t in ref.attempt_trace])
+    acc = dg["accepted"].astype(bool)
+    clear = np.abs(eta - o_bar) > 1e-9 * o_bar  # not borderline
+    assert np.all((eta <= o_bar)[clear] == acc[clear])
+    fin = np.isfinite(o_bar)
+    assert np.all(np.isfinite(dg["eta_bar"]) == fin)
+    assert np.max(np.abs(dg["eta_bar"][fin] / o_bar[fin] - 1.0), initial=0.0) <= 1e-6
+    k = np.arange(1, len(eta), dtype=np.float64)
+    rule = np.minimum((1 - (k + 1) ** -0.3) * dg["eta_bar"][:-1], (1 + (k + 1) ** -0.6) * eta[:-1])
+    np.testing.assert_allclose(eta[1:], rule, rtol=1e-13)
+    assert list(dg["restart"]) == [c[0] for c in ref.check_trace]
+    np.testing.assert_allclose(dg["omega"], [c[1] for c in ref.check_trace], rtol=1e-9)
+    assert res["restarts"] == ref.restarts
+    assert_iterate_parity(dg, ref)
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_adaptive_restarted_steps_by_replay(P, name):
+    check_replay(P, inst(name), 150)
+
+
+@pytest.mark.parametrize("lanes", [(2, 2), (32, 32), (4, 16)])
+def test_lanes_do_not_change_iterates(P, lanes):
+    check_replay(P, inst("set_cover_2000x8000"), 150, lanes_A=lanes[0], lanes_AT=lanes[1])
+
+
+def one_ulp_copy(lp, seed=0):
+    """The same LP with every cost moved by one ulp in a seeded random direction."""
+    rng = np.random.default_rng(seed)
+    lp2 = lpgen.LP(**{k: getattr(lp, k) for k in lp.__dataclass_fields__})
+    lp2.c = np.where(rng.random(lp.n) < 0.5, np.nextafter(lp.c, -np.inf), np.nextafter(lp.c, np.inf))
+    return lp2
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_adaptive_1000_steps_within_the_method_sensitivity(P, name):
+    """Past ~100-200 adaptive steps the method itself amplifies rounding: the oracle
+    run against the same LP with every cost moved by one ulp parts from itself at
+    the same rate.  At K = 1000 the GPU must stay as close to the oracle as that
+    self-distance allows (a factor 100 of slack), and make the same progress."""
+    lp = inst(name)
+    K = 1000
+    _, _, res, its = gpu_iterates(P, lp, iter_limit=K, terminate=0)
+    ref = O.solve(lp, O.Params(iter_limit=K, terminate=False))
+    alt = O.solve(one_ulp_copy(lp), O.Params(iter_limit=K, terminate=False))
+    for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
+        self_d = rel(getattr(alt, k), getattr(ref, k))
+        assert rel(its[k], getattr(ref, k)) <= max(PARITY, 100.0 * self_d), (k, self_d)
+    g = O.kkt_original(lp, its["x_cur"], its["y_cur"]).rel_kkt
+    o = O.kkt_original(lp, ref.x_cur, ref.y_cur).rel_kkt
+    assert g <= 10.0 * o + 1e-12
+
+
+def test_full_solve_fp64_to_1e8(P):
+    """A full solve to 1e-8: the point passes the oracle's KKT, the objective matches
+    HiGHS, and the iteration count is of the oracle's order (the trajectories are
+    not comparable step by step this far, see check_replay)."""
+    lp = inst("mip_relaxation_200x400")
+    x, y, res = P.pdlp_solve(lp, P.default_params(tol=1e-8))
+    ref = O.solve(lp, O.Params(tol=1e-8))
+    assert res["status"] == P.PDLP_OPTIMAL == ref.status
+    assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-8
+    obj, _, _, _ = R.highs(lp)
+    assert abs(res["primal_obj"] - obj) / (1 + abs(obj)) <= 1e-7
+    assert 0.5 * ref.iters <= res["iters"] <= 2.0 * ref.iters
+
+
+# ---------------------------------------------------------------- solves to tolerance
+@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "set_cover_2000x8000", "energy_system_24h",
+                                  "random_free_eq_300x500", "skewed_6000x3000"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_solve_reaches_tolerance(P, name, prec):
+    lp = inst(name)
+    tol = 1e-4
+    x, y, res = P.pdlp_solve(lp, P.default_params(tol=tol, precision=prec))
+    assert res["status"] == P.PDLP_OPTIMAL, res
+    k = O.kkt_original(lp, x, y)  # float64 judge on the returned point
+    assert k.rel_kkt <= tol * 1.01, (k, res)
+    assert res["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
+    obj, _, _, _ = R.highs(lp)
+    assert abs(res["primal_obj"] - obj) / (1 + abs(obj)) <= 5e-4
+    assert np.all(x >= lp.l) and np.all(x <= lp.u)
+
+
+def test_precision_used_follows_the_values(P):
+    # integer values in [-5,5] are exact in bf16; all-ones is a bare pattern
+    # (after the <=-row sign flip the covering rows keep +1); 0.1..10 reals are not
+    _, _, r1 = P.pdlp_solve(inst("mip_relaxation_200x400"), P.default_params(precision="bf16"))
+    _, _, r2 = P.pdlp_solve(inst("set_cover_2000x8000"), P.default_params(precision="bf16"))
+    _, _, r3 = P.pdlp_solve(inst("energy_system_24h"), P.default_params(precision="bf16"))
+    assert r1["precision_used"] == 2 and r2["precision_used"] == 3 and r3["precision_used"] == 1
+
+
+# ---------------------------------------------------------------- device API
+def test_device_api_matches_host_api(P):
+    import torch
+    lp = inst("energy_system_24h")
+    prm = P.default_params(tol=1e-4, precision="fp32")
+    xh, yh, rh = P.pdlp_solve(lp, prm)
+    d = P.DeviceLP(lp)
+    xd, yd, rd = P.pdlp_solve_device(d, prm)
+    torch.cuda.synchronize()
+    assert rd["iters"] == rh["iters"]
+    np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+    np.testing.assert_array_equal(yd.cpu().numpy(), yh)
+
+
+def test_device_api_on_a_side_stream_with_caller_workspace(P):
+    import torch
+    lp = inst("mip_relaxation_200x400")
+    prm = P.default_params(tol=1e-6)
+    d = P.DeviceLP(lp)
+    ws = torch.empty(P.workspace_size(lp.m, lp.n, lp.nnz, prm) + 256, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    x, y, r = P.pdlp_solve_device(d, prm, workspace=ws, stream=s)
+    s.synchronize()
+    k = O.kkt_original(lp, x.cpu().numpy(), y.cpu().numpy())
+    assert r["status"] == P.PDLP_OPTIMAL and k.rel_kkt <= 1.01e-6
+
+
+# ---------------------------------------------------------------- edge cases
+def test_no_rows_closed_form(P):
+    n = 5
+    c = np.array([1.0, -2.0, 0.0, 3.0, -0.5])
+    l = np.array([-1.0, 0.0, 0.5, -3.0, 2.0])
+    u = np.array([1.0, 2.0, 1.0, 5.0, 7.0])
+    lp = lpgen._lp(0, n, np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), np.zeros(0),
+                   np.zeros(0, np.uint8), c, l, u, np.zeros(n, np.uint8), "norows")
+    x, y, res = P.pdlp_solve(lp, P.default_params(tol=1e-12))
+    assert res["status"] == P.PDLP_OPTIMAL
+    np.testing.assert_array_equal(x, [-1.0, 2.0, 0.5, -3.0, 7.0])
+
+
+def test_empty_rows_and_columns(P):
+    lp = lpgen.random_sparse_lp(5, 60, 80)  # has empty rows and columns
+    assert np.any(np.diff(lp.row_ptr) == 0)
+    assert np.any(np.bincount(lp.col, minlength=lp.n) == 0)
+    check_replay(P, lp, 300)
+
+
+def test_iteration_limit_zero_returns_the_start(P):
+    lp = inst("mip_relaxation_200x400")
+    x, y, res = P.pdlp_solve(lp, P.default_params(iter_limit=0))
+    assert res["status"] == P.PDLP_ITER_LIMIT and res["iters"] == 0
+    np.testing.assert_array_equal(x, np.clip(0.0, lp.l, lp.u))
+    np.testing.assert_array_equal(y, np.zeros(lp.m))
+
+
+def test_iteration_limit_status(P):
+    lp = inst("set_cover_2000x8000")
+    _, _, res = P.pdlp_solve(lp, P.default_params(tol=1e-12, iter_limit=130))
+    assert res["status"] == P.PDLP_ITER_LIMIT and res["iters"] == 130
+
+
+def test_time_limit_status(P):
+    lp = inst("energy_system_24h")
+    _, _, res = P.pdlp_solve(lp, P.default_params(tol=1e-14, time_limit_s=1e-6))
+    assert res["status"] == P.PDLP_TIME_LIMIT
+
+
+def test_warm_start_from_the_oracle_solution(P):
+    lp = inst("mip_relaxation_200x400")
+    ref = O.solve(lp, O.Params(tol=1e-8))
+    x, y, res = P.pdlp_solve(lp, P.default_params(tol=1e-6), x0=ref.x, y0=ref.y)
+    assert res["status"] == P.PDLP_OPTIMAL and res["iters"] <= 128
+    # and warm-started iterates still match the warm-started oracle
+    _, _, _, its = gpu_iterates(P, lp, iter_limit=50, terminate=0)
+    _, _, _, its2 = P.pdlp_solve(lp, P.default_params(iter_limit=50, terminate=0), x0=ref.x, y0=ref.y,
+                                 iterates=True)
+    ref2 = O.solve(lp, O.Params(iter_limit=50, terminate=False), x0=ref.x, y0=ref.y)
+    assert_iterate_parity(its2, ref2)
+
+
+@pytest.mark.parametrize("breakage", ["nan_c", "col_range", "l_gt_u", "sense", "row_ptr", "inf_val"])
+def test_invalid_input_is_rejected(P, breakage):
+    lp = lpgen.mip_relaxation(2)
+    if breakage == "nan_c":
+        lp.c = lp.c.copy(); lp.c[3] = np.nan
+    elif breakage == "col_range":
+        lp.col = lp.col.copy(); lp.col[5] = lp.n
+    elif breakage == "l_gt_u":
+        lp.l = lp.l.copy(); lp.l[0] = 2.0
+    elif breakage == "sense":
+        lp.sense = lp.sense.copy(); lp.sense[1] = ord("X")
+    elif breakage == "row_ptr":
+        lp.row_ptr = lp.row_ptr.copy(); lp.row_ptr[3] = lp.row_ptr[4] + 1
+    elif breakage == "inf_val":
+        lp.val = lp.val.copy(); lp.val[0] = np.inf
+    with pytest.raises(P.PdlpError, match="INVALID_INPUT"):
+        P.pdlp_solve(lp)
+
+
+def test_bad_params_are_rejected(P):
+    lp = inst("mip_relaxation_200x400")
+    for kw in ({"tol": 0.0}, {"check_period": 0}, {"precision": 7}, {"lanes_A": 3}):
+        with pytest.raises(P.PdlpError, match="INVALID_INPUT"):
+            P.pdlp_solve(lp, P.default_params(**kw))
+
+
+# ---------------------------------------------------------------- full-size workload
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp64"])
+def test_set_cover_full_size(P, prec):
+    """m = 50,000, n = 200,000, ~1.3M nnz: the benchmark workload, same launch path."""
+    gold = json.load(open(os.path.join(GOLDEN, "set_cover_2025.json")))
+    lp = lpgen.set_cover(2025)
+    x, y, res = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec))
+    assert res["status"] == P.PDLP_OPTIMAL, res
+    k = O.kkt_original(lp, x, y)
+    assert k.rel_kkt <= 1.01e-4, k
+    assert abs(res["primal_obj"] - gold["highs_obj"]) / (1 + abs(gold["highs_obj"])) <= 5e-4

@@ -290,3 +290,17 @@ def test_step_growth_when_eta_bar_is_infinite():
     r2 = O.solve(lp, O.Params(iter_limit=2, fixed_eta=1.0, terminate=False, restarts=False))
     assert r1.eta == pytest.approx(1.6597539553864471, rel=1e-15)
     assert r2.eta == pytest.approx(1.6597539553864471 * 1.5172818579717866, rel=1e-14)
+
+
+def test_replaying_the_own_trace_reproduces_the_run():
+    """The replay mode (step sizes and accept flags from a trace) is a pure
+    substitution: replaying a run's own trace gives the same run bit for bit."""
+    lp = lpgen.mip_relaxation(3)
+    r = O.solve(lp, O.Params(iter_limit=700, terminate=False))
+    eta = [t[0] for t in r.attempt_trace]
+    acc = [t[2] for t in r.attempt_trace]
+    r2 = O.solve(lp, O.Params(iter_limit=700, terminate=False, replay_eta=eta, replay_accepted=acc))
+    assert r2.attempts == r.attempts and r2.restarts == r.restarts
+    np.testing.assert_array_equal(r2.x_cur, r.x_cur)
+    np.testing.assert_array_equal(r2.y_avg, r.y_avg)
+    assert r2.check_trace == r.check_trace
