@@ -515,7 +515,9 @@ cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* 
   size_t doff = (size_t)(d_nlong + 1 - tmp);
   doff = (doff + 3) & ~(size_t)3;
   int* desc = tmp + doff;
-  const size_t max_desc = (size_t)nnz / 32 + 2;  // bound on tiles of segments longer than 32
+  // bound on tiles of segments longer than 32, rounded up to even so that the
+  // int4 array placed after 2 * max_desc ints starts on a 16-byte boundary
+  const size_t max_desc = ((size_t)nnz / 32 + 3) & ~(size_t)1;
   int* bsum = desc + 8 * max_desc;
   RET(cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), s));
   if (nnz > 0) {
@@ -584,7 +586,7 @@ cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* 
 }
 
 size_t transpose_tmp_ints(int m, int n, long long nnz) {
-  return (size_t)(n + 1) + 2 * (size_t)nnz + (size_t)n + 1 + 4 + 8 * ((size_t)nnz / 32 + 2) +
+  return (size_t)(n + 1) + 2 * (size_t)nnz + (size_t)n + 1 + 4 + 8 * ((size_t)nnz / 32 + 3) +
          scan_tmp_ints((long long)std::max(m, n) + 1) + 64;
 }
 
