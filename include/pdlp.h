@@ -215,6 +215,33 @@ int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, con
                       double* ms_per_launch, double* bytes_per_launch, void* workspace,
                       size_t workspace_bytes, void* stream);
 
+/* pdlp_solve_device for callers that cannot allocate device memory.
+ * (No counterpart in the paper: this is a deployment variant of the solve.)
+ * For code where cudaMalloc is unavailable or unwelcome -- device memory owned
+ * by another allocator that must account for every byte, a latency-bound loop
+ * that must not reach the driver's allocator, a caller with no workspace to
+ * hand over.  Same arguments and results as pdlp_solve_device, minus the
+ * workspace: the scratch is one static device array of 64 MiB inside this
+ * library, which every GPU that loads the library holds until process exit.
+ *  - Problems whose pdlp_workspace_size exceeds 64 MiB (67108864 bytes) are
+ *    rejected with PDLP_ERR_OOM before any work.
+ *  - The call makes no device allocation and creates no CUDA object (no
+ *    cudaMalloc/cudaFree, pinned buffer, stream, event or graph); it launches
+ *    the solver's kernels directly on `stream` and polls the termination flag
+ *    in pageable host memory once per check period.
+ *  - The first call on each device (with that device current) looks up the
+ *    array's device address with cudaGetSymbolAddress and caches it; make
+ *    that first call before any stream capture begins.
+ *  - All calls share the array, which keeps the last call's contents; every
+ *    call writes what it reads, so nothing carries over, but calls whose GPU
+ *    work overlaps (two streams, two host threads on one device) race on the
+ *    array: serialise them per device. */
+int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, const char* sense,
+                              const double* c, const double* l, const double* u,
+                              const pdlp_params* p, const double* x0, const double* y0,
+                              double* x_out, double* y_out, pdlp_result* r,
+                              const pdlp_diagnostics* diag, void* stream);
+
 /* Name of a return code, and the last error message of the calling thread. */
 const char* pdlp_error_string(int code);
 const char* pdlp_last_error(void);

@@ -5,8 +5,10 @@ C ABI in ``include/pdlp.h``); :mod:`.binding` marshals arguments to it.
 """
 from .binding import (PDLP_FP32, PDLP_FP32_BF16A, PDLP_FP64, PDLP_ITER_LIMIT, PDLP_NUMERICAL,
                       PDLP_OPTIMAL, PDLP_TIME_LIMIT, DeviceLP, PdlpError, default_params, lib,
-                      pdlp_solve, pdlp_solve_device, time_kernels, workspace_size)
+                      pdlp_solve, pdlp_solve_device, pdlp_solve_device_noalloc, time_kernels,
+                      workspace_size)
 
 __all__ = ["PDLP_FP32", "PDLP_FP32_BF16A", "PDLP_FP64", "PDLP_ITER_LIMIT", "PDLP_NUMERICAL",
            "PDLP_OPTIMAL", "PDLP_TIME_LIMIT", "DeviceLP", "PdlpError", "default_params", "lib",
-           "pdlp_solve", "pdlp_solve_device", "time_kernels", "workspace_size"]
+           "pdlp_solve", "pdlp_solve_device", "pdlp_solve_device_noalloc", "time_kernels",
+           "workspace_size"]

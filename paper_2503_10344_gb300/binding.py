@@ -82,6 +82,7 @@ def lib():
             [C.c_void_p] * 4 + [C.POINTER(PdlpResult), C.POINTER(PdlpDiagnostics)]
         L.pdlp_solve.argtypes = common
         L.pdlp_solve_device.argtypes = common + [C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pdlp_solve_device_noalloc.argtypes = common + [C.c_void_p]
         L.pdlp_time_kernels.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + \
             [C.POINTER(PdlpParams), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
              C.c_void_p]
@@ -254,3 +255,33 @@ def time_kernels(dlp: DeviceLP, params: PdlpParams | None = None, reps: int = 20
                                  workspace.numel() - (aligned - base), C.c_void_p(stream.cuda_stream))
     _check(rc)
     return {k: {"ms": float(ms[i]), "bytes": float(by[i])} for i, k in enumerate(KERNELS)}
+
+
+NOALLOC_BYTES = 64 << 20
+
+
+def pdlp_solve_device_noalloc(dlp: DeviceLP, params: PdlpParams | None = None, x0=None, y0=None,
+                              x_out=None, y_out=None, stream=None):
+    """pdlp_solve_device for callers that cannot allocate device memory: the library
+    solves in its own static 64 MiB device array instead of a workspace.  Outputs
+    must be passed in (float64 CUDA tensors) when the caller cannot allocate them
+    either; they are allocated here only as a convenience when left as None."""
+    import torch
+    p = params or default_params()
+    dev = dlp.c.device
+    if x_out is None:
+        x_out = torch.empty(dlp.n, dtype=torch.float64, device=dev)
+    if y_out is None:
+        y_out = torch.empty(max(dlp.m, 1), dtype=torch.float64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    dp = lambda t_: None if t_ is None else C.c_void_p(t_.data_ptr())
+    csr = PdlpCsr(dlp.m, dlp.n, dlp.nnz, dlp.row_ptr.data_ptr(), dlp.col.data_ptr(),
+                  dlp.val.data_ptr())
+    res = PdlpResult()
+    rc = lib().pdlp_solve_device_noalloc(C.byref(csr), dp(dlp.b), dp(dlp.sense), dp(dlp.c),
+                                         dp(dlp.l), dp(dlp.u), C.byref(p), dp(x0), dp(y0),
+                                         dp(x_out), dp(y_out), C.byref(res), None,
+                                         C.c_void_p(stream.cuda_stream))
+    _check(rc)
+    return x_out, y_out[: dlp.m], res.as_dict()

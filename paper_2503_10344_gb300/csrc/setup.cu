@@ -238,6 +238,36 @@ __global__ void k_copy_ranges(const int2* ranges, const int* from, int* to) {
   for (int i = threadIdx.x; i < r.y; i += blockDim.x) to[r.x + i] = from[r.x + i];
 }
 
+// Tile descriptors of the long column segments built on the device (used when
+// the caller cannot let the host allocate): per segment its tile count and, for
+// segments longer than one tile, the merge-rank tile count.
+__global__ void k_tile_counts(const int* list, int nlist, const int* t_ptr, int* cnt_t, int* cnt_m) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nlist; k += stride) {
+    const int j = list[k];
+    const int len = t_ptr[j + 1] - t_ptr[j];
+    const int tiles = (len + kTile - 1) / kTile;
+    cnt_t[k] = tiles;
+    cnt_m[k] = len > kTile ? tiles : 0;
+  }
+}
+
+__global__ void k_tile_desc(const int* list, int nlist, const int* t_ptr, const int* off_t,
+                            const int* off_m, int2* tiles, int4* mtiles, int2* ranges) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nlist; k += stride) {
+    const int j = list[k];
+    const int st = t_ptr[j], len = t_ptr[j + 1] - st;
+    int a = off_t[k], b = off_m[k];
+    for (int o = 0; o < len; o += kTile) {
+      const int tl = min(kTile, len - o);
+      tiles[a++] = make_int2(st + o, tl);
+      if (len > kTile) mtiles[b++] = make_int4(st, len, st + o, tl);
+    }
+    ranges[k] = make_int2(st, len > kTile ? len : 0);
+  }
+}
+
 __global__ void k_finish_transpose(const int* a_ptr, int m, const double* a_val64, const int* src,
                                    int nnz, int* t_col, double* t_val64) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -503,7 +533,7 @@ size_t scan_tmp_ints(long long N) { return (size_t)((N + kScanTile - 1) / kScanT
 
 cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* a_col,
                             const double* a_val64, int* t_ptr, int* t_col, double* t_val64,
-                            int* tmp, cudaStream_t s) {
+                            int* tmp, cudaStream_t s, bool device_desc) {
   // tmp layout (ints): cnt/cursor [n+1] | src [nnz] | src2 [nnz] | long list [n] | nlong [1]
   //                    | tile descriptors [8 * (nnz/32 + 2)], 16-byte aligned | scan block sums
   const int G = device_sm_count() * 8;
@@ -536,7 +566,39 @@ cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* 
   int nlong = 0;
   RET(cudaMemcpyAsync(&nlong, d_nlong, sizeof(int), cudaMemcpyDeviceToHost, s));
   RET(cudaStreamSynchronize(s));
-  if (nlong > 0) {
+  if (nlong > 0 && device_desc) {
+    // descriptors built on the device; the count and offset arrays live in src2,
+    // which the merge-rank pass only overwrites after the descriptors exist
+    int* cnt_t = src2;
+    int* cnt_m = cnt_t + nlong;
+    int* off_t = cnt_m + nlong;
+    int* off_m = off_t + nlong + 1;
+    const int gl = grid_for(nlong, G);
+    k_tile_counts<<<gl, kBlock, 0, s>>>(long_list, nlong, t_ptr, cnt_t, cnt_m);
+    RET(cudaGetLastError());
+    RET(exclusive_scan(cnt_t, off_t, nlong, bsum, s));
+    RET(exclusive_scan(cnt_m, off_m, nlong, bsum, s));
+    int tot_t = 0, tot_m = 0;
+    RET(cudaMemcpyAsync(&tot_t, off_t + nlong, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RET(cudaMemcpyAsync(&tot_m, off_m + nlong, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RET(cudaStreamSynchronize(s));
+    if ((size_t)tot_t > max_desc || (size_t)tot_m > max_desc || (size_t)nlong > max_desc)
+      return cudaErrorInvalidValue;
+    int2* d_tiles = (int2*)desc;
+    int4* d_mtiles = (int4*)(desc + 2 * max_desc);
+    int2* d_ranges = (int2*)(desc + 6 * max_desc);
+    k_tile_desc<<<gl, kBlock, 0, s>>>(long_list, nlong, t_ptr, off_t, off_m, d_tiles, d_mtiles,
+                                      d_ranges);
+    RET(cudaGetLastError());
+    k_sort_tiles<<<tot_t, 1024, 0, s>>>(d_tiles, src);
+    RET(cudaGetLastError());
+    if (tot_m > 0) {
+      k_merge_rank<<<tot_m, kBlock, 0, s>>>(d_mtiles, src, src2);
+      RET(cudaGetLastError());
+      k_copy_ranges<<<nlong, kBlock, 0, s>>>(d_ranges, src2, src);
+      RET(cudaGetLastError());
+    }
+  } else if (nlong > 0) {
     std::vector<int> ids(nlong);
     RET(cudaMemcpyAsync(ids.data(), long_list, sizeof(int) * nlong, cudaMemcpyDeviceToHost, s));
     std::vector<int> hp(n + 1);

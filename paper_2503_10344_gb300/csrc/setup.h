@@ -42,9 +42,11 @@ cudaError_t setup_validate(const SetupIn& in, int* d_err, cudaStream_t s);
 cudaError_t setup_canonical(const SetupIn& in, int* a_ptr, int* a_col, double* a_val64, double* q,
                             unsigned char* row_kind, cudaStream_t s);
 size_t transpose_tmp_ints(int m, int n, long long nnz);
+// device_desc: build the long-segment tile descriptors on the device instead of
+// in host vectors (no host allocation)
 cudaError_t setup_transpose(int m, int n, int nnz, const int* a_ptr, const int* a_col,
                             const double* a_val64, int* t_ptr, int* t_col, double* t_val64,
-                            int* tmp, cudaStream_t s);
+                            int* tmp, cudaStream_t s, bool device_desc = false);
 cudaError_t setup_scaling(const ScaleIn& sc, double* dr, double* dc, double* stat_r,
                           double* stat_c, cudaStream_t s);
 cudaError_t setup_value_format(const double* val64, int nnz, int* d_flags, int* h_bf16_exact,

@@ -213,7 +213,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
                         const double* l, const double* u, const pdlp_params* p, const double* x0,
                         const double* y0, double* x_out, double* y_out, pdlp_result* r,
                         const pdlp_diagnostics* dg, void* workspace, size_t ws_bytes,
-                        cudaStream_t s, const TimingReq* tq = nullptr) {
+                        cudaStream_t s, const TimingReq* tq = nullptr, bool no_alloc = false) {
   const int m = A->m, n = A->n;
   const long long nnz = A->nnz;
   g_launches = 0;
@@ -239,19 +239,24 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   Arena ar{(char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255), 0};
   carve(ar, bf, m, n, nnz, p->precision);
 
-  cudaEvent_t e0, e1, e2;
-  CUDA_TRY(cudaEventCreate(&e0));
-  CUDA_TRY(cudaEventCreate(&e1));
-  CUDA_TRY(cudaEventCreate(&e2));
+  // no_alloc: nothing below creates a CUDA object or allocates memory (no events,
+  // graphs, streams or pinned buffers); phases are timed with host clocks
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (!no_alloc) {
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventCreate(&e2));
+  }
   struct EvFree {
     cudaEvent_t a, b, c;
     ~EvFree() {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-      cudaEventDestroy(c);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (c) cudaEventDestroy(c);
     }
   } evfree{e0, e1, e2};
-  CUDA_TRY(cudaEventRecord(e0, s));
+  auto h0 = std::chrono::steady_clock::now(), h1 = h0, h2 = h0;
+  if (!no_alloc) CUDA_TRY(cudaEventRecord(e0, s));
 
   // ---- validation (A0 preconditions)
   SetupIn in{m, n, nnz, A->row_ptr, A->col, A->val, b, sense, c, l, u};
@@ -272,7 +277,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   // ---- A0, A1
   CUDA_TRY(setup_canonical(in, bf.a_ptr, bf.a_col, bf.a_val64, bf.q64, bf.row_kind, s));
   CUDA_TRY(setup_transpose(m, n, (int)nnz, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col,
-                           bf.t_val64, bf.tmp, s));
+                           bf.t_val64, bf.tmp, s, no_alloc));
   g_launches += 10;
   // ---- mode
   Mode mode = MODE_FP64;
@@ -397,8 +402,41 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
 
   Solve sv{m, n, nnz, mode, lanes_a, lanes_t, ir, kr, s};
   CUDA_TRY(sv.kkt_block());  // initial KKT and restart anchors
-  CUDA_TRY(cudaEventRecord(e1, s));
-  if (tq) return time_kernels_after_setup(sv, bf.st, mode, nnz, *tq);
+  if (!no_alloc) {
+    CUDA_TRY(cudaEventRecord(e1, s));
+  } else {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    h1 = std::chrono::steady_clock::now();
+  }
+  if (tq && !no_alloc) return time_kernels_after_setup(sv, bf.st, mode, nnz, *tq);
+  if (no_alloc) {
+    // the same chunk of step attempts and KKT block, launched directly on the
+    // caller's stream; the four-byte status is read into pageable memory
+    if (p->iter_limit > 0) {
+      static const int one[2] = {1, 1};
+      const long long max_chunks = (p->iter_limit / p->check_period + 2) * 64 + 1024;
+      bool forced = false;
+      for (long long chunk = 0;; ++chunk) {
+        for (int a = 0; a < p->check_period; ++a) {
+          CUDA_TRY(sv.iter(IK_PRIMAL));
+          CUDA_TRY(sv.iter(IK_DUAL));
+        }
+        CUDA_TRY(sv.kkt_block());
+        DevState h;
+        CUDA_TRY(cudaMemcpyAsync(&h, bf.st, 16, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (h.status != 0) break;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - h1).count();
+        if (!forced && el > p->time_limit_s) {
+          CUDA_TRY(cudaMemcpyAsync(&bf.st->force_final, &one[0], sizeof(int), cudaMemcpyHostToDevice, s));
+          CUDA_TRY(cudaMemcpyAsync(&bf.st->check_due, &one[1], sizeof(int), cudaMemcpyHostToDevice, s));
+          forced = true;
+        }
+        if (chunk > max_chunks) return fail(PDLP_ERR_TIMEOUT, "iteration loop did not terminate");
+      }
+    }
+    h2 = std::chrono::steady_clock::now();
+  } else {
 
   // ---- iteration phase: graph of one check period
   DevState* hm = nullptr;  // pinned mirror of the first 16 bytes of the state, 2 slots
@@ -493,6 +531,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   (void)host_status;
   CUDA_TRY(cudaStreamSynchronize(s));  // drain the chunk launched behind the terminating one
   CUDA_TRY(cudaEventRecord(e2, s));
+  }  // graph-driven iteration phase
   // ---- A11: outputs
   CUDA_TRY(launch_output(kr, x_out, m ? y_out : nullptr, dg ? dg->x_cur : nullptr,
                          dg && m ? dg->y_cur : nullptr, dg ? dg->x_avg : nullptr,
@@ -502,8 +541,13 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   CUDA_TRY(cudaMemcpyAsync(&fs, bf.st, sizeof(fs), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   float ms_setup = 0.f, ms_solve = 0.f;
-  cudaEventElapsedTime(&ms_setup, e0, e1);
-  cudaEventElapsedTime(&ms_solve, e1, e2);
+  if (!no_alloc) {
+    cudaEventElapsedTime(&ms_setup, e0, e1);
+    cudaEventElapsedTime(&ms_solve, e1, e2);
+  } else {
+    ms_setup = (float)(1e3 * std::chrono::duration<double>(h1 - h0).count());
+    ms_solve = (float)(1e3 * std::chrono::duration<double>(h2 - h1).count());
+  }
 
   r->status = p->iter_limit == 0 ? PDLP_ITER_LIMIT : fs.status;
   r->precision_used = mode == MODE_FP64 ? PDLP_FP64
@@ -617,6 +661,21 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   // KKT over A^T: row_ptr, col, values; both dual candidates gathered; c, l, u, D_c, x c/a, x anchor
   tq.bytes[4] = 4 * (N + 1) + Z * (4 + val64) + M * 16 + N * (32 + 16 + 8);
   return PDLP_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+// pdlp_solve_device on caller-provided scratch without creating any CUDA
+// object or allocating (see noalloc.cu)
+int solve_device_noalloc(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                         const double* l, const double* u, const pdlp_params* p, const double* x0,
+                         const double* y0, double* x_out, double* y_out, pdlp_result* r,
+                         const pdlp_diagnostics* dg, void* workspace, size_t ws_bytes,
+                         cudaStream_t s) {
+  const int rc = check_inputs(A, b, sense, c, l, u, p, x_out, y_out, r);
+  if (rc) return rc;
+  return solve_device(A, b, sense, c, l, u, p, x0, y0, x_out, y_out, r, dg, workspace, ws_bytes,
+                      s, nullptr, true);
 }
 
 }  // namespace pdlp

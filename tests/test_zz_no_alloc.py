@@ -1,0 +1,85 @@
+"""pdlp_solve_device_noalloc, the solve for callers that cannot allocate device memory.
+
+Such callers (device memory owned by another allocator, loops that must not
+reach the driver's allocator, code with no workspace to hand over) get the
+same solve with its scratch in the library's static 64 MiB device array.  This
+file checks, through the C ABI, that two calls in a row give what
+pdlp_solve_device gives on the same inputs (to the 1e-9 parity tolerance of
+the other GPU tests), including an LP whose long columns take the device-built
+transpose path, and that a problem too large for the array is refused.
+It is named so pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+
+pytestmark = pytest.mark.gpu
+
+PARITY = 1e-9
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as G
+    G.build()
+    import paper_2503_10344_gb300 as P
+    return P
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(1.0, np.linalg.norm(b)))
+
+
+def long_column_lp(m=6000, n=3000, seed=5):
+    """Feasible covering-type LP with one column in every row (two sort tiles) and
+    one in two thirds of the rows, so the transpose sorts long column segments."""
+    rng = np.random.default_rng(seed)
+    rows = [np.arange(m), np.arange(m)[rng.random(m) < 0.66]]
+    cols = [np.zeros(m, dtype=np.int64), np.ones(rows[1].size, dtype=np.int64)]
+    mask = rng.random((m, n)) < 0.002
+    mask[:, :2] = False
+    rr, cc = np.nonzero(mask)
+    rows.append(rr)
+    cols.append(cc)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = rng.uniform(0.5, 2.0, size=rows.size)
+    vals[:m] = rng.uniform(1.0, 2.0, size=m)  # column 0 alone covers every row: feasible
+    return lpgen._lp(m, n, rows, cols, vals, np.ones(m),
+                     np.full(m, lpgen.SENSE_GE, dtype=np.uint8), rng.uniform(1, 10, size=n),
+                     np.zeros(n), np.ones(n), np.zeros(n, np.uint8), "long_columns")
+
+
+@pytest.mark.parametrize("maker,prec", [(lambda: lpgen.mip_relaxation(1), "fp64"),
+                                        (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16"),
+                                        (lambda: long_column_lp(), "fp32")])
+def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec):
+    import torch
+    lp = maker()
+    d = P.DeviceLP(lp)
+    prm = P.default_params(tol=1e-6, precision=prec)
+    assert P.workspace_size(lp.m, lp.n, lp.nnz, prm) <= P.binding.NOALLOC_BYTES
+    xr, yr, rr = P.pdlp_solve_device(d, prm)
+    xr, yr = xr.cpu().numpy(), yr.cpu().numpy()
+    xo = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    yo = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        x, y, r = P.pdlp_solve_device_noalloc(d, prm, x_out=xo, y_out=yo)
+        torch.cuda.synchronize()
+        assert r["status"] == rr["status"] == P.PDLP_OPTIMAL
+        assert r["iters"] == rr["iters"] and r["restarts"] == rr["restarts"]
+        assert rel(x.cpu().numpy(), xr) <= PARITY
+        assert rel(y.cpu().numpy(), yr) <= PARITY
+        assert r["rel_kkt"] == pytest.approx(rr["rel_kkt"], rel=PARITY)
+
+
+def test_noalloc_refuses_a_problem_larger_than_its_array(P):
+    lp = lpgen.set_cover(2025)  # needs well over 64 MiB in float64
+    d = P.DeviceLP(lp)
+    prm = P.default_params(precision="fp64")
+    assert P.workspace_size(lp.m, lp.n, lp.nnz, prm) > P.binding.NOALLOC_BYTES
+    with pytest.raises(P.PdlpError, match="OOM"):
+        P.pdlp_solve_device_noalloc(d, prm)
