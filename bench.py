@@ -43,7 +43,17 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=400)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only time the fused kernels (pdlp_time_kernels) and print them")
+    ap.add_argument("--reps", type=int, default=200)
+    for k in ("lanes-a", "lanes-at", "lanes-kkt-a", "lanes-kkt-at"):
+        ap.add_argument("--" + k, type=int, default=0, help="SpMV lanes per row (0 = automatic)")
     return ap.parse_args()
+
+
+def lane_params(args) -> dict:
+    return {"lanes_A": args.lanes_a, "lanes_AT": args.lanes_at, "lanes_kkt_A": args.lanes_kkt_a,
+            "lanes_kkt_AT": args.lanes_kkt_at}
 
 
 def dist_env():
@@ -196,7 +206,7 @@ def run_gpu(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, iters, launches, res, (xo, yo)
 
-    prm = P.default_params(tol=1e-4, precision=args.precision)
+    prm = P.default_params(tol=1e-4, precision=args.precision, **lane_params(args))
     with ClockSampler(dev.index) as clk:
         ms, iters, launches, res, (xo, yo) = timed_solves(prm, args.steps, args.warmup)
     clocks = clk.summary()
@@ -257,7 +267,7 @@ def run_gpu(args):
             "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": prec_used, "l2_flush": True,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                       "lanes": "auto"},
+                       "lanes": lane_params(args)},
             "time_to_tol_s": total_s / args.steps,
             "iters_per_solve": iters / args.steps,
             "status": res["status"], "rel_kkt": res["rel_kkt"], "primal_obj": res["primal_obj"],
@@ -278,9 +288,28 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_kernels_only(args):
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    lp = lpgen.set_cover(2025)
+    d = P.DeviceLP(lp)
+    kt = P.time_kernels(d, P.default_params(tol=1e-4, precision=args.precision, **lane_params(args)),
+                        reps=args.reps)
+    torch.cuda.synchronize()
+    print(json.dumps({k: {"us": 1e3 * v["ms"], "bytes": v["bytes"],
+                          "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9} for k, v in kt.items()}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.kernels_only:
+        run_kernels_only(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gpu(a)

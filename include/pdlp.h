@@ -108,8 +108,10 @@ typedef struct {
   double fixed_eta;     /* > 0 overrides the initial step size eta0 */
   double fixed_omega;   /* > 0 overrides the initial primal weight omega0 */
   int terminate;        /* 1 (default): stop at tol; 0: run to iter_limit */
-  int lanes_A;          /* SpMV lanes per row of A (0 = automatic; 2,4,8,16,32) */
-  int lanes_AT;         /* SpMV lanes per row of A^T (0 = automatic) */
+  int lanes_A;          /* SpMV lanes per row of A in the step kernels (0 = automatic; 2,4,8,16,32) */
+  int lanes_AT;         /* SpMV lanes per row of A^T in the step kernels (0 = automatic) */
+  int lanes_kkt_A;      /* lanes per row of A in the float64 KKT pass (0 = automatic) */
+  int lanes_kkt_AT;     /* lanes per row of A^T in the float64 KKT pass (0 = automatic) */
   int verbose;          /* 0 quiet; 1 one line per KKT check on stderr */
 } pdlp_params;
 

@@ -38,7 +38,7 @@ class PdlpParams(C.Structure):
                 ("ruiz_iters", C.c_int), ("pc_alpha", C.c_double), ("adaptive_step", C.c_int),
                 ("restarts", C.c_int), ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("terminate", C.c_int), ("lanes_A", C.c_int), ("lanes_AT", C.c_int),
-                ("verbose", C.c_int)]
+                ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int)]
 
 
 class PdlpResult(C.Structure):

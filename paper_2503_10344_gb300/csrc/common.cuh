@@ -66,6 +66,18 @@ struct DevState {
   double norm_q, norm_c;  // ||q||_2, ||c||_2 of the unscaled data
   // results of the last KKT check: [0] current, [1] average
   double pobj[2], dobj[2], relp[2], reld[2], relgap[2];
+  // per-attempt scalars prepared by the deciding thread, in both precisions, so
+  // the step kernels run no float64 arithmetic in the float32 modes:
+  //   tau = eta / omega, sigma = eta * omega, pw = pending_w
+  double tau_d, sigma_d, inv_omega;
+  float tau_f, sigma_f, pw_f, eta_f, omega_f, inv_omega_f;
+  // step-rule factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 for attempts k = 1..fac_n
+  // (computed on the host with the C library pow; beyond the table, pow here)
+  const double* fac_dec;
+  const double* fac_inc;
+  const float* fac_dec_f;
+  const float* fac_inc_f;
+  long long fac_n;
   // optional decision trace (device arrays, capacity 0 = off)
   double* tr_eta;
   double* tr_eta_bar;
@@ -138,6 +150,49 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (&out)[NV]) {
     }
   }
   __syncthreads();
+}
+
+// Deterministic block sum in the element type T (float reductions stay in the
+// float32 pipe); thread 0 gets the result.
+template <typename T>
+__device__ __forceinline__ T block_sum1(T v) {
+  __shared__ T sh[kWarps];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kWarps; ++i) s += sh[i];
+  __syncthreads();
+  return s;
+}
+
+// Three sums at once (one shared-memory round instead of three); thread 0 gets them.
+template <typename T>
+__device__ __forceinline__ void block_sum3(T& a, T& b, T& c) {
+  __shared__ T sh[3][kWarps];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][w] = a;
+    sh[1][w] = b;
+    sh[2][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = b = c = 0;
+    for (int i = 0; i < kWarps; ++i) {
+      a += sh[0][i];
+      b += sh[1][i];
+      c += sh[2][i];
+    }
+  }
 }
 
 // Fixed-order reduction of NV partial arrays part[k * stride + i], i < count,

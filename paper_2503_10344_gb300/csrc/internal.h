@@ -44,6 +44,8 @@ struct KktRaw {
   int a_nlong, t_nlong, a_thresh, t_thresh;
   int m, n;
   const double *c, *l, *u, *q, *dr, *dc;  // unscaled canonical data, scaling
+  const double *inv_dr, *inv_dc;           // 1 / D_r, 1 / D_c
+  const unsigned char* bflags;             // per column: bit 0 l finite, bit 1 u finite
   const unsigned char* row_kind;           // 0 >=-row, 1 =-row, 2 <=-row flipped to >=
   void *x[2], *y[2], *sum_x, *sum_y;       // iterates (float or double; x as (x_j, dx_j) pairs)
   double *Xc, *Xa, *Yc, *Ya, *Xl, *Yl;     // unscaled float64 candidates and restart anchors

@@ -1,21 +1,33 @@
 // Fused PDHG step kernels (rows A4-A7 of the hot path).
 //
 // One step attempt is two launches:
-//   k_primal  -- row-split CSR SpMV over A^T (one group of LANES lanes per
-//                column), fused with the projected primal update
+//   k_primal  -- CSR SpMV over A^T fused with the projected primal update
 //                x' = proj_[l,u](x - tau (c - K^T y)) and the partial sums of
 //                ||x' - x||^2 (scaled norm).
-//   k_dual    -- row-split CSR SpMV over A, fused with the extrapolated dual
-//                update y' = proj_Y(y + sigma (q - K(2x' - x))) and the partial
-//                sums of ||y' - y||^2 and (y' - y)^T K (x' - x); its last block
+//   k_dual    -- CSR SpMV over A fused with the extrapolated dual update
+//                y' = proj_Y(y + sigma (q - K(2x' - x))) and the partial sums
+//                of ||y' - y||^2 and (y' - y)^T K (x' - x); its last block
 //                reduces the partials in a fixed order and takes the adaptive
 //                step-size decision (accept / retry) on the device.
 // The primal iterate is stored as interleaved pairs (x'_j, x'_j - x_j): one
 // vector gather per nonzero gives the dual kernel both K x' and K (x' - x),
 // so K(2x' - x) = K x' + K dx and the step-size interaction term dy^T K dx are
 // formed from K dx itself, not from the cancelling difference K x' - K x.
+//
+// Row traversal:
+//   float32 iterates -- one aligned group of LANES lanes per row, rows
+//     grid-strided (many warps in flight for the gathers); the group's first
+//     lane runs the row's float32 epilogue.
+//   float64 iterates -- a warp owns a tile of 32 consecutive rows, runs the
+//     SpMV of the tile LANES lanes per row, stages the 32 row sums in shared
+//     memory and then runs the 32 epilogues one per lane: on GB300 a float64
+//     warp instruction costs the SM's FP64 pipe ~16 cycles however few lanes
+//     are active, so the float64 epilogue must fill the warp.
 // Rows longer than a threshold are handled by extra blocks at the end of the
 // grid, one block per long row, so a skewed row cannot stall a group.
+//
+// The float32 kernels execute no float64 instruction: step sizes arrive
+// prepared in float (DevState::tau_f ...), partial sums are reduced in float.
 //
 // Two storage forms (both are the same preconditioned iteration):
 //   IMPLICIT = false: K~ = D_r K D_c is stored; vectors live in scaled space.
@@ -25,6 +37,8 @@
 //                     the scaled norms divide by tw / sw.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pdlp {
@@ -33,6 +47,19 @@ __device__ __forceinline__ float clampv(float v, float lo, float hi) { return fm
 __device__ __forceinline__ double clampv(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
 __device__ __forceinline__ float maxv(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double maxv(double a, double b) { return fmax(a, b); }
+
+// per-attempt scalars in the iterate type
+template <typename T> struct StepT;
+template <> struct StepT<float> {
+  static __device__ __forceinline__ float tau(const DevState* s) { return s->tau_f; }
+  static __device__ __forceinline__ float sigma(const DevState* s) { return s->sigma_f; }
+  static __device__ __forceinline__ float pw(const DevState* s) { return s->pw_f; }
+};
+template <> struct StepT<double> {
+  static __device__ __forceinline__ double tau(const DevState* s) { return s->tau_d; }
+  static __device__ __forceinline__ double sigma(const DevState* s) { return s->sigma_d; }
+  static __device__ __forceinline__ double pw(const DevState* s) { return s->pending_w; }
+};
 
 template <typename T, typename V>
 struct IterData {
@@ -47,8 +74,8 @@ struct IterData {
   vec2_t<T>* x[2];                                     // (x_j, x_j - previous x_j) pairs
   T* y[2];
   T* sum_x; T* sum_y;
-  double* part_p;                                      // [grid_p]
-  double* part_d;                                      // [2][grid_d]
+  T* part_p;                                           // [grid_p]
+  T* part_d;                                           // [2][grid_d]
   int grid_p_short, grid_p, grid_d_short, grid_d;
   DevState* st;
 };
@@ -64,9 +91,46 @@ __device__ __forceinline__ void rows_short(int nrows, const int* __restrict__ pt
     const int s = __ldg(ptr + r), e = __ldg(ptr + r + 1);
     if (e - s > thresh) continue;  // uniform within the group
     Acc acc{};
+#pragma unroll 4  // independent index loads and gathers in flight per lane
     for (int p = s + lane; p < e; p += LANES) acc += load(p);
     acc = group_sum<LANES>(acc);
     if (lane == 0) epi((int)r, acc);
+  }
+}
+
+// Tiles of 32 consecutive rows per warp: SpMV with LANES lanes per row in
+// LANES passes, row sums staged in shared memory, then one epilogue per lane.
+template <int LANES, typename Acc, typename Load, typename Epi>
+__device__ __forceinline__ void rows_tiled(int nrows, const int* __restrict__ ptr, int thresh,
+                                           int nblocks, Load load, Epi epi) {
+  constexpr int GPW = 32 / LANES;  // rows per pass
+  __shared__ Acc stage[kWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / LANES, gl = lane & (LANES - 1);
+  const long long W = (long long)nblocks * kWarps;
+  for (long long t = (long long)blockIdx.x * kWarps + warp; t * 32 < nrows; t += W) {
+    const long long r0 = t * 32;
+#pragma unroll 4
+    for (int pass = 0; pass < LANES; ++pass) {
+      const long long r = r0 + pass * GPW + g;
+      Acc acc{};
+      if (r < nrows) {
+        const int s = __ldg(ptr + r), e = __ldg(ptr + r + 1);
+        if (e - s <= thresh) {
+#pragma unroll 4
+          for (int p = s + gl; p < e; p += LANES) acc += load(p);
+        }
+      }
+      acc = group_sum<LANES>(acc);
+      if (gl == 0) stage[warp][pass * GPW + g] = acc;
+    }
+    __syncwarp();
+    const long long r = r0 + lane;
+    if (r < nrows) {
+      const int s = __ldg(ptr + r), e = __ldg(ptr + r + 1);
+      if (e - s <= thresh) epi((int)r, stage[warp][lane]);
+    }
+    __syncwarp();
   }
 }
 
@@ -97,30 +161,34 @@ __device__ __forceinline__ void rows_long(const int* __restrict__ ptr, const int
   }
 }
 
-template <typename T, typename V, int LANES, typename Epi, typename Vec>
-__device__ __forceinline__ void spmv_rows(int nrows, const int* ptr, const int* col, const V* val,
-                                          const Vec* vec, int thresh, const int* list, int nlist,
-                                          int nshort, Epi epi) {
-  auto load = [&](int p) -> T { return Ld<T, V>::get(val, p) * (T)__ldg(vec + __ldg(col + p)); };
-  if ((int)blockIdx.x < nshort)
-    rows_short<LANES, T>(nrows, ptr, thresh, nshort, load, epi);
-  else
-    rows_long<T>(ptr, list, nlist, nshort, load, epi);
+// Short rows by groups (float) or warp tiles (double), long rows by blocks.
+template <bool TILED, int LANES, typename Acc, typename Load, typename Epi>
+__device__ __forceinline__ void rows_all(int nrows, const int* ptr, int thresh, const int* list,
+                                         int nlist, int nshort, Load load, Epi epi) {
+  if ((int)blockIdx.x < nshort) {
+    if constexpr (TILED)
+      rows_tiled<LANES, Acc>(nrows, ptr, thresh, nshort, load, epi);
+    else
+      rows_short<LANES, Acc>(nrows, ptr, thresh, nshort, load, epi);
+  } else {
+    rows_long<Acc>(ptr, list, nlist, nshort, load, epi);
+  }
 }
 
 // ---------------------------------------------------------------- A4: primal
 template <int LANES, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock) k_primal(IterData<T, V> d) {
+  constexpr bool TILED = std::is_same<T, double>::value;
   DevState* st = d.st;
   if (st->status != 0 || st->check_due) return;
   const int cur = st->cur;
-  const vec2_t<T>* __restrict__ x = d.x[cur];
-  vec2_t<T>* __restrict__ xn = d.x[cur ^ 1];
-  const T* __restrict__ y = d.y[cur];
-  const T tau = (T)(st->eta / st->omega);
-  const double pw64 = st->pending_w;
-  const T pw = (T)pw64;
+  const vec2_t<T>* __restrict__ x = cur ? d.x[1] : d.x[0];
+  vec2_t<T>* __restrict__ xn = cur ? d.x[0] : d.x[1];
+  const T* __restrict__ y = cur ? d.y[1] : d.y[0];
+  const T tau = StepT<T>::tau(st);
+  const T pw = StepT<T>::pw(st);
   T dx2 = 0;
+  auto load = [&](int p) -> T { return Ld<T, V>::get(d.t_val, p) * __ldg(y + __ldg(d.t_col + p)); };
   auto epi = [&](int j, T aty) {
     const T xo = x[j].x;
     const T g = d.c[j] - aty;
@@ -131,63 +199,104 @@ __global__ void __launch_bounds__(kBlock) k_primal(IterData<T, V> d) {
     o.x = xv;
     o.y = dd;
     xn[j] = o;
-    if (pw64 != 0.0) d.sum_x[j] += pw * xo;  // A7: add the iterate whose weight is pending
+    if (pw != (T)0) d.sum_x[j] += pw * xo;  // A7: add the iterate whose weight is pending
     dx2 += IMPLICIT ? dd * dd / d.tw[j] : dd * dd;
   };
-  spmv_rows<T, V, LANES>(d.n, d.t_ptr, d.t_col, d.t_val, y, d.t_thresh, d.t_long, d.t_nlong,
-                         d.grid_p_short, epi);
-  double v[1] = {(double)dx2}, out[1];
-  block_sum<1>(v, out);
-  if (threadIdx.x == 0) d.part_p[blockIdx.x] = out[0];
+  rows_all<TILED, LANES, T>(d.n, d.t_ptr, d.t_thresh, d.t_long, d.t_nlong, d.grid_p_short, load, epi);
+  const T s = block_sum1<T>(dx2);
+  if (threadIdx.x == 0) d.part_p[blockIdx.x] = s;
 }
 
-// A6: adaptive step-size rule, decided once per attempt by one thread.
-__device__ __forceinline__ void decide_step(DevState* st, double dx2, double dy2, double dkd) {
+// step-rule factors of attempt k (1-based)
+__device__ __forceinline__ void step_factors(const DevState* st, long long k, double* fd, double* fi) {
+  if (k <= st->fac_n) {
+    *fd = st->fac_dec[k - 1];
+    *fi = st->fac_inc[k - 1];
+  } else {
+    *fd = 1.0 - pow((double)k + 1.0, -0.3);
+    *fi = 1.0 + pow((double)k + 1.0, -0.6);
+  }
+}
+
+__device__ __forceinline__ void step_factors(const DevState* st, long long k, float* fd, float* fi) {
+  if (k <= st->fac_n) {
+    *fd = st->fac_dec_f[k - 1];
+    *fi = st->fac_inc_f[k - 1];
+  } else {
+    *fd = 1.0f - powf((float)k + 1.0f, -0.3f);
+    *fi = 1.0f + powf((float)k + 1.0f, -0.6f);
+  }
+}
+
+// A6: adaptive step-size rule, decided once per attempt by one thread, in the
+// iterate precision (float64 for the parity mode; float32 otherwise, with the
+// float64 state mirrored for the restart logic and the report).
+template <typename T>
+__device__ __forceinline__ void decide_step(DevState* st, T dx2, T dy2, T dkd) {
+  constexpr bool F64 = std::is_same<T, double>::value;
   st->attempts += 1;
-  const double k = (double)st->attempts;
-  const double eta = st->eta, om = st->omega;
+  const long long k = st->attempts;
   if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(dkd)) {
     st->status = 4;  // PDLP_NUMERICAL
     return;
   }
-  const double den = 2.0 * fabs(dkd);
-  const double num = om * dx2 + dy2 / om;
-  const double eta_bar = den > 0.0 ? num / den : INFINITY;
+  const T eta = F64 ? (T)st->eta : (T)st->eta_f;
+  const T om = F64 ? (T)st->omega : (T)st->omega_f;
+  const T iom = F64 ? (T)st->inv_omega : (T)st->inv_omega_f;
+  const T den = (T)2 * fabs(dkd);
+  // float64 (the parity mode) divides where the definition divides; float32
+  // multiplies by the prepared reciprocal
+  const T num = F64 ? om * dx2 + dy2 / om : om * dx2 + dy2 * iom;
+  const T eta_bar = den > (T)0 ? num / den : (T)INFINITY;
   bool accept = true;
-  double eta_next = eta;
+  T eta_next = eta;
   if (st->adaptive) {
-    eta_next = fmin((1.0 - pow(k + 1.0, -0.3)) * eta_bar, (1.0 + pow(k + 1.0, -0.6)) * eta);
+    T fd, fi;
+    step_factors(st, k, &fd, &fi);
+    eta_next = fmin(fd * eta_bar, fi * eta);
     accept = !(eta > eta_bar);
   }
-  const long long t = st->attempts - 1;
+  const long long t = k - 1;
   if (t < st->tr_cap) {
-    st->tr_eta[t] = eta;
-    st->tr_eta_bar[t] = eta_bar;
+    st->tr_eta[t] = (double)eta;
+    st->tr_eta_bar[t] = (double)eta_bar;
     st->tr_accepted[t] = accept ? 1 : 0;
   }
-  st->pending_w = 0.0;
   if (accept) {
     st->cur ^= 1;
-    st->pending_w = eta;
-    st->sum_w += eta;
+    st->pending_w = (double)eta;
+    st->pw_f = (float)eta;
+    st->sum_w += (double)eta;
     st->iters += 1;
     if (st->iters % st->period == 0 || st->iters >= st->iter_limit) st->check_due = 1;
+  } else {
+    st->pending_w = 0.0;
+    st->pw_f = 0.0f;
   }
-  st->eta = eta_next;
+  if (F64) {
+    st->eta = (double)eta_next;
+    st->tau_d = (double)(eta_next / om);
+    st->sigma_d = (double)(eta_next * om);
+  } else {
+    st->eta_f = (float)eta_next;
+    st->eta = (double)eta_next;
+    st->tau_f = (float)(eta_next * iom);
+    st->sigma_f = (float)(eta_next * om);
+  }
 }
 
 // ---------------------------------------------------------------- A5 + A6: dual
 template <int LANES, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock) k_dual(IterData<T, V> d) {
+  constexpr bool TILED = std::is_same<T, double>::value;
   DevState* st = d.st;
   if (st->status != 0 || st->check_due) return;
   const int cur = st->cur;
-  const vec2_t<T>* __restrict__ xn = d.x[cur ^ 1];
-  const T* __restrict__ y = d.y[cur];
-  T* __restrict__ yn = d.y[cur ^ 1];
-  const T sigma = (T)(st->eta * st->omega);
-  const double pw64 = st->pending_w;
-  const T pw = (T)pw64;
+  const vec2_t<T>* __restrict__ xn = cur ? d.x[0] : d.x[1];
+  const T* __restrict__ y = cur ? d.y[1] : d.y[0];
+  T* __restrict__ yn = cur ? d.y[0] : d.y[1];
+  const T sigma = StepT<T>::sigma(st);
+  const T pw = StepT<T>::pw(st);
   T dy2 = 0, dkd = 0;
   // acc.a = (K x')_i, acc.b = (K dx)_i
   auto load = [&](int p) -> P2<T> {
@@ -202,41 +311,34 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterData<T, V> d) {
     T v = yo + step * (d.q[i] - kxbar);
     if (d.row_kind[i] != 1) v = maxv(v, (T)0);
     yn[i] = v;
-    if (pw64 != 0.0) d.sum_y[i] += pw * yo;
+    if (pw != (T)0) d.sum_y[i] += pw * yo;
     const T dd = v - yo;
     dy2 += IMPLICIT ? dd * dd / d.sw[i] : dd * dd;
     dkd += dd * acc.b;
   };
-  if ((int)blockIdx.x < d.grid_d_short)
-    rows_short<LANES, P2<T>>(d.m, d.a_ptr, d.a_thresh, d.grid_d_short, load, epi);
-  else
-    rows_long<P2<T>>(d.a_ptr, d.a_long, d.a_nlong, d.grid_d_short, load, epi);
-  double v[2] = {(double)dy2, (double)dkd}, out[2];
-  block_sum<2>(v, out);
+  rows_all<TILED, LANES, P2<T>>(d.m, d.a_ptr, d.a_thresh, d.a_long, d.a_nlong, d.grid_d_short,
+                                load, epi);
+  const T s0 = block_sum1<T>(dy2);
+  const T s1 = block_sum1<T>(dkd);
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    d.part_d[blockIdx.x] = out[0];
-    d.part_d[d.grid_d + blockIdx.x] = out[1];
+    d.part_d[blockIdx.x] = s0;
+    d.part_d[d.grid_d + blockIdx.x] = s1;
     __threadfence();
     last = (atomicAdd(&st->counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double sp[1], sd[2];
-  {
-    double a[1] = {0.0};
-    for (int i = threadIdx.x; i < d.grid_p; i += kBlock) a[0] += __ldcg(d.part_p + i);
-    block_sum<1>(a, sp);
-    double b[2] = {0.0, 0.0};
-    for (int i = threadIdx.x; i < d.grid_d; i += kBlock) {
-      b[0] += __ldcg(d.part_d + i);
-      b[1] += __ldcg(d.part_d + d.grid_d + i);
-    }
-    block_sum<2>(b, sd);
+  T a = 0, b0 = 0, b1 = 0;
+  for (int i = threadIdx.x; i < d.grid_p; i += kBlock) a += __ldcg(d.part_p + i);
+  for (int i = threadIdx.x; i < d.grid_d; i += kBlock) {
+    b0 += __ldcg(d.part_d + i);
+    b1 += __ldcg(d.part_d + d.grid_d + i);
   }
+  block_sum3<T>(a, b0, b1);
   if (threadIdx.x == 0) {
-    decide_step(st, sp[0], sd[0], sd[1]);
+    decide_step<T>(st, a, b0, b1);
     st->counter = 0;
   }
 }

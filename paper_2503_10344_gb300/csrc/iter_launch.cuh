@@ -22,7 +22,7 @@ IterData<T, V> typed(const IterRaw& r) {
     d.x[k] = (vec2_t<T>*)r.x[k]; d.y[k] = (T*)r.y[k];
   }
   d.sum_x = (T*)r.sum_x; d.sum_y = (T*)r.sum_y;
-  d.part_p = r.part_p; d.part_d = r.part_d;
+  d.part_p = (T*)r.part_p; d.part_d = (T*)r.part_d;
   d.grid_p_short = r.grid_p_short; d.grid_p = r.grid_p;
   d.grid_d_short = r.grid_d_short; d.grid_d = r.grid_d;
   d.st = r.st;

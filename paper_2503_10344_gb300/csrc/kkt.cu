@@ -23,6 +23,10 @@ namespace pdlp {
 
 namespace {
 
+// weighted average sum / sw: a division for float64 iterates (the parity mode
+// divides where the definition divides), the block's reciprocal otherwise
+#define avg_of(sum, sw, isw) (std::is_same<T, double>::value ? (sum) / (sw) : (sum) * (isw))
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
   DevState* st = r.st;
@@ -33,10 +37,14 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
   const T* y = (const T*)r.y[cur];
   const T* sx = (const T*)r.sum_x;
   const T* sy = (const T*)r.sum_y;
+  __shared__ double inv_sh;  // one float64 division per block, not per element
+  if (threadIdx.x == 0) inv_sh = sw > 0.0 ? 1.0 / sw : 0.0;
+  __syncthreads();
+  const double isw = inv_sh;
   const long long stride = (long long)gridDim.x * kBlock;
   for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
     const double xc = (double)x[j].x;
-    const double xa = sw > 0.0 ? ((double)sx[j] + pw * xc) / sw : xc;
+    const double xa = sw > 0.0 ? avg_of((double)sx[j] + pw * xc, sw, isw) : xc;
     const double s = r.scaled ? r.dc[j] : 1.0;
     // unscaled candidates, clipped to [l, u] so the KKT measured here is the
     // KKT of exactly the point the solver returns (A11)
@@ -45,7 +53,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
   }
   for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
     const double yc = (double)y[i];
-    const double ya = sw > 0.0 ? ((double)sy[i] + pw * yc) / sw : yc;
+    const double ya = sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc;
     const double s = r.scaled ? r.dr[i] : 1.0;
     r.Yc[i] = s * yc;
     r.Ya[i] = s * ya;
@@ -77,14 +85,12 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
       acc[0 + k] += rp * rp;
       acc[2 + k] += (dr * rp) * (dr * rp);
       acc[4 + k] += q * yv[k];
-      const double dd = (yv[k] - r.Yl[i]) / dr;
+      const double dd = (yv[k] - r.Yl[i]) * r.inv_dr[i];
       acc[6 + k] += dd * dd;
     }
   };
-  if ((int)blockIdx.x < r.grid_r_short)
-    rows_short<LANES, D2>(r.m, r.a_ptr, r.a_thresh, r.grid_r_short, load, epi);
-  else
-    rows_long<D2>(r.a_ptr, r.a_long, r.a_nlong, r.grid_r_short, load, epi);
+  rows_all<true, LANES, D2>(r.m, r.a_ptr, r.a_thresh, r.a_long, r.a_nlong, r.grid_r_short, load,
+                            epi);
   double out[8];
   block_sum<8>(acc, out);
   if (threadIdx.x == 0)
@@ -105,26 +111,27 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
     return D2{v * r.Yc[i], v * r.Ya[i]};
   };
   auto epi = [&](int j, D2 aty) {
-    const double c = r.c[j], l = r.l[j], u = r.u[j], dc = r.dc[j];
+    const double c = r.c[j], dc = r.dc[j], idc = r.inv_dc[j];
+    const unsigned f = r.bflags[j];
+    const bool lfin = f & 1u, ufin = f & 2u;
+    const double l = lfin ? r.l[j] : 0.0, u = ufin ? r.u[j] : 0.0;
     const double kty[2] = {aty.a, aty.b};
     const double xv[2] = {r.Xc[j], r.Xa[j]};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const double lam = c - kty[k];
       const double lp = fmax(lam, 0.0), lm = fmax(-lam, 0.0);
-      const double rd = (l == -INFINITY ? lp : 0.0) + (u == INFINITY ? lm : 0.0);
+      const double rd = (lfin ? 0.0 : lp) + (ufin ? 0.0 : lm);
       acc[0 + k] += rd * rd;
       acc[2 + k] += (dc * rd) * (dc * rd);
       acc[4 + k] += c * xv[k];
-      acc[6 + k] += (isfinite(l) ? l * lp : 0.0) - (isfinite(u) ? u * lm : 0.0);
-      const double dd = (xv[k] - r.Xl[j]) / dc;
+      acc[6 + k] += l * lp - u * lm;  // l, u read as 0 where infinite
+      const double dd = (xv[k] - r.Xl[j]) * idc;
       acc[8 + k] += dd * dd;
     }
   };
-  if ((int)blockIdx.x < r.grid_c_short)
-    rows_short<LANES, D2>(r.n, r.t_ptr, r.t_thresh, r.grid_c_short, load, epi);
-  else
-    rows_long<D2>(r.t_ptr, r.t_long, r.t_nlong, r.grid_c_short, load, epi);
+  rows_all<true, LANES, D2>(r.n, r.t_ptr, r.t_thresh, r.t_long, r.t_nlong, r.grid_c_short, load,
+                            epi);
   double out[10];
   block_sum<10>(acc, out);
   if (threadIdx.x == 0)
@@ -191,7 +198,17 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
     } else {
       // A10: primal weight from the scaled distances moved since the last restart
       const double ddx = sqrt(pc[8 + ua]), ddy = sqrt(pr[6 + ua]);
-      if (ddx > 1e-10 && ddy > 1e-10) st->omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(om));
+      if (ddx > 1e-10 && ddy > 1e-10) {
+        st->omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(om));
+        // step scalars of the next attempt in both precisions
+        st->inv_omega = 1.0 / st->omega;
+        st->omega_f = (float)st->omega;
+        st->inv_omega_f = (float)st->inv_omega;
+        st->tau_d = st->eta / st->omega;
+        st->sigma_d = st->eta * st->omega;
+        st->tau_f = st->eta_f * st->inv_omega_f;
+        st->sigma_f = st->eta_f * st->omega_f;
+      }
       st->last_rp2 = pr[2 + ua];
       st->last_rd2 = pc[2 + ua];
       st->last_gap2 = gap2[ua];
@@ -220,12 +237,16 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
   T* y = (T*)r.y[cur];
   T* sx = (T*)r.sum_x;
   T* sy = (T*)r.sum_y;
+  __shared__ double inv_sh;
+  if (threadIdx.x == 0) inv_sh = sw > 0.0 ? 1.0 / sw : 0.0;
+  __syncthreads();
+  const double isw = inv_sh;
   const long long stride = (long long)gridDim.x * kBlock;
   for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
     if (kind == 2) {
       const double xc = (double)x[j].x;
       vec2_t<T> v;
-      v.x = (T)(sw > 0.0 ? ((double)sx[j] + pw * xc) / sw : xc);
+      v.x = (T)(sw > 0.0 ? avg_of((double)sx[j] + pw * xc, sw, isw) : xc);
       v.y = (T)0;  // the step into the restart point is never read
       x[j] = v;
       r.Xl[j] = r.Xa[j];
@@ -237,7 +258,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
   for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
     if (kind == 2) {
       const double yc = (double)y[i];
-      y[i] = (T)(sw > 0.0 ? ((double)sy[i] + pw * yc) / sw : yc);
+      y[i] = (T)(sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc);
       r.Yl[i] = r.Ya[i];
     } else {
       r.Yl[i] = r.Yc[i];
@@ -252,6 +273,7 @@ __global__ void k_kkt_end(KktRaw r) {
   if (st->restart_kind != 0) {
     st->sum_w = 0.0;
     st->pending_w = 0.0;
+    st->pw_f = 0.0f;
   }
   st->restart_kind = 0;
   st->check_due = 0;

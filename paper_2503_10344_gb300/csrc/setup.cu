@@ -459,6 +459,20 @@ __global__ void k_finish_scalars(const double* vpart, int nv, const double* mpar
   }
 }
 
+// float64 auxiliaries of the KKT passes: 1 / D_r, 1 / D_c and, per column, bit 0
+// = lower bound finite, bit 1 = upper bound finite (integer tests instead of
+// float64 compares in the per-column epilogue)
+__global__ void k_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,
+                          const double* u, double* inv_dr, double* inv_dc, unsigned char* bflags) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    inv_dr[i] = 1.0 / dr[i];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    inv_dc[j] = 1.0 / dc[j];
+    bflags[j] = (unsigned char)((isfinite(l[j]) ? 1 : 0) | (isfinite(u[j]) ? 2 : 0));
+  }
+}
+
 // deterministic list of rows longer than thresh: flags, scan, scatter
 __global__ void k_long_flags(const int* ptr, int nrows, int thresh, int* flags) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -741,6 +755,14 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
 size_t setup_part_doubles(int m, int n) {
   const int G = device_sm_count() * 8;
   return (size_t)G * 4 + (size_t)G + 16;
+}
+
+cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,
+                          const double* u, double* inv_dr, double* inv_dc, unsigned char* bflags,
+                          cudaStream_t s) {
+  k_kkt_aux<<<grid_for(std::max(m, n), device_sm_count() * 8), kBlock, 0, s>>>(
+      m, n, dr, dc, l, u, inv_dr, inv_dc, bflags);
+  return cudaGetLastError();
 }
 
 cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, int* pos, int* bsum,

@@ -62,6 +62,9 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
                                const int* a_col, const double* a_val64, double* part,
                                double* scalars_out, cudaStream_t s);
 size_t scan_tmp_ints(long long N);
+cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,
+                          const double* u, double* inv_dr, double* inv_dc, unsigned char* bflags,
+                          cudaStream_t s);
 cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, int* pos, int* bsum,
                             int* list, int* h_count, cudaStream_t s);
 

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "../../include/pdlp.h"
@@ -54,12 +55,35 @@ struct Arena {
   }
 };
 
+// Step-rule factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 of attempts k = 1..kFacN,
+// computed once per process with the C library pow (static storage, no heap).
+constexpr int kFacN = 32768;
+struct FacTable {
+  double dec[kFacN], inc[kFacN];
+  float dec_f[kFacN], inc_f[kFacN];
+};
+static FacTable g_fac;
+static std::once_flag g_fac_once;
+static const FacTable& fac_table() {
+  std::call_once(g_fac_once, [] {
+    for (int i = 0; i < kFacN; ++i) {
+      const double k1 = (double)(i + 1) + 1.0;
+      g_fac.dec[i] = 1.0 - std::pow(k1, -0.3);
+      g_fac.inc[i] = 1.0 + std::pow(k1, -0.6);
+      g_fac.dec_f[i] = (float)g_fac.dec[i];
+      g_fac.inc_f[i] = (float)g_fac.inc[i];
+    }
+  });
+  return g_fac;
+}
+
 struct Bufs {
+  FacTable* fac;
   int *a_ptr, *a_col, *t_ptr, *t_col;
   double *a_val64, *t_val64;
   void *a_valit, *t_valit;
-  double *q64, *dr, *dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *stat_r, *stat_c;
-  unsigned char* row_kind;
+  double *q64, *dr, *dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *stat_r, *stat_c, *inv_dr, *inv_dc;
+  unsigned char *row_kind, *bflags;
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
   int *a_long, *t_long, *tmp, *flags2;
@@ -86,6 +110,7 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   elem_sizes(precision, &eb, &vb);
   const size_t G = (size_t)max_blocks() + kMaxLongBlocks;
   const size_t M = (size_t)m, N = (size_t)n, Z = (size_t)nnz;
+  b.fac = (FacTable*)ar.take(sizeof(FacTable));
   b.a_ptr = (int*)ar.take(4 * (M + 1));
   b.t_ptr = (int*)ar.take(4 * (N + 1));
   b.a_col = (int*)ar.take(4 * Z);
@@ -106,6 +131,9 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.stat_r = (double*)ar.take(8 * M);
   b.stat_c = (double*)ar.take(8 * N);
   b.row_kind = (unsigned char*)ar.take(M);
+  b.inv_dr = (double*)ar.take(8 * M);
+  b.inv_dc = (double*)ar.take(8 * N);
+  b.bflags = (unsigned char*)ar.take(N);
   b.c_it = ar.take(eb * N);
   b.l_it = ar.take(eb * N);
   b.u_it = ar.take(eb * N);
@@ -134,9 +162,13 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   return ar.off + 256;
 }
 
-static int auto_lanes(double avg_len) {
+// Lanes per row: the smallest power of two giving each lane at most `per_lane`
+// entries of an average row, in [2, 32].  Fewer lanes put more rows in a warp
+// (fewer shuffle levels, more rows per epilogue instruction); on GB300 float64
+// kernels pay ~16 pipe cycles per warp instruction, so they use fewer lanes.
+static int auto_lanes(double avg_len, double per_lane) {
   int l = 2;
-  while (l < 32 && l < avg_len) l <<= 1;
+  while (l < 32 && l * per_lane < avg_len) l <<= 1;
   return l;
 }
 
@@ -149,7 +181,8 @@ struct Solve {
   int m, n;
   long long nnz;
   Mode mode;
-  int lanes_a, lanes_t;
+  int lanes_a, lanes_t;    // step kernels
+  int lanes_ka, lanes_kt;  // KKT passes
   IterRaw ir;
   KktRaw kr;
   cudaStream_t s;
@@ -168,7 +201,7 @@ struct Solve {
     cudaError_t e;
     for (int k : {KK_PREP, KK_ROWS, KK_COLS, KK_FINAL, KK_APPLY, KK_END}) {
       ++g_launches;
-      if ((e = launch_kkt(k, lanes_a, lanes_t, kr, s)) != cudaSuccess) return e;
+      if ((e = launch_kkt(k, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
@@ -193,7 +226,9 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
     return fail(PDLP_ERR_INVALID_INPUT, "invalid parameter value");
   if (p->precision != PDLP_FP64 && p->precision != PDLP_FP32 && p->precision != PDLP_FP32_BF16A)
     return fail(PDLP_ERR_INVALID_INPUT, "unknown precision mode");
-  if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)))
+  if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)) ||
+      (p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
+      (p->lanes_kkt_AT && !valid_lanes(p->lanes_kkt_AT)))
     return fail(PDLP_ERR_INVALID_INPUT, "lanes must be 0, 2, 4, 8, 16 or 32");
   return PDLP_OK;
 }
@@ -295,6 +330,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
              p->pc_alpha};
   CUDA_TRY(setup_scaling(sc, bf.dr, bf.dc, bf.stat_r, bf.stat_c, s));
   g_launches += 2 + 4 * p->ruiz_iters + (p->pc_alpha >= 0 ? 4 : 0);
+  CUDA_TRY(setup_kkt_aux(m, n, bf.dr, bf.dc, l, u, bf.inv_dr, bf.inv_dc, bf.bflags, s));
+  ++g_launches;
   if (mode != MODE_PAT) {
     const int vt = mode == MODE_FP64 ? 0 : (mode == MODE_FP32 ? 1 : 2);
     CUDA_TRY(setup_iter_values(vt, bf.a_ptr, bf.a_col, bf.a_val64, m, bf.dr, bf.dc, 1, scaled,
@@ -310,9 +347,14 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   double sca[5];
   CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
   // ---- launch shapes and long rows
-  const int lanes_a = p->lanes_A ? p->lanes_A : auto_lanes(m ? (double)nnz / m : 1.0);
-  const int lanes_t = p->lanes_AT ? p->lanes_AT : auto_lanes((double)nnz / n);
-  const int th_a = long_thresh(lanes_a), th_t = long_thresh(lanes_t);
+  const double avg_a = m ? (double)nnz / m : 1.0, avg_t = (double)nnz / n;
+  const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
+  const int lanes_a = p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane);
+  const int lanes_t = p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane);
+  const int lanes_ka = p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0);
+  const int lanes_kt = p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0);
+  const int th_a = long_thresh(std::max(lanes_a, lanes_ka));
+  const int th_t = long_thresh(std::max(lanes_t, lanes_kt));
   int nlong_a = 0, nlong_t = 0;
   {
     const size_t R = (size_t)std::max(m, n) + 1;
@@ -324,11 +366,22 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     g_launches += 10;
   }
   const int MB = max_blocks();
-  const int gp_short = grid_for((long long)n * lanes_t, MB);
-  const int gd_short = grid_for((long long)std::max(m, 1) * lanes_a, MB);
+  // float32 step kernels: one group of lanes per row, rows grid-strided;
+  // float64 kernels (float64 steps, KKT passes): warp tiles of 32 rows
+  const bool tiled = mode == MODE_FP64;
+  const int gp_short = tiled ? grid_for(((long long)n + 31) / 32 * 32, MB)
+                             : grid_for((long long)n * lanes_t, MB);
+  const int gd_short = tiled ? grid_for(((long long)std::max(m, 1) + 31) / 32 * 32, MB)
+                             : grid_for((long long)std::max(m, 1) * lanes_a, MB);
   const int gp = gp_short + std::min(nlong_t, kMaxLongBlocks);
   const int gd = gd_short + std::min(nlong_a, kMaxLongBlocks);
   const int ge = grid_for(std::max(m, n), MB);
+  // KKT passes: at most two blocks per SM keeps the one-block final reduction short
+  const int KB = 2 * device_sm_count();
+  const int gr_short = grid_for(((long long)std::max(m, 1) + 31) / 32 * 32, KB);
+  const int gc_short = grid_for(((long long)n + 31) / 32 * 32, KB);
+  const int gr = gr_short + std::min(nlong_a, kMaxLongBlocks);
+  const int gc = gc_short + std::min(nlong_t, kMaxLongBlocks);
 
   IterRaw ir;
   ir.a_ptr = bf.a_ptr; ir.a_col = bf.a_col; ir.a_val = mode == MODE_PAT ? nullptr : bf.a_valit;
@@ -352,12 +405,13 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   kr.a_nlong = nlong_a; kr.t_nlong = nlong_t; kr.a_thresh = th_a; kr.t_thresh = th_t;
   kr.m = m; kr.n = n;
   kr.c = c; kr.l = l; kr.u = u; kr.q = bf.q64; kr.dr = bf.dr; kr.dc = bf.dc;
+  kr.inv_dr = bf.inv_dr; kr.inv_dc = bf.inv_dc; kr.bflags = bf.bflags;
   kr.row_kind = bf.row_kind;
   for (int k = 0; k < 2; ++k) { kr.x[k] = bf.x[k]; kr.y[k] = bf.y[k]; }
   kr.sum_x = bf.sum_x; kr.sum_y = bf.sum_y;
   kr.Xc = bf.Xc; kr.Xa = bf.Xa; kr.Xl = bf.Xl; kr.Yc = bf.Yc; kr.Ya = bf.Ya; kr.Yl = bf.Yl;
   kr.part_r = bf.part_r; kr.part_c = bf.part_c;
-  kr.grid_r_short = gd_short; kr.grid_r = gd; kr.grid_c_short = gp_short; kr.grid_c = gp;
+  kr.grid_r_short = gr_short; kr.grid_r = gr; kr.grid_c_short = gc_short; kr.grid_c = gc;
   kr.grid_e = ge;
   kr.scaled = scaled; kr.fp32 = fp32;
   kr.st = bf.st;
@@ -382,6 +436,24 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   hs.tol = p->tol;
   hs.norm_c = sca[2];
   hs.norm_q = sca[3];
+  hs.inv_omega = 1.0 / hs.omega;
+  hs.tau_d = hs.eta / hs.omega;
+  hs.sigma_d = hs.eta * hs.omega;
+  hs.eta_f = (float)hs.eta;
+  hs.omega_f = (float)hs.omega;
+  hs.inv_omega_f = (float)hs.inv_omega;
+  hs.tau_f = hs.eta_f * hs.inv_omega_f;
+  hs.sigma_f = hs.eta_f * hs.omega_f;
+  hs.pw_f = 0.0f;
+  {
+    const FacTable& ft = fac_table();
+    CUDA_TRY(cudaMemcpyAsync(bf.fac, &ft, sizeof(FacTable), cudaMemcpyHostToDevice, s));
+    hs.fac_dec = bf.fac->dec;
+    hs.fac_inc = bf.fac->inc;
+    hs.fac_dec_f = bf.fac->dec_f;
+    hs.fac_inc_f = bf.fac->inc_f;
+    hs.fac_n = kFacN;
+  }
   if (dg && dg->attempt_capacity > 0 && dg->eta && dg->eta_bar && dg->accepted) {
     hs.tr_eta = dg->eta;
     hs.tr_eta_bar = dg->eta_bar;
@@ -400,7 +472,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   CUDA_TRY(cudaMemsetAsync(bf.Xl, 0, 8 * (size_t)n, s));
   if (m) CUDA_TRY(cudaMemsetAsync(bf.Yl, 0, 8 * (size_t)m, s));
 
-  Solve sv{m, n, nnz, mode, lanes_a, lanes_t, ir, kr, s};
+  Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s};
   CUDA_TRY(sv.kkt_block());  // initial KKT and restart anchors
   if (!no_alloc) {
     CUDA_TRY(cudaEventRecord(e1, s));
@@ -611,8 +683,8 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
     for (int i = 0; i < tq.reps && ce == cudaSuccess; ++i) {
       if (which == 0 || which == 2) ce = cap.iter(IK_PRIMAL);
       if (ce == cudaSuccess && (which == 1 || which == 2)) ce = cap.iter(IK_DUAL);
-      if (which == 3) ce = launch_kkt(KK_ROWS, sv.lanes_a, sv.lanes_t, sv.kr, cs);
-      if (which == 4) ce = launch_kkt(KK_COLS, sv.lanes_a, sv.lanes_t, sv.kr, cs);
+      if (which == 3) ce = launch_kkt(KK_ROWS, sv.lanes_ka, sv.lanes_kt, sv.kr, cs);
+      if (which == 4) ce = launch_kkt(KK_COLS, sv.lanes_ka, sv.lanes_kt, sv.kr, cs);
     }
     cudaError_t ee = cudaStreamEndCapture(cs, &g);
     if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
