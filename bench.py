@@ -107,6 +107,19 @@ class ClockSampler:
                 "reasons": reasons}
 
 
+def ncu_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, if one exists for
+    this kernel version and precision (profiles/dram_traffic.txt), else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) == 3 and not line.startswith("#") and f[0] == kernel and f[1] == precision:
+            return float(f[2])
+    return None
+
+
 # ------------------------------------------------------------------ CPU oracle
 CPU_SNIPPET = r"""
 import json, sys, time
@@ -247,7 +260,7 @@ def run_gpu(args):
     dom = max(("primal_step", "dual_step"), key=lambda k: kt[k]["ms"])
     ach = kt[dom]["bytes"] / (kt[dom]["ms"] * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "traffic": None,
+            "frac": ach / peak, "traffic": ncu_traffic(dom, args.precision),
             "peak_source": "measured" if peaks else "fallback",
             "kernels": {k: {"us": 1e3 * v["ms"], "bytes": v["bytes"],
                             "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9} for k, v in kt.items()}}
