@@ -244,6 +244,57 @@ int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, const char* se
                               double* x_out, double* y_out, pdlp_result* r,
                               const pdlp_diagnostics* diag, void* stream);
 
+/* ---- fix-and-propagate consumer (section 2 of the paper) --------------
+ * The LP solution ranks and drives the fixings of a fix-and-propagate
+ * heuristic: integers are ordered by a variable strategy (section 2, "LP-based
+ * variable strategies"), fixed by LP-based randomized fixing ("LP-based
+ * fixing": d_i = x - floor(x), d ~ U(0,1), floor if d > d_i else ceil), branched
+ * with the integer-aware rule of Alg. 1 (2 or 3 bound changes, the fixing
+ * first), propagated (linear activity bound tightening) with depth-first
+ * backtracking; when every integer is fixed the remaining LP is solved (the
+ * paper's "final LP", here by pdlp_solve in float64).  Host code. */
+#define FP_FRAC 0     /* ascending fractionality of the LP value */
+#define FP_REDCOST 1  /* descending |reduced cost| */
+#define FP_DUAL 2     /* rows by descending |y|, their integers by descending |reduced cost| */
+#define FP_TYPE 3     /* binaries first, then general integers (stable) */
+#define FP_FEASIBLE 1    /* all integers fixed and the final LP feasible (rel. 1e-6) */
+#define FP_INFEASIBLE 2  /* search exhausted, root infeasible, or final LP infeasible: abort */
+#define FP_NODE_LIMIT 3  /* node limit reached */
+#define FP_NO_FINAL_LP 4 /* all integers fixed; final LP not requested */
+
+typedef struct {
+  size_t struct_size;  /* sizeof(fp_params); set by fp_default_params */
+  int var_strategy;    /* FP_FRAC | FP_REDCOST | FP_DUAL | FP_TYPE (default) */
+  uint64_t seed;       /* SplitMix64 seed of the fixing draws, default 1 */
+  int64_t node_limit;  /* branching nodes; <= 0 means 10 x (number of integers) */
+  int final_lp;        /* 1 (default): solve the final LP; 0: stop after the search */
+  double final_lp_tol; /* relative KKT tolerance of the final LP, default 1e-8 */
+} fp_params;
+
+typedef struct {
+  int status;              /* FP_FEASIBLE, FP_INFEASIBLE, FP_NODE_LIMIT, FP_NO_FINAL_LP */
+  double obj;              /* c^T x of the returned point (NaN unless FP_FEASIBLE) */
+  int64_t nodes;           /* branching nodes visited */
+  int64_t backtracks;      /* exhausted nodes popped */
+  int64_t final_lp_iters;  /* PDHG iterations of the final LP */
+  double final_rel_primal; /* relative primal residual of the final LP */
+  double search_s, lp_s;   /* host seconds in the search, in the final LP */
+} fp_result;
+
+int fp_default_params(fp_params* p);
+
+/* Run the heuristic on HOST buffers.
+ *   A, b, sense, c, l, u: the MIP's LP in the layout of pdlp_solve.
+ *   x_lp[n]: an LP solution (e.g. pdlp_solve's x_out); y_lp[m]: its duals in
+ *     pdlp's sign convention (needed by FP_REDCOST and FP_DUAL, else may be NULL).
+ *   is_int[n]: 1 for integer columns.
+ *   x_out[n]: the integer assignment (NaN in continuous columns unless the
+ *     final LP ran) and, after the final LP, the whole point.
+ * Returns PDLP_OK or an error code (the outcome is r->status). */
+int fp_run(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+           const double* l, const double* u, const double* x_lp, const double* y_lp,
+           const uint8_t* is_int, const fp_params* p, double* x_out, fp_result* r);
+
 /* Name of a return code, and the last error message of the calling thread. */
 const char* pdlp_error_string(int code);
 const char* pdlp_last_error(void);

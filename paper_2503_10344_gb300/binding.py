@@ -285,3 +285,56 @@ def pdlp_solve_device_noalloc(dlp: DeviceLP, params: PdlpParams | None = None, x
                                          C.c_void_p(stream.cuda_stream))
     _check(rc)
     return x_out, y_out[: dlp.m], res.as_dict()
+
+
+# ------------------------------------------------------------------ fix-and-propagate
+FP_FRAC, FP_REDCOST, FP_DUAL, FP_TYPE = 0, 1, 2, 3
+FP_FEASIBLE, FP_INFEASIBLE, FP_NODE_LIMIT, FP_NO_FINAL_LP = 1, 2, 3, 4
+FP_STRATEGY = {"frac": FP_FRAC, "redcost": FP_REDCOST, "dual": FP_DUAL, "type": FP_TYPE}
+
+
+class FpParams(C.Structure):
+    _fields_ = [("struct_size", C.c_size_t), ("var_strategy", C.c_int), ("seed", C.c_uint64),
+                ("node_limit", C.c_int64), ("final_lp", C.c_int), ("final_lp_tol", C.c_double)]
+
+
+class FpResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("obj", C.c_double), ("nodes", C.c_int64),
+                ("backtracks", C.c_int64), ("final_lp_iters", C.c_int64),
+                ("final_rel_primal", C.c_double), ("search_s", C.c_double), ("lp_s", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def fp_run(lp, x_lp, y_lp=None, is_int=None, strategy="type", seed: int = 1, node_limit: int = 0,
+           final_lp: bool = True, final_lp_tol: float = 1e-8):
+    """Fix-and-propagate on host buffers; returns (x, result dict)."""
+    L = lib()
+    if not getattr(L, "_fp_ready", False):
+        L.fp_default_params.argtypes = [C.POINTER(FpParams)]
+        L.fp_run.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 8 + [C.POINTER(FpParams),
+                                                                      C.c_void_p, C.POINTER(FpResult)]
+        L._fp_ready = True
+    p = FpParams()
+    L.fp_default_params(C.byref(p))
+    p.var_strategy = FP_STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    p.seed = seed
+    p.node_limit = node_limit
+    p.final_lp = 1 if final_lp else 0
+    p.final_lp_tol = final_lp_tol
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    row_ptr = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(lp.col, dtype=np.int32)
+    val, b, c, l, u = f64(lp.val), f64(lp.b), f64(lp.c), f64(lp.l), f64(lp.u)
+    sense = np.ascontiguousarray(lp.sense, dtype=np.uint8)
+    ii = np.ascontiguousarray(lp.is_int if is_int is None else is_int, dtype=np.uint8)
+    xl = f64(x_lp)
+    yl = None if y_lp is None else f64(y_lp)
+    csr = PdlpCsr(lp.m, lp.n, int(row_ptr[-1]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    x = np.empty(lp.n)
+    r = FpResult()
+    rc = L.fp_run(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u), _ptr(xl), _ptr(yl),
+                  _ptr(ii), C.byref(p), _ptr(x), C.byref(r))
+    _check(rc)
+    return x, r.as_dict()

@@ -29,7 +29,7 @@ def _nvcc() -> str:
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _deps():
@@ -53,8 +53,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *CFLAGS, "-c", src, "-o", obj]
+        base, ext = os.path.splitext(os.path.basename(src))
+        obj = os.path.join(BUILD, base + ".o")
+        # host-only C++: no FMA contraction, so its float decisions are reproducible
+        extra = ["-Xcompiler", "-ffp-contract=off"] if ext == ".cpp" else []
+        cmd = [nvcc, *ARCH, *CFLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
