@@ -177,6 +177,25 @@ int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const doub
                const double* y0, double* x_out, double* y_out, pdlp_result* r,
                const pdlp_diagnostics* diag);
 
+/* Solve `count` LPs of uneven size together (north-star pattern "batched":
+ * relaxations such as those left after the partial fixings of the heuristic).
+ * Arrays of per-LP HOST pointers in the layout of pdlp_solve; one parameter
+ * set for all; r[count] results.  x_out / y_out may be NULL (or hold NULL
+ * entries) for outputs not wanted.
+ * The LPs form one block-diagonal problem on the device: each LP is set up
+ * (canonical form, transpose, scaling) on its own, then every step kernel and
+ * KKT pass runs over all LPs in one launch; each LP keeps its own step size,
+ * primal weight, restarts and termination, and stops independently.  One CUDA
+ * graph holds check_period attempts plus the KKT block of the whole batch.
+ * All LPs share one precision mode: FP32_BF16A picks the pattern / bf16 form
+ * only if every LP qualifies.  Limits: total rows, columns and nonzeros below
+ * 2^31.  Returns PDLP_OK or an error code (an invalid LP names its index in
+ * pdlp_last_error). */
+int pdlp_solve_batch(int count, const pdlp_csr* const* A, const double* const* b,
+                     const char* const* sense, const double* const* c, const double* const* l,
+                     const double* const* u, const pdlp_params* p, double* const* x_out,
+                     double* const* y_out, pdlp_result* r);
+
 /* Device workspace, in bytes, that pdlp_solve_device needs for this size and
  * these parameters (precision mode and value format decide it).  Returns 0 on
  * invalid sizes.  The bound holds for every value pattern. */

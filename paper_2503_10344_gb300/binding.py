@@ -338,3 +338,42 @@ def fp_run(lp, x_lp, y_lp=None, is_int=None, strategy="type", seed: int = 1, nod
                   _ptr(ii), C.byref(p), _ptr(x), C.byref(r))
     _check(rc)
     return x, r.as_dict()
+
+
+def pdlp_solve_batch(lps, params: PdlpParams | None = None, want_y: bool = True):
+    """Solve a list of LPs together (host buffers); returns (xs, ys, results)."""
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.pdlp_solve_batch.argtypes = [C.c_int, C.c_void_p] + [C.c_void_p] * 5 + \
+            [C.POINTER(PdlpParams), C.c_void_p, C.c_void_p, C.c_void_p]
+        L._batch_ready = True
+    p = params or default_params()
+    k = len(lps)
+    keep = []  # keeps the numpy arrays alive during the call
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    csrs = (PdlpCsr * k)()
+    ptrs = {name: (C.c_void_p * k)() for name in ("b", "sense", "c", "l", "u", "x", "y")}
+    xs = [np.empty(lp.n) for lp in lps]
+    ys = [np.empty(lp.m) for lp in lps]
+    for i, lp in enumerate(lps):
+        rp = arr(lp.row_ptr, np.int64)
+        csrs[i] = PdlpCsr(lp.m, lp.n, int(rp[-1]), _ptr(rp), _ptr(arr(lp.col, np.int32)),
+                          _ptr(arr(lp.val, np.float64)))
+        ptrs["b"][i] = _ptr(arr(lp.b, np.float64))
+        ptrs["sense"][i] = _ptr(arr(lp.sense, np.uint8))
+        ptrs["c"][i] = _ptr(arr(lp.c, np.float64))
+        ptrs["l"][i] = _ptr(arr(lp.l, np.float64))
+        ptrs["u"][i] = _ptr(arr(lp.u, np.float64))
+        ptrs["x"][i] = _ptr(xs[i])
+        ptrs["y"][i] = _ptr(ys[i]) if want_y else None
+    csr_ptrs = (C.c_void_p * k)(*[C.cast(C.pointer(csrs[i]), C.c_void_p) for i in range(k)])
+    res = (PdlpResult * k)()
+    rc = L.pdlp_solve_batch(k, csr_ptrs, ptrs["b"], ptrs["sense"], ptrs["c"], ptrs["l"], ptrs["u"],
+                            C.byref(p), ptrs["x"], ptrs["y"], res)
+    _check(rc)
+    return xs, ys, [res[i].as_dict() for i in range(k)]

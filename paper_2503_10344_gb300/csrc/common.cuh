@@ -88,6 +88,60 @@ struct DevState {
   long long tr_check_cap;
 };
 
+// ---------------------------------------------------------------- batches
+// Launch tables of a batch of LPs solved together (all NULL for one LP): the
+// batch is one block-diagonal problem with global row/column indices; every
+// block of a kernel belongs to one LP and processes that LP's rows only.
+struct Tables {
+  const int* blk_lp;  // [grid] block -> LP
+  const int* blk0;    // [count] first block of the LP (also its first partial slot)
+  const int* nshort;  // [count] blocks over short rows
+  const int* nblk;    // [count] all blocks of the LP (short + one per long row)
+  const int* row0;    // [count] first global row of the LP in this matrix
+  const int* nrows;   // [count] rows of the LP in this matrix
+  const int* long0;   // [count] first entry of the LP in the long-row list
+  const int* nlong;   // [count] long rows of the LP
+};
+
+// The rows of one LP and the blocks that own them, as seen by one block.
+struct Span {
+  int lp;            // LP index (0 for a single LP)
+  int row0, nrows;   // global row range
+  int bidx;          // block index within the LP's blocks
+  int nshort, nblk;  // the LP's short-row blocks and all its blocks
+  int part0;         // global index of the LP's first block (its first partial slot)
+  const int* list;   // the LP's long rows (global ids)
+  int nlist;
+};
+
+__device__ __forceinline__ Span make_span(const Tables& t, int nrows1, int nshort1,
+                                          const int* list1, int nlist1) {
+  Span s;
+  if (t.blk_lp == nullptr) {
+    s.lp = 0;
+    s.row0 = 0;
+    s.nrows = nrows1;
+    s.bidx = blockIdx.x;
+    s.nshort = nshort1;
+    s.nblk = gridDim.x;
+    s.part0 = 0;
+    s.list = list1;
+    s.nlist = nlist1;
+  } else {
+    const int k = t.blk_lp[blockIdx.x];
+    s.lp = k;
+    s.row0 = t.row0[k];
+    s.nrows = t.nrows[k];
+    s.part0 = t.blk0[k];
+    s.bidx = blockIdx.x - s.part0;
+    s.nshort = t.nshort[k];
+    s.nblk = t.nblk[k];
+    s.list = list1 + t.long0[k];
+    s.nlist = t.nlong[k];
+  }
+  return s;
+}
+
 // ---------------------------------------------------------------- reductions
 template <int LANES, typename T>
 __device__ __forceinline__ T group_sum(T v) {

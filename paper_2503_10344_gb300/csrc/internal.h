@@ -25,7 +25,8 @@ struct IterRaw {
   void *x[2], *y[2], *sum_x, *sum_y;  // x: interleaved (x_j, dx_j) pairs
   double *part_p, *part_d;
   int grid_p_short, grid_p, grid_d_short, grid_d;
-  DevState* st;
+  DevState* st;  // [count]
+  Tables tp, td; // batch tables over A^T and A (all NULL for one LP)
 };
 
 enum IterKernel { IK_PRIMAL = 0, IK_DUAL = 1 };
@@ -53,7 +54,10 @@ struct KktRaw {
   int grid_r_short, grid_r, grid_c_short, grid_c, grid_e;
   int scaled;  // iterates are in scaled space (explicit K~)
   int fp32;    // iterate element type is float
-  DevState* st;
+  DevState* st;  // [count]
+  int count;     // LPs in the batch (1 for a single LP)
+  Tables tr, tc; // batch tables over A and A^T (all NULL for one LP); the elementwise
+                 // kernels use tc's block map with grid_c blocks
 };
 
 enum KktKernel { KK_PREP = 0, KK_ROWS = 1, KK_COLS = 2, KK_FINAL = 3, KK_APPLY = 4, KK_END = 5 };

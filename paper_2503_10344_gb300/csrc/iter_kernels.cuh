@@ -77,17 +77,20 @@ struct IterData {
   T* part_p;                                           // [grid_p]
   T* part_d;                                           // [2][grid_d]
   int grid_p_short, grid_p, grid_d_short, grid_d;
-  DevState* st;
+  DevState* st;                                        // [count] (one per LP)
+  Tables tp, td;                                       // batch tables over A^T / A (NULL: one LP)
 };
 
-// Rows r = g, g + G, ... of a CSR matrix, one aligned group of LANES lanes per
-// row; rows longer than `thresh` are skipped here (the long-row blocks own them).
+// Rows of one LP (span), one aligned group of LANES lanes per row, rows
+// grid-strided over the LP's short-row blocks; rows longer than `thresh` are
+// skipped here (the long-row blocks own them).
 template <int LANES, typename Acc, typename Load, typename Epi>
-__device__ __forceinline__ void rows_short(int nrows, const int* __restrict__ ptr, int thresh,
-                                           int nblocks, Load load, Epi epi) {
+__device__ __forceinline__ void rows_short(const Span& sp, const int* __restrict__ ptr, int thresh,
+                                           Load load, Epi epi) {
   const int lane = threadIdx.x & (LANES - 1);
-  const long long G = (long long)nblocks * kBlock / LANES;
-  for (long long r = ((long long)blockIdx.x * kBlock + threadIdx.x) / LANES; r < nrows; r += G) {
+  const long long G = (long long)sp.nshort * kBlock / LANES;
+  const long long end = (long long)sp.row0 + sp.nrows;
+  for (long long r = sp.row0 + ((long long)sp.bidx * kBlock + threadIdx.x) / LANES; r < end; r += G) {
     const int s = __ldg(ptr + r), e = __ldg(ptr + r + 1);
     if (e - s > thresh) continue;  // uniform within the group
     Acc acc{};
@@ -101,20 +104,21 @@ __device__ __forceinline__ void rows_short(int nrows, const int* __restrict__ pt
 // Tiles of 32 consecutive rows per warp: SpMV with LANES lanes per row in
 // LANES passes, row sums staged in shared memory, then one epilogue per lane.
 template <int LANES, typename Acc, typename Load, typename Epi>
-__device__ __forceinline__ void rows_tiled(int nrows, const int* __restrict__ ptr, int thresh,
-                                           int nblocks, Load load, Epi epi) {
+__device__ __forceinline__ void rows_tiled(const Span& sp, const int* __restrict__ ptr, int thresh,
+                                           Load load, Epi epi) {
   constexpr int GPW = 32 / LANES;  // rows per pass
   __shared__ Acc stage[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / LANES, gl = lane & (LANES - 1);
-  const long long W = (long long)nblocks * kWarps;
-  for (long long t = (long long)blockIdx.x * kWarps + warp; t * 32 < nrows; t += W) {
-    const long long r0 = t * 32;
+  const long long W = (long long)sp.nshort * kWarps;
+  const long long end = (long long)sp.row0 + sp.nrows;
+  for (long long t = (long long)sp.bidx * kWarps + warp; t * 32 < sp.nrows; t += W) {
+    const long long r0 = sp.row0 + t * 32;
 #pragma unroll 4
     for (int pass = 0; pass < LANES; ++pass) {
       const long long r = r0 + pass * GPW + g;
       Acc acc{};
-      if (r < nrows) {
+      if (r < end) {
         const int s = __ldg(ptr + r), e = __ldg(ptr + r + 1);
         if (e - s <= thresh) {
 #pragma unroll 4
@@ -126,7 +130,7 @@ __device__ __forceinline__ void rows_tiled(int nrows, const int* __restrict__ pt
     }
     __syncwarp();
     const long long r = r0 + lane;
-    if (r < nrows) {
+    if (r < end) {
       const int s = __ldg(ptr + r), e = __ldg(ptr + r + 1);
       if (e - s <= thresh) epi((int)r, stage[warp][lane]);
     }
@@ -147,12 +151,12 @@ __device__ __forceinline__ Acc block_allsum(Acc v) {
   return s;  // valid in thread 0
 }
 
-// Long rows: one block per row of the list, blocks [first, gridDim.x).
+// Long rows of the LP: one block per row of its list, its blocks [nshort, nblk).
 template <typename Acc, typename Load, typename Epi>
-__device__ __forceinline__ void rows_long(const int* __restrict__ ptr, const int* __restrict__ list,
-                                          int nlist, int first, Load load, Epi epi) {
-  for (int k = blockIdx.x - first; k < nlist; k += gridDim.x - first) {
-    const int r = list[k];
+__device__ __forceinline__ void rows_long(const Span& sp, const int* __restrict__ ptr, Load load,
+                                          Epi epi) {
+  for (int k = sp.bidx - sp.nshort; k < sp.nlist; k += sp.nblk - sp.nshort) {
+    const int r = sp.list[k];
     const int s = ptr[r], e = ptr[r + 1];
     Acc acc{};
     for (int p = s + threadIdx.x; p < e; p += kBlock) acc += load(p);
@@ -163,15 +167,15 @@ __device__ __forceinline__ void rows_long(const int* __restrict__ ptr, const int
 
 // Short rows by groups (float) or warp tiles (double), long rows by blocks.
 template <bool TILED, int LANES, typename Acc, typename Load, typename Epi>
-__device__ __forceinline__ void rows_all(int nrows, const int* ptr, int thresh, const int* list,
-                                         int nlist, int nshort, Load load, Epi epi) {
-  if ((int)blockIdx.x < nshort) {
+__device__ __forceinline__ void rows_all(const Span& sp, const int* ptr, int thresh, Load load,
+                                         Epi epi) {
+  if (sp.bidx < sp.nshort) {
     if constexpr (TILED)
-      rows_tiled<LANES, Acc>(nrows, ptr, thresh, nshort, load, epi);
+      rows_tiled<LANES, Acc>(sp, ptr, thresh, load, epi);
     else
-      rows_short<LANES, Acc>(nrows, ptr, thresh, nshort, load, epi);
+      rows_short<LANES, Acc>(sp, ptr, thresh, load, epi);
   } else {
-    rows_long<Acc>(ptr, list, nlist, nshort, load, epi);
+    rows_long<Acc>(sp, ptr, load, epi);
   }
 }
 
@@ -179,7 +183,8 @@ __device__ __forceinline__ void rows_all(int nrows, const int* ptr, int thresh, 
 template <int LANES, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock) k_primal(IterData<T, V> d) {
   constexpr bool TILED = std::is_same<T, double>::value;
-  DevState* st = d.st;
+  const Span sp = make_span(d.tp, d.n, d.grid_p_short, d.t_long, d.t_nlong);
+  DevState* st = d.st + sp.lp;
   if (st->status != 0 || st->check_due) return;
   const int cur = st->cur;
   const vec2_t<T>* __restrict__ x = cur ? d.x[1] : d.x[0];
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_primal(IterData<T, V> d) {
     if (pw != (T)0) d.sum_x[j] += pw * xo;  // A7: add the iterate whose weight is pending
     dx2 += IMPLICIT ? dd * dd / d.tw[j] : dd * dd;
   };
-  rows_all<TILED, LANES, T>(d.n, d.t_ptr, d.t_thresh, d.t_long, d.t_nlong, d.grid_p_short, load, epi);
+  rows_all<TILED, LANES, T>(sp, d.t_ptr, d.t_thresh, load, epi);
   const T s = block_sum1<T>(dx2);
   if (threadIdx.x == 0) d.part_p[blockIdx.x] = s;
 }
@@ -289,7 +294,8 @@ __device__ __forceinline__ void decide_step(DevState* st, T dx2, T dy2, T dkd) {
 template <int LANES, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock) k_dual(IterData<T, V> d) {
   constexpr bool TILED = std::is_same<T, double>::value;
-  DevState* st = d.st;
+  const Span sp = make_span(d.td, d.m, d.grid_d_short, d.a_long, d.a_nlong);
+  DevState* st = d.st + sp.lp;
   if (st->status != 0 || st->check_due) return;
   const int cur = st->cur;
   const vec2_t<T>* __restrict__ xn = cur ? d.x[0] : d.x[1];
@@ -316,8 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterData<T, V> d) {
     dy2 += IMPLICIT ? dd * dd / d.sw[i] : dd * dd;
     dkd += dd * acc.b;
   };
-  rows_all<TILED, LANES, P2<T>>(d.m, d.a_ptr, d.a_thresh, d.a_long, d.a_nlong, d.grid_d_short,
-                                load, epi);
+  rows_all<TILED, LANES, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
   const T s0 = block_sum1<T>(dy2);
   const T s1 = block_sum1<T>(dkd);
   __shared__ bool last;
@@ -325,16 +330,22 @@ __global__ void __launch_bounds__(kBlock) k_dual(IterData<T, V> d) {
     d.part_d[blockIdx.x] = s0;
     d.part_d[d.grid_d + blockIdx.x] = s1;
     __threadfence();
-    last = (atomicAdd(&st->counter, 1u) == gridDim.x - 1);
+    last = (atomicAdd(&st->counter, 1u) == (unsigned)sp.nblk - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // this LP's partial slots: its primal blocks and its dual blocks
+  int p0 = 0, pn = d.grid_p;
+  if (d.tp.blk_lp != nullptr) {
+    p0 = d.tp.blk0[sp.lp];
+    pn = d.tp.nblk[sp.lp];
+  }
   T a = 0, b0 = 0, b1 = 0;
-  for (int i = threadIdx.x; i < d.grid_p; i += kBlock) a += __ldcg(d.part_p + i);
-  for (int i = threadIdx.x; i < d.grid_d; i += kBlock) {
-    b0 += __ldcg(d.part_d + i);
-    b1 += __ldcg(d.part_d + d.grid_d + i);
+  for (int i = threadIdx.x; i < pn; i += kBlock) a += __ldcg(d.part_p + p0 + i);
+  for (int i = threadIdx.x; i < sp.nblk; i += kBlock) {
+    b0 += __ldcg(d.part_d + sp.part0 + i);
+    b1 += __ldcg(d.part_d + d.grid_d + sp.part0 + i);
   }
   block_sum3<T>(a, b0, b1);
   if (threadIdx.x == 0) {

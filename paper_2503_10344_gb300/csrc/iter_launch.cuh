@@ -26,6 +26,8 @@ IterData<T, V> typed(const IterRaw& r) {
   d.grid_p_short = r.grid_p_short; d.grid_p = r.grid_p;
   d.grid_d_short = r.grid_d_short; d.grid_d = r.grid_d;
   d.st = r.st;
+  d.tp = r.tp;
+  d.td = r.td;
   return d;
 }
 

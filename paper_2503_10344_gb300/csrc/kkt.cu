@@ -27,9 +27,21 @@ namespace {
 // divides where the definition divides), the block's reciprocal otherwise
 #define avg_of(sum, sw, isw) (std::is_same<T, double>::value ? (sum) / (sw) : (sum) * (isw))
 
+// columns and rows of one LP for the elementwise kernels (prep, apply, output)
+struct ESpan {
+  int lp, c0, nc, r0, nr, bidx, nblk;
+};
+__device__ __forceinline__ ESpan make_espan(const KktRaw& r) {
+  if (r.tc.blk_lp == nullptr) return ESpan{0, 0, r.n, 0, r.m, (int)blockIdx.x, (int)gridDim.x};
+  const int k = r.tc.blk_lp[blockIdx.x];
+  return ESpan{k, r.tc.row0[k], r.tc.nrows[k], r.tr.row0[k], r.tr.nrows[k],
+               (int)blockIdx.x - r.tc.blk0[k], r.tc.nblk[k]};
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
-  DevState* st = r.st;
+  const ESpan es = make_espan(r);
+  DevState* st = r.st + es.lp;
   if (!st->check_due || st->status != 0) return;
   const int cur = st->cur;
   const double pw = st->pending_w, sw = st->sum_w;
@@ -41,8 +53,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
   if (threadIdx.x == 0) inv_sh = sw > 0.0 ? 1.0 / sw : 0.0;
   __syncthreads();
   const double isw = inv_sh;
-  const long long stride = (long long)gridDim.x * kBlock;
-  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+  const long long stride = (long long)es.nblk * kBlock;
+  for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
     const double xc = (double)x[j].x;
     const double xa = sw > 0.0 ? avg_of((double)sx[j] + pw * xc, sw, isw) : xc;
     const double s = r.scaled ? r.dc[j] : 1.0;
@@ -51,7 +63,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
     r.Xc[j] = fmin(fmax(s * xc, r.l[j]), r.u[j]);
     r.Xa[j] = fmin(fmax(s * xa, r.l[j]), r.u[j]);
   }
-  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+  for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double yc = (double)y[i];
     const double ya = sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc;
     const double s = r.scaled ? r.dr[i] : 1.0;
@@ -64,7 +76,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
 // [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2
 template <int LANES>
 __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
-  DevState* st = r.st;
+  const Span sp = make_span(r.tr, r.m, r.grid_r_short, r.a_long, r.a_nlong);
+  DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const double* __restrict__ val = r.a_val64;
@@ -89,8 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
       acc[6 + k] += dd * dd;
     }
   };
-  rows_all<true, LANES, D2>(r.m, r.a_ptr, r.a_thresh, r.a_long, r.a_nlong, r.grid_r_short, load,
-                            epi);
+  rows_all<true, LANES, D2>(sp, r.a_ptr, r.a_thresh, load, epi);
   double out[8];
   block_sum<8>(acc, out);
   if (threadIdx.x == 0)
@@ -101,7 +113,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
 // [6,7] bound terms of the dual objective, [8,9] ||(x - x_last) / D_c||^2
 template <int LANES>
 __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
-  DevState* st = r.st;
+  const Span sp = make_span(r.tc, r.n, r.grid_c_short, r.t_long, r.t_nlong);
+  DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const double* __restrict__ val = r.t_val64;
@@ -130,8 +143,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
       acc[8 + k] += dd * dd;
     }
   };
-  rows_all<true, LANES, D2>(r.n, r.t_ptr, r.t_thresh, r.t_long, r.t_nlong, r.grid_c_short, load,
-                            epi);
+  rows_all<true, LANES, D2>(sp, r.t_ptr, r.t_thresh, load, epi);
   double out[10];
   block_sum<10>(acc, out);
   if (threadIdx.x == 0)
@@ -139,11 +151,20 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
-  DevState* st = r.st;
+  // one block per LP
+  const int k = blockIdx.x;
+  DevState* st = r.st + k;
   if (!st->check_due || st->status != 0) return;
+  int r0 = 0, rn = r.grid_r, c0 = 0, cn = r.grid_c;
+  if (r.tr.blk_lp != nullptr) {
+    r0 = r.tr.blk0[k];
+    rn = r.tr.nblk[k];
+    c0 = r.tc.blk0[k];
+    cn = r.tc.nblk[k];
+  }
   double pr[8], pc[10];
-  reduce_partials<8>(r.part_r, r.grid_r, r.grid_r, pr);
-  reduce_partials<10>(r.part_c, r.grid_c, r.grid_c, pc);
+  reduce_partials<8>(r.part_r + r0, r.grid_r, rn, pr);
+  reduce_partials<10>(r.part_c + c0, r.grid_c, cn, pc);
   if (threadIdx.x != 0) return;
   double relk[2], gap2[2];
   for (int k = 0; k < 2; ++k) {
@@ -227,7 +248,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
-  DevState* st = r.st;
+  const ESpan es = make_espan(r);
+  DevState* st = r.st + es.lp;
   if (!st->check_due || st->status != 0) return;
   const int kind = st->restart_kind;
   if (kind == 0) return;
@@ -241,8 +263,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
   if (threadIdx.x == 0) inv_sh = sw > 0.0 ? 1.0 / sw : 0.0;
   __syncthreads();
   const double isw = inv_sh;
-  const long long stride = (long long)gridDim.x * kBlock;
-  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+  const long long stride = (long long)es.nblk * kBlock;
+  for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
     if (kind == 2) {
       const double xc = (double)x[j].x;
       vec2_t<T> v;
@@ -255,7 +277,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
     }
     sx[j] = (T)0;
   }
-  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+  for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     if (kind == 2) {
       const double yc = (double)y[i];
       y[i] = (T)(sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc);
@@ -268,7 +290,9 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
 }
 
 __global__ void k_kkt_end(KktRaw r) {
-  DevState* st = r.st;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per LP
+  if (k >= r.count) return;
+  DevState* st = r.st + k;
   if (!st->check_due || st->status != 0) return;
   if (st->restart_kind != 0) {
     st->sum_w = 0.0;
@@ -282,16 +306,17 @@ __global__ void k_kkt_end(KktRaw r) {
 __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, double* y_out,
                                                    double* x_cur, double* y_cur, double* x_avg,
                                                    double* y_avg) {
-  const int ua = r.st->used_avg;
-  const long long stride = (long long)gridDim.x * kBlock;
-  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+  const ESpan es = make_espan(r);
+  const int ua = r.st[es.lp].used_avg;
+  const long long stride = (long long)es.nblk * kBlock;
+  for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
     const double l = r.l[j], u = r.u[j];
     const double xc = fmin(fmax(r.Xc[j], l), u), xa = fmin(fmax(r.Xa[j], l), u);
     if (x_out) x_out[j] = ua ? xa : xc;
     if (x_cur) x_cur[j] = xc;
     if (x_avg) x_avg[j] = xa;
   }
-  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+  for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double s = r.row_kind[i] == 2 ? -1.0 : 1.0;
     const double yc = s * r.Yc[i], ya = s * r.Ya[i];
     if (y_out) y_out[i] = ua ? ya : yc;
@@ -299,6 +324,9 @@ __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, doub
     if (y_avg) y_avg[i] = ya;
   }
 }
+
+// elementwise kernels: grid_e blocks for one LP, the A^T block map (grid_c) for a batch
+inline int egrid(const KktRaw& r) { return r.tc.blk_lp ? r.grid_c : r.grid_e; }
 
 template <int LANES>
 cudaError_t launch_rc(int which, const KktRaw& r, cudaStream_t s) {
@@ -325,20 +353,20 @@ cudaError_t launch_rc_lanes(int which, int lanes, const KktRaw& r, cudaStream_t 
 cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s) {
   switch (which) {
     case KK_PREP:
-      if (r.fp32) k_kkt_prep<float><<<r.grid_e, kBlock, 0, s>>>(r);
-      else k_kkt_prep<double><<<r.grid_e, kBlock, 0, s>>>(r);
+      if (r.fp32) k_kkt_prep<float><<<egrid(r), kBlock, 0, s>>>(r);
+      else k_kkt_prep<double><<<egrid(r), kBlock, 0, s>>>(r);
       return cudaGetLastError();
     case KK_ROWS: return launch_rc_lanes(KK_ROWS, lanes_r, r, s);
     case KK_COLS: return launch_rc_lanes(KK_COLS, lanes_c, r, s);
     case KK_FINAL:
-      k_kkt_final<<<1, kBlock, 0, s>>>(r);
+      k_kkt_final<<<r.count, kBlock, 0, s>>>(r);
       return cudaGetLastError();
     case KK_APPLY:
-      if (r.fp32) k_kkt_apply<float><<<r.grid_e, kBlock, 0, s>>>(r);
-      else k_kkt_apply<double><<<r.grid_e, kBlock, 0, s>>>(r);
+      if (r.fp32) k_kkt_apply<float><<<egrid(r), kBlock, 0, s>>>(r);
+      else k_kkt_apply<double><<<egrid(r), kBlock, 0, s>>>(r);
       return cudaGetLastError();
     case KK_END:
-      k_kkt_end<<<1, 1, 0, s>>>(r);
+      k_kkt_end<<<(r.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(r);
       return cudaGetLastError();
     default: return cudaErrorInvalidValue;
   }
@@ -346,7 +374,7 @@ cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cud
 
 cudaError_t launch_output(const KktRaw& r, double* x_out, double* y_out, double* x_cur,
                           double* y_cur, double* x_avg, double* y_avg, cudaStream_t s) {
-  k_output<<<r.grid_e, kBlock, 0, s>>>(r, x_out, y_out, x_cur, y_cur, x_avg, y_avg);
+  k_output<<<egrid(r), kBlock, 0, s>>>(r, x_out, y_out, x_cur, y_cur, x_avg, y_avg);
   return cudaGetLastError();
 }
 

@@ -765,6 +765,19 @@ cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, cons
   return cudaGetLastError();
 }
 
+__global__ void k_offset_copy(int* dst, const int* src, long long count, int offset) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    dst[i] = src[i] + offset;
+}
+
+cudaError_t setup_offset_copy(int* dst, const int* src, long long count, int offset,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_offset_copy<<<grid_for(count, device_sm_count() * 8), kBlock, 0, s>>>(dst, src, count, offset);
+  return cudaGetLastError();
+}
+
 cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, int* pos, int* bsum,
                             int* list, int* h_count, cudaStream_t s) {
   const int G = device_sm_count() * 8;

@@ -62,6 +62,9 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
                                const int* a_col, const double* a_val64, double* part,
                                double* scalars_out, cudaStream_t s);
 size_t scan_tmp_ints(long long N);
+// dst[i] = src[i] + offset (index arrays moved into a batch's global numbering)
+cudaError_t setup_offset_copy(int* dst, const int* src, long long count, int offset,
+                              cudaStream_t s);
 cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,
                           const double* u, double* inv_dr, double* inv_dc, unsigned char* bflags,
                           cudaStream_t s);

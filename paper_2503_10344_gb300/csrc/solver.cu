@@ -22,6 +22,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/pdlp.h"
 #include "setup.h"
@@ -244,6 +245,120 @@ struct TimingReq {
 static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
                                     const TimingReq& tq);
 
+// Products of the device setup of one LP (rows A0-A3) into the buffers of a Bufs.
+struct SetupOut {
+  Mode mode;
+  int scaled, fp32;
+  double sca[5];  // ||c~||, ||q~||, ||c||, ||q||, max |K~|
+  int lanes_a, lanes_t, lanes_ka, lanes_kt, th_a, th_t, nlong_a, nlong_t;
+};
+
+// Validation, canonical form, transpose, value format, scaling, iteration-space
+// data and long-row lists of one LP.  forced_mode >= 0 skips the value-format
+// choice; forced_lanes (A, A^T, KKT A, KKT A^T) overrides the lanes heuristic
+// (a batch shares one kernel instantiation).
+static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                    const double* l, const double* u, const pdlp_params* p, const double* x0,
+                    const double* y0, Bufs& bf, cudaStream_t s, bool no_alloc, int forced_mode,
+                    const int* forced_lanes, SetupOut* so) {
+  const int m = A->m, n = A->n;
+  const long long nnz = A->nnz;
+  // ---- validation (A0 preconditions)
+  SetupIn in{m, n, nnz, A->row_ptr, A->col, A->val, b, sense, c, l, u};
+  CUDA_TRY(setup_validate(in, bf.flags2, s));
+  g_launches += 3;
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, bf.flags2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) {
+    std::string msg = "invalid input:";
+    if (err & ERR_ROWPTR) msg += " row_ptr";
+    if (err & ERR_COL) msg += " column index";
+    if (err & ERR_NONFINITE) msg += " non-finite value";
+    if (err & ERR_SENSE) msg += " sense";
+    if (err & ERR_BOUNDS) msg += " bounds";
+    return fail(PDLP_ERR_INVALID_INPUT, msg);
+  }
+  // ---- A0, A1
+  CUDA_TRY(setup_canonical(in, bf.a_ptr, bf.a_col, bf.a_val64, bf.q64, bf.row_kind, s));
+  CUDA_TRY(setup_transpose(m, n, (int)nnz, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col,
+                           bf.t_val64, bf.tmp, s, no_alloc));
+  g_launches += 10;
+  // ---- mode
+  Mode mode = MODE_FP64;
+  int bf16_exact = 0, all_one = 0;
+  if (p->precision == PDLP_FP32) mode = MODE_FP32;
+  if (forced_mode >= 0) {
+    mode = (Mode)forced_mode;
+  } else if (p->precision == PDLP_FP32_BF16A) {
+    CUDA_TRY(setup_value_format(bf.a_val64, (int)nnz, bf.flags2, &bf16_exact, &all_one, s));
+    ++g_launches;
+    mode = all_one ? MODE_PAT : (bf16_exact ? MODE_BF16 : MODE_FP32);
+  }
+  const int scaled = (mode == MODE_FP64 || mode == MODE_FP32) ? 1 : 0;
+  const int fp32 = mode != MODE_FP64;
+  // ---- A2
+  ScaleIn sc{m, n, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col, bf.t_val64, p->ruiz_iters,
+             p->pc_alpha};
+  CUDA_TRY(setup_scaling(sc, bf.dr, bf.dc, bf.stat_r, bf.stat_c, s));
+  g_launches += 2 + 4 * p->ruiz_iters + (p->pc_alpha >= 0 ? 4 : 0);
+  CUDA_TRY(setup_kkt_aux(m, n, bf.dr, bf.dc, l, u, bf.inv_dr, bf.inv_dc, bf.bflags, s));
+  ++g_launches;
+  if (mode != MODE_PAT) {
+    const int vt = mode == MODE_FP64 ? 0 : (mode == MODE_FP32 ? 1 : 2);
+    CUDA_TRY(setup_iter_values(vt, bf.a_ptr, bf.a_col, bf.a_val64, m, bf.dr, bf.dc, 1, scaled,
+                               bf.a_valit, s));
+    CUDA_TRY(setup_iter_values(vt, bf.t_ptr, bf.t_col, bf.t_val64, n, bf.dc, bf.dr, 0, scaled,
+                               bf.t_valit, s));
+    g_launches += 2;
+  }
+  VecIn vi{m, n, bf.dr, bf.dc, c, l, u, bf.q64, bf.row_kind, x0, y0, scaled};
+  CUDA_TRY(setup_iter_vectors(vi, fp32, bf.c_it, bf.l_it, bf.u_it, bf.q_it, bf.tw, bf.sw, bf.x[0],
+                              bf.y[0], bf.a_ptr, bf.a_col, bf.a_val64, bf.part_setup, bf.scalars, s));
+  g_launches += 3;
+  double sca[5];
+  CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
+  // ---- launch shapes and long rows
+  const double avg_a = m ? (double)nnz / m : 1.0, avg_t = (double)nnz / n;
+  const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
+  int lanes_a = p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane);
+  int lanes_t = p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane);
+  int lanes_ka = p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0);
+  int lanes_kt = p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0);
+  if (forced_lanes) {
+    lanes_a = forced_lanes[0];
+    lanes_t = forced_lanes[1];
+    lanes_ka = forced_lanes[2];
+    lanes_kt = forced_lanes[3];
+  }
+  const int th_a = long_thresh(std::max(lanes_a, lanes_ka));
+  const int th_t = long_thresh(std::max(lanes_t, lanes_kt));
+  int nlong_a = 0, nlong_t = 0;
+  {
+    const size_t R = (size_t)std::max(m, n) + 1;
+    int* flags = bf.tmp;
+    int* pos = flags + R;
+    int* bsum = pos + R + 1;
+    if (m > 0) CUDA_TRY(setup_long_rows(bf.a_ptr, m, th_a, flags, pos, bsum, bf.a_long, &nlong_a, s));
+    CUDA_TRY(setup_long_rows(bf.t_ptr, n, th_t, flags, pos, bsum, bf.t_long, &nlong_t, s));
+    g_launches += 10;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));  // scalars
+  so->mode = mode;
+  so->scaled = scaled;
+  so->fp32 = fp32;
+  for (int k = 0; k < 5; ++k) so->sca[k] = sca[k];
+  so->lanes_a = lanes_a;
+  so->lanes_t = lanes_t;
+  so->lanes_ka = lanes_ka;
+  so->lanes_kt = lanes_kt;
+  so->th_a = th_a;
+  so->th_t = th_t;
+  so->nlong_a = nlong_a;
+  so->nlong_t = nlong_t;
+  return PDLP_OK;
+}
+
 static int solve_device(const pdlp_csr* A, const double* b, const char* sense, const double* c,
                         const double* l, const double* u, const pdlp_params* p, const double* x0,
                         const double* y0, double* x_out, double* y_out, pdlp_result* r,
@@ -293,78 +408,16 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   auto h0 = std::chrono::steady_clock::now(), h1 = h0, h2 = h0;
   if (!no_alloc) CUDA_TRY(cudaEventRecord(e0, s));
 
-  // ---- validation (A0 preconditions)
-  SetupIn in{m, n, nnz, A->row_ptr, A->col, A->val, b, sense, c, l, u};
-  CUDA_TRY(setup_validate(in, bf.flags2, s));
-  g_launches += 3;
-  int err = 0;
-  CUDA_TRY(cudaMemcpyAsync(&err, bf.flags2, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if (err) {
-    std::string msg = "invalid input:";
-    if (err & ERR_ROWPTR) msg += " row_ptr";
-    if (err & ERR_COL) msg += " column index";
-    if (err & ERR_NONFINITE) msg += " non-finite value";
-    if (err & ERR_SENSE) msg += " sense";
-    if (err & ERR_BOUNDS) msg += " bounds";
-    return fail(PDLP_ERR_INVALID_INPUT, msg);
-  }
-  // ---- A0, A1
-  CUDA_TRY(setup_canonical(in, bf.a_ptr, bf.a_col, bf.a_val64, bf.q64, bf.row_kind, s));
-  CUDA_TRY(setup_transpose(m, n, (int)nnz, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col,
-                           bf.t_val64, bf.tmp, s, no_alloc));
-  g_launches += 10;
-  // ---- mode
-  Mode mode = MODE_FP64;
-  int bf16_exact = 0, all_one = 0;
-  if (p->precision == PDLP_FP32) mode = MODE_FP32;
-  if (p->precision == PDLP_FP32_BF16A) {
-    CUDA_TRY(setup_value_format(bf.a_val64, (int)nnz, bf.flags2, &bf16_exact, &all_one, s));
-    ++g_launches;
-    mode = all_one ? MODE_PAT : (bf16_exact ? MODE_BF16 : MODE_FP32);
-  }
-  const int scaled = (mode == MODE_FP64 || mode == MODE_FP32) ? 1 : 0;
-  const int fp32 = mode != MODE_FP64;
-  // ---- A2
-  ScaleIn sc{m, n, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col, bf.t_val64, p->ruiz_iters,
-             p->pc_alpha};
-  CUDA_TRY(setup_scaling(sc, bf.dr, bf.dc, bf.stat_r, bf.stat_c, s));
-  g_launches += 2 + 4 * p->ruiz_iters + (p->pc_alpha >= 0 ? 4 : 0);
-  CUDA_TRY(setup_kkt_aux(m, n, bf.dr, bf.dc, l, u, bf.inv_dr, bf.inv_dc, bf.bflags, s));
-  ++g_launches;
-  if (mode != MODE_PAT) {
-    const int vt = mode == MODE_FP64 ? 0 : (mode == MODE_FP32 ? 1 : 2);
-    CUDA_TRY(setup_iter_values(vt, bf.a_ptr, bf.a_col, bf.a_val64, m, bf.dr, bf.dc, 1, scaled,
-                               bf.a_valit, s));
-    CUDA_TRY(setup_iter_values(vt, bf.t_ptr, bf.t_col, bf.t_val64, n, bf.dc, bf.dr, 0, scaled,
-                               bf.t_valit, s));
-    g_launches += 2;
-  }
-  VecIn vi{m, n, bf.dr, bf.dc, c, l, u, bf.q64, bf.row_kind, x0, y0, scaled};
-  CUDA_TRY(setup_iter_vectors(vi, fp32, bf.c_it, bf.l_it, bf.u_it, bf.q_it, bf.tw, bf.sw, bf.x[0],
-                              bf.y[0], bf.a_ptr, bf.a_col, bf.a_val64, bf.part_setup, bf.scalars, s));
-  g_launches += 3;
-  double sca[5];
-  CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
-  // ---- launch shapes and long rows
-  const double avg_a = m ? (double)nnz / m : 1.0, avg_t = (double)nnz / n;
-  const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
-  const int lanes_a = p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane);
-  const int lanes_t = p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane);
-  const int lanes_ka = p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0);
-  const int lanes_kt = p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0);
-  const int th_a = long_thresh(std::max(lanes_a, lanes_ka));
-  const int th_t = long_thresh(std::max(lanes_t, lanes_kt));
-  int nlong_a = 0, nlong_t = 0;
+  SetupOut so;
   {
-    const size_t R = (size_t)std::max(m, n) + 1;
-    int* flags = bf.tmp;
-    int* pos = flags + R;
-    int* bsum = pos + R + 1;
-    if (m > 0) CUDA_TRY(setup_long_rows(bf.a_ptr, m, th_a, flags, pos, bsum, bf.a_long, &nlong_a, s));
-    CUDA_TRY(setup_long_rows(bf.t_ptr, n, th_t, flags, pos, bsum, bf.t_long, &nlong_t, s));
-    g_launches += 10;
+    const int rc = setup_lp(A, b, sense, c, l, u, p, x0, y0, bf, s, no_alloc, -1, nullptr, &so);
+    if (rc) return rc;
   }
+  const Mode mode = so.mode;
+  const int scaled = so.scaled, fp32 = so.fp32;
+  const double* sca = so.sca;
+  const int lanes_a = so.lanes_a, lanes_t = so.lanes_t, lanes_ka = so.lanes_ka, lanes_kt = so.lanes_kt;
+  const int th_a = so.th_a, th_t = so.th_t, nlong_a = so.nlong_a, nlong_t = so.nlong_t;
   const int MB = max_blocks();
   // float32 step kernels: one group of lanes per row, rows grid-strided;
   // float64 kernels (float64 steps, KKT passes): warp tiles of 32 rows
@@ -383,7 +436,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   const int gr = gr_short + std::min(nlong_a, kMaxLongBlocks);
   const int gc = gc_short + std::min(nlong_t, kMaxLongBlocks);
 
-  IterRaw ir;
+  IterRaw ir{};  // batch tables stay NULL: one LP
   ir.a_ptr = bf.a_ptr; ir.a_col = bf.a_col; ir.a_val = mode == MODE_PAT ? nullptr : bf.a_valit;
   ir.t_ptr = bf.t_ptr; ir.t_col = bf.t_col; ir.t_val = mode == MODE_PAT ? nullptr : bf.t_valit;
   ir.a_long = bf.a_long; ir.t_long = bf.t_long;
@@ -398,7 +451,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   ir.grid_p_short = gp_short; ir.grid_p = gp; ir.grid_d_short = gd_short; ir.grid_d = gd;
   ir.st = bf.st;
 
-  KktRaw kr;
+  KktRaw kr{};
+  kr.count = 1;
   kr.a_ptr = bf.a_ptr; kr.a_col = bf.a_col; kr.a_val64 = bf.a_val64;
   kr.t_ptr = bf.t_ptr; kr.t_col = bf.t_col; kr.t_val64 = bf.t_val64;
   kr.a_long = bf.a_long; kr.t_long = bf.t_long;
@@ -735,6 +789,475 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   return PDLP_OK;
 }
 
+// ---------------------------------------------------------------- batches
+// Many LPs solved together: each LP is set up with setup_lp into a per-LP
+// scratch workspace, then exported into one block-diagonal problem (global row
+// and column numbering, global vectors).  The step and KKT kernels run over all
+// LPs in one launch each; every block belongs to one LP (launch tables) and
+// each LP keeps its own device state, step size, primal weight, restarts and
+// termination.  One graph holds check_period attempts plus the KKT block for
+// the whole batch.
+struct LpShape {
+  int m, n;
+  long long nnz;
+  long long R, C, Z;  // global first row, column, nonzero
+};
+
+// blocks of one LP in a launch map: proportional to its rows, at least one,
+// never more than its rows need
+static void build_map(const std::vector<LpShape>& sh, bool over_cols, int lanes, bool tiled,
+                      const std::vector<int>& nlong, const std::vector<int>& long0, long long total_rows,
+                      int budget, std::vector<int>& tab, int* grid) {
+  const int K = (int)sh.size();
+  std::vector<int> nshort(K), nblk(K), blk0(K), row0(K), nrows(K);
+  long long g = 0;
+  for (int k = 0; k < K; ++k) {
+    const long long rows = over_cols ? sh[k].n : sh[k].m;
+    const long long need = tiled ? (rows + 255) / 256 : (rows * lanes + kBlock - 1) / kBlock;
+    long long share = total_rows > 0 ? (long long)((double)budget * (double)rows / (double)total_rows) : 1;
+    share = std::max(1LL, std::min(share, std::max(1LL, need)));
+    nshort[k] = (int)share;
+    nblk[k] = nshort[k] + std::min(nlong[k], kMaxLongBlocks);
+    blk0[k] = (int)g;
+    g += nblk[k];
+    row0[k] = (int)(over_cols ? sh[k].C : sh[k].R);
+    nrows[k] = (int)rows;
+  }
+  *grid = (int)g;
+  tab.assign((size_t)g + 7 * (size_t)K, 0);
+  for (int k = 0; k < K; ++k)
+    for (int b = 0; b < nblk[k]; ++b) tab[blk0[k] + b] = k;
+  int* t = tab.data() + g;
+  for (int k = 0; k < K; ++k) {
+    t[0 * K + k] = blk0[k];
+    t[1 * K + k] = nshort[k];
+    t[2 * K + k] = nblk[k];
+    t[3 * K + k] = row0[k];
+    t[4 * K + k] = nrows[k];
+    t[5 * K + k] = long0[k];
+    t[6 * K + k] = nlong[k];
+  }
+}
+
+static Tables tables_at(int* dev, int grid, int K) {
+  Tables t;
+  t.blk_lp = dev;
+  t.blk0 = dev + grid;
+  t.nshort = dev + grid + K;
+  t.nblk = dev + grid + 2 * K;
+  t.row0 = dev + grid + 3 * K;
+  t.nrows = dev + grid + 4 * K;
+  t.long0 = dev + grid + 5 * K;
+  t.nlong = dev + grid + 6 * K;
+  return t;
+}
+
+static int solve_batch(int count, const pdlp_csr* const* A, const double* const* b,
+                       const char* const* sense, const double* const* c, const double* const* l,
+                       const double* const* u, const pdlp_params* p, double* const* x_out,
+                       double* const* y_out, pdlp_result* res) {
+  g_launches = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s;
+  CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct SFree {
+    cudaStream_t s;
+    ~SFree() { cudaStreamDestroy(s); }
+  } sfree{s};
+  // ---- shapes and global numbering
+  std::vector<LpShape> sh(count);
+  long long M = 0, N = 0, Z = 0;
+  int mmax = 0, nmax = 0;
+  long long zmax = 0;
+  for (int k = 0; k < count; ++k) {
+    sh[k] = {A[k]->m, A[k]->n, A[k]->nnz, M, N, Z};
+    M += A[k]->m;
+    N += A[k]->n;
+    Z += A[k]->nnz;
+    mmax = std::max(mmax, A[k]->m);
+    nmax = std::max(nmax, A[k]->n);
+    zmax = std::max(zmax, (long long)A[k]->nnz);
+  }
+  if (M >= INT32_MAX || N >= INT32_MAX || Z >= INT32_MAX)
+    return fail(PDLP_ERR_INVALID_INPUT, "a batch must have fewer than 2^31 rows, columns and nonzeros");
+  // ---- one mode and one set of lanes for the whole batch (one kernel instantiation)
+  int mode = p->precision == PDLP_FP64 ? MODE_FP64 : MODE_FP32;
+  if (p->precision == PDLP_FP32_BF16A) {
+    bool all_one = true, bf16 = true;
+    for (int k = 0; k < count; ++k)
+      for (int i = 0; i < A[k]->m; ++i) {
+        const double sg = sense[k][i] == 'L' ? -1.0 : 1.0;
+        for (int64_t q = A[k]->row_ptr[i]; q < A[k]->row_ptr[i + 1]; ++q) {
+          const double v = sg * A[k]->val[q];
+          all_one = all_one && v == 1.0;
+          const float f = (float)v;
+          uint32_t bits;
+          memcpy(&bits, &f, 4);
+          bf16 = bf16 && (double)f == v && (bits & 0xffffu) == 0;
+        }
+      }
+    mode = all_one ? MODE_PAT : (bf16 ? MODE_BF16 : MODE_FP32);
+  }
+  const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
+  const double avg_a = M ? (double)Z / (double)M : 1.0, avg_t = N ? (double)Z / (double)N : 1.0;
+  int lanes[4] = {p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane),
+                  p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane),
+                  p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0),
+                  p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0)};
+  // ---- per-LP scratch (inputs and a single-LP workspace, sized for the largest LP)
+  const size_t eb = mode == MODE_FP64 ? 8 : 4;
+  const size_t vb = mode == MODE_FP64 ? 8 : mode == MODE_FP32 ? 4 : mode == MODE_BF16 ? 2 : 0;
+  Bufs one;
+  Arena dry{nullptr, 0};
+  const size_t one_bytes = carve(dry, one, mmax, std::max(nmax, 1), zmax, p->precision);
+  const size_t in_bytes = 8 * ((size_t)mmax + 1) + 12 * (size_t)zmax + 9 * (size_t)mmax +
+                          24 * (size_t)nmax + 8 * 256;
+  // ---- global arrays
+  struct G {
+    int *a_ptr, *a_col, *t_ptr, *t_col, *a_long, *t_long, *tabA, *tabT;
+    double *a_val64, *t_val64, *q64, *dr, *dc, *inv_dr, *inv_dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl;
+    double *c64, *l64, *u64, *part_p, *part_d, *part_r, *part_c, *x_out, *y_out;
+    void *a_valit, *t_valit, *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
+    unsigned char *row_kind, *bflags;
+    DevState* st;
+    FacTable* fac;
+  } g{};
+  // long rows and launch maps need the per-LP setups first: upper bounds here
+  const int MB = max_blocks();
+  const int budget = 4 * MB;
+  const size_t gmax = (size_t)budget + (size_t)count * (kMaxLongBlocks + 2);
+  auto lay = [&](Arena& ar) {
+    g.fac = (FacTable*)ar.take(sizeof(FacTable));
+    g.a_ptr = (int*)ar.take(4 * (M + 1));
+    g.t_ptr = (int*)ar.take(4 * (N + 1));
+    g.a_col = (int*)ar.take(4 * Z);
+    g.t_col = (int*)ar.take(4 * Z);
+    g.a_val64 = (double*)ar.take(8 * Z);
+    g.t_val64 = (double*)ar.take(8 * Z);
+    g.a_valit = ar.take(vb * Z);
+    g.t_valit = ar.take(vb * Z);
+    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yc, &g.Ya, &g.Yl, &g.y_out}) *v = (double*)ar.take(8 * M);
+    for (double** v : {&g.dc, &g.inv_dc, &g.Xc, &g.Xa, &g.Xl, &g.c64, &g.l64, &g.u64, &g.x_out})
+      *v = (double*)ar.take(8 * N);
+    g.row_kind = (unsigned char*)ar.take(M);
+    g.bflags = (unsigned char*)ar.take(N);
+    for (void** v : {&g.c_it, &g.l_it, &g.u_it, &g.tw, &g.sum_x}) *v = ar.take(eb * N);
+    for (void** v : {&g.q_it, &g.sw, &g.sum_y}) *v = ar.take(eb * M);
+    for (int k = 0; k < 2; ++k) {
+      g.x[k] = ar.take(2 * eb * N);
+      g.y[k] = ar.take(eb * M);
+    }
+    g.part_p = (double*)ar.take(8 * gmax);
+    g.part_d = (double*)ar.take(8 * 2 * gmax);
+    g.part_r = (double*)ar.take(8 * 8 * gmax);
+    g.part_c = (double*)ar.take(8 * 10 * gmax);
+    g.a_long = (int*)ar.take(4 * (M + 1));
+    g.t_long = (int*)ar.take(4 * (N + 1));
+    g.tabA = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
+    g.tabT = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
+    g.st = (DevState*)ar.take(sizeof(DevState) * count);
+    one.fac = nullptr;
+  };
+  Arena gdry{nullptr, 0};
+  lay(gdry);
+  const size_t total = gdry.off + 256 + one_bytes + 256 + in_bytes + 256;
+  void* dev = nullptr;
+  {
+    cudaError_t e = cudaMallocAsync(&dev, total, s);
+    if (e != cudaSuccess) return fail(PDLP_ERR_OOM, std::string("batch buffers: ") + cudaGetErrorString(e));
+  }
+  struct DevFree {
+    void* p;
+    cudaStream_t s;
+    ~DevFree() {
+      cudaFreeAsync(p, s);
+      cudaStreamSynchronize(s);
+    }
+  } dfree{dev, s};
+  Arena gar{(char*)dev, 0};
+  lay(gar);
+  char* one_base = (char*)dev + ((gdry.off + 255) & ~(size_t)255) + 256;
+  one_base = (char*)(((uintptr_t)one_base + 255) & ~(uintptr_t)255);
+  Arena oar{one_base, 0};
+  carve(oar, one, mmax, std::max(nmax, 1), zmax, p->precision);
+  char* in_base = (char*)(((uintptr_t)(one_base + one_bytes) + 255) & ~(uintptr_t)255);
+  // ---- set up every LP and export it into the global numbering
+  std::vector<DevState> hs(count);
+  std::vector<int> nlong_a(count), nlong_t(count), long0_a(count), long0_t(count);
+  int th_a = 0, th_t = 0;
+  long long la_total = 0, lt_total = 0;
+  const FacTable& ft = fac_table();
+  CUDA_TRY(cudaMemcpyAsync(g.fac, &ft, sizeof(FacTable), cudaMemcpyHostToDevice, s));
+  for (int k = 0; k < count; ++k) {
+    const int m = sh[k].m, n = sh[k].n;
+    const long long z = sh[k].nnz;
+    Arena iar{in_base, 0};
+    int64_t* d_rp = (int64_t*)iar.take(8 * ((size_t)m + 1));
+    int32_t* d_col = (int32_t*)iar.take(4 * (size_t)z);
+    double* d_val = (double*)iar.take(8 * (size_t)z);
+    double* d_b = (double*)iar.take(8 * (size_t)m);
+    char* d_sense = (char*)iar.take((size_t)m);
+    double* d_c = (double*)iar.take(8 * (size_t)n);
+    double* d_l = (double*)iar.take(8 * (size_t)n);
+    double* d_u = (double*)iar.take(8 * (size_t)n);
+    CUDA_TRY(cudaMemcpyAsync(d_rp, A[k]->row_ptr, 8 * ((size_t)m + 1), cudaMemcpyHostToDevice, s));
+    if (z) {
+      CUDA_TRY(cudaMemcpyAsync(d_col, A[k]->col, 4 * (size_t)z, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(d_val, A[k]->val, 8 * (size_t)z, cudaMemcpyHostToDevice, s));
+    }
+    if (m) {
+      CUDA_TRY(cudaMemcpyAsync(d_b, b[k], 8 * (size_t)m, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(d_sense, sense[k], (size_t)m, cudaMemcpyHostToDevice, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_c, c[k], 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_l, l[k], 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_u, u[k], 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    pdlp_csr dA{m, n, z, d_rp, d_col, d_val};
+    SetupOut so;
+    {
+      const int rc = setup_lp(&dA, d_b, d_sense, d_c, d_l, d_u, p, nullptr, nullptr, one, s, false,
+                              mode, lanes, &so);
+      if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
+    }
+    th_a = so.th_a;
+    th_t = so.th_t;
+    const LpShape& q = sh[k];
+    // index arrays in the global numbering
+    CUDA_TRY(setup_offset_copy(g.a_ptr + q.R, one.a_ptr, m, (int)q.Z, s));
+    CUDA_TRY(setup_offset_copy(g.t_ptr + q.C, one.t_ptr, n, (int)q.Z, s));
+    CUDA_TRY(setup_offset_copy(g.a_col + q.Z, one.a_col, z, (int)q.C, s));
+    CUDA_TRY(setup_offset_copy(g.t_col + q.Z, one.t_col, z, (int)q.R, s));
+    nlong_a[k] = so.nlong_a;
+    nlong_t[k] = so.nlong_t;
+    long0_a[k] = (int)la_total;
+    long0_t[k] = (int)lt_total;
+    CUDA_TRY(setup_offset_copy(g.a_long + la_total, one.a_long, so.nlong_a, (int)q.R, s));
+    CUDA_TRY(setup_offset_copy(g.t_long + lt_total, one.t_long, so.nlong_t, (int)q.C, s));
+    la_total += so.nlong_a;
+    lt_total += so.nlong_t;
+    g_launches += 6;
+    auto d2d = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+    };
+    CUDA_TRY(d2d(g.a_val64 + q.Z, one.a_val64, 8 * (size_t)z));
+    CUDA_TRY(d2d(g.t_val64 + q.Z, one.t_val64, 8 * (size_t)z));
+    if (vb) {
+      CUDA_TRY(d2d((char*)g.a_valit + vb * q.Z, one.a_valit, vb * (size_t)z));
+      CUDA_TRY(d2d((char*)g.t_valit + vb * q.Z, one.t_valit, vb * (size_t)z));
+    }
+    CUDA_TRY(d2d(g.q64 + q.R, one.q64, 8 * (size_t)m));
+    CUDA_TRY(d2d(g.dr + q.R, one.dr, 8 * (size_t)m));
+    CUDA_TRY(d2d(g.inv_dr + q.R, one.inv_dr, 8 * (size_t)m));
+    CUDA_TRY(d2d(g.row_kind + q.R, one.row_kind, (size_t)m));
+    CUDA_TRY(d2d(g.dc + q.C, one.dc, 8 * (size_t)n));
+    CUDA_TRY(d2d(g.inv_dc + q.C, one.inv_dc, 8 * (size_t)n));
+    CUDA_TRY(d2d(g.bflags + q.C, one.bflags, (size_t)n));
+    CUDA_TRY(d2d(g.c64 + q.C, d_c, 8 * (size_t)n));
+    CUDA_TRY(d2d(g.l64 + q.C, d_l, 8 * (size_t)n));
+    CUDA_TRY(d2d(g.u64 + q.C, d_u, 8 * (size_t)n));
+    CUDA_TRY(d2d((char*)g.c_it + eb * q.C, one.c_it, eb * (size_t)n));
+    CUDA_TRY(d2d((char*)g.l_it + eb * q.C, one.l_it, eb * (size_t)n));
+    CUDA_TRY(d2d((char*)g.u_it + eb * q.C, one.u_it, eb * (size_t)n));
+    CUDA_TRY(d2d((char*)g.tw + eb * q.C, one.tw, eb * (size_t)n));
+    CUDA_TRY(d2d((char*)g.q_it + eb * q.R, one.q_it, eb * (size_t)m));
+    CUDA_TRY(d2d((char*)g.sw + eb * q.R, one.sw, eb * (size_t)m));
+    CUDA_TRY(d2d((char*)g.x[0] + 2 * eb * q.C, one.x[0], 2 * eb * (size_t)n));
+    CUDA_TRY(d2d((char*)g.y[0] + eb * q.R, one.y[0], eb * (size_t)m));
+    // device state of the LP (the A3 scalars of this LP)
+    DevState& h = hs[k];
+    memset(&h, 0, sizeof(h));
+    const double nct = so.sca[0], nqt = so.sca[1], kmax = so.sca[4];
+    h.omega = (nct > 1e-10 && nqt > 1e-10) ? nct / nqt : 1.0;
+    h.eta = kmax > 0.0 ? 1.0 / kmax : 1.0;
+    if (p->fixed_eta > 0.0) h.eta = p->fixed_eta;
+    if (p->fixed_omega > 0.0) h.omega = p->fixed_omega;
+    h.check_due = 1;
+    h.init_pending = 1;
+    h.prev_cand = INFINITY;
+    h.iter_limit = p->iter_limit;
+    h.period = p->check_period;
+    h.adaptive = p->adaptive_step ? 1 : 0;
+    h.restarts_on = p->restarts ? 1 : 0;
+    h.terminate = p->terminate ? 1 : 0;
+    h.tol = p->tol;
+    h.norm_c = so.sca[2];
+    h.norm_q = so.sca[3];
+    h.inv_omega = 1.0 / h.omega;
+    h.tau_d = h.eta / h.omega;
+    h.sigma_d = h.eta * h.omega;
+    h.eta_f = (float)h.eta;
+    h.omega_f = (float)h.omega;
+    h.inv_omega_f = (float)h.inv_omega;
+    h.tau_f = h.eta_f * h.inv_omega_f;
+    h.sigma_f = h.eta_f * h.omega_f;
+    h.fac_dec = g.fac->dec;
+    h.fac_inc = g.fac->inc;
+    h.fac_dec_f = g.fac->dec_f;
+    h.fac_inc_f = g.fac->inc_f;
+    h.fac_n = kFacN;
+    CUDA_TRY(cudaStreamSynchronize(s));  // the per-LP scratch is reused by the next LP
+  }
+  {
+    const int zi = (int)Z;
+    CUDA_TRY(cudaMemcpyAsync(g.a_ptr + M, &zi, sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g.t_ptr + N, &zi, sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(g.sum_x, 0, eb * N, s));
+    if (M) CUDA_TRY(cudaMemsetAsync(g.sum_y, 0, eb * M, s));
+    CUDA_TRY(cudaMemsetAsync(g.Xl, 0, 8 * N, s));
+    if (M) CUDA_TRY(cudaMemsetAsync(g.Yl, 0, 8 * M, s));
+    CUDA_TRY(cudaMemcpyAsync(g.st, hs.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  // ---- launch maps
+  const bool tiled = mode == MODE_FP64;
+  std::vector<int> tabA, tabT;
+  int gridA = 0, gridT = 0;
+  build_map(sh, false, lanes[0], tiled, nlong_a, long0_a, M, budget, tabA, &gridA);
+  build_map(sh, true, lanes[1], tiled, nlong_t, long0_t, N, budget, tabT, &gridT);
+  if ((size_t)gridA > gmax || (size_t)gridT > gmax) return fail(PDLP_ERR_OOM, "launch map too large");
+  CUDA_TRY(cudaMemcpyAsync(g.tabA, tabA.data(), 4 * tabA.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(g.tabT, tabT.data(), 4 * tabT.size(), cudaMemcpyHostToDevice, s));
+  const Tables tA = tables_at(g.tabA, gridA, count), tT = tables_at(g.tabT, gridT, count);
+  IterRaw ir{};
+  ir.a_ptr = g.a_ptr; ir.a_col = g.a_col; ir.a_val = mode == MODE_PAT ? nullptr : g.a_valit;
+  ir.t_ptr = g.t_ptr; ir.t_col = g.t_col; ir.t_val = mode == MODE_PAT ? nullptr : g.t_valit;
+  ir.a_long = g.a_long; ir.t_long = g.t_long;
+  ir.a_nlong = (int)la_total; ir.t_nlong = (int)lt_total; ir.a_thresh = th_a; ir.t_thresh = th_t;
+  ir.m = (int)M; ir.n = (int)N;
+  const int scaled = (mode == MODE_FP64 || mode == MODE_FP32) ? 1 : 0;
+  ir.c = g.c_it; ir.l = g.l_it; ir.u = g.u_it; ir.q = g.q_it;
+  ir.tw = scaled ? nullptr : g.tw; ir.sw = scaled ? nullptr : g.sw;
+  ir.row_kind = g.row_kind;
+  for (int k = 0; k < 2; ++k) { ir.x[k] = g.x[k]; ir.y[k] = g.y[k]; }
+  ir.sum_x = g.sum_x; ir.sum_y = g.sum_y;
+  ir.part_p = g.part_p; ir.part_d = g.part_d;
+  ir.grid_p_short = gridT; ir.grid_p = gridT; ir.grid_d_short = gridA; ir.grid_d = gridA;
+  ir.st = g.st;
+  ir.tp = tT;
+  ir.td = tA;
+  KktRaw kr{};
+  kr.a_ptr = g.a_ptr; kr.a_col = g.a_col; kr.a_val64 = g.a_val64;
+  kr.t_ptr = g.t_ptr; kr.t_col = g.t_col; kr.t_val64 = g.t_val64;
+  kr.a_long = g.a_long; kr.t_long = g.t_long;
+  kr.a_nlong = (int)la_total; kr.t_nlong = (int)lt_total; kr.a_thresh = th_a; kr.t_thresh = th_t;
+  kr.m = (int)M; kr.n = (int)N;
+  kr.c = g.c64; kr.l = g.l64; kr.u = g.u64; kr.q = g.q64; kr.dr = g.dr; kr.dc = g.dc;
+  kr.inv_dr = g.inv_dr; kr.inv_dc = g.inv_dc; kr.bflags = g.bflags;
+  kr.row_kind = g.row_kind;
+  for (int k = 0; k < 2; ++k) { kr.x[k] = g.x[k]; kr.y[k] = g.y[k]; }
+  kr.sum_x = g.sum_x; kr.sum_y = g.sum_y;
+  kr.Xc = g.Xc; kr.Xa = g.Xa; kr.Xl = g.Xl; kr.Yc = g.Yc; kr.Ya = g.Ya; kr.Yl = g.Yl;
+  kr.part_r = g.part_r; kr.part_c = g.part_c;
+  kr.grid_r_short = gridA; kr.grid_r = gridA; kr.grid_c_short = gridT; kr.grid_c = gridT;
+  kr.grid_e = gridT;
+  kr.scaled = scaled; kr.fp32 = mode != MODE_FP64;
+  kr.st = g.st;
+  kr.count = count;
+  kr.tr = tA;
+  kr.tc = tT;
+  Solve sv{(int)M, (int)N, Z, (Mode)mode, lanes[0], lanes[1], lanes[2], lanes[3], ir, kr, s};
+  CUDA_TRY(sv.kkt_block());  // initial KKT of every LP
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const double setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // ---- iteration phase: one graph of a check period for the whole batch
+  const auto t1 = std::chrono::steady_clock::now();
+  if (p->iter_limit > 0) {
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    Solve cap = sv;
+    cap.s = cs;
+    const long long before = g_launches;
+    cudaGraph_t graph;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int a = 0; a < p->check_period && ce == cudaSuccess; ++a) {
+      ce = cap.iter(IK_PRIMAL);
+      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
+    }
+    if (ce == cudaSuccess) ce = cap.kkt_block();
+    cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    CUDA_TRY(ee);
+    const long long nodes = g_launches - before;
+    g_launches = before;
+    cudaGraphExec_t ge;
+    cudaError_t ie = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(ie);
+    struct GFree {
+      cudaGraphExec_t g;
+      ~GFree() { cudaGraphExecDestroy(g); }
+    } gfree{ge};
+    DevState* hm = nullptr;
+    CUDA_TRY(cudaMallocHost(&hm, sizeof(DevState) * count));
+    struct HFree {
+      void* p;
+      ~HFree() { cudaFreeHost(p); }
+    } hfree{hm};
+    const long long max_launches = (p->iter_limit / p->check_period + 2) * 64 + 1024;
+    bool forced = false;
+    static const int one_flag[2] = {1, 1};
+    for (long long launch = 0;; ++launch) {
+      CUDA_TRY(cudaGraphLaunch(ge, s));
+      g_launches += nodes;
+      CUDA_TRY(cudaMemcpyAsync(hm, g.st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      int running = 0;
+      for (int k = 0; k < count; ++k) running += hm[k].status == 0;
+      if (!running) break;
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+      if (!forced && el > p->time_limit_s) {
+        for (int k = 0; k < count; ++k) {
+          CUDA_TRY(cudaMemcpyAsync(&g.st[k].force_final, &one_flag[0], sizeof(int), cudaMemcpyHostToDevice, s));
+          CUDA_TRY(cudaMemcpyAsync(&g.st[k].check_due, &one_flag[1], sizeof(int), cudaMemcpyHostToDevice, s));
+        }
+        forced = true;
+      }
+      if (launch > max_launches) return fail(PDLP_ERR_TIMEOUT, "batch iteration loop did not terminate");
+    }
+  }
+  const double solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+  // ---- outputs
+  CUDA_TRY(launch_output(kr, g.x_out, M ? g.y_out : nullptr, nullptr, nullptr, nullptr, nullptr, s));
+  ++g_launches;
+  std::vector<DevState> fs(count);
+  CUDA_TRY(cudaMemcpyAsync(fs.data(), g.st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+  for (int k = 0; k < count; ++k) {
+    if (x_out && x_out[k])
+      CUDA_TRY(cudaMemcpyAsync(x_out[k], g.x_out + sh[k].C, 8 * (size_t)sh[k].n, cudaMemcpyDeviceToHost, s));
+    if (y_out && y_out[k] && sh[k].m)
+      CUDA_TRY(cudaMemcpyAsync(y_out[k], g.y_out + sh[k].R, 8 * (size_t)sh[k].m, cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < count; ++k) {
+    pdlp_result& r = res[k];
+    memset(&r, 0, sizeof(r));
+    const DevState& f = fs[k];
+    r.status = p->iter_limit == 0 ? PDLP_ITER_LIMIT : f.status;
+    r.precision_used = mode == MODE_FP64 ? PDLP_FP64 : mode == MODE_FP32 ? PDLP_FP32
+                       : mode == MODE_BF16 ? PDLP_USED_BF16 : PDLP_USED_PATTERN;
+    r.iters = f.iters;
+    r.attempts = f.attempts;
+    r.restarts = f.restarts;
+    r.kkt_checks = f.checks;
+    const int a = f.used_avg ? 1 : 0;
+    r.used_average = a;
+    r.primal_obj = f.pobj[a];
+    r.dual_obj = f.dobj[a];
+    r.rel_primal_res = f.relp[a];
+    r.rel_dual_res = f.reld[a];
+    r.rel_gap = f.relgap[a];
+    r.rel_kkt = std::max(r.rel_primal_res, std::max(r.rel_dual_res, r.rel_gap));
+    r.eta = f.eta;
+    r.omega = f.omega;
+    r.setup_s = setup_s;
+    r.solve_s = solve_s;
+    r.kernel_launches = g_launches;
+  }
+  return PDLP_OK;
+}
+
 int set_error(int code, const char* msg) { return fail(code, msg); }
 
 // pdlp_solve_device on caller-provided scratch without creating any CUDA
@@ -927,6 +1450,27 @@ int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, con
   TimingReq tq{reps, ms_per_launch, bytes_per_launch};
   return solve_device(A, b, sense, c, l, u, p, nullptr, nullptr, nullptr, nullptr, &r, nullptr,
                       workspace, workspace_bytes, (cudaStream_t)stream, &tq);
+}
+
+int pdlp_solve_batch(int count, const pdlp_csr* const* A, const double* const* b,
+                     const char* const* sense, const double* const* c, const double* const* l,
+                     const double* const* u, const pdlp_params* p, double* const* x_out,
+                     double* const* y_out, pdlp_result* r) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  if (count < 1 || !A || !b || !sense || !c || !l || !u || !r)
+    return fail(PDLP_ERR_INVALID_INPUT, "batch: count >= 1 and every pointer array required");
+  for (int k = 0; k < count; ++k) {
+    double dummy = 0.0;
+    const int rc = check_inputs(A[k], b[k], sense[k], c[k], l[k], u[k], p,
+                                x_out ? (void*)x_out[k] : (void*)&dummy,
+                                (y_out && y_out[k]) ? (void*)y_out[k] : (void*)&dummy, &r[k]);
+    if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
+  }
+  return solve_batch(count, A, b, sense, c, l, u, p, x_out, y_out, r);
 }
 
 const char* pdlp_error_string(int code) {

@@ -1,0 +1,73 @@
+"""Batched solves (the north-star "batched" pattern): many uneven LPs in one set of
+launches, each with its own step size, restarts and termination."""
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import pdlp_oracle as O
+from oracle import reference_lp as R
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as G
+    G.build()
+    import paper_2503_10344_gb300 as P
+    return P
+
+
+def mixed_lps():
+    import test_gpu_pdlp as T
+    return [lpgen.mip_relaxation(1), lpgen.set_cover(7, m=2000, n=8000), lpgen.energy_system(hours=24),
+            lpgen.random_sparse_lp(11, 300, 500), T.skewed_lp(), lpgen.mip_relaxation(2, m=60, n=90)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_mixed_batch_reaches_tolerance(P, prec):
+    lps = mixed_lps()
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision=prec))
+    for lp, x, y, r in zip(lps, xs, ys, res):
+        assert r["status"] == P.PDLP_OPTIMAL, (lp.name, r)
+        k = O.kkt_original(lp, x, y)
+        assert k.rel_kkt <= 1.01e-4, (lp.name, k)
+        assert r["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
+        obj, _, _, _ = R.highs(lp)
+        assert abs(r["primal_obj"] - obj) / (1 + abs(obj)) <= 5e-4, lp.name
+    assert len({r["iters"] for r in res}) > 1  # the LPs stop independently
+
+
+@pytest.mark.parametrize("K", [1, 10, 60])
+def test_fp64_batch_matches_oracle_per_lp(P, K):
+    """Each LP of a float64 batch follows its own oracle run (the returned point, the
+    better of current and average at the last check, to 1e-9)."""
+    lps = mixed_lps()
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(iter_limit=K, terminate=0))
+    for lp, x, y, r in zip(lps, xs, ys, res):
+        ref = O.solve(lp, O.Params(iter_limit=K, terminate=False))
+        assert r["iters"] == ref.iters == K and r["attempts"] == ref.attempts
+        for got, want in ((x, ref.x), (y, ref.y)):
+            err = np.linalg.norm(got - want) / max(1.0, np.linalg.norm(want))
+            assert err <= 1e-9, (lp.name, err)
+
+
+def test_batch_of_fixed_cover_subproblems(P):
+    """Covering sub-LPs with 10-50 % of the columns fixed to 0/1 (as fix-and-propagate
+    leaves them), float32 iterates on the pattern matrix."""
+    lps = [lpgen.set_cover_fixed(4000 + k, int(m)) for k, m in
+           enumerate(np.random.default_rng(0).integers(2000, 6001, size=12))]
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="bf16"))
+    for lp, x, y, r in zip(lps, xs, ys, res):
+        assert r["status"] == P.PDLP_OPTIMAL and r["precision_used"] == 3
+        assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4
+        assert np.all(x >= lp.l) and np.all(x <= lp.u)
+
+
+def test_batch_rejects_an_invalid_member(P):
+    lps = mixed_lps()[:3]
+    bad = lpgen.mip_relaxation(5)
+    bad.l = bad.l.copy()
+    bad.l[0] = 2.0  # l > u
+    with pytest.raises(P.PdlpError, match="LP 3"):
+        P.pdlp_solve_batch(lps + [bad])
