@@ -26,6 +26,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -46,6 +48,10 @@ def parse():
     ap.add_argument("--kernels-only", action="store_true",
                     help="only time the fused kernels (pdlp_time_kernels) and print them")
     ap.add_argument("--reps", type=int, default=200)
+    ap.add_argument("--workload", default="set_cover", choices=["set_cover", "batch"],
+                    help="batch: 256 uneven covering sub-LPs (m in [2000, 40000], n = 4m, "
+                         "10-50 %% of the columns fixed), solved together by pdlp_solve_batch")
+    ap.add_argument("--batch-count", type=int, default=256)
     for k in ("lanes-a", "lanes-at", "lanes-kkt-a", "lanes-kkt-at"):
         ap.add_argument("--" + k, type=int, default=0, help="SpMV lanes per row (0 = automatic)")
     return ap.parse_args()
@@ -318,9 +324,53 @@ def run_kernels_only(args):
                           "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9} for k, v in kt.items()}))
 
 
+def run_batch(args):
+    """All LPs of the batch to rel. KKT 1e-4 in one pdlp_solve_batch call (host buffers:
+    the call uploads, sets up, solves and downloads; setup and solve are timed apart)."""
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    lps = lpgen.set_cover_batch(args.batch_count)
+    prm = P.default_params(tol=1e-4, precision=args.precision, **lane_params(args))
+    for _ in range(args.warmup):
+        P.pdlp_solve_batch(lps, prm, want_y=False)
+    times, setup, solve, iters, launches = [], [], [], [], 0
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, res = P.pdlp_solve_batch(lps, prm, want_y=False)
+            times.append(time.perf_counter() - t0)
+            setup.append(res[0]["setup_s"])
+            solve.append(res[0]["solve_s"])
+            iters.append(sum(r["iters"] for r in res))
+            launches += res[0]["kernel_launches"]
+    ok = sum(r["status"] == P.PDLP_OPTIMAL for r in res)
+    it = np.array([r["iters"] for r in res])
+    line = {"metric": METRIC, "value": sum(iters) / sum(solve), "unit": UNIT + " (sum over the batch)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {len(lps)} set-cover sub-LPs, sum m={sum(l.m for l in lps)}, "
+                                   f"sum n={sum(l.n for l in lps)}, nnz={sum(l.nnz for l in lps)}, tol=1e-4",
+                       "precision": args.precision},
+            "solve_s": sum(solve) / args.steps, "setup_s": sum(setup) / args.steps,
+            "lps_per_s": len(lps) / (sum(solve) / args.steps), "optimal": ok,
+            "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.kernels_only:
+    if a.workload == "batch" and a.impl == "gpu":
+        run_batch(a)
+    elif a.kernels_only:
         run_kernels_only(a)
     elif a.impl == "reference":
         run_reference(a)
