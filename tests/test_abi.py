@@ -34,6 +34,7 @@ def lib():
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert "pdlp_solve" in names and "pdlp_solve_device" in names
+    assert "gnn_train" in names and "pdlp_solve_warm" in names
     for n in names:
         assert hasattr(lib, n), n
 
@@ -41,10 +42,14 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_the_header(tmp_path):
     """Compile a C program against the header and compare sizeof/offsetof with ctypes."""
     import paper_2503_10344_gb300.binding as B
+    import paper_2503_10344_gb300.gnn as N
     prog = tmp_path / "sz.c"
     fields = {"pdlp_params": B.PdlpParams, "pdlp_result": B.PdlpResult, "pdlp_csr": B.PdlpCsr,
-              "pdlp_diagnostics": B.PdlpDiagnostics}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdlp.h"', "int main(void){"]
+              "pdlp_diagnostics": B.PdlpDiagnostics, "fp_params": B.FpParams,
+              "fp_result": B.FpResult, "gnn_adam": N.GnnAdam, "gnn_train_params": N.GnnTrainParams,
+              "gnn_warm_info": N.GnnWarmInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdlp.h"', '#include "gnn.h"',
+             "int main(void){"]
     for s, cls in fields.items():
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
         for f, _ in cls._fields_:
