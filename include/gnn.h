@@ -152,9 +152,12 @@ typedef struct {
 } gnn_warm_info;
 
 /* pdlp_solve with a learned start: builds the LP's graph, predicts (x0, y0),
- * projects it, compares its relative KKT with the cold start's and runs
- * pdlp_solve from the better (ties: cold).  Arguments as in pdlp_solve;
- * info (may be NULL) reports the decision.  model NULL = cold start. */
+ * projects it, compares its relative KKT with the cold start's and runs PDLP
+ * from the better point (ties: cold).  The initial primal weight comes from the
+ * projected prediction in either case, as in pdlp_solve_hinted (the ratio of
+ * its scaled dual and primal norms, the balance the weight stands for), unless
+ * p->fixed_omega > 0.  Arguments as in pdlp_solve; info (may be NULL) reports
+ * the decision.  model NULL = plain cold pdlp_solve. */
 int pdlp_solve_warm(gnn_model* model, const pdlp_csr* A, const double* b, const char* sense,
                     const double* c, const double* l, const double* u, const pdlp_params* p,
                     double* x_out, double* y_out, pdlp_result* r, gnn_warm_info* info);

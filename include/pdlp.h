@@ -113,6 +113,15 @@ typedef struct {
   int lanes_kkt_A;      /* lanes per row of A in the float64 KKT pass (0 = automatic) */
   int lanes_kkt_AT;     /* lanes per row of A^T in the float64 KKT pass (0 = automatic) */
   int verbose;          /* 0 quiet; 1 one line per KKT check on stderr */
+  int persistent;       /* 1: the step attempts of a check period run in one cooperative
+                           kernel with grid-wide barriers; 0 (default): two kernel launches
+                           per attempt.  Same iteration either way; batches always use the
+                           two-launch form. */
+  int autotune;         /* 1: before iterating, time the step kernels with 2, 4, 8, 16 and
+                           32 lanes per row (each kernel separately, on this LP, without
+                           moving the iterate) and keep the fastest; cached per (device,
+                           precision mode, m, n, nnz) for the process.  Lanes set explicitly
+                           in lanes_A / lanes_AT are kept.  0 (default): size heuristic. */
 } pdlp_params;
 
 typedef struct {
@@ -129,6 +138,7 @@ typedef struct {
   int used_average;       /* 1 if the returned point is the weighted average iterate */
   double setup_s;         /* device setup: canonical form, transpose, scaling */
   double solve_s;         /* iteration phase, from the first step to termination */
+  int lanes_A, lanes_AT;  /* lanes per row the step kernels used over A and A^T */
 } pdlp_result;
 
 /* Optional diagnostic outputs (same memory space as the entry point's outputs;
@@ -177,6 +187,25 @@ int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const doub
                const double* y0, double* x_out, double* y_out, pdlp_result* r,
                const pdlp_diagnostics* diag);
 
+/* pdlp_solve whose initial primal weight comes from a hint instead of the
+ * default estimate ||c~|| / ||q~|| (step A3):
+ *     omega0 = ||y~_h||_2 / ||x~_h||_2,
+ * the norms of the hint (x_hint[n], y_hint[m], caller's convention) after the
+ * same projection and scaling a start point gets (x~ = proj(x / D_c) onto the
+ * scaled bounds, y~ = proj_Y(S y / D_r)).  The primal weight balances the
+ * primal and dual distances the method has to travel; when an estimate of the
+ * solution is at hand, its norms give that balance (the ratio the weight
+ * updates of step A10 move toward).  Used when both norms exceed 1e-10, else
+ * the default; pdlp_params.fixed_omega > 0 still overrides.  The hint is
+ * independent of the start (x0, y0), which may be NULL.  No counterpart in the
+ * paper (which runs PDLP cold); the learned warm start (gnn.h) passes its
+ * prediction here.  Returns as pdlp_solve; INVALID_INPUT if a hint is NULL. */
+int pdlp_solve_hinted(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, const double* x_hint, const double* y_hint,
+                      double* x_out, double* y_out, pdlp_result* r,
+                      const pdlp_diagnostics* diag);
+
 /* Solve `count` LPs of uneven size together (north-star pattern "batched":
  * relaxations such as those left after the partial fixings of the heuristic).
  * Arrays of per-LP HOST pointers in the layout of pdlp_solve; one parameter
@@ -222,11 +251,14 @@ int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, con
 /* Kernel timing for roofline reports (a profiling aid; not needed to solve).
  * Runs the same device setup as pdlp_solve_device on the same DEVICE inputs,
  * then launches each fused kernel `reps` times back to back from a CUDA graph
- * (step attempts stay live: no KKT check falls due) and writes, for
+ * (step attempts stay live: no KKT check falls due) and writes into
+ * ms_per_launch[6] and bytes_per_launch[6], for
  *   [0] the primal step kernel (A^T SpMV + projected update),
  *   [1] the dual step kernel (A SpMV + extrapolated update + step decision),
  *   [2] one whole attempt ([0] then [1]),
  *   [3] the float64 KKT pass over A, [4] the float64 KKT pass over A^T,
+ *   [5] one attempt inside the persistent step kernel (reps attempts in one
+ *       launch; 0 when p->persistent is 0),
  * the average device time per launch in ms (graph launch gaps included) and
  * the algorithmic bytes per launch (every array the kernel needs, each element
  * once, gathered vectors counted once).  Workspace and stream as in

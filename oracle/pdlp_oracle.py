@@ -20,7 +20,10 @@ are listed one by one in the design notes and marked "reading" here:
   A2  Ruiz equilibration (10 passes, inf-norm) then Pock-Chambolle (alpha = 1)
       diagonal scaling, K~ = D_r K D_c.
   A3  x0 = proj_[l~,u~](0), y0 = 0, omega0 = ||c~|| / ||q~|| (if both > 1e-10,
-      else 1), eta0 = 1 / max|K~_ij|.
+      else 1), eta0 = 1 / max|K~_ij|.  With a primal-weight hint (x_h, y_h),
+      omega0 = ||y~_h|| / ||x~_h|| of the hint projected and scaled like a
+      start (if both > 1e-10) -- an addition for the learned warm start, not
+      part of the paper's cold PDLP.
   A4/A5  PDHG step  x' = proj_X(x - (eta/omega)(c~ - K~^T y)),
                     y' = proj_Y(y + eta*omega (q~ - K~ (2x' - x))).
   A6  adaptive step size: eta_bar = (omega ||dx||^2 + ||dy||^2/omega)
@@ -192,6 +195,7 @@ class Params:
     beta_nec: float = 0.8
     beta_art: float = 0.36
     omega_smooth: float = 0.5
+    omega_hint: object = None       # (x_h, y_h) caller convention: omega0 from their scaled norms
     # replay: step size and accept flag of every attempt taken from another run's
     # decision trace (eta_bar and all restart decisions are still computed here)
     replay_eta: object = None
@@ -245,6 +249,12 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
         y = proj_dual(s * np.asarray(y0, dtype=np.float64) / dr, is_eq)
     nc, nq = float(np.linalg.norm(ct)), float(np.linalg.norm(qt))
     omega = nc / nq if (nc > 1e-10 and nq > 1e-10) else 1.0
+    if p.omega_hint is not None:
+        xh = proj_box(np.asarray(p.omega_hint[0], dtype=np.float64) / dc, lt, ut)
+        yh = proj_dual(s * np.asarray(p.omega_hint[1], dtype=np.float64) / dr, is_eq)
+        nxh, nyh = float(np.linalg.norm(xh)), float(np.linalg.norm(yh))
+        if nxh > 1e-10 and nyh > 1e-10:
+            omega = nyh / nxh
     kmax = float(abs(kt).max()) if kt.nnz else 0.0
     eta = 1.0 / kmax if kmax > 0 else 1.0
     if p.fixed_eta is not None:

@@ -38,7 +38,8 @@ class PdlpParams(C.Structure):
                 ("ruiz_iters", C.c_int), ("pc_alpha", C.c_double), ("adaptive_step", C.c_int),
                 ("restarts", C.c_int), ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("terminate", C.c_int), ("lanes_A", C.c_int), ("lanes_AT", C.c_int),
-                ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int)]
+                ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int),
+                ("persistent", C.c_int), ("autotune", C.c_int)]
 
 
 class PdlpResult(C.Structure):
@@ -48,7 +49,8 @@ class PdlpResult(C.Structure):
                 ("dual_obj", C.c_double), ("rel_primal_res", C.c_double),
                 ("rel_dual_res", C.c_double), ("rel_gap", C.c_double), ("rel_kkt", C.c_double),
                 ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
-                ("setup_s", C.c_double), ("solve_s", C.c_double)]
+                ("setup_s", C.c_double), ("solve_s", C.c_double), ("lanes_A", C.c_int),
+                ("lanes_AT", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +83,9 @@ def lib():
         common = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + [C.POINTER(PdlpParams)] + \
             [C.c_void_p] * 4 + [C.POINTER(PdlpResult), C.POINTER(PdlpDiagnostics)]
         L.pdlp_solve.argtypes = common
+        L.pdlp_solve_hinted.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + \
+            [C.POINTER(PdlpParams)] + [C.c_void_p] * 6 + [C.POINTER(PdlpResult),
+                                                         C.POINTER(PdlpDiagnostics)]
         L.pdlp_solve_device.argtypes = common + [C.c_void_p, C.c_size_t, C.c_void_p]
         L.pdlp_solve_device_noalloc.argtypes = common + [C.c_void_p]
         L.pdlp_time_kernels.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + \
@@ -119,12 +124,14 @@ DIAG_ITERATES = ("x_cur", "y_cur", "x_avg", "y_avg")
 
 
 def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates: bool = False,
-               trace: int = 0):
+               trace: int = 0, omega_hint=None):
     """Solve ``lp`` (an :class:`lpgen.LP`-like object) from host memory.
 
     Returns (x, y, result dict) or, with ``iterates`` or ``trace`` > 0,
     (x, y, result dict, diagnostics dict); ``trace`` is the capacity of the
     per-attempt decision trace (the per-check trace gets trace // 16 + 16).
+    ``omega_hint`` = (x_h, y_h) calls pdlp_solve_hinted: the initial primal weight
+    is the ratio of the hint's scaled norms.
     """
     p = params or default_params()
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
@@ -150,9 +157,15 @@ def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates:
         dgp = PdlpDiagnostics(*[_ptr(diag[k]) for k in DIAG_ITERATES], trace, _ptr(diag["eta"]),
                               _ptr(diag["eta_bar"]), _ptr(diag["accepted"]), tc,
                               _ptr(diag["restart"]), _ptr(diag["omega"]))
-    rc = lib().pdlp_solve(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u),
-                          C.byref(p), _ptr(x0a), _ptr(y0a), _ptr(x), _ptr(y), C.byref(res),
-                          C.byref(dgp) if dgp is not None else None)
+    if omega_hint is None:
+        rc = lib().pdlp_solve(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u),
+                              C.byref(p), _ptr(x0a), _ptr(y0a), _ptr(x), _ptr(y), C.byref(res),
+                              C.byref(dgp) if dgp is not None else None)
+    else:
+        xh, yh = f64(omega_hint[0]), f64(omega_hint[1])
+        rc = lib().pdlp_solve_hinted(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u),
+                                     C.byref(p), _ptr(x0a), _ptr(y0a), _ptr(xh), _ptr(yh), _ptr(x),
+                                     _ptr(y), C.byref(res), C.byref(dgp) if dgp is not None else None)
     _check(rc)
     out = res.as_dict()
     if diag is None:
@@ -229,7 +242,7 @@ def pdlp_solve_device(dlp: DeviceLP, params: PdlpParams | None = None, x0=None, 
     return x_out, y_out[: dlp.m], res.as_dict()
 
 
-KERNELS = ("primal_step", "dual_step", "attempt", "kkt_rows", "kkt_cols")
+KERNELS = ("primal_step", "dual_step", "attempt", "kkt_rows", "kkt_cols", "persistent_attempt")
 
 
 def time_kernels(dlp: DeviceLP, params: PdlpParams | None = None, reps: int = 200,
@@ -245,8 +258,8 @@ def time_kernels(dlp: DeviceLP, params: PdlpParams | None = None, reps: int = 20
     aligned = (base + 255) & ~255
     if stream is None:
         stream = torch.cuda.current_stream(dev)
-    ms = np.zeros(5)
-    by = np.zeros(5)
+    ms = np.zeros(len(KERNELS))
+    by = np.zeros(len(KERNELS))
     csr = PdlpCsr(dlp.m, dlp.n, dlp.nnz, dlp.row_ptr.data_ptr(), dlp.col.data_ptr(),
                   dlp.val.data_ptr())
     dp = lambda t_: C.c_void_p(t_.data_ptr())

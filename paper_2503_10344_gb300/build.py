@@ -34,7 +34,7 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        [os.path.join(ROOT, "include", "pdlp.h"), __file__]
+        glob.glob(os.path.join(ROOT, "include", "*.h")) + [__file__]
 
 
 def up_to_date() -> bool:

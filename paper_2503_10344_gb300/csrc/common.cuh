@@ -55,6 +55,7 @@ struct DevState {
   int init_pending;      // the first KKT block only records the "last restart" data
   int used_avg;          // output candidate of the last check
   int force_final;       // host asked for a final check (time limit)
+  int dry;               // 1: step kernels run but the decision is skipped (launch-shape tuning)
   unsigned int counter;  // last-block counter of the dual-step kernel
   long long last_restart_it;
   double last_rp2, last_rd2, last_gap2;  // scaled KKT triple of the last restart point
@@ -86,7 +87,13 @@ struct DevState {
   signed char* tr_restart;
   double* tr_omega;
   long long tr_check_cap;
+  // grid barrier of the persistent step kernel (arrivals, generation, failure flag)
+  unsigned int bar_count, bar_gen;
+  int bar_err;
 };
+
+// status value of a persistent step kernel whose bounded barrier wait gave up
+constexpr int kStatusWaitFailed = 5;
 
 // ---------------------------------------------------------------- batches
 // Launch tables of a batch of LPs solved together (all NULL for one LP): the
@@ -140,6 +147,22 @@ __device__ __forceinline__ Span make_span(const Tables& t, int nrows1, int nshor
     s.nlist = t.nlong[k];
   }
   return s;
+}
+
+// ---------------------------------------------------------------- dependent launch
+// Programmatic dependent launch: kernels of the iteration chain are launched
+// with the programmatic-serialization attribute, so the next kernel's blocks
+// are scheduled while this one drains.  Every such kernel waits for its
+// predecessor grid (completion and memory flush) before it reads anything,
+// then lets its own dependents launch.  Launched without the attribute, both
+// instructions return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_launch_dependents();
 }
 
 // ---------------------------------------------------------------- reductions

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/gnn.h"
+#include "internal.h"
 #include "setup.h"
 
 namespace pdlp {
@@ -1456,7 +1457,7 @@ int gnn_graph_features(const gnn_graph* g, float* fv, float* fc) {
 
 int gnn_graph_free(gnn_graph* g) {
   if (!g) return PDLP_OK;
-  if (g->owner && g->owner->s) cudaStreamSynchronize(g->owner->s);
+  // cudaFree waits for the device; the owner is not touched (it may be gone)
   g->d.release();
   void* ps[] = {g->inv_deg_r, g->inv_deg_c, g->fv, g->fc, g->x_star, g->y_star};
   for (void* p : ps)
@@ -1649,10 +1650,12 @@ int pdlp_solve_warm(gnn_model* md, const pdlp_csr* A, const double* b, const cha
   const double predict_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const bool warm = rc == PDLP_OK && hk[3] < hk[7];
   if (rc == PDLP_OK) {
+    // the start point is the judged one; the primal weight always comes from the
+    // projected prediction's norms (pdlp_solve_hinted)
     pdlp_csr Ad{m, n, (int64_t)g->d.nnz, g->d.ptr64, g->d.a_col, g->d.a_val};
-    rc = pdlp_solve_device(&Ad, g->d.b, g->d.sense, g->d.c, g->d.l, g->d.u, p,
-                           warm ? md->xpred : nullptr, warm ? md->ypred : nullptr, xo, yo, r,
-                           nullptr, nullptr, 0, (void*)s);
+    rc = pdlp::solve_device_hint(&Ad, g->d.b, g->d.sense, g->d.c, g->d.l, g->d.u, p,
+                                 warm ? md->xpred : nullptr, warm ? md->ypred : nullptr,
+                                 md->xpred, md->ypred, xo, yo, r, s);
   }
   if (rc == PDLP_OK) {
     if (n > 0) e = cudaMemcpyAsync(x_out, xo, sizeof(double) * n, cudaMemcpyDeviceToHost, s);

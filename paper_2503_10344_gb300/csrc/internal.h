@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "../../include/pdlp.h"
 
 namespace pdlp {
 
@@ -24,12 +25,23 @@ struct IterRaw {
   const unsigned char* row_kind;
   void *x[2], *y[2], *sum_x, *sum_y;  // x: interleaved (x_j, dx_j) pairs
   double *part_p, *part_d;
+  unsigned* cnt;  // [count][32][8] zeroed group counters of the dual kernel
   int grid_p_short, grid_p, grid_d_short, grid_d;
   DevState* st;  // [count]
   Tables tp, td; // batch tables over A^T and A (all NULL for one LP)
 };
 
 enum IterKernel { IK_PRIMAL = 0, IK_DUAL = 1 };
+
+// persistent attempts kernel (one LP; see iter_kernels.cuh): grid 0 = resident maximum
+cudaError_t launch_persist_fp64(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
+                                int grid, int* grid_out, cudaStream_t s);
+cudaError_t launch_persist_fp32(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
+                                int grid, int* grid_out, cudaStream_t s);
+cudaError_t launch_persist_bf16(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
+                                int grid, int* grid_out, cudaStream_t s);
+cudaError_t launch_persist_pat(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
+                               int grid, int* grid_out, cudaStream_t s);
 
 cudaError_t launch_iter_fp64(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_t s);
@@ -67,7 +79,32 @@ cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cud
 cudaError_t launch_output(const KktRaw& r, double* x_out, double* y_out, double* x_cur,
                           double* y_cur, double* x_avg, double* y_avg, cudaStream_t s);
 
+// pdlp_solve_device (device buffers, stream order) whose initial primal weight is
+// ||y~_h|| / ||x~_h|| of the hint (hx, hy), projected and scaled like a start
+int solve_device_hint(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, const double* hx, const double* hy, double* x_out,
+                      double* y_out, pdlp_result* r, cudaStream_t s);
+
 int grid_for(long long work_items, int max_blocks);
+
+// Launch of a kernel of the iteration chain with programmatic dependent launch
+// (the kernel calls pdl_enter() first).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
 int device_sm_count();
 
 }  // namespace pdlp

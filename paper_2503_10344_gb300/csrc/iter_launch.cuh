@@ -2,6 +2,8 @@
 // pair; each iter_*.cu translation unit instantiates one pair.
 #pragma once
 
+#include <algorithm>
+
 #include "internal.h"
 #include "iter_kernels.cuh"
 
@@ -23,6 +25,7 @@ IterData<T, V> typed(const IterRaw& r) {
   }
   d.sum_x = (T*)r.sum_x; d.sum_y = (T*)r.sum_y;
   d.part_p = (T*)r.part_p; d.part_d = (T*)r.part_d;
+  d.cnt = r.cnt;
   d.grid_p_short = r.grid_p_short; d.grid_p = r.grid_p;
   d.grid_d_short = r.grid_d_short; d.grid_d = r.grid_d;
   d.st = r.st;
@@ -34,11 +37,10 @@ IterData<T, V> typed(const IterRaw& r) {
 template <int LANES, typename T, typename V, bool IMPLICIT>
 cudaError_t launch_one(int which, const IterData<T, V>& d, cudaStream_t s) {
   switch (which) {
-    case IK_PRIMAL: k_primal<LANES, T, V, IMPLICIT><<<d.grid_p, kBlock, 0, s>>>(d); break;
-    case IK_DUAL: k_dual<LANES, T, V, IMPLICIT><<<d.grid_d, kBlock, 0, s>>>(d); break;
+    case IK_PRIMAL: return launch_pdl(k_primal<LANES, T, V, IMPLICIT>, d.grid_p, kBlock, s, d);
+    case IK_DUAL: return launch_pdl(k_dual<LANES, T, V, IMPLICIT>, d.grid_d, kBlock, s, d);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <typename T, typename V, bool IMPLICIT>
@@ -50,6 +52,61 @@ cudaError_t launch_iter_t(int which, int lanes, const IterRaw& r, cudaStream_t s
     case 8: return launch_one<8, T, V, IMPLICIT>(which, d, s);
     case 16: return launch_one<16, T, V, IMPLICIT>(which, d, s);
     case 32: return launch_one<32, T, V, IMPLICIT>(which, d, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Persistent attempts kernel (k_persist) of the lanes pair (LA over A, LT over
+// A^T): one cooperative launch of `grid` blocks (0 = as many as can be resident,
+// at most four per SM); *grid_out receives the grid used.
+template <int LA, int LT, typename T, typename V, bool IMPLICIT>
+cudaError_t launch_persist_one(const IterData<T, V>& d, int max_attempts, int grid,
+                               int* grid_out, cudaStream_t s) {
+  auto kern = k_persist<LA, LT, T, V, IMPLICIT>;
+  if (grid <= 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    grid = std::min(per_sm, 4) * device_sm_count();
+  }
+  if (grid_out) *grid_out = grid;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, d, max_attempts);
+}
+
+template <int LA, typename T, typename V, bool IMPLICIT>
+cudaError_t launch_persist_la(int lanes_t, const IterData<T, V>& d, int max_attempts, int grid,
+                              int* grid_out, cudaStream_t s) {
+  switch (lanes_t) {
+    case 2: return launch_persist_one<LA, 2, T, V, IMPLICIT>(d, max_attempts, grid, grid_out, s);
+    case 4: return launch_persist_one<LA, 4, T, V, IMPLICIT>(d, max_attempts, grid, grid_out, s);
+    case 8: return launch_persist_one<LA, 8, T, V, IMPLICIT>(d, max_attempts, grid, grid_out, s);
+    case 16: return launch_persist_one<LA, 16, T, V, IMPLICIT>(d, max_attempts, grid, grid_out, s);
+    case 32: return launch_persist_one<LA, 32, T, V, IMPLICIT>(d, max_attempts, grid, grid_out, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, typename V, bool IMPLICIT>
+cudaError_t launch_persist_t(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
+                             int grid, int* grid_out, cudaStream_t s) {
+  const IterData<T, V> d = typed<T, V>(r);
+  switch (lanes_a) {
+    case 2: return launch_persist_la<2, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);
+    case 4: return launch_persist_la<4, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);
+    case 8: return launch_persist_la<8, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);
+    case 16: return launch_persist_la<16, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);
+    case 32: return launch_persist_la<32, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);
     default: return cudaErrorInvalidValue;
   }
 }

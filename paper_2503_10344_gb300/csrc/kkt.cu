@@ -40,6 +40,7 @@ __device__ __forceinline__ ESpan make_espan(const KktRaw& r) {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
+  pdl_enter();
   const ESpan es = make_espan(r);
   DevState* st = r.st + es.lp;
   if (!st->check_due || st->status != 0) return;
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
 // [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2
 template <int LANES>
 __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
+  pdl_enter();
   const Span sp = make_span(r.tr, r.m, r.grid_r_short, r.a_long, r.a_nlong);
   DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
 // [6,7] bound terms of the dual objective, [8,9] ||(x - x_last) / D_c||^2
 template <int LANES>
 __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
+  pdl_enter();
   const Span sp = make_span(r.tc, r.n, r.grid_c_short, r.t_long, r.t_nlong);
   DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
+  pdl_enter();
   // one block per LP
   const int k = blockIdx.x;
   DevState* st = r.st + k;
@@ -248,6 +252,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
+  pdl_enter();
   const ESpan es = make_espan(r);
   DevState* st = r.st + es.lp;
   if (!st->check_due || st->status != 0) return;
@@ -290,6 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
 }
 
 __global__ void k_kkt_end(KktRaw r) {
+  pdl_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per LP
   if (k >= r.count) return;
   DevState* st = r.st + k;
@@ -331,10 +337,8 @@ inline int egrid(const KktRaw& r) { return r.tc.blk_lp ? r.grid_c : r.grid_e; }
 template <int LANES>
 cudaError_t launch_rc(int which, const KktRaw& r, cudaStream_t s) {
   if (which == KK_ROWS)
-    k_kkt_rows<LANES><<<r.grid_r, kBlock, 0, s>>>(r);
-  else
-    k_kkt_cols<LANES><<<r.grid_c, kBlock, 0, s>>>(r);
-  return cudaGetLastError();
+    return launch_pdl(k_kkt_rows<LANES>, r.grid_r, kBlock, s, r);
+  return launch_pdl(k_kkt_cols<LANES>, r.grid_c, kBlock, s, r);
 }
 
 cudaError_t launch_rc_lanes(int which, int lanes, const KktRaw& r, cudaStream_t s) {
@@ -353,21 +357,17 @@ cudaError_t launch_rc_lanes(int which, int lanes, const KktRaw& r, cudaStream_t 
 cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s) {
   switch (which) {
     case KK_PREP:
-      if (r.fp32) k_kkt_prep<float><<<egrid(r), kBlock, 0, s>>>(r);
-      else k_kkt_prep<double><<<egrid(r), kBlock, 0, s>>>(r);
-      return cudaGetLastError();
+      if (r.fp32) return launch_pdl(k_kkt_prep<float>, egrid(r), kBlock, s, r);
+      return launch_pdl(k_kkt_prep<double>, egrid(r), kBlock, s, r);
     case KK_ROWS: return launch_rc_lanes(KK_ROWS, lanes_r, r, s);
     case KK_COLS: return launch_rc_lanes(KK_COLS, lanes_c, r, s);
     case KK_FINAL:
-      k_kkt_final<<<r.count, kBlock, 0, s>>>(r);
-      return cudaGetLastError();
+      return launch_pdl(k_kkt_final, r.count, kBlock, s, r);
     case KK_APPLY:
-      if (r.fp32) k_kkt_apply<float><<<egrid(r), kBlock, 0, s>>>(r);
-      else k_kkt_apply<double><<<egrid(r), kBlock, 0, s>>>(r);
-      return cudaGetLastError();
+      if (r.fp32) return launch_pdl(k_kkt_apply<float>, egrid(r), kBlock, s, r);
+      return launch_pdl(k_kkt_apply<double>, egrid(r), kBlock, s, r);
     case KK_END:
-      k_kkt_end<<<(r.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(r);
-      return cudaGetLastError();
+      return launch_pdl(k_kkt_end, (r.count + kBlock - 1) / kBlock, kBlock, s, r);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -36,6 +36,7 @@ struct VecIn {
   const unsigned char* row_kind;
   const double *x0, *y0;        // caller warm start (device) or NULL
   int scaled;
+  const double *wx, *wy;        // primal-weight hint (device, caller convention) or NULL
 };
 
 cudaError_t setup_validate(const SetupIn& in, int* d_err, cudaStream_t s);
@@ -56,7 +57,8 @@ cudaError_t setup_iter_values(int which_type, const int* ptr, const int* col, co
                               int nrows, const double* own, const double* other, int own_is_row,
                               int scaled, void* out, cudaStream_t s);
 size_t setup_part_doubles(int m, int n);
-// scalars_out: [0] ||c~||, [1] ||q~||, [2] ||c||, [3] ||q||, [4] max |K~_ij|
+// scalars_out: [0] ||c~||, [1] ||q~||, [2] ||c||, [3] ||q||, [4] max |K~_ij|,
+// [5] ||x~_hint||, [6] ||y~_hint|| (scaled space, projected; 0 without a hint)
 cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void* u, void* q,
                                void* tw, void* sw, void* x0, void* y0, const int* a_ptr,
                                const int* a_col, const double* a_val64, double* part,

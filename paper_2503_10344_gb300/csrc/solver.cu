@@ -20,7 +20,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -88,6 +90,7 @@ struct Bufs {
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
   int *a_long, *t_long, *tmp, *flags2;
+  unsigned* cnt;  // group counters of the dual kernel (32 x 8 words)
   DevState* st;
 };
 
@@ -159,6 +162,7 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
                                    2 * (std::max(M, N) + 1) + scan_tmp_ints((long long)std::max(M, N) + 1));
   b.tmp = (int*)ar.take(4 * tmp_ints);
   b.flags2 = (int*)ar.take(16);
+  b.cnt = (unsigned*)ar.take(4 * 32 * 8);
   b.st = (DevState*)ar.take(sizeof(DevState));
   return ar.off + 256;
 }
@@ -187,6 +191,29 @@ struct Solve {
   IterRaw ir;
   KktRaw kr;
   cudaStream_t s;
+  int persist_grid;  // > 0: one persistent kernel per check period (one LP)
+
+  cudaError_t persist(int max_attempts) {
+    ++g_launches;
+    int g = 0;
+    switch (mode) {
+      case MODE_FP64: return launch_persist_fp64(lanes_a, lanes_t, ir, max_attempts, persist_grid, &g, s);
+      case MODE_FP32: return launch_persist_fp32(lanes_a, lanes_t, ir, max_attempts, persist_grid, &g, s);
+      case MODE_BF16: return launch_persist_bf16(lanes_a, lanes_t, ir, max_attempts, persist_grid, &g, s);
+      default: return launch_persist_pat(lanes_a, lanes_t, ir, max_attempts, persist_grid, &g, s);
+    }
+  }
+  // the step attempts of one check period: one persistent launch, or two
+  // launches per attempt
+  cudaError_t period_steps(int period) {
+    if (persist_grid > 0) return persist(4 * period);
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < period && e == cudaSuccess; ++a) {
+      e = iter(IK_PRIMAL);
+      if (e == cudaSuccess) e = iter(IK_DUAL);
+    }
+    return e;
+  }
 
   cudaError_t iter(int which) {
     ++g_launches;
@@ -227,6 +254,10 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
     return fail(PDLP_ERR_INVALID_INPUT, "invalid parameter value");
   if (p->precision != PDLP_FP64 && p->precision != PDLP_FP32 && p->precision != PDLP_FP32_BF16A)
     return fail(PDLP_ERR_INVALID_INPUT, "unknown precision mode");
+  if (p->persistent != 0 && p->persistent != 1)
+    return fail(PDLP_ERR_INVALID_INPUT, "persistent must be 0 or 1");
+  if (p->autotune != 0 && p->autotune != 1)
+    return fail(PDLP_ERR_INVALID_INPUT, "autotune must be 0 or 1");
   if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)) ||
       (p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
       (p->lanes_kkt_AT && !valid_lanes(p->lanes_kkt_AT)))
@@ -238,8 +269,9 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
 // fused kernel is launched `reps` times back to back from a CUDA graph.
 struct TimingReq {
   int reps;
-  double* ms;     // [5] primal, dual, attempt (primal + dual), KKT pass over A, over A^T
-  double* bytes;  // [5] algorithmic bytes per launch of the same kernels
+  double* ms;     // [6] primal, dual, attempt (primal + dual), KKT pass over A, over A^T,
+                  // one attempt inside the persistent kernel
+  double* bytes;  // [6] algorithmic bytes per launch of the same kernels (per attempt for [5])
 };
 
 static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
@@ -249,7 +281,7 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
 struct SetupOut {
   Mode mode;
   int scaled, fp32;
-  double sca[5];  // ||c~||, ||q~||, ||c||, ||q||, max |K~|
+  double sca[7];  // ||c~||, ||q~||, ||c||, ||q||, max |K~|, ||x~_hint||, ||y~_hint||
   int lanes_a, lanes_t, lanes_ka, lanes_kt, th_a, th_t, nlong_a, nlong_t;
 };
 
@@ -260,7 +292,8 @@ struct SetupOut {
 static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const double* c,
                     const double* l, const double* u, const pdlp_params* p, const double* x0,
                     const double* y0, Bufs& bf, cudaStream_t s, bool no_alloc, int forced_mode,
-                    const int* forced_lanes, SetupOut* so) {
+                    const int* forced_lanes, SetupOut* so, const double* hx = nullptr,
+                    const double* hy = nullptr) {
   const int m = A->m, n = A->n;
   const long long nnz = A->nnz;
   // ---- validation (A0 preconditions)
@@ -312,11 +345,11 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
                                bf.t_valit, s));
     g_launches += 2;
   }
-  VecIn vi{m, n, bf.dr, bf.dc, c, l, u, bf.q64, bf.row_kind, x0, y0, scaled};
+  VecIn vi{m, n, bf.dr, bf.dc, c, l, u, bf.q64, bf.row_kind, x0, y0, scaled, hx, hy};
   CUDA_TRY(setup_iter_vectors(vi, fp32, bf.c_it, bf.l_it, bf.u_it, bf.q_it, bf.tw, bf.sw, bf.x[0],
                               bf.y[0], bf.a_ptr, bf.a_col, bf.a_val64, bf.part_setup, bf.scalars, s));
   g_launches += 3;
-  double sca[5];
+  double sca[7];
   CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
   // ---- launch shapes and long rows
   const double avg_a = m ? (double)nnz / m : 1.0, avg_t = (double)nnz / n;
@@ -347,7 +380,7 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   so->mode = mode;
   so->scaled = scaled;
   so->fp32 = fp32;
-  for (int k = 0; k < 5; ++k) so->sca[k] = sca[k];
+  for (int k = 0; k < 7; ++k) so->sca[k] = sca[k];
   so->lanes_a = lanes_a;
   so->lanes_t = lanes_t;
   so->lanes_ka = lanes_ka;
@@ -359,11 +392,119 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   return PDLP_OK;
 }
 
+// ---------------------------------------------------------------- launch-shape autotuner
+// Lanes per row of the two step kernels, chosen by timing: every candidate
+// (2, 4, 8, 16, 32 lanes; the primal kernel's over A^T and the dual kernel's
+// over A independently) runs a CUDA graph of kTuneReps launches on this LP with
+// the state in dry mode (the kernels do all their work, the step decision is
+// skipped, the current iterate is untouched), and the fastest is kept.  Results
+// are cached per (device, mode, m, n, nnz) for the life of the process.
+constexpr int kTuneReps = 16;
+struct TuneKey {
+  int dev, mode, count;
+  long long m, n, nnz;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, mode, count, m, n, nnz) < std::tie(o.dev, o.mode, o.count, o.m, o.n, o.nnz);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+// Sets sv.lanes_t / sv.lanes_a; set_grids(lanes_t, lanes_a) applies a choice to
+// the launch shapes (grids, batch maps); set_dry(on) switches the state(s)
+// between dry mode (check_due 0, dry 1) and ready (check_due 1, dry 0).
+template <typename SetGrids, typename SetDry>
+static int autotune_lanes(Solve& sv, int count, bool tune_t, bool tune_a, SetGrids set_grids,
+                          SetDry set_dry) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const TuneKey key{dev, (int)sv.mode, count, sv.m, sv.n, sv.nnz};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      if (tune_t) sv.lanes_t = it->second.first;
+      if (tune_a) sv.lanes_a = it->second.second;
+      return set_grids(sv.lanes_t, sv.lanes_a);
+    }
+  }
+  const cudaStream_t s = sv.s;
+  int rc = set_dry(true);
+  if (rc) return rc;
+  cudaStream_t cs;
+  CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t a, b;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  struct Free {
+    cudaStream_t s;
+    cudaEvent_t a, b;
+    ~Free() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaStreamDestroy(s);
+    }
+  } fr{cs, a, b};
+  auto time_one = [&](int which, double* out) -> int {
+    Solve cap = sv;
+    cap.s = cs;
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int i = 0; i < kTuneReps && ce == cudaSuccess; ++i) ce = cap.iter(which);
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("tuning capture: ") + cudaGetErrorString(ce));
+    CUDA_TRY(ee);
+    cudaGraphExec_t ge;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(ie);
+    struct GFree {
+      cudaGraphExec_t g;
+      ~GFree() { cudaGraphExecDestroy(g); }
+    } gf{ge};
+    CUDA_TRY(cudaGraphLaunch(ge, s));  // warm
+    CUDA_TRY(cudaEventRecord(a, s));
+    CUDA_TRY(cudaGraphLaunch(ge, s));
+    CUDA_TRY(cudaEventRecord(b, s));
+    CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    *out = ms;
+    g_launches += 2LL * kTuneReps;
+    return PDLP_OK;
+  };
+  static const int cand[5] = {2, 4, 8, 16, 32};
+  for (int which : {IK_PRIMAL, IK_DUAL}) {
+    if ((which == IK_PRIMAL && !tune_t) || (which == IK_DUAL && !tune_a)) continue;
+    double best = INFINITY;
+    int best_l = which == IK_PRIMAL ? sv.lanes_t : sv.lanes_a;
+    for (int L : cand) {
+      if (which == IK_PRIMAL) sv.lanes_t = L; else sv.lanes_a = L;
+      if ((rc = set_grids(sv.lanes_t, sv.lanes_a)) != PDLP_OK) return rc;
+      double ms = 0.0;
+      if ((rc = time_one(which, &ms)) != PDLP_OK) return rc;
+      if (ms < best) {
+        best = ms;
+        best_l = L;
+      }
+    }
+    if (which == IK_PRIMAL) sv.lanes_t = best_l; else sv.lanes_a = best_l;
+    if ((rc = set_grids(sv.lanes_t, sv.lanes_a)) != PDLP_OK) return rc;
+  }
+  if ((rc = set_dry(false)) != PDLP_OK) return rc;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {sv.lanes_t, sv.lanes_a};
+  return PDLP_OK;
+}
+
 static int solve_device(const pdlp_csr* A, const double* b, const char* sense, const double* c,
                         const double* l, const double* u, const pdlp_params* p, const double* x0,
                         const double* y0, double* x_out, double* y_out, pdlp_result* r,
                         const pdlp_diagnostics* dg, void* workspace, size_t ws_bytes,
-                        cudaStream_t s, const TimingReq* tq = nullptr, bool no_alloc = false) {
+                        cudaStream_t s, const TimingReq* tq = nullptr, bool no_alloc = false,
+                        const double* hx = nullptr, const double* hy = nullptr) {
   const int m = A->m, n = A->n;
   const long long nnz = A->nnz;
   g_launches = 0;
@@ -410,7 +551,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
 
   SetupOut so;
   {
-    const int rc = setup_lp(A, b, sense, c, l, u, p, x0, y0, bf, s, no_alloc, -1, nullptr, &so);
+    const int rc = setup_lp(A, b, sense, c, l, u, p, x0, y0, bf, s, no_alloc, -1, nullptr, &so, hx,
+                            hy);
     if (rc) return rc;
   }
   const Mode mode = so.mode;
@@ -419,13 +561,13 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   const int lanes_a = so.lanes_a, lanes_t = so.lanes_t, lanes_ka = so.lanes_ka, lanes_kt = so.lanes_kt;
   const int th_a = so.th_a, th_t = so.th_t, nlong_a = so.nlong_a, nlong_t = so.nlong_t;
   const int MB = max_blocks();
-  // float32 step kernels: one group of lanes per row, rows grid-strided;
+  // float32 step kernels: one group of lanes per two rows, rows grid-strided;
   // float64 kernels (float64 steps, KKT passes): warp tiles of 32 rows
   const bool tiled = mode == MODE_FP64;
   const int gp_short = tiled ? grid_for(((long long)n + 31) / 32 * 32, MB)
-                             : grid_for((long long)n * lanes_t, MB);
+                             : grid_for(((long long)n + 1) / 2 * lanes_t, MB);
   const int gd_short = tiled ? grid_for(((long long)std::max(m, 1) + 31) / 32 * 32, MB)
-                             : grid_for((long long)std::max(m, 1) * lanes_a, MB);
+                             : grid_for(((long long)std::max(m, 1) + 1) / 2 * lanes_a, MB);
   const int gp = gp_short + std::min(nlong_t, kMaxLongBlocks);
   const int gd = gd_short + std::min(nlong_a, kMaxLongBlocks);
   const int ge = grid_for(std::max(m, n), MB);
@@ -450,6 +592,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   ir.part_p = bf.part_p; ir.part_d = bf.part_d;
   ir.grid_p_short = gp_short; ir.grid_p = gp; ir.grid_d_short = gd_short; ir.grid_d = gd;
   ir.st = bf.st;
+  ir.cnt = bf.cnt;
 
   KktRaw kr{};
   kr.count = 1;
@@ -476,6 +619,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   memset(&hs, 0, sizeof(hs));
   const double nct = sca[0], nqt = sca[1], kmax = sca[4];
   hs.omega = (nct > 1e-10 && nqt > 1e-10) ? nct / nqt : 1.0;
+  // a primal-weight hint replaces the ||c~|| / ||q~|| estimate by the ratio of the
+  // hint's own scaled norms (the balance the weight is meant to strike)
+  if ((hx || hy) && sca[5] > 1e-10 && sca[6] > 1e-10) hs.omega = sca[6] / sca[5];
   hs.eta = kmax > 0.0 ? 1.0 / kmax : 1.0;
   if (p->fixed_eta > 0.0) hs.eta = p->fixed_eta;
   if (p->fixed_omega > 0.0) hs.omega = p->fixed_omega;
@@ -520,13 +666,49 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     hs.tr_check_cap = dg->check_capacity;
   }
   CUDA_TRY(cudaMemcpyAsync(bf.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(bf.cnt, 0, 4 * 32 * 8, s));
   const size_t eb = fp32 ? 4 : 8;
   CUDA_TRY(cudaMemsetAsync(bf.sum_x, 0, eb * n, s));
   if (m) CUDA_TRY(cudaMemsetAsync(bf.sum_y, 0, eb * m, s));
   CUDA_TRY(cudaMemsetAsync(bf.Xl, 0, 8 * (size_t)n, s));
   if (m) CUDA_TRY(cudaMemsetAsync(bf.Yl, 0, 8 * (size_t)m, s));
 
-  Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s};
+  Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s, 0};
+  if (p->autotune && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
+    auto set_grids = [&](int lt, int la) -> int {
+      const int gps = tiled ? gp_short : grid_for(((long long)n + 1) / 2 * lt, MB);
+      const int gds = tiled ? gd_short : grid_for(((long long)std::max(m, 1) + 1) / 2 * la, MB);
+      sv.ir.grid_p_short = gps;
+      sv.ir.grid_p = gps + std::min(nlong_t, kMaxLongBlocks);
+      sv.ir.grid_d_short = gds;
+      sv.ir.grid_d = gds + std::min(nlong_a, kMaxLongBlocks);
+      return PDLP_OK;
+    };
+    auto set_dry = [&](bool on) -> int {
+      static const int v[2][2] = {{1, 0}, {0, 1}};  // {check_due, dry}: ready, dry
+      CUDA_TRY(cudaMemcpyAsync(&bf.st->check_due, &v[on][0], sizeof(int), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(&bf.st->dry, &v[on][1], sizeof(int), cudaMemcpyHostToDevice, s));
+      return PDLP_OK;
+    };
+    const int rc = autotune_lanes(sv, 1, !p->lanes_AT, !p->lanes_A, set_grids, set_dry);
+    if (rc) return rc;
+  }
+  if (p->persistent) {
+    // the resident grid of the persistent kernel (probe launch with nothing to do:
+    // the state says check_due, so every block returns at entry)
+    int g = 0;
+    cudaError_t e;
+    switch (mode) {
+      case MODE_FP64: e = launch_persist_fp64(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
+      case MODE_FP32: e = launch_persist_fp32(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
+      case MODE_BF16: e = launch_persist_bf16(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
+      default: e = launch_persist_pat(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
+    }
+    ++g_launches;
+    if (e != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("persistent kernel: ") + cudaGetErrorString(e));
+    if (g > 4 * device_sm_count()) return fail(PDLP_ERR_CUDA, "persistent grid larger than its partial buffers");
+    sv.persist_grid = g;
+  }
   CUDA_TRY(sv.kkt_block());  // initial KKT and restart anchors
   if (!no_alloc) {
     CUDA_TRY(cudaEventRecord(e1, s));
@@ -543,10 +725,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       const long long max_chunks = (p->iter_limit / p->check_period + 2) * 64 + 1024;
       bool forced = false;
       for (long long chunk = 0;; ++chunk) {
-        for (int a = 0; a < p->check_period; ++a) {
-          CUDA_TRY(sv.iter(IK_PRIMAL));
-          CUDA_TRY(sv.iter(IK_DUAL));
-        }
+        CUDA_TRY(sv.period_steps(p->check_period));
         CUDA_TRY(sv.kkt_block());
         DevState h;
         CUDA_TRY(cudaMemcpyAsync(&h, bf.st, 16, cudaMemcpyDeviceToHost, s));
@@ -591,11 +770,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     const long long before = g_launches;
     cudaGraph_t graph;
     CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
-    for (int a = 0; a < p->check_period && ce == cudaSuccess; ++a) {
-      ce = cap.iter(IK_PRIMAL);
-      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
-    }
+    cudaError_t ce = cap.period_steps(p->check_period);
     if (ce == cudaSuccess) ce = cap.kkt_block();
     cudaError_t ee = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
@@ -675,11 +850,15 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     ms_solve = (float)(1e3 * std::chrono::duration<double>(h2 - h1).count());
   }
 
+  if (fs.status == kStatusWaitFailed)
+    return fail(PDLP_ERR_TIMEOUT, "a grid barrier wait of the persistent step kernel gave up");
   r->status = p->iter_limit == 0 ? PDLP_ITER_LIMIT : fs.status;
   r->precision_used = mode == MODE_FP64 ? PDLP_FP64
                       : mode == MODE_FP32 ? PDLP_FP32
                       : mode == MODE_BF16 ? PDLP_USED_BF16
                                           : PDLP_USED_PATTERN;
+  r->lanes_A = sv.lanes_a;
+  r->lanes_AT = sv.lanes_t;
   r->iters = fs.iters;
   r->attempts = fs.attempts;
   r->restarts = fs.restarts;
@@ -734,7 +913,8 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
     cudaGraph_t g;
     CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
-    for (int i = 0; i < tq.reps && ce == cudaSuccess; ++i) {
+    if (which == 5) ce = cap.persist(tq.reps);  // reps attempts inside one launch
+    for (int i = 0; i < tq.reps && ce == cudaSuccess && which != 5; ++i) {
       if (which == 0 || which == 2) ce = cap.iter(IK_PRIMAL);
       if (ce == cudaSuccess && (which == 1 || which == 2)) ce = cap.iter(IK_DUAL);
       if (which == 3) ce = launch_kkt(KK_ROWS, sv.lanes_ka, sv.lanes_kt, sv.kr, cs);
@@ -759,12 +939,17 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
     *out_ms = (double)ms / tq.reps;
-    g_launches += 2LL * tq.reps * (which == 2 ? 2 : 1);
+    g_launches += which == 5 ? 2 : 2LL * tq.reps * (which == 2 ? 2 : 1);
     return PDLP_OK;
   };
   int rc;
   for (int w = 0; w < 3; ++w)
     if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
+  if (sv.persist_grid > 0) {
+    if ((rc = time_one(5, &tq.ms[5])) != PDLP_OK) return rc;
+  } else {
+    tq.ms[5] = 0.0;
+  }
   CUDA_TRY(cudaMemcpyAsync(&st->check_due, &one, sizeof(int), cudaMemcpyHostToDevice, s));
   for (int w = 3; w < 5; ++w)
     if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
@@ -786,6 +971,8 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   tq.bytes[3] = 4 * (M + 1) + Z * (4 + val64) + N * 16 + M * (8 + 8 + 1 + 16 + 8);
   // KKT over A^T: row_ptr, col, values; both dual candidates gathered; c, l, u, D_c, x c/a, x anchor
   tq.bytes[4] = 4 * (N + 1) + Z * (4 + val64) + M * 16 + N * (32 + 16 + 8);
+  // one attempt of the persistent kernel: the primal and dual bytes
+  tq.bytes[5] = tq.bytes[2];
   return PDLP_OK;
 }
 
@@ -813,7 +1000,7 @@ static void build_map(const std::vector<LpShape>& sh, bool over_cols, int lanes,
   long long g = 0;
   for (int k = 0; k < K; ++k) {
     const long long rows = over_cols ? sh[k].n : sh[k].m;
-    const long long need = tiled ? (rows + 255) / 256 : (rows * lanes + kBlock - 1) / kBlock;
+    const long long need = tiled ? (rows + 255) / 256 : ((rows + 1) / 2 * lanes + kBlock - 1) / kBlock;
     long long share = total_rows > 0 ? (long long)((double)budget * (double)rows / (double)total_rows) : 1;
     share = std::max(1LL, std::min(share, std::max(1LL, need)));
     nshort[k] = (int)share;
@@ -920,6 +1107,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     void *a_valit, *t_valit, *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
     unsigned char *row_kind, *bflags;
     DevState* st;
+    unsigned* cnt;
     FacTable* fac;
   } g{};
   // long rows and launch maps need the per-LP setups first: upper bounds here
@@ -956,6 +1144,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.tabA = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.tabT = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.st = (DevState*)ar.take(sizeof(DevState) * count);
+    g.cnt = (unsigned*)ar.take(4 * 32 * 8 * (size_t)count);
     one.fac = nullptr;
   };
   Arena gdry{nullptr, 0};
@@ -1106,6 +1295,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     CUDA_TRY(cudaMemsetAsync(g.Xl, 0, 8 * N, s));
     if (M) CUDA_TRY(cudaMemsetAsync(g.Yl, 0, 8 * M, s));
     CUDA_TRY(cudaMemcpyAsync(g.st, hs.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(g.cnt, 0, 4 * 32 * 8 * (size_t)count, s));
     CUDA_TRY(cudaStreamSynchronize(s));
   }
   // ---- launch maps
@@ -1133,6 +1323,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   ir.part_p = g.part_p; ir.part_d = g.part_d;
   ir.grid_p_short = gridT; ir.grid_p = gridT; ir.grid_d_short = gridA; ir.grid_d = gridA;
   ir.st = g.st;
+  ir.cnt = g.cnt;
   ir.tp = tT;
   ir.td = tA;
   KktRaw kr{};
@@ -1156,6 +1347,46 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   kr.tr = tA;
   kr.tc = tT;
   Solve sv{(int)M, (int)N, Z, (Mode)mode, lanes[0], lanes[1], lanes[2], lanes[3], ir, kr, s};
+  if (p->autotune && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
+    // a lanes choice changes the blocks each LP gets: rebuild both launch maps
+    auto set_grids = [&](int lt, int la) -> int {
+      build_map(sh, false, la, tiled, nlong_a, long0_a, M, budget, tabA, &gridA);
+      build_map(sh, true, lt, tiled, nlong_t, long0_t, N, budget, tabT, &gridT);
+      if ((size_t)gridA > gmax || (size_t)gridT > gmax) return fail(PDLP_ERR_OOM, "launch map too large");
+      CUDA_TRY(cudaMemcpyAsync(g.tabA, tabA.data(), 4 * tabA.size(), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(g.tabT, tabT.data(), 4 * tabT.size(), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors are refilled next time
+      const Tables a2 = tables_at(g.tabA, gridA, count), t2 = tables_at(g.tabT, gridT, count);
+      sv.ir.grid_p_short = sv.ir.grid_p = gridT;
+      sv.ir.grid_d_short = sv.ir.grid_d = gridA;
+      sv.ir.tp = t2;
+      sv.ir.td = a2;
+      sv.kr.grid_r_short = sv.kr.grid_r = gridA;
+      sv.kr.grid_c_short = sv.kr.grid_c = gridT;
+      sv.kr.grid_e = gridT;
+      sv.kr.tr = a2;
+      sv.kr.tc = t2;
+      return PDLP_OK;
+    };
+    std::vector<DevState> hst(count);
+    auto set_dry = [&](bool on) -> int {
+      CUDA_TRY(cudaMemcpyAsync(hst.data(), g.st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (DevState& h : hst) {
+        h.check_due = on ? 0 : 1;
+        h.dry = on ? 1 : 0;
+      }
+      CUDA_TRY(cudaMemcpyAsync(g.st, hst.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      return PDLP_OK;
+    };
+    const int rc = autotune_lanes(sv, count, !p->lanes_AT, !p->lanes_A, set_grids, set_dry);
+    if (rc) return rc;
+    lanes[0] = sv.lanes_a;
+    lanes[1] = sv.lanes_t;
+    ir = sv.ir;  // the output kernels below use these copies
+    kr = sv.kr;
+  }
   CUDA_TRY(sv.kkt_block());  // initial KKT of every LP
   CUDA_TRY(cudaStreamSynchronize(s));
   const double setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1169,11 +1400,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     const long long before = g_launches;
     cudaGraph_t graph;
     CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
-    for (int a = 0; a < p->check_period && ce == cudaSuccess; ++a) {
-      ce = cap.iter(IK_PRIMAL);
-      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
-    }
+    cudaError_t ce = cap.period_steps(p->check_period);
     if (ce == cudaSuccess) ce = cap.kkt_block();
     cudaError_t ee = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
@@ -1237,6 +1464,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     r.status = p->iter_limit == 0 ? PDLP_ITER_LIMIT : f.status;
     r.precision_used = mode == MODE_FP64 ? PDLP_FP64 : mode == MODE_FP32 ? PDLP_FP32
                        : mode == MODE_BF16 ? PDLP_USED_BF16 : PDLP_USED_PATTERN;
+    r.lanes_A = lanes[0];
+    r.lanes_AT = lanes[1];
     r.iters = f.iters;
     r.attempts = f.attempts;
     r.restarts = f.restarts;
@@ -1293,6 +1522,8 @@ int pdlp_default_params(pdlp_params* p) {
   p->adaptive_step = 1;
   p->restarts = 1;
   p->terminate = 1;
+  p->persistent = 0;
+  p->autotune = 0;
   return PDLP_OK;
 }
 
@@ -1324,10 +1555,16 @@ int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, con
                       workspace_bytes, (cudaStream_t)stream);
 }
 
-int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const double* c,
-               const double* l, const double* u, const pdlp_params* p, const double* x0,
-               const double* y0, double* x_out, double* y_out, pdlp_result* r,
-               const pdlp_diagnostics* diag) {
+}  // extern "C"
+
+namespace pdlp {
+
+// pdlp_solve and pdlp_solve_hinted: host buffers in, one device block for the
+// inputs, outputs, diagnostics and workspace
+static int solve_host(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, const double* hx, const double* hy, double* x_out,
+                      double* y_out, pdlp_result* r, const pdlp_diagnostics* diag) {
   pdlp_params d;
   if (!p) {
     pdlp_default_params(&d);
@@ -1364,8 +1601,10 @@ int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const doub
     ptrs[18] = ar.take(TA);          // accepted
     ptrs[19] = ar.take(TC);          // restart
     ptrs[20] = ar.take(8 * TC);      // omega
+    ptrs[21] = ar.take(8 * N);       // primal-weight hint x
+    ptrs[22] = ar.take(8 * M);       // primal-weight hint y
   };
-  void* dp[21];
+  void* dp[23];
   Arena dry{nullptr, 0};
   lay(dry, dp);
   const size_t io_bytes = dry.off + 256;
@@ -1402,6 +1641,8 @@ int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const doub
   CUDA_TRY(h2d(dp[7], u, 8 * N));
   CUDA_TRY(h2d(dp[8], x0, 8 * N));
   CUDA_TRY(h2d(dp[9], y0, 8 * M));
+  CUDA_TRY(h2d(dp[21], hx, 8 * N));
+  CUDA_TRY(h2d(dp[22], hy, 8 * M));
   pdlp_csr dA{A->m, A->n, A->nnz, (const int64_t*)dp[0], (const int32_t*)dp[1], (const double*)dp[2]};
   pdlp_diagnostics ddg{(double*)dp[12], (double*)dp[13], (double*)dp[14], (double*)dp[15],
                        (int64_t)TA, (double*)dp[16], (double*)dp[17], (int8_t*)dp[18],
@@ -1409,7 +1650,8 @@ int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const doub
   rc = solve_device(&dA, (const double*)dp[3], (const char*)dp[4], (const double*)dp[5],
                     (const double*)dp[6], (const double*)dp[7], p, x0 ? (const double*)dp[8] : nullptr,
                     y0 ? (const double*)dp[9] : nullptr, (double*)dp[10], (double*)dp[11], r,
-                    diag ? &ddg : nullptr, ws, ws_bytes, s);
+                    diag ? &ddg : nullptr, ws, ws_bytes, s, nullptr, false,
+                    hx ? (const double*)dp[21] : nullptr, hy ? (const double*)dp[22] : nullptr);
   if (rc) return rc;
   CUDA_TRY(d2h(x_out, dp[10], 8 * N));
   CUDA_TRY(d2h(y_out, dp[11], 8 * M));
@@ -1430,6 +1672,44 @@ int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const doub
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   return PDLP_OK;
+}
+
+// pdlp_solve_device with a primal-weight hint (device buffers), used by the
+// learned warm start
+int solve_device_hint(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, const double* hx, const double* hy, double* x_out,
+                      double* y_out, pdlp_result* r, cudaStream_t s) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  const int rc = check_inputs(A, b, sense, c, l, u, p, x_out, y_out, r);
+  if (rc) return rc;
+  return solve_device(A, b, sense, c, l, u, p, x0, y0, x_out, y_out, r, nullptr, nullptr, 0, s,
+                      nullptr, false, hx, hy);
+}
+
+}  // namespace pdlp
+
+extern "C" {
+
+int pdlp_solve(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+               const double* l, const double* u, const pdlp_params* p, const double* x0,
+               const double* y0, double* x_out, double* y_out, pdlp_result* r,
+               const pdlp_diagnostics* diag) {
+  return solve_host(A, b, sense, c, l, u, p, x0, y0, nullptr, nullptr, x_out, y_out, r, diag);
+}
+
+int pdlp_solve_hinted(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                      const double* l, const double* u, const pdlp_params* p, const double* x0,
+                      const double* y0, const double* x_hint, const double* y_hint,
+                      double* x_out, double* y_out, pdlp_result* r,
+                      const pdlp_diagnostics* diag) {
+  if (!x_hint || (!y_hint && A && A->m > 0))
+    return fail(PDLP_ERR_INVALID_INPUT, "pdlp_solve_hinted needs x_hint[n] and y_hint[m]");
+  return solve_host(A, b, sense, c, l, u, p, x0, y0, x_hint, y_hint, x_out, y_out, r, diag);
 }
 
 int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, const double* c,

@@ -71,3 +71,23 @@ def test_batch_rejects_an_invalid_member(P):
     bad.l[0] = 2.0  # l > u
     with pytest.raises(P.PdlpError, match="LP 3"):
         P.pdlp_solve_batch(lps + [bad])
+
+
+def test_autotuned_batch(P):
+    """The tuner picks the lanes of the whole batch in dry mode: the float64 batch with
+    autotune follows the batch run with the picked lanes set explicitly (to rounding: the
+    long-row cut-off follows the lanes known at setup, so a long row may be summed by a
+    block in one run and by a lane group in the other); a float32 autotuned batch reaches
+    the tolerance."""
+    lps = mixed_lps()
+    kw = dict(iter_limit=60, terminate=0)
+    xs1, ys1, r1 = P.pdlp_solve_batch(lps, P.default_params(autotune=1, **kw))
+    la, lt = r1[0]["lanes_A"], r1[0]["lanes_AT"]
+    assert la in (2, 4, 8, 16, 32) and lt in (2, 4, 8, 16, 32)
+    xs2, ys2, r2 = P.pdlp_solve_batch(lps, P.default_params(lanes_A=la, lanes_AT=lt, **kw))
+    for a, b in zip(xs1 + ys1, xs2 + ys2):
+        assert np.linalg.norm(a - b) <= 1e-11 * max(1.0, np.linalg.norm(b))
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="bf16", autotune=1))
+    for lp, x, y, r in zip(lps, xs, ys, res):
+        assert r["status"] == P.PDLP_OPTIMAL, lp.name
+        assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4, lp.name

@@ -359,3 +359,102 @@ def test_set_cover_full_size(P, prec):
     k = O.kkt_original(lp, x, y)
     assert k.rel_kkt <= 1.01e-4, k
     assert abs(res["primal_obj"] - gold["highs_obj"]) / (1 + abs(gold["highs_obj"])) <= 5e-4
+
+
+# ---------------------------------------------------------------- primal-weight hint
+def seeded_hint(lp, seed):
+    rng = np.random.default_rng(seed)
+    box = np.isfinite(lp.l) & np.isfinite(lp.u)
+    xh = np.where(box, np.where(box, lp.l, 0) + rng.random(lp.n) * np.where(box, lp.u - lp.l, 0),
+                  rng.normal(size=lp.n) * 3)
+    return xh, rng.normal(size=lp.m) * 5   # some components outside the cone: projected
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_primal_weight_hint_matches_oracle(P, name):
+    lp = inst(name)
+    hint = seeded_hint(lp, 17)
+    # fixed step, no restarts: omega stays omega0
+    _, _, res, its = P.pdlp_solve(lp, P.default_params(iter_limit=10, terminate=0, adaptive_step=0,
+                                                       restarts=0, fixed_eta=0.9),
+                                  iterates=True, omega_hint=hint)
+    ref = O.solve(lp, O.Params(iter_limit=10, terminate=False, adaptive=False, restarts=False,
+                               fixed_eta=0.9, omega_hint=hint))
+    assert res["omega"] == pytest.approx(ref.omega, rel=1e-12)
+    assert_iterate_parity(its, ref)
+    # full mode from a warm start plus the hint
+    x0, y0 = seeded_hint(lp, 18)
+    _, _, res, its = P.pdlp_solve(lp, P.default_params(iter_limit=100, terminate=0), x0=x0, y0=y0,
+                                  iterates=True, omega_hint=hint)
+    ref = O.solve(lp, O.Params(iter_limit=100, terminate=False, omega_hint=hint), x0=x0, y0=y0)
+    assert res["attempts"] == ref.attempts and res["restarts"] == ref.restarts
+    assert_iterate_parity(its, ref)
+
+
+def test_primal_weight_hint_zero_part_falls_back(P):
+    lp = inst("set_cover_2000x8000")
+    kw = dict(iter_limit=1, terminate=0, adaptive_step=0, restarts=0, fixed_eta=0.9)
+    _, _, r0 = P.pdlp_solve(lp, P.default_params(**kw))
+    _, _, r1 = P.pdlp_solve(lp, P.default_params(**kw), omega_hint=(np.zeros(lp.n), np.ones(lp.m)))
+    assert r1["omega"] == r0["omega"]
+    _, _, r2 = P.pdlp_solve(lp, P.default_params(fixed_omega=3.0, **kw),
+                            omega_hint=seeded_hint(lp, 1))
+    assert r2["omega"] == 3.0
+
+
+# ---------------------------------------------------------------- persistent step kernel
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_persistent_kernel_matches_two_launch_form(P, name):
+    """The cooperative persistent kernel (default) and the two-launch form run the same
+    iteration: float64 fixed-step iterates agree to rounding (the partial sums are
+    reduced in a different order), and a full adaptive run matches the oracle."""
+    lp = inst(name)
+    kw = dict(iter_limit=300, adaptive_step=0, restarts=0, terminate=0, fixed_eta=0.9)
+    _, _, r1, it1 = gpu_iterates(P, lp, persistent=1, **kw)
+    _, _, r0, it0 = gpu_iterates(P, lp, persistent=0, **kw)
+    assert r1["iters"] == r0["iters"] == 300
+    for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
+        assert rel(it1[k], it0[k]) <= 1e-13, k
+    # fewer launches: one per check period instead of two per attempt
+    assert r1["kernel_launches"] < r0["kernel_launches"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_persistent_and_two_launch_reach_the_same_tolerance(P, prec):
+    lp = inst("set_cover_2000x8000")
+    for persistent in (0, 1):
+        x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec, persistent=persistent))
+        assert r["status"] == P.PDLP_OPTIMAL
+        assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4
+
+
+def test_persistent_parameter_is_checked(P):
+    lp = inst("mip_relaxation_200x400")
+    with pytest.raises(P.PdlpError):
+        P.pdlp_solve(lp, P.default_params(persistent=2))
+
+
+# ---------------------------------------------------------------- launch-shape autotuner
+def test_autotune_picks_lanes_without_moving_the_iterate(P):
+    """The tuner times the step kernels in dry mode: a float64 run with autotune equals,
+    bit for bit, a run with the lanes it picked set explicitly; the choice is cached."""
+    lp = lpgen.set_cover(41, m=3000, n=12000)
+    kw = dict(iter_limit=100, terminate=0)
+    _, _, r1, it1 = gpu_iterates(P, lp, autotune=1, **kw)
+    assert r1["lanes_A"] in (2, 4, 8, 16, 32) and r1["lanes_AT"] in (2, 4, 8, 16, 32)
+    _, _, r2, it2 = gpu_iterates(P, lp, lanes_A=r1["lanes_A"], lanes_AT=r1["lanes_AT"], **kw)
+    for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
+        assert np.array_equal(it1[k], it2[k]), k
+    _, _, r3, _ = gpu_iterates(P, lp, autotune=1, **kw)  # cached: same choice
+    assert (r3["lanes_A"], r3["lanes_AT"]) == (r1["lanes_A"], r1["lanes_AT"])
+    # explicit lanes are kept
+    _, _, r4, _ = gpu_iterates(P, lp, autotune=1, lanes_A=2, lanes_AT=32, **kw)
+    assert (r4["lanes_A"], r4["lanes_AT"]) == (2, 32)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_autotuned_solve_reaches_tolerance(P, prec):
+    lp = inst("set_cover_2000x8000")
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec, autotune=1))
+    assert r["status"] == P.PDLP_OPTIMAL
+    assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4

@@ -41,6 +41,11 @@ MUTANTS = [
      ["test_average_is_step_size_weighted"]),
     ("primal residual ignores violated >=-rows", "np.maximum(q - kx, 0.0)", "np.minimum(q - kx, 0.0)",
      ["test_kkt_primal_residual_senses_by_hand"]),
+    ("primal-weight hint ratio inverted", "omega = nyh / nxh", "omega = nxh / nyh",
+     ["test_primal_weight_hint_by_hand"]),
+    ("primal-weight hint not projected onto the bounds",
+     "xh = proj_box(np.asarray(p.omega_hint[0], dtype=np.float64) / dc, lt, ut)",
+     "xh = np.asarray(p.omega_hint[0], dtype=np.float64) / dc", ["test_primal_weight_hint_by_hand"]),
 ]
 
 

@@ -304,3 +304,20 @@ def test_replaying_the_own_trace_reproduces_the_run():
     np.testing.assert_array_equal(r2.x_cur, r.x_cur)
     np.testing.assert_array_equal(r2.y_avg, r.y_avg)
     assert r2.check_trace == r.check_trace
+
+
+def test_primal_weight_hint_by_hand():
+    """K = I on two >=-rows: Ruiz and Pock-Chambolle leave D_r = D_c = I, so the hinted
+    omega0 is the ratio of the projected hint's plain norms."""
+    lp = _lp_from_dense(np.eye(2), [1.0, 1.0], "GG", [1.0, 1.0], [0.0, 0.0], [10.0, 4.0])
+    k, _, _, _ = O.canonicalize(lp)
+    dr, dc = O.ruiz_pock_chambolle(k)
+    assert dr.tolist() == [1.0, 1.0] and dc.tolist() == [1.0, 1.0]
+    fixed = dict(iter_limit=1, adaptive=False, restarts=False, terminate=False)
+    # x = (3, 40) projects to (3, 4): norm 5; y = (-7, 10) projects to (0, 10): norm 10
+    r = O.solve(lp, O.Params(omega_hint=(np.array([3.0, 40.0]), np.array([-7.0, 10.0])), **fixed))
+    assert r.omega == 2.0
+    # without a hint: ||c|| / ||b|| = 1; a hint with a zero part falls back to it
+    assert O.solve(lp, O.Params(**fixed)).omega == 1.0
+    r0 = O.solve(lp, O.Params(omega_hint=(np.zeros(2), np.array([0.0, 10.0])), **fixed))
+    assert r0.omega == 1.0
