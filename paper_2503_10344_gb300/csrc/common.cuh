@@ -32,7 +32,7 @@ template <> struct Ld<double, double> {
 };
 
 // Device-resident solver state.  Written by one thread of the deciding block
-// (the last block of the dual-step kernel, the KKT finalisation kernel) and
+// (the step-decision kernel, the KKT finalisation kernel) and
 // read by every kernel at entry; kernels launched after a terminating or a
 // KKT-pending decision return immediately, so a captured chunk of iterations
 // is safe to over-launch.
@@ -56,7 +56,6 @@ struct DevState {
   int used_avg;          // output candidate of the last check
   int force_final;       // host asked for a final check (time limit)
   int dry;               // 1: step kernels run but the decision is skipped (launch-shape tuning)
-  unsigned int counter;  // last-block counter of the dual-step kernel
   long long last_restart_it;
   double last_rp2, last_rd2, last_gap2;  // scaled KKT triple of the last restart point
   double prev_cand;                      // KKT_omega of the previous candidate (inf after restart)

@@ -25,12 +25,13 @@ struct IterRaw {
   const unsigned char* row_kind;
   void *x[2], *y[2], *sum_x, *sum_y;  // x: interleaved (x_j, dx_j) pairs
   double *part_p, *part_d;
-  unsigned* cnt;  // [count][32][8] zeroed group counters of the dual kernel
   int grid_p_short, grid_p, grid_d_short, grid_d;
   DevState* st;  // [count]
+  int count;     // LPs (1 for a single LP)
   Tables tp, td; // batch tables over A^T and A (all NULL for one LP)
 };
 
+// IK_DUAL launches the dual step kernel and then the step decision (k_decide)
 enum IterKernel { IK_PRIMAL = 0, IK_DUAL = 1 };
 
 // persistent attempts kernel (one LP; see iter_kernels.cuh): grid 0 = resident maximum

@@ -6,9 +6,10 @@
 //                ||x' - x||^2 (scaled norm).
 //   k_dual    -- CSR SpMV over A fused with the extrapolated dual update
 //                y' = proj_Y(y + sigma (q - K(2x' - x))) and the partial sums
-//                of ||y' - y||^2 and (y' - y)^T K (x' - x); its last block
-//                reduces the partials in a fixed order and takes the adaptive
-//                step-size decision (accept / retry) on the device.
+//                of ||y' - y||^2 and (y' - y)^T K (x' - x);
+//   k_decide  -- one block per LP: the partial sums in a fixed order and the
+//                adaptive step-size decision (accept / retry) on the device.
+// All three are launched with programmatic dependent launch (see common.cuh).
 // The primal iterate is stored as interleaved pairs (x'_j, x'_j - x_j): one
 // vector gather per nonzero gives the dual kernel both K x' and K (x' - x),
 // so K(2x' - x) = K x' + K dx and the step-size interaction term dy^T K dx are
@@ -76,9 +77,9 @@ struct IterData {
   T* sum_x; T* sum_y;
   T* part_p;                                           // [grid_p]
   T* part_d;                                           // [2][grid_d]
-  unsigned* cnt;                                       // [count][kCountGroups][8] group counters
   int grid_p_short, grid_p, grid_d_short, grid_d;
   DevState* st;                                        // [count] (one per LP)
+  int count;                                           // LPs (1 for a single LP)
   Tables tp, td;                                       // batch tables over A^T / A (NULL: one LP)
 };
 
@@ -103,49 +104,91 @@ __device__ __forceinline__ void rows_short(const Span& sp, const int* __restrict
 }
 
 // Two rows per group and pass, rows g and g + G of the grid's G groups, their
-// index loads and gathers interleaved in one loop (twice the loads in flight of
-// one row at a time), and each row's epilogue operands fetched by the epilogue
-// lane before the SpMV (they depend on the row index only), so the epilogue
-// does not add a round trip after the gathers.  `pref(r)` returns the operands,
-// `epi(r, acc, pre)` finishes the row.  Rows longer than `thresh` are skipped.
-template <int LANES, typename Acc, typename Pre, typename Load, typename PreF, typename Epi>
-__device__ __forceinline__ void rows_short2(const Span& sp, const int* __restrict__ ptr, int thresh,
-                                            Load load, PreF pref, Epi epi) {
+// loads interleaved in one loop (twice the loads in flight of one row at a
+// time).  The first row pair's row pointers and each lane's first kPre column
+// indices and values do not depend on the iterate: they are loaded BEFORE
+// `enter()` waits for the preceding kernel (programmatic dependent launch), so
+// after the wait a row costs its vector gathers; the epilogue operands
+// (`pref_c` constant, `pref_v` iterate) are issued alongside the gathers.  `enter()` returns false when the state says the kernel has
+// nothing to do (uniform over the block).  `val(p)` is the stored value at
+// position p, `term(v, j)` the row-sum term of value v and gathered entry j,
+// `fin(r, acc, pc, pv)` finishes a row.  Rows longer than `thresh` are skipped
+// (long-row blocks own them).
+constexpr int kPre = 2;
+
+template <int LANES, typename Acc, typename PC, typename PV, typename Val, typename Term,
+          typename PrefC, typename PrefV, typename Fin, typename Enter>
+__device__ __forceinline__ bool rows_short2(const Span& sp, const int* __restrict__ ptr,
+                                            const int* __restrict__ col, int thresh, Val val,
+                                            Term term, PrefC pref_c, PrefV pref_v, Fin fin,
+                                            Enter enter) {
+  using VT = decltype(val(0));
   const int lane = threadIdx.x & (LANES - 1);
   const long long G = (long long)sp.nshort * kBlock / LANES;
   const long long end = (long long)sp.row0 + sp.nrows;
-  for (long long r0 = sp.row0 + ((long long)sp.bidx * kBlock + threadIdx.x) / LANES; r0 < end;
-       r0 += 2 * G) {
-    const long long r1 = r0 + G;
-    const bool has1 = r1 < end;
-    int s0 = __ldg(ptr + r0), e0 = __ldg(ptr + r0 + 1);
-    int s1 = 0, e1 = 0;
-    if (has1) {
-      s1 = __ldg(ptr + r1);
-      e1 = __ldg(ptr + r1 + 1);
+  long long r0 = sp.row0 + ((long long)sp.bidx * kBlock + threadIdx.x) / LANES;
+  int s0 = 0, s1 = 0, n0 = 0, n1 = 0;
+  int c0[kPre], c1[kPre];
+  VT v0[kPre], v1[kPre];
+  PC pc0{}, pc1{};
+  auto fetch = [&](long long ra) {
+    const long long rb = ra + G;
+    s0 = __ldg(ptr + ra);
+    const int e0 = __ldg(ptr + ra + 1);
+    s1 = 0;
+    int e1 = 0;
+    if (rb < end) {
+      s1 = __ldg(ptr + rb);
+      e1 = __ldg(ptr + rb + 1);
     }
-    const bool ok0 = e0 - s0 <= thresh;  // uniform within the group
-    const bool ok1 = has1 && e1 - s1 <= thresh;
-    const int n0 = ok0 ? e0 - s0 : 0, n1 = ok1 ? e1 - s1 : 0;
-    Pre p0{}, p1{};
-    if (lane == 0) {
-      if (ok0) p0 = pref((int)r0);
-      if (ok1) p1 = pref((int)r1);
+    n0 = e0 - s0 <= thresh ? e0 - s0 : -1;  // -1: a long row, not ours (uniform in the group)
+    n1 = rb < end ? (e1 - s1 <= thresh ? e1 - s1 : -1) : -1;
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int q = lane + k * LANES;
+      c0[k] = q < n0 ? __ldg(col + s0 + q) : 0;
+      v0[k] = q < n0 ? val(s0 + q) : VT(0);
+      c1[k] = q < n1 ? __ldg(col + s1 + q) : 0;
+      v1[k] = q < n1 ? val(s1 + q) : VT(0);
+    }
+  };
+  if (r0 < end) fetch(r0);
+  if (!enter()) return false;
+  for (bool first = true; r0 < end; r0 += 2 * G, first = false) {
+    if (!first) fetch(r0);
+    const long long r1 = r0 + G;
+    PV pv0{}, pv1{};
+    if (lane == 0) {  // independent of the gathers below: issued together with them
+      if (n0 >= 0) {
+        pc0 = pref_c((int)r0);
+        pv0 = pref_v((int)r0);
+      }
+      if (n1 >= 0) {
+        pc1 = pref_c((int)r1);
+        pv1 = pref_v((int)r1);
+      }
     }
     Acc a0{}, a1{};
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int q = lane + k * LANES;
+      if (q < n0) a0 += term(v0[k], c0[k]);
+      if (q < n1) a1 += term(v1[k], c1[k]);
+    }
     const int nmax = n0 > n1 ? n0 : n1;
 #pragma unroll 2
-    for (int k = lane; k < nmax; k += LANES) {
-      if (k < n0) a0 += load(s0 + k);
-      if (k < n1) a1 += load(s1 + k);
+    for (int q = lane + kPre * LANES; q < nmax; q += LANES) {
+      if (q < n0) a0 += term(val(s0 + q), __ldg(col + s0 + q));
+      if (q < n1) a1 += term(val(s1 + q), __ldg(col + s1 + q));
     }
     a0 = group_sum<LANES>(a0);
     a1 = group_sum<LANES>(a1);
     if (lane == 0) {
-      if (ok0) epi((int)r0, a0, p0);
-      if (ok1) epi((int)r1, a1, p1);
+      if (n0 >= 0) fin((int)r0, a0, pc0, pv0);
+      if (n1 >= 0) fin((int)r1, a1, pc1, pv1);
     }
   }
+  return true;
 }
 
 // Tiles of 32 consecutive rows per warp: SpMV with LANES lanes per row in
@@ -234,64 +277,83 @@ __device__ __forceinline__ void rows_all(const Span& sp, const int* ptr, int thr
 template <typename T> struct StepOcc { static constexpr int value = 6; };
 template <> struct StepOcc<double> { static constexpr int value = 1; };
 
-// group counters of the dual kernel's last-block detection (per LP)
-constexpr int kCountGroups = 32;
-
+// epilogue operands of a row: constant ones (read before the dependent-launch
+// wait) and iterate ones (after it)
 template <typename T>
-struct PreP {  // epilogue operands of a primal row
-  T xo, c, l, u, tw, sx;
+struct PreCP {  // primal row j: c, l, u, step weight
+  T c, l, u, tw;
 };
 template <typename T>
-struct PreD {  // epilogue operands of a dual row
-  T yo, q, sw, sy;
+struct PreVP {  // primal row j: x_j, running sum
+  T xo, sx;
+};
+template <typename T>
+struct PreCD {  // dual row i: q, step weight, row kind
+  T q, sw;
   int kind;
 };
+template <typename T>
+struct PreVD {  // dual row i: y_i, running sum
+  T yo, sy;
+};
 
+// Iterate vectors written by the preceding kernels are read with ordinary
+// (weak, L1-cacheable) loads after the dependent-launch wait, whose guarantee
+// covers them; never through the non-coherent read-only path (__ldg), which
+// assumes data that no grid in flight writes.
 template <int LANES, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_primal(IterData<T, V> d) {
-  pdl_enter();
   constexpr bool TILED = std::is_same<T, double>::value;
   const Span sp = make_span(d.tp, d.n, d.grid_p_short, d.t_long, d.t_nlong);
   DevState* st = d.st + sp.lp;
-  if (st->status != 0 || st->check_due) return;
-  const int cur = st->cur;
-  const vec2_t<T>* __restrict__ x = cur ? d.x[1] : d.x[0];
-  vec2_t<T>* __restrict__ xn = cur ? d.x[0] : d.x[1];
-  const T* __restrict__ y = cur ? d.y[1] : d.y[0];
-  const T tau = StepT<T>::tau(st);
-  const T pw = StepT<T>::pw(st);
+  const vec2_t<T>* x = nullptr;
+  vec2_t<T>* xn = nullptr;
+  const T* y = nullptr;
+  T tau = 0, pw = 0;
+  auto enter = [&]() -> bool {
+    pdl_enter();
+    if (st->status != 0 || st->check_due) return false;
+    const int cur = st->cur;
+    x = cur ? d.x[1] : d.x[0];
+    xn = cur ? d.x[0] : d.x[1];
+    y = cur ? d.y[1] : d.y[0];
+    tau = StepT<T>::tau(st);
+    pw = StepT<T>::pw(st);
+    return true;
+  };
   T dx2 = 0;
-  auto load = [&](int p) -> T { return Ld<T, V>::get(d.t_val, p) * __ldg(y + __ldg(d.t_col + p)); };
-  auto pref = [&](int j) -> PreP<T> {
-    PreP<T> o;
-    o.xo = x[j].x;
-    o.c = d.c[j];
-    o.l = d.l[j];
-    o.u = d.u[j];
-    o.tw = IMPLICIT ? d.tw[j] : (T)1;
-    o.sx = pw != (T)0 ? d.sum_x[j] : (T)0;
-    return o;
+  auto val = [&](int p) -> T { return Ld<T, V>::get(d.t_val, p); };
+  auto term = [&](T v, int i) -> T { return v * y[i]; };
+  auto load = [&](int p) -> T { return term(val(p), __ldg(d.t_col + p)); };
+  auto pref_c = [&](int j) -> PreCP<T> {
+    return PreCP<T>{__ldg(d.c + j), __ldg(d.l + j), __ldg(d.u + j), IMPLICIT ? __ldg(d.tw + j) : (T)1};
   };
-  auto fin = [&](int j, T aty, const PreP<T>& o) {
-    const T g = o.c - aty;
-    const T step = IMPLICIT ? tau * o.tw : tau;
-    const T xv = clampv(o.xo - step * g, o.l, o.u);
-    const T dd = xv - o.xo;
-    vec2_t<T> v;
-    v.x = xv;
-    v.y = dd;
-    xn[j] = v;
-    if (pw != (T)0) d.sum_x[j] = o.sx + pw * o.xo;  // A7: add the iterate whose weight is pending
-    dx2 += IMPLICIT ? dd * dd / o.tw : dd * dd;
+  auto pref_v = [&](int j) -> PreVP<T> {
+    return PreVP<T>{x[j].x, pw != (T)0 ? d.sum_x[j] : (T)0};
   };
-  auto epi = [&](int j, T aty) { fin(j, aty, pref(j)); };
+  auto fin = [&](int j, T aty, const PreCP<T>& c, const PreVP<T>& v) {
+    const T g = c.c - aty;
+    const T step = IMPLICIT ? tau * c.tw : tau;
+    const T xv = clampv(v.xo - step * g, c.l, c.u);
+    const T dd = xv - v.xo;
+    vec2_t<T> o;
+    o.x = xv;
+    o.y = dd;
+    xn[j] = o;
+    if (pw != (T)0) d.sum_x[j] = v.sx + pw * v.xo;  // A7: add the iterate whose weight is pending
+    dx2 += IMPLICIT ? dd * dd / c.tw : dd * dd;
+  };
+  auto epi = [&](int j, T aty) { fin(j, aty, pref_c(j), pref_v(j)); };
   if constexpr (TILED) {
+    if (!enter()) return;
     rows_all<true, LANES, T>(sp, d.t_ptr, d.t_thresh, load, epi);
+  } else if (sp.bidx < sp.nshort) {
+    if (!rows_short2<LANES, T, PreCP<T>, PreVP<T>>(sp, d.t_ptr, d.t_col, d.t_thresh, val, term,
+                                                   pref_c, pref_v, fin, enter))
+      return;
   } else {
-    if (sp.bidx < sp.nshort)
-      rows_short2<LANES, T, PreP<T>>(sp, d.t_ptr, d.t_thresh, load, pref, fin);
-    else
-      rows_long<T>(sp, d.t_ptr, load, epi);
+    if (!enter()) return;
+    rows_long<T>(sp, d.t_ptr, load, epi);
   }
   const T s = block_sum1<T>(dx2);
   if (threadIdx.x == 0) d.part_p[blockIdx.x] = s;
@@ -396,109 +458,98 @@ __device__ __forceinline__ void store_step_state(DevState* g, const DevState& l)
 // ---------------------------------------------------------------- A5 + A6: dual
 template <int LANES, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, V> d) {
-  pdl_enter();
   constexpr bool TILED = std::is_same<T, double>::value;
   const Span sp = make_span(d.td, d.m, d.grid_d_short, d.a_long, d.a_nlong);
   DevState* st = d.st + sp.lp;
-  if (st->status != 0 || st->check_due) return;
-  const int cur = st->cur;
-  const vec2_t<T>* __restrict__ xn = cur ? d.x[0] : d.x[1];
-  const T* __restrict__ y = cur ? d.y[1] : d.y[0];
-  T* __restrict__ yn = cur ? d.y[0] : d.y[1];
-  const T sigma = StepT<T>::sigma(st);
-  const T pw = StepT<T>::pw(st);
-  // the state and this attempt's step-rule factors, taken at entry: if this
-  // block turns out to be the LP's last, its decision needs no further load
-  __shared__ DevState ls;
-  __shared__ T fac[2];
-  if (threadIdx.x == 0) {
-    ls = *st;
-    step_factors(&ls, ls.attempts + 1, &fac[0], &fac[1]);
-  }
+  const vec2_t<T>* xn = nullptr;
+  const T* y = nullptr;
+  T* yn = nullptr;
+  T sigma = 0, pw = 0;
+  auto enter = [&]() -> bool {
+    pdl_enter();
+    if (st->status != 0 || st->check_due) return false;
+    const int cur = st->cur;
+    xn = cur ? d.x[0] : d.x[1];
+    y = cur ? d.y[1] : d.y[0];
+    yn = cur ? d.y[0] : d.y[1];
+    sigma = StepT<T>::sigma(st);
+    pw = StepT<T>::pw(st);
+    return true;
+  };
   T dy2 = 0, dkd = 0;
   // acc.a = (K x')_i, acc.b = (K dx)_i
-  auto load = [&](int p) -> P2<T> {
-    const T v = Ld<T, V>::get(d.a_val, p);
-    const vec2_t<T> xv = xn[__ldg(d.a_col + p)];
+  auto val = [&](int p) -> T { return Ld<T, V>::get(d.a_val, p); };
+  auto term = [&](T v, int j) -> P2<T> {
+    const vec2_t<T> xv = xn[j];
     return P2<T>{v * xv.x, v * xv.y};
   };
-  auto pref = [&](int i) -> PreD<T> {
-    PreD<T> o;
-    o.yo = y[i];
-    o.q = d.q[i];
-    o.sw = IMPLICIT ? d.sw[i] : (T)1;
-    o.sy = pw != (T)0 ? d.sum_y[i] : (T)0;
-    o.kind = d.row_kind[i];
-    return o;
+  auto load = [&](int p) -> P2<T> { return term(val(p), __ldg(d.a_col + p)); };
+  auto pref_c = [&](int i) -> PreCD<T> {
+    return PreCD<T>{__ldg(d.q + i), IMPLICIT ? __ldg(d.sw + i) : (T)1, (int)__ldg(d.row_kind + i)};
   };
-  auto fin = [&](int i, P2<T> acc, const PreD<T>& o) {
+  auto pref_v = [&](int i) -> PreVD<T> {
+    return PreVD<T>{y[i], pw != (T)0 ? d.sum_y[i] : (T)0};
+  };
+  auto fin = [&](int i, P2<T> acc, const PreCD<T>& c, const PreVD<T>& v) {
     const T kxbar = acc.a + acc.b;  // K (2x' - x)
-    const T step = IMPLICIT ? sigma * o.sw : sigma;
-    T v = o.yo + step * (o.q - kxbar);
-    if (o.kind != 1) v = maxv(v, (T)0);
-    yn[i] = v;
-    if (pw != (T)0) d.sum_y[i] = o.sy + pw * o.yo;
-    const T dd = v - o.yo;
-    dy2 += IMPLICIT ? dd * dd / o.sw : dd * dd;
+    const T step = IMPLICIT ? sigma * c.sw : sigma;
+    T yv = v.yo + step * (c.q - kxbar);
+    if (c.kind != 1) yv = maxv(yv, (T)0);
+    yn[i] = yv;
+    if (pw != (T)0) d.sum_y[i] = v.sy + pw * v.yo;
+    const T dd = yv - v.yo;
+    dy2 += IMPLICIT ? dd * dd / c.sw : dd * dd;
     dkd += dd * acc.b;
   };
-  auto epi = [&](int i, P2<T> acc) { fin(i, acc, pref(i)); };
+  auto epi = [&](int i, P2<T> acc) { fin(i, acc, pref_c(i), pref_v(i)); };
   if constexpr (TILED) {
+    if (!enter()) return;
     rows_all<true, LANES, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
+  } else if (sp.bidx < sp.nshort) {
+    if (!rows_short2<LANES, P2<T>, PreCD<T>, PreVD<T>>(sp, d.a_ptr, d.a_col, d.a_thresh, val, term,
+                                                       pref_c, pref_v, fin, enter))
+      return;
   } else {
-    if (sp.bidx < sp.nshort)
-      rows_short2<LANES, P2<T>, PreD<T>>(sp, d.a_ptr, d.a_thresh, load, pref, fin);
-    else
-      rows_long<P2<T>>(sp, d.a_ptr, load, epi);
+    if (!enter()) return;
+    rows_long<P2<T>>(sp, d.a_ptr, load, epi);
   }
   const T s0 = block_sum1<T>(dy2);
   const T s1 = block_sum1<T>(dkd);
-  // Last-block detection in two levels, so that the blocks finishing together do
-  // not queue on one address: block b of the LP counts on group counter
-  // b % ng (ng = min(32, blocks), each on its own 32-byte sector); the last of
-  // a group resets it and counts on the LP's counter; the last of those decides.
-  __shared__ bool last;
   if (threadIdx.x == 0) {
     d.part_d[blockIdx.x] = s0;
     d.part_d[d.grid_d + blockIdx.x] = s1;
-    __threadfence();
-    const int ng = sp.nblk < kCountGroups ? sp.nblk : kCountGroups;
-    const int g = sp.bidx % ng;
-    const unsigned gsize = (unsigned)((sp.nblk - g + ng - 1) / ng);
-    unsigned* gc = d.cnt + ((size_t)sp.lp * kCountGroups + g) * 8;
-    bool top = false;
-    if (atomicAdd(gc, 1u) == gsize - 1) {
-      *gc = 0u;  // every member of the group has counted this attempt
-      __threadfence();
-      top = atomicAdd(&st->counter, 1u) == (unsigned)ng - 1;
-    }
-    last = top;
   }
-  __syncthreads();
-  if (!last) return;
-  if (st->dry) {  // shape tuning: the iterate and the state stay as they were
-    if (threadIdx.x == 0) st->counter = 0;
-    return;
-  }
-  __threadfence();
-  // this LP's partial slots: its primal blocks and its dual blocks
-  int p0 = 0, pn = d.grid_p;
+}
+
+// ---------------------------------------------------------------- A6: decision
+// One block per LP, launched after the dual kernel (programmatic dependent
+// launch: its blocks are resident before the dual kernel ends and start as soon
+// as its results are visible): the LP's partial sums of ||dx||^2, ||dy||^2 and
+// dy^T K dx in the order of their slots, then the step decision.  In dry mode
+// (launch-shape tuning) nothing is decided.
+template <typename T, typename V>
+__global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
+  pdl_enter();
+  const int k = blockIdx.x;
+  DevState* st = d.st + k;
+  if (st->status != 0 || st->check_due || st->dry) return;
+  int p0 = 0, pn = d.grid_p, q0 = 0, qn = d.grid_d;
   if (d.tp.blk_lp != nullptr) {
-    p0 = d.tp.blk0[sp.lp];
-    pn = d.tp.nblk[sp.lp];
+    p0 = d.tp.blk0[k];
+    pn = d.tp.nblk[k];
+    q0 = d.td.blk0[k];
+    qn = d.td.nblk[k];
   }
+  T fd = 0, fi = 0;
+  if (threadIdx.x == 0) step_factors(st, st->attempts + 1, &fd, &fi);  // issued early
   T a = 0, b0 = 0, b1 = 0;
-  for (int i = threadIdx.x; i < pn; i += kBlock) a += __ldcg(d.part_p + p0 + i);
-  for (int i = threadIdx.x; i < sp.nblk; i += kBlock) {
-    b0 += __ldcg(d.part_d + sp.part0 + i);
-    b1 += __ldcg(d.part_d + d.grid_d + sp.part0 + i);
+  for (int i = threadIdx.x; i < pn; i += kBlock) a += d.part_p[p0 + i];
+  for (int i = threadIdx.x; i < qn; i += kBlock) {
+    b0 += d.part_d[q0 + i];
+    b1 += d.part_d[d.grid_d + q0 + i];
   }
   block_sum3<T>(a, b0, b1);
-  if (threadIdx.x == 0) {
-    decide_step<T>(&ls, a, b0, b1, fac[0], fac[1]);
-    store_step_state(st, ls);
-    st->counter = 0;
-  }
+  if (threadIdx.x == 0) decide_step<T>(st, a, b0, b1, fd, fi);
 }
 
 // ---------------------------------------------------------------- persistent attempts

@@ -25,20 +25,42 @@ IterData<T, V> typed(const IterRaw& r) {
   }
   d.sum_x = (T*)r.sum_x; d.sum_y = (T*)r.sum_y;
   d.part_p = (T*)r.part_p; d.part_d = (T*)r.part_d;
-  d.cnt = r.cnt;
   d.grid_p_short = r.grid_p_short; d.grid_p = r.grid_p;
   d.grid_d_short = r.grid_d_short; d.grid_d = r.grid_d;
   d.st = r.st;
+  d.count = r.count;
   d.tp = r.tp;
   d.td = r.td;
   return d;
 }
 
+// The float32 primal kernel gathers y (4 bytes per row of A): ask for the
+// largest L1 (the kernel uses almost no shared memory) so that y stays cached
+// on the SM.  Set once per instantiation and device.
+template <typename K>
+cudaError_t prefer_l1(K kernel) {
+  static int done_dev = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || done_dev == dev) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  if (e == cudaSuccess) done_dev = dev;
+  return e;
+}
+
 template <int LANES, typename T, typename V, bool IMPLICIT>
 cudaError_t launch_one(int which, const IterData<T, V>& d, cudaStream_t s) {
+  if (which == IK_PRIMAL) {
+    const cudaError_t e = prefer_l1(k_primal<LANES, T, V, IMPLICIT>);
+    if (e != cudaSuccess) return e;
+  }
   switch (which) {
     case IK_PRIMAL: return launch_pdl(k_primal<LANES, T, V, IMPLICIT>, d.grid_p, kBlock, s, d);
-    case IK_DUAL: return launch_pdl(k_dual<LANES, T, V, IMPLICIT>, d.grid_d, kBlock, s, d);
+    case IK_DUAL: {  // the dual step, then the step decision of every LP
+      const cudaError_t e = launch_pdl(k_dual<LANES, T, V, IMPLICIT>, d.grid_d, kBlock, s, d);
+      if (e != cudaSuccess) return e;
+      return launch_pdl(k_decide<T, V>, d.count, kBlock, s, d);
+    }
     default: return cudaErrorInvalidValue;
   }
 }

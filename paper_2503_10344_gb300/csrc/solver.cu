@@ -90,7 +90,6 @@ struct Bufs {
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
   int *a_long, *t_long, *tmp, *flags2;
-  unsigned* cnt;  // group counters of the dual kernel (32 x 8 words)
   DevState* st;
 };
 
@@ -162,7 +161,6 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
                                    2 * (std::max(M, N) + 1) + scan_tmp_ints((long long)std::max(M, N) + 1));
   b.tmp = (int*)ar.take(4 * tmp_ints);
   b.flags2 = (int*)ar.take(16);
-  b.cnt = (unsigned*)ar.take(4 * 32 * 8);
   b.st = (DevState*)ar.take(sizeof(DevState));
   return ar.off + 256;
 }
@@ -216,7 +214,7 @@ struct Solve {
   }
 
   cudaError_t iter(int which) {
-    ++g_launches;
+    g_launches += which == IK_DUAL ? 2 : 1;  // the dual step is followed by the decision
     const int lanes = which == IK_PRIMAL ? lanes_t : lanes_a;
     switch (mode) {
       case MODE_FP64: return launch_iter_fp64(which, lanes, ir, s);
@@ -592,7 +590,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   ir.part_p = bf.part_p; ir.part_d = bf.part_d;
   ir.grid_p_short = gp_short; ir.grid_p = gp; ir.grid_d_short = gd_short; ir.grid_d = gd;
   ir.st = bf.st;
-  ir.cnt = bf.cnt;
+  ir.count = 1;
 
   KktRaw kr{};
   kr.count = 1;
@@ -666,7 +664,6 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     hs.tr_check_cap = dg->check_capacity;
   }
   CUDA_TRY(cudaMemcpyAsync(bf.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemsetAsync(bf.cnt, 0, 4 * 32 * 8, s));
   const size_t eb = fp32 ? 4 : 8;
   CUDA_TRY(cudaMemsetAsync(bf.sum_x, 0, eb * n, s));
   if (m) CUDA_TRY(cudaMemsetAsync(bf.sum_y, 0, eb * m, s));
@@ -1107,7 +1104,6 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     void *a_valit, *t_valit, *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
     unsigned char *row_kind, *bflags;
     DevState* st;
-    unsigned* cnt;
     FacTable* fac;
   } g{};
   // long rows and launch maps need the per-LP setups first: upper bounds here
@@ -1144,7 +1140,6 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.tabA = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.tabT = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.st = (DevState*)ar.take(sizeof(DevState) * count);
-    g.cnt = (unsigned*)ar.take(4 * 32 * 8 * (size_t)count);
     one.fac = nullptr;
   };
   Arena gdry{nullptr, 0};
@@ -1295,7 +1290,6 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     CUDA_TRY(cudaMemsetAsync(g.Xl, 0, 8 * N, s));
     if (M) CUDA_TRY(cudaMemsetAsync(g.Yl, 0, 8 * M, s));
     CUDA_TRY(cudaMemcpyAsync(g.st, hs.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(g.cnt, 0, 4 * 32 * 8 * (size_t)count, s));
     CUDA_TRY(cudaStreamSynchronize(s));
   }
   // ---- launch maps
@@ -1323,7 +1317,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   ir.part_p = g.part_p; ir.part_d = g.part_d;
   ir.grid_p_short = gridT; ir.grid_p = gridT; ir.grid_d_short = gridA; ir.grid_d = gridA;
   ir.st = g.st;
-  ir.cnt = g.cnt;
+  ir.count = count;
   ir.tp = tT;
   ir.td = tA;
   KktRaw kr{};
