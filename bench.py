@@ -297,6 +297,7 @@ def run_gpu(args):
                        "lanes": lane_params(args)},
             "time_to_tol_s": total_s / args.steps,
             "iters_per_solve": iters / args.steps,
+            "setup_ms": 1e3 * res["setup_s"], "iteration_phase_ms": 1e3 * res["solve_s"],
             "status": res["status"], "rel_kkt": res["rel_kkt"], "primal_obj": res["primal_obj"],
             "fp64_baseline": {"time_to_tol_s": sum(ms64) / 1e3 / len(ms64),
                               "iters_per_s": it64 / (sum(ms64) / 1e3),

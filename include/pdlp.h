@@ -112,7 +112,8 @@ typedef struct {
   int lanes_AT;         /* SpMV lanes per row of A^T in the step kernels (0 = automatic) */
   int lanes_kkt_A;      /* lanes per row of A in the float64 KKT pass (0 = automatic) */
   int lanes_kkt_AT;     /* lanes per row of A^T in the float64 KKT pass (0 = automatic) */
-  int verbose;          /* 0 quiet; 1 one line per KKT check on stderr */
+  int verbose;          /* 0 quiet; 1 one line per KKT check on stderr; 2 also the host-side
+                           time of each setup phase (synchronising the stream at each) */
   int persistent;       /* 1: the step attempts of a check period run in one cooperative
                            kernel with grid-wide barriers; 0 (default): two kernel launches
                            per attempt.  Same iteration either way; batches always use the
@@ -308,7 +309,9 @@ int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, const char* se
 #define FP_REDCOST 1  /* descending |reduced cost| */
 #define FP_DUAL 2     /* rows by descending |y|, their integers by descending |reduced cost| */
 #define FP_TYPE 3     /* binaries first, then general integers (stable) */
-#define FP_FEASIBLE 1    /* all integers fixed and the final LP feasible (rel. 1e-6) */
+#define FP_FEASIBLE 1    /* all integers fixed and the final LP's point satisfies every
+                            row to 1e-6 max(1, |b_i|) (solved at final_lp_tol, and once
+                            more at final_lp_tol / 100 from that point if a row misses) */
 #define FP_INFEASIBLE 2  /* search exhausted, root infeasible, or final LP infeasible: abort */
 #define FP_NODE_LIMIT 3  /* node limit reached */
 #define FP_NO_FINAL_LP 4 /* all integers fixed; final LP not requested */

@@ -270,6 +270,23 @@ void variable_order(const Problem& P, int strategy, const double* x_lp, const do
     if (!seen[j]) order.push_back(j);
 }
 
+// Largest row violation of x, each scaled by max(1, |b_i|) (the paper's
+// relative feasibility tolerance, section 4, read per row).
+double max_row_violation(const Problem& P, const double* x) {
+  double worst = 0.0;
+  for (int i = 0; i < P.m; ++i) {
+    double act = 0.0;
+    for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) act += P.val[p] * x[P.col[p]];
+    const double bi = P.b[i];
+    double v = 0.0;
+    if (P.sense[i] == 'L') v = act - bi;
+    else if (P.sense[i] == 'G') v = bi - act;
+    else v = fabs(act - bi);
+    worst = std::max(worst, v / std::max(1.0, fabs(bi)));
+  }
+  return worst;
+}
+
 int fp_fail(fp_result* r, int status) {
   r->status = status;
   r->obj = NAN;
@@ -401,19 +418,34 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     fl[j] = is_int[j] ? d.lo[j] : l[j];
     fu[j] = is_int[j] ? d.lo[j] : u[j];
   }
+  // The final point counts as feasible when every row holds to kFeasTol max(1, |b_i|).
+  // A first-order solution at final_lp_tol may miss a row by a little: then the
+  // LP is solved once more from that point at a hundred times tighter tolerance.
   pdlp_params pp;
   pdlp_default_params(&pp);
   pp.tol = prm->final_lp_tol;
   pdlp_result lr;
   const auto t1 = std::chrono::steady_clock::now();
-  const int rc = pdlp_solve(A, b, sense, c, fl.data(), fu.data(), &pp, nullptr, nullptr,
-                            xf.data(), yf.data(), &lr, nullptr);
-  r->lp_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+  int rc = pdlp_solve(A, b, sense, c, fl.data(), fu.data(), &pp, nullptr, nullptr, xf.data(),
+                      yf.data(), &lr, nullptr);
   if (rc != PDLP_OK) return rc;
-  r->final_lp_iters = lr.iters;
-  r->final_rel_primal = lr.rel_primal_res;
+  long long lp_iters = lr.iters;
   for (int j = 0; j < P.n; ++j) x_out[j] = is_int[j] ? d.lo[j] : xf[j];
-  if (lr.status != PDLP_OPTIMAL || lr.rel_primal_res > kFeasTol) return fp_fail(r, FP_INFEASIBLE);
+  double viol = max_row_violation(P, x_out);
+  if (lr.status == PDLP_OPTIMAL && viol > kFeasTol) {
+    std::vector<double> x0(xf), y0(yf);
+    pp.tol = prm->final_lp_tol * 1e-2;
+    rc = pdlp_solve(A, b, sense, c, fl.data(), fu.data(), &pp, x0.data(), y0.data(), xf.data(),
+                    yf.data(), &lr, nullptr);
+    if (rc != PDLP_OK) return rc;
+    lp_iters += lr.iters;
+    for (int j = 0; j < P.n; ++j) x_out[j] = is_int[j] ? d.lo[j] : xf[j];
+    viol = max_row_violation(P, x_out);
+  }
+  r->lp_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+  r->final_lp_iters = lp_iters;
+  r->final_rel_primal = lr.rel_primal_res;
+  if (lr.status != PDLP_OPTIMAL || viol > kFeasTol) return fp_fail(r, FP_INFEASIBLE);
   double obj = 0.0;
   for (int j = 0; j < P.n; ++j) obj += c[j] * x_out[j];
   r->status = FP_FEASIBLE;

@@ -523,16 +523,27 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
 
 // ---------------------------------------------------------------- A6: decision
 // One block per LP, launched after the dual kernel (programmatic dependent
-// launch: its blocks are resident before the dual kernel ends and start as soon
-// as its results are visible): the LP's partial sums of ||dx||^2, ||dy||^2 and
-// dy^T K dx in the order of their slots, then the step decision.  In dry mode
-// (launch-shape tuning) nothing is decided.
+// launch): the LP's partial sums of ||dx||^2, ||dy||^2 and dy^T K dx in the
+// order of their slots, then the step decision.  The state was last written by
+// the previous decision or KKT block, grids that completed before the primal
+// and dual kernels of this attempt began, so it is copied to shared memory, and
+// this attempt's step-rule factors looked up, BEFORE the wait; after it only
+// the partial sums are read.  In dry mode (launch-shape tuning) nothing is
+// decided.
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
-  pdl_enter();
+  __shared__ DevState ls;
+  __shared__ T fac[2];
   const int k = blockIdx.x;
   DevState* st = d.st + k;
-  if (st->status != 0 || st->check_due || st->dry) return;
+  if (threadIdx.x < 32) {  // warp 0 copies the state word by word
+    static_assert(sizeof(DevState) % 8 == 0, "state copied in 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(st);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ls);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / 8); w += 32) dst[w] = src[w];
+    __syncwarp();
+    if (threadIdx.x == 0) step_factors(&ls, ls.attempts + 1, &fac[0], &fac[1]);
+  }
   int p0 = 0, pn = d.grid_p, q0 = 0, qn = d.grid_d;
   if (d.tp.blk_lp != nullptr) {
     p0 = d.tp.blk0[k];
@@ -540,8 +551,9 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
     q0 = d.td.blk0[k];
     qn = d.td.nblk[k];
   }
-  T fd = 0, fi = 0;
-  if (threadIdx.x == 0) step_factors(st, st->attempts + 1, &fd, &fi);  // issued early
+  __syncthreads();
+  pdl_enter();
+  if (ls.status != 0 || ls.check_due || ls.dry) return;
   T a = 0, b0 = 0, b1 = 0;
   for (int i = threadIdx.x; i < pn; i += kBlock) a += d.part_p[p0 + i];
   for (int i = threadIdx.x; i < qn; i += kBlock) {
@@ -549,7 +561,10 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
     b1 += d.part_d[d.grid_d + q0 + i];
   }
   block_sum3<T>(a, b0, b1);
-  if (threadIdx.x == 0) decide_step<T>(st, a, b0, b1, fd, fi);
+  if (threadIdx.x == 0) {
+    decide_step<T>(&ls, a, b0, b1, fac[0], fac[1]);
+    store_step_state(st, ls);
+  }
 }
 
 // ---------------------------------------------------------------- persistent attempts

@@ -289,29 +289,60 @@ __global__ void k_finish_transpose(const int* a_ptr, int m, const double* a_val6
 // op 0 = max, op 1 = sum of |K~|^power.  In the A^T orientation the roles of
 // the two scale vectors swap (rowscale = dc, colscale = dr) but the product is
 // formed in the same order as in A: (dr_i |K_ij|) dc_j.
+// Row statistics of the scaled matrix D_own K D_other (one group of LANES lanes
+// per row): op 0 the max of |k~_ij|, op 1 the sum of |k~_ij|^power.  Float64
+// throughout (the scaling feeds the float64 parity mode); on GB300 a float64
+// warp instruction costs the FP64 pipe ~16 cycles whatever the active lanes,
+// so a short row gets few lanes instead of a whole warp.
+template <int LANES>
 __global__ void k_rowstat(const int* ptr, const int* col, const double* val, int nrows,
                           const double* own, const double* other, int own_is_row, int op,
                           double power, double* out) {
-  const int lane = threadIdx.x & 31;
-  const long long W = (long long)gridDim.x * blockDim.x / 32;
-  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < nrows; r += W) {
+  const int lane = threadIdx.x & (LANES - 1);
+  const long long G = (long long)gridDim.x * blockDim.x / LANES;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / LANES; r < nrows; r += G) {
     const int s = ptr[r], e = ptr[r + 1];
     const double so = own[r];
     double acc = 0.0;
-    for (int p = s + lane; p < e; p += 32) {
+    for (int p = s + lane; p < e; p += LANES) {
       const double a = fabs(val[p]);
       const double o = other[col[p]];
       const double kt = own_is_row ? (so * a) * o : (o * a) * so;
       if (op == 0) acc = fmax(acc, kt);
       else acc += power == 1.0 ? kt : pow(kt, power);
     }
+    const unsigned mask = LANES == 32 ? 0xffffffffu
+                                      : (((1u << LANES) - 1u) << ((threadIdx.x & 31) & ~(LANES - 1)));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double t = __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = LANES / 2; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(mask, acc, o);
       acc = op == 0 ? fmax(acc, t) : acc + t;
     }
     if (lane == 0) out[r] = acc;
   }
+}
+
+// lanes per row for an average row length (about four entries per lane)
+static int stat_lanes(double avg) {
+  int l = 2;
+  while (l < 32 && 4.0 * l < avg) l <<= 1;
+  return l;
+}
+
+static cudaError_t rowstat(const int* ptr, const int* col, const double* val, int nrows, long long nnz,
+                           const double* own, const double* other, int own_is_row, int op,
+                           double power, double* out, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  const int L = stat_lanes(nrows > 0 ? (double)nnz / nrows : 1.0);
+  const int g = grid_for((long long)nrows * L, G);
+  switch (L) {
+    case 2: k_rowstat<2><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
+    case 4: k_rowstat<4><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
+    case 8: k_rowstat<8><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
+    case 16: k_rowstat<16><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
+    default: k_rowstat<32><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
+  }
+  return cudaGetLastError();
 }
 
 __global__ void k_apply_scale(double* d, const double* stat, int nrows) {
@@ -686,24 +717,18 @@ cudaError_t setup_scaling(const ScaleIn& sc, double* dr, double* dc, double* sta
   RET(cudaGetLastError());
   k_fill<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, 1.0, sc.n);
   RET(cudaGetLastError());
-  const int gr = grid_for((long long)sc.m * 32, G), gc = grid_for((long long)sc.n * 32, G);
+  const long long znz = sc.nnz;
   for (int it = 0; it < sc.ruiz_iters; ++it) {
-    k_rowstat<<<gr, kBlock, 0, s>>>(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, dr, dc, 1, 0, 1.0, stat_r);
-    RET(cudaGetLastError());
-    k_rowstat<<<gc, kBlock, 0, s>>>(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, dc, dr, 0, 0, 1.0, stat_c);
-    RET(cudaGetLastError());
+    RET(rowstat(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, znz, dr, dc, 1, 0, 1.0, stat_r, s));
+    RET(rowstat(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, znz, dc, dr, 0, 0, 1.0, stat_c, s));
     k_apply_scale<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, stat_r, sc.m);
     RET(cudaGetLastError());
     k_apply_scale<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, stat_c, sc.n);
     RET(cudaGetLastError());
   }
   if (sc.pc_alpha >= 0.0) {
-    k_rowstat<<<gr, kBlock, 0, s>>>(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, dr, dc, 1, 1,
-                                    2.0 - sc.pc_alpha, stat_r);
-    RET(cudaGetLastError());
-    k_rowstat<<<gc, kBlock, 0, s>>>(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, dc, dr, 0, 1, sc.pc_alpha,
-                                    stat_c);
-    RET(cudaGetLastError());
+    RET(rowstat(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, znz, dr, dc, 1, 1, 2.0 - sc.pc_alpha, stat_r, s));
+    RET(rowstat(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, znz, dc, dr, 0, 1, sc.pc_alpha, stat_c, s));
     k_apply_scale<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, stat_r, sc.m);
     RET(cudaGetLastError());
     k_apply_scale<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, stat_c, sc.n);

@@ -27,6 +27,7 @@ struct ScaleIn {
   const double* t_val64;
   int ruiz_iters;
   double pc_alpha;  // < 0: no Pock-Chambolle pass
+  long long nnz;    // nonzeros (picks the lanes per row of the statistics passes)
 };
 
 struct VecIn {

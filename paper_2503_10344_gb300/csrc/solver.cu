@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -291,7 +292,8 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
                     const double* l, const double* u, const pdlp_params* p, const double* x0,
                     const double* y0, Bufs& bf, cudaStream_t s, bool no_alloc, int forced_mode,
                     const int* forced_lanes, SetupOut* so, const double* hx = nullptr,
-                    const double* hy = nullptr) {
+                    const double* hy = nullptr,
+                    const std::function<void(const char*)>& mark = [](const char*) {}) {
   const int m = A->m, n = A->n;
   const long long nnz = A->nnz;
   // ---- validation (A0 preconditions)
@@ -310,11 +312,13 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
     if (err & ERR_BOUNDS) msg += " bounds";
     return fail(PDLP_ERR_INVALID_INPUT, msg);
   }
+  mark("validate");
   // ---- A0, A1
   CUDA_TRY(setup_canonical(in, bf.a_ptr, bf.a_col, bf.a_val64, bf.q64, bf.row_kind, s));
   CUDA_TRY(setup_transpose(m, n, (int)nnz, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col,
                            bf.t_val64, bf.tmp, s, no_alloc));
   g_launches += 10;
+  mark("canonical + transpose");
   // ---- mode
   Mode mode = MODE_FP64;
   int bf16_exact = 0, all_one = 0;
@@ -330,9 +334,11 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   const int fp32 = mode != MODE_FP64;
   // ---- A2
   ScaleIn sc{m, n, bf.a_ptr, bf.a_col, bf.a_val64, bf.t_ptr, bf.t_col, bf.t_val64, p->ruiz_iters,
-             p->pc_alpha};
+             p->pc_alpha, nnz};
+  mark("value format");
   CUDA_TRY(setup_scaling(sc, bf.dr, bf.dc, bf.stat_r, bf.stat_c, s));
   g_launches += 2 + 4 * p->ruiz_iters + (p->pc_alpha >= 0 ? 4 : 0);
+  mark("Ruiz + Pock-Chambolle");
   CUDA_TRY(setup_kkt_aux(m, n, bf.dr, bf.dc, l, u, bf.inv_dr, bf.inv_dc, bf.bflags, s));
   ++g_launches;
   if (mode != MODE_PAT) {
@@ -349,6 +355,7 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   g_launches += 3;
   double sca[7];
   CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
+  mark("iteration values + vectors");
   // ---- launch shapes and long rows
   const double avg_a = m ? (double)nnz / m : 1.0, avg_t = (double)nnz / n;
   const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
@@ -388,6 +395,46 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   so->nlong_a = nlong_a;
   so->nlong_t = nlong_t;
   return PDLP_OK;
+}
+
+// ---------------------------------------------------------------- graph cache
+// The CUDA graph of one check period captures the launch parameters by value
+// (workspace pointers, grids, lanes, mode), so a caller that solves again into
+// the same workspace with the same shape can relaunch the same executable
+// graph.  Keyed by the bytes of those parameters and the device; a few entries,
+// least recently used first out; never destroyed at process exit (the CUDA
+// context may be gone by then).
+struct GraphKey {
+  int dev, mode, lanes[4], period, persist;
+  IterRaw ir;
+  KktRaw kr;
+  bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  long long nodes;
+  unsigned long long used;
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry>* g_graphs = new std::vector<GraphEntry>();
+static unsigned long long g_graph_clock = 0;
+constexpr size_t kGraphCacheSize = 8;
+
+static GraphKey graph_key(const Solve& sv, int period) {
+  GraphKey k;
+  memset(&k, 0, sizeof(k));  // padding bytes take part in the comparison
+  cudaGetDevice(&k.dev);
+  k.mode = (int)sv.mode;
+  k.lanes[0] = sv.lanes_a;
+  k.lanes[1] = sv.lanes_t;
+  k.lanes[2] = sv.lanes_ka;
+  k.lanes[3] = sv.lanes_kt;
+  k.period = period;
+  k.persist = sv.persist_grid;
+  memcpy(&k.ir, &sv.ir, sizeof(IterRaw));
+  memcpy(&k.kr, &sv.kr, sizeof(KktRaw));
+  return k;
 }
 
 // ---------------------------------------------------------------- launch-shape autotuner
@@ -547,12 +594,24 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   auto h0 = std::chrono::steady_clock::now(), h1 = h0, h2 = h0;
   if (!no_alloc) CUDA_TRY(cudaEventRecord(e0, s));
 
+  // verbose >= 2: host-side phase times (the stream is synchronised at each mark)
+  auto tmark = std::chrono::steady_clock::now();
+  auto phase = [&](const char* what) {
+    if (p->verbose < 2) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "pdlp: %-28s %9.3f ms\n", what,
+            1e3 * std::chrono::duration<double>(now - tmark).count());
+    tmark = now;
+  };
+  phase("workspace");
   SetupOut so;
   {
     const int rc = setup_lp(A, b, sense, c, l, u, p, x0, y0, bf, s, no_alloc, -1, nullptr, &so, hx,
-                            hy);
+                            hy, phase);
     if (rc) return rc;
   }
+  phase("long rows + scalars");
   const Mode mode = so.mode;
   const int scaled = so.scaled, fp32 = so.fp32;
   const double* sca = so.sca;
@@ -706,7 +765,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     if (g > 4 * device_sm_count()) return fail(PDLP_ERR_CUDA, "persistent grid larger than its partial buffers");
     sv.persist_grid = g;
   }
+  phase("state, tuning, probe");
   CUDA_TRY(sv.kkt_block());  // initial KKT and restart anchors
+  phase("initial KKT");
   if (!no_alloc) {
     CUDA_TRY(cudaEventRecord(e1, s));
   } else {
@@ -759,7 +820,20 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   } ev2{ev};
   cudaGraphExec_t gexec = nullptr;
   long long graph_nodes = 0;
+  bool cached = false;
+  const GraphKey gkey = graph_key(sv, p->check_period);
   if (p->iter_limit > 0) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (GraphEntry& e : *g_graphs)
+      if (e.key == gkey) {
+        gexec = e.exec;
+        graph_nodes = e.nodes;
+        e.used = ++g_graph_clock;
+        cached = true;
+        break;
+      }
+  }
+  if (p->iter_limit > 0 && !cached) {
     cudaStream_t cs;
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     Solve cap = sv;
@@ -778,13 +852,16 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
     cudaGraphDestroy(graph);
     CUDA_TRY(ie);
-  }
-  struct GraphFree {
-    cudaGraphExec_t g;
-    ~GraphFree() {
-      if (g) cudaGraphExecDestroy(g);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    if (g_graphs->size() >= kGraphCacheSize) {
+      auto old = std::min_element(g_graphs->begin(), g_graphs->end(),
+                                  [](const GraphEntry& a, const GraphEntry& b) { return a.used < b.used; });
+      cudaGraphExecDestroy(old->exec);
+      g_graphs->erase(old);
     }
-  } gfree{gexec};
+    g_graphs->push_back(GraphEntry{gkey, gexec, graph_nodes, ++g_graph_clock});
+  }
+  phase("graph capture + instantiate");
 
   const auto t_start = std::chrono::steady_clock::now();
   long long launched = 0, seen = 0;
@@ -828,6 +905,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   }
   (void)host_status;
   CUDA_TRY(cudaStreamSynchronize(s));  // drain the chunk launched behind the terminating one
+  phase("iterations");
   CUDA_TRY(cudaEventRecord(e2, s));
   }  // graph-driven iteration phase
   // ---- A11: outputs
