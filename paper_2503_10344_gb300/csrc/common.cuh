@@ -56,6 +56,7 @@ struct DevState {
   int used_avg;          // output candidate of the last check
   int force_final;       // host asked for a final check (time limit)
   int dry;               // 1: step kernels run but the decision is skipped (launch-shape tuning)
+  int loop_attempts;     // attempts since the start of the current check-period graph
   long long last_restart_it;
   double last_rp2, last_rd2, last_gap2;  // scaled KKT triple of the last restart point
   double prev_cand;                      // KKT_omega of the previous candidate (inf after restart)

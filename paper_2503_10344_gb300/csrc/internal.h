@@ -28,6 +28,8 @@ struct IterRaw {
   int grid_p_short, grid_p, grid_d_short, grid_d;
   DevState* st;  // [count]
   int count;     // LPs (1 for a single LP)
+  unsigned long long cond;  // while-loop handle of the check-period graph (0: none)
+  int loop_cap;             // attempts per graph launch at most (with cond)
   Tables tp, td; // batch tables over A^T and A (all NULL for one LP)
 };
 

@@ -80,6 +80,8 @@ struct IterData {
   int grid_p_short, grid_p, grid_d_short, grid_d;
   DevState* st;                                        // [count] (one per LP)
   int count;                                           // LPs (1 for a single LP)
+  unsigned long long cond;                             // while-loop handle of the graph (0: none)
+  int loop_cap;                                        // attempts per graph launch at most
   Tables tp, td;                                       // batch tables over A^T / A (NULL: one LP)
 };
 
@@ -553,7 +555,11 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
   }
   __syncthreads();
   pdl_enter();
-  if (ls.status != 0 || ls.check_due || ls.dry) return;
+  if (ls.status != 0 || ls.check_due || ls.dry) {
+    // inside a graph's while loop: nothing left to step in this check period
+    if (d.cond && k == 0 && threadIdx.x == 0) cudaGraphSetConditional(d.cond, 0u);
+    return;
+  }
   T a = 0, b0 = 0, b1 = 0;
   for (int i = threadIdx.x; i < pn; i += kBlock) a += d.part_p[p0 + i];
   for (int i = threadIdx.x; i < qn; i += kBlock) {
@@ -564,6 +570,14 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
   if (threadIdx.x == 0) {
     decide_step<T>(&ls, a, b0, b1, fac[0], fac[1]);
     store_step_state(st, ls);
+    if (d.cond && k == 0) {
+      // one LP in a graph with a while loop: keep stepping until a KKT check falls
+      // due, the solve stops, or this graph launch has run loop_cap attempts
+      const int la = ls.loop_attempts + 1;
+      st->loop_attempts = la;
+      cudaGraphSetConditional(d.cond,
+                              (ls.status == 0 && !ls.check_due && la < d.loop_cap) ? 1u : 0u);
+    }
   }
 }
 

@@ -29,6 +29,8 @@ IterData<T, V> typed(const IterRaw& r) {
   d.grid_d_short = r.grid_d_short; d.grid_d = r.grid_d;
   d.st = r.st;
   d.count = r.count;
+  d.cond = r.cond;
+  d.loop_cap = r.loop_cap;
   d.tp = r.tp;
   d.td = r.td;
   return d;

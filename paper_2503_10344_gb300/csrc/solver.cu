@@ -836,17 +836,71 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   if (p->iter_limit > 0 && !cached) {
     cudaStream_t cs;
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct SFree {
+      cudaStream_t s;
+      ~SFree() { cudaStreamDestroy(s); }
+    } csfree{cs};
     Solve cap = sv;
     cap.s = cs;
     const long long before = g_launches;
     cudaGraph_t graph;
-    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cap.period_steps(p->check_period);
-    if (ce == cudaSuccess) ce = cap.kkt_block();
-    cudaError_t ee = cudaStreamEndCapture(cs, &graph);
-    cudaStreamDestroy(cs);
-    if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
-    CUDA_TRY(ee);
+    if (sv.persist_grid > 0) {
+      CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cap.period_steps(p->check_period);
+      if (ce == cudaSuccess) ce = cap.kkt_block();
+      cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+      if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+      CUDA_TRY(ee);
+    } else {
+      // One check period: reset the attempt counter, then a while loop whose body is
+      // one step attempt (primal, dual, decision) and whose condition the decision
+      // kernel sets (go on until the KKT check falls due), then the KKT block.  No
+      // launch is spent on attempts after the check fell due.
+      CUDA_TRY(cudaGraphCreate(&graph, 0));
+      struct GDestroy {
+        cudaGraph_t g;
+        bool keep;
+        ~GDestroy() {
+          if (!keep) cudaGraphDestroy(g);
+        }
+      } gd{graph, false};
+      cudaGraphConditionalHandle cond;
+      CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+      cudaMemsetParams mp = {};
+      mp.dst = &bf.st->loop_attempts;
+      mp.value = 0;
+      mp.elementSize = sizeof(int);
+      mp.width = 1;
+      mp.height = 1;
+      cudaGraphNode_t reset;
+      CUDA_TRY(cudaGraphAddMemsetNode(&reset, graph, nullptr, 0, &mp));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t loop;
+      CUDA_TRY(cudaGraphAddNode(&loop, graph, &reset, nullptr, 1, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      cap.ir.cond = cond;
+      cap.ir.loop_cap = 4 * p->check_period;
+      CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cap.iter(IK_PRIMAL);
+      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
+      cudaGraph_t body_out = body;
+      cudaError_t ee = cudaStreamEndCapture(cs, &body_out);
+      if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+      CUDA_TRY(ee);
+      CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, graph, &loop, nullptr, 1,
+                                             cudaStreamCaptureModeThreadLocal));
+      ce = cap.kkt_block();
+      cudaGraph_t main_out = graph;
+      ee = cudaStreamEndCapture(cs, &main_out);
+      if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+      CUDA_TRY(ee);
+      gd.keep = true;
+    }
     graph_nodes = g_launches - before;
     g_launches = before;
     cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
@@ -950,6 +1004,10 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   r->omega = fs.omega;
   r->setup_s = ms_setup * 1e-3;
   r->solve_s = ms_solve * 1e-3;
+  // the while-loop graph was counted with one attempt per launch; its other
+  // attempts ran as further iterations of the loop body (three kernels each)
+  if (!no_alloc && sv.persist_grid == 0 && p->iter_limit > 0)
+    g_launches += 3 * std::max(0LL, fs.attempts - fs.checks);
   r->kernel_launches = g_launches;
   return PDLP_OK;
 }
