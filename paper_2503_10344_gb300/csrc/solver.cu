@@ -95,6 +95,7 @@ struct Bufs {
 };
 
 constexpr int kMaxLongBlocks = 1024;
+constexpr int kAttemptsPerBody = 8;  // step attempts per iteration of the graph's while loop
 
 static int max_blocks() { return device_sm_count() * 8; }
 
@@ -853,9 +854,11 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       CUDA_TRY(ee);
     } else {
       // One check period: reset the attempt counter, then a while loop whose body is
-      // one step attempt (primal, dual, decision) and whose condition the decision
-      // kernel sets (go on until the KKT check falls due), then the KKT block.  No
-      // launch is spent on attempts after the check fell due.
+      // kAttemptsPerBody step attempts (primal, dual, decision; dependent launches
+      // between them) and whose condition the decision kernels set (go on until the
+      // KKT check falls due), then the KKT block.  A body boundary costs a full
+      // dependency, so a body holds several attempts; after the check falls due the
+      // rest of the body returns at kernel entry.
       CUDA_TRY(cudaGraphCreate(&graph, 0));
       struct GDestroy {
         cudaGraph_t g;
@@ -886,8 +889,11 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       cap.ir.loop_cap = 4 * p->check_period;
       CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
-      cudaError_t ce = cap.iter(IK_PRIMAL);
-      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
+      cudaError_t ce = cudaSuccess;
+      for (int a = 0; a < kAttemptsPerBody && ce == cudaSuccess; ++a) {
+        ce = cap.iter(IK_PRIMAL);
+        if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
+      }
       cudaGraph_t body_out = body;
       cudaError_t ee = cudaStreamEndCapture(cs, &body_out);
       if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
@@ -1007,7 +1013,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   // the while-loop graph was counted with one attempt per launch; its other
   // attempts ran as further iterations of the loop body (three kernels each)
   if (!no_alloc && sv.persist_grid == 0 && p->iter_limit > 0)
-    g_launches += 3 * std::max(0LL, fs.attempts - fs.checks);
+    g_launches += 3LL * kAttemptsPerBody *
+                  std::max(0LL, (fs.attempts + kAttemptsPerBody - 1) / kAttemptsPerBody - fs.checks);
   r->kernel_launches = g_launches;
   return PDLP_OK;
 }
