@@ -209,6 +209,63 @@ def set_cover_fixed(seed: int, m: int, n: int | None = None) -> LP:
                fixed_fraction=float(frac))
 
 
+def set_cover_dead(seed: int, m: int, n: int | None = None, dead: int = 1) -> LP:
+    """An infeasible covering sub-LP: ``set_cover_fixed`` whose fixings leave
+    ``dead`` rows with every column fixed to 0 (the conflict fix-and-propagate
+    runs into when its fixings contradict a covering row)."""
+    lp = set_cover_fixed(seed, m, n)
+    rng = np.random.default_rng(seed + 7919)
+    rows = np.repeat(np.arange(lp.m), np.diff(lp.row_ptr))
+    u = lp.u.copy()
+    l = lp.l.copy()
+    for i in rng.choice(lp.m, size=dead, replace=False):
+        js = lp.col[lp.row_ptr[i]:lp.row_ptr[i + 1]]
+        l[js] = 0.0
+        u[js] = 0.0
+    return _lp(lp.m, lp.n, rows, lp.col, lp.val, lp.b, lp.sense, lp.c, l, u, lp.is_int,
+               f"set_cover_dead(seed={seed},m={lp.m},dead={dead})")
+
+
+def mip_relaxation_contradiction(seed: int = 1, m: int = 200, n: int = 400,
+                                 density: float = 0.02) -> LP:
+    """An infeasible LP: ``mip_relaxation`` plus one >=-row that repeats the
+    pattern and values of a random non-empty row r with right-hand side
+    b_r + U[1,3], so that row r and the new row cannot both hold."""
+    lp = mip_relaxation(seed, m, n, density)
+    rng = np.random.default_rng(seed + 104729)
+    nz = np.nonzero(np.diff(lp.row_ptr) > 0)[0]
+    r = int(rng.choice(nz))
+    rows = np.repeat(np.arange(lp.m), np.diff(lp.row_ptr))
+    seg = slice(lp.row_ptr[r], lp.row_ptr[r + 1])
+    rows = np.concatenate([rows, np.full(seg.stop - seg.start, lp.m)])
+    cols = np.concatenate([lp.col, lp.col[seg]])
+    vals = np.concatenate([lp.val, lp.val[seg]])
+    b = np.append(lp.b, lp.b[r] + rng.uniform(1.0, 3.0))
+    sense = np.append(lp.sense, SENSE_GE)
+    return _lp(lp.m + 1, lp.n, rows, cols, vals, b, sense, lp.c, lp.l, lp.u, lp.is_int,
+               f"mip_relaxation_contradiction(seed={seed},m={m},n={n})", row=r)
+
+
+def mip_relaxation_unbounded(seed: int = 1, m: int = 200, n: int = 400, density: float = 0.02,
+                             rays: int = 3) -> LP:
+    """An unbounded LP: ``mip_relaxation`` where ``rays`` continuous columns
+    lose their upper bound, get cost -U[0.5,1] and nonpositive coefficients
+    (every <=-row stays satisfied as they grow, so each is a ray of descent)."""
+    lp = mip_relaxation(seed, m, n, density)
+    rng = np.random.default_rng(seed + 15485863)
+    js = rng.choice(np.arange(n // 2, n), size=rays, replace=False)
+    rows = np.repeat(np.arange(lp.m), np.diff(lp.row_ptr))
+    vals = lp.val.copy()
+    hit = np.isin(lp.col, js)
+    vals[hit] = -np.abs(vals[hit])
+    u = lp.u.copy()
+    c = lp.c.copy()
+    u[js] = np.inf
+    c[js] = -rng.uniform(0.5, 1.0, size=rays)
+    return _lp(lp.m, lp.n, rows, lp.col, vals, lp.b, lp.sense, c, lp.l, u, lp.is_int,
+               f"mip_relaxation_unbounded(seed={seed},m={m},n={n})", ray_cols=js)
+
+
 def set_cover_batch(count: int = 256, seed0: int = 4000, mmin: int = 2_000,
                     mmax: int = 40_000) -> list[LP]:
     """``count`` uneven covering sub-LPs, m ~ U[mmin, mmax], n = 4m, seeds seed0.."""

@@ -37,6 +37,27 @@ are listed one by one in the design notes and marked "reading" here:
       KKT_omega = sqrt(omega ||r_p~||^2 + ||r_d~||^2 / omega + gap^2).
   A10 primal weight omega <- exp(0.5 ln(dy/dx) + 0.5 ln omega) on restart.
   A11 stop when min(relKKT(current), relKKT(average)) <= tol; unscale.
+  A12 infeasibility certificates (PDLP's test on iterate differences; the
+      paper only says FP aborts when the LP is infeasible, section 2, so
+      every detail is a reading): at each check, after the tolerance test,
+      take the unscaled displacement since the last restart anchor,
+      dx = x - x_last and dy = y - y_last (the points as A11 returns them).
+      Dual ray y^ = proj_Y(dy), lambda^ = -K^T y^,
+        d^ = q^T y^ + sum_{l finite} l lambda^+ - sum_{u finite} u lambda^-,
+        r^_d = lambda^+ [l = -inf] + lambda^- [u = +inf];
+      primal infeasible iff d^ > kappa |d^|_terms and ||r^_d|| <= eps d^
+      (Farkas: no x in [l,u] with Kx >= q exists when r^_d = 0 and d^ > 0).
+      Primal ray x^ = dx projected onto the recession cone of [l, u]
+      (0 where both bounds are finite, dx+ where only l is, dx- where only u
+      is), r^_p,i = max(0, -(Kx^)_i) on >=-rows, |(Kx^)_i| on =-rows,
+        p^ = c^T x^;
+      dual infeasible iff -p^ > kappa |p^|_terms and ||r^_p|| <= eps (-p^).
+      eps = 1e-8; |.|_terms is the sum of the magnitudes of the terms the
+      objective adds up, and kappa = 1e-9 keeps an objective that is zero up
+      to rounding (a feasible LP whose ray objective is exactly 0) from
+      passing.  The primal test is taken first.  The certificate is returned
+      in place of the dual (primal infeasible) or primal (dual infeasible)
+      output.
 
 Part I (the definition every result is judged by): for a point x in [l,u] and
 y in Y of the canonical problem,
@@ -64,6 +85,8 @@ SENSE_LE, SENSE_GE, SENSE_EQ = ord("L"), ord("G"), ord("E")
 STATUS_OPTIMAL = 1
 STATUS_ITER_LIMIT = 2
 STATUS_TIME_LIMIT = 3
+STATUS_PRIMAL_INFEASIBLE = 5
+STATUS_DUAL_INFEASIBLE = 6
 
 
 # ---------------------------------------------------------------- A0 -------
@@ -196,6 +219,8 @@ class Params:
     beta_art: float = 0.36
     omega_smooth: float = 0.5
     omega_hint: object = None       # (x_h, y_h) caller convention: omega0 from their scaled norms
+    detect_infeasibility: bool = True  # A12 (only where terminate is set)
+    eps_infeasible: float = 1e-8
     # replay: step size and accept flag of every attempt taken from another run's
     # decision trace (eta_bar and all restart decisions are still computed here)
     replay_eta: object = None
@@ -222,6 +247,54 @@ class Result:
     trace: list = field(default_factory=list)
     attempt_trace: list = field(default_factory=list)  # (eta, eta_bar, accepted) per attempt
     check_trace: list = field(default_factory=list)    # (restart kind, omega after) per check
+    rays: list = field(default_factory=list)           # Rays of every check (A12)
+
+
+@dataclass
+class Rays:
+    """A12: the two candidate certificates of one check, unscaled, canonical signs."""
+    x_ray: np.ndarray
+    y_ray: np.ndarray
+    dual_ray_obj: float     # d^
+    dual_ray_res: float     # ||r^_d||
+    dual_ray_abs: float     # sum of |terms| of d^
+    primal_ray_obj: float   # p^
+    primal_ray_res: float   # ||r^_p||
+    primal_ray_abs: float   # sum of |c_j x^_j|
+
+    def primal_infeasible(self, eps, kappa=1e-9):
+        d = self.dual_ray_obj
+        return d > 0 and d > kappa * self.dual_ray_abs and self.dual_ray_res <= eps * d
+
+    def dual_infeasible(self, eps, kappa=1e-9):
+        p = -self.primal_ray_obj
+        return p > 0 and p > kappa * self.primal_ray_abs and self.primal_ray_res <= eps * p
+
+
+def recession_proj(dx, l, u):
+    """Projection onto the recession cone of [l, u]: {d : d_j >= 0 where l_j is
+    finite, d_j <= 0 where u_j is finite}."""
+    d = np.where(np.isfinite(l), np.maximum(dx, 0.0), dx)
+    return np.where(np.isfinite(u), np.minimum(d, 0.0), d)
+
+
+def rays_canonical(k, q, is_eq, c, l, u, dx, dy) -> Rays:
+    """A12 on the canonical LP from the displacements (dx, dy)."""
+    y_ray = proj_dual(dy, is_eq)
+    lam = -(k.T @ y_ray)
+    lp_ = np.maximum(lam, 0.0)
+    lm = np.maximum(-lam, 0.0)
+    r_d = np.where(np.isinf(l), lp_, 0.0) + np.where(np.isinf(u), lm, 0.0)
+    lfin = np.isfinite(l)
+    ufin = np.isfinite(u)
+    d_obj = float(q @ y_ray + l[lfin] @ lp_[lfin] - u[ufin] @ lm[ufin])
+    d_abs = float(np.abs(q) @ np.abs(y_ray) + np.abs(l[lfin]) @ lp_[lfin]
+                  + np.abs(u[ufin]) @ lm[ufin])
+    x_ray = recession_proj(dx, l, u)
+    kx = k @ x_ray
+    r_p = np.where(is_eq, np.abs(kx), np.maximum(-kx, 0.0))
+    return Rays(x_ray, y_ray, d_obj, float(np.linalg.norm(r_d)), d_abs,
+                float(c @ x_ray), float(np.linalg.norm(r_p)), float(np.abs(c) @ np.abs(x_ray)))
 
 
 def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
@@ -291,6 +364,12 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
 
     attempt_trace = []
     check_trace = []
+    rays = []
+    cert = None
+
+    def unscaled_point(xs, ys):
+        return proj_box(dc * xs, lp.l, lp.u), dr * ys
+
     while it < p.iter_limit:
         attempts += 1
         if p.replay_eta is not None:
@@ -339,6 +418,20 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                 status = STATUS_OPTIMAL
                 check_trace.append((0, omega))
                 break
+            # A12
+            xu, yu = unscaled_point(x, y)
+            xl, yl = unscaled_point(x_last, y_last)
+            ry = rays_canonical(k, q, is_eq, lp.c, lp.l, lp.u, xu - xl, yu - yl)
+            rays.append(ry)
+            if p.terminate and p.detect_infeasibility:
+                if ry.primal_infeasible(p.eps_infeasible):
+                    status = STATUS_PRIMAL_INFEASIBLE
+                elif ry.dual_infeasible(p.eps_infeasible):
+                    status = STATUS_DUAL_INFEASIBLE
+                if status != STATUS_ITER_LIMIT:
+                    cert = ry
+                    check_trace.append((0, omega))
+                    break
             if time.perf_counter() - t0 > p.time_limit_s:
                 status = STATUS_TIME_LIMIT
                 check_trace.append((0, omega))
@@ -396,8 +489,13 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
         # A11: y = D_r y~, then back to the caller's sign convention
         return s * (dr * ys)
 
+    x_out, y_out = unscale_x(xo), unscale_y(yo)
+    if status == STATUS_PRIMAL_INFEASIBLE:
+        y_out = s * cert.y_ray     # the Farkas ray, caller's sign convention
+    elif status == STATUS_DUAL_INFEASIBLE:
+        x_out = cert.x_ray
     return Result(status, it, attempts, restarts,
-                  unscale_x(xo), unscale_y(yo), chosen_kkt,
+                  x_out, y_out, chosen_kkt,
                   unscale_x(x), unscale_y(y), unscale_x(xa), unscale_y(ya),
                   eta, omega, chosen_avg, time.perf_counter() - t0, trace, attempt_trace,
-                  check_trace)
+                  check_trace, rays)
