@@ -65,6 +65,21 @@ extern "C" {
 #define PDLP_ITER_LIMIT 2   /* iter_limit accepted iterations reached */
 #define PDLP_TIME_LIMIT 3   /* time_limit_s reached */
 #define PDLP_NUMERICAL 4    /* a NaN / Inf appeared in the iteration */
+/* Certificates (pdlp_params.detect_infeasibility).  The paper's heuristic stops
+ * when an LP has no solution (section 2); the test is PDLP's, on the movement of
+ * the iterate since the last restart, at each KKT check after the tolerance test:
+ * y^ = that movement of y projected onto the dual cone, lambda^ = -A^T y^ (in the
+ * >=-form), d^ = b^T y^ plus the finite-bound terms of lambda^; x^ = that movement
+ * of x projected onto the recession cone of [l, u]. */
+#define PDLP_PRIMAL_INFEASIBLE 5 /* d^ > 0 (beyond the rounding of its terms: d^ >
+                                    1e-9 x the sum of their magnitudes) and the part of
+                                    lambda^ against infinite bounds has 2-norm <= 1e-8 d^:
+                                    no x satisfies the rows within [l, u].  y_out holds
+                                    y^ in the caller's sign convention (Farkas ray) */
+#define PDLP_DUAL_INFEASIBLE 6   /* c^T x^ < 0 beyond rounding and the rows' violation by
+                                    x^ (max(0, -(Kx^)_i) on inequalities, |(Kx^)_i| on
+                                    equalities) has 2-norm <= 1e-8 |c^T x^|: the LP is
+                                    unbounded if it is feasible.  x_out holds x^ */
 
 /* ---- precision modes (pdlp_params.precision) -------------------------
  * PDLP_FP64:      iterates, SpMV and reductions in float64 on the explicitly
@@ -123,10 +138,14 @@ typedef struct {
                            moving the iterate) and keep the fastest; cached per (device,
                            precision mode, m, n, nnz) for the process.  Lanes set explicitly
                            in lanes_A / lanes_AT are kept.  0 (default): size heuristic. */
+  int detect_infeasibility; /* 1 (default): test the two certificates above at each KKT
+                           check (with terminate = 1); 0: never (an infeasible LP runs to
+                           its iteration or time limit) */
 } pdlp_params;
 
 typedef struct {
-  int status;             /* PDLP_OPTIMAL, PDLP_ITER_LIMIT, PDLP_TIME_LIMIT, PDLP_NUMERICAL */
+  int status;             /* PDLP_OPTIMAL, PDLP_ITER_LIMIT, PDLP_TIME_LIMIT, PDLP_NUMERICAL,
+                             PDLP_PRIMAL_INFEASIBLE, PDLP_DUAL_INFEASIBLE */
   int precision_used;     /* PDLP_FP64, PDLP_FP32, PDLP_USED_BF16 or PDLP_USED_PATTERN */
   int64_t iters;          /* accepted PDHG iterations */
   int64_t attempts;       /* step attempts, rejected ones included */
@@ -140,6 +159,9 @@ typedef struct {
   double setup_s;         /* device setup: canonical form, transpose, scaling */
   double solve_s;         /* iteration phase, from the first step to termination */
   int lanes_A, lanes_AT;  /* lanes per row the step kernels used over A and A^T */
+  double ray_obj;         /* certificate statuses: d^ (PRIMAL_INFEASIBLE) or c^T x^
+                             (DUAL_INFEASIBLE); NaN otherwise */
+  double ray_res;         /* the 2-norm of the certificate's residual; NaN otherwise */
 } pdlp_result;
 
 /* Optional diagnostic outputs (same memory space as the entry point's outputs;

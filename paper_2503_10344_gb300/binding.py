@@ -22,6 +22,7 @@ PDLP_OK = 0
 ERRORS = {-1: "PDLP_ERR_INVALID_INPUT", -2: "PDLP_ERR_CUDA", -3: "PDLP_ERR_OOM",
           -4: "PDLP_ERR_TIMEOUT", -5: "PDLP_ERR_UNSUPPORTED"}
 PDLP_OPTIMAL, PDLP_ITER_LIMIT, PDLP_TIME_LIMIT, PDLP_NUMERICAL = 1, 2, 3, 4
+PDLP_PRIMAL_INFEASIBLE, PDLP_DUAL_INFEASIBLE = 5, 6
 PDLP_FP64, PDLP_FP32, PDLP_FP32_BF16A = 0, 1, 2
 PDLP_USED_BF16, PDLP_USED_PATTERN = 2, 3
 PRECISION = {"fp64": PDLP_FP64, "fp32": PDLP_FP32, "bf16": PDLP_FP32_BF16A}
@@ -39,7 +40,8 @@ class PdlpParams(C.Structure):
                 ("restarts", C.c_int), ("fixed_eta", C.c_double), ("fixed_omega", C.c_double),
                 ("terminate", C.c_int), ("lanes_A", C.c_int), ("lanes_AT", C.c_int),
                 ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int),
-                ("persistent", C.c_int), ("autotune", C.c_int)]
+                ("persistent", C.c_int), ("autotune", C.c_int),
+                ("detect_infeasibility", C.c_int)]
 
 
 class PdlpResult(C.Structure):
@@ -50,7 +52,7 @@ class PdlpResult(C.Structure):
                 ("rel_dual_res", C.c_double), ("rel_gap", C.c_double), ("rel_kkt", C.c_double),
                 ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("lanes_A", C.c_int),
-                ("lanes_AT", C.c_int)]
+                ("lanes_AT", C.c_int), ("ray_obj", C.c_double), ("ray_res", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -38,7 +38,8 @@ template <> struct Ld<double, double> {
 // is safe to over-launch.
 struct DevState {
   // host-visible summary first (copied back after every chunk)
-  int status;            // 0 running, else PDLP_OPTIMAL / ITER_LIMIT / TIME_LIMIT / NUMERICAL
+  int status;            // 0 running, else PDLP_OPTIMAL / ITER_LIMIT / TIME_LIMIT / NUMERICAL /
+                         // PRIMAL_INFEASIBLE / DUAL_INFEASIBLE
   int check_due;         // 1: the KKT block must run before the next step
   long long iters;       // accepted iterations
   long long attempts;    // all step attempts (k of the step-size rule, 1-based after increment)
@@ -63,7 +64,11 @@ struct DevState {
   // parameters
   long long iter_limit;
   int period, adaptive, restarts_on, terminate;
+  int detect_inf;         // 1: test the certificates of infeasibility at each check
   double tol;
+  // certificate of the terminating check (status 5 / 6): its ray objective and
+  // the norm of its residual
+  double ray_obj, ray_res;
   double norm_q, norm_c;  // ||q||_2, ||c||_2 of the unscaled data
   // results of the last KKT check: [0] current, [1] average
   double pobj[2], dobj[2], relp[2], reld[2], relgap[2];
@@ -93,7 +98,7 @@ struct DevState {
 };
 
 // status value of a persistent step kernel whose bounded barrier wait gave up
-constexpr int kStatusWaitFailed = 5;
+constexpr int kStatusWaitFailed = 99;
 
 // ---------------------------------------------------------------- batches
 // Launch tables of a batch of LPs solved together (all NULL for one LP): the
@@ -191,6 +196,24 @@ template <int LANES, typename T>
 __device__ __forceinline__ P2<T> group_sum(P2<T> v) {
   v.a = group_sum<LANES, T>(v.a);
   v.b = group_sum<LANES, T>(v.b);
+  return v;
+}
+
+// three partial sums reduced together (two candidates and a ray)
+struct D3 {
+  double a, b, c;
+  __device__ __forceinline__ D3& operator+=(const D3& o) {
+    a += o.a;
+    b += o.b;
+    c += o.c;
+    return *this;
+  }
+};
+template <int LANES>
+__device__ __forceinline__ D3 group_sum(D3 v) {
+  v.a = group_sum<LANES, double>(v.a);
+  v.b = group_sum<LANES, double>(v.b);
+  v.c = group_sum<LANES, double>(v.c);
   return v;
 }
 

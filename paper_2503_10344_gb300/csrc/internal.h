@@ -65,7 +65,10 @@ struct KktRaw {
   const unsigned char* row_kind;           // 0 >=-row, 1 =-row, 2 <=-row flipped to >=
   void *x[2], *y[2], *sum_x, *sum_y;       // iterates (float or double; x as (x_j, dx_j) pairs)
   double *Xc, *Xa, *Yc, *Ya, *Xl, *Yl;     // unscaled float64 candidates and restart anchors
-  double *part_r, *part_c;
+  double *Xr, *Yr;                         // rays of the certificate tests (x - x_last, y - y_last
+                                           // projected onto the recession cones)
+  double *part_r, *part_c;                 // kPartR / kPartC partial rows of grid_r / grid_c
+  int rays;                                // the KKT passes also accumulate the ray terms
   int grid_r_short, grid_r, grid_c_short, grid_c, grid_e;
   int scaled;  // iterates are in scaled space (explicit K~)
   int fp32;    // iterate element type is float
@@ -74,6 +77,10 @@ struct KktRaw {
   Tables tr, tc; // batch tables over A and A^T (all NULL for one LP); the elementwise
                  // kernels use tc's block map with grid_c blocks
 };
+
+// partial sums per block of the KKT passes over A (rows) and A^T (columns)
+constexpr int kPartR = 11;
+constexpr int kPartC = 15;
 
 enum KktKernel { KK_PREP = 0, KK_ROWS = 1, KK_COLS = 2, KK_FINAL = 3, KK_APPLY = 4, KK_END = 5 };
 cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s);

@@ -2,7 +2,9 @@
 // all in float64 on the unscaled canonical data, run once per check period.
 //
 //   k_kkt_prep   unscaled float64 current iterate and step-size-weighted
-//                average (A7) into scratch vectors
+//                average (A7) into scratch vectors; with the certificate test
+//                on, also the rays x^ = x - x_last projected onto the recession
+//                cone of [l, u] and y^ = y - y_last projected onto Y
 //   k_kkt_rows   K x for both candidates in one pass over A, fused with the
 //                primal residuals (unscaled and scaled), q^T y and the scaled
 //                dual distance to the last restart point
@@ -11,8 +13,9 @@
 //                primal distance to the last restart point
 //   k_kkt_final  one block: fixed-order reduction of the partials, relative
 //                KKT of both candidates (the termination test of the paper's
-//                relative tolerances, section 4), the KKT restart criteria and
-//                the primal-weight update
+//                relative tolerances, section 4), the certificates of primal
+//                and dual infeasibility, the KKT restart criteria and the
+//                primal-weight update
 //   k_kkt_apply  restart: replace the iterate by the average if chosen, move
 //                the restart anchors, clear the running sums
 //   k_kkt_end    one thread: clear the per-check flags
@@ -61,34 +64,56 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
     const double s = r.scaled ? r.dc[j] : 1.0;
     // unscaled candidates, clipped to [l, u] so the KKT measured here is the
     // KKT of exactly the point the solver returns (A11)
-    r.Xc[j] = fmin(fmax(s * xc, r.l[j]), r.u[j]);
+    const double Xc = fmin(fmax(s * xc, r.l[j]), r.u[j]);
+    r.Xc[j] = Xc;
     r.Xa[j] = fmin(fmax(s * xa, r.l[j]), r.u[j]);
+    if (r.rays) {
+      // displacement since the restart anchor, on the recession cone of [l, u]
+      const unsigned f = r.bflags[j];
+      double d = Xc - r.Xl[j];
+      if (f & 1u) d = fmax(d, 0.0);
+      if (f & 2u) d = fmin(d, 0.0);
+      r.Xr[j] = d;
+    }
   }
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double yc = (double)y[i];
     const double ya = sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc;
     const double s = r.scaled ? r.dr[i] : 1.0;
-    r.Yc[i] = s * yc;
+    const double Yc = s * yc;
+    r.Yc[i] = Yc;
     r.Ya[i] = s * ya;
+    if (r.rays) {
+      const double d = Yc - r.Yl[i];
+      r.Yr[i] = r.row_kind[i] == 1 ? d : fmax(d, 0.0);
+    }
   }
 }
 
 // partial layout over rows of A: [0,1] ||r_p||^2 cur/avg, [2,3] ||D_r r_p||^2,
-// [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2
-template <int LANES>
+// [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2; with RAYS also [8] ||r^_p||^2 of
+// the primal ray, [9] q^T y^ and [10] sum |q_i y^_i| of the dual ray
+template <int LANES, bool RAYS>
 __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
   pdl_enter();
   const Span sp = make_span(r.tr, r.m, r.grid_r_short, r.a_long, r.a_nlong);
   DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  constexpr int NV = RAYS ? 11 : 8;
+  using Acc = typename std::conditional<RAYS, D3, D2>::type;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   const double* __restrict__ val = r.a_val64;
-  auto load = [&](int p) -> D2 {
+  auto load = [&](int p) -> Acc {
     const double v = val ? __ldg(val + p) : 1.0;
     const int j = __ldg(r.a_col + p);
-    return D2{v * r.Xc[j], v * r.Xa[j]};
+    if constexpr (RAYS)
+      return D3{v * r.Xc[j], v * r.Xa[j], v * r.Xr[j]};
+    else
+      return D2{v * r.Xc[j], v * r.Xa[j]};
   };
-  auto epi = [&](int i, D2 ax) {
+  auto epi = [&](int i, Acc ax) {
     const double q = r.q[i], dr = r.dr[i];
     const bool eq = r.row_kind[i] == 1;
     const double kx[2] = {ax.a, ax.b};
@@ -103,30 +128,48 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
       const double dd = (yv[k] - r.Yl[i]) * r.inv_dr[i];
       acc[6 + k] += dd * dd;
     }
+    if constexpr (RAYS) {
+      // A12: the primal ray must keep K x^ >= 0 (= 0 on equality rows)
+      const double rr = eq ? fabs(ax.c) : fmax(-ax.c, 0.0);
+      acc[8] += rr * rr;
+      const double qy = q * r.Yr[i];
+      acc[9] += qy;
+      acc[10] += fabs(qy);
+    }
   };
-  rows_all<true, LANES, D2>(sp, r.a_ptr, r.a_thresh, load, epi);
-  double out[8];
-  block_sum<8>(acc, out);
+  rows_all<true, LANES, Acc>(sp, r.a_ptr, r.a_thresh, load, epi);
+  double out[NV];
+  block_sum<NV>(acc, out);
   if (threadIdx.x == 0)
-    for (int k = 0; k < 8; ++k) r.part_r[(size_t)k * r.grid_r + blockIdx.x] = out[k];
+    for (int k = 0; k < NV; ++k) r.part_r[(size_t)k * r.grid_r + blockIdx.x] = out[k];
 }
 
 // partial layout over rows of A^T: [0,1] ||r_d||^2, [2,3] ||D_c r_d||^2, [4,5] c^T x,
-// [6,7] bound terms of the dual objective, [8,9] ||(x - x_last) / D_c||^2
-template <int LANES>
+// [6,7] bound terms of the dual objective, [8,9] ||(x - x_last) / D_c||^2; with
+// RAYS also, for the dual ray (lambda^ = -K^T y^): [10] ||r^_d||^2, [11] its
+// bound terms, [12] their magnitudes, and for the primal ray [13] c^T x^,
+// [14] sum |c_j x^_j|
+template <int LANES, bool RAYS>
 __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
   pdl_enter();
   const Span sp = make_span(r.tc, r.n, r.grid_c_short, r.t_long, r.t_nlong);
   DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  constexpr int NV = RAYS ? 15 : 10;
+  using Acc = typename std::conditional<RAYS, D3, D2>::type;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   const double* __restrict__ val = r.t_val64;
-  auto load = [&](int p) -> D2 {
+  auto load = [&](int p) -> Acc {
     const double v = val ? __ldg(val + p) : 1.0;
     const int i = __ldg(r.t_col + p);
-    return D2{v * r.Yc[i], v * r.Ya[i]};
+    if constexpr (RAYS)
+      return D3{v * r.Yc[i], v * r.Ya[i], v * r.Yr[i]};
+    else
+      return D2{v * r.Yc[i], v * r.Ya[i]};
   };
-  auto epi = [&](int j, D2 aty) {
+  auto epi = [&](int j, Acc aty) {
     const double c = r.c[j], dc = r.dc[j], idc = r.inv_dc[j];
     const unsigned f = r.bflags[j];
     const bool lfin = f & 1u, ufin = f & 2u;
@@ -145,12 +188,32 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
       const double dd = (xv[k] - r.Xl[j]) * idc;
       acc[8 + k] += dd * dd;
     }
+    if constexpr (RAYS) {
+      // A12: the dual ray's reduced cost has no c
+      const double lam = -aty.c;
+      const double lp = fmax(lam, 0.0), lm = fmax(-lam, 0.0);
+      const double rd = (lfin ? 0.0 : lp) + (ufin ? 0.0 : lm);
+      acc[10] += rd * rd;
+      acc[11] += l * lp - u * lm;
+      acc[12] += fabs(l) * lp + fabs(u) * lm;
+      const double cx = c * r.Xr[j];
+      acc[13] += cx;
+      acc[14] += fabs(cx);
+    }
   };
-  rows_all<true, LANES, D2>(sp, r.t_ptr, r.t_thresh, load, epi);
-  double out[10];
-  block_sum<10>(acc, out);
+  rows_all<true, LANES, Acc>(sp, r.t_ptr, r.t_thresh, load, epi);
+  double out[NV];
+  block_sum<NV>(acc, out);
   if (threadIdx.x == 0)
-    for (int k = 0; k < 10; ++k) r.part_c[(size_t)k * r.grid_c + blockIdx.x] = out[k];
+    for (int k = 0; k < NV; ++k) r.part_c[(size_t)k * r.grid_c + blockIdx.x] = out[k];
+}
+
+// A12: a ray whose objective `obj` (oriented so that a certificate has obj > 0)
+// clears the rounding of its terms (`mag`, the sum of their magnitudes) and whose
+// residual is within eps_inf of it
+__device__ __forceinline__ bool inf_certificate(double obj, double mag, double res) {
+  constexpr double eps_inf = 1e-8, kappa = 1e-9;
+  return obj > 0.0 && obj > kappa * mag && res <= eps_inf * obj;
 }
 
 __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
@@ -166,9 +229,17 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
     c0 = r.tc.blk0[k];
     cn = r.tc.nblk[k];
   }
-  double pr[8], pc[10];
-  reduce_partials<8>(r.part_r + r0, r.grid_r, rn, pr);
-  reduce_partials<10>(r.part_c + c0, r.grid_c, cn, pc);
+  double pr[kPartR], pc[kPartC];
+  if (r.rays) {
+    reduce_partials<kPartR>(r.part_r + r0, r.grid_r, rn, pr);
+    reduce_partials<kPartC>(r.part_c + c0, r.grid_c, cn, pc);
+  } else {
+    double a[8], b[10];
+    reduce_partials<8>(r.part_r + r0, r.grid_r, rn, a);
+    reduce_partials<10>(r.part_c + c0, r.grid_c, cn, b);
+    for (int k = 0; k < kPartR; ++k) pr[k] = k < 8 ? a[k] : 0.0;
+    for (int k = 0; k < kPartC; ++k) pc[k] = k < 10 ? b[k] : 0.0;
+  }
   if (threadIdx.x != 0) return;
   double relk[2], gap2[2];
   for (int k = 0; k < 2; ++k) {
@@ -201,6 +272,18 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
     st->status = 4;  // PDLP_NUMERICAL
   } else if (st->terminate && best <= st->tol) {
     st->status = 1;  // PDLP_OPTIMAL
+  } else if (r.rays && st->terminate && st->detect_inf &&
+             inf_certificate(pr[9] + pc[11], pr[10] + pc[12], sqrt(pc[10]))) {
+    // A12: y^ proves that no x satisfies the rows within the bounds
+    st->status = 5;  // PDLP_PRIMAL_INFEASIBLE
+    st->ray_obj = pr[9] + pc[11];
+    st->ray_res = sqrt(pc[10]);
+  } else if (r.rays && st->terminate && st->detect_inf &&
+             inf_certificate(-pc[13], pc[14], sqrt(pr[8]))) {
+    // A12: x^ is a direction of unbounded descent
+    st->status = 6;  // PDLP_DUAL_INFEASIBLE
+    st->ray_obj = pc[13];
+    st->ray_res = sqrt(pr[8]);
   } else if (st->iters >= st->iter_limit) {
     st->status = 2;  // PDLP_ITER_LIMIT
   } else if (st->force_final) {
@@ -314,18 +397,21 @@ __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, doub
                                                    double* y_avg) {
   const ESpan es = make_espan(r);
   const int ua = r.st[es.lp].used_avg;
+  // a certificate replaces the primal (unbounded) or dual (infeasible) output
+  const int status = r.st[es.lp].status;
+  const bool x_ray = r.rays && status == 6, y_ray = r.rays && status == 5;
   const long long stride = (long long)es.nblk * kBlock;
   for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
     const double l = r.l[j], u = r.u[j];
     const double xc = fmin(fmax(r.Xc[j], l), u), xa = fmin(fmax(r.Xa[j], l), u);
-    if (x_out) x_out[j] = ua ? xa : xc;
+    if (x_out) x_out[j] = x_ray ? r.Xr[j] : ua ? xa : xc;
     if (x_cur) x_cur[j] = xc;
     if (x_avg) x_avg[j] = xa;
   }
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double s = r.row_kind[i] == 2 ? -1.0 : 1.0;
     const double yc = s * r.Yc[i], ya = s * r.Ya[i];
-    if (y_out) y_out[i] = ua ? ya : yc;
+    if (y_out) y_out[i] = y_ray ? s * r.Yr[i] : ua ? ya : yc;
     if (y_cur) y_cur[i] = yc;
     if (y_avg) y_avg[i] = ya;
   }
@@ -337,8 +423,10 @@ inline int egrid(const KktRaw& r) { return r.tc.blk_lp ? r.grid_c : r.grid_e; }
 template <int LANES>
 cudaError_t launch_rc(int which, const KktRaw& r, cudaStream_t s) {
   if (which == KK_ROWS)
-    return launch_pdl(k_kkt_rows<LANES>, r.grid_r, kBlock, s, r);
-  return launch_pdl(k_kkt_cols<LANES>, r.grid_c, kBlock, s, r);
+    return r.rays ? launch_pdl(k_kkt_rows<LANES, true>, r.grid_r, kBlock, s, r)
+                  : launch_pdl(k_kkt_rows<LANES, false>, r.grid_r, kBlock, s, r);
+  return r.rays ? launch_pdl(k_kkt_cols<LANES, true>, r.grid_c, kBlock, s, r)
+                : launch_pdl(k_kkt_cols<LANES, false>, r.grid_c, kBlock, s, r);
 }
 
 cudaError_t launch_rc_lanes(int which, int lanes, const KktRaw& r, cudaStream_t s) {

@@ -86,7 +86,7 @@ struct Bufs {
   int *a_ptr, *a_col, *t_ptr, *t_col;
   double *a_val64, *t_val64;
   void *a_valit, *t_valit;
-  double *q64, *dr, *dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *stat_r, *stat_c, *inv_dr, *inv_dc;
+  double *q64, *dr, *dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *Xr, *Yr, *stat_r, *stat_c, *inv_dr, *inv_dc;
   unsigned char *row_kind, *bflags;
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
@@ -133,6 +133,8 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.Yc = (double*)ar.take(8 * M);
   b.Ya = (double*)ar.take(8 * M);
   b.Yl = (double*)ar.take(8 * M);
+  b.Xr = (double*)ar.take(8 * N);
+  b.Yr = (double*)ar.take(8 * M);
   b.stat_r = (double*)ar.take(8 * M);
   b.stat_c = (double*)ar.take(8 * N);
   b.row_kind = (unsigned char*)ar.take(M);
@@ -153,8 +155,8 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.sum_y = ar.take(eb * M);
   b.part_p = (double*)ar.take(8 * G);
   b.part_d = (double*)ar.take(8 * 2 * G);
-  b.part_r = (double*)ar.take(8 * 8 * G);
-  b.part_c = (double*)ar.take(8 * 10 * G);
+  b.part_r = (double*)ar.take(8 * kPartR * G);
+  b.part_c = (double*)ar.take(8 * kPartC * G);
   b.part_setup = (double*)ar.take(8 * setup_part_doubles(m, n));
   b.scalars = (double*)ar.take(8 * 8);
   b.a_long = (int*)ar.take(4 * (M + 1));
@@ -665,6 +667,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   for (int k = 0; k < 2; ++k) { kr.x[k] = bf.x[k]; kr.y[k] = bf.y[k]; }
   kr.sum_x = bf.sum_x; kr.sum_y = bf.sum_y;
   kr.Xc = bf.Xc; kr.Xa = bf.Xa; kr.Xl = bf.Xl; kr.Yc = bf.Yc; kr.Ya = bf.Ya; kr.Yl = bf.Yl;
+  kr.Xr = bf.Xr; kr.Yr = bf.Yr;
+  kr.rays = p->detect_infeasibility && p->terminate ? 1 : 0;
   kr.part_r = bf.part_r; kr.part_c = bf.part_c;
   kr.grid_r_short = gr_short; kr.grid_r = gr; kr.grid_c_short = gc_short; kr.grid_c = gc;
   kr.grid_e = ge;
@@ -691,6 +695,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   hs.adaptive = p->adaptive_step ? 1 : 0;
   hs.restarts_on = p->restarts ? 1 : 0;
   hs.terminate = p->terminate ? 1 : 0;
+  hs.detect_inf = p->detect_infeasibility ? 1 : 0;
   hs.tol = p->tol;
   hs.norm_c = sca[2];
   hs.norm_q = sca[3];
@@ -1008,6 +1013,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   r->rel_kkt = std::max(r->rel_primal_res, std::max(r->rel_dual_res, r->rel_gap));
   r->eta = fs.eta;
   r->omega = fs.omega;
+  const bool cert = fs.status == PDLP_PRIMAL_INFEASIBLE || fs.status == PDLP_DUAL_INFEASIBLE;
+  r->ray_obj = cert ? fs.ray_obj : NAN;
+  r->ray_res = cert ? fs.ray_res : NAN;
   r->setup_s = ms_setup * 1e-3;
   r->solve_s = ms_solve * 1e-3;
   // the while-loop graph was counted with one attempt per launch; its other
@@ -1242,7 +1250,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   // ---- global arrays
   struct G {
     int *a_ptr, *a_col, *t_ptr, *t_col, *a_long, *t_long, *tabA, *tabT;
-    double *a_val64, *t_val64, *q64, *dr, *dc, *inv_dr, *inv_dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl;
+    double *a_val64, *t_val64, *q64, *dr, *dc, *inv_dr, *inv_dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *Xr, *Yr;
     double *c64, *l64, *u64, *part_p, *part_d, *part_r, *part_c, *x_out, *y_out;
     void *a_valit, *t_valit, *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
     unsigned char *row_kind, *bflags;
@@ -1263,8 +1271,9 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.t_val64 = (double*)ar.take(8 * Z);
     g.a_valit = ar.take(vb * Z);
     g.t_valit = ar.take(vb * Z);
-    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yc, &g.Ya, &g.Yl, &g.y_out}) *v = (double*)ar.take(8 * M);
-    for (double** v : {&g.dc, &g.inv_dc, &g.Xc, &g.Xa, &g.Xl, &g.c64, &g.l64, &g.u64, &g.x_out})
+    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yc, &g.Ya, &g.Yl, &g.Yr, &g.y_out})
+      *v = (double*)ar.take(8 * M);
+    for (double** v : {&g.dc, &g.inv_dc, &g.Xc, &g.Xa, &g.Xl, &g.Xr, &g.c64, &g.l64, &g.u64, &g.x_out})
       *v = (double*)ar.take(8 * N);
     g.row_kind = (unsigned char*)ar.take(M);
     g.bflags = (unsigned char*)ar.take(N);
@@ -1276,8 +1285,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     }
     g.part_p = (double*)ar.take(8 * gmax);
     g.part_d = (double*)ar.take(8 * 2 * gmax);
-    g.part_r = (double*)ar.take(8 * 8 * gmax);
-    g.part_c = (double*)ar.take(8 * 10 * gmax);
+    g.part_r = (double*)ar.take(8 * kPartR * gmax);
+    g.part_c = (double*)ar.take(8 * kPartC * gmax);
     g.a_long = (int*)ar.take(4 * (M + 1));
     g.t_long = (int*)ar.take(4 * (N + 1));
     g.tabA = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
@@ -1406,6 +1415,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     h.adaptive = p->adaptive_step ? 1 : 0;
     h.restarts_on = p->restarts ? 1 : 0;
     h.terminate = p->terminate ? 1 : 0;
+    h.detect_inf = p->detect_infeasibility ? 1 : 0;
     h.tol = p->tol;
     h.norm_c = so.sca[2];
     h.norm_q = so.sca[3];
@@ -1475,6 +1485,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   for (int k = 0; k < 2; ++k) { kr.x[k] = g.x[k]; kr.y[k] = g.y[k]; }
   kr.sum_x = g.sum_x; kr.sum_y = g.sum_y;
   kr.Xc = g.Xc; kr.Xa = g.Xa; kr.Xl = g.Xl; kr.Yc = g.Yc; kr.Ya = g.Ya; kr.Yl = g.Yl;
+  kr.Xr = g.Xr; kr.Yr = g.Yr;
+  kr.rays = p->detect_infeasibility && p->terminate ? 1 : 0;
   kr.part_r = g.part_r; kr.part_c = g.part_c;
   kr.grid_r_short = gridA; kr.grid_r = gridA; kr.grid_c_short = gridT; kr.grid_c = gridT;
   kr.grid_e = gridT;
@@ -1617,6 +1629,9 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     r.rel_kkt = std::max(r.rel_primal_res, std::max(r.rel_dual_res, r.rel_gap));
     r.eta = f.eta;
     r.omega = f.omega;
+    const bool cert = f.status == PDLP_PRIMAL_INFEASIBLE || f.status == PDLP_DUAL_INFEASIBLE;
+    r.ray_obj = cert ? f.ray_obj : NAN;
+    r.ray_res = cert ? f.ray_res : NAN;
     r.setup_s = setup_s;
     r.solve_s = solve_s;
     r.kernel_launches = g_launches;
@@ -1661,6 +1676,7 @@ int pdlp_default_params(pdlp_params* p) {
   p->terminate = 1;
   p->persistent = 0;
   p->autotune = 0;
+  p->detect_infeasibility = 1;
   return PDLP_OK;
 }
 

@@ -73,6 +73,7 @@ def test_default_params(lib):
     assert p.tol == 1e-4 and p.check_period == 64 and p.ruiz_iters == 10 and p.pc_alpha == 1.0
     assert p.adaptive_step == 1 and p.restarts == 1 and p.terminate == 1
     assert p.precision == P.PDLP_FP64
+    assert p.detect_infeasibility == 1 and p.persistent == 0 and p.autotune == 0
 
 
 def test_workspace_size_rejects_bad_sizes(lib):
