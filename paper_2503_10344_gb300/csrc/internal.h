@@ -51,6 +51,13 @@ cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_
 cudaError_t launch_iter_bf16(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_pat(int which, int lanes, const IterRaw& r, cudaStream_t s);
 
+// The float64 candidates of one column (or row) of a KKT check side by side, so
+// that a gathered entry is one 32-byte sector: c current, a average, r ray
+// (0 unless the certificate test needs it), unscaled.
+struct alignas(32) Cand {
+  double c, a, r, pad;
+};
+
 struct KktRaw {
   const int *a_ptr, *a_col;
   const double* a_val64;  // raw canonical K (NULL = every value +1)
@@ -64,11 +71,12 @@ struct KktRaw {
   const unsigned char* bflags;             // per column: bit 0 l finite, bit 1 u finite
   const unsigned char* row_kind;           // 0 >=-row, 1 =-row, 2 <=-row flipped to >=
   void *x[2], *y[2], *sum_x, *sum_y;       // iterates (float or double; x as (x_j, dx_j) pairs)
-  double *Xc, *Xa, *Yc, *Ya, *Xl, *Yl;     // unscaled float64 candidates and restart anchors
-  double *Xr, *Yr;                         // rays of the certificate tests (x - x_last, y - y_last
-                                           // projected onto the recession cones)
+  Cand *XG, *YG;    // candidates per column / row; the ray slot holds x - x_last, y - y_last
+                    // projected onto the recession cone of [l, u] and onto Y
+  double *Xl, *Yl;  // unscaled restart anchors
   double *part_r, *part_c;                 // kPartR / kPartC partial rows of grid_r / grid_c
-  int rays;                                // the KKT passes also accumulate the ray terms
+  int rays;  // ray terms in the KKT passes: 0 none, 1 the dual ray only (every column
+             // boxed, so the primal ray is 0), 2 both
   int grid_r_short, grid_r, grid_c_short, grid_c, grid_e;
   int scaled;  // iterates are in scaled space (explicit K~)
   int fp32;    // iterate element type is float

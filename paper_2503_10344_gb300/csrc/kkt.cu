@@ -30,6 +30,16 @@ namespace {
 // divides where the definition divides), the block's reciprocal otherwise
 #define avg_of(sum, sw, isw) (std::is_same<T, double>::value ? (sum) / (sw) : (sum) * (isw))
 
+// (current, average) and the ray of a candidate entry: one 16-byte load for the
+// pair, the ray from the second half of the same 32-byte sector (ordinary loads:
+// the vectors are written by the preceding kernel of the same chain)
+__device__ __forceinline__ double2 cand2(const Cand* g, long long i) {
+  return reinterpret_cast<const double2*>(g)[2 * i];
+}
+__device__ __forceinline__ double cand_r(const Cand* g, long long i) {
+  return reinterpret_cast<const double2*>(g)[2 * i + 1].x;
+}
+
 // columns and rows of one LP for the elementwise kernels (prep, apply, output)
 struct ESpan {
   int lp, c0, nc, r0, nr, bidx, nblk;
@@ -65,42 +75,46 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
     // unscaled candidates, clipped to [l, u] so the KKT measured here is the
     // KKT of exactly the point the solver returns (A11)
     const double Xc = fmin(fmax(s * xc, r.l[j]), r.u[j]);
-    r.Xc[j] = Xc;
-    r.Xa[j] = fmin(fmax(s * xa, r.l[j]), r.u[j]);
-    if (r.rays) {
+    double d = 0.0;
+    if (r.rays == 2) {
       // displacement since the restart anchor, on the recession cone of [l, u]
       const unsigned f = r.bflags[j];
-      double d = Xc - r.Xl[j];
+      d = Xc - r.Xl[j];
       if (f & 1u) d = fmax(d, 0.0);
       if (f & 2u) d = fmin(d, 0.0);
-      r.Xr[j] = d;
     }
+    double2* g = reinterpret_cast<double2*>(r.XG + j);
+    g[0] = make_double2(Xc, fmin(fmax(s * xa, r.l[j]), r.u[j]));
+    g[1] = make_double2(d, 0.0);
   }
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double yc = (double)y[i];
     const double ya = sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc;
     const double s = r.scaled ? r.dr[i] : 1.0;
     const double Yc = s * yc;
-    r.Yc[i] = Yc;
-    r.Ya[i] = s * ya;
+    double d = 0.0;
     if (r.rays) {
-      const double d = Yc - r.Yl[i];
-      r.Yr[i] = r.row_kind[i] == 1 ? d : fmax(d, 0.0);
+      d = Yc - r.Yl[i];
+      if (r.row_kind[i] != 1) d = fmax(d, 0.0);
     }
+    double2* g = reinterpret_cast<double2*>(r.YG + i);
+    g[0] = make_double2(Yc, s * ya);
+    g[1] = make_double2(d, 0.0);
   }
 }
 
 // partial layout over rows of A: [0,1] ||r_p||^2 cur/avg, [2,3] ||D_r r_p||^2,
-// [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2; with RAYS also [8] ||r^_p||^2 of
-// the primal ray, [9] q^T y^ and [10] sum |q_i y^_i| of the dual ray
-template <int LANES, bool RAYS>
+// [4,5] q^T y, [6,7] ||(y - y_last) / D_r||^2; with RAYS >= 1 also [9] q^T y^ and
+// [10] sum |q_i y^_i| of the dual ray, with RAYS = 2 [8] ||r^_p||^2 of the primal ray
+// (RAYS = 1 when every column is boxed: the primal ray is 0 and [8] stays 0)
+template <int LANES, int RAYS>
 __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
   pdl_enter();
   const Span sp = make_span(r.tr, r.m, r.grid_r_short, r.a_long, r.a_nlong);
   DevState* st = r.st + sp.lp;
   if (!st->check_due || st->status != 0) return;
   constexpr int NV = RAYS ? 11 : 8;
-  using Acc = typename std::conditional<RAYS, D3, D2>::type;
+  using Acc = typename std::conditional<RAYS == 2, D3, D2>::type;
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
@@ -108,16 +122,18 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
   auto load = [&](int p) -> Acc {
     const double v = val ? __ldg(val + p) : 1.0;
     const int j = __ldg(r.a_col + p);
-    if constexpr (RAYS)
-      return D3{v * r.Xc[j], v * r.Xa[j], v * r.Xr[j]};
+    const double2 x2 = cand2(r.XG, j);
+    if constexpr (RAYS == 2)
+      return D3{v * x2.x, v * x2.y, v * cand_r(r.XG, j)};
     else
-      return D2{v * r.Xc[j], v * r.Xa[j]};
+      return D2{v * x2.x, v * x2.y};
   };
   auto epi = [&](int i, Acc ax) {
     const double q = r.q[i], dr = r.dr[i];
     const bool eq = r.row_kind[i] == 1;
     const double kx[2] = {ax.a, ax.b};
-    const double yv[2] = {r.Yc[i], r.Ya[i]};
+    const double2 y2 = cand2(r.YG, i);
+    const double yv[2] = {y2.x, y2.y};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       double rp = q - kx[k];
@@ -128,11 +144,13 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
       const double dd = (yv[k] - r.Yl[i]) * r.inv_dr[i];
       acc[6 + k] += dd * dd;
     }
-    if constexpr (RAYS) {
+    if constexpr (RAYS == 2) {
       // A12: the primal ray must keep K x^ >= 0 (= 0 on equality rows)
       const double rr = eq ? fabs(ax.c) : fmax(-ax.c, 0.0);
       acc[8] += rr * rr;
-      const double qy = q * r.Yr[i];
+    }
+    if constexpr (RAYS >= 1) {
+      const double qy = q * cand_r(r.YG, i);
       acc[9] += qy;
       acc[10] += fabs(qy);
     }
@@ -146,10 +164,10 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
 
 // partial layout over rows of A^T: [0,1] ||r_d||^2, [2,3] ||D_c r_d||^2, [4,5] c^T x,
 // [6,7] bound terms of the dual objective, [8,9] ||(x - x_last) / D_c||^2; with
-// RAYS also, for the dual ray (lambda^ = -K^T y^): [10] ||r^_d||^2, [11] its
-// bound terms, [12] their magnitudes, and for the primal ray [13] c^T x^,
-// [14] sum |c_j x^_j|
-template <int LANES, bool RAYS>
+// RAYS >= 1 also, for the dual ray (lambda^ = -K^T y^): [11] its bound terms,
+// [12] their magnitudes; with RAYS = 2 [10] ||r^_d||^2 and for the primal ray
+// [13] c^T x^, [14] sum |c_j x^_j| (all 0 when every column is boxed)
+template <int LANES, int RAYS>
 __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
   pdl_enter();
   const Span sp = make_span(r.tc, r.n, r.grid_c_short, r.t_long, r.t_nlong);
@@ -164,10 +182,11 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
   auto load = [&](int p) -> Acc {
     const double v = val ? __ldg(val + p) : 1.0;
     const int i = __ldg(r.t_col + p);
+    const double2 y2 = cand2(r.YG, i);
     if constexpr (RAYS)
-      return D3{v * r.Yc[i], v * r.Ya[i], v * r.Yr[i]};
+      return D3{v * y2.x, v * y2.y, v * cand_r(r.YG, i)};
     else
-      return D2{v * r.Yc[i], v * r.Ya[i]};
+      return D2{v * y2.x, v * y2.y};
   };
   auto epi = [&](int j, Acc aty) {
     const double c = r.c[j], dc = r.dc[j], idc = r.inv_dc[j];
@@ -175,30 +194,37 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
     const bool lfin = f & 1u, ufin = f & 2u;
     const double l = lfin ? r.l[j] : 0.0, u = ufin ? r.u[j] : 0.0;
     const double kty[2] = {aty.a, aty.b};
-    const double xv[2] = {r.Xc[j], r.Xa[j]};
+    const double2 x2 = cand2(r.XG, j);
+    const double xv[2] = {x2.x, x2.y};
+    // lambda+ = lam, lambda- = 0 when lam > 0, else lambda+ = 0, lambda- = -lam: each
+    // term below keeps only its nonzero part (the same values; the sign test is an
+    // integer compare, so the float64 pipe does the arithmetic only)
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const double lam = c - kty[k];
-      const double lp = fmax(lam, 0.0), lm = fmax(-lam, 0.0);
-      const double rd = (lfin ? 0.0 : lp) + (ufin ? 0.0 : lm);
+      const bool pos = __double_as_longlong(lam) > 0;
+      const double rd = pos ? (lfin ? 0.0 : lam) : (ufin ? 0.0 : -lam);
       acc[0 + k] += rd * rd;
       acc[2 + k] += (dc * rd) * (dc * rd);
       acc[4 + k] += c * xv[k];
-      acc[6 + k] += l * lp - u * lm;  // l, u read as 0 where infinite
+      acc[6 + k] += (pos ? l : u) * lam;  // l lambda+ - u lambda-; l, u read as 0 where infinite
       const double dd = (xv[k] - r.Xl[j]) * idc;
       acc[8 + k] += dd * dd;
     }
-    if constexpr (RAYS) {
+    if constexpr (RAYS >= 1) {
       // A12: the dual ray's reduced cost has no c
       const double lam = -aty.c;
-      const double lp = fmax(lam, 0.0), lm = fmax(-lam, 0.0);
-      const double rd = (lfin ? 0.0 : lp) + (ufin ? 0.0 : lm);
-      acc[10] += rd * rd;
-      acc[11] += l * lp - u * lm;
-      acc[12] += fabs(l) * lp + fabs(u) * lm;
-      const double cx = c * r.Xr[j];
-      acc[13] += cx;
-      acc[14] += fabs(cx);
+      const bool pos = __double_as_longlong(lam) > 0;
+      const double t = (pos ? l : u) * lam;
+      acc[11] += t;
+      acc[12] += fabs(t);
+      if constexpr (RAYS == 2) {
+        const double rd = pos ? (lfin ? 0.0 : lam) : (ufin ? 0.0 : -lam);
+        acc[10] += rd * rd;
+        const double cx = c * cand_r(r.XG, j);
+        acc[13] += cx;
+        acc[14] += fabs(cx);
+      }
     }
   };
   rows_all<true, LANES, Acc>(sp, r.t_ptr, r.t_thresh, load, epi);
@@ -359,9 +385,9 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
       v.x = (T)(sw > 0.0 ? avg_of((double)sx[j] + pw * xc, sw, isw) : xc);
       v.y = (T)0;  // the step into the restart point is never read
       x[j] = v;
-      r.Xl[j] = r.Xa[j];
+      r.Xl[j] = cand2(r.XG, j).y;
     } else {
-      r.Xl[j] = r.Xc[j];
+      r.Xl[j] = cand2(r.XG, j).x;
     }
     sx[j] = (T)0;
   }
@@ -369,9 +395,9 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
     if (kind == 2) {
       const double yc = (double)y[i];
       y[i] = (T)(sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc);
-      r.Yl[i] = r.Ya[i];
+      r.Yl[i] = cand2(r.YG, i).y;
     } else {
-      r.Yl[i] = r.Yc[i];
+      r.Yl[i] = cand2(r.YG, i).x;
     }
     sy[i] = (T)0;
   }
@@ -399,19 +425,21 @@ __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, doub
   const int ua = r.st[es.lp].used_avg;
   // a certificate replaces the primal (unbounded) or dual (infeasible) output
   const int status = r.st[es.lp].status;
-  const bool x_ray = r.rays && status == 6, y_ray = r.rays && status == 5;
+  const bool x_ray = r.rays == 2 && status == 6, y_ray = r.rays && status == 5;
   const long long stride = (long long)es.nblk * kBlock;
   for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
     const double l = r.l[j], u = r.u[j];
-    const double xc = fmin(fmax(r.Xc[j], l), u), xa = fmin(fmax(r.Xa[j], l), u);
-    if (x_out) x_out[j] = x_ray ? r.Xr[j] : ua ? xa : xc;
+    const double2 x2 = cand2(r.XG, j);
+    const double xc = fmin(fmax(x2.x, l), u), xa = fmin(fmax(x2.y, l), u);
+    if (x_out) x_out[j] = x_ray ? cand_r(r.XG, j) : ua ? xa : xc;
     if (x_cur) x_cur[j] = xc;
     if (x_avg) x_avg[j] = xa;
   }
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double s = r.row_kind[i] == 2 ? -1.0 : 1.0;
-    const double yc = s * r.Yc[i], ya = s * r.Ya[i];
-    if (y_out) y_out[i] = y_ray ? s * r.Yr[i] : ua ? ya : yc;
+    const double2 y2 = cand2(r.YG, i);
+    const double yc = s * y2.x, ya = s * y2.y;
+    if (y_out) y_out[i] = y_ray ? s * cand_r(r.YG, i) : ua ? ya : yc;
     if (y_cur) y_cur[i] = yc;
     if (y_avg) y_avg[i] = ya;
   }
@@ -420,13 +448,19 @@ __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, doub
 // elementwise kernels: grid_e blocks for one LP, the A^T block map (grid_c) for a batch
 inline int egrid(const KktRaw& r) { return r.tc.blk_lp ? r.grid_c : r.grid_e; }
 
+template <int LANES, int RAYS>
+cudaError_t launch_rc_mode(int which, const KktRaw& r, cudaStream_t s) {
+  if (which == KK_ROWS) return launch_pdl(k_kkt_rows<LANES, RAYS>, r.grid_r, kBlock, s, r);
+  return launch_pdl(k_kkt_cols<LANES, RAYS>, r.grid_c, kBlock, s, r);
+}
+
 template <int LANES>
 cudaError_t launch_rc(int which, const KktRaw& r, cudaStream_t s) {
-  if (which == KK_ROWS)
-    return r.rays ? launch_pdl(k_kkt_rows<LANES, true>, r.grid_r, kBlock, s, r)
-                  : launch_pdl(k_kkt_rows<LANES, false>, r.grid_r, kBlock, s, r);
-  return r.rays ? launch_pdl(k_kkt_cols<LANES, true>, r.grid_c, kBlock, s, r)
-                : launch_pdl(k_kkt_cols<LANES, false>, r.grid_c, kBlock, s, r);
+  switch (r.rays) {
+    case 0: return launch_rc_mode<LANES, 0>(which, r, s);
+    case 1: return launch_rc_mode<LANES, 1>(which, r, s);
+    default: return launch_rc_mode<LANES, 2>(which, r, s);
+  }
 }
 
 cudaError_t launch_rc_lanes(int which, int lanes, const KktRaw& r, cudaStream_t s) {

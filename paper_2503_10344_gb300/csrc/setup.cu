@@ -406,9 +406,10 @@ __global__ void k_iter_values<__nv_bfloat16>(const int* ptr, const int* col, con
 template <typename T>
 __global__ void k_iter_vectors(VecIn v, T* c, T* l, T* u, T* q, T* tw, T* sw, T* x0, T* y0,
                                double* part) {
-  // part[b*6 + k]: k = 0 ||D_c c||^2, 1 ||D_r q||^2, 2 ||c||^2, 3 ||q||^2, 4 ||x~_hint||^2,
-  // 5 ||y~_hint||^2 (the hint projected like a start, in scaled space)
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  // part[b*7 + k]: k = 0 ||D_c c||^2, 1 ||D_r q||^2, 2 ||c||^2, 3 ||q||^2, 4 ||x~_hint||^2,
+  // 5 ||y~_hint||^2 (the hint projected like a start, in scaled space), 6 columns with
+  // an infinite bound
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
     const double d = v.dc[j], cj = v.c[j];
@@ -429,6 +430,7 @@ __global__ void k_iter_vectors(VecIn v, T* c, T* l, T* u, T* q, T* tw, T* sw, T*
     x0[2 * j + 1] = (T)0;
     acc[0] += (d * cj) * (d * cj);
     acc[2] += cj * cj;
+    acc[6] += (isfinite(v.l[j]) && isfinite(v.u[j])) ? 0.0 : 1.0;
     if (v.wx) {
       const double xh = fmin(fmax(v.wx[j] / d, v.l[j] / d), v.u[j] / d);
       acc[4] += xh * xh;
@@ -457,10 +459,10 @@ __global__ void k_iter_vectors(VecIn v, T* c, T* l, T* u, T* q, T* tw, T* sw, T*
       acc[5] += yh * yh;
     }
   }
-  double out[6];
-  block_sum<6>(acc, out);
+  double out[7];
+  block_sum<7>(acc, out);
   if (threadIdx.x == 0)
-    for (int k = 0; k < 6; ++k) part[(size_t)blockIdx.x * 6 + k] = out[k];
+    for (int k = 0; k < 7; ++k) part[(size_t)blockIdx.x * 7 + k] = out[k];
 }
 
 __global__ void k_absmax_scaled(const int* ptr, const int* col, const double* val64, int nrows,
@@ -486,11 +488,11 @@ __global__ void k_absmax_scaled(const int* ptr, const int* col, const double* va
 __global__ void k_finish_scalars(const double* vpart, int nv, const double* mpart, int nmx,
                                  double* out) {
   // out: [0] ||c~||, [1] ||q~||, [2] ||c||, [3] ||q||, [4] max |K~|, [5] ||x~_hint||,
-  // [6] ||y~_hint||
-  double a[6] = {0, 0, 0, 0, 0, 0}, r[6];
+  // [6] ||y~_hint||, [7] columns with an infinite bound
+  double a[7] = {0, 0, 0, 0, 0, 0, 0}, r[7];
   for (int b = threadIdx.x; b < nv; b += kBlock)
-    for (int k = 0; k < 6; ++k) a[k] += vpart[(size_t)b * 6 + k];
-  block_sum<6>(a, r);
+    for (int k = 0; k < 7; ++k) a[k] += vpart[(size_t)b * 7 + k];
+  block_sum<7>(a, r);
   __shared__ double mx;
   if (threadIdx.x == 0) {
     double m = 0.0;
@@ -500,6 +502,7 @@ __global__ void k_finish_scalars(const double* vpart, int nv, const double* mpar
     out[4] = mx;
     out[5] = sqrt(r[4]);
     out[6] = sqrt(r[5]);
+    out[7] = r[6];
   }
 }
 
@@ -783,7 +786,7 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
                                                  part);
   RET(cudaGetLastError());
   const int gm = grid_for((long long)v.m * 32, G);
-  double* mpart = part + (size_t)gv * 6;
+  double* mpart = part + (size_t)gv * 7;
   k_absmax_scaled<<<gm, kBlock, 0, s>>>(a_ptr, a_col, a_val64, v.m, v.dr, v.dc, mpart);
   RET(cudaGetLastError());
   k_finish_scalars<<<1, kBlock, 0, s>>>(part, gv, mpart, gm, scalars_out);
@@ -792,7 +795,7 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
 
 size_t setup_part_doubles(int m, int n) {
   const int G = device_sm_count() * 8;
-  return (size_t)G * 6 + (size_t)G + 16;
+  return (size_t)G * 7 + (size_t)G + 16;
 }
 
 cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,

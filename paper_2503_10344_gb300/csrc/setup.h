@@ -59,7 +59,8 @@ cudaError_t setup_iter_values(int which_type, const int* ptr, const int* col, co
                               int scaled, void* out, cudaStream_t s);
 size_t setup_part_doubles(int m, int n);
 // scalars_out: [0] ||c~||, [1] ||q~||, [2] ||c||, [3] ||q||, [4] max |K~_ij|,
-// [5] ||x~_hint||, [6] ||y~_hint|| (scaled space, projected; 0 without a hint)
+// [5] ||x~_hint||, [6] ||y~_hint|| (scaled space, projected; 0 without a hint),
+// [7] the number of columns with an infinite bound
 cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void* u, void* q,
                                void* tw, void* sw, void* x0, void* y0, const int* a_ptr,
                                const int* a_col, const double* a_val64, double* part,

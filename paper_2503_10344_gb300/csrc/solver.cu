@@ -86,7 +86,8 @@ struct Bufs {
   int *a_ptr, *a_col, *t_ptr, *t_col;
   double *a_val64, *t_val64;
   void *a_valit, *t_valit;
-  double *q64, *dr, *dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *Xr, *Yr, *stat_r, *stat_c, *inv_dr, *inv_dc;
+  double *q64, *dr, *dc, *Xl, *Yl, *stat_r, *stat_c, *inv_dr, *inv_dc;
+  Cand *XG, *YG;
   unsigned char *row_kind, *bflags;
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
@@ -127,14 +128,10 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.q64 = (double*)ar.take(8 * M);
   b.dr = (double*)ar.take(8 * M);
   b.dc = (double*)ar.take(8 * N);
-  b.Xc = (double*)ar.take(8 * N);
-  b.Xa = (double*)ar.take(8 * N);
+  b.XG = (Cand*)ar.take(sizeof(Cand) * N);
   b.Xl = (double*)ar.take(8 * N);
-  b.Yc = (double*)ar.take(8 * M);
-  b.Ya = (double*)ar.take(8 * M);
+  b.YG = (Cand*)ar.take(sizeof(Cand) * M);
   b.Yl = (double*)ar.take(8 * M);
-  b.Xr = (double*)ar.take(8 * N);
-  b.Yr = (double*)ar.take(8 * M);
   b.stat_r = (double*)ar.take(8 * M);
   b.stat_c = (double*)ar.take(8 * N);
   b.row_kind = (unsigned char*)ar.take(M);
@@ -194,6 +191,11 @@ struct Solve {
   KktRaw kr;
   cudaStream_t s;
   int persist_grid;  // > 0: one persistent kernel per check period (one LP)
+  // while capturing a graph: a second stream and two events that let the KKT
+  // passes over A and A^T run side by side (the first waits on memory, the second
+  // on the float64 pipe); null outside a capture, where they run one after the other
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   cudaError_t persist(int max_attempts) {
     ++g_launches;
@@ -229,11 +231,47 @@ struct Solve {
   }
   cudaError_t kkt_block() {
     cudaError_t e;
-    for (int k : {KK_PREP, KK_ROWS, KK_COLS, KK_FINAL, KK_APPLY, KK_END}) {
-      ++g_launches;
-      if ((e = launch_kkt(k, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
+    if (s2 == nullptr) {
+      for (int k : {KK_PREP, KK_ROWS, KK_COLS, KK_FINAL, KK_APPLY, KK_END}) {
+        ++g_launches;
+        if ((e = launch_kkt(k, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
     }
+    g_launches += 6;
+    if ((e = launch_kkt(KK_PREP, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s2, ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_kkt(KK_COLS, lanes_ka, lanes_kt, kr, s2)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_join, s2)) != cudaSuccess) return e;
+    if ((e = launch_kkt(KK_ROWS, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, ev_join, 0)) != cudaSuccess) return e;
+    for (int k : {KK_FINAL, KK_APPLY, KK_END})
+      if ((e = launch_kkt(k, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
     return cudaSuccess;
+  }
+};
+
+// The second capture stream and the fork / join events of a captured KKT block.
+// The graph keeps the dependencies, not these objects, so they go with the capture.
+struct Fork {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t f = nullptr, j = nullptr;
+  cudaError_t make(Solve& sv) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+      sv.s2 = s2;
+      sv.ev_fork = f;
+      sv.ev_join = j;
+    }
+    return e;
+  }
+  ~Fork() {
+    if (j) cudaEventDestroy(j);
+    if (f) cudaEventDestroy(f);
+    if (s2) cudaStreamDestroy(s2);
   }
 };
 
@@ -283,7 +321,8 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
 struct SetupOut {
   Mode mode;
   int scaled, fp32;
-  double sca[7];  // ||c~||, ||q~||, ||c||, ||q||, max |K~|, ||x~_hint||, ||y~_hint||
+  double sca[8];  // ||c~||, ||q~||, ||c||, ||q||, max |K~|, ||x~_hint||, ||y~_hint||,
+                  // columns with an infinite bound
   int lanes_a, lanes_t, lanes_ka, lanes_kt, th_a, th_t, nlong_a, nlong_t;
 };
 
@@ -356,7 +395,7 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   CUDA_TRY(setup_iter_vectors(vi, fp32, bf.c_it, bf.l_it, bf.u_it, bf.q_it, bf.tw, bf.sw, bf.x[0],
                               bf.y[0], bf.a_ptr, bf.a_col, bf.a_val64, bf.part_setup, bf.scalars, s));
   g_launches += 3;
-  double sca[7];
+  double sca[8];
   CUDA_TRY(cudaMemcpyAsync(sca, bf.scalars, sizeof(sca), cudaMemcpyDeviceToHost, s));
   mark("iteration values + vectors");
   // ---- launch shapes and long rows
@@ -388,7 +427,7 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   so->mode = mode;
   so->scaled = scaled;
   so->fp32 = fp32;
-  for (int k = 0; k < 7; ++k) so->sca[k] = sca[k];
+  for (int k = 0; k < 8; ++k) so->sca[k] = sca[k];
   so->lanes_a = lanes_a;
   so->lanes_t = lanes_t;
   so->lanes_ka = lanes_ka;
@@ -666,9 +705,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   kr.row_kind = bf.row_kind;
   for (int k = 0; k < 2; ++k) { kr.x[k] = bf.x[k]; kr.y[k] = bf.y[k]; }
   kr.sum_x = bf.sum_x; kr.sum_y = bf.sum_y;
-  kr.Xc = bf.Xc; kr.Xa = bf.Xa; kr.Xl = bf.Xl; kr.Yc = bf.Yc; kr.Ya = bf.Ya; kr.Yl = bf.Yl;
-  kr.Xr = bf.Xr; kr.Yr = bf.Yr;
-  kr.rays = p->detect_infeasibility && p->terminate ? 1 : 0;
+  kr.XG = bf.XG; kr.Xl = bf.Xl; kr.YG = bf.YG; kr.Yl = bf.Yl;
+  // every column boxed: the primal ray is 0, only the dual ray is accumulated
+  kr.rays = p->detect_infeasibility && p->terminate ? (sca[7] > 0.0 ? 2 : 1) : 0;
   kr.part_r = bf.part_r; kr.part_c = bf.part_c;
   kr.grid_r_short = gr_short; kr.grid_r = gr; kr.grid_c_short = gc_short; kr.grid_c = gc;
   kr.grid_e = ge;
@@ -848,6 +887,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     } csfree{cs};
     Solve cap = sv;
     cap.s = cs;
+    Fork fork;
+    CUDA_TRY(fork.make(cap));
     const long long before = g_launches;
     cudaGraph_t graph;
     if (sv.persist_grid > 0) {
@@ -1250,7 +1291,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   // ---- global arrays
   struct G {
     int *a_ptr, *a_col, *t_ptr, *t_col, *a_long, *t_long, *tabA, *tabT;
-    double *a_val64, *t_val64, *q64, *dr, *dc, *inv_dr, *inv_dc, *Xc, *Xa, *Xl, *Yc, *Ya, *Yl, *Xr, *Yr;
+    double *a_val64, *t_val64, *q64, *dr, *dc, *inv_dr, *inv_dc, *Xl, *Yl;
+    Cand *XG, *YG;
     double *c64, *l64, *u64, *part_p, *part_d, *part_r, *part_c, *x_out, *y_out;
     void *a_valit, *t_valit, *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
     unsigned char *row_kind, *bflags;
@@ -1271,9 +1313,10 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.t_val64 = (double*)ar.take(8 * Z);
     g.a_valit = ar.take(vb * Z);
     g.t_valit = ar.take(vb * Z);
-    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yc, &g.Ya, &g.Yl, &g.Yr, &g.y_out})
-      *v = (double*)ar.take(8 * M);
-    for (double** v : {&g.dc, &g.inv_dc, &g.Xc, &g.Xa, &g.Xl, &g.Xr, &g.c64, &g.l64, &g.u64, &g.x_out})
+    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yl, &g.y_out}) *v = (double*)ar.take(8 * M);
+    g.YG = (Cand*)ar.take(sizeof(Cand) * M);
+    g.XG = (Cand*)ar.take(sizeof(Cand) * N);
+    for (double** v : {&g.dc, &g.inv_dc, &g.Xl, &g.c64, &g.l64, &g.u64, &g.x_out})
       *v = (double*)ar.take(8 * N);
     g.row_kind = (unsigned char*)ar.take(M);
     g.bflags = (unsigned char*)ar.take(N);
@@ -1321,6 +1364,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   std::vector<DevState> hs(count);
   std::vector<int> nlong_a(count), nlong_t(count), long0_a(count), long0_t(count);
   int th_a = 0, th_t = 0;
+  bool any_unboxed = false;  // some LP has a column with an infinite bound
   long long la_total = 0, lt_total = 0;
   const FacTable& ft = fac_table();
   CUDA_TRY(cudaMemcpyAsync(g.fac, &ft, sizeof(FacTable), cudaMemcpyHostToDevice, s));
@@ -1419,6 +1463,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     h.tol = p->tol;
     h.norm_c = so.sca[2];
     h.norm_q = so.sca[3];
+    any_unboxed = any_unboxed || so.sca[7] > 0.0;
     h.inv_omega = 1.0 / h.omega;
     h.tau_d = h.eta / h.omega;
     h.sigma_d = h.eta * h.omega;
@@ -1484,9 +1529,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   kr.row_kind = g.row_kind;
   for (int k = 0; k < 2; ++k) { kr.x[k] = g.x[k]; kr.y[k] = g.y[k]; }
   kr.sum_x = g.sum_x; kr.sum_y = g.sum_y;
-  kr.Xc = g.Xc; kr.Xa = g.Xa; kr.Xl = g.Xl; kr.Yc = g.Yc; kr.Ya = g.Ya; kr.Yl = g.Yl;
-  kr.Xr = g.Xr; kr.Yr = g.Yr;
-  kr.rays = p->detect_infeasibility && p->terminate ? 1 : 0;
+  kr.XG = g.XG; kr.Xl = g.Xl; kr.YG = g.YG; kr.Yl = g.Yl;
+  kr.rays = p->detect_infeasibility && p->terminate ? (any_unboxed ? 2 : 1) : 0;
   kr.part_r = g.part_r; kr.part_c = g.part_c;
   kr.grid_r_short = gridA; kr.grid_r = gridA; kr.grid_c_short = gridT; kr.grid_c = gridT;
   kr.grid_e = gridT;
@@ -1546,6 +1590,14 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     Solve cap = sv;
     cap.s = cs;
+    Fork fork;
+    {
+      const cudaError_t fe = fork.make(cap);
+      if (fe != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(PDLP_ERR_CUDA, std::string("fork stream: ") + cudaGetErrorString(fe));
+      }
+    }
     const long long before = g_launches;
     cudaGraph_t graph;
     CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
