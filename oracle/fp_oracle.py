@@ -336,13 +336,13 @@ def fp_run(lp, x_lp, y_lp, is_int, strategy=TYPE, seed=1, node_limit=None, final
     lp2.l = np.where(is_int, fixed, lp.l)
     lp2.u = np.where(is_int, fixed, lp.u)
     # feasible when every row holds to FEAS_TOL max(1, |b_i|) (reading: the relative 1e-6
-    # of section 4, per row); a first-order point that misses a row is solved once more
-    # from itself at a hundred times tighter tolerance
+    # of section 4, per row); a first-order point that misses a row is polished (A13:
+    # the same PDHG on the objective-free problem from that point, to final_tol)
     r = PO.solve(lp2, PO.Params(tol=final_tol, iter_limit=500_000))
     x = np.where(is_int, fixed, r.x)
     viol = max_row_violation(lp, x)
     if r.status == PO.STATUS_OPTIMAL and viol > FEAS_TOL:
-        r = PO.solve(lp2, PO.Params(tol=final_tol * 1e-2, iter_limit=500_000), x0=r.x, y0=r.y)
+        r = PO.polish_primal(lp2, r.x, PO.Params(tol=final_tol, iter_limit=500_000))
         x = np.where(is_int, fixed, r.x)
         viol = max_row_violation(lp, x)
     ok = r.status == PO.STATUS_OPTIMAL and viol <= FEAS_TOL

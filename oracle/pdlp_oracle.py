@@ -58,6 +58,8 @@ are listed one by one in the design notes and marked "reading" here:
       passing.  The primal test is taken first.  The certificate is returned
       in place of the dual (primal infeasible) or primal (dual infeasible)
       output.
+  A13 primal feasibility polishing (``polish_primal``): the same iteration on
+      the LP with its objective replaced by 0, from (x, 0).
 
 Part I (the definition every result is judged by): for a point x in [l,u] and
 y in Y of the canonical problem,
@@ -499,3 +501,22 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                   unscale_x(x), unscale_y(y), unscale_x(xa), unscale_y(ya),
                   eta, omega, chosen_avg, time.perf_counter() - t0, trace, attempt_trace,
                   check_trace, rays)
+
+
+# ---------------------------------------------------------------- A13 ------
+def polish_primal(lp, x, params: Params | None = None) -> Result:
+    """A13: primal feasibility polishing of a point x (reading of PDLP's feasibility
+    polishing; the paper only needs feasible points for its heuristic, section 2).
+
+    The same PDHG (A0-A12) on the primal feasibility problem -- the LP with its
+    objective replaced by 0 -- started from (x, y = 0).  With c = 0 every dual
+    iterate that stays 0 leaves x unchanged, so a feasible x is a fixed point;
+    otherwise the iteration moves x onto the feasible set with y as the
+    multipliers of the violated rows.  The result's x is the polished point
+    (status OPTIMAL: relative KKT of the feasibility problem <= tol, so
+    ||r_p|| <= tol (1 + ||q||)); an infeasible LP ends PRIMAL_INFEASIBLE.
+    """
+    import copy
+    lp0 = copy.copy(lp)
+    lp0.c = np.zeros(lp.n)
+    return solve(lp0, params, x0=x, y0=None)
