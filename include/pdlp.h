@@ -229,6 +229,21 @@ int pdlp_solve_hinted(const pdlp_csr* A, const double* b, const char* sense, con
                       double* x_out, double* y_out, pdlp_result* r,
                       const pdlp_diagnostics* diag);
 
+/* Primal feasibility polishing of a point x_in[n] (PDLP's feasibility polishing
+ * as read here; the paper's heuristic needs LP points that satisfy the rows,
+ * section 2): the PDHG of pdlp_solve on the same rows and bounds with the
+ * objective replaced by 0, started from (x_in, y = 0).  A strictly feasible x_in
+ * is a fixed point; a point that misses rows moves onto the feasible set, by a
+ * distance of the order of its violation, the objective changing accordingly.
+ * p->tol bounds the relative KKT of the objective-free problem, so the rows'
+ * residual ||r_p||_2 <= tol (1 + ||b||_2).  x_out[n] (required) receives the
+ * polished point, y_out[m] (may be NULL) the multipliers of the violated rows;
+ * an infeasible LP ends with status PDLP_PRIMAL_INFEASIBLE and its Farkas ray.
+ * Inputs, ownership and return codes as pdlp_solve. */
+int pdlp_polish_primal(const pdlp_csr* A, const double* b, const char* sense, const double* l,
+                       const double* u, const pdlp_params* p, const double* x_in,
+                       double* x_out, double* y_out, pdlp_result* r);
+
 /* Solve `count` LPs of uneven size together (north-star pattern "batched":
  * relaxations such as those left after the partial fixings of the heuristic).
  * Arrays of per-LP HOST pointers in the layout of pdlp_solve; one parameter
@@ -275,13 +290,17 @@ int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, con
  * Runs the same device setup as pdlp_solve_device on the same DEVICE inputs,
  * then launches each fused kernel `reps` times back to back from a CUDA graph
  * (step attempts stay live: no KKT check falls due) and writes into
- * ms_per_launch[6] and bytes_per_launch[6], for
+ * ms_per_launch[7] and bytes_per_launch[7], for
  *   [0] the primal step kernel (A^T SpMV + projected update),
  *   [1] the dual step kernel (A SpMV + extrapolated update + step decision),
  *   [2] one whole attempt ([0] then [1]),
  *   [3] the float64 KKT pass over A, [4] the float64 KKT pass over A^T,
  *   [5] one attempt inside the persistent step kernel (reps attempts in one
  *       launch; 0 when p->persistent is 0),
+ *   [6] one whole KKT block as a check runs it (candidates, both passes, the
+ *       decision, the restart, the flags; a reset of the check flag before each,
+ *       so each block starts after a full dependency as in a solve; bytes: [3]
+ *       + [4]),
  * the average device time per launch in ms (graph launch gaps included) and
  * the algorithmic bytes per launch (every array the kernel needs, each element
  * once, gathered vectors counted once).  Workspace and stream as in
@@ -332,8 +351,8 @@ int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, const char* se
 #define FP_DUAL 2     /* rows by descending |y|, their integers by descending |reduced cost| */
 #define FP_TYPE 3     /* binaries first, then general integers (stable) */
 #define FP_FEASIBLE 1    /* all integers fixed and the final LP's point satisfies every
-                            row to 1e-6 max(1, |b_i|) (solved at final_lp_tol, and once
-                            more at final_lp_tol / 100 from that point if a row misses) */
+                            row to 1e-6 max(1, |b_i|) (solved at final_lp_tol; a point
+                            that misses a row is polished, pdlp_polish_primal) */
 #define FP_INFEASIBLE 2  /* search exhausted, root infeasible, or final LP infeasible: abort */
 #define FP_NODE_LIMIT 3  /* node limit reached */
 #define FP_NO_FINAL_LP 4 /* all integers fixed; final LP not requested */

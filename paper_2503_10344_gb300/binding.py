@@ -93,6 +93,8 @@ def lib():
         L.pdlp_time_kernels.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 5 + \
             [C.POINTER(PdlpParams), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
              C.c_void_p]
+        L.pdlp_polish_primal.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 4 + \
+            [C.POINTER(PdlpParams)] + [C.c_void_p] * 3 + [C.POINTER(PdlpResult)]
         L.pdlp_error_string.argtypes = [C.c_int]
         L.pdlp_error_string.restype = C.c_char_p
         L.pdlp_last_error.restype = C.c_char_p
@@ -182,6 +184,26 @@ def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates:
     return x, y, out, diag
 
 
+def pdlp_polish_primal(lp, x, params: PdlpParams | None = None):
+    """Primal feasibility polishing of ``x`` (host buffers): the PDHG on the
+    objective-free problem from (x, 0).  Returns (x_polished, y, result dict)."""
+    L = lib()
+    p = params or default_params()
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    row_ptr = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(lp.col, dtype=np.int32)
+    val = f64(lp.val)
+    b, l, u, xi = f64(lp.b), f64(lp.l), f64(lp.u), f64(x)
+    sense = np.ascontiguousarray(lp.sense, dtype=np.uint8)
+    csr = PdlpCsr(lp.m, lp.n, int(row_ptr[-1]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    xo = np.empty(lp.n)
+    yo = np.empty(lp.m)
+    res = PdlpResult()
+    _check(L.pdlp_polish_primal(C.byref(csr), _ptr(b), _ptr(sense), _ptr(l), _ptr(u), C.byref(p),
+                                _ptr(xi), _ptr(xo), _ptr(yo) if lp.m else None, C.byref(res)))
+    return xo, yo, res.as_dict()
+
+
 def workspace_size(m: int, n: int, nnz: int, params: PdlpParams | None = None) -> int:
     p = params or default_params()
     return int(lib().pdlp_workspace_size(m, n, nnz, C.byref(p)))
@@ -244,7 +266,8 @@ def pdlp_solve_device(dlp: DeviceLP, params: PdlpParams | None = None, x0=None, 
     return x_out, y_out[: dlp.m], res.as_dict()
 
 
-KERNELS = ("primal_step", "dual_step", "attempt", "kkt_rows", "kkt_cols", "persistent_attempt")
+KERNELS = ("primal_step", "dual_step", "attempt", "kkt_rows", "kkt_cols", "persistent_attempt",
+           "kkt_block")
 
 
 def time_kernels(dlp: DeviceLP, params: PdlpParams | None = None, reps: int = 200,

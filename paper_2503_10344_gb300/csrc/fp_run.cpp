@@ -419,8 +419,8 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     fu[j] = is_int[j] ? d.lo[j] : u[j];
   }
   // The final point counts as feasible when every row holds to kFeasTol max(1, |b_i|).
-  // A first-order solution at final_lp_tol may miss a row by a little: then the
-  // LP is solved once more from that point at a hundred times tighter tolerance.
+  // A first-order solution at final_lp_tol may miss a row by a little: then that
+  // point is polished (the same PDHG on the objective-free problem from it).
   pdlp_params pp;
   pdlp_default_params(&pp);
   pp.tol = prm->final_lp_tol;
@@ -433,10 +433,9 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
   for (int j = 0; j < P.n; ++j) x_out[j] = is_int[j] ? d.lo[j] : xf[j];
   double viol = max_row_violation(P, x_out);
   if (lr.status == PDLP_OPTIMAL && viol > kFeasTol) {
-    std::vector<double> x0(xf), y0(yf);
-    pp.tol = prm->final_lp_tol * 1e-2;
-    rc = pdlp_solve(A, b, sense, c, fl.data(), fu.data(), &pp, x0.data(), y0.data(), xf.data(),
-                    yf.data(), &lr, nullptr);
+    const std::vector<double> x0(xf);
+    rc = pdlp_polish_primal(A, b, sense, fl.data(), fu.data(), &pp, x0.data(), xf.data(),
+                            yf.data(), &lr);
     if (rc != PDLP_OK) return rc;
     lp_iters += lr.iters;
     for (int j = 0; j < P.n; ++j) x_out[j] = is_int[j] ? d.lo[j] : xf[j];

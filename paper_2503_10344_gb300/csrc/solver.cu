@@ -309,9 +309,9 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
 // fused kernel is launched `reps` times back to back from a CUDA graph.
 struct TimingReq {
   int reps;
-  double* ms;     // [6] primal, dual, attempt (primal + dual), KKT pass over A, over A^T,
+  double* ms;     // [7] primal, dual, attempt (primal + dual), KKT pass over A, over A^T,
                   // one attempt inside the persistent kernel
-  double* bytes;  // [6] algorithmic bytes per launch of the same kernels (per attempt for [5])
+  double* bytes;  // [7] algorithmic bytes per launch of the same kernels (per attempt for [5])
 };
 
 static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
@@ -1097,7 +1097,9 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   } efree{a, b};
   Solve cap = sv;
   cap.s = cs;
-  // which: 0 primal, 1 dual, 2 attempt, 3 KKT rows, 4 KKT cols
+  Fork fork;
+  CUDA_TRY(fork.make(cap));
+  // which: 0 primal, 1 dual, 2 attempt, 3 KKT rows, 4 KKT cols, 5 persistent, 6 KKT block
   auto time_one = [&](int which, double* out_ms) -> int {
     cudaGraph_t g;
     CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -1108,6 +1110,11 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
       if (ce == cudaSuccess && (which == 1 || which == 2)) ce = cap.iter(IK_DUAL);
       if (which == 3) ce = launch_kkt(KK_ROWS, sv.lanes_ka, sv.lanes_kt, sv.kr, cs);
       if (which == 4) ce = launch_kkt(KK_COLS, sv.lanes_ka, sv.lanes_kt, sv.kr, cs);
+      if (which == 6) {
+        // check_due is 0 or 1, so setting its low byte (little endian) makes it 1
+        ce = cudaMemsetAsync(&st->check_due, 1, 1, cs);
+        if (ce == cudaSuccess) ce = cap.kkt_block();
+      }
     }
     cudaError_t ee = cudaStreamEndCapture(cs, &g);
     if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
@@ -1128,7 +1135,7 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
     *out_ms = (double)ms / tq.reps;
-    g_launches += which == 5 ? 2 : 2LL * tq.reps * (which == 2 ? 2 : 1);
+    g_launches += which == 5 ? 2 : 2LL * tq.reps * (which == 2 ? 2 : which == 6 ? 6 : 1);
     return PDLP_OK;
   };
   int rc;
@@ -1142,6 +1149,8 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   CUDA_TRY(cudaMemcpyAsync(&st->check_due, &one, sizeof(int), cudaMemcpyHostToDevice, s));
   for (int w = 3; w < 5; ++w)
     if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
+  // whole KKT blocks last: they move the restart anchors and the iterate
+  if ((rc = time_one(6, &tq.ms[6])) != PDLP_OK) return rc;
   CUDA_TRY(cudaMemcpyAsync(&st->check_due, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   // algorithmic bytes per launch: every array the kernel needs, each element once
@@ -1162,6 +1171,7 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   tq.bytes[4] = 4 * (N + 1) + Z * (4 + val64) + M * 16 + N * (32 + 16 + 8);
   // one attempt of the persistent kernel: the primal and dual bytes
   tq.bytes[5] = tq.bytes[2];
+  tq.bytes[6] = tq.bytes[3] + tq.bytes[4];
   return PDLP_OK;
 }
 
@@ -1915,6 +1925,22 @@ int pdlp_solve_hinted(const pdlp_csr* A, const double* b, const char* sense, con
   if (!x_hint || (!y_hint && A && A->m > 0))
     return fail(PDLP_ERR_INVALID_INPUT, "pdlp_solve_hinted needs x_hint[n] and y_hint[m]");
   return solve_host(A, b, sense, c, l, u, p, x0, y0, x_hint, y_hint, x_out, y_out, r, diag);
+}
+
+int pdlp_polish_primal(const pdlp_csr* A, const double* b, const char* sense, const double* l,
+                       const double* u, const pdlp_params* p, const double* x_in,
+                       double* x_out, double* y_out, pdlp_result* r) {
+  if (!A || A->n < 1 || !x_in || !x_out)
+    return fail(PDLP_ERR_INVALID_INPUT, "pdlp_polish_primal needs A, x_in[n] and x_out[n]");
+  // the objective-free problem from (x_in, 0)
+  const std::vector<double> zero_c((size_t)A->n, 0.0);
+  std::vector<double> y_tmp;
+  if (!y_out && A->m > 0) {
+    y_tmp.resize((size_t)A->m);
+    y_out = y_tmp.data();
+  }
+  return solve_host(A, b, sense, zero_c.data(), l, u, p, x_in, nullptr, nullptr, nullptr, x_out,
+                    y_out, r, nullptr);
 }
 
 int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, const double* c,
