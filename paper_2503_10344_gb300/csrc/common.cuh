@@ -252,6 +252,51 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (&out)[NV]) {
   __syncthreads();
 }
 
+// Deterministic sum of NV <= 16 float64 values over a block, thread 0 gets the
+// result.  Within a warp a reduce-scatter: at each of the offsets 16, 8, 4, 2 a
+// lane keeps the half of its values its offset bit selects and adds the partner's
+// copy of that half, so 8 + 4 + 2 + 1 (+ 1 at offset 1) float64 additions per lane
+// replace 5 NV shuffle-additions (a float64 warp instruction holds GB300's float64
+// pipe ~16 cycles however many lanes it uses); then one thread per value adds the
+// warps' totals in warp order.
+template <int NV>
+__device__ __forceinline__ void block_sum_rs(const double (&v)[NV], double (&out)[NV]) {
+  static_assert(NV >= 1 && NV <= 16, "block_sum_rs takes at most 16 values");
+  __shared__ double sh[kWarps][16];
+  __shared__ double res[16];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double a[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[k] = k < NV ? v[k] : 0.0;
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const double send = hi ? a[k] : a[k + h];
+      const double keep = hi ? a[k + h] : a[k];
+      a[k] = keep + __shfl_xor_sync(full, send, o);
+    }
+  }
+  a[0] += __shfl_xor_sync(full, a[0], 1);
+  // lanes L and L ^ 1 now hold the warp total of value 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of L)
+  if ((lane & 1) == 0) sh[w][((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                          ((lane >> 1) & 1)] = a[0];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int i = 0; i < kWarps; ++i) t += sh[i][threadIdx.x];
+    res[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = res[k];
+  }
+  __syncthreads();
+}
+
 // Deterministic block sum in the element type T (float reductions stay in the
 // float32 pipe); thread 0 gets the result.
 template <typename T>
@@ -307,7 +352,7 @@ __device__ __forceinline__ void reduce_partials(const double* part, int stride, 
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] += part[(size_t)k * stride + i];
   }
-  block_sum<NV>(v, out);
+  block_sum_rs<NV>(v, out);
 }
 
 __device__ __forceinline__ double kkt_omega(double omega, double rp2, double rd2, double gap2) {

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
   };
   rows_all<true, LANES, Acc>(sp, r.a_ptr, r.a_thresh, load, epi);
   double out[NV];
-  block_sum<NV>(acc, out);
+  block_sum_rs<NV>(acc, out);
   if (threadIdx.x == 0)
     for (int k = 0; k < NV; ++k) r.part_r[(size_t)k * r.grid_r + blockIdx.x] = out[k];
 }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
   };
   rows_all<true, LANES, Acc>(sp, r.t_ptr, r.t_thresh, load, epi);
   double out[NV];
-  block_sum<NV>(acc, out);
+  block_sum_rs<NV>(acc, out);
   if (threadIdx.x == 0)
     for (int k = 0; k < NV; ++k) r.part_c[(size_t)k * r.grid_c + blockIdx.x] = out[k];
 }
