@@ -295,21 +295,23 @@ __global__ void k_finish_transpose(const int* a_ptr, int m, const double* a_val6
 // warp instruction costs the FP64 pipe ~16 cycles whatever the active lanes,
 // so a short row gets few lanes instead of a whole warp.
 template <int LANES>
-__global__ void k_rowstat(const int* ptr, const int* col, const double* val, int nrows,
-                          const double* own, const double* other, int own_is_row, int op,
-                          double power, double* out) {
+__device__ __forceinline__ void rowstat_rows(const int* ptr, const int* col, const double* val,
+                                             int nrows, const double* own, const double* other,
+                                             int own_is_row, int op, double power, double* out,
+                                             int bidx, int nblk) {
   const int lane = threadIdx.x & (LANES - 1);
-  const long long G = (long long)gridDim.x * blockDim.x / LANES;
-  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / LANES; r < nrows; r += G) {
+  const long long G = (long long)nblk * blockDim.x / LANES;
+  for (long long r = ((long long)bidx * blockDim.x + threadIdx.x) / LANES; r < nrows; r += G) {
     const int s = ptr[r], e = ptr[r + 1];
     const double so = own[r];
     double acc = 0.0;
     for (int p = s + lane; p < e; p += LANES) {
       const double a = fabs(val[p]);
       const double o = other[col[p]];
-      const double kt = own_is_row ? (so * a) * o : (o * a) * so;
+      // (D_r |K|) D_c rounded product by product, never fused into an add
+      const double kt = own_is_row ? __dmul_rn(__dmul_rn(so, a), o) : __dmul_rn(__dmul_rn(o, a), so);
       if (op == 0) acc = fmax(acc, kt);
-      else acc += power == 1.0 ? kt : pow(kt, power);
+      else acc = __dadd_rn(acc, power == 1.0 ? kt : pow(kt, power));
     }
     const unsigned mask = LANES == 32 ? 0xffffffffu
                                       : (((1u << LANES) - 1u) << ((threadIdx.x & 31) & ~(LANES - 1)));
@@ -322,6 +324,41 @@ __global__ void k_rowstat(const int* ptr, const int* col, const double* val, int
   }
 }
 
+// One statistics pass of the scaling over both orientations in one launch: blocks
+// [0, ga) take the rows of A (row statistics), the rest the rows of A^T (column
+// statistics); the two halves read the same D_r, D_c and run side by side.
+struct StatPass {
+  const int *a_ptr, *a_col, *t_ptr, *t_col;
+  const double *a_val, *t_val, *dr, *dc;
+  int m, n, ga, op;
+  double pow_r, pow_c;
+  double *stat_r, *stat_c;
+};
+
+template <int LA, int LT>
+__global__ void k_stat_pass(StatPass q) {
+  pdl_enter();
+  if ((int)blockIdx.x < q.ga)
+    rowstat_rows<LA>(q.a_ptr, q.a_col, q.a_val, q.m, q.dr, q.dc, 1, q.op, q.pow_r, q.stat_r,
+                     blockIdx.x, q.ga);
+  else
+    rowstat_rows<LT>(q.t_ptr, q.t_col, q.t_val, q.n, q.dc, q.dr, 0, q.op, q.pow_c, q.stat_c,
+                     blockIdx.x - q.ga, gridDim.x - q.ga);
+}
+
+// D_r /= sqrt(stat_r), D_c /= sqrt(stat_c) (a zero statistic leaves the factor)
+__global__ void k_apply_scale2(double* dr, const double* stat_r, int m, double* dc,
+                               const double* stat_c, int n) {
+  pdl_enter();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)m + n;
+       i += stride) {
+    double* d = i < m ? dr + i : dc + (i - m);
+    const double st = i < m ? stat_r[i] : stat_c[i - m];
+    *d = *d / (st > 0.0 ? sqrt(st) : 1.0);
+  }
+}
+
 // lanes per row for an average row length (about four entries per lane)
 static int stat_lanes(double avg) {
   int l = 2;
@@ -329,28 +366,44 @@ static int stat_lanes(double avg) {
   return l;
 }
 
-static cudaError_t rowstat(const int* ptr, const int* col, const double* val, int nrows, long long nnz,
-                           const double* own, const double* other, int own_is_row, int op,
-                           double power, double* out, cudaStream_t s) {
-  const int G = device_sm_count() * 8;
-  const int L = stat_lanes(nrows > 0 ? (double)nnz / nrows : 1.0);
-  const int g = grid_for((long long)nrows * L, G);
-  switch (L) {
-    case 2: k_rowstat<2><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
-    case 4: k_rowstat<4><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
-    case 8: k_rowstat<8><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
-    case 16: k_rowstat<16><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
-    default: k_rowstat<32><<<g, kBlock, 0, s>>>(ptr, col, val, nrows, own, other, own_is_row, op, power, out); break;
+template <int LA>
+static cudaError_t stat_pass_la(int lt, int grid, const StatPass& q, cudaStream_t s) {
+  switch (lt) {
+    case 1: return launch_pdl(k_stat_pass<LA, 1>, grid, kBlock, s, q);
+    case 2: return launch_pdl(k_stat_pass<LA, 2>, grid, kBlock, s, q);
+    case 4: return launch_pdl(k_stat_pass<LA, 4>, grid, kBlock, s, q);
+    case 8: return launch_pdl(k_stat_pass<LA, 8>, grid, kBlock, s, q);
+    case 16: return launch_pdl(k_stat_pass<LA, 16>, grid, kBlock, s, q);
+    default: return launch_pdl(k_stat_pass<LA, 32>, grid, kBlock, s, q);
   }
-  return cudaGetLastError();
 }
 
-__global__ void k_apply_scale(double* d, const double* stat, int nrows) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride) {
-    const double s = stat[r];
-    d[r] = d[r] / (s > 0.0 ? sqrt(s) : 1.0);
+// one statistics pass (op 0: max |K~|, op 1: sum |K~|^pow) over A and A^T, then
+// the application of both scale vectors.  A maximum is exact in any order; a sum
+// runs one thread per row over the entries in storage order (rows of A by column,
+// rows of A^T by row), the order of a sequential CSR row sum, so that the
+// Pock-Chambolle factors round exactly as a plain sequential sum does.
+static cudaError_t stat_pass(const ScaleIn& sc, double* dr, double* dc, double* stat_r,
+                             double* stat_c, int op, double pow_r, double pow_c, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  const int la = op == 1 ? 1 : stat_lanes(sc.m > 0 ? (double)sc.nnz / sc.m : 1.0);
+  const int lt = op == 1 ? 1 : stat_lanes((double)sc.nnz / sc.n);
+  const int ga = sc.m > 0 ? grid_for((long long)sc.m * la, G) : 0;
+  const int gt = grid_for((long long)sc.n * lt, G);
+  const StatPass q{sc.a_ptr, sc.a_col, sc.t_ptr, sc.t_col, sc.a_val64, sc.t_val64, dr, dc,
+                   sc.m, sc.n, ga, op, pow_r, pow_c, stat_r, stat_c};
+  cudaError_t e;
+  switch (la) {
+    case 1: e = stat_pass_la<1>(lt, ga + gt, q, s); break;
+    case 2: e = stat_pass_la<2>(lt, ga + gt, q, s); break;
+    case 4: e = stat_pass_la<4>(lt, ga + gt, q, s); break;
+    case 8: e = stat_pass_la<8>(lt, ga + gt, q, s); break;
+    case 16: e = stat_pass_la<16>(lt, ga + gt, q, s); break;
+    default: e = stat_pass_la<32>(lt, ga + gt, q, s); break;
   }
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_apply_scale2, grid_for((long long)sc.m + sc.n, G), kBlock, s, dr, stat_r,
+                    sc.m, dc, stat_c, sc.n);
 }
 
 __global__ void k_fill(double* p, double v, long long n) {
@@ -720,23 +773,10 @@ cudaError_t setup_scaling(const ScaleIn& sc, double* dr, double* dc, double* sta
   RET(cudaGetLastError());
   k_fill<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, 1.0, sc.n);
   RET(cudaGetLastError());
-  const long long znz = sc.nnz;
-  for (int it = 0; it < sc.ruiz_iters; ++it) {
-    RET(rowstat(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, znz, dr, dc, 1, 0, 1.0, stat_r, s));
-    RET(rowstat(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, znz, dc, dr, 0, 0, 1.0, stat_c, s));
-    k_apply_scale<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, stat_r, sc.m);
-    RET(cudaGetLastError());
-    k_apply_scale<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, stat_c, sc.n);
-    RET(cudaGetLastError());
-  }
-  if (sc.pc_alpha >= 0.0) {
-    RET(rowstat(sc.a_ptr, sc.a_col, sc.a_val64, sc.m, znz, dr, dc, 1, 1, 2.0 - sc.pc_alpha, stat_r, s));
-    RET(rowstat(sc.t_ptr, sc.t_col, sc.t_val64, sc.n, znz, dc, dr, 0, 1, sc.pc_alpha, stat_c, s));
-    k_apply_scale<<<grid_for(sc.m, G), kBlock, 0, s>>>(dr, stat_r, sc.m);
-    RET(cudaGetLastError());
-    k_apply_scale<<<grid_for(sc.n, G), kBlock, 0, s>>>(dc, stat_c, sc.n);
-    RET(cudaGetLastError());
-  }
+  for (int it = 0; it < sc.ruiz_iters; ++it)
+    RET(stat_pass(sc, dr, dc, stat_r, stat_c, 0, 1.0, 1.0, s));
+  if (sc.pc_alpha >= 0.0)
+    RET(stat_pass(sc, dr, dc, stat_r, stat_c, 1, 2.0 - sc.pc_alpha, sc.pc_alpha, s));
   return cudaSuccess;
 }
 

@@ -379,7 +379,7 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
              p->pc_alpha, nnz};
   mark("value format");
   CUDA_TRY(setup_scaling(sc, bf.dr, bf.dc, bf.stat_r, bf.stat_c, s));
-  g_launches += 2 + 4 * p->ruiz_iters + (p->pc_alpha >= 0 ? 4 : 0);
+  g_launches += 2 + 2 * p->ruiz_iters + (p->pc_alpha >= 0 ? 2 : 0);
   mark("Ruiz + Pock-Chambolle");
   CUDA_TRY(setup_kkt_aux(m, n, bf.dr, bf.dc, l, u, bf.inv_dr, bf.inv_dc, bf.bflags, s));
   ++g_launches;
