@@ -1165,10 +1165,14 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   // dual: row_ptr, col, values; x pairs gathered; y, q (+ sw), row kind, y write, sum r/w
   tq.bytes[1] = 4 * (M + 1) + Z * (4 + sv_b) + N * 2 * sx + M * (sx * (1 + 1 + impl + 1 + 2) + 1);
   tq.bytes[2] = tq.bytes[0] + tq.bytes[1];
-  // KKT over A: row_ptr, col, float64 values; both candidates gathered; q, D_r, kind, y c/a, y anchor
-  tq.bytes[3] = 4 * (M + 1) + Z * (4 + val64) + N * 16 + M * (8 + 8 + 1 + 16 + 8);
-  // KKT over A^T: row_ptr, col, values; both dual candidates gathered; c, l, u, D_c, x c/a, x anchor
-  tq.bytes[4] = 4 * (N + 1) + Z * (4 + val64) + M * 16 + N * (32 + 16 + 8);
+  // certificate terms: the dual ray (rays >= 1) and the primal ray (rays == 2)
+  const double ry = sv.kr.rays >= 1 ? 8 : 0, rx = sv.kr.rays == 2 ? 8 : 0;
+  // KKT over A: row_ptr, col, float64 values; x candidates gathered (and the primal ray);
+  // q, D_r, 1/D_r, kind, y candidates (and the dual ray), y anchor
+  tq.bytes[3] = 4 * (M + 1) + Z * (4 + val64) + N * (16 + rx) + M * (8 + 8 + 8 + 1 + 16 + ry + 8);
+  // KKT over A^T: row_ptr, col, values; y candidates gathered (and the dual ray); c, l, u,
+  // D_c, 1/D_c, bound flags, x candidates (and the primal ray), x anchor
+  tq.bytes[4] = 4 * (N + 1) + Z * (4 + val64) + M * (16 + ry) + N * (8 + 16 + 8 + 8 + 1 + 16 + rx + 8);
   // one attempt of the persistent kernel: the primal and dual bytes
   tq.bytes[5] = tq.bytes[2];
   tq.bytes[6] = tq.bytes[3] + tq.bytes[4];
