@@ -289,11 +289,14 @@ int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, con
 /* Kernel timing for roofline reports (a profiling aid; not needed to solve).
  * Runs the same device setup as pdlp_solve_device on the same DEVICE inputs,
  * then launches each fused kernel `reps` times back to back from a CUDA graph
- * (step attempts stay live: no KKT check falls due) and writes into
+ * (step attempts stay live: no KKT check falls due; every timing starts from
+ * the state after setup) and writes into
  * ms_per_launch[7] and bytes_per_launch[7], for
  *   [0] the primal step kernel (A^T SpMV + projected update),
- *   [1] the dual step kernel (A SpMV + extrapolated update + step decision),
- *   [2] one whole attempt ([0] then [1]),
+ *   [1] the dual half-step (A SpMV + extrapolated update, then the step
+ *       decision), timed as [2] - [0]: repeated on its own it would step y
+ *       away without bound,
+ *   [2] one whole attempt (the primal step, then the dual half-step),
  *   [3] the float64 KKT pass over A, [4] the float64 KKT pass over A^T,
  *   [5] one attempt inside the persistent step kernel (reps attempts in one
  *       launch; 0 when p->persistent is 0),

@@ -133,7 +133,11 @@ __device__ __forceinline__ Span make_span(const Tables& t, int nrows1, int nshor
     s.lp = 0;
     s.row0 = 0;
     s.nrows = nrows1;
-    s.bidx = blockIdx.x;
+    // the long-row blocks (the grid's last gridDim.x - nshort1 logical blocks) take the
+    // lowest block indices, so that they are scheduled first and their long loops
+    // overlap the short rows instead of trailing behind them
+    const int nl = (int)gridDim.x - nshort1;
+    s.bidx = (int)blockIdx.x < nl ? nshort1 + (int)blockIdx.x : (int)blockIdx.x - nl;
     s.nshort = nshort1;
     s.nblk = gridDim.x;
     s.part0 = 0;

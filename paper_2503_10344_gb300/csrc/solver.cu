@@ -1078,6 +1078,12 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   static const int zero = 0, one = 1;
   CUDA_TRY(cudaMemcpyAsync(&st->period, &big_period, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&st->iter_limit, &big_limit, sizeof(long long), cudaMemcpyHostToDevice, s));
+  // the state every timing starts from: a step kind repeated on its own can drive the
+  // iterate out of range (dual steps without primal steps grow y without bound), and
+  // a NaN ends the iteration at the next decision, after which the kernels return at
+  // entry; each timed launch therefore starts from this state
+  DevState st0;
+  CUDA_TRY(cudaMemcpyAsync(&st0, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   cudaStream_t cs;
   CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1127,10 +1133,15 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
       cudaGraphExec_t g;
       ~GFree() { cudaGraphExecDestroy(g); }
     } gfree{ge};
+    DevState run = st0;
+    run.check_due = (which == 3 || which == 4) ? 1 : 0;
+    CUDA_TRY(cudaMemcpyAsync(st, &run, sizeof(DevState), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaGraphLaunch(ge, s));  // warm
+    CUDA_TRY(cudaMemcpyAsync(st, &run, sizeof(DevState), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(a, s));
     CUDA_TRY(cudaGraphLaunch(ge, s));
     CUDA_TRY(cudaEventRecord(b, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // `run` is read by the copies above
     CUDA_TRY(cudaEventSynchronize(b));
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
@@ -1139,14 +1150,16 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
     return PDLP_OK;
   };
   int rc;
-  for (int w = 0; w < 3; ++w)
-    if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
+  // the primal step and the whole attempt repeat what a solve does; the dual half-step
+  // is their difference (repeated on its own it would step y away without bound)
+  if ((rc = time_one(0, &tq.ms[0])) != PDLP_OK) return rc;
+  if ((rc = time_one(2, &tq.ms[2])) != PDLP_OK) return rc;
+  tq.ms[1] = tq.ms[2] - tq.ms[0];
   if (sv.persist_grid > 0) {
     if ((rc = time_one(5, &tq.ms[5])) != PDLP_OK) return rc;
   } else {
     tq.ms[5] = 0.0;
   }
-  CUDA_TRY(cudaMemcpyAsync(&st->check_due, &one, sizeof(int), cudaMemcpyHostToDevice, s));
   for (int w = 3; w < 5; ++w)
     if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
   // whole KKT blocks last: they move the restart anchors and the iterate
