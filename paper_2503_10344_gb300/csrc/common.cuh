@@ -12,6 +12,8 @@ namespace pdlp {
 
 constexpr int kBlock = 256;         // threads per block of every streaming kernel
 constexpr int kWarps = kBlock / 32;
+// resident blocks per SM the float32 step kernels are compiled for
+constexpr int kStepBlocksPerSmF32 = 6;
 
 // Matrix value formats of the iteration matrix.
 struct Pattern {};  // every stored value is exactly +1: no value array at all

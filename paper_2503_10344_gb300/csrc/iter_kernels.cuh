@@ -276,7 +276,7 @@ __device__ __forceinline__ void rows_all(const Span& sp, const int* ptr, int thr
 // budget 42): the float32 solve of the 50k x 200k covering LP needs 782 blocks
 // for one pass, six per SM keep them all resident; the float64 kernels keep
 // their registers (a tighter budget spills)
-template <typename T> struct StepOcc { static constexpr int value = 6; };
+template <typename T> struct StepOcc { static constexpr int value = kStepBlocksPerSmF32; };
 template <> struct StepOcc<double> { static constexpr int value = 1; };
 
 // epilogue operands of a row: constant ones (read before the dependent-launch

@@ -663,10 +663,16 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   // float32 step kernels: one group of lanes per two rows, rows grid-strided;
   // float64 kernels (float64 steps, KKT passes): warp tiles of 32 rows
   const bool tiled = mode == MODE_FP64;
+  // float32 step kernels: at most one wave of resident blocks (six per SM) including the
+  // long-row blocks, the short rows grid-strided; a second partial wave would trail
+  const int lt_blk = std::min(nlong_t, kMaxLongBlocks), la_blk = std::min(nlong_a, kMaxLongBlocks);
+  const int wave = kStepBlocksPerSmF32 * device_sm_count();
+  const int MBp = std::max(device_sm_count(), wave - lt_blk);
+  const int MBd = std::max(device_sm_count(), wave - la_blk);
   const int gp_short = tiled ? grid_for(((long long)n + 31) / 32 * 32, MB)
-                             : grid_for(((long long)n + 1) / 2 * lanes_t, MB);
+                             : grid_for(((long long)n + 1) / 2 * lanes_t, MBp);
   const int gd_short = tiled ? grid_for(((long long)std::max(m, 1) + 31) / 32 * 32, MB)
-                             : grid_for(((long long)std::max(m, 1) + 1) / 2 * lanes_a, MB);
+                             : grid_for(((long long)std::max(m, 1) + 1) / 2 * lanes_a, MBd);
   const int gp = gp_short + std::min(nlong_t, kMaxLongBlocks);
   const int gd = gd_short + std::min(nlong_a, kMaxLongBlocks);
   const int ge = grid_for(std::max(m, n), MB);
@@ -777,8 +783,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s, 0};
   if (p->autotune && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
     auto set_grids = [&](int lt, int la) -> int {
-      const int gps = tiled ? gp_short : grid_for(((long long)n + 1) / 2 * lt, MB);
-      const int gds = tiled ? gd_short : grid_for(((long long)std::max(m, 1) + 1) / 2 * la, MB);
+      const int gps = tiled ? gp_short : grid_for(((long long)n + 1) / 2 * lt, MBp);
+      const int gds = tiled ? gd_short : grid_for(((long long)std::max(m, 1) + 1) / 2 * la, MBd);
       sv.ir.grid_p_short = gps;
       sv.ir.grid_p = gps + std::min(nlong_t, kMaxLongBlocks);
       sv.ir.grid_d_short = gds;
