@@ -359,17 +359,25 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
   struct Frame {
     size_t mark;
     int var;
+    size_t pos;  // position of var in the order
     std::vector<Change> alts;
   };
   std::vector<Frame> frames;
   int status = 0;
   while (true) {
+    // the first integer of the order that is not fixed yet.  Every integer before the
+    // top frame's position was fixed when that frame was made, and the search below it
+    // only undoes to that state or narrows domains, so the scan starts there (a scan
+    // from the front made the search quadratic in the number of integers)
     int j = -1;
-    for (int v : order)
+    size_t pos = frames.empty() ? 0 : frames.back().pos;
+    for (; pos < order.size(); ++pos) {
+      const int v = order[pos];
       if (d.hi[v] - d.lo[v] > 0.5) {
         j = v;
         break;
       }
+    }
     if (j < 0) {
       status = FP_FEASIBLE;
       break;
@@ -380,7 +388,7 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     }
     ++r->nodes;
     const double a = lp_fixing_value(x_lp[j], d.lo[j], d.hi[j], rng.uniform());
-    frames.push_back({d.trail.size(), j, {}});
+    frames.push_back({d.trail.size(), j, pos, {}});
     branching(d.lo[j], d.hi[j], a, c[j], frames.back().alts);
     bool descended = false;
     while (!descended) {
