@@ -46,9 +46,19 @@ struct Change {
   double lo, hi;
 };
 
+// at most three alternatives per branching node, kept in place (no allocation per node)
+struct Alts {
+  Change c[3];
+  int n = 0;
+  void push_back(Change x) { c[n++] = x; }
+  bool empty() const { return n == 0; }
+  Change back() const { return c[n - 1]; }
+  void pop_back() { --n; }
+};
+
 // Alg. 1: bound changes of integer x_i with fixing value a, increasing priority
-void branching(double l, double u, double a, double c, std::vector<Change>& out) {
-  out.clear();
+void branching(double l, double u, double a, double c, Alts& out) {
+  out.n = 0;
   if (l < a && a < u) {
     if (c > 0) {
       out.push_back({a + 1, u});
@@ -153,6 +163,7 @@ bool propagate(const Problem& P, Domains& d, const int32_t* rows, int64_t nrows,
     const char sn = P.sense[i];
     const bool le = sn == 'L' || sn == 'E', ge = sn == 'G' || sn == 'E';
     double minact = 0.0, maxact = 0.0;
+    double maxrange = 0.0, mag = 0.0;  // largest |a_j| (hi_j - lo_j); sum of |a_j| |bounds|
     int ninf_min = 0, ninf_max = 0;
     for (int64_t p = s; p < e; ++p) {
       const double a = P.val[p];
@@ -165,12 +176,21 @@ bool propagate(const Problem& P, Domains& d, const int32_t* rows, int64_t nrows,
         if (hi == INFINITY) ++ninf_min; else minact += a * hi;
         if (lo == -INFINITY) ++ninf_max; else maxact += a * lo;
       }
+      maxrange = std::max(maxrange, fabs(a) * (hi - lo));
+      mag += fabs(a) * ((lo > -INFINITY ? fabs(lo) : 0.0) + (hi < INFINITY ? fabs(hi) : 0.0));
     }
     const double tol = kFeasTol * std::max(1.0, fabs(bi));
     if ((le && ninf_min == 0 && minact > bi + tol) || (ge && ninf_max == 0 && maxact < bi - tol)) {
       ok = false;
       continue;
     }
+    // No entry can be tightened when the row's slack covers every entry's whole range
+    // (with a margin far above the rounding of the activities), or when two or more
+    // entries are unbounded on the side that would derive a bound: skip the pass.
+    const double margin = 1e-9 * (fabs(bi) + mag);
+    const bool quiet_le = !le || ninf_min >= 2 || (ninf_min == 0 && bi - minact >= maxrange + margin);
+    const bool quiet_ge = !ge || ninf_max >= 2 || (ninf_max == 0 && maxact - bi >= maxrange + margin);
+    if (quiet_le && quiet_ge) continue;
     for (int64_t p = s; p < e && ok; ++p) {
       const double a = P.val[p];
       const int j = P.col[p];
@@ -360,7 +380,7 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     size_t mark;
     int var;
     size_t pos;  // position of var in the order
-    std::vector<Change> alts;
+    Alts alts;
   };
   std::vector<Frame> frames;
   int status = 0;
