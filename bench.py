@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--kernels-only", action="store_true",
                     help="only time the fused kernels (pdlp_time_kernels) and print them")
     ap.add_argument("--reps", type=int, default=200)
-    ap.add_argument("--workload", default="set_cover", choices=["set_cover", "batch", "energy"],
+    ap.add_argument("--workload", default="set_cover", choices=["set_cover", "batch", "energy", "fp"],
                     help="batch: 256 uneven covering sub-LPs (m in [2000, 40000], n = 4m, "
                          "10-50 %% of the columns fixed), solved together by pdlp_solve_batch")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -431,9 +431,42 @@ def run_energy(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fp(args):
+    """The paper's heuristic end to end on the covering LP (section 2): the LP relaxation
+    by PDLP to 1e-4 on the GPU, fix-and-propagate on the host from its point, the final
+    LP with every integer fixed; the time breakdown the paper reports (section 4.1)."""
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    lp = lpgen.set_cover(2025)
+    prm = P.default_params(tol=1e-4, precision=args.precision)
+    P.pdlp_solve(lp, prm)  # warm: graph capture and library load
+    rows = []
+    for strat in ("type", "frac", "redcost", "dual"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x_lp, y_lp, r = P.pdlp_solve(lp, prm)
+        t_lp = time.perf_counter() - t0
+        x, f = P.fp_run(lp, x_lp, y_lp, strategy=strat, final_lp=True, final_lp_tol=1e-8)
+        total = t_lp + f["search_s"] + f["lp_s"]
+        rows.append({"strategy": strat, "status": f["status"], "obj": f["obj"],
+                     "lp_bound": r["dual_obj"], "gap": (f["obj"] - r["dual_obj"]) / abs(f["obj"])
+                     if f["status"] == P.FP_FEASIBLE else None,
+                     "initial_lp_s": t_lp, "search_s": f["search_s"], "final_lp_s": f["lp_s"],
+                     "initial_lp_share": t_lp / total, "nodes": f["nodes"]})
+    print(json.dumps({"workload": "fix-and-propagate on set_cover m=50000 n=200000 (all binary)",
+                      "precision": args.precision, "runs": rows}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.workload == "energy" and a.impl == "gpu":
+    if a.workload == "fp" and a.impl == "gpu":
+        run_fp(a)
+    elif a.workload == "energy" and a.impl == "gpu":
         run_energy(a)
     elif a.workload == "batch" and a.impl == "gpu":
         run_batch(a)
