@@ -96,6 +96,52 @@ struct Problem {
   const double* u;
   std::vector<int64_t> at_ptr;  // rows of each column, ascending
   std::vector<int32_t> at_row;
+  std::vector<double> at_val;   // the matching coefficients
+};
+
+// Row activities kept up to date as bounds change: a filter only.  A row whose cached
+// slack clears, with a margin, the largest range its entries had at the root is one
+// whose full pass could neither find it infeasible nor tighten a bound, so the pass is
+// skipped; every other row runs the full pass, which recomputes the activities exactly
+// (as the oracle does) and resets the cache.  The margin (2e-9 of the row's magnitude)
+// exceeds the rounding an incremental sum gathers over the 2^20 updates allowed
+// between two exact recomputations.
+struct RowAct {
+  std::vector<double> minact, maxact;  // finite parts
+  std::vector<int32_t> ninf_min, ninf_max;
+  std::vector<double> range0;          // max_j |a_ij| (u_j - l_j) at the root (inf if unbounded)
+  std::vector<double> mag0;            // sum_j |a_ij| 2 max(|l_j|, |u_j|), finite bounds
+  std::vector<uint32_t> updates;
+  static constexpr uint32_t kMaxUpdates = 1u << 20;
+
+  // contribution of bound b (a finite value, or +-inf) to an activity
+  static void add(double& act, int32_t& ninf, double a, double b, int sign) {
+    if (isinf(b)) ninf += sign;
+    else act += sign > 0 ? a * b : -(a * b);
+  }
+  // column j (entries of the column lists) moves from [olo, ohi] to [nlo, nhi]
+  void change(const Problem& P, int j, double olo, double ohi, double nlo, double nhi) {
+    for (int64_t q = P.at_ptr[j]; q < P.at_ptr[j + 1]; ++q) {
+      const int i = P.at_row[q];
+      const double a = P.at_val[q];
+      const bool pos = a > 0;
+      add(minact[i], ninf_min[i], a, pos ? olo : ohi, -1);
+      add(minact[i], ninf_min[i], a, pos ? nlo : nhi, +1);
+      add(maxact[i], ninf_max[i], a, pos ? ohi : olo, -1);
+      add(maxact[i], ninf_max[i], a, pos ? nhi : nlo, +1);
+      if (updates[i] < kMaxUpdates) ++updates[i];
+    }
+  }
+  bool quiet(const Problem& P, int i) const {
+    if (updates[i] >= kMaxUpdates) return false;
+    const char sn = P.sense[i];
+    const bool le = sn == 'L' || sn == 'E', ge = sn == 'G' || sn == 'E';
+    const double bi = P.b[i];
+    const double need = range0[i] + 2e-9 * (fabs(bi) + mag0[i]);
+    const bool q_le = !le || ninf_min[i] >= 2 || (ninf_min[i] == 0 && bi - minact[i] >= need);
+    const bool q_ge = !ge || ninf_max[i] >= 2 || (ninf_max[i] == 0 && maxact[i] - bi >= need);
+    return q_le && q_ge;
+  }
 };
 
 struct Domains {
@@ -106,8 +152,11 @@ struct Domains {
     double lo, hi;
   };
   std::vector<Entry> trail;
+  const Problem* P = nullptr;  // with act: row activities follow every change
+  RowAct* act = nullptr;
   void set(int j, double l, double h) {
     trail.push_back({j, lo[j], hi[j]});
+    if (act) act->change(*P, j, lo[j], hi[j], l, h);
     lo[j] = l;
     hi[j] = h;
   }
@@ -115,6 +164,7 @@ struct Domains {
     while (trail.size() > mark) {
       const Entry e = trail.back();
       trail.pop_back();
+      if (act) act->change(*P, e.j, lo[e.j], hi[e.j], e.lo, e.hi);
       lo[e.j] = e.lo;
       hi[e.j] = e.hi;
     }
@@ -158,6 +208,7 @@ bool propagate(const Problem& P, Domains& d, const int32_t* rows, int64_t nrows,
     const int i = queue[head++];
     inq[i] = 0;
     if (!ok) continue;  // drain the queue flags
+    if (d.act && d.act->quiet(P, i)) continue;
     const int64_t s = P.rp[i], e = P.rp[i + 1];
     const double bi = P.b[i];
     const char sn = P.sense[i];
@@ -178,6 +229,13 @@ bool propagate(const Problem& P, Domains& d, const int32_t* rows, int64_t nrows,
       }
       maxrange = std::max(maxrange, fabs(a) * (hi - lo));
       mag += fabs(a) * ((lo > -INFINITY ? fabs(lo) : 0.0) + (hi < INFINITY ? fabs(hi) : 0.0));
+    }
+    if (d.act) {  // the exact activities replace the cached ones
+      d.act->minact[i] = minact;
+      d.act->maxact[i] = maxact;
+      d.act->ninf_min[i] = ninf_min;
+      d.act->ninf_max[i] = ninf_max;
+      d.act->updates[i] = 0;
     }
     const double tol = kFeasTol * std::max(1.0, fabs(bi));
     if ((le && ninf_min == 0 && minact > bi + tol) || (ge && ninf_max == 0 && maxact < bi - tol)) {
@@ -352,10 +410,15 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
   }
   for (int j = 0; j < P.n; ++j) P.at_ptr[j + 1] += P.at_ptr[j];
   P.at_row.resize(A->nnz);
+  P.at_val.resize(A->nnz);
   {
     std::vector<int64_t> cur(P.at_ptr.begin(), P.at_ptr.end() - 1);
     for (int i = 0; i < P.m; ++i)
-      for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) P.at_row[cur[P.col[p]]++] = i;
+      for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
+        const int64_t q = cur[P.col[p]]++;
+        P.at_row[q] = i;
+        P.at_val[q] = P.val[p];
+      }
   }
   Domains d;
   d.lo.assign(l, l + P.n);
@@ -369,6 +432,28 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     if (isfinite(d.hi[j])) d.hi[j] = floor(d.hi[j] + kIntEps);
   }
   const int64_t limit = prm->node_limit > 0 ? prm->node_limit : 10 * n_int;
+  // row activities of the root domains, then kept up to date by every bound change
+  RowAct act;
+  act.minact.assign(P.m, 0.0);
+  act.maxact.assign(P.m, 0.0);
+  act.ninf_min.assign(P.m, 0);
+  act.ninf_max.assign(P.m, 0);
+  act.range0.assign(P.m, 0.0);
+  act.mag0.assign(P.m, 0.0);
+  act.updates.assign(P.m, 0);
+  for (int i = 0; i < P.m; ++i)
+    for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
+      const double a = P.val[p];
+      const int j = P.col[p];
+      const double lo = d.lo[j], hi = d.hi[j];
+      RowAct::add(act.minact[i], act.ninf_min[i], a, a > 0 ? lo : hi, +1);
+      RowAct::add(act.maxact[i], act.ninf_max[i], a, a > 0 ? hi : lo, +1);
+      act.range0[i] = std::max(act.range0[i], fabs(a) * (hi - lo));
+      act.mag0[i] += fabs(a) * 2.0 *
+                     std::max(isfinite(lo) ? fabs(lo) : 0.0, isfinite(hi) ? fabs(hi) : 0.0);
+    }
+  d.P = &P;
+  d.act = &act;
   std::vector<uint8_t> inq(P.m, 0);
   std::vector<int32_t> queue, all_rows(P.m);
   for (int i = 0; i < P.m; ++i) all_rows[i] = i;

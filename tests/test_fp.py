@@ -168,6 +168,35 @@ def test_cabi_search_matches_oracle(P, seed, strategy):
             np.testing.assert_array_equal(x[ints], np.array(dom.lo)[ints])
 
 
+def _mixed_lp(seed):
+    """Mixed-sense LP with free columns, half of the boxed columns integer."""
+    lp = lpgen.random_sparse_lp(seed, 60, 90, density=0.08)
+    ints = np.random.default_rng(seed).random(lp.n) < 0.5
+    lp.is_int = (ints & np.isfinite(lp.l) & np.isfinite(lp.u)).astype(np.uint8)
+    return lp
+
+
+@pytest.mark.parametrize("maker", [lambda: lpgen.set_cover_fixed(20, 150), lambda: _mixed_lp(30),
+                                   lambda: lpgen.mip_relaxation(5, m=120, n=240, density=0.04)],
+                         ids=["cover_fixed", "mixed_free_eq", "denser_relaxation"])
+@pytest.mark.parametrize("strategy", ["frac", "dual"])
+def test_cabi_search_matches_oracle_on_other_shapes(P, maker, strategy):
+    """The same node-for-node agreement on covering sub-LPs (fixed columns, >=-rows), mixed
+    senses with free continuous columns, and a denser relaxation (the row filter of the
+    C++ search, which skips rows whose slack covers every range, must not change a decision)."""
+    lp = maker()
+    r = O.solve(lp, O.Params(tol=1e-4, iter_limit=20000))
+    sid = {"frac": F.FRAC, "dual": F.DUAL}[strategy]
+    for draw_seed in (1, 7):
+        st, dom, nodes, backtracks = F.fp_search(lp, r.x, r.y, lp.is_int, sid, draw_seed)
+        x, res = P.fp_run(lp, r.x, r.y, strategy=strategy, seed=draw_seed, final_lp=False)
+        assert res["status"] == (F.NO_FINAL_LP if st == F.FEASIBLE else st)
+        assert res["nodes"] == nodes and res["backtracks"] == backtracks
+        if st == F.FEASIBLE:
+            ints = lp.is_int == 1
+            np.testing.assert_array_equal(x[ints], np.array(dom.lo)[ints])
+
+
 def test_cabi_rejects_bad_arguments(P):
     lp, x, y = hand_mip()
     with pytest.raises(P.PdlpError):
