@@ -324,9 +324,14 @@ def run_kernels_only(args):
     import lpgen
     import paper_2503_10344_gb300 as P
 
-    lp = lpgen.set_cover(2025)
+    if args.workload == "energy":
+        lp = lpgen.energy_system()
+        prec = "fp32" if args.precision == "bf16" else args.precision
+    else:
+        lp = lpgen.set_cover(2025)
+        prec = args.precision
     d = P.DeviceLP(lp)
-    kt = P.time_kernels(d, P.default_params(tol=1e-4, precision=args.precision, **lane_params(args)),
+    kt = P.time_kernels(d, P.default_params(tol=1e-4, precision=prec, **lane_params(args)),
                         reps=args.reps)
     torch.cuda.synchronize()
     print(json.dumps({k: {"us": 1e3 * v["ms"], "bytes": v["bytes"],
@@ -464,14 +469,14 @@ def run_fp(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.workload == "fp" and a.impl == "gpu":
+    if a.kernels_only and a.impl == "gpu":
+        run_kernels_only(a)
+    elif a.workload == "fp" and a.impl == "gpu":
         run_fp(a)
     elif a.workload == "energy" and a.impl == "gpu":
         run_energy(a)
     elif a.workload == "batch" and a.impl == "gpu":
         run_batch(a)
-    elif a.kernels_only:
-        run_kernels_only(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
