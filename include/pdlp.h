@@ -141,6 +141,12 @@ typedef struct {
   int detect_infeasibility; /* 1 (default): test the two certificates above at each KKT
                            check (with terminate = 1); 0: never (an infeasible LP runs to
                            its iteration or time limit) */
+  int debug_skip_barrier; /* fault-handling tests only (default 0): with persistent = 1,
+                           block 0 of the persistent step kernel skips its grid-barrier
+                           arrivals, so every block's bounded wait (2^16 polls in this
+                           mode, 2^23 otherwise) runs out; the kernel records the failure
+                           and returns, and the call returns PDLP_ERR_TIMEOUT with the
+                           device context intact */
 } pdlp_params;
 
 typedef struct {

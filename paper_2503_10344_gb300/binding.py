@@ -41,7 +41,7 @@ class PdlpParams(C.Structure):
                 ("terminate", C.c_int), ("lanes_A", C.c_int), ("lanes_AT", C.c_int),
                 ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int),
                 ("persistent", C.c_int), ("autotune", C.c_int),
-                ("detect_infeasibility", C.c_int)]
+                ("detect_infeasibility", C.c_int), ("debug_skip_barrier", C.c_int)]
 
 
 class PdlpResult(C.Structure):

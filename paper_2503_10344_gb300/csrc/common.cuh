@@ -97,10 +97,15 @@ struct DevState {
   // grid barrier of the persistent step kernel (arrivals, generation, failure flag)
   unsigned int bar_count, bar_gen;
   int bar_err;
+  int bar_skip;          // fault-handling tests: block 0 skips its barrier arrivals
+  long long spin_limit;  // polls of one barrier wait before it gives up
 };
 
 // status value of a persistent step kernel whose bounded barrier wait gave up
 constexpr int kStatusWaitFailed = 99;
+// polls of one grid-barrier wait (seconds at L2 latency); fault-handling tests use 2^16
+constexpr long long kSpinLimit = 1LL << 23;
+constexpr long long kSpinLimitTest = 1LL << 16;
 
 // ---------------------------------------------------------------- batches
 // Launch tables of a batch of LPs solved together (all NULL for one LP): the

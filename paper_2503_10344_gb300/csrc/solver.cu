@@ -741,6 +741,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   hs.restarts_on = p->restarts ? 1 : 0;
   hs.terminate = p->terminate ? 1 : 0;
   hs.detect_inf = p->detect_infeasibility ? 1 : 0;
+  hs.bar_skip = p->debug_skip_barrier ? 1 : 0;
+  hs.spin_limit = p->debug_skip_barrier ? kSpinLimitTest : kSpinLimit;
   hs.tol = p->tol;
   hs.norm_c = sca[2];
   hs.norm_q = sca[3];
@@ -1493,6 +1495,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     h.restarts_on = p->restarts ? 1 : 0;
     h.terminate = p->terminate ? 1 : 0;
     h.detect_inf = p->detect_infeasibility ? 1 : 0;
+    h.spin_limit = kSpinLimit;
     h.tol = p->tol;
     h.norm_c = so.sca[2];
     h.norm_q = so.sca[3];

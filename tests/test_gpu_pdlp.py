@@ -402,6 +402,21 @@ def test_primal_weight_hint_zero_part_falls_back(P):
     assert r2["omega"] == 3.0
 
 
+# ---------------------------------------------------------------- fault handling
+def test_missed_barrier_arrival_times_out_and_the_context_survives(P):
+    """A grid-barrier arrival that never comes (block 0 of the persistent kernel skips its
+    arrivals): every block's bounded wait runs out, the kernel records the failure and
+    returns, the call reports PDLP_ERR_TIMEOUT, and the next solve on the same context
+    succeeds.  No trap, no fault: only a wait that ends."""
+    lp = lpgen.set_cover(7, m=2000, n=8000)
+    with pytest.raises(P.PdlpError, match="PDLP_ERR_TIMEOUT"):
+        P.pdlp_solve(lp, P.default_params(persistent=1, debug_skip_barrier=1))
+    _, _, r = P.pdlp_solve(lp, P.default_params(persistent=1))
+    assert r["status"] == P.PDLP_OPTIMAL
+    _, _, r = P.pdlp_solve(lp, P.default_params())
+    assert r["status"] == P.PDLP_OPTIMAL
+
+
 # ---------------------------------------------------------------- persistent step kernel
 @pytest.mark.parametrize("name", list(INSTANCES))
 def test_persistent_kernel_matches_two_launch_form(P, name):
