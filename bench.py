@@ -324,15 +324,20 @@ def run_kernels_only(args):
     import lpgen
     import paper_2503_10344_gb300 as P
 
-    if args.workload == "energy":
-        lp = lpgen.energy_system()
-        prec = "fp32" if args.precision == "bf16" else args.precision
+    if args.workload == "batch":
+        kt = P.time_kernels_batch(lpgen.set_cover_batch(args.batch_count),
+                                  P.default_params(tol=1e-4, precision=args.precision,
+                                                   **lane_params(args)), reps=args.reps)
     else:
-        lp = lpgen.set_cover(2025)
-        prec = args.precision
-    d = P.DeviceLP(lp)
-    kt = P.time_kernels(d, P.default_params(tol=1e-4, precision=prec, **lane_params(args)),
-                        reps=args.reps)
+        if args.workload == "energy":
+            lp = lpgen.energy_system()
+            prec = "fp32" if args.precision == "bf16" else args.precision
+        else:
+            lp = lpgen.set_cover(2025)
+            prec = args.precision
+        d = P.DeviceLP(lp)
+        kt = P.time_kernels(d, P.default_params(tol=1e-4, precision=prec, **lane_params(args)),
+                            reps=args.reps)
     torch.cuda.synchronize()
     print(json.dumps({k: {"us": 1e3 * v["ms"], "bytes": v["bytes"],
                           "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9}
@@ -366,6 +371,15 @@ def run_batch(args):
             launches += res[0]["kernel_launches"]
     ok = sum(r["status"] == P.PDLP_OPTIMAL for r in res)
     it = np.array([r["iters"] for r in res])
+    # roofline of the step kernels over the whole batch, every LP live (HBM: ~3 GB per attempt)
+    kt = P.time_kernels_batch(lps, prm, reps=20)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    kern = {k: {"us": 1e3 * v["ms"], "bytes": v["bytes"], "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                "frac": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peak}
+            for k, v in kt.items() if v["ms"] > 0}
+    dom = max(("primal_step", "dual_step"), key=lambda k: kt[k]["ms"])
     line = {"metric": METRIC, "value": sum(iters) / sum(solve), "unit": UNIT + " (sum over the batch)",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -377,6 +391,9 @@ def run_batch(args):
             "solve_s": sum(solve) / args.steps, "setup_s": sum(setup) / args.steps,
             "lps_per_s": len(lps) / (sum(solve) / args.steps), "optimal": ok,
             "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
+                         "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": None,
+                         "peak_source": "measured" if peaks else "fallback", "kernels": kern},
             "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 

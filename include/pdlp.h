@@ -235,6 +235,17 @@ int pdlp_solve_hinted(const pdlp_csr* A, const double* b, const char* sense, con
                       double* x_out, double* y_out, pdlp_result* r,
                       const pdlp_diagnostics* diag);
 
+/* pdlp_time_kernels for a batch (pdlp_solve_batch's inputs, host buffers): the same
+ * setup as pdlp_solve_batch, then each fused kernel over the whole batch (every LP
+ * live) `reps` times from a CUDA graph; ms_per_launch[7] and bytes_per_launch[7] as in
+ * pdlp_time_kernels, the bytes summed over the batch ([5] and [6] are 0: batches use
+ * the two-launch form, and the whole KKT block is timed for single LPs only).  The batch form of spec pattern 2; the paper has no
+ * counterpart.  Returns PDLP_OK or an error code. */
+int pdlp_time_kernels_batch(int count, const pdlp_csr* const* A, const double* const* b,
+                            const char* const* sense, const double* const* c,
+                            const double* const* l, const double* const* u, const pdlp_params* p,
+                            int reps, double* ms_per_launch, double* bytes_per_launch);
+
 /* Primal feasibility polishing of a point x_in[n] (PDLP's feasibility polishing
  * as read here; the paper's heuristic needs LP points that satisfy the rows,
  * section 2): the PDHG of pdlp_solve on the same rows and bounds with the

@@ -9,7 +9,7 @@ from .binding import (FP_DUAL, FP_FEASIBLE, FP_FRAC, FP_INFEASIBLE, FP_NODE_LIMI
                       PDLP_OPTIMAL, PDLP_TIME_LIMIT, PDLP_PRIMAL_INFEASIBLE, PDLP_DUAL_INFEASIBLE,
                       DeviceLP, PdlpError, default_params, lib,
                       pdlp_polish_primal, pdlp_solve, pdlp_solve_batch, pdlp_solve_device, pdlp_solve_device_noalloc,
-                      time_kernels,
+                      time_kernels, time_kernels_batch,
                       workspace_size)
 from .gnn import GnnGraph, GnnModel, pdlp_solve_warm, start_kkt
 
@@ -18,5 +18,5 @@ __all__ = ["FP_DUAL", "FP_FEASIBLE", "FP_FRAC", "FP_INFEASIBLE", "FP_NODE_LIMIT"
            "PDLP_OPTIMAL", "PDLP_TIME_LIMIT", "PDLP_PRIMAL_INFEASIBLE", "PDLP_DUAL_INFEASIBLE",
            "DeviceLP", "PdlpError", "default_params", "lib",
            "pdlp_polish_primal", "pdlp_solve", "pdlp_solve_batch", "pdlp_solve_device",
-           "pdlp_solve_device_noalloc", "time_kernels",
+           "pdlp_solve_device_noalloc", "time_kernels", "time_kernels_batch",
            "workspace_size", "GnnGraph", "GnnModel", "pdlp_solve_warm", "start_kkt"]

@@ -378,16 +378,10 @@ def fp_run(lp, x_lp, y_lp=None, is_int=None, strategy="type", seed: int = 1, nod
     return x, r.as_dict()
 
 
-def pdlp_solve_batch(lps, params: PdlpParams | None = None, want_y: bool = True):
-    """Solve a list of LPs together (host buffers); returns (xs, ys, results)."""
-    L = lib()
-    if not getattr(L, "_batch_ready", False):
-        L.pdlp_solve_batch.argtypes = [C.c_int, C.c_void_p] + [C.c_void_p] * 5 + \
-            [C.POINTER(PdlpParams), C.c_void_p, C.c_void_p, C.c_void_p]
-        L._batch_ready = True
-    p = params or default_params()
+def _batch_arrays(lps, xs=None, ys=None):
+    """The pointer arrays of a batch call; `keep` holds the numpy arrays alive."""
     k = len(lps)
-    keep = []  # keeps the numpy arrays alive during the call
+    keep = []
 
     def arr(a, dt):
         a = np.ascontiguousarray(a, dtype=dt)
@@ -396,8 +390,6 @@ def pdlp_solve_batch(lps, params: PdlpParams | None = None, want_y: bool = True)
 
     csrs = (PdlpCsr * k)()
     ptrs = {name: (C.c_void_p * k)() for name in ("b", "sense", "c", "l", "u", "x", "y")}
-    xs = [np.empty(lp.n) for lp in lps]
-    ys = [np.empty(lp.m) for lp in lps]
     for i, lp in enumerate(lps):
         rp = arr(lp.row_ptr, np.int64)
         csrs[i] = PdlpCsr(lp.m, lp.n, int(rp[-1]), _ptr(rp), _ptr(arr(lp.col, np.int32)),
@@ -407,11 +399,47 @@ def pdlp_solve_batch(lps, params: PdlpParams | None = None, want_y: bool = True)
         ptrs["c"][i] = _ptr(arr(lp.c, np.float64))
         ptrs["l"][i] = _ptr(arr(lp.l, np.float64))
         ptrs["u"][i] = _ptr(arr(lp.u, np.float64))
-        ptrs["x"][i] = _ptr(xs[i])
-        ptrs["y"][i] = _ptr(ys[i]) if want_y else None
+        ptrs["x"][i] = _ptr(xs[i]) if xs is not None else None
+        ptrs["y"][i] = _ptr(ys[i]) if ys is not None else None
+    keep.append(csrs)
     csr_ptrs = (C.c_void_p * k)(*[C.cast(C.pointer(csrs[i]), C.c_void_p) for i in range(k)])
+    return csr_ptrs, ptrs, keep
+
+
+def pdlp_solve_batch(lps, params: PdlpParams | None = None, want_y: bool = True):
+    """Solve a list of LPs together (host buffers); returns (xs, ys, results)."""
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.pdlp_solve_batch.argtypes = [C.c_int, C.c_void_p] + [C.c_void_p] * 5 + \
+            [C.POINTER(PdlpParams), C.c_void_p, C.c_void_p, C.c_void_p]
+        L._batch_ready = True
+    p = params or default_params()
+    k = len(lps)
+    xs = [np.empty(lp.n) for lp in lps]
+    ys = [np.empty(lp.m) for lp in lps]
+    csr_ptrs, ptrs, keep = _batch_arrays(lps, xs, ys if want_y else None)
     res = (PdlpResult * k)()
     rc = L.pdlp_solve_batch(k, csr_ptrs, ptrs["b"], ptrs["sense"], ptrs["c"], ptrs["l"], ptrs["u"],
                             C.byref(p), ptrs["x"], ptrs["y"], res)
     _check(rc)
+    del keep
     return xs, ys, [res[i].as_dict() for i in range(k)]
+
+
+def time_kernels_batch(lps, params: PdlpParams | None = None, reps: int = 20) -> dict:
+    """Average device ms and algorithmic bytes per launch of each fused kernel over a
+    whole batch (every LP live), as :func:`time_kernels` for one LP."""
+    L = lib()
+    if not getattr(L, "_batch_timing_ready", False):
+        L.pdlp_time_kernels_batch.argtypes = [C.c_int, C.c_void_p] + [C.c_void_p] * 5 + \
+            [C.POINTER(PdlpParams), C.c_int, C.c_void_p, C.c_void_p]
+        L._batch_timing_ready = True
+    p = params or default_params()
+    csr_ptrs, ptrs, keep = _batch_arrays(lps)
+    ms = np.zeros(len(KERNELS))
+    by = np.zeros(len(KERNELS))
+    rc = L.pdlp_time_kernels_batch(len(lps), csr_ptrs, ptrs["b"], ptrs["sense"], ptrs["c"],
+                                   ptrs["l"], ptrs["u"], C.byref(p), reps, _ptr(ms), _ptr(by))
+    _check(rc)
+    del keep
+    return {k: {"ms": float(ms[i]), "bytes": float(by[i])} for i, k in enumerate(KERNELS)}

@@ -315,7 +315,7 @@ struct TimingReq {
 };
 
 static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
-                                    const TimingReq& tq);
+                                    const TimingReq& tq, int count);
 
 // Products of the device setup of one LP (rows A0-A3) into the buffers of a Bufs.
 struct SetupOut {
@@ -827,7 +827,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     CUDA_TRY(cudaStreamSynchronize(s));
     h1 = std::chrono::steady_clock::now();
   }
-  if (tq && !no_alloc) return time_kernels_after_setup(sv, bf.st, mode, nnz, *tq);
+  if (tq && !no_alloc) return time_kernels_after_setup(sv, bf.st, mode, nnz, *tq, 1);
   if (no_alloc) {
     // the same chunk of step attempts and KKT block, launched directly on the
     // caller's stream; the four-byte status is read into pageable memory
@@ -1077,22 +1077,22 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
 }
 
 static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long nnz,
-                                    const TimingReq& tq) {
+                                    const TimingReq& tq, int count) {
   const cudaStream_t s = sv.s;
   const int m = sv.m, n = sv.n;
-  // keep every step attempt live: no KKT check becomes due while timing
-  const int big_period = 1 << 30;
-  const long long big_limit = 1LL << 62;
-  static const int zero = 0, one = 1;
-  CUDA_TRY(cudaMemcpyAsync(&st->period, &big_period, sizeof(int), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(&st->iter_limit, &big_limit, sizeof(long long), cudaMemcpyHostToDevice, s));
-  // the state every timing starts from: a step kind repeated on its own can drive the
-  // iterate out of range (dual steps without primal steps grow y without bound), and
-  // a NaN ends the iteration at the next decision, after which the kernels return at
-  // entry; each timed launch therefore starts from this state
-  DevState st0;
-  CUDA_TRY(cudaMemcpyAsync(&st0, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  // the state every timing starts from (one per LP of a batch): every step attempt stays
+  // live (no KKT check falls due, no iteration limit), and a step kind repeated on its own
+  // can drive the iterate out of range (dual steps without primal steps grow y without
+  // bound) -- a NaN ends the iteration at the next decision, after which the kernels
+  // return at entry -- so each timed launch starts from this state
+  std::vector<DevState> st0((size_t)count);
+  CUDA_TRY(cudaMemcpyAsync(st0.data(), st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  for (DevState& h : st0) {
+    h.period = 1 << 30;
+    h.iter_limit = 1LL << 62;
+  }
+  static const int zero = 0;
   cudaStream_t cs;
   CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   struct SFree {
@@ -1141,11 +1141,12 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
       cudaGraphExec_t g;
       ~GFree() { cudaGraphExecDestroy(g); }
     } gfree{ge};
-    DevState run = st0;
-    run.check_due = (which == 3 || which == 4) ? 1 : 0;
-    CUDA_TRY(cudaMemcpyAsync(st, &run, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    std::vector<DevState> run(st0);
+    for (DevState& h : run) h.check_due = (which == 3 || which == 4) ? 1 : 0;
+    const size_t sb = sizeof(DevState) * run.size();
+    CUDA_TRY(cudaMemcpyAsync(st, run.data(), sb, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaGraphLaunch(ge, s));  // warm
-    CUDA_TRY(cudaMemcpyAsync(st, &run, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(st, run.data(), sb, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(a, s));
     CUDA_TRY(cudaGraphLaunch(ge, s));
     CUDA_TRY(cudaEventRecord(b, s));
@@ -1170,9 +1171,15 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   }
   for (int w = 3; w < 5; ++w)
     if ((rc = time_one(w, &tq.ms[w])) != PDLP_OK) return rc;
-  // whole KKT blocks last: they move the restart anchors and the iterate
-  if ((rc = time_one(6, &tq.ms[6])) != PDLP_OK) return rc;
-  CUDA_TRY(cudaMemcpyAsync(&st->check_due, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  // whole KKT blocks last: they move the restart anchors and the iterate (one LP: the
+  // graph sets that LP's check flag before each block; a batch's block is not timed)
+  if (count == 1) {
+    if ((rc = time_one(6, &tq.ms[6])) != PDLP_OK) return rc;
+  } else {
+    tq.ms[6] = 0.0;
+  }
+  for (int k = 0; k < count; ++k)
+    CUDA_TRY(cudaMemcpyAsync(&st[k].check_due, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   // algorithmic bytes per launch: every array the kernel needs, each element once
   // (gathered vectors counted once, not once per nonzero)
@@ -1266,7 +1273,7 @@ static Tables tables_at(int* dev, int grid, int K) {
 static int solve_batch(int count, const pdlp_csr* const* A, const double* const* b,
                        const char* const* sense, const double* const* c, const double* const* l,
                        const double* const* u, const pdlp_params* p, double* const* x_out,
-                       double* const* y_out, pdlp_result* res) {
+                       double* const* y_out, pdlp_result* res, const TimingReq* tq = nullptr) {
   g_launches = 0;
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s;
@@ -1618,6 +1625,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   }
   CUDA_TRY(sv.kkt_block());  // initial KKT of every LP
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (tq) return time_kernels_after_setup(sv, g.st, mode, Z, *tq, count);
   const double setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // ---- iteration phase: one graph of a check period for the whole batch
   const auto t1 = std::chrono::steady_clock::now();
@@ -2008,6 +2016,28 @@ int pdlp_solve_batch(int count, const pdlp_csr* const* A, const double* const* b
     if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
   }
   return solve_batch(count, A, b, sense, c, l, u, p, x_out, y_out, r);
+}
+
+int pdlp_time_kernels_batch(int count, const pdlp_csr* const* A, const double* const* b,
+                            const char* const* sense, const double* const* c,
+                            const double* const* l, const double* const* u, const pdlp_params* p,
+                            int reps, double* ms_per_launch, double* bytes_per_launch) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  if (count < 1 || !A || !b || !sense || !c || !l || !u || reps < 1 || !ms_per_launch ||
+      !bytes_per_launch)
+    return fail(PDLP_ERR_INVALID_INPUT, "batch timing: count >= 1, reps >= 1 and every array required");
+  std::vector<pdlp_result> r((size_t)count);
+  for (int k = 0; k < count; ++k) {
+    double dummy = 0.0;
+    const int rc = check_inputs(A[k], b[k], sense[k], c[k], l[k], u[k], p, &dummy, &dummy, &r[k]);
+    if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
+  }
+  TimingReq tq{reps, ms_per_launch, bytes_per_launch};
+  return solve_batch(count, A, b, sense, c, l, u, p, nullptr, nullptr, r.data(), &tq);
 }
 
 const char* pdlp_error_string(int code) {

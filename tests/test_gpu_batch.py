@@ -91,3 +91,20 @@ def test_autotuned_batch(P):
     for lp, x, y, r in zip(lps, xs, ys, res):
         assert r["status"] == P.PDLP_OPTIMAL, lp.name
         assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4, lp.name
+
+
+def test_batch_kernel_timing(P):
+    """pdlp_time_kernels_batch times every fused kernel over the whole batch; the bytes are
+    the single-LP formulas summed over the LPs' sizes, and a solve afterwards is unaffected."""
+    lps = [lpgen.set_cover_fixed(4000 + k, m) for k, m in enumerate((2000, 3000, 4000))]
+    prm = P.default_params(tol=1e-4, precision="bf16")
+    kt = P.time_kernels_batch(lps, prm, reps=5)
+    for k in ("primal_step", "dual_step", "attempt", "kkt_rows", "kkt_cols"):
+        assert kt[k]["ms"] > 0 and kt[k]["bytes"] > 0, k
+    assert kt["persistent_attempt"]["ms"] == 0.0 and kt["kkt_block"]["ms"] == 0.0
+    one = [P.time_kernels(P.DeviceLP(lp), prm, reps=2) for lp in lps]
+    for k in ("primal_step", "dual_step", "kkt_rows", "kkt_cols"):
+        # the same formulas, up to the per-LP row-pointer terminators
+        assert kt[k]["bytes"] == pytest.approx(sum(o[k]["bytes"] for o in one), rel=1e-5), k
+    _, _, res = P.pdlp_solve_batch(lps, prm)
+    assert all(r["status"] == P.PDLP_OPTIMAL for r in res)
