@@ -481,11 +481,12 @@ static GraphKey graph_key(const Solve& sv, int period) {
 
 // ---------------------------------------------------------------- launch-shape autotuner
 // Lanes per row of the two step kernels, chosen by timing: every candidate
-// (2, 4, 8, 16, 32 lanes; the primal kernel's over A^T and the dual kernel's
-// over A independently) runs a CUDA graph of kTuneReps launches on this LP with
-// the state in dry mode (the kernels do all their work, the step decision is
-// skipped, the current iterate is untouched), and the fastest is kept.  Results
-// are cached per (device, mode, m, n, nnz) for the life of the process.
+// (2, 4, 8, 16, 32 lanes; the primal kernel's over A^T, then the dual kernel's
+// over A with the primal choice kept) runs a CUDA graph of kTuneReps whole step
+// attempts on this LP with the state in dry mode (the kernels do all their work,
+// the step decision is skipped, the current iterate is untouched), and the
+// fastest is kept.  Results are cached per (device, mode, m, n, nnz) for the life
+// of the process.
 constexpr int kTuneReps = 16;
 struct TuneKey {
   int dev, mode, count;
@@ -538,7 +539,14 @@ static int autotune_lanes(Solve& sv, int count, bool tune_t, bool tune_a, SetGri
     cudaGraph_t g;
     CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
-    for (int i = 0; i < kTuneReps && ce == cudaSuccess; ++i) ce = cap.iter(which);
+    // whole attempts whichever orientation is tuned: a kernel timed back to back with
+    // itself runs from inputs it left in L2 and, alone, ranked 4 lanes over A ahead of 8 on
+    // the covering LP, the reverse of their order inside attempts (27.0 against 22.2 us)
+    (void)which;
+    for (int i = 0; i < kTuneReps && ce == cudaSuccess; ++i) {
+      ce = cap.iter(IK_PRIMAL);
+      if (ce == cudaSuccess) ce = cap.iter(IK_DUAL);
+    }
     cudaError_t ee = cudaStreamEndCapture(cs, &g);
     if (ce != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("tuning capture: ") + cudaGetErrorString(ce));
     CUDA_TRY(ee);
@@ -558,7 +566,7 @@ static int autotune_lanes(Solve& sv, int count, bool tune_t, bool tune_a, SetGri
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
     *out = ms;
-    g_launches += 2LL * kTuneReps;
+    g_launches += 2LL * 3 * kTuneReps;
     return PDLP_OK;
   };
   static const int cand[5] = {2, 4, 8, 16, 32};
