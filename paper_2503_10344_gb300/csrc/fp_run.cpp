@@ -401,7 +401,7 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     return PDLP_ERR_INVALID_INPUT;
   memset(r, 0, sizeof(*r));
   const auto t0 = std::chrono::steady_clock::now();
-  Problem P{A->m, A->n, A->row_ptr, A->col, A->val, b, sense, c, l, u, {}, {}};
+  Problem P{A->m, A->n, A->row_ptr, A->col, A->val, b, sense, c, l, u, {}, {}, {}};
   // column lists, rows ascending
   P.at_ptr.assign(P.n + 1, 0);
   for (int64_t p = 0; p < A->nnz; ++p) {

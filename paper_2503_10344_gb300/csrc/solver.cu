@@ -1000,7 +1000,6 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     ++launched;
     return e;
   };
-  int host_status = 0;
   if (p->iter_limit > 0) {
     CUDA_TRY(launch());
     while (true) {
@@ -1008,10 +1007,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       CUDA_TRY(cudaEventSynchronize(ev[seen & 1]));
       const DevState& h = hm[seen & 1];
       ++seen;
-      if (h.status != 0) {
-        host_status = h.status;
-        break;
-      }
+      if (h.status != 0) break;
       if (p->verbose)
         fprintf(stderr, "pdlp: chunk %lld iters %lld\n", seen, (long long)h.iters);
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
@@ -1025,7 +1021,6 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       if (launched > max_launches) return fail(PDLP_ERR_TIMEOUT, "iteration loop did not terminate");
     }
   }
-  (void)host_status;
   CUDA_TRY(cudaStreamSynchronize(s));  // drain the chunk launched behind the terminating one
   phase("iterations");
   CUDA_TRY(cudaEventRecord(e2, s));
@@ -1590,7 +1585,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   kr.count = count;
   kr.tr = tA;
   kr.tc = tT;
-  Solve sv{(int)M, (int)N, Z, (Mode)mode, lanes[0], lanes[1], lanes[2], lanes[3], ir, kr, s};
+  Solve sv{(int)M, (int)N, Z, (Mode)mode, lanes[0], lanes[1], lanes[2], lanes[3], ir, kr, s, 0};
   if (p->autotune && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
     // a lanes choice changes the blocks each LP gets: rebuild both launch maps
     auto set_grids = [&](int lt, int la) -> int {
