@@ -350,6 +350,22 @@ def fp_run(lp, x_lp, y_lp, is_int, strategy=TYPE, seed=1, node_limit=None, final
                     backtracks, fixed)
 
 
+def fp_run_refs(lp, x_refs, y_lp, is_int, strategy=TYPE, seed=1, node_limit=None,
+                final_lp=True, final_tol=1e-8):
+    """The heuristic from several LP reference points (the paper's suggestion to use
+    PDLP's cycling for more than one reference, section 5): fp_run from each point in
+    turn, the same strategy, seed and dual point; the feasible result with the lowest
+    objective is kept (ties: the earlier point).  Returns (result, index), index -1 when
+    no run is feasible (the result is then the last run's)."""
+    best, best_i, last = None, -1, None
+    for i, x in enumerate(x_refs):
+        r = fp_run(lp, x, y_lp, is_int, strategy, seed, node_limit, final_lp, final_tol)
+        last = r
+        if r.status == FEASIBLE and (best is None or r.obj < best.obj):
+            best, best_i = r, i
+    return (best, best_i) if best is not None else (last, -1)
+
+
 def max_row_violation(lp, x):
     """Largest row violation of x, each scaled by max(1, |b_i|)."""
     worst = 0.0

@@ -223,6 +223,7 @@ class Params:
     omega_hint: object = None       # (x_h, y_h) caller convention: omega0 from their scaled norms
     detect_infeasibility: bool = True  # A12 (only where terminate is set)
     eps_infeasible: float = 1e-8
+    record_checks: int = 0          # keep the unscaled current point of the last n checks
     # replay: step size and accept flag of every attempt taken from another run's
     # decision trace (eta_bar and all restart decisions are still computed here)
     replay_eta: object = None
@@ -250,6 +251,7 @@ class Result:
     attempt_trace: list = field(default_factory=list)  # (eta, eta_bar, accepted) per attempt
     check_trace: list = field(default_factory=list)    # (restart kind, omega after) per check
     rays: list = field(default_factory=list)           # Rays of every check (A12)
+    check_points: list = field(default_factory=list)   # unscaled current x of the last checks
 
 
 @dataclass
@@ -367,6 +369,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
     attempt_trace = []
     check_trace = []
     rays = []
+    check_points = []
     cert = None
 
     def unscaled_point(xs, ys):
@@ -416,6 +419,11 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
             chosen_avg = ka.rel_kkt < kc.rel_kkt
             chosen_kkt = ka if chosen_avg else kc
             trace.append(("check", it, kc.rel_kkt, ka.rel_kkt, eta, omega))
+            if p.record_checks > 0:
+                # the current point as the check sees it (A11's clipped unscaled point),
+                # reference points for the heuristic from PDLP's cycling (section 5)
+                check_points.append(proj_box(dc * x, lp.l, lp.u))
+                del check_points[:-p.record_checks]
             if p.terminate and chosen_kkt.rel_kkt <= p.tol:
                 status = STATUS_OPTIMAL
                 check_trace.append((0, omega))
@@ -500,7 +508,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                   x_out, y_out, chosen_kkt,
                   unscale_x(x), unscale_y(y), unscale_x(xa), unscale_y(ya),
                   eta, omega, chosen_avg, time.perf_counter() - t0, trace, attempt_trace,
-                  check_trace, rays)
+                  check_trace, rays, check_points)
 
 
 # ---------------------------------------------------------------- A13 ------

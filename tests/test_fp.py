@@ -243,3 +243,30 @@ def test_exhausted_search_is_infeasible(P):
     assert st == F.INFEASIBLE and nodes == 1 and bt == 1
     x, res = P.fp_run(lp, [0.5, 0.5], None, strategy="frac", seed=3, final_lp=False)
     assert res["status"] == P.FP_INFEASIBLE and res["nodes"] == 1 and res["backtracks"] == 1
+
+
+# ------------------------------------------------------- several reference points
+def test_recorded_check_points_are_the_iterates_of_shorter_runs():
+    """The oracle keeps the current point of the last checks; each is the current point of
+    a run stopped at that check (the same steps, no termination test)."""
+    lp = lpgen.mip_relaxation(2)
+    r = O.solve(lp, O.Params(tol=1e-4, record_checks=3))
+    k_last = r.iters // 64
+    assert len(r.check_points) == 3
+    for back, x in enumerate(reversed(r.check_points)):
+        k = k_last - back
+        ref = O.solve(lp, O.Params(iter_limit=64 * k, terminate=False))
+        np.testing.assert_array_equal(x, ref.x_cur)
+
+
+def test_fp_run_refs_keeps_the_best_feasible_run():
+    lp = lpgen.mip_relaxation(5)
+    r = O.solve(lp, O.Params(tol=1e-4, record_checks=4))
+    runs = [F.fp_run(lp, x, r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6) for x in r.check_points]
+    best, i = F.fp_run_refs(lp, r.check_points, r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
+    objs = [q.obj if q.status == F.FEASIBLE else np.inf for q in runs]
+    assert i == int(np.argmin(objs)) and best.obj == min(objs)
+    # one reference is fp_run itself
+    one, j = F.fp_run_refs(lp, [r.x], r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
+    direct = F.fp_run(lp, r.x, r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
+    assert j == (0 if direct.status == F.FEASIBLE else -1) and one.obj == direct.obj
