@@ -181,7 +181,13 @@ typedef struct {
  *    eta_bar it computed (+INFINITY when dy^T K dx = 0) and whether it was
  *    accepted (1) or retried with a smaller step (0);
  *  - per KKT check: the restart taken (0 none, 1 to the current iterate, 2 to
- *    the average) and the primal weight after the check.
+ *    the average) and the primal weight after the check;
+ *  - the current point of the last checks (unscaled, clipped to [l, u], as the
+ *    check measures it): check k = 0, 1, ... writes row k mod point_capacity of
+ *    check_points [point_capacity x n]; with pdlp_result.kkt_checks = K the last
+ *    min(K, point_capacity) rows hold checks K - min(K, capacity) .. K - 1.  The
+ *    paper suggests PDLP's cycling as a source of several reference points for
+ *    fix-and-propagate (section 5; fp_run_refs).  Single LPs only.
  * The trace lets a second implementation replay the step-size sequence and
  * check every decision (the rule is sensitive enough that two correct
  * float64 implementations part after a few hundred adaptive steps). */
@@ -197,6 +203,8 @@ typedef struct {
   int64_t check_capacity;    /* length of restart, omega */
   int8_t* restart;
   double* omega;
+  int64_t point_capacity;    /* rows of check_points */
+  double* check_points;      /* [point_capacity x n] */
 } pdlp_diagnostics;
 
 /* Fill *p with the defaults listed above.  Returns PDLP_OK or INVALID_INPUT (p NULL). */
@@ -409,6 +417,18 @@ int fp_default_params(fp_params* p);
 int fp_run(const pdlp_csr* A, const double* b, const char* sense, const double* c,
            const double* l, const double* u, const double* x_lp, const double* y_lp,
            const uint8_t* is_int, const fp_params* p, double* x_out, fp_result* r);
+
+/* The heuristic from several LP reference points (the paper suggests PDLP's cycling
+ * as a source of more than one reference solution, section 5; for instance the check
+ * points of pdlp_diagnostics): fp_run from each x_refs[k], k < nrefs, with the same
+ * y_lp, strategy and seed; the feasible result with the lowest objective is kept
+ * (ties: the earlier point).  x_out and *r are that run's and *chosen its index; when
+ * no run is feasible they are the last run's and *chosen is -1.  Returns PDLP_OK or an
+ * error code. */
+int fp_run_refs(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                const double* l, const double* u, const double* const* x_refs, int nrefs,
+                const double* y_lp, const uint8_t* is_int, const fp_params* p, double* x_out,
+                fp_result* r, int* chosen);
 
 /* Name of a return code, and the last error message of the calling thread. */
 const char* pdlp_error_string(int code);

@@ -4,7 +4,7 @@ The compute path is the CUDA library ``libpdlp.so`` (sources in ``csrc/``,
 C ABI in ``include/pdlp.h``); :mod:`.binding` marshals arguments to it.
 """
 from .binding import (FP_DUAL, FP_FEASIBLE, FP_FRAC, FP_INFEASIBLE, FP_NODE_LIMIT,
-                      FP_NO_FINAL_LP, FP_REDCOST, FP_TYPE, fp_run,
+                      FP_NO_FINAL_LP, FP_REDCOST, FP_TYPE, fp_run, fp_run_refs,
                       PDLP_FP32, PDLP_FP32_BF16A, PDLP_FP64, PDLP_ITER_LIMIT, PDLP_NUMERICAL,
                       PDLP_OPTIMAL, PDLP_TIME_LIMIT, PDLP_PRIMAL_INFEASIBLE, PDLP_DUAL_INFEASIBLE,
                       DeviceLP, PdlpError, default_params, lib,
@@ -14,7 +14,7 @@ from .binding import (FP_DUAL, FP_FEASIBLE, FP_FRAC, FP_INFEASIBLE, FP_NODE_LIMI
 from .gnn import GnnGraph, GnnModel, pdlp_solve_warm, start_kkt
 
 __all__ = ["FP_DUAL", "FP_FEASIBLE", "FP_FRAC", "FP_INFEASIBLE", "FP_NODE_LIMIT",
-           "FP_NO_FINAL_LP", "FP_REDCOST", "FP_TYPE", "fp_run", "PDLP_FP32", "PDLP_FP32_BF16A", "PDLP_FP64", "PDLP_ITER_LIMIT", "PDLP_NUMERICAL",
+           "FP_NO_FINAL_LP", "FP_REDCOST", "FP_TYPE", "fp_run", "fp_run_refs", "PDLP_FP32", "PDLP_FP32_BF16A", "PDLP_FP64", "PDLP_ITER_LIMIT", "PDLP_NUMERICAL",
            "PDLP_OPTIMAL", "PDLP_TIME_LIMIT", "PDLP_PRIMAL_INFEASIBLE", "PDLP_DUAL_INFEASIBLE",
            "DeviceLP", "PdlpError", "default_params", "lib",
            "pdlp_polish_primal", "pdlp_solve", "pdlp_solve_batch", "pdlp_solve_device",

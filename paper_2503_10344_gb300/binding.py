@@ -62,7 +62,8 @@ class PdlpDiagnostics(C.Structure):
     _fields_ = [("x_cur", C.c_void_p), ("y_cur", C.c_void_p), ("x_avg", C.c_void_p),
                 ("y_avg", C.c_void_p), ("attempt_capacity", C.c_int64), ("eta", C.c_void_p),
                 ("eta_bar", C.c_void_p), ("accepted", C.c_void_p), ("check_capacity", C.c_int64),
-                ("restart", C.c_void_p), ("omega", C.c_void_p)]
+                ("restart", C.c_void_p), ("omega", C.c_void_p), ("point_capacity", C.c_int64),
+                ("check_points", C.c_void_p)]
 
 
 _LIB = None
@@ -128,14 +129,15 @@ DIAG_ITERATES = ("x_cur", "y_cur", "x_avg", "y_avg")
 
 
 def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates: bool = False,
-               trace: int = 0, omega_hint=None):
+               trace: int = 0, omega_hint=None, check_points: int = 0):
     """Solve ``lp`` (an :class:`lpgen.LP`-like object) from host memory.
 
     Returns (x, y, result dict) or, with ``iterates`` or ``trace`` > 0,
     (x, y, result dict, diagnostics dict); ``trace`` is the capacity of the
     per-attempt decision trace (the per-check trace gets trace // 16 + 16).
     ``omega_hint`` = (x_h, y_h) calls pdlp_solve_hinted: the initial primal weight
-    is the ratio of the hint's scaled norms.
+    is the ratio of the hint's scaled norms.  ``check_points`` = R keeps the current
+    point of the last R KKT checks: diagnostics["check_points"], oldest first.
     """
     p = params or default_params()
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
@@ -152,15 +154,17 @@ def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates:
     res = PdlpResult()
     diag = None
     dgp = None
-    if iterates or trace > 0:
+    if iterates or trace > 0 or check_points > 0:
         diag = {k: np.empty(lp.n if k[0] == "x" else lp.m) for k in DIAG_ITERATES}
+        diag["check_points"] = np.zeros((check_points, lp.n))
         tc = trace // 16 + 16 if trace > 0 else 0
         diag.update(eta=np.full(trace, np.nan), eta_bar=np.full(trace, np.nan),
                     accepted=np.full(trace, -1, dtype=np.int8), restart=np.full(tc, -1, dtype=np.int8),
                     omega=np.full(tc, np.nan))
         dgp = PdlpDiagnostics(*[_ptr(diag[k]) for k in DIAG_ITERATES], trace, _ptr(diag["eta"]),
                               _ptr(diag["eta_bar"]), _ptr(diag["accepted"]), tc,
-                              _ptr(diag["restart"]), _ptr(diag["omega"]))
+                              _ptr(diag["restart"]), _ptr(diag["omega"]), check_points,
+                              _ptr(diag["check_points"]) if check_points > 0 else None)
     if omega_hint is None:
         rc = lib().pdlp_solve(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u),
                               C.byref(p), _ptr(x0a), _ptr(y0a), _ptr(x), _ptr(y), C.byref(res),
@@ -174,6 +178,10 @@ def pdlp_solve(lp, params: PdlpParams | None = None, x0=None, y0=None, iterates:
     out = res.as_dict()
     if diag is None:
         return x, y, out
+    if check_points > 0:  # ring buffer -> the last checks, oldest first
+        kc = out["kkt_checks"]
+        rows = [(k % check_points) for k in range(max(0, kc - check_points), kc)]
+        diag["check_points"] = diag["check_points"][rows]
     if trace > 0:
         na = min(trace, out["attempts"])
         nc = min(tc, out["kkt_checks"])
@@ -376,6 +384,43 @@ def fp_run(lp, x_lp, y_lp=None, is_int=None, strategy="type", seed: int = 1, nod
                   _ptr(ii), C.byref(p), _ptr(x), C.byref(r))
     _check(rc)
     return x, r.as_dict()
+
+
+def fp_run_refs(lp, x_refs, y_lp=None, is_int=None, strategy="type", seed: int = 1,
+                node_limit: int = 0, final_lp: bool = True, final_lp_tol: float = 1e-8):
+    """fp_run from each of several LP points (host buffers); returns (x, result dict, chosen
+    index, -1 when no run is feasible)."""
+    L = lib()
+    if not getattr(L, "_fp_refs_ready", False):
+        L.fp_run_refs.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 6 + [C.c_int] + \
+            [C.c_void_p] * 2 + [C.POINTER(FpParams), C.c_void_p, C.POINTER(FpResult),
+                                C.POINTER(C.c_int)]
+        L.fp_default_params.argtypes = [C.POINTER(FpParams)]
+        L._fp_refs_ready = True
+    p = FpParams()
+    L.fp_default_params(C.byref(p))
+    p.var_strategy = FP_STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    p.seed = seed
+    p.node_limit = node_limit
+    p.final_lp = 1 if final_lp else 0
+    p.final_lp_tol = final_lp_tol
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    row_ptr = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(lp.col, dtype=np.int32)
+    val, b, c, l, u = f64(lp.val), f64(lp.b), f64(lp.c), f64(lp.l), f64(lp.u)
+    sense = np.ascontiguousarray(lp.sense, dtype=np.uint8)
+    ii = np.ascontiguousarray(lp.is_int if is_int is None else is_int, dtype=np.uint8)
+    refs = [f64(x) for x in x_refs]
+    rp = (C.c_void_p * len(refs))(*[_ptr(x) for x in refs])
+    yl = None if y_lp is None else f64(y_lp)
+    csr = PdlpCsr(lp.m, lp.n, int(row_ptr[-1]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    x = np.empty(lp.n)
+    r = FpResult()
+    chosen = C.c_int(-1)
+    _check(L.fp_run_refs(C.byref(csr), _ptr(b), _ptr(sense), _ptr(c), _ptr(l), _ptr(u), rp,
+                         len(refs), _ptr(yl), _ptr(ii), C.byref(p), _ptr(x), C.byref(r),
+                         C.byref(chosen)))
+    return x, r.as_dict(), chosen.value
 
 
 def _batch_arrays(lps, xs=None, ys=None):

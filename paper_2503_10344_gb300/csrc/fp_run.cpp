@@ -564,3 +564,31 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
   r->obj = obj;
   return PDLP_OK;
 }
+
+extern "C" int fp_run_refs(const pdlp_csr* A, const double* b, const char* sense, const double* c,
+                           const double* l, const double* u, const double* const* x_refs,
+                           int nrefs, const double* y_lp, const uint8_t* is_int,
+                           const fp_params* prm, double* x_out, fp_result* r, int* chosen) {
+  if (!A || !x_refs || nrefs < 1 || !x_out || !r || !chosen || A->n < 1)
+    return PDLP_ERR_INVALID_INPUT;
+  for (int k = 0; k < nrefs; ++k)
+    if (!x_refs[k]) return PDLP_ERR_INVALID_INPUT;
+  std::vector<double> x((size_t)A->n);
+  fp_result cur;
+  bool have = false;
+  *chosen = -1;
+  for (int k = 0; k < nrefs; ++k) {
+    const int rc = fp_run(A, b, sense, c, l, u, x_refs[k], y_lp, is_int, prm, x.data(), &cur);
+    if (rc != PDLP_OK) return rc;
+    const bool better = cur.status == FP_FEASIBLE && (!have || cur.obj < r->obj);
+    if (better || (!have && k == nrefs - 1)) {
+      *r = cur;
+      std::copy(x.begin(), x.end(), x_out);
+    }
+    if (better) {
+      have = true;
+      *chosen = k;
+    }
+  }
+  return PDLP_OK;
+}

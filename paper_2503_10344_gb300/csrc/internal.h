@@ -74,6 +74,8 @@ struct KktRaw {
   Cand *XG, *YG;    // candidates per column / row; the ray slot holds x - x_last, y - y_last
                     // projected onto the recession cone of [l, u] and onto Y
   double *Xl, *Yl;  // unscaled restart anchors
+  double* chk_pts;  // [chk_cap x n] current point of the last checks (NULL: not kept)
+  long long chk_cap;
   double *part_r, *part_c;                 // kPartR / kPartC partial rows of grid_r / grid_c
   int rays;  // ray terms in the KKT passes: 0 none, 1 the dual ray only (every column
              // boxed, so the primal ray is 0), 2 both

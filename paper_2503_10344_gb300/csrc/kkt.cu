@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
     double2* g = reinterpret_cast<double2*>(r.XG + j);
     g[0] = make_double2(Xc, fmin(fmax(s * xa, r.l[j]), r.u[j]));
     g[1] = make_double2(d, 0.0);
+    if (r.chk_pts && !st->init_pending)  // row (completed checks) mod capacity
+      r.chk_pts[(size_t)(st->checks % r.chk_cap) * (size_t)r.n + (size_t)j] = Xc;
   }
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double yc = (double)y[i];

@@ -720,6 +720,10 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   for (int k = 0; k < 2; ++k) { kr.x[k] = bf.x[k]; kr.y[k] = bf.y[k]; }
   kr.sum_x = bf.sum_x; kr.sum_y = bf.sum_y;
   kr.XG = bf.XG; kr.Xl = bf.Xl; kr.YG = bf.YG; kr.Yl = bf.Yl;
+  if (dg && dg->point_capacity > 0 && dg->check_points) {
+    kr.chk_pts = dg->check_points;
+    kr.chk_cap = dg->point_capacity;
+  }
   // every column boxed: the primal ray is 0, only the dual ray is accumulated
   kr.rays = p->detect_infeasibility && p->terminate ? (sca[7] > 0.0 ? 2 : 1) : 0;
   kr.part_r = bf.part_r; kr.part_c = bf.part_c;
@@ -1827,6 +1831,8 @@ static int solve_host(const pdlp_csr* A, const double* b, const char* sense, con
   const size_t M = (size_t)A->m, N = (size_t)A->n, Z = (size_t)A->nnz;
   const size_t TA = diag && diag->attempt_capacity > 0 ? (size_t)diag->attempt_capacity : 0;
   const size_t TC = diag && diag->check_capacity > 0 ? (size_t)diag->check_capacity : 0;
+  const size_t TP = diag && diag->point_capacity > 0 && diag->check_points
+                        ? (size_t)diag->point_capacity : 0;
   cudaStream_t s;
   CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   struct StreamFree {
@@ -1855,8 +1861,9 @@ static int solve_host(const pdlp_csr* A, const double* b, const char* sense, con
     ptrs[20] = ar.take(8 * TC);      // omega
     ptrs[21] = ar.take(8 * N);       // primal-weight hint x
     ptrs[22] = ar.take(8 * M);       // primal-weight hint y
+    ptrs[23] = ar.take(8 * TP * N);  // check points
   };
-  void* dp[23];
+  void* dp[24];
   Arena dry{nullptr, 0};
   lay(dry, dp);
   const size_t io_bytes = dry.off + 256;
@@ -1898,7 +1905,8 @@ static int solve_host(const pdlp_csr* A, const double* b, const char* sense, con
   pdlp_csr dA{A->m, A->n, A->nnz, (const int64_t*)dp[0], (const int32_t*)dp[1], (const double*)dp[2]};
   pdlp_diagnostics ddg{(double*)dp[12], (double*)dp[13], (double*)dp[14], (double*)dp[15],
                        (int64_t)TA, (double*)dp[16], (double*)dp[17], (int8_t*)dp[18],
-                       (int64_t)TC, (int8_t*)dp[19], (double*)dp[20]};
+                       (int64_t)TC, (int8_t*)dp[19], (double*)dp[20], (int64_t)TP,
+                       TP ? (double*)dp[23] : nullptr};
   rc = solve_device(&dA, (const double*)dp[3], (const char*)dp[4], (const double*)dp[5],
                     (const double*)dp[6], (const double*)dp[7], p, x0 ? (const double*)dp[8] : nullptr,
                     y0 ? (const double*)dp[9] : nullptr, (double*)dp[10], (double*)dp[11], r,
@@ -1921,6 +1929,7 @@ static int solve_host(const pdlp_csr* A, const double* b, const char* sense, con
       CUDA_TRY(d2h(diag->restart, dp[19], TC));
       CUDA_TRY(d2h(diag->omega, dp[20], 8 * TC));
     }
+    if (TP) CUDA_TRY(d2h(diag->check_points, dp[23], 8 * TP * N));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   return PDLP_OK;

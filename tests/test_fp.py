@@ -270,3 +270,15 @@ def test_fp_run_refs_keeps_the_best_feasible_run():
     one, j = F.fp_run_refs(lp, [r.x], r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
     direct = F.fp_run(lp, r.x, r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
     assert j == (0 if direct.status == F.FEASIBLE else -1) and one.obj == direct.obj
+
+
+def test_cabi_refs_without_final_lp_returns_the_last_run(P):
+    """Without the final LP no run is declared feasible: fp_run_refs reports index -1 and
+    the last reference's search (the same as fp_run from it)."""
+    lp = lpgen.mip_relaxation(3)
+    r = O.solve(lp, O.Params(tol=1e-4, record_checks=2))
+    x, res, k = P.fp_run_refs(lp, r.check_points, r.y, strategy="dual", final_lp=False)
+    x1, res1 = P.fp_run(lp, r.check_points[-1], r.y, strategy="dual", final_lp=False)
+    assert k == -1 and res["status"] == res1["status"] and res["nodes"] == res1["nodes"]
+    ints = lp.is_int == 1
+    np.testing.assert_array_equal(x[ints], x1[ints])

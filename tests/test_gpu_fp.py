@@ -57,3 +57,35 @@ def test_final_lp_matches_oracle(P, strategy):
     ints = lp.is_int == 1
     np.testing.assert_array_equal(x[ints], ref.x[ints])
     assert abs(fr["obj"] - ref.obj) <= 1e-6 * (1 + abs(ref.obj))
+
+
+def test_check_points_match_oracle(P):
+    """The current point of the last KKT checks (float64 path) equals the oracle's; a fixed
+    step keeps the two runs on the same rounding over the 192 steps (with the adaptive step
+    they part by ~1e-8 after ~150 steps, the method's own sensitivity)."""
+    lp = lpgen.mip_relaxation(2)
+    _, _, r, dg = P.pdlp_solve(lp, P.default_params(iter_limit=192, terminate=0, adaptive_step=0,
+                                                    fixed_eta=0.9), check_points=2)
+    ref = O.solve(lp, O.Params(iter_limit=192, terminate=False, adaptive=False, fixed_eta=0.9,
+                               record_checks=2))
+    assert r["kkt_checks"] == 3 and dg["check_points"].shape == (2, lp.n)
+    for got, want in zip(dg["check_points"], ref.check_points):
+        assert np.linalg.norm(got - want) <= 1e-9 * max(1.0, np.linalg.norm(want))
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_fp_from_several_reference_points_matches_oracle(P, seed):
+    """fp_run_refs keeps the best feasible run over the references (the search is exact,
+    the final LPs agree to their tolerance): the oracle's choice and objective."""
+    lp = lpgen.mip_relaxation(seed)
+    ref = O.solve(lp, O.Params(tol=1e-4, record_checks=4))
+    x, res, k = P.fp_run_refs(lp, ref.check_points, ref.y, strategy="frac", final_lp_tol=1e-6)
+    best, i = F.fp_run_refs(lp, ref.check_points, ref.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
+    assert (k >= 0) == (i >= 0)
+    if i >= 0:
+        assert res["status"] == P.FP_FEASIBLE
+        assert res["obj"] == pytest.approx(best.obj, rel=1e-6, abs=1e-6)
+        objs = [F.fp_run(lp, x0, ref.y, lp.is_int, F.FRAC, 1, final_tol=1e-6).obj
+                for x0 in ref.check_points]
+        assert objs[k] == pytest.approx(min(objs), rel=1e-6, abs=1e-6)
+        assert F.max_row_violation(lp, x) <= 1e-6
