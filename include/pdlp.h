@@ -269,6 +269,25 @@ int pdlp_polish_primal(const pdlp_csr* A, const double* b, const char* sense, co
                        const double* u, const pdlp_params* p, const double* x_in,
                        double* x_out, double* y_out, pdlp_result* r);
 
+/* Dual feasibility polishing of a dual point y_in[m] (the dual side of the
+ * feasibility polishing above; y in the sign convention of pdlp_solve): the
+ * PDHG of pdlp_solve on the dual feasibility problem -- the same rows, senses
+ * and objective with b replaced by 0 and every finite bound by 0 (infinite
+ * bounds stay) -- started from (x = 0, y_in).  That problem's dual has the
+ * feasible set of the LP's dual and objective 0, so a dual-feasible y_in (every
+ * part of lambda = c - A^T y that no finite bound carries is 0) is a fixed
+ * point; otherwise y moves onto the dual feasible set by a distance of the
+ * order of its violation.  p->tol bounds the relative KKT of that problem, so
+ * the dual residual ||r_d||_2 <= tol (1 + ||c||_2).  y_out[m] (required when
+ * m > 0) receives the polished dual point, x_out[n] (may be NULL) the
+ * multipliers of the violated reduced costs; an LP whose dual is infeasible
+ * ends with status PDLP_DUAL_INFEASIBLE and x_out holds its ray of descent.
+ * b is not read.  Inputs, ownership and return codes as pdlp_solve (l > u in
+ * any column is PDLP_ERR_INVALID_INPUT). */
+int pdlp_polish_dual(const pdlp_csr* A, const char* sense, const double* c, const double* l,
+                     const double* u, const pdlp_params* p, const double* y_in, double* x_out,
+                     double* y_out, pdlp_result* r);
+
 /* Solve `count` LPs of uneven size together (north-star pattern "batched":
  * relaxations such as those left after the partial fixings of the heuristic).
  * Arrays of per-LP HOST pointers in the layout of pdlp_solve; one parameter

@@ -59,7 +59,9 @@ are listed one by one in the design notes and marked "reading" here:
       in place of the dual (primal infeasible) or primal (dual infeasible)
       output.
   A13 primal feasibility polishing (``polish_primal``): the same iteration on
-      the LP with its objective replaced by 0, from (x, 0).
+      the LP with its objective replaced by 0, from (x, 0).  Dual feasibility
+      polishing (``polish_dual``): the same iteration on the LP with b = 0 and
+      every finite bound moved to 0, from (0, y).
 
 Part I (the definition every result is judged by): for a point x in [l,u] and
 y in Y of the canonical problem,
@@ -528,3 +530,26 @@ def polish_primal(lp, x, params: Params | None = None) -> Result:
     lp0 = copy.copy(lp)
     lp0.c = np.zeros(lp.n)
     return solve(lp0, params, x0=x, y0=None)
+
+
+def polish_dual(lp, y, params: Params | None = None) -> Result:
+    """A13, dual side: dual feasibility polishing of a dual point y (reading of
+    PDLP's feasibility polishing, as for ``polish_primal``; y in the caller's
+    sign convention of ``kkt_original``).
+
+    The same PDHG (A0-A12) on the dual feasibility problem -- the LP with its
+    right-hand side replaced by 0 and every finite bound by 0 (infinite bounds
+    stay infinite) -- started from (x = 0, y).  The dual of that problem has the
+    original dual's feasible set (y in Y, lambda = c - K^T y carried by the
+    bounds that are finite) and a zero objective, so a dual-feasible y leaves
+    x = 0 and is a fixed point; otherwise y moves onto the dual feasible set
+    with x as the multipliers of the violated reduced costs.  The result's y is
+    the polished dual point (status OPTIMAL: ||r_d|| <= tol (1 + ||c||)); an
+    LP whose dual is infeasible ends DUAL_INFEASIBLE with a ray of descent.
+    """
+    import copy
+    lp0 = copy.copy(lp)
+    lp0.b = np.zeros(lp.m)
+    lp0.l = np.where(np.isfinite(lp.l), 0.0, lp.l)
+    lp0.u = np.where(np.isfinite(lp.u), 0.0, lp.u)
+    return solve(lp0, params, x0=None, y0=y)

@@ -96,6 +96,8 @@ def lib():
              C.c_void_p]
         L.pdlp_polish_primal.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 4 + \
             [C.POINTER(PdlpParams)] + [C.c_void_p] * 3 + [C.POINTER(PdlpResult)]
+        L.pdlp_polish_dual.argtypes = [C.POINTER(PdlpCsr)] + [C.c_void_p] * 4 + \
+            [C.POINTER(PdlpParams)] + [C.c_void_p] * 3 + [C.POINTER(PdlpResult)]
         L.pdlp_error_string.argtypes = [C.c_int]
         L.pdlp_error_string.restype = C.c_char_p
         L.pdlp_last_error.restype = C.c_char_p
@@ -209,6 +211,29 @@ def pdlp_polish_primal(lp, x, params: PdlpParams | None = None):
     res = PdlpResult()
     _check(L.pdlp_polish_primal(C.byref(csr), _ptr(b), _ptr(sense), _ptr(l), _ptr(u), C.byref(p),
                                 _ptr(xi), _ptr(xo), _ptr(yo) if lp.m else None, C.byref(res)))
+    return xo, yo, res.as_dict()
+
+
+def pdlp_polish_dual(lp, y, params: PdlpParams | None = None):
+    """Dual feasibility polishing of ``y`` (host buffers): the PDHG on the LP with
+    b = 0 and finite bounds at 0, from (0, y).  Returns (x, y_polished, result
+    dict); x is the multiplier of the violated reduced costs, or the ray of descent
+    when the status is PDLP_DUAL_INFEASIBLE."""
+    L = lib()
+    p = params or default_params()
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    row_ptr = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(lp.col, dtype=np.int32)
+    val = f64(lp.val)
+    c, l, u, yi = f64(lp.c), f64(lp.l), f64(lp.u), f64(y)
+    sense = np.ascontiguousarray(lp.sense, dtype=np.uint8)
+    csr = PdlpCsr(lp.m, lp.n, int(row_ptr[-1]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    xo = np.empty(lp.n)
+    yo = np.empty(lp.m)
+    res = PdlpResult()
+    _check(L.pdlp_polish_dual(C.byref(csr), _ptr(sense), _ptr(c), _ptr(l), _ptr(u), C.byref(p),
+                              _ptr(yi) if lp.m else None, _ptr(xo), _ptr(yo) if lp.m else None,
+                              C.byref(res)))
     return xo, yo, res.as_dict()
 
 

@@ -1989,6 +1989,28 @@ int pdlp_polish_primal(const pdlp_csr* A, const double* b, const char* sense, co
                     y_out, r, nullptr);
 }
 
+int pdlp_polish_dual(const pdlp_csr* A, const char* sense, const double* c, const double* l,
+                     const double* u, const pdlp_params* p, const double* y_in, double* x_out,
+                     double* y_out, pdlp_result* r) {
+  if (!A || A->n < 1 || A->m < 0 || (A->m > 0 && (!y_in || !y_out)) || !c || !l || !u)
+    return fail(PDLP_ERR_INVALID_INPUT, "pdlp_polish_dual needs A, c, l, u, y_in[m] and y_out[m]");
+  // the dual feasibility problem from (0, y_in): b = 0, finite bounds moved to 0
+  const size_t N = (size_t)A->n;
+  const std::vector<double> zero_b((size_t)A->m, 0.0);
+  std::vector<double> l0(N), u0(N), x_tmp;
+  for (size_t j = 0; j < N; ++j) {
+    if (l[j] > u[j]) return fail(PDLP_ERR_INVALID_INPUT, "l > u in column " + std::to_string(j));
+    l0[j] = std::isfinite(l[j]) ? 0.0 : l[j];  // NaN stays NaN: the setup rejects it
+    u0[j] = std::isfinite(u[j]) ? 0.0 : u[j];
+  }
+  if (!x_out) {
+    x_tmp.resize(N);
+    x_out = x_tmp.data();
+  }
+  return solve_host(A, zero_b.data(), sense, c, l0.data(), u0.data(), p, nullptr, y_in, nullptr,
+                    nullptr, x_out, y_out, r, nullptr);
+}
+
 int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, const double* c,
                       const double* l, const double* u, const pdlp_params* p, int reps,
                       double* ms_per_launch, double* bytes_per_launch, void* workspace,

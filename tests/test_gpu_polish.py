@@ -1,19 +1,22 @@
-"""GPU primal feasibility polishing (A13) through the C ABI against the oracle.
+"""GPU primal and dual feasibility polishing (A13) through the C ABI against the oracle.
 
-* float64: the polished point after K objective-free PDHG steps from the same
-  loose point agrees with the oracle to 1e-9 relative;
+* float64: the polished point after K PDHG steps of the objective-free problem
+  (or of the dual feasibility problem) from the same loose point agrees with
+  the oracle to 1e-9 relative;
 * every precision mode makes a 1e-4 point row-feasible (checked row by row on
-  the original data) and keeps it in its bounds; a strictly feasible point
-  comes back unchanged;
-* an infeasible LP ends with a Farkas ray.
+  the original data) and keeps it in its bounds, and a 1e-4 dual point dual
+  feasible (checked reduced cost by reduced cost); strictly feasible and
+  dual-feasible points come back unchanged;
+* an infeasible LP ends with a Farkas ray, an unbounded one (dual side) with
+  a ray of descent.
 """
 import numpy as np
 import pytest
 
 import lpgen
 from oracle import pdlp_oracle as O
-from test_oracle_infeasibility import INFEASIBLE, farkas_ray_margin
-from test_oracle_polish import row_violation
+from test_oracle_infeasibility import INFEASIBLE, UNBOUNDED, descent_ray_margin, farkas_ray_margin
+from test_oracle_polish import DUAL_CASES, dual_violation, row_violation
 
 pytestmark = pytest.mark.gpu
 
@@ -82,3 +85,55 @@ def test_polishing_an_infeasible_lp(P):
     assert r["status"] == P.PDLP_PRIMAL_INFEASIBLE
     margin, res = farkas_ray_margin(lp, yg)
     assert margin > 0 and res <= 1e-8 * margin
+
+
+def loose_dual(name):
+    """The LP and the oracle's dual point at relative KKT 1e-4 (it leaves reduced
+    costs that no finite bound carries)."""
+    key = ("dual", name)
+    if key not in _cache:
+        lp = DUAL_CASES[name]()
+        _cache[key] = (lp, O.solve(lp, O.Params(tol=1e-4)).y)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("name", list(DUAL_CASES))
+@pytest.mark.parametrize("K", [1, 10, 100])
+def test_fp64_dual_polishing_matches_oracle(P, name, K):
+    lp, y = loose_dual(name)
+    xg, yg, r = P.pdlp_polish_dual(lp, y, P.default_params(iter_limit=K, terminate=0))
+    ref = O.polish_dual(lp, y, O.Params(iter_limit=K, terminate=False))
+    assert r["iters"] == ref.iters == K
+    for got, want in ((xg, ref.x), (yg, ref.y)):
+        assert np.linalg.norm(got - want) <= 1e-9 * max(1.0, np.linalg.norm(want))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("name", list(DUAL_CASES))
+def test_dual_polishing_makes_the_dual_point_feasible(P, name, prec):
+    lp, y = loose_dual(name)
+    before = dual_violation(lp, y)
+    assert before > 1e-8
+    tol = 1e-8 if prec == "fp64" else 1e-6
+    _, yg, r = P.pdlp_polish_dual(lp, y, P.default_params(tol=tol, precision=prec))
+    assert r["status"] == P.PDLP_OPTIMAL
+    assert dual_violation(lp, yg) <= (1e-8 * before + 1e-14 if prec == "fp64" else 10 * tol)
+    assert np.linalg.norm(yg - y) <= 100.0 * max(1.0, np.linalg.norm(y)) * max(before, tol)
+
+
+def test_dual_feasible_point_comes_back(P):
+    # every column of a covering LP has finite bounds: every y >= 0 is dual feasible
+    lp = lpgen.set_cover(7, m=2000, n=8000)
+    y = np.random.default_rng(3).uniform(0.0, 5.0, lp.m)
+    xg, yg, r = P.pdlp_polish_dual(lp, y, P.default_params(tol=1e-8))
+    assert r["status"] == P.PDLP_OPTIMAL and r["iters"] == 64
+    np.testing.assert_allclose(yg, y, rtol=1e-15, atol=0)
+    assert np.all(xg == 0.0)
+
+
+def test_dual_polishing_an_unbounded_lp(P):
+    lp = UNBOUNDED["relaxation1"]()
+    xg, _, r = P.pdlp_polish_dual(lp, np.zeros(lp.m), P.default_params(tol=1e-8, iter_limit=20000))
+    assert r["status"] == P.PDLP_DUAL_INFEASIBLE
+    descent, res = descent_ray_margin(lp, xg)
+    assert descent > 0 and res <= 1e-8 * descent
