@@ -71,6 +71,22 @@ def dist_env():
     return ws, rank, local
 
 
+def combine_ranks(total_s: float, iters: int, ws: int, device="cpu"):
+    """Whole-job figures of a replicas-only run: the timed region's MAX over the
+    ranks and the accepted iterations SUMMED over them (one all-reduce each; the
+    process group is the caller's).  With one rank, the rank's own figures."""
+    if ws == 1:
+        return total_s, float(iters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_s, float(iters)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -233,16 +249,7 @@ def run_gpu(args):
     clocks = clk.summary()
     total_s = sum(ms) / 1e3
     # max over ranks of the timed region, units summed over ranks
-    t_local = torch.tensor([total_s, float(iters)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        tmax = t_local.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t_local.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_s, all_iters = float(tmax[0]), float(tsum[1])
-    else:
-        all_iters = float(iters)
+    total_s, all_iters = combine_ranks(total_s, iters, ws, dev)
     value = all_iters / total_s
 
     # plain float64 PDLP on the same instance (the comparison line)
@@ -257,6 +264,7 @@ def run_gpu(args):
         if k > 0:  # first call warms the host path
             e2e_t += dt
             e2e_it += r["iters"]
+    e2e_t, e2e_it = combine_ranks(e2e_t, e2e_it, ws, dev)
     h2d = 8 * (lp.m + 1) + 12 * lp.nnz + 9 * lp.m + 24 * lp.n
     d2h = 8 * (lp.n + lp.m)
     # roofline of the dominant kernel, timed live with CUDA events on this stream

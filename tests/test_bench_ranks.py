@@ -1,0 +1,64 @@
+"""The multi-rank bench path on CPU: two gloo ranks (replicas only, no data-path
+collective) combine their timed regions by MAX and their iterations by SUM, and
+the reference arm runs on rank 0 alone."""
+import json
+import os
+import socket
+import types
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, port, figures, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=len(figures))
+    try:
+        out[rank] = bench.combine_ranks(*figures[rank], len(figures))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time_and_all_iterations():
+    figures = [(1.25, 896), (1.5, 960)]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank, args=(_free_port(), figures, out), nprocs=2, join=True,
+                           start_method="spawn")
+        got = dict(out)
+    assert got[0] == got[1] == (1.5, 1856.0)
+    # whole-job throughput = units of every rank / the slowest rank's time
+    assert got[0][1] / got[0][0] == pytest.approx(1856 / 1.5)
+
+
+def test_one_rank_keeps_its_own_figures():
+    assert bench.combine_ranks(2.0, 700, 1) == (2.0, 700.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    calls = []
+    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda iters: calls.append(iters) or
+                        {"value": 50.0, "unit": bench.UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "stub"})
+    args = types.SimpleNamespace(warmup=3, steps=2, cpu_sample_iters=40, gpus=2)
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(args)
+    assert calls == [] and capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert calls == [40] * 5
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] == 50.0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
