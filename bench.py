@@ -87,6 +87,20 @@ def combine_ranks(total_s: float, iters: int, ws: int, device="cpu"):
     return float(tmax[0]), float(tsum[1])
 
 
+def shard_by_nnz(sizes, ws: int):
+    """Split independent LPs across ranks by a greedy balance of their nonzeros:
+    largest first, each onto the least loaded rank (ties: the lower rank).  Every
+    rank computes the same split from the sizes alone, so no exchange is needed.
+    Returns one sorted index list per rank."""
+    load = [0] * ws
+    parts = [[] for _ in range(ws)]
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(ws), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -353,23 +367,46 @@ def run_kernels_only(args):
 
 
 def run_batch(args):
-    """All LPs of the batch to rel. KKT 1e-4 in one pdlp_solve_batch call (host buffers:
-    the call uploads, sets up, solves and downloads; setup and solve are timed apart)."""
+    """All LPs of the batch to rel. KKT 1e-4 by pdlp_solve_batch (host buffers: the
+    call uploads, sets up, solves and downloads; setup and solve are timed apart).
+    With N > 1 processes the LPs are independent problems: each rank solves the
+    share ``shard_by_nnz`` gives it (no data-path collective), the timed region is
+    the slowest rank's and the iterations are summed over the ranks; the total work
+    is the one batch, so the scaling is strong."""
     import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
 
     import __graft_entry__ as G
     G.build()
     import lpgen
     import paper_2503_10344_gb300 as P
 
-    lps = lpgen.set_cover_batch(args.batch_count)
+    every = lpgen.set_cover_batch(args.batch_count)
+    if len(every) < ws:
+        raise SystemExit(f"a batch of {len(every)} LPs cannot be shared by {ws} ranks")
+    mine = shard_by_nnz([l.nnz for l in every], ws)[rank]
+    lps = [every[i] for i in mine]
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
     prm = P.default_params(tol=1e-4, precision=args.precision, **lane_params(args))
     for _ in range(args.warmup):
         P.pdlp_solve_batch(lps, prm, want_y=False)
     times, setup, solve, iters, launches = [], [], [], [], 0
-    with ClockSampler(0) as clk:
+    with ClockSampler(dev.index) as clk:
+        barrier()
         for _ in range(args.steps):
-            torch.cuda.synchronize()
+            torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             _, _, res = P.pdlp_solve_batch(lps, prm, want_y=False)
             times.append(time.perf_counter() - t0)
@@ -377,9 +414,18 @@ def run_batch(args):
             solve.append(res[0]["solve_s"])
             iters.append(sum(r["iters"] for r in res))
             launches += res[0]["kernel_launches"]
+        barrier()
+    solve_s, all_iters = combine_ranks(sum(solve), sum(iters), ws, dev)
+    wall_s, all_launches = combine_ranks(sum(times), launches, ws, dev)
+    its = [r["iters"] for r in res]
     ok = sum(r["status"] == P.PDLP_OPTIMAL for r in res)
-    it = np.array([r["iters"] for r in res])
-    # roofline of the step kernels over the whole batch, every LP live (HBM: ~3 GB per attempt)
+    if ws > 1:  # the results' gather, outside the timed region
+        got = [None] * ws
+        torch.distributed.all_gather_object(got, (ok, its))
+        ok, its = sum(g[0] for g in got), [i for g in got for i in g[1]]
+    it = np.array(its)
+    # roofline of the step kernels over this rank's batch, every LP live (HBM: ~3 GB per
+    # attempt for the whole batch)
     kt = P.time_kernels_batch(lps, prm, reps=20)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
@@ -388,22 +434,28 @@ def run_batch(args):
                 "frac": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peak}
             for k, v in kt.items() if v["ms"] > 0}
     dom = max(("primal_step", "dual_step"), key=lambda k: kt[k]["ms"])
-    line = {"metric": METRIC, "value": sum(iters) / sum(solve), "unit": UNIT + " (sum over the batch)",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
-            "data": "synthetic",
-            "config": {"workload": f"batch of {len(lps)} set-cover sub-LPs, sum m={sum(l.m for l in lps)}, "
-                                   f"sum n={sum(l.n for l in lps)}, nnz={sum(l.nnz for l in lps)}, tol=1e-4",
-                       "precision": args.precision},
-            "solve_s": sum(solve) / args.steps, "setup_s": sum(setup) / args.steps,
-            "lps_per_s": len(lps) / (sum(solve) / args.steps), "optimal": ok,
-            "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
-                         "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": None,
-                         "peak_source": "measured" if peaks else "fallback", "kernels": kern},
-            "gpu_launches": launches, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        line = {"metric": METRIC, "value": all_iters / solve_s, "unit": UNIT + " (sum over the batch)",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * wall_s / args.steps, "higher_is_better": True,
+                "scaling": "strong" if ws > 1 else "weak",
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": f"batch of {len(every)} set-cover sub-LPs, "
+                                       f"sum m={sum(l.m for l in every)}, sum n={sum(l.n for l in every)}, "
+                                       f"nnz={sum(l.nnz for l in every)}, tol=1e-4",
+                           "precision": args.precision,
+                           "parallelism": f"lps sharded by nnz over {ws} ranks" if ws > 1 else "single"},
+                "solve_s": solve_s / args.steps, "setup_s": sum(setup) / args.steps,
+                "lps_per_s": len(every) / (solve_s / args.steps), "optimal": ok,
+                "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
+                             "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": None,
+                             "peak_source": "measured" if peaks else "fallback", "kernels": kern},
+                "gpu_launches": int(all_launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_energy(args):

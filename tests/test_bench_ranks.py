@@ -1,11 +1,13 @@
-"""The multi-rank bench path on CPU: two gloo ranks (replicas only, no data-path
-collective) combine their timed regions by MAX and their iterations by SUM, and
-the reference arm runs on rank 0 alone."""
+"""The multi-rank bench path on CPU: two gloo ranks (no data-path collective)
+combine their timed regions by MAX and their iterations by SUM, agree on the
+split of a batch of independent LPs without an exchange, and the reference arm
+runs on rank 0 alone."""
 import json
 import os
 import socket
 import types
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -62,3 +64,42 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     assert calls == [40] * 5
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] == 50.0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_shard_by_nnz_is_a_balanced_partition():
+    sizes = np.random.default_rng(5).integers(10_000, 2_000_000, 256).tolist()
+    for ws in (1, 2, 3, 8):
+        parts = bench.shard_by_nnz(sizes, ws)
+        assert len(parts) == ws
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(sizes)))          # each LP on exactly one rank
+        loads = [sum(sizes[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)    # greedy bound
+        assert parts == bench.shard_by_nnz(sizes, ws)   # the same split on every call
+    # 9 -> rank 0, 7 -> rank 1, 5 -> rank 1 (load 7 < 9), 1 -> rank 0 (load 9 < 12)
+    assert bench.shard_by_nnz([5, 9, 7, 1], 2) == [[1, 3], [0, 2]]
+
+
+def _split_rank(rank, port, sizes, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    try:
+        mine = bench.shard_by_nnz(sizes, 2)[rank]  # computed locally, no exchange
+        got = [None, None]
+        dist.all_gather_object(got, mine)      # gathered here only to check them
+        out[rank] = got
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_agree_on_the_split_without_an_exchange():
+    sizes = np.random.default_rng(6).integers(1, 10**6, 37).tolist()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.start_processes(_split_rank, args=(_free_port(), sizes, out), nprocs=2, join=True,
+                           start_method="spawn")
+        got = dict(out)
+    assert got[0] == got[1]
+    a, b = got[0]
+    assert not set(a) & set(b) and sorted(a + b) == list(range(37))
