@@ -1325,7 +1325,16 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   }
   const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
   const double avg_a = M ? (double)Z / (double)M : 1.0, avg_t = N ? (double)Z / (double)N : 1.0;
-  int lanes[4] = {p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane),
+  // a float32 batch whose step data is well beyond L2 streams from HBM, where the dual
+  // kernel gathers the (x', dx) pairs from DRAM: a quarter of the lanes per row (four
+  // times the rows per warp in flight) measured faster there (256 covering sub-LPs,
+  // 142M nonzeros: 629 us per dual half-step against 815 us with 8 lanes, the
+  // iteration phase 0.295 against 0.343 s), while L2-resident problems keep the count
+  // that wins on them (float64 batches were not measured and keep theirs)
+  const double step_bytes = 2.0 * (double)Z * 8.0 + 40.0 * (double)(M + N);
+  const double per_lane_a =
+      mode != MODE_FP64 && step_bytes > 256e6 ? 4.0 * per_lane : per_lane;
+  int lanes[4] = {p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane_a),
                   p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane),
                   p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0),
                   p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0)};
