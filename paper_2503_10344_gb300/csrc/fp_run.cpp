@@ -25,6 +25,12 @@
 
 #include "../../include/pdlp.h"
 
+#include <string>
+
+namespace pdlp {
+extern thread_local std::string g_last_error;  // pdlp_last_error (defined with the solver)
+}
+
 namespace {
 
 constexpr double kIntEps = 1e-6;
@@ -371,6 +377,12 @@ int fp_fail(fp_result* r, int status) {
   return PDLP_OK;
 }
 
+// a rejected argument: PDLP_ERR_INVALID_INPUT with its reason for pdlp_last_error
+int bad_input(const char* why) {
+  pdlp::g_last_error = why;
+  return PDLP_ERR_INVALID_INPUT;
+}
+
 }  // namespace
 
 extern "C" int fp_default_params(fp_params* p) {
@@ -393,19 +405,22 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
     fp_default_params(&dflt);
     prm = &dflt;
   }
-  if (!A || !r || !x_out || !is_int || !x_lp || !c || !l || !u || (A->m > 0 && (!b || !sense)) ||
-      prm->struct_size != sizeof(fp_params) || A->m < 0 || A->n < 1 || A->nnz < 0 ||
-      prm->var_strategy < FP_FRAC || prm->var_strategy > FP_TYPE)
-    return PDLP_ERR_INVALID_INPUT;
+  if (!A || !r || !x_out || !is_int || !x_lp || !c || !l || !u || (A->m > 0 && (!b || !sense)))
+    return bad_input("fp_run: NULL problem, vector, result or output argument");
+  if (prm->struct_size != sizeof(fp_params))
+    return bad_input("fp_params.struct_size mismatch (use fp_default_params)");
+  if (A->m < 0 || A->n < 1 || A->nnz < 0) return bad_input("fp_run: need m >= 0, n >= 1, nnz >= 0");
+  if (prm->var_strategy < FP_FRAC || prm->var_strategy > FP_TYPE)
+    return bad_input("fp_run: unknown var_strategy");
   if ((prm->var_strategy == FP_REDCOST || prm->var_strategy == FP_DUAL) && !y_lp && A->m > 0)
-    return PDLP_ERR_INVALID_INPUT;
+    return bad_input("fp_run: FP_REDCOST and FP_DUAL need y_lp");
   memset(r, 0, sizeof(*r));
   const auto t0 = std::chrono::steady_clock::now();
   Problem P{A->m, A->n, A->row_ptr, A->col, A->val, b, sense, c, l, u, {}, {}, {}};
   // column lists, rows ascending
   P.at_ptr.assign(P.n + 1, 0);
   for (int64_t p = 0; p < A->nnz; ++p) {
-    if (A->col[p] < 0 || A->col[p] >= P.n) return PDLP_ERR_INVALID_INPUT;
+    if (A->col[p] < 0 || A->col[p] >= P.n) return bad_input("fp_run: column index out of range");
     ++P.at_ptr[A->col[p] + 1];
   }
   for (int j = 0; j < P.n; ++j) P.at_ptr[j + 1] += P.at_ptr[j];
@@ -570,9 +585,9 @@ extern "C" int fp_run_refs(const pdlp_csr* A, const double* b, const char* sense
                            int nrefs, const double* y_lp, const uint8_t* is_int,
                            const fp_params* prm, double* x_out, fp_result* r, int* chosen) {
   if (!A || !x_refs || nrefs < 1 || !x_out || !r || !chosen || A->n < 1)
-    return PDLP_ERR_INVALID_INPUT;
+    return bad_input("fp_run_refs: need A, nrefs >= 1 reference points, x_out, r and chosen");
   for (int k = 0; k < nrefs; ++k)
-    if (!x_refs[k]) return PDLP_ERR_INVALID_INPUT;
+    if (!x_refs[k]) return bad_input("fp_run_refs: NULL reference point");
   std::vector<double> x((size_t)A->n);
   fp_result cur;
   bool have = false;

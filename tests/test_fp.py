@@ -199,10 +199,12 @@ def test_cabi_search_matches_oracle_on_other_shapes(P, maker, strategy):
 
 def test_cabi_rejects_bad_arguments(P):
     lp, x, y = hand_mip()
-    with pytest.raises(P.PdlpError):
+    with pytest.raises(P.PdlpError, match="need y_lp"):
         P.fp_run(lp, x, None, strategy="dual", final_lp=False)  # Dual needs y
-    with pytest.raises(P.PdlpError):
+    with pytest.raises(P.PdlpError, match="unknown var_strategy"):
         P.fp_run(lp, x, y, strategy=7, final_lp=False)
+    with pytest.raises(P.PdlpError, match="nrefs >= 1"):
+        P.fp_run_refs(lp, [], y, final_lp=False)
 
 
 def tight_mip(seed, m=30, n=40):
