@@ -8,7 +8,7 @@
  * prediction is projected onto the bounds and the dual cone, and PDLP starts
  * from it only if its relative KKT error (the measure of pdlp.h, section 4's
  * relative tolerances) is below that of the cold start -- cold PDLP stays the
- * fallback and the judge.  The network is not in the paper; its definition:
+ * fallback and decides which start is taken.  The network is not in the paper; its definition:
  *
  *   hidden width H = 64, L = 3 layers, weights stored in bfloat16 (float32
  *   master copies for training), all arithmetic in float32;

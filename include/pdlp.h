@@ -361,7 +361,7 @@ int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, con
  * (No counterpart in the paper: this is a deployment variant of the solve.)
  * For code where cudaMalloc is unavailable or unwelcome -- device memory owned
  * by another allocator that must account for every byte, a latency-bound loop
- * that must not reach the driver's allocator, a caller with no workspace to
+ * that must not reach the CUDA driver's allocator, a caller with no workspace to
  * hand over.  Same arguments and results as pdlp_solve_device, minus the
  * workspace: the scratch is one static device array of 64 MiB inside this
  * library, which every GPU that loads the library holds until process exit.

@@ -1650,7 +1650,7 @@ int pdlp_solve_warm(gnn_model* md, const pdlp_csr* A, const double* b, const cha
   const double predict_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const bool warm = rc == PDLP_OK && hk[3] < hk[7];
   if (rc == PDLP_OK) {
-    // the start point is the judged one; the primal weight always comes from the
+    // the start point is the one chosen above; the primal weight always comes from the
     // projected prediction's norms (pdlp_solve_hinted)
     pdlp_csr Ad{m, n, (int64_t)g->d.nnz, g->d.ptr64, g->d.a_col, g->d.a_val};
     rc = pdlp::solve_device_hint(&Ad, g->d.b, g->d.sense, g->d.c, g->d.l, g->d.u, p,

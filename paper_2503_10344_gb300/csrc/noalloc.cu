@@ -4,7 +4,7 @@
 // Who needs it: code that runs where cudaMalloc is unavailable or unwelcome,
 // for example a process whose device memory is owned by another allocator (a
 // framework's pool that must see every byte), a latency-bound loop that must
-// never reach the driver's allocator, or a caller that has no way to hand us
+// never reach the CUDA driver's allocator, or a caller that has no way to hand us
 // a workspace.  Such a caller passes only its inputs and outputs.
 //
 // The scratch of the solve lives in one file-scope __device__ array of

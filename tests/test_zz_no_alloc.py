@@ -1,7 +1,7 @@
 """pdlp_solve_device_noalloc, the solve for callers that cannot allocate device memory.
 
 Such callers (device memory owned by another allocator, loops that must not
-reach the driver's allocator, code with no workspace to hand over) get the
+reach the CUDA driver's allocator, code with no workspace to hand over) get the
 same solve with its scratch in the library's static 64 MiB device array.  This
 file checks, through the C ABI, that two calls in a row give what
 pdlp_solve_device gives on the same inputs (to the 1e-9 parity tolerance of
