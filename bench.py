@@ -544,8 +544,25 @@ def run_fp(args):
                       "precision": args.precision, "runs": rows}), flush=True)
 
 
+def single_gpu_rank(args) -> bool:
+    """The energy, fix-and-propagate and kernel-timing workloads measure one GPU: under a
+    multi-process launch rank 0 runs them on its own device and the other ranks leave
+    without work.  Returns whether this process runs the workload."""
+    ws, rank, local = dist_env()
+    if ws == 1:
+        return True
+    if rank != 0:
+        return False
+    import torch
+    torch.cuda.set_device(local)
+    return True
+
+
 if __name__ == "__main__":
     a = parse()
+    if a.impl == "gpu" and (a.kernels_only or a.workload in ("energy", "fp")) \
+            and not single_gpu_rank(a):
+        sys.exit(0)
     if a.kernels_only and a.impl == "gpu":
         run_kernels_only(a)
     elif a.workload == "fp" and a.impl == "gpu":

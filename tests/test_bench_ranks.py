@@ -103,3 +103,13 @@ def test_two_ranks_agree_on_the_split_without_an_exchange():
     assert got[0] == got[1]
     a, b = got[0]
     assert not set(a) & set(b) and sorted(a + b) == list(range(37))
+
+
+@pytest.mark.parametrize("argv", [["--workload", "energy"], ["--workload", "fp"], ["--kernels-only"]])
+def test_single_gpu_workloads_leave_other_ranks_idle(argv):
+    import subprocess
+    import sys
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"),
+                          *argv], env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout == ""
