@@ -184,6 +184,27 @@ def cpu_oracle_sample(iters: int) -> dict:
                       f"on the full workload, {d['seconds']:.1f} s"}
 
 
+def cpu_oracle_all_cores(iters: int, procs: int | None = None) -> dict:
+    """The same oracle sample in one single-threaded process per host core, all at once
+    (independent replicas, as the GPU ranks are): the host's aggregate oracle throughput,
+    the sum of the processes' rates, each timed over its own solve."""
+    procs = procs or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = CPU_SNIPPET.format(root=ROOT, iters=iters)
+    runs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                             stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+    outs = []
+    for r in runs:
+        out, err = r.communicate()
+        if r.returncode != 0:
+            raise RuntimeError(f"oracle replica failed: {err.strip()[-200:]}")
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    rate = sum(d["iters"] / d["seconds"] for d in outs)
+    return {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} concurrent single-threaded replicas, {iters} accepted iterations "
+                      f"each on the full workload, {max(d['seconds'] for d in outs):.1f} s at most"}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -306,6 +327,10 @@ def run_gpu(args):
             cpu = cpu_oracle_sample(args.cpu_sample_iters)
         except Exception as e:  # reported, never silently replaced
             cpu = {"error": str(e)[:200]}
+        try:
+            cpu["all_cores"] = cpu_oracle_all_cores(max(1, args.cpu_sample_iters // 4))
+        except Exception as e:
+            cpu["all_cores"] = {"error": str(e)[:200]}
     if rank == 0:
         prec_used = {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
                      3: "fp32 iterates, pattern matrix"}[res["precision_used"]]

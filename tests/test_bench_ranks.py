@@ -113,3 +113,9 @@ def test_single_gpu_workloads_leave_other_ranks_idle(argv):
     out = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"),
                           *argv], env=env, capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and out.stdout == ""
+
+
+def test_all_core_oracle_sample_sums_concurrent_replicas():
+    d = bench.cpu_oracle_all_cores(iters=2, procs=2)
+    assert d["cores"] == 2 and d["kind"] == "oracle" and d["value"] > 0
+    assert "2 concurrent single-threaded replicas" in d["sample"]
