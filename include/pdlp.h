@@ -30,8 +30,12 @@
  *  - Return codes: 0 (PDLP_OK) or a negative PDLP_ERR_* value.  The solver
  *    outcome (tolerance met, iteration limit, ...) is pdlp_result.status,
  *    never the return code.  pdlp_error_string() names every code.
- *  - Reentrancy: calls share no mutable global state; concurrent calls on
- *    different streams are independent.
+ *  - Reentrancy: calls share no mutable state but two mutex-guarded caches
+ *    (the executable CUDA graphs of recent check periods, keyed by every
+ *    launch parameter including the workspace addresses, and the autotuner's
+ *    lanes per shape) and the static scratch array of
+ *    pdlp_solve_device_noalloc (its note below); concurrent calls on different
+ *    streams into different workspaces are independent.
  *
  * Relative KKT measures reported in pdlp_result (the definition every result
  * is judged by), for x in [l,u] and y in the dual cone, on the original data:
