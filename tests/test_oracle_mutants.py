@@ -11,6 +11,7 @@ import types
 import numpy as np
 import pytest
 
+import lpgen
 import test_oracle_pins as P
 
 ORACLE_SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -46,7 +47,24 @@ MUTANTS = [
     ("primal-weight hint not projected onto the bounds",
      "xh = proj_box(np.asarray(p.omega_hint[0], dtype=np.float64) / dc, lt, ut)",
      "xh = np.asarray(p.omega_hint[0], dtype=np.float64) / dc", ["test_primal_weight_hint_by_hand"]),
+    ("initial primal weight inverted", "omega = nc / nq if", "omega = nq / nc if",
+     ["test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly"]),
+    ("step bound weighs dy by omega and dx by 1/omega",
+     "num = omega * float(dx @ dx) + float(dy @ dy) / omega",
+     "num = float(dx @ dx) / omega + omega * float(dy @ dy)",
+     ["test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly"]),
+    ("dual step with sigma = eta / omega", "y + eta * omega * (qt - kt @", "y + eta / omega * (qt - kt @",
+     ["test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly"]),
 ]
+
+
+def _pin_args(name):
+    """Arguments of a parametrised pin when it is called directly."""
+    if name == "test_mip_relaxation_matches_highs":
+        return {"seed": 1}
+    if name == "test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly":
+        return {"maker": lambda: lpgen.mip_relaxation(1)}
+    return {}
 
 
 def _mutant_module(old, new):
@@ -70,11 +88,8 @@ def test_mutant_is_caught(desc, old, new, pins, monkeypatch):
     caught = []
     for name in pins:
         fn = getattr(P, name)
-        params = {}
-        if name == "test_mip_relaxation_matches_highs":
-            params = {"seed": 1}
         try:
-            fn(**params)
+            fn(**_pin_args(name))
         except Exception:  # an assertion, or the mutant breaking outright
             caught.append(name)
     assert caught, f"mutant '{desc}' passed every pin in {pins}"
@@ -86,4 +101,4 @@ def test_unmutated_copy_passes_the_same_pins(monkeypatch):
     monkeypatch.setattr(P, "O", mod)
     for _, _, _, pins in MUTANTS:
         for name in pins:
-            getattr(P, name)(**({"seed": 1} if name == "test_mip_relaxation_matches_highs" else {}))
+            getattr(P, name)(**_pin_args(name))

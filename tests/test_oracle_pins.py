@@ -247,6 +247,29 @@ def test_row_and_column_rescaling_keeps_the_solution():
     assert r1.kkt.primal_obj == pytest.approx(r2.kkt.primal_obj, rel=1e-6)
 
 
+@pytest.mark.parametrize("maker", [lambda: lpgen.mip_relaxation(1),
+                                   lambda: lpgen.random_sparse_lp(11, 300, 500)],
+                         ids=["relaxation1", "free_eq"])
+def test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly(maker):
+    """Right-hand side and bounds times beta, costs times gamma (powers of two, so every
+    product is exact): in exact arithmetic PDLP's iterates become (beta x, gamma y) -- the
+    primal weight's start ||c~|| / ||q~|| moves by gamma / beta, which keeps tau * (c - K^T y)
+    and sigma * (q - K x) in step, and the step bound eta_bar (omega on dx, 1/omega on dy) is
+    unchanged.  With scalings by powers of two the run is the same bit for bit (adaptive
+    steps, restarts off: the restart metric's gap term does not scale with the others)."""
+    lp = maker()
+    beta, gamma = 8.0, 0.25
+    rows = np.repeat(np.arange(lp.m), np.diff(lp.row_ptr))
+    lp2 = lpgen._lp(lp.m, lp.n, rows, lp.col, lp.val, lp.b * beta, lp.sense, lp.c * gamma,
+                    lp.l * beta, lp.u * beta, lp.is_int, "scaled")
+    prm = O.Params(iter_limit=150, terminate=False, restarts=False)
+    r1, r2 = O.solve(lp, prm), O.solve(lp2, prm)
+    assert r2.attempts == r1.attempts and r2.omega == r1.omega * gamma / beta
+    for a, b, f in ((r2.x_cur, r1.x_cur, beta), (r2.y_cur, r1.y_cur, gamma),
+                    (r2.x_avg, r1.x_avg, beta), (r2.y_avg, r1.y_avg, gamma)):
+        np.testing.assert_array_equal(a, f * b)
+
+
 def test_looser_tolerance_never_needs_more_iterations():
     lp = lpgen.mip_relaxation(6)
     its = [O.solve(lp, O.Params(tol=t)).iters for t in (1e-2, 1e-4, 1e-6, 1e-8)]
