@@ -55,6 +55,14 @@ MUTANTS = [
      ["test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly"]),
     ("dual step with sigma = eta / omega", "y + eta * omega * (qt - kt @", "y + eta / omega * (qt - kt @",
      ["test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly"]),
+    ("restart candidate with the higher KKT", "use_avg = ma < mc", "use_avg = ma > mc",
+     ["test_restarts_and_primal_weight_by_hand"]),
+    ("primal weight ratio inverted", "math.log(ddy / ddx)", "math.log(ddx / ddy)",
+     ["test_restarts_and_primal_weight_by_hand"]),
+    ("primal weight without smoothing", "+ (1.0 - p.omega_smooth) * math.log(omega))",
+     "+ p.omega_smooth * math.log(ddy / ddx))", ["test_restarts_and_primal_weight_by_hand"]),
+    ("artificial restart fraction 0.36 read as 0.6", "beta_art: float = 0.36",
+     "beta_art: float = 0.6", ["test_restarts_and_primal_weight_by_hand"]),
 ]
 
 

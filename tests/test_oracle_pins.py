@@ -270,6 +270,34 @@ def test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly(maker):
         np.testing.assert_array_equal(a, f * b)
 
 
+def test_restarts_and_primal_weight_by_hand():
+    """A9/A10 worked by hand: min x s.t. x >= 1, x in [0, 10], no scaling, eta = 0.5, a check
+    after every step.  KKT_w(z) = sqrt(w r_p^2 + r_d^2 / w + gap^2); r_d = 0 (finite bounds).
+    z0 = (0, 0): KKT 1.
+    it 1: z = (0, 0.5): r_p = 1, gap 0.5, KKT sqrt(1.25) = 1.118; average = current (tie ->
+      current); 1 - 0 >= 0.36: artificial restart; dx = 0: w stays 1.
+    it 2: z = (0, 1), KKT sqrt(2) = 1.414 > 0.8 * 1.118; 2 - 1 >= 0.72: artificial restart.
+    it 3: z = (0, 1.5): lambda = -0.5 on the upper bound 10, dual obj 1.5 - 5, gap 3.5,
+      KKT 3.64; no criterion (1 < 1.08): no restart.
+    it 4: z = (0.25, 1.75), KKT 6.05; average since it 2 = (0.125, 1.625), KKT 4.83 -> the
+      candidate; 4 - 2 >= 1.44: restart to the average; dx = 0.125, dy = 0.625 from the
+      anchor (0, 1): w = exp(0.5 ln 5 + 0.5 ln 1) = sqrt(5).
+    it 5: x = 0.125 + (0.5 / sqrt5) 0.625, y = 1.625 + 0.5 sqrt5 (1 - (2x - 0.125))."""
+    lp = _lp_from_dense([[1.0]], [1.0], "G", [1.0], [0.0], [10.0])
+    r = O.solve(lp, O.Params(iter_limit=5, check_period=1, adaptive=False, fixed_eta=0.5,
+                             ruiz_iters=0, pc_alpha=None, terminate=False))
+    s5 = math.sqrt(5.0)
+    kinds = [k for k, _ in r.check_trace]
+    omegas = [w for _, w in r.check_trace]
+    assert kinds == [1, 1, 0, 2, 0] and r.restarts == 3
+    assert omegas[:3] == [1.0, 1.0, 1.0]
+    assert omegas[3] == pytest.approx(s5, rel=1e-15) and omegas[4] == omegas[3]
+    x5 = 0.125 + (0.5 / s5) * 0.625
+    y5 = 1.625 + 0.5 * s5 * (1.0 - (2.0 * x5 - 0.125))
+    assert r.x_cur[0] == pytest.approx(x5, rel=1e-14)
+    assert r.y_cur[0] == pytest.approx(y5, rel=1e-14)
+
+
 def test_looser_tolerance_never_needs_more_iterations():
     lp = lpgen.mip_relaxation(6)
     its = [O.solve(lp, O.Params(tol=t)).iters for t in (1e-2, 1e-4, 1e-6, 1e-8)]
