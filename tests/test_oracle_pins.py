@@ -298,6 +298,24 @@ def test_restarts_and_primal_weight_by_hand():
     assert r.y_cur[0] == pytest.approx(y5, rel=1e-14)
 
 
+def test_sufficient_decay_restart_by_hand():
+    """A9's sufficient-decay rule worked by hand: min x s.t. x >= 1, x in [0, inf), no
+    scaling, eta = 1, a check after every step; r_d = lambda^- (u infinite).
+    it 1: z = (0, 1), KKT sqrt(1 + 1) (r_p 1, gap 1): artificial restart (1 >= 0.36).
+    it 2: z = (0, 2), lambda = -1: KKT sqrt(1 + 1 + 4) = 2.449: artificial restart (1 >= 0.72).
+    it 3: z = (1, 1), the optimum: KKT 0.  The artificial rule does not fire (1 < 1.08) and
+      the necessary one needs a previous candidate (there is none after a restart), so only
+      sufficient decay (0 <= 0.2 * 2.449) restarts; dx = dy = 1 from the anchor (0, 2):
+      w = exp(0.5 ln 1 + 0.5 ln 1) = 1.
+    it 4: the last step, (1, 1) again."""
+    lp = _lp_from_dense([[1.0]], [1.0], "G", [1.0], [0.0], [np.inf])
+    r = O.solve(lp, O.Params(iter_limit=4, check_period=1, adaptive=False, fixed_eta=1.0,
+                             ruiz_iters=0, pc_alpha=None, terminate=False))
+    assert [k for k, _ in r.check_trace] == [1, 1, 1, 0] and r.restarts == 3
+    assert all(w == 1.0 for _, w in r.check_trace)
+    assert r.x_cur.tolist() == [1.0] and r.y_cur.tolist() == [1.0]
+
+
 def test_looser_tolerance_never_needs_more_iterations():
     lp = lpgen.mip_relaxation(6)
     its = [O.solve(lp, O.Params(tol=t)).iters for t in (1e-2, 1e-4, 1e-6, 1e-8)]
