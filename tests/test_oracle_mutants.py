@@ -63,6 +63,11 @@ MUTANTS = [
      "+ p.omega_smooth * math.log(ddy / ddx))", ["test_restarts_and_primal_weight_by_hand"]),
     ("artificial restart fraction 0.36 read as 0.6", "beta_art: float = 0.36",
      "beta_art: float = 0.6", ["test_restarts_and_primal_weight_by_hand"]),
+    ("necessary-decay restart without the rise over the previous candidate",
+     "or (m_cand <= p.beta_nec * m_last and m_cand > kkt_prev_cand)",
+     "or (m_cand <= p.beta_nec * m_last)", ["test_necessary_decay_restart_by_hand"]),
+    ("necessary-decay factor 0.8 read as 0.5", "beta_nec: float = 0.8", "beta_nec: float = 0.5",
+     ["test_necessary_decay_restart_by_hand"]),
     ("sufficient-decay restart dropped", "do_restart = (m_cand <= p.beta_suff * m_last\n",
      "do_restart = (False\n", ["test_sufficient_decay_restart_by_hand"]),
 ]

@@ -316,6 +316,25 @@ def test_sufficient_decay_restart_by_hand():
     assert r.x_cur.tolist() == [1.0] and r.y_cur.tolist() == [1.0]
 
 
+def test_necessary_decay_restart_by_hand():
+    """A9's necessary-decay rule worked by hand (the artificial rule moved out of the way,
+    beta_art = 1, so only the first check restarts by it): min 2x s.t. x >= 2, x in [0, 4],
+    no scaling, w0 = ||c|| / ||q|| = 1, eta = 0.5, a check after every step;
+    KKT = sqrt(r_p^2 + gap^2) (finite bounds: r_d = 0), dual obj 2y - 4 max(y - 2, 0).
+    it 1: z = (0, 1), KKT sqrt(8): first check, restart; anchor (0, 1), last KKT 2.828.
+    it 2: z = (0, 2), KKT sqrt(20) = 4.47: no rule (> 0.8 * 2.828 = 2.26).
+    it 3: z = (0, 3), KKT sqrt(8) = 2.83 (average (0, 2.5): 3.61): no rule.
+    it 4: z = (0.5, 3.5), KKT 1.5 <= 2.26 but below the previous candidate 2.83: no restart.
+    it 5: z = (1.25, 3.5), KKT sqrt(2.8125) = 1.68 (average (0.4375, 3): 1.93): <= 2.26 and
+      above the previous candidate 1.5: necessary decay restarts (sufficient decay would
+      need <= 0.57); dx = 1.25, dy = 2.5 from the anchor: w = exp(0.5 ln 2 + 0.5 ln 1)."""
+    lp = _lp_from_dense([[1.0]], [2.0], "G", [2.0], [0.0], [4.0])
+    r = O.solve(lp, O.Params(iter_limit=6, check_period=1, adaptive=False, fixed_eta=0.5,
+                             ruiz_iters=0, pc_alpha=None, terminate=False, beta_art=1.0))
+    assert [k for k, _ in r.check_trace] == [1, 0, 0, 0, 1, 0] and r.restarts == 2
+    assert r.check_trace[4][1] == pytest.approx(math.sqrt(2.0), rel=1e-15)
+
+
 def test_looser_tolerance_never_needs_more_iterations():
     lp = lpgen.mip_relaxation(6)
     its = [O.solve(lp, O.Params(tol=t)).iters for t in (1e-2, 1e-4, 1e-6, 1e-8)]
