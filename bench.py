@@ -188,7 +188,9 @@ def cpu_oracle_all_cores(iters: int, procs: int | None = None) -> dict:
     """The same oracle sample in one single-threaded process per host core, all at once
     (independent replicas, as the GPU ranks are): the host's aggregate oracle throughput,
     the sum of the processes' rates, each timed over its own solve."""
-    procs = procs or os.cpu_count() or 1
+    if procs is None:  # the cores this process may run on, at most 32 replicas
+        procs = min(32, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                    else (os.cpu_count() or 1))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = CPU_SNIPPET.format(root=ROOT, iters=iters)
     runs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
