@@ -330,7 +330,7 @@ def run_gpu(args):
         except Exception as e:  # reported, never silently replaced
             cpu = {"error": str(e)[:200]}
         try:
-            cpu["all_cores"] = cpu_oracle_all_cores(max(1, args.cpu_sample_iters // 4))
+            cpu["all_cores"] = cpu_oracle_all_cores(args.cpu_sample_iters)
         except Exception as e:
             cpu["all_cores"] = {"error": str(e)[:200]}
     if rank == 0:
