@@ -119,3 +119,12 @@ def test_all_core_oracle_sample_sums_concurrent_replicas():
     d = bench.cpu_oracle_all_cores(iters=2, procs=2)
     assert d["cores"] == 2 and d["kind"] == "oracle" and d["value"] > 0
     assert "2 concurrent single-threaded replicas" in d["sample"]
+
+
+def test_roofline_traffic_comes_from_the_committed_capture():
+    """bench.py reads the DRAM bytes per launch of its roofline kernel from the committed
+    ncu summary, and reports none for a kernel or precision that was not captured."""
+    assert bench.ncu_traffic("dual_step", "bf16") == 7_760_640
+    assert bench.ncu_traffic("primal_step", "bf16") == 11_007_232
+    assert bench.ncu_traffic("dual_step", "fp64") is None
+    assert bench.ncu_traffic("persistent_attempt", "bf16") is None
