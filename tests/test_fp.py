@@ -274,6 +274,14 @@ def test_fp_run_refs_keeps_the_best_feasible_run():
     assert j == (0 if direct.status == F.FEASIBLE else -1) and one.obj == direct.obj
 
 
+def test_fp_run_refs_ties_go_to_the_earlier_point():
+    # the same point twice: equal objectives, the first reference is kept
+    lp = lpgen.mip_relaxation(5)
+    r = O.solve(lp, O.Params(tol=1e-4))
+    best, i = F.fp_run_refs(lp, [r.x, r.x.copy()], r.y, lp.is_int, F.FRAC, 1, final_tol=1e-6)
+    assert best.status == F.FEASIBLE and i == 0
+
+
 def test_cabi_refs_without_final_lp_returns_the_last_run(P):
     """Without the final LP no run is declared feasible: fp_run_refs reports index -1 and
     the last reference's search (the same as fp_run from it)."""
