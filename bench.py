@@ -310,8 +310,8 @@ def run_gpu(args):
     peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    # the persistent kernel (default) runs every step attempt of a check period; the
-    # two-launch form times its primal and dual kernels apart
+    # the persistent kernel (persistent = 1, not the default) runs every step attempt of a
+    # check period in one launch; the two-launch form times its primal and dual kernels apart
     if prm.persistent and kt["persistent_attempt"]["ms"] > 0:
         dom = "persistent_attempt"
     else:

@@ -137,11 +137,13 @@ typedef struct {
                            kernel with grid-wide barriers; 0 (default): two kernel launches
                            per attempt.  Same iteration either way; batches always use the
                            two-launch form. */
-  int autotune;         /* 1: before iterating, time the step kernels with 2, 4, 8, 16 and
-                           32 lanes per row (each kernel separately, on this LP, without
-                           moving the iterate) and keep the fastest; cached per (device,
-                           precision mode, m, n, nnz) for the process.  Lanes set explicitly
-                           in lanes_A / lanes_AT are kept.  0 (default): size heuristic. */
+  int autotune;         /* 1: before iterating, time whole step attempts (primal kernel,
+                           dual kernel and decision) with 2, 4, 8, 16 and 32 lanes per row,
+                           first for the primal kernel's A^T, then for the dual kernel's A,
+                           on this LP without moving the iterate, and keep the fastest;
+                           cached per (device, precision mode, m, n, nnz) for the process.
+                           Lanes set explicitly in lanes_A / lanes_AT are kept.  0
+                           (default): size heuristic. */
   int detect_infeasibility; /* 1 (default): test the two certificates above at each KKT
                            check (with terminate = 1); 0: never (an infeasible LP runs to
                            its iteration or time limit) */
@@ -251,8 +253,9 @@ int pdlp_solve_hinted(const pdlp_csr* A, const double* b, const char* sense, con
  * setup as pdlp_solve_batch, then each fused kernel over the whole batch (every LP
  * live) `reps` times from a CUDA graph; ms_per_launch[7] and bytes_per_launch[7] as in
  * pdlp_time_kernels, the bytes summed over the batch ([5] and [6] are 0: batches use
- * the two-launch form, and the whole KKT block is timed for single LPs only).  The batch form of spec pattern 2; the paper has no
- * counterpart.  Returns PDLP_OK or an error code. */
+ * the two-launch form, and the whole KKT block is timed for single LPs only).  A
+ * profiling aid for the batched solve below; the paper has no counterpart.  Returns
+ * PDLP_OK or an error code. */
 int pdlp_time_kernels_batch(int count, const pdlp_csr* const* A, const double* const* b,
                             const char* const* sense, const double* const* c,
                             const double* const* l, const double* const* u, const pdlp_params* p,
@@ -292,8 +295,8 @@ int pdlp_polish_dual(const pdlp_csr* A, const char* sense, const double* c, cons
                      const double* u, const pdlp_params* p, const double* y_in, double* x_out,
                      double* y_out, pdlp_result* r);
 
-/* Solve `count` LPs of uneven size together (north-star pattern "batched":
- * relaxations such as those left after the partial fixings of the heuristic).
+/* Solve `count` LPs of uneven size together (batched relaxations, such as those
+ * left after the partial fixings of the heuristic; no counterpart in the paper).
  * Arrays of per-LP HOST pointers in the layout of pdlp_solve; one parameter
  * set for all; r[count] results.  x_out / y_out may be NULL (or hold NULL
  * entries) for outputs not wanted.
@@ -375,9 +378,14 @@ int pdlp_time_kernels(const pdlp_csr* A, const double* b, const char* sense, con
  *    cudaMalloc/cudaFree, pinned buffer, stream, event or graph); it launches
  *    the solver's kernels directly on `stream` and polls the termination flag
  *    in pageable host memory once per check period.
+ *  - p->autotune = 1 is rejected with PDLP_ERR_INVALID_INPUT: the autotuner
+ *    times its candidates with a stream, events and graphs of its own.  The
+ *    size heuristic and explicit lanes_A / lanes_AT are honoured.
  *  - The first call on each device (with that device current) looks up the
- *    array's device address with cudaGetSymbolAddress and caches it; make
- *    that first call before any stream capture begins.
+ *    array's device address with cudaGetSymbolAddress and caches it.  Every
+ *    call synchronises `stream` (validation, termination flag), so no call may
+ *    be made while that stream is being captured.  cudaDeviceReset makes the
+ *    cached address stale: do not call again on a device after resetting it.
  *  - All calls share the array, which keeps the last call's contents; every
  *    call writes what it reads, so nothing carries over, but calls whose GPU
  *    work overlaps (two streams, two host threads on one device) race on the

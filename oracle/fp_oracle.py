@@ -25,7 +25,7 @@ fixing", "Integer-aware branching strategy", Alg. 1):
   not a single value, draw d, branch, propagate, backtrack on conflict; when
   every integer is fixed, solve the final LP with the integers fixed.
 
-Readings where the paper is silent (listed in the design notes): the random
+Readings where the paper is silent: the random
 generator is SplitMix64 (published by S. Vigna) with u = (r >> 11) * 2^-53,
 one draw per branching node; the LP value is clamped to the current domain
 before d_i is taken; the only propagator is linear activity bound tightening

@@ -1,9 +1,9 @@
 """FP64 CPU oracle of the learned warm start: a bipartite message-passing network
 over the LP's variable / constraint graph (test infrastructure only).
 
-The network (hidden width H = 64, three layers; the paper has no learned part:
-this is the north-star "learned warm start" pattern, its definition is this
-file and the design notes):
+The network (hidden width H = 64, three layers).  The paper has no learned part:
+this network is an addition that predicts a PDLP start point, and its
+definition is this file:
 
   features  F_v[j] = (c_j / c_max, g(l_j), g(u_j), ||A_:j|| / max, deg_j / max, 1)
                       g(v) = sign(v) log(1 + |v|) of v clipped to [-1e3, 1e3] (infinite bounds too)

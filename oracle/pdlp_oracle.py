@@ -12,8 +12,8 @@ The paper (Kempke & Koch, arXiv 2503.10344) solves the LP relaxation of eq. (1)
 *relative* tolerance (section 4, "Hardware and software": relative primal/dual
 tolerances; 1e-4 and 1e-6 in section 4.1 and Table "lp_results").  It runs PDLP
 as a black box and does not restate its internals.  Every internal step below
-is therefore the published PDLP method as this project reads it; the readings
-are listed one by one in the design notes and marked "reading" here:
+is therefore the published PDLP method as this project reads it; each such
+reading is marked "reading" where it is used below:
 
   A0  canonical form: flip <=-rows to >=, K = S A, q = S b; dual cone Y has
       y_i >= 0 on inequality rows and y_i free on equality rows.

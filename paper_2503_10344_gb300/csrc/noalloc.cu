@@ -25,7 +25,15 @@
 // The call itself makes no device allocation and creates no CUDA object: no
 // cudaMalloc / cudaFree, no pinned host buffer, no stream, event or graph; it
 // launches the same kernels as pdlp_solve_device one by one on the caller's
-// stream and polls the termination flag once per check period.
+// stream and polls the termination flag once per check period.  The launch-shape
+// autotuner times candidate shapes with its own stream, events and graphs, so a
+// request for it (pdlp_params.autotune = 1) is refused here; the size heuristic
+// and explicit lanes_A / lanes_AT work as usual.
+//
+// Every call synchronises the stream (input validation, the termination flag),
+// so no call may be made while the stream is being captured into a graph.  The
+// cached address belongs to the device's current context: after cudaDeviceReset
+// it is stale, so a process that resets a device must not call this again.
 #include <mutex>
 
 #include "../../include/pdlp.h"
@@ -63,6 +71,10 @@ extern "C" int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, con
     p = &d;
   }
   if (!A) return pdlp::set_error(PDLP_ERR_INVALID_INPUT, "NULL problem");
+  if (p->autotune != 0)
+    return pdlp::set_error(PDLP_ERR_INVALID_INPUT,
+                           "autotune = 1 needs its own stream, events and graphs; "
+                           "pdlp_solve_device_noalloc creates none (use autotune = 0)");
   const size_t need = pdlp_workspace_size(A->m, A->n, A->nnz, p);
   if (need == 0) return pdlp::set_error(PDLP_ERR_INVALID_INPUT, "invalid sizes");
   if (need > kNoAllocBytes)

@@ -795,7 +795,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   if (m) CUDA_TRY(cudaMemsetAsync(bf.Yl, 0, 8 * (size_t)m, s));
 
   Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s, 0};
-  if (p->autotune && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
+  // the autotuner creates a stream, events and graphs: never without allocation
+  if (p->autotune && !no_alloc && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
     auto set_grids = [&](int lt, int la) -> int {
       const int gps = tiled ? gp_short : grid_for(((long long)n + 1) / 2 * lt, MBp);
       const int gds = tiled ? gd_short : grid_for(((long long)std::max(m, 1) + 1) / 2 * la, MBd);

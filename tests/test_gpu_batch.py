@@ -1,4 +1,4 @@
-"""Batched solves (the north-star "batched" pattern): many uneven LPs in one set of
+"""Batched solves: many uneven LPs in one set of
 launches, each with its own step size, restarts and termination."""
 import numpy as np
 import pytest

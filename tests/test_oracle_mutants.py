@@ -70,6 +70,24 @@ MUTANTS = [
      ["test_necessary_decay_restart_by_hand"]),
     ("sufficient-decay restart dropped", "do_restart = (m_cand <= p.beta_suff * m_last\n",
      "do_restart = (False\n", ["test_sufficient_decay_restart_by_hand"]),
+    ("eta0 from the unscaled matrix", "kmax = float(abs(kt).max()) if kt.nnz else 0.0",
+     "kmax = float(abs(k).max()) if k.nnz else 0.0",
+     ["test_eta0_is_one_over_the_largest_scaled_entry_by_hand"]),
+    ("eta0 from the Frobenius norm of K~", "kmax = float(abs(kt).max()) if kt.nnz else 0.0",
+     "kmax = float(sp.linalg.norm(kt)) if kt.nnz else 0.0",
+     ["test_eta0_is_one_over_the_largest_scaled_entry_by_hand"]),
+    ("eta0 from the spectral norm of K~", "kmax = float(abs(kt).max()) if kt.nnz else 0.0",
+     "kmax = float(np.linalg.norm(kt.toarray(), 2)) if kt.nnz else 0.0",
+     ["test_eta0_is_one_over_the_largest_scaled_entry_by_hand"]),
+    ("restart metric KKT_omega on the unscaled point",
+     "return kkt_canonical(kt, qt, is_eq, ct, lt, ut, xs, ys)", "return unscaled_kkt(xs, ys)",
+     ["test_restart_metric_is_taken_in_scaled_space_by_hand"]),
+    ("primal-weight distances measured unscaled",
+     "ddx = float(np.linalg.norm(cand_x - x_last))\n"
+     "                    ddy = float(np.linalg.norm(cand_y - y_last))",
+     "ddx = float(np.linalg.norm(dc * (cand_x - x_last)))\n"
+     "                    ddy = float(np.linalg.norm(dr * (cand_y - y_last)))",
+     ["test_primal_weight_distances_are_taken_in_scaled_space_by_hand"]),
 ]
 
 

@@ -409,3 +409,86 @@ def test_primal_weight_hint_by_hand():
     assert O.solve(lp, O.Params(**fixed)).omega == 1.0
     r0 = O.solve(lp, O.Params(omega_hint=(np.zeros(2), np.array([0.0, 10.0])), **fixed))
     assert r0.omega == 1.0
+
+
+# ---------------------------------------------------------------- exact non-identity scaling
+# K = diag(4, 16): the first Ruiz pass takes r = s = (sqrt 4, sqrt 16) = (2, 4) from the same
+# K~, so D_r = D_c = (1/2, 1/4) and K~ = I; every later pass and Pock-Chambolle (row and
+# column sums of |K~| = 1) leave it there.  All of it is exact in floating point.
+# K = [[1, 1], [1, 1]]: Ruiz keeps it (maxima 1); Pock-Chambolle divides rows and columns by
+# sqrt(2), so K~ = [[1/2, 1/2], [1/2, 1/2]] up to one rounding of sqrt(2)^2.
+
+
+def test_eta0_is_one_over_the_largest_scaled_entry_by_hand():
+    """A3: eta0 = 1 / max |K~_ij| of the SCALED matrix, from the unforced start (no
+    fixed_eta; with adaptive = False the step size stays eta0, which the result reports).
+      diag(4, 16):  K~ = I                 -> eta0 = 1
+                    (1/max|K| = 1/16, 1/||K~||_F = 1/sqrt 2: both wrong)
+      ones(2, 2):   K~ = ones / 2          -> eta0 = 2
+                    (1/||K~||_2 = 1, 1/||K~||_F = 1, 1/max|K| = 1: all wrong)"""
+    fixed = dict(iter_limit=1, adaptive=False, restarts=False, terminate=False)
+    lp = _lp_from_dense([[4.0, 0.0], [0.0, 16.0]], [1.0, 1.0], "GG", [1.0, 1.0], [0.0, 0.0],
+                        [10.0, 10.0])
+    k, _, _, _ = O.canonicalize(lp)
+    dr, dc = O.ruiz_pock_chambolle(k)
+    assert dr.tolist() == [0.5, 0.25] and dc.tolist() == [0.5, 0.25]
+    assert O.solve(lp, O.Params(**fixed)).eta == 1.0
+    lp = _lp_from_dense([[1.0, 1.0], [1.0, 1.0]], [1.0, 1.0], "GG", [1.0, 1.0], [0.0, 0.0],
+                        [10.0, 10.0])
+    assert O.solve(lp, O.Params(**fixed)).eta == pytest.approx(2.0, rel=1e-15)
+
+
+def test_restart_metric_is_taken_in_scaled_space_by_hand():
+    """A9 reads KKT_w on the SCALED iterate.  min 4x s.t. 4x >= 4, x in [0, 2]: K = [4]
+    scales to K~ = [1] with D_r = D_c = 1/2 exactly, so q~ = 2, c~ = 2, u~ = 4, w0 =
+    ||c~|| / ||q~|| = 1 -- in scaled space exactly the problem of
+    test_necessary_decay_restart_by_hand (eta = 0.5, a check after every step, beta_art = 1),
+    whose restarts are [1, 0, 0, 0, 1, 0] with w = sqrt 2 after the fifth check.
+    In unscaled space r_p doubles (r_p = r_p~ / D_r) and the gap is unchanged, so the same
+    checks would read: z1 = (0, 1): sqrt(16 + 4) = 4.47 (the restart anchor); z3 (0, 3):
+    sqrt(16 + 4) = 4.47; z4 (0.5, 3.5): r_p 3, gap 0 -> 3 (<= 0.8 * 4.47 = 3.58 but below
+    the previous 4.47); z5 (1.25, 3.5): r_p 1.5, gap 1.5 -> 2.12, below the previous
+    candidate 3, so no necessary-decay restart there.  Unscaled, the returned iterate is
+    x = D_c x~, y = D_r y~."""
+    lp = _lp_from_dense([[4.0]], [4.0], "G", [4.0], [0.0], [2.0])
+    k, _, _, _ = O.canonicalize(lp)
+    assert [v.tolist() for v in O.ruiz_pock_chambolle(k)] == [[0.5], [0.5]]
+    r = O.solve(lp, O.Params(iter_limit=6, check_period=1, adaptive=False, fixed_eta=0.5,
+                             terminate=False, beta_art=1.0))
+    assert [kd for kd, _ in r.check_trace] == [1, 0, 0, 0, 1, 0] and r.restarts == 2
+    assert r.check_trace[4][1] == pytest.approx(math.sqrt(2.0), rel=1e-15)
+    # z5 = (1.25, 3.5) scaled; the restart at check 5 keeps it, step 6 from it with
+    # w = sqrt 2: x~ = 1.25 - (0.5 / sqrt 2)(2 - 3.5), y~ = 3.5 + 0.5 sqrt 2 (2 - (2 x~ - 1.25))
+    s2 = math.sqrt(2.0)
+    x6 = 1.25 - (0.5 / s2) * (2.0 - 3.5)
+    y6 = 3.5 + 0.5 * s2 * (2.0 - (2.0 * x6 - 1.25))
+    assert r.x_cur[0] == pytest.approx(0.5 * x6, rel=1e-14)
+    assert r.y_cur[0] == pytest.approx(0.5 * y6, rel=1e-14)
+
+
+def test_primal_weight_distances_are_taken_in_scaled_space_by_hand():
+    """A10 measures the distances moved since the last restart in SCALED space.
+    K = diag(4, 16) (D_r = D_c = (1/2, 1/4)), rows 4 x1 >= 0 and 16 x2 >= 8, c = (-2, 0),
+    x in [0, 0.25] x [0, 1]: scaled q~ = (0, 2), c~ = (-1, 0), u~ = (0.5, 4), so
+    w0 = ||c~|| / ||q~|| = 1/2; eta = 0.5 gives tau = eta / w = 1, sigma = eta w = 1/4.
+      step 1 from 0: x~ = proj((0, 0) + (1, 0)) = (0.5, 0) (x1 at its bound);
+                     y~ = proj_Y(0.25 ((0, 2) - (1, 0))) = (0, 0.5).
+      check 1 (artificial restart, 1 >= 0.36; average = current): dx~ = 0.5, dy~ = 0.5,
+        w1 = exp(0.5 ln(0.5 / 0.5) + 0.5 ln(1/2)) = sqrt(1/2).
+        (Unscaled distances ||D_c dx~|| = 0.25, ||D_r dy~|| = 0.125 would give w = 1/2.)
+      step 2, tau = 0.5 / w1 = sqrt(2)/2, sigma = sqrt(2)/4:
+        x~ = proj((0.5, 0) - tau ((-1, 0) - (0, 0.5))) = (0.5, sqrt(2)/4),
+        y~2 = 0.5 + sigma (2 - 2 sqrt(2)/4) = 0.25 + sqrt(2)/2, y~1 = max(0, -sigma/2) = 0.
+      Unscaled: x = D_c x~ = (0.25, sqrt(2)/16), y = D_r y~ = (0, (0.25 + sqrt(2)/2)/4)."""
+    lp = _lp_from_dense([[4.0, 0.0], [0.0, 16.0]], [0.0, 8.0], "GG", [-2.0, 0.0], [0.0, 0.0],
+                        [0.25, 1.0])
+    r1 = O.solve(lp, O.Params(iter_limit=1, check_period=1, adaptive=False, fixed_eta=0.5,
+                              terminate=False))
+    assert r1.x_cur.tolist() == [0.25, 0.0] and r1.y_cur.tolist() == [0.0, 0.125]
+    r = O.solve(lp, O.Params(iter_limit=2, check_period=1, adaptive=False, fixed_eta=0.5,
+                             terminate=False))
+    s2 = math.sqrt(2.0)
+    assert r.check_trace[0][0] == 1
+    assert r.check_trace[0][1] == pytest.approx(math.sqrt(0.5), rel=1e-15)
+    np.testing.assert_allclose(r.x_cur, [0.25, s2 / 16.0], rtol=1e-14, atol=0)
+    np.testing.assert_allclose(r.y_cur, [0.0, (0.25 + s2 / 2.0) / 4.0], rtol=1e-14, atol=0)

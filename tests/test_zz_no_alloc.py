@@ -6,8 +6,10 @@ same solve with its scratch in the library's static 64 MiB device array.  This
 file checks, through the C ABI, that two calls in a row give what
 pdlp_solve_device gives on the same inputs (to the 1e-9 parity tolerance of
 the other GPU tests), including an LP whose long columns take the device-built
-transpose path, and that a problem too large for the array is refused.
-It is named so pytest collects it last.
+transpose path and the persistent step kernel; that a call leaves the device's
+allocated and free memory unchanged; that a request for the autotuner (which
+needs its own stream, events and graphs) and a problem too large for the array
+are refused.  It is named so pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -53,14 +55,19 @@ def long_column_lp(m=6000, n=3000, seed=5):
                      np.zeros(n), np.ones(n), np.zeros(n, np.uint8), "long_columns")
 
 
-@pytest.mark.parametrize("maker,prec", [(lambda: lpgen.mip_relaxation(1), "fp64"),
-                                        (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16"),
-                                        (lambda: long_column_lp(), "fp32")])
-def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec):
+CASES = [(lambda: lpgen.mip_relaxation(1), "fp64", 0),
+         (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16", 0),
+         (lambda: long_column_lp(), "fp32", 0),
+         (lambda: lpgen.mip_relaxation(2), "fp64", 1),
+         (lambda: lpgen.set_cover(8, m=2000, n=8000), "fp32", 1)]
+
+
+@pytest.mark.parametrize("maker,prec,persistent", CASES)
+def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec, persistent):
     import torch
     lp = maker()
     d = P.DeviceLP(lp)
-    prm = P.default_params(tol=1e-6, precision=prec)
+    prm = P.default_params(tol=1e-6, precision=prec, persistent=persistent)
     assert P.workspace_size(lp.m, lp.n, lp.nnz, prm) <= P.binding.NOALLOC_BYTES
     xr, yr, rr = P.pdlp_solve_device(d, prm)
     xr, yr = xr.cpu().numpy(), yr.cpu().numpy()
@@ -74,6 +81,37 @@ def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec):
         assert rel(x.cpu().numpy(), xr) <= PARITY
         assert rel(y.cpu().numpy(), yr) <= PARITY
         assert r["rel_kkt"] == pytest.approx(rr["rel_kkt"], rel=PARITY)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_noalloc_call_leaves_device_memory_unchanged(P, persistent):
+    """The property the entry point exists for: after a first call (which may load
+    the library's module, and with it the static array), a call changes neither the
+    memory PyTorch has allocated nor the device's free memory."""
+    import torch
+    lp = lpgen.set_cover(9, m=2000, n=8000)
+    d = P.DeviceLP(lp)
+    prm = P.default_params(tol=1e-4, precision="fp32", persistent=persistent)
+    xo = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    yo = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+    P.pdlp_solve_device_noalloc(d, prm, x_out=xo, y_out=yo)
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    _, _, r = P.pdlp_solve_device_noalloc(d, prm, x_out=xo, y_out=yo)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert r["status"] == P.PDLP_OPTIMAL
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+
+
+def test_noalloc_refuses_the_autotuner(P):
+    lp = lpgen.set_cover(7, m=2000, n=8000)
+    d = P.DeviceLP(lp)
+    prm = P.default_params(tol=1e-4, precision="fp32", autotune=1)
+    with pytest.raises(P.PdlpError, match="INVALID_INPUT.*autotune"):
+        P.pdlp_solve_device_noalloc(d, prm)
 
 
 def test_noalloc_refuses_a_problem_larger_than_its_array(P):
