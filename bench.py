@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the energy, batch and 200 x 400 workloads of the default line")
     ap.add_argument("--cpu-sample-iters", type=int, default=400)
     ap.add_argument("--kernels-only", action="store_true",
                     help="only time the fused kernels (pdlp_time_kernels) and print them")
@@ -54,6 +56,9 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
                     help="1: one cooperative step kernel per check period; 0: two launches per attempt")
+    ap.add_argument("--tiles", type=int, default=0, choices=[0, 1],
+                    help="float32 steps: 1 staged tile kernels (bulk copies into shared memory); "
+                         "0 lanes-per-row kernels")
     for k in ("lanes-a", "lanes-at", "lanes-kkt-a", "lanes-kkt-at"):
         ap.add_argument("--" + k, type=int, default=0, help="SpMV lanes per row (0 = automatic)")
     return ap.parse_args()
@@ -61,7 +66,7 @@ def parse():
 
 def lane_params(args) -> dict:
     return {"lanes_A": args.lanes_a, "lanes_AT": args.lanes_at, "lanes_kkt_A": args.lanes_kkt_a,
-            "lanes_kkt_AT": args.lanes_kkt_at, "persistent": args.persistent}
+            "lanes_kkt_AT": args.lanes_kkt_at, "persistent": args.persistent, "tiles": args.tiles}
 
 
 def dist_env():
@@ -165,46 +170,74 @@ sys.path.insert(0, {root!r})
 import lpgen
 from oracle import pdlp_oracle as O
 lp = lpgen.set_cover(2025)
+start_at = {start_at!r}
+while start_at is not None and time.time() < start_at:  # replicas start together
+    time.sleep(0.001)
+w0 = time.time()
 t = time.perf_counter()
-r = O.solve(lp, O.Params(iter_limit={iters}, terminate=False, check_period=64))
+r = O.solve(lp, O.Params(iter_limit={iters}, terminate={terminate}, check_period=64, tol=1e-4))
 dt = time.perf_counter() - t
-print(json.dumps({{"iters": r.iters, "seconds": dt}}))
+print(json.dumps({{"iters": r.iters, "seconds": dt, "status": r.status, "rel_kkt": r.kkt.rel_kkt,
+                  "wall0": w0, "wall1": time.time()}}))
 """
+
+
+def _oracle_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
 
 
 def cpu_oracle_sample(iters: int) -> dict:
     """The float64 oracle, as it stands, on the full workload for a bounded number of
     iterations, single-threaded (numpy/scipy with one BLAS thread)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, iters=iters)],
-                         capture_output=True, text=True, env=env, check=True)
+    code = CPU_SNIPPET.format(root=ROOT, iters=iters, terminate=False, start_at=None)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         env=_oracle_env(), check=True)
     d = json.loads(out.stdout.strip().splitlines()[-1])
     return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{d['iters']} accepted iterations of the float64 oracle (scaling included) "
                       f"on the full workload, {d['seconds']:.1f} s"}
 
 
+def cpu_oracle_to_tolerance() -> dict:
+    """The float64 oracle, as it stands, solving the full workload to rel. KKT 1e-4 on one
+    core: its iterations per second and its time to tolerance (scaling included)."""
+    code = CPU_SNIPPET.format(root=ROOT, iters=100_000, terminate=True, start_at=None)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         env=_oracle_env(), check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "time_to_tol_s": d["seconds"], "iters": d["iters"], "status": d["status"],
+            "rel_kkt": d["rel_kkt"],
+            "sample": f"one solve of the full workload to rel. KKT 1e-4 by the float64 oracle "
+                      f"(scaling included): {d['iters']} iterations in {d['seconds']:.1f} s"}
+
+
 def cpu_oracle_all_cores(iters: int, procs: int | None = None) -> dict:
-    """The same oracle sample in one single-threaded process per host core, all at once
-    (independent replicas, as the GPU ranks are): the host's aggregate oracle throughput,
-    the sum of the processes' rates, each timed over its own solve."""
+    """The same oracle sample in one single-threaded process per host core, started
+    together (each builds the LP, then waits for a common wall-clock start): the host's
+    aggregate oracle throughput = all accepted iterations / (latest end - earliest start)."""
     if procs is None:  # the cores this process may run on, at most 32 replicas
         procs = min(32, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
                     else (os.cpu_count() or 1))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = CPU_SNIPPET.format(root=ROOT, iters=iters)
+    start_at = time.time() + 8.0 + 0.05 * procs  # time for the imports and the LP build
+    code = CPU_SNIPPET.format(root=ROOT, iters=iters, terminate=False, start_at=start_at)
     runs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
-                             stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+                             stderr=subprocess.PIPE, text=True, env=_oracle_env()) for _ in range(procs)]
     outs = []
     for r in runs:
         out, err = r.communicate()
         if r.returncode != 0:
             raise RuntimeError(f"oracle replica failed: {err.strip()[-200:]}")
         outs.append(json.loads(out.strip().splitlines()[-1]))
-    rate = sum(d["iters"] / d["seconds"] for d in outs)
+    t0 = min(d["wall0"] for d in outs)
+    t1 = max(d["wall1"] for d in outs)
+    late = max(d["wall0"] for d in outs) - t0
+    rate = sum(d["iters"] for d in outs) / (t1 - t0)
     return {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{procs} concurrent single-threaded replicas, {iters} accepted iterations "
-                      f"each on the full workload, {max(d['seconds'] for d in outs):.1f} s at most"}
+            "sample": f"{procs} single-threaded replicas started together, {iters} accepted "
+                      f"iterations each on the full workload; all iterations / "
+                      f"(latest end - earliest start) = {t1 - t0:.1f} s "
+                      f"(starts spread over {late:.2f} s)"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -326,13 +359,21 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_oracle_sample(args.cpu_sample_iters)
+            cpu = cpu_oracle_to_tolerance()
         except Exception as e:  # reported, never silently replaced
             cpu = {"error": str(e)[:200]}
         try:
             cpu["all_cores"] = cpu_oracle_all_cores(args.cpu_sample_iters)
         except Exception as e:
             cpu["all_cores"] = {"error": str(e)[:200]}
+    extra = {}
+    if rank == 0 and ws == 1 and not args.no_extra:
+        # the other workloads, one GPU each (replicas only under torchrun: rank 0 alone)
+        for key, fn in (("c1", c1_section), ("energy", energy_section), ("batch", batch_section)):
+            try:
+                extra[key] = fn(args, dev, stream, peak)
+            except Exception as e:  # reported, never silently replaced
+                extra[key] = {"error": str(e)[:300]}
     if rank == 0:
         prec_used = {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
                      3: "fp32 iterates, pattern matrix"}[res["precision_used"]]
@@ -360,9 +401,166 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ other workloads
+def kernel_roofline(kt, peak, peak_source):
+    """Roofline of the step kernels from pdlp_time_kernels: the dominant of the primal
+    step and the dual half-step, with every timed kernel's bytes, time and GB/s."""
+    kern = {k: {"us": 1e3 * v["ms"], "bytes": v["bytes"], "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                "frac": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peak}
+            for k, v in kt.items() if v["ms"] > 0}
+    dom = max(("primal_step", "dual_step"), key=lambda k: kt[k]["ms"])
+    return {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kern[dom]["frac"], "traffic": None, "peak_source": peak_source, "kernels": kern}
+
+
+def _peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path))["hbm_gbs"], "measured"
+    return 6800.0, "fallback"
+
+
+def energy_section(args, dev, stream, peak):
+    """The energy-system LP (8760 h x 20 regions x 6 technologies: 2.10M rows, 2.45M
+    columns, 7.88M nonzeros, coefficients in [0.1, 10]) to rel. KKT 1e-4 with float32
+    iterates, next to plain float64 PDLP on the same instance; inputs resident, CUDA
+    events on the stream; its step data (~0.3 GB per attempt) streams from HBM."""
+    import torch
+
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    lp = lpgen.energy_system()
+    d = P.DeviceLP(lp, device=dev)
+
+    def solves(prm, steps, warmup):
+        wbuf = torch.empty(P.workspace_size(lp.m, lp.n, lp.nnz, prm) + 256, dtype=torch.uint8,
+                           device=dev)
+        for _ in range(warmup):
+            P.pdlp_solve_device(d, prm, workspace=wbuf, stream=stream)
+        ms, res = [], None
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            _, _, res = P.pdlp_solve_device(d, prm, workspace=wbuf, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms), res
+
+    prm = P.default_params(tol=1e-4, precision="fp32", iter_limit=200_000, tiles=args.tiles)
+    with ClockSampler(dev.index) as clk:
+        ms, res = solves(prm, 2, 1)
+    ms64, res64 = solves(P.default_params(tol=1e-4, precision="fp64", iter_limit=200_000), 1, 0)
+    kt = P.time_kernels(d, prm, reps=50, stream=stream)
+    pk, src = _peak()
+    obj64 = res64["primal_obj"]
+    return {"workload": f"energy system 8760 h x 20 regions x 6 technologies, m={lp.m}, n={lp.n}, "
+                        f"nnz={lp.nnz}, tol=1e-4",
+            "precision": "fp32 iterates, fp32 matrix, fp64 KKT", "tiles": res["tiles"],
+            "time_to_tol_s": ms / 1e3, "iters": res["iters"], "iters_per_s": res["iters"] / (ms / 1e3),
+            "status": res["status"], "rel_kkt": res["rel_kkt"], "primal_obj": res["primal_obj"],
+            "setup_ms": 1e3 * res["setup_s"],
+            "fp64": {"time_to_tol_s": ms64 / 1e3, "iters": res64["iters"],
+                     "iters_per_s": res64["iters"] / (ms64 / 1e3), "status": res64["status"],
+                     "rel_kkt": res64["rel_kkt"], "primal_obj": obj64},
+            "obj_rel_diff_vs_fp64": abs(res["primal_obj"] - obj64) / (1.0 + abs(obj64)),
+            "speedup_vs_fp64_time_to_tol": ms64 / ms,
+            "roofline": kernel_roofline(kt, pk, src), "clocks": clk.summary()}
+
+
+def _batch_lps(count):
+    """lpgen.set_cover_batch(count), generated by one process per core (spawned)."""
+    import multiprocessing as mp
+
+    import lpgen
+    seeds = list(range(4000, 4000 + count))
+    ms = [int(np.random.default_rng(s).integers(2000, 40001)) for s in seeds]
+    procs = max(1, min(16, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                       else (os.cpu_count() or 1)))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.starmap(lpgen.set_cover_fixed, zip(seeds, ms), chunksize=4)
+
+
+def batch_section(args, dev, stream, peak):
+    """The batch of 256 uneven covering sub-LPs (m ~ U[2,000, 40,000], n = 4m, 10-50 % of
+    the columns fixed to 0/1; 142M nonzeros) to rel. KKT 1e-4 per LP by pdlp_solve_batch
+    from host buffers: setup and iteration phase timed apart by the library."""
+    import torch
+
+    import paper_2503_10344_gb300 as P
+
+    lps = _batch_lps(args.batch_count)
+    prm = P.default_params(tol=1e-4, precision="bf16", tiles=args.tiles)
+    P.pdlp_solve_batch(lps, prm, want_y=False)  # warm
+    walls, setup, solve, iters = [], [], [], []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(2):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            _, _, res = P.pdlp_solve_batch(lps, prm, want_y=False)
+            walls.append(time.perf_counter() - t0)
+            setup.append(res[0]["setup_s"])
+            solve.append(res[0]["solve_s"])
+            iters.append(sum(r["iters"] for r in res))
+    it = np.array([r["iters"] for r in res])
+    kt = P.time_kernels_batch(lps, prm, reps=20)
+    pk, src = _peak()
+    return {"workload": f"batch of {len(lps)} set-cover sub-LPs, sum m={sum(l.m for l in lps)}, "
+                        f"sum n={sum(l.n for l in lps)}, nnz={sum(l.nnz for l in lps)}, tol=1e-4",
+            "precision": {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
+                          3: "fp32 iterates, pattern matrix"}[res[0]["precision_used"]],
+            "tiles": res[0]["tiles"], "optimal": int(sum(r["status"] == P.PDLP_OPTIMAL for r in res)),
+            "wall_s": statistics.median(walls), "setup_s": statistics.median(setup),
+            "solve_s": statistics.median(solve), "iters_sum": iters[-1],
+            "iters_per_s": iters[-1] / solve[-1], "lps_per_s": len(lps) / statistics.median(solve),
+            "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+            "roofline": kernel_roofline(kt, pk, src), "clocks": clk.summary()}
+
+
+def c1_section(args, dev, stream, peak):
+    """The 200 x 400 MIP relaxation (seeds 1..20): float64 PDLP to rel. KKT 1e-4 and to
+    1e-8 through the host API (latency of a small LP: setup, iterations, copies), then
+    fix-and-propagate (Frac order) from the 1e-4 point with its final LP at 1e-8."""
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    rows = []
+    P.pdlp_solve(lpgen.mip_relaxation(1), P.default_params(tol=1e-4))  # warm
+    for seed in range(1, 21):
+        lp = lpgen.mip_relaxation(seed)
+        out = {"seed": seed}
+        for tol in (1e-4, 1e-8):
+            t0 = time.perf_counter()
+            x, y, r = P.pdlp_solve(lp, P.default_params(tol=tol))
+            out[f"{tol:g}"] = {"wall_s": time.perf_counter() - t0, "solve_s": r["solve_s"],
+                               "setup_s": r["setup_s"], "iters": r["iters"], "status": r["status"],
+                               "rel_kkt": r["rel_kkt"], "obj": r["primal_obj"]}
+            if tol == 1e-4:
+                x4, y4 = x, y
+        t0 = time.perf_counter()
+        xf, f = P.fp_run(lp, x4, y4, strategy="frac", final_lp=True, final_lp_tol=1e-8)
+        out["fp"] = {"wall_s": time.perf_counter() - t0, "status": f["status"], "obj": f["obj"],
+                     "nodes": f["nodes"], "search_s": f["search_s"], "final_lp_s": f["lp_s"]}
+        rows.append(out)
+    med = lambda key, tol: float(np.median([r[tol][key] for r in rows]))
+    feas = [r for r in rows if r["fp"]["status"] == P.FP_FEASIBLE]
+    return {"workload": "mip_relaxation m=200 n=400 seeds 1..20 (float64)",
+            "time_to_1e-4_s": {"median_wall": med("wall_s", "0.0001"), "median_solve": med("solve_s", "0.0001")},
+            "time_to_1e-8_s": {"median_wall": med("wall_s", "1e-08"), "median_solve": med("solve_s", "1e-08")},
+            "iters_1e-4_median": med("iters", "0.0001"), "iters_1e-8_median": med("iters", "1e-08"),
+            "optimal": int(sum(r[t]["status"] == P.PDLP_OPTIMAL for r in rows for t in ("0.0001", "1e-08"))),
+            "fp_run": {"feasible": len(feas), "median_wall_s": float(np.median([r["fp"]["wall_s"] for r in rows])),
+                       "median_gap_to_lp": float(np.median([(r["fp"]["obj"] - r["1e-08"]["obj"]) /
+                                                            max(1.0, abs(r["fp"]["obj"])) for r in feas]))
+                       if feas else None}}
 
 
 def run_kernels_only(args):

@@ -153,6 +153,15 @@ typedef struct {
                            mode, 2^23 otherwise) runs out; the kernel records the failure
                            and returns, and the call returns PDLP_ERR_TIMEOUT with the
                            device context intact */
+  int tiles;            /* float32 iterates (PDLP_FP32, PDLP_FP32_BF16A): 1 runs the
+                           step attempts with the staged tile kernels -- each block streams
+                           work items of at most 256 rows and 1280 nonzeros (rows longer
+                           than 256 entries in slices) into shared memory with bulk copies,
+                           gathers from the staged indices and sums each row in storage
+                           order; 0 (default) uses the lanes-per-row kernels (lanes_A,
+                           lanes_AT).
+                           Same iteration either way; float32 sums differ in rounding.
+                           Ignored in float64 and with persistent = 1. */
 } pdlp_params;
 
 typedef struct {
@@ -174,6 +183,7 @@ typedef struct {
   double ray_obj;         /* certificate statuses: d^ (PRIMAL_INFEASIBLE) or c^T x^
                              (DUAL_INFEASIBLE); NaN otherwise */
   double ray_res;         /* the 2-norm of the certificate's residual; NaN otherwise */
+  int tiles;              /* 1 if the staged tile step kernels ran (pdlp_params.tiles) */
 } pdlp_result;
 
 /* Optional diagnostic outputs (same memory space as the entry point's outputs;

@@ -494,3 +494,85 @@ def random_sparse_lp(seed: int, m: int, n: int, density: float = 0.05, free_frac
     c = atw + rc
     return _lp(m, n, rows, cols, vals, b, sense, c, l, u, np.zeros(n, dtype=np.uint8),
                f"random_sparse_lp(seed={seed},m={m},n={n})")
+
+
+# --------------------------------------------------------------------------
+# Structured parity cases: skewed rows and columns, long and very short rows
+# --------------------------------------------------------------------------
+def skewed_lp(seed: int = 3, m: int = 6000, n: int = 3000) -> LP:
+    """Random LP with a dense row (n nnz), a column in every row (m nnz), a column in
+    2/3 of the rows, and a sparse remainder; mixed senses, some infinite bounds;
+    feasible by construction."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    rows.append(np.zeros(n, dtype=np.int64)); cols.append(np.arange(n))
+    rows.append(np.arange(1, m)); cols.append(np.zeros(m - 1, dtype=np.int64))
+    r2 = np.arange(1, m)[rng.random(m - 1) < 0.66]
+    rows.append(r2); cols.append(np.ones(r2.size, dtype=np.int64))
+    mask = rng.random((m, n)) < 0.002
+    mask[0, :] = False
+    mask[:, :2] = False
+    rr, cc = np.nonzero(mask)
+    rows.append(rr); cols.append(cc)
+    rows = np.concatenate(rows); cols = np.concatenate(cols)
+    vals = rng.uniform(0.5, 2.0, size=rows.size) * np.where(rng.random(rows.size) < 0.3, -1, 1)
+    l = np.zeros(n); u = rng.uniform(1, 3, size=n)
+    u[rng.random(n) < 0.1] = np.inf
+    x0 = rng.random(n) * np.where(np.isfinite(u), u, 1.0)
+    ax0 = np.zeros(m)
+    np.add.at(ax0, rows, vals * x0[cols])
+    sense = np.where(rng.random(m) < 0.5, SENSE_LE, SENSE_GE).astype(np.uint8)
+    sense[rng.random(m) < 0.1] = SENSE_EQ
+    slack = rng.uniform(0, 1, size=m)
+    b = np.where(sense == SENSE_LE, ax0 + slack, np.where(sense == SENSE_GE, ax0 - slack, ax0))
+    c = rng.uniform(0.1, 1.0, size=n)
+    return _lp(m, n, rows, cols, vals, b, sense, c, l, u, np.zeros(n, np.uint8), "skewed")
+
+
+def long_rows_lp(m: int = 6500, n: int = 3000, seed: int = 5) -> LP:
+    """Covering-type LP with long rows and columns: column 0 in every row, column 1
+    in two thirds of the rows, row 7 with over 900 entries, a sparse remainder;
+    feasible (column 0 alone covers every row)."""
+    rng = np.random.default_rng(seed)
+    rows = [np.arange(m), np.arange(m)[rng.random(m) < 0.66], np.full(900, 7)]
+    cols = [np.zeros(m, dtype=np.int64), np.ones(rows[1].size, dtype=np.int64),
+            2 + rng.choice(n - 2, size=900, replace=False)]
+    mask = rng.random((m, n)) < 0.002
+    mask[:, :2] = False
+    mask[7, :] = False
+    rr, cc = np.nonzero(mask)
+    rows.append(rr)
+    cols.append(cc)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = rng.uniform(0.5, 2.0, size=rows.size)
+    vals[:m] = rng.uniform(1.0, 2.0, size=m)
+    return _lp(m, n, rows, cols, vals, np.ones(m), np.full(m, SENSE_GE, dtype=np.uint8),
+               rng.uniform(1, 10, size=n), np.zeros(n), np.ones(n), np.zeros(n, np.uint8),
+               "long_rows")
+
+
+def short_rows_lp(m: int = 3000, n: int = 40000, seed: int = 9) -> LP:
+    """Covering LP whose columns have one or two entries (A^T has very short rows);
+    all values 1, costs U{1..100}; every row covered."""
+    rng = np.random.default_rng(seed)
+    cols = np.arange(n)
+    rows = rng.integers(0, m, size=n)
+    extra = rng.random(n) < 0.3
+    rows2 = rng.integers(0, m, size=int(extra.sum()))
+    r = np.concatenate([rows, rows2])
+    c = np.concatenate([cols, cols[extra]])
+    key = r.astype(np.int64) * n + c
+    _, keep = np.unique(key, return_index=True)
+    r, c = r[keep], c[keep]
+    cover = np.zeros(m, bool)
+    cover[r] = True
+    miss = np.nonzero(~cover)[0]
+    r = np.concatenate([r, miss])
+    c = np.concatenate([c, rng.integers(0, n, size=miss.size)])
+    key = r.astype(np.int64) * n + c
+    _, keep = np.unique(key, return_index=True)
+    r, c = r[keep], c[keep]
+    return _lp(m, n, r, c, np.ones(r.size), np.ones(m), np.full(m, SENSE_GE, dtype=np.uint8),
+               rng.integers(1, 101, n).astype(float), np.zeros(n), np.ones(n),
+               np.zeros(n, np.uint8), "short_rows")

@@ -41,7 +41,8 @@ class PdlpParams(C.Structure):
                 ("terminate", C.c_int), ("lanes_A", C.c_int), ("lanes_AT", C.c_int),
                 ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int),
                 ("persistent", C.c_int), ("autotune", C.c_int),
-                ("detect_infeasibility", C.c_int), ("debug_skip_barrier", C.c_int)]
+                ("detect_infeasibility", C.c_int), ("debug_skip_barrier", C.c_int),
+                ("tiles", C.c_int)]
 
 
 class PdlpResult(C.Structure):
@@ -52,7 +53,8 @@ class PdlpResult(C.Structure):
                 ("rel_dual_res", C.c_double), ("rel_gap", C.c_double), ("rel_kkt", C.c_double),
                 ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("lanes_A", C.c_int),
-                ("lanes_AT", C.c_int), ("ray_obj", C.c_double), ("ray_res", C.c_double)]
+                ("lanes_AT", C.c_int), ("ray_obj", C.c_double), ("ray_res", C.c_double),
+                ("tiles", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -165,6 +165,37 @@ __device__ __forceinline__ Span make_span(const Tables& t, int nrows1, int nshor
   return s;
 }
 
+// ---------------------------------------------------------------- tiles
+// Work items of the staged tile step kernels (tile_kernels.cuh), built at setup
+// (setup_tiles).  A tile is a run of at most kTileRows consecutive rows of at
+// most kLongRow entries whose nonzeros start inside one window of W entries
+// (kTileWindowMin <= W <= kTileWindowMax); a longer row is cut into slices of at
+// most W entries.  No item straddles two LPs of a batch.
+constexpr int kTileRows = kBlock;
+constexpr int kLongRow = 256;
+constexpr int kTileWindowMin = 256;
+constexpr int kTileWindowMax = 1024;
+
+// One work item (32 bytes).  Tile: rows [r0, r1), nonzeros [nb, ne), first = -1.
+// Slice: row r0 (r1 = r0 + 1), nonzeros [nb, ne) of it, first = index of the row's
+// first slice, nsl = slices of the row, lid = the row's long-row slot.
+struct TileItem {
+  int r0, r1, nb, ne;
+  int lp, first, nsl, lid;
+};
+
+// Item tables of one orientation and the slots the kernels write.
+struct TileSet {
+  const TileItem* item;  // [n]
+  int n;                 // items
+  const int* item0;      // [count + 1] first item of each LP
+  const int* lng0;       // [count + 1] first long-row slot of each LP
+  float2* part;          // [n] per-(block, LP) partial sums, in the slot of the run's first item
+  float2* rowpart;       // [n] a slice's partial row sum(s)
+  float2* lterm;         // [long rows] a finished long row's partial-sum terms
+  int* ticket;           // [n] slices done, in the slot of a row's first slice (0 between launches)
+};
+
 // ---------------------------------------------------------------- dependent launch
 // Programmatic dependent launch: kernels of the iteration chain are launched
 // with the programmatic-serialization attribute, so the next kernel's blocks

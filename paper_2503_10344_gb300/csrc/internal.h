@@ -31,6 +31,10 @@ struct IterRaw {
   unsigned long long cond;  // while-loop handle of the check-period graph (0: none)
   int loop_cap;             // attempts per graph launch at most (with cond)
   Tables tp, td; // batch tables over A^T and A (all NULL for one LP)
+  // staged tile step kernels (float32 iterates; tile_kernels.cuh): 1 = on
+  int tile;
+  TileSet tt, ta;        // items over A^T (primal step) and over A (dual step)
+  int grid_tt, grid_ta;  // their grids (k_decide reads one partial slot per block and LP)
 };
 
 // IK_DUAL launches the dual step kernel and then the step decision (k_decide)
@@ -45,6 +49,11 @@ cudaError_t launch_persist_bf16(int lanes_a, int lanes_t, const IterRaw& r, int 
                                 int grid, int* grid_out, cudaStream_t s);
 cudaError_t launch_persist_pat(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
                                int grid, int* grid_out, cudaStream_t s);
+
+// blocks of the staged tile kernels (primal, dual) resident at once on this device
+cudaError_t tile_resident_fp32(int* primal_blocks, int* dual_blocks);
+cudaError_t tile_resident_bf16(int* primal_blocks, int* dual_blocks);
+cudaError_t tile_resident_pat(int* primal_blocks, int* dual_blocks);
 
 cudaError_t launch_iter_fp64(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_t s);
@@ -117,6 +126,22 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)block);
   cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+// the same with `smem` bytes of dynamic shared memory
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl_smem(void (*kernel)(KArgs...), int grid, int block, int smem, cudaStream_t s,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

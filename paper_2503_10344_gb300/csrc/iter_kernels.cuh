@@ -83,6 +83,9 @@ struct IterData {
   unsigned long long cond;                             // while-loop handle of the graph (0: none)
   int loop_cap;                                        // attempts per graph launch at most
   Tables tp, td;                                       // batch tables over A^T / A (NULL: one LP)
+  int tile;                                            // staged tile kernels (float32 only)
+  TileSet tt, ta;                                      // their items over A^T and A
+  int grid_tt, grid_ta;
 };
 
 // Rows of one LP (span), one aligned group of LANES lanes per row, rows
@@ -561,10 +564,29 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
     return;
   }
   T a = 0, b0 = 0, b1 = 0;
-  for (int i = threadIdx.x; i < pn; i += kBlock) a += d.part_p[p0 + i];
-  for (int i = threadIdx.x; i < qn; i += kBlock) {
-    b0 += d.part_d[q0 + i];
-    b1 += d.part_d[d.grid_d + q0 + i];
+  if (std::is_same<T, float>::value && d.tile) {
+    // tile kernels: one slot per (block, LP) run -- the LP's first min(items, grid)
+    // item slots -- and one per long row
+    const int i0 = d.tt.item0[k], i1 = min(d.tt.item0[k + 1], i0 + d.grid_tt);
+    for (int i = i0 + threadIdx.x; i < i1; i += kBlock) a += (T)d.tt.part[i].x;
+    for (int i = d.tt.lng0[k] + threadIdx.x; i < d.tt.lng0[k + 1]; i += kBlock) a += (T)d.tt.lterm[i].x;
+    const int j0 = d.ta.item0[k], j1 = min(d.ta.item0[k + 1], j0 + d.grid_ta);
+    for (int i = j0 + threadIdx.x; i < j1; i += kBlock) {
+      const float2 v = d.ta.part[i];
+      b0 += (T)v.x;
+      b1 += (T)v.y;
+    }
+    for (int i = d.ta.lng0[k] + threadIdx.x; i < d.ta.lng0[k + 1]; i += kBlock) {
+      const float2 v = d.ta.lterm[i];
+      b0 += (T)v.x;
+      b1 += (T)v.y;
+    }
+  } else {
+    for (int i = threadIdx.x; i < pn; i += kBlock) a += d.part_p[p0 + i];
+    for (int i = threadIdx.x; i < qn; i += kBlock) {
+      b0 += d.part_d[q0 + i];
+      b1 += d.part_d[d.grid_d + q0 + i];
+    }
   }
   block_sum3<T>(a, b0, b1);
   if (threadIdx.x == 0) {

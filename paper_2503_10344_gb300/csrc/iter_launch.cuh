@@ -6,6 +6,7 @@
 
 #include "internal.h"
 #include "iter_kernels.cuh"
+#include "tile_kernels.cuh"
 
 namespace pdlp {
 
@@ -33,6 +34,11 @@ IterData<T, V> typed(const IterRaw& r) {
   d.loop_cap = r.loop_cap;
   d.tp = r.tp;
   d.td = r.td;
+  d.tile = r.tile;
+  d.tt = r.tt;
+  d.ta = r.ta;
+  d.grid_tt = r.grid_tt;
+  d.grid_ta = r.grid_ta;
   return d;
 }
 
@@ -67,9 +73,41 @@ cudaError_t launch_one(int which, const IterData<T, V>& d, cudaStream_t s) {
   }
 }
 
+// The staged tile kernel of one orientation (kTileStages stages of dynamic shared
+// memory, allowed for the device by tile_resident during the setup).
+template <typename V, bool IMPLICIT, bool DUAL>
+cudaError_t launch_tile(const IterData<float, V>& d, cudaStream_t s) {
+  const int smem = kTileStages * StageLayout<V, DUAL>::bytes;
+  return launch_pdl_smem(k_tile<V, IMPLICIT, DUAL>, DUAL ? d.grid_ta : d.grid_tt, kBlock, smem, s, d);
+}
+
+// Blocks of the tile kernel of one orientation that fit on the device at once; also
+// allows the kernel its dynamic shared memory on the current device.
+template <typename V, bool IMPLICIT, bool DUAL>
+cudaError_t tile_resident(int* blocks) {
+  auto kern = k_tile<V, IMPLICIT, DUAL>;
+  const int smem = kTileStages * StageLayout<V, DUAL>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
+  if (e != cudaSuccess) return e;
+  *blocks = std::max(1, per_sm) * device_sm_count();
+  return cudaSuccess;
+}
+
 template <typename T, typename V, bool IMPLICIT>
 cudaError_t launch_iter_t(int which, int lanes, const IterRaw& r, cudaStream_t s) {
   const IterData<T, V> d = typed<T, V>(r);
+  if constexpr (std::is_same<T, float>::value) {
+    if (r.tile) {
+      if (which == IK_PRIMAL) return launch_tile<V, IMPLICIT, false>(d, s);
+      if (which != IK_DUAL) return cudaErrorInvalidValue;
+      const cudaError_t e = launch_tile<V, IMPLICIT, true>(d, s);
+      if (e != cudaSuccess) return e;
+      return launch_pdl(k_decide<T, V>, d.count, kBlock, s, d);
+    }
+  }
   switch (lanes) {
     case 2: return launch_one<2, T, V, IMPLICIT>(which, d, s);
     case 4: return launch_one<4, T, V, IMPLICIT>(which, d, s);

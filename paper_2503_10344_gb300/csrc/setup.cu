@@ -871,4 +871,127 @@ cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, i
   return cudaStreamSynchronize(s);
 }
 
+// ------------------------------------------------------------------ tile items
+namespace {
+
+// cnt[r] = work items that start at row r (0: row r continues the tile before it);
+// lfl[r] = 1 if row r is long.  A row starts an item if it is the first row, a
+// multiple of kTileRows, long, follows a long row, or starts in another window of
+// W nonzeros than the row before it.
+__global__ void k_tile_count(const int* ptr, int R, int W, int* cnt, int* lfl) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride) {
+    const int r = (int)i;
+    const int s = ptr[r], e = ptr[r + 1];
+    const bool lng = e - s > kLongRow;
+    bool start = r == 0 || r % kTileRows == 0 || lng;
+    if (!start) {
+      const int sp = ptr[r - 1];
+      start = s / W != sp / W || s - sp > kLongRow;
+    }
+    cnt[r] = start ? (lng ? (e - s + W - 1) / W : 1) : 0;
+    lfl[r] = lng ? 1 : 0;
+  }
+}
+
+// the first row of every LP of a batch starts an item
+__global__ void k_tile_lp_starts(const int* lp_row0, int count, int R, int* cnt) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    const int r = lp_row0[k];
+    if (r < R && cnt[r] == 0) cnt[r] = 1;
+  }
+}
+
+__device__ int lp_of_row(const int* lp_row0, int count, int r) {
+  // the last LP whose first row is <= r (empty LPs share their first row with the next)
+  int lo = 0, hi = count;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (lp_row0[mid] <= r) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_tile_emit(const int* ptr, int R, int W, const int* lp_row0, int count,
+                            const int* cnt, const int* off, const int* loff, TileItem* items) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride) {
+    const int r = (int)i;
+    const int c = cnt[r];
+    if (c == 0) continue;
+    const int lp = lp_row0 ? lp_of_row(lp_row0, count, r) : 0;
+    const int s = ptr[r], e = ptr[r + 1], i0 = off[r];
+    if (e - s > kLongRow) {
+      for (int t = 0; t < c; ++t)
+        items[i0 + t] = TileItem{r, r + 1, s + t * W, (int)min((long long)s + (long long)(t + 1) * W,
+                                                               (long long)e), lp, i0, c, loff[r]};
+    } else {
+      int re = r + 1;
+      while (re < R && cnt[re] == 0) ++re;
+      items[i0] = TileItem{r, re, s, ptr[re], lp, -1, 0, -1};
+    }
+  }
+}
+
+__global__ void k_tile_lp_ranges(const int* lp_row0, int count, int R, const int* off,
+                                 const int* loff, int* item0, int* lng0) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= count; k += gridDim.x * blockDim.x) {
+    const int r = k == count ? R : (lp_row0 ? lp_row0[k] : 0);
+    item0[k] = off[r];
+    lng0[k] = loff[r];
+  }
+}
+
+}  // namespace
+
+int tile_window(int R, long long nnz) {
+  const double avg = R > 0 ? (double)nnz / (double)R : 1.0;
+  const double w = (double)kTileRows * avg;
+  return (int)std::max((double)kTileWindowMin, std::min((double)kTileWindowMax, w));
+}
+
+size_t tile_item_cap(int R, long long nnz, int count) {
+  // starts: multiples of kTileRows, window crossings (W >= kTileWindowMin), the rows at
+  // and after each long row, LP starts; plus the slices of the long rows
+  return (size_t)R / kTileRows + 5 * (size_t)(nnz / kTileWindowMin) + (size_t)count + 8;
+}
+
+size_t tile_tmp_ints(int R) { return 4 * ((size_t)R + 1) + scan_tmp_ints((long long)R + 1) + 8; }
+
+cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0, int count,
+                        int* tmp, TileItem* items, int* item0, int* lng0, int* ticket,
+                        size_t item_cap, int* h_counts, int* W_out, cudaStream_t s) {
+  const int W = tile_window(R, nnz);
+  *W_out = W;
+  int* cnt = tmp;
+  int* off = cnt + (R + 1);
+  int* lfl = off + (R + 1);
+  int* loff = lfl + (R + 1);
+  int* bsum = loff + (R + 1);
+  const int G = device_sm_count() * 8;
+  if (R > 0) {
+    k_tile_count<<<grid_for(R, G), kBlock, 0, s>>>(ptr, R, W, cnt, lfl);
+    RET(cudaGetLastError());
+    if (lp_row0 && count > 1) {
+      k_tile_lp_starts<<<grid_for(count, G), kBlock, 0, s>>>(lp_row0, count, R, cnt);
+      RET(cudaGetLastError());
+    }
+  }
+  RET(exclusive_scan(cnt, off, R, bsum, s));
+  RET(exclusive_scan(lfl, loff, R, bsum, s));
+  RET(cudaMemcpyAsync(h_counts, off + R, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RET(cudaMemcpyAsync(h_counts + 1, loff + R, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RET(cudaStreamSynchronize(s));
+  if ((size_t)h_counts[0] > item_cap) return cudaErrorInvalidValue;
+  if (R > 0) {
+    k_tile_emit<<<grid_for(R, G), kBlock, 0, s>>>(ptr, R, W, lp_row0, count, cnt, off, loff, items);
+    RET(cudaGetLastError());
+  }
+  k_tile_lp_ranges<<<grid_for(count + 1, G), kBlock, 0, s>>>(lp_row0, count, R, off, loff, item0,
+                                                              lng0);
+  RET(cudaGetLastError());
+  if (h_counts[0] > 0) RET(cudaMemsetAsync(ticket, 0, sizeof(int) * (size_t)h_counts[0], s));
+  return cudaSuccess;
+}
+
 }  // namespace pdlp

@@ -75,4 +75,17 @@ cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, cons
 cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, int* pos, int* bsum,
                             int* list, int* h_count, cudaStream_t s);
 
+// Work items of the staged tile step kernels over one orientation of a matrix with
+// R rows (int32 row pointers ptr[R + 1], global numbering for a batch): items[],
+// per-LP first item item0[count + 1] and first long-row slot lng0[count + 1]
+// (lp_row0[count]: each LP's first row, NULL for one LP), tickets zeroed.
+// h_counts[0] = items, h_counts[1] = long rows (read back; the stream is
+// synchronised).  cudaErrorInvalidValue if the items exceed item_cap.
+int tile_window(int R, long long nnz);
+size_t tile_item_cap(int R, long long nnz, int count);
+size_t tile_tmp_ints(int R);
+cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0, int count,
+                        int* tmp, TileItem* items, int* item0, int* lng0, int* ticket,
+                        size_t item_cap, int* h_counts, int* W_out, cudaStream_t s);
+
 }  // namespace pdlp

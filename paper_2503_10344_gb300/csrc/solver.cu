@@ -93,6 +93,11 @@ struct Bufs {
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
   int *a_long, *t_long, *tmp, *flags2;
   DevState* st;
+  // staged tile kernels (float32 iterates): items over A (dual step) and A^T (primal)
+  TileItem *ti_a, *ti_t;
+  float2 *tpart_a, *tpart_t, *trow_a, *trow_t, *tlong_a, *tlong_t;
+  int *tick_a, *tick_t, *tlp_a, *tlp_t;  // tickets; [item0[0..count], lng0[0..count]]
+  size_t tcap_a, tcap_t;
 };
 
 constexpr int kMaxLongBlocks = 1024;
@@ -160,9 +165,24 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.t_long = (int*)ar.take(4 * (N + 1));
   const size_t tmp_ints = std::max(transpose_tmp_ints(m, n, nnz),
                                    2 * (std::max(M, N) + 1) + scan_tmp_ints((long long)std::max(M, N) + 1));
-  b.tmp = (int*)ar.take(4 * tmp_ints);
   b.flags2 = (int*)ar.take(16);
   b.st = (DevState*)ar.take(sizeof(DevState));
+  b.tcap_a = b.tcap_t = 0;
+  size_t tile_tmp = 0;
+  if (precision != PDLP_FP64) {
+    b.tcap_a = tile_item_cap(m, nnz, 1);
+    b.tcap_t = tile_item_cap(n, nnz, 1);
+    b.ti_a = (TileItem*)ar.take(sizeof(TileItem) * b.tcap_a);
+    b.ti_t = (TileItem*)ar.take(sizeof(TileItem) * b.tcap_t);
+    for (float2** v : {&b.tpart_a, &b.trow_a, &b.tlong_a}) *v = (float2*)ar.take(8 * b.tcap_a);
+    for (float2** v : {&b.tpart_t, &b.trow_t, &b.tlong_t}) *v = (float2*)ar.take(8 * b.tcap_t);
+    b.tick_a = (int*)ar.take(4 * b.tcap_a);
+    b.tick_t = (int*)ar.take(4 * b.tcap_t);
+    b.tlp_a = (int*)ar.take(4 * 4);
+    b.tlp_t = (int*)ar.take(4 * 4);
+    tile_tmp = tile_tmp_ints(std::max(m, n));
+  }
+  b.tmp = (int*)ar.take(4 * std::max(tmp_ints, tile_tmp));
   return ar.off + 256;
 }
 
@@ -179,6 +199,24 @@ static int auto_lanes(double avg_len, double per_lane) {
 static int long_thresh(int lanes) { return std::max(1024, 128 * lanes); }
 
 static bool valid_lanes(int l) { return l == 2 || l == 4 || l == 8 || l == 16 || l == 32; }
+
+// Grid of a staged tile kernel over `items` work items with at most `resident`
+// blocks at once: every block gets the same number of items, give or take one
+// (ceil(items / blocks) rounds for all), in one wave.
+static int tile_grid(int items, int resident) {
+  if (items <= 0) return 1;
+  const int rounds = (items + resident - 1) / resident;
+  return (items + rounds - 1) / rounds;
+}
+
+static cudaError_t tile_resident_mode(Mode mode, int* bp, int* bd) {
+  switch (mode) {
+    case MODE_FP32: return tile_resident_fp32(bp, bd);
+    case MODE_BF16: return tile_resident_bf16(bp, bd);
+    case MODE_PAT: return tile_resident_pat(bp, bd);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 // ---------------------------------------------------------------- solver
 struct Solve {
@@ -298,6 +336,7 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
     return fail(PDLP_ERR_INVALID_INPUT, "persistent must be 0 or 1");
   if (p->autotune != 0 && p->autotune != 1)
     return fail(PDLP_ERR_INVALID_INPUT, "autotune must be 0 or 1");
+  if (p->tiles != 0 && p->tiles != 1) return fail(PDLP_ERR_INVALID_INPUT, "tiles must be 0 or 1");
   if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)) ||
       (p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
       (p->lanes_kkt_AT && !valid_lanes(p->lanes_kkt_AT)))
@@ -324,6 +363,7 @@ struct SetupOut {
   double sca[8];  // ||c~||, ||q~||, ||c||, ||q||, max |K~|, ||x~_hint||, ||y~_hint||,
                   // columns with an infinite bound
   int lanes_a, lanes_t, lanes_ka, lanes_kt, th_a, th_t, nlong_a, nlong_t;
+  int tiles, n_ta, n_tt;  // staged tile kernels built; their items over A and A^T
 };
 
 // Validation, canonical form, transpose, value format, scaling, iteration-space
@@ -335,7 +375,8 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
                     const double* y0, Bufs& bf, cudaStream_t s, bool no_alloc, int forced_mode,
                     const int* forced_lanes, SetupOut* so, const double* hx = nullptr,
                     const double* hy = nullptr,
-                    const std::function<void(const char*)>& mark = [](const char*) {}) {
+                    const std::function<void(const char*)>& mark = [](const char*) {},
+                    bool build_tiles = true) {
   const int m = A->m, n = A->n;
   const long long nnz = A->nnz;
   // ---- validation (A0 preconditions)
@@ -422,6 +463,20 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
     if (m > 0) CUDA_TRY(setup_long_rows(bf.a_ptr, m, th_a, flags, pos, bsum, bf.a_long, &nlong_a, s));
     CUDA_TRY(setup_long_rows(bf.t_ptr, n, th_t, flags, pos, bsum, bf.t_long, &nlong_t, s));
     g_launches += 10;
+  }
+  // work items of the staged tile kernels (float32 iterates)
+  so->tiles = 0;
+  so->n_ta = so->n_tt = 0;
+  if (build_tiles && fp32 && p->tiles && !p->persistent && bf.tcap_t > 0) {
+    int cnt[2] = {0, 0}, W = 0;
+    CUDA_TRY(setup_tiles(bf.a_ptr, m, nnz, nullptr, 1, bf.tmp, bf.ti_a, bf.tlp_a, bf.tlp_a + 2,
+                         bf.tick_a, bf.tcap_a, cnt, &W, s));
+    so->n_ta = cnt[0];
+    CUDA_TRY(setup_tiles(bf.t_ptr, n, nnz, nullptr, 1, bf.tmp, bf.ti_t, bf.tlp_t, bf.tlp_t + 2,
+                         bf.tick_t, bf.tcap_t, cnt, &W, s));
+    so->n_tt = cnt[0];
+    so->tiles = 1;
+    g_launches += 14;
   }
   CUDA_TRY(cudaStreamSynchronize(s));  // scalars
   so->mode = mode;
@@ -706,6 +761,15 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   ir.grid_p_short = gp_short; ir.grid_p = gp; ir.grid_d_short = gd_short; ir.grid_d = gd;
   ir.st = bf.st;
   ir.count = 1;
+  if (so.tiles) {
+    int bp = 0, bd = 0;
+    CUDA_TRY(tile_resident_mode(mode, &bp, &bd));
+    ir.tile = 1;
+    ir.tt = TileSet{bf.ti_t, so.n_tt, bf.tlp_t, bf.tlp_t + 2, bf.tpart_t, bf.trow_t, bf.tlong_t, bf.tick_t};
+    ir.ta = TileSet{bf.ti_a, so.n_ta, bf.tlp_a, bf.tlp_a + 2, bf.tpart_a, bf.trow_a, bf.tlong_a, bf.tick_a};
+    ir.grid_tt = tile_grid(so.n_tt, bp);
+    ir.grid_ta = tile_grid(so.n_ta, bd);
+  }
 
   KktRaw kr{};
   kr.count = 1;
@@ -795,8 +859,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   if (m) CUDA_TRY(cudaMemsetAsync(bf.Yl, 0, 8 * (size_t)m, s));
 
   Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s, 0};
-  // the autotuner creates a stream, events and graphs: never without allocation
-  if (p->autotune && !no_alloc && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
+  // the autotuner creates a stream, events and graphs: never without allocation; the
+  // staged tile kernels have no lanes to tune
+  if (p->autotune && !no_alloc && !so.tiles && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
     auto set_grids = [&](int lt, int la) -> int {
       const int gps = tiled ? gp_short : grid_for(((long long)n + 1) / 2 * lt, MBp);
       const int gds = tiled ? gd_short : grid_for(((long long)std::max(m, 1) + 1) / 2 * la, MBd);
@@ -1048,7 +1113,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   }
 
   if (fs.status == kStatusWaitFailed)
-    return fail(PDLP_ERR_TIMEOUT, "a grid barrier wait of the persistent step kernel gave up");
+    return fail(PDLP_ERR_TIMEOUT,
+                "a bounded wait of a step kernel gave up (a grid barrier of the persistent kernel "
+                "or a staged copy of the tile kernels)");
   r->status = p->iter_limit == 0 ? PDLP_ITER_LIMIT : fs.status;
   r->precision_used = mode == MODE_FP64 ? PDLP_FP64
                       : mode == MODE_FP32 ? PDLP_FP32
@@ -1056,6 +1123,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
                                           : PDLP_USED_PATTERN;
   r->lanes_A = sv.lanes_a;
   r->lanes_AT = sv.lanes_t;
+  r->tiles = sv.ir.tile;
   r->iters = fs.iters;
   r->attempts = fs.attempts;
   r->restarts = fs.restarts;
@@ -1357,7 +1425,14 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     unsigned char *row_kind, *bflags;
     DevState* st;
     FacTable* fac;
+    // staged tile kernels over the block-diagonal A and A^T
+    TileItem *ti_a, *ti_t;
+    float2 *tpart_a, *tpart_t, *trow_a, *trow_t, *tlong_a, *tlong_t;
+    int *tick_a, *tick_t, *tlp_a, *tlp_t, *row0_a, *row0_t, *ttmp;
   } g{};
+  const bool use_tiles = mode != MODE_FP64 && p->tiles && !p->persistent;
+  const size_t tcap_a = use_tiles ? tile_item_cap((int)M, Z, count) : 0;
+  const size_t tcap_t = use_tiles ? tile_item_cap((int)N, Z, count) : 0;
   // long rows and launch maps need the per-LP setups first: upper bounds here
   const int MB = max_blocks();
   const int budget = 4 * MB;
@@ -1394,6 +1469,17 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.tabA = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.tabT = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.st = (DevState*)ar.take(sizeof(DevState) * count);
+    if (use_tiles) {
+      g.ti_a = (TileItem*)ar.take(sizeof(TileItem) * tcap_a);
+      g.ti_t = (TileItem*)ar.take(sizeof(TileItem) * tcap_t);
+      for (float2** v : {&g.tpart_a, &g.trow_a, &g.tlong_a}) *v = (float2*)ar.take(8 * tcap_a);
+      for (float2** v : {&g.tpart_t, &g.trow_t, &g.tlong_t}) *v = (float2*)ar.take(8 * tcap_t);
+      g.tick_a = (int*)ar.take(4 * tcap_a);
+      g.tick_t = (int*)ar.take(4 * tcap_t);
+      for (int** v : {&g.tlp_a, &g.tlp_t}) *v = (int*)ar.take(4 * 2 * ((size_t)count + 1));
+      for (int** v : {&g.row0_a, &g.row0_t}) *v = (int*)ar.take(4 * ((size_t)count + 1));
+      g.ttmp = (int*)ar.take(4 * tile_tmp_ints((int)std::max(M, N)));
+    }
     one.fac = nullptr;
   };
   Arena gdry{nullptr, 0};
@@ -1455,7 +1541,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     SetupOut so;
     {
       const int rc = setup_lp(&dA, d_b, d_sense, d_c, d_l, d_u, p, nullptr, nullptr, one, s, false,
-                              mode, lanes, &so);
+                              mode, lanes, &so, nullptr, nullptr, [](const char*) {}, false);
       if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
     }
     th_a = so.th_a;
@@ -1578,6 +1664,31 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   ir.count = count;
   ir.tp = tT;
   ir.td = tA;
+  if (use_tiles) {
+    // work items over the global A and A^T, none straddling two LPs
+    std::vector<int> r0a(count + 1), r0t(count + 1);
+    for (int k = 0; k < count; ++k) {
+      r0a[k] = (int)sh[k].R;
+      r0t[k] = (int)sh[k].C;
+    }
+    r0a[count] = (int)M;
+    r0t[count] = (int)N;
+    CUDA_TRY(cudaMemcpyAsync(g.row0_a, r0a.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g.row0_t, r0t.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
+    int ca[2] = {0, 0}, ct[2] = {0, 0}, W = 0;
+    CUDA_TRY(setup_tiles(g.a_ptr, (int)M, Z, g.row0_a, count, g.ttmp, g.ti_a, g.tlp_a,
+                         g.tlp_a + count + 1, g.tick_a, tcap_a, ca, &W, s));
+    CUDA_TRY(setup_tiles(g.t_ptr, (int)N, Z, g.row0_t, count, g.ttmp, g.ti_t, g.tlp_t,
+                         g.tlp_t + count + 1, g.tick_t, tcap_t, ct, &W, s));
+    g_launches += 16;
+    int bp = 0, bd = 0;
+    CUDA_TRY(tile_resident_mode((Mode)mode, &bp, &bd));
+    ir.tile = 1;
+    ir.tt = TileSet{g.ti_t, ct[0], g.tlp_t, g.tlp_t + count + 1, g.tpart_t, g.trow_t, g.tlong_t, g.tick_t};
+    ir.ta = TileSet{g.ti_a, ca[0], g.tlp_a, g.tlp_a + count + 1, g.tpart_a, g.trow_a, g.tlong_a, g.tick_a};
+    ir.grid_tt = tile_grid(ct[0], bp);
+    ir.grid_ta = tile_grid(ca[0], bd);
+  }
   KktRaw kr{};
   kr.a_ptr = g.a_ptr; kr.a_col = g.a_col; kr.a_val64 = g.a_val64;
   kr.t_ptr = g.t_ptr; kr.t_col = g.t_col; kr.t_val64 = g.t_val64;
@@ -1600,7 +1711,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   kr.tr = tA;
   kr.tc = tT;
   Solve sv{(int)M, (int)N, Z, (Mode)mode, lanes[0], lanes[1], lanes[2], lanes[3], ir, kr, s, 0};
-  if (p->autotune && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
+  if (p->autotune && !use_tiles && (!p->lanes_A || !p->lanes_AT) && p->iter_limit > 0) {
     // a lanes choice changes the blocks each LP gets: rebuild both launch maps
     auto set_grids = [&](int lt, int la) -> int {
       build_map(sh, false, la, tiled, nlong_a, long0_a, M, budget, tabA, &gridA);
@@ -1707,6 +1818,14 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     }
   }
   const double solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+  {
+    std::vector<DevState> chk(count);
+    CUDA_TRY(cudaMemcpyAsync(chk.data(), g.st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (const DevState& f : chk)
+      if (f.status == kStatusWaitFailed)
+        return fail(PDLP_ERR_TIMEOUT, "a bounded wait of a step kernel gave up");
+  }
   // ---- outputs
   CUDA_TRY(launch_output(kr, g.x_out, M ? g.y_out : nullptr, nullptr, nullptr, nullptr, nullptr, s));
   ++g_launches;
@@ -1728,6 +1847,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
                        : mode == MODE_BF16 ? PDLP_USED_BF16 : PDLP_USED_PATTERN;
     r.lanes_A = lanes[0];
     r.lanes_AT = lanes[1];
+    r.tiles = ir.tile;
     r.iters = f.iters;
     r.attempts = f.attempts;
     r.restarts = f.restarts;
@@ -1790,6 +1910,7 @@ int pdlp_default_params(pdlp_params* p) {
   p->persistent = 0;
   p->autotune = 0;
   p->detect_infeasibility = 1;
+  p->tiles = 0;
   return PDLP_OK;
 }
 

@@ -37,33 +37,7 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1.0, np.linalg.norm(b)))
 
 
-def skewed_lp(seed=3, m=6000, n=3000):
-    """Random LP with a dense row (n nnz), a column in every row (m nnz, two sort
-    tiles), a column in 2/3 of the rows, and a sparse remainder; mixed senses."""
-    rng = np.random.default_rng(seed)
-    rows, cols = [], []
-    rows.append(np.zeros(n, dtype=np.int64)); cols.append(np.arange(n))
-    rows.append(np.arange(1, m)); cols.append(np.zeros(m - 1, dtype=np.int64))
-    r2 = np.arange(1, m)[rng.random(m - 1) < 0.66]
-    rows.append(r2); cols.append(np.ones(r2.size, dtype=np.int64))
-    mask = rng.random((m, n)) < 0.002
-    mask[0, :] = False
-    mask[:, :2] = False
-    rr, cc = np.nonzero(mask)
-    rows.append(rr); cols.append(cc)
-    rows = np.concatenate(rows); cols = np.concatenate(cols)
-    vals = rng.uniform(0.5, 2.0, size=rows.size) * np.where(rng.random(rows.size) < 0.3, -1, 1)
-    l = np.zeros(n); u = rng.uniform(1, 3, size=n)
-    u[rng.random(n) < 0.1] = np.inf
-    x0 = rng.random(n) * np.where(np.isfinite(u), u, 1.0)
-    ax0 = np.zeros(m)
-    np.add.at(ax0, rows, vals * x0[cols])
-    sense = np.where(rng.random(m) < 0.5, lpgen.SENSE_LE, lpgen.SENSE_GE).astype(np.uint8)
-    sense[rng.random(m) < 0.1] = lpgen.SENSE_EQ
-    slack = rng.uniform(0, 1, size=m)
-    b = np.where(sense == lpgen.SENSE_LE, ax0 + slack, np.where(sense == lpgen.SENSE_GE, ax0 - slack, ax0))
-    c = rng.uniform(0.1, 1.0, size=n)
-    return lpgen._lp(m, n, rows, cols, vals, b, sense, c, l, u, np.zeros(n, np.uint8), "skewed")
+skewed_lp = lpgen.skewed_lp
 
 
 INSTANCES = {
