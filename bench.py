@@ -753,7 +753,8 @@ def run_fp(args):
     prm = P.default_params(tol=1e-4, precision=args.precision)
     P.pdlp_solve(lp, prm)  # warm: graph capture and library load
     rows = []
-    for strat in ("type", "frac", "redcost", "dual"):
+    for strat in ("type", "frac", "redcost", "dual", "frac_dual", "frac_redcost", "dual_frac",
+                  "redcost_frac"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x_lp, y_lp, r = P.pdlp_solve(lp, prm)

@@ -419,6 +419,15 @@ int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, const char* se
 #define FP_REDCOST 1  /* descending |reduced cost| */
 #define FP_DUAL 2     /* rows by descending |y|, their integers by descending |reduced cost| */
 #define FP_TYPE 3     /* binaries first, then general integers (stable) */
+/* Hybrid strategies (section 2, "Tiebreaking and hybrid strategies": a strategy whose
+ * equally ranked variables are ordered by a second one; ties left after both keep the
+ * first strategy's own tie order) */
+#define FP_FRAC_DUAL 4    /* fractionality; ties by position in the FP_DUAL order */
+#define FP_FRAC_REDCOST 5 /* fractionality; ties by descending |reduced cost| */
+#define FP_DUAL_FRAC 6    /* FP_DUAL with each row's new integers by descending |reduced
+                             cost|, then ascending fractionality; integers in no row by
+                             ascending fractionality */
+#define FP_REDCOST_FRAC 7 /* descending |reduced cost|; ties by ascending fractionality */
 #define FP_FEASIBLE 1    /* all integers fixed and the final LP's point satisfies every
                             row to 1e-6 max(1, |b_i|) (solved at final_lp_tol; a point
                             that misses a row is polished, pdlp_polish_primal) */
@@ -428,7 +437,8 @@ int pdlp_solve_device_noalloc(const pdlp_csr* A, const double* b, const char* se
 
 typedef struct {
   size_t struct_size;  /* sizeof(fp_params); set by fp_default_params */
-  int var_strategy;    /* FP_FRAC | FP_REDCOST | FP_DUAL | FP_TYPE (default) */
+  int var_strategy;    /* FP_FRAC | FP_REDCOST | FP_DUAL | FP_TYPE (default) | one of the
+                          hybrids FP_FRAC_DUAL .. FP_REDCOST_FRAC */
   uint64_t seed;       /* SplitMix64 seed of the fixing draws, default 1 */
   int64_t node_limit;  /* branching nodes; <= 0 means 10 x (number of integers) */
   int final_lp;        /* 1 (default): solve the final LP; 0: stop after the search */

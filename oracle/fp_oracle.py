@@ -13,6 +13,15 @@ fixing", "Integer-aware branching strategy", Alg. 1):
     DUAL    rows by descending |y| (stable); each row's integers not yet
             seen, by descending |lambda| (stable); remaining integers by index;
     TYPE    stable, binaries first, then general integers;
+  and the hybrid strategies of section 2, "Tiebreaking and hybrid strategies"
+  (Frac with ties broken by Dual or by RedCost, and the reverse): a variable
+  strategy whose equal-ranked variables are ordered by a second one,
+    FRAC_DUAL     ascending fractionality; ties by position in the DUAL order;
+    FRAC_REDCOST  ascending fractionality; ties by descending |lambda|, then index;
+    DUAL_FRAC     the DUAL order with each row's new integers by descending
+                  |lambda| and then ascending fractionality (then storage order),
+                  and the integers of no row by ascending fractionality, then index;
+    REDCOST_FRAC  descending |lambda|; ties by ascending fractionality, then index;
 * LP-based fixing: x = LP value clamped to the current domain,
   d_i = x - floor(x), d ~ U(0,1); fix to floor(x) if d > d_i, else ceil(x);
 * Alg. 1 branching: bound changes in increasing priority,
@@ -42,6 +51,7 @@ import numpy as np
 
 SENSE_LE, SENSE_GE, SENSE_EQ = ord("L"), ord("G"), ord("E")
 FRAC, REDCOST, DUAL, TYPE = 0, 1, 2, 3
+FRAC_DUAL, FRAC_REDCOST, DUAL_FRAC, REDCOST_FRAC = 4, 5, 6, 7
 FEASIBLE, INFEASIBLE, NODE_LIMIT, NO_FINAL_LP = 1, 2, 3, 4
 MASK = (1 << 64) - 1
 INT_EPS = 1e-6   # rounding slack of integer bounds
@@ -95,28 +105,54 @@ def reduced_costs(lp, y):
     return lam
 
 
+def fractionality(v: float) -> float:
+    return min(v - math.floor(v), math.ceil(v) - v)
+
+
+def dual_order(lp, lam, y_lp, is_int, frac=None):
+    """DUAL: rows by descending |y|; each row's integers not yet seen by descending
+    |lambda| (and, given ``frac``, then ascending fractionality); the integers of no
+    row last, in index order (or by ascending fractionality given ``frac``).  Python's
+    sort is stable: remaining ties keep storage or index order."""
+    rows = sorted(range(lp.m), key=lambda i: -abs(y_lp[i]))
+    seen = [False] * lp.n
+    out = []
+    for i in rows:
+        cols = [int(lp.col[p]) for p in range(lp.row_ptr[i], lp.row_ptr[i + 1])
+                if is_int[lp.col[p]] and not seen[lp.col[p]]]
+        if frac is None:
+            cols = sorted(cols, key=lambda j: -abs(lam[j]))
+        else:
+            cols = sorted(cols, key=lambda j: (-abs(lam[j]), frac[j]))
+        for j in cols:
+            if not seen[j]:
+                seen[j] = True
+                out.append(j)
+    rest = [j for j in range(lp.n) if is_int[j] and not seen[j]]
+    if frac is not None:
+        rest = sorted(rest, key=lambda j: frac[j])
+    return out + rest
+
+
 def variable_order(lp, strategy, x_lp, y_lp, is_int):
     ints = [j for j in range(lp.n) if is_int[j]]
+    frac = [fractionality(x_lp[j]) for j in range(lp.n)]
     if strategy == FRAC:
-        key = [min(x_lp[j] - math.floor(x_lp[j]), math.ceil(x_lp[j]) - x_lp[j]) for j in range(lp.n)]
-        return sorted(ints, key=lambda j: key[j])
-    lam = reduced_costs(lp, y_lp) if strategy in (REDCOST, DUAL) else None
+        return sorted(ints, key=lambda j: frac[j])
+    lam = reduced_costs(lp, y_lp) if strategy not in (TYPE,) else None
     if strategy == REDCOST:
         return sorted(ints, key=lambda j: -abs(lam[j]))
     if strategy == DUAL:
-        rows = sorted(range(lp.m), key=lambda i: -abs(y_lp[i]))
-        seen = [False] * lp.n
-        out = []
-        for i in rows:
-            cols = [int(lp.col[p]) for p in range(lp.row_ptr[i], lp.row_ptr[i + 1])
-                    if is_int[lp.col[p]] and not seen[lp.col[p]]]
-            cols = sorted(cols, key=lambda j: -abs(lam[j]))
-            for j in cols:
-                if not seen[j]:
-                    seen[j] = True
-                    out.append(j)
-        out += [j for j in ints if not seen[j]]
-        return out
+        return dual_order(lp, lam, y_lp, is_int)
+    if strategy == FRAC_DUAL:
+        rank = {j: k for k, j in enumerate(dual_order(lp, lam, y_lp, is_int))}
+        return sorted(ints, key=lambda j: (frac[j], rank[j]))
+    if strategy == FRAC_REDCOST:
+        return sorted(ints, key=lambda j: (frac[j], -abs(lam[j])))
+    if strategy == DUAL_FRAC:
+        return dual_order(lp, lam, y_lp, is_int, frac=frac)
+    if strategy == REDCOST_FRAC:
+        return sorted(ints, key=lambda j: (-abs(lam[j]), frac[j]))
     if strategy == TYPE:
         binary = [j for j in ints if lp.l[j] == 0.0 and lp.u[j] == 1.0]
         general = [j for j in ints if not (lp.l[j] == 0.0 and lp.u[j] == 1.0)]

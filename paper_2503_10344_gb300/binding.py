@@ -363,7 +363,10 @@ def pdlp_solve_device_noalloc(dlp: DeviceLP, params: PdlpParams | None = None, x
 # ------------------------------------------------------------------ fix-and-propagate
 FP_FRAC, FP_REDCOST, FP_DUAL, FP_TYPE = 0, 1, 2, 3
 FP_FEASIBLE, FP_INFEASIBLE, FP_NODE_LIMIT, FP_NO_FINAL_LP = 1, 2, 3, 4
-FP_STRATEGY = {"frac": FP_FRAC, "redcost": FP_REDCOST, "dual": FP_DUAL, "type": FP_TYPE}
+FP_FRAC_DUAL, FP_FRAC_REDCOST, FP_DUAL_FRAC, FP_REDCOST_FRAC = 4, 5, 6, 7
+FP_STRATEGY = {"frac": FP_FRAC, "redcost": FP_REDCOST, "dual": FP_DUAL, "type": FP_TYPE,
+               "frac_dual": FP_FRAC_DUAL, "frac_redcost": FP_FRAC_REDCOST,
+               "dual_frac": FP_DUAL_FRAC, "redcost_frac": FP_REDCOST_FRAC}
 
 
 class FpParams(C.Structure):

@@ -298,18 +298,57 @@ bool propagate(const Problem& P, Domains& d, const int32_t* rows, int64_t nrows,
   return ok;
 }
 
+static double fractionality(double v) { return std::min(v - floor(v), ceil(v) - v); }
+
+// DUAL: rows by descending |y| (stable); each row's integers not yet seen by
+// descending |lambda| -- with `frac`, then by ascending fractionality -- in storage
+// order otherwise; the integers of no row last, by index (with `frac`: by ascending
+// fractionality, then index).
+static void dual_order(const Problem& P, const std::vector<double>& lam, const double* y_lp,
+                       const uint8_t* is_int, const std::vector<double>* frac,
+                       std::vector<int>& order) {
+  std::vector<int> rows(P.m);
+  for (int i = 0; i < P.m; ++i) rows[i] = i;
+  std::stable_sort(rows.begin(), rows.end(),
+                   [&](int a, int b) { return fabs(y_lp[a]) > fabs(y_lp[b]); });
+  std::vector<uint8_t> seen(P.n, 0);
+  std::vector<int> cols;
+  for (int i : rows) {
+    cols.clear();
+    for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
+      const int j = P.col[p];
+      if (is_int[j] && !seen[j]) cols.push_back(j);
+    }
+    std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) {
+      const double la = fabs(lam[a]), lb = fabs(lam[b]);
+      if (la != lb) return la > lb;
+      return frac ? (*frac)[a] < (*frac)[b] : false;
+    });
+    for (int j : cols)
+      if (!seen[j]) {
+        seen[j] = 1;
+        order.push_back(j);
+      }
+  }
+  std::vector<int> rest;
+  for (int j = 0; j < P.n; ++j)
+    if (is_int[j] && !seen[j]) rest.push_back(j);
+  if (frac)
+    std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return (*frac)[a] < (*frac)[b]; });
+  order.insert(order.end(), rest.begin(), rest.end());
+}
+
 void variable_order(const Problem& P, int strategy, const double* x_lp, const double* y_lp,
                     const uint8_t* is_int, std::vector<int>& order) {
   std::vector<int> ints;
   for (int j = 0; j < P.n; ++j)
     if (is_int[j]) ints.push_back(j);
   order.clear();
+  std::vector<double> frac(P.n);
+  for (int j = 0; j < P.n; ++j) frac[j] = fractionality(x_lp[j]);
   if (strategy == FP_FRAC) {
-    std::vector<double> key(P.n);
-    for (int j = 0; j < P.n; ++j)
-      key[j] = std::min(x_lp[j] - floor(x_lp[j]), ceil(x_lp[j]) - x_lp[j]);
     order = ints;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return frac[a] < frac[b]; });
     return;
   }
   if (strategy == FP_TYPE) {
@@ -323,35 +362,46 @@ void variable_order(const Problem& P, int strategy, const double* x_lp, const do
   std::vector<double> lam(P.c, P.c + P.n);
   for (int i = 0; i < P.m; ++i)
     for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) lam[P.col[p]] -= P.val[p] * y_lp[i];
-  if (strategy == FP_REDCOST) {
-    order = ints;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return fabs(lam[a]) > fabs(lam[b]); });
-    return;
-  }
-  // FP_DUAL
-  std::vector<int> rows(P.m);
-  for (int i = 0; i < P.m; ++i) rows[i] = i;
-  std::stable_sort(rows.begin(), rows.end(),
-                   [&](int a, int b) { return fabs(y_lp[a]) > fabs(y_lp[b]); });
-  std::vector<uint8_t> seen(P.n, 0);
-  std::vector<int> cols;
-  for (int i : rows) {
-    cols.clear();
-    for (int64_t p = P.rp[i]; p < P.rp[i + 1]; ++p) {
-      const int j = P.col[p];
-      if (is_int[j] && !seen[j]) cols.push_back(j);
+  switch (strategy) {
+    case FP_REDCOST:
+      order = ints;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int b) { return fabs(lam[a]) > fabs(lam[b]); });
+      return;
+    case FP_DUAL:
+      dual_order(P, lam, y_lp, is_int, nullptr, order);
+      return;
+    case FP_FRAC_DUAL: {  // fractionality, ties by position in the DUAL order
+      std::vector<int> dual;
+      dual_order(P, lam, y_lp, is_int, nullptr, dual);
+      std::vector<int> rank(P.n, 0);
+      for (size_t k = 0; k < dual.size(); ++k) rank[dual[k]] = (int)k;
+      order = ints;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (frac[a] != frac[b]) return frac[a] < frac[b];
+        return rank[a] < rank[b];
+      });
+      return;
     }
-    std::stable_sort(cols.begin(), cols.end(),
-                     [&](int a, int b) { return fabs(lam[a]) > fabs(lam[b]); });
-    for (int j : cols)
-      if (!seen[j]) {
-        seen[j] = 1;
-        order.push_back(j);
-      }
+    case FP_FRAC_REDCOST:  // fractionality, ties by descending |lambda|, then index
+      order = ints;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (frac[a] != frac[b]) return frac[a] < frac[b];
+        return fabs(lam[a]) > fabs(lam[b]);
+      });
+      return;
+    case FP_DUAL_FRAC:
+      dual_order(P, lam, y_lp, is_int, &frac, order);
+      return;
+    default:  // FP_REDCOST_FRAC: descending |lambda|, ties by fractionality, then index
+      order = ints;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double la = fabs(lam[a]), lb = fabs(lam[b]);
+        if (la != lb) return la > lb;
+        return frac[a] < frac[b];
+      });
+      return;
   }
-  for (int j : ints)
-    if (!seen[j]) order.push_back(j);
 }
 
 // Largest row violation of x, each scaled by max(1, |b_i|) (the paper's
@@ -410,10 +460,10 @@ extern "C" int fp_run(const pdlp_csr* A, const double* b, const char* sense, con
   if (prm->struct_size != sizeof(fp_params))
     return bad_input("fp_params.struct_size mismatch (use fp_default_params)");
   if (A->m < 0 || A->n < 1 || A->nnz < 0) return bad_input("fp_run: need m >= 0, n >= 1, nnz >= 0");
-  if (prm->var_strategy < FP_FRAC || prm->var_strategy > FP_TYPE)
+  if (prm->var_strategy < FP_FRAC || prm->var_strategy > FP_REDCOST_FRAC)
     return bad_input("fp_run: unknown var_strategy");
-  if ((prm->var_strategy == FP_REDCOST || prm->var_strategy == FP_DUAL) && !y_lp && A->m > 0)
-    return bad_input("fp_run: FP_REDCOST and FP_DUAL need y_lp");
+  if (prm->var_strategy != FP_FRAC && prm->var_strategy != FP_TYPE && !y_lp && A->m > 0)
+    return bad_input("fp_run: FP_REDCOST, FP_DUAL and the hybrid strategies need y_lp");
   memset(r, 0, sizeof(*r));
   const auto t0 = std::chrono::steady_clock::now();
   Problem P{A->m, A->n, A->row_ptr, A->col, A->val, b, sense, c, l, u, {}, {}, {}};

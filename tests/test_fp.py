@@ -89,6 +89,43 @@ def test_variable_orders_by_hand():
     assert F.variable_order(lp, F.TYPE, x, y, ii) == [0, 1, 3, 2]
 
 
+def tie_mip():
+    """rows: x0 + x1 <= 1;  x2 + x3 <= 1;  x3 + x4 <= 1 (all <=); seven binaries, x5 and x6
+    in no row; c = (-2, -1, -3, -4, -2, 0.5, 2); LP point x = (1, 0, 0.5, 0.5, 0, 0.3, 0.9),
+    y = (-1, -2, -3).  Built so that every strategy meets ties."""
+    a = [[1, 1, 0, 0, 0, 0, 0], [0, 0, 1, 1, 0, 0, 0], [0, 0, 0, 1, 1, 0, 0]]
+    lp = _mip(a, [1, 1, 1], "LLL", [-2, -1, -3, -4, -2, 0.5, 2], [0] * 7, [1] * 7, [1] * 7)
+    return lp, np.array([1.0, 0.0, 0.5, 0.5, 0.0, 0.3, 0.9]), np.array([-1.0, -2.0, -3.0])
+
+
+def test_hybrid_orders_by_hand():
+    """Section 2, "Tiebreaking and hybrid strategies": Frac with ties broken by Dual or by
+    RedCost, and the reverse.  A^T y = (-1, -1, -2, -5, -3, 0, 0), so lambda = c - A^T y =
+    (-1, 0, -1, 1, 1, 0.5, 2); |lambda| = (1, 0, 1, 1, 1, 0.5, 2); fractionality
+    (0, 0, 0.5, 0.5, 0, 0.3, 0.1).
+    FRAC:    0: {0, 1, 4} | 0.1: 6 | 0.3: 5 | 0.5: {2, 3}            -> 0 1 4 6 5 2 3
+    REDCOST: 2: 6 | 1: {0, 2, 3, 4} | 0.5: 5 | 0: 1                   -> 6 0 2 3 4 5 1
+    DUAL:    rows by |y|: r2, r1, r0; r2 -> 3, 4 (|lambda| tie, storage order); r1 -> 2;
+             r0 -> 0, 1; no row: 5, 6 by index                        -> 3 4 2 0 1 5 6
+    FRAC_DUAL:    {0, 1, 4} by DUAL rank (3, 4, 1) -> 4 0 1; 6; 5;
+                  {2, 3} by rank (2, 0) -> 3 2                        -> 4 0 1 6 5 3 2
+    FRAC_REDCOST: {0, 1, 4} by |lambda| (1, 0, 1) -> 0 4 1; 6; 5;
+                  {2, 3} tie on both -> index                         -> 0 4 1 6 5 2 3
+    DUAL_FRAC:    r2: 3, 4 tie on |lambda| -> by frac (0.5, 0) -> 4 3; r1 -> 2;
+                  r0 -> 0 1; no row by frac (0.3, 0.1) -> 6 5        -> 4 3 2 0 1 6 5
+    REDCOST_FRAC: 6; {0, 2, 3, 4} by frac (0, 0.5, 0.5, 0) -> 0 4 2 3; 5; 1
+                                                                      -> 6 0 4 2 3 5 1"""
+    lp, x, y = tie_mip()
+    np.testing.assert_allclose(F.reduced_costs(lp, y), [-1, 0, -1, 1, 1, 0.5, 2])
+    ii = lp.is_int
+    want = {F.FRAC: [0, 1, 4, 6, 5, 2, 3], F.REDCOST: [6, 0, 2, 3, 4, 5, 1],
+            F.DUAL: [3, 4, 2, 0, 1, 5, 6], F.FRAC_DUAL: [4, 0, 1, 6, 5, 3, 2],
+            F.FRAC_REDCOST: [0, 4, 1, 6, 5, 2, 3], F.DUAL_FRAC: [4, 3, 2, 0, 1, 6, 5],
+            F.REDCOST_FRAC: [6, 0, 4, 2, 3, 5, 1]}
+    for strategy, order in want.items():
+        assert F.variable_order(lp, strategy, x, y, ii) == order, strategy
+
+
 def test_propagation_by_hand():
     """Fixing x0 = 1 forces x1 <= (1 - 1)/1 = 0 (row 0) and then x2 <= 2 - 0 - 0 = 2 (row 1)."""
     lp, _, _ = hand_mip()
@@ -149,14 +186,19 @@ def P():
     return P
 
 
+STRATEGY_IDS = {"frac": F.FRAC, "redcost": F.REDCOST, "dual": F.DUAL, "type": F.TYPE,
+                "frac_dual": F.FRAC_DUAL, "frac_redcost": F.FRAC_REDCOST,
+                "dual_frac": F.DUAL_FRAC, "redcost_frac": F.REDCOST_FRAC}
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
-@pytest.mark.parametrize("strategy", ["frac", "redcost", "dual", "type"])
+@pytest.mark.parametrize("strategy", list(STRATEGY_IDS))
 def test_cabi_search_matches_oracle(P, seed, strategy):
     """fp_run (final_lp = 0) takes exactly the oracle's decisions: the same integer
     assignment, node and backtrack counts and status, on 200 x 400 MIP relaxations."""
     lp = lpgen.mip_relaxation(seed)
     r = O.solve(lp, O.Params(tol=1e-4))
-    sid = {"frac": F.FRAC, "redcost": F.REDCOST, "dual": F.DUAL, "type": F.TYPE}[strategy]
+    sid = STRATEGY_IDS[strategy]
     for draw_seed in (1, 99):
         st, dom, nodes, backtracks = F.fp_search(lp, r.x, r.y, lp.is_int, sid, draw_seed)
         x, res = P.fp_run(lp, r.x, r.y, strategy=strategy, seed=draw_seed, final_lp=False)
@@ -179,14 +221,15 @@ def _mixed_lp(seed):
 @pytest.mark.parametrize("maker", [lambda: lpgen.set_cover_fixed(20, 150), lambda: _mixed_lp(30),
                                    lambda: lpgen.mip_relaxation(5, m=120, n=240, density=0.04)],
                          ids=["cover_fixed", "mixed_free_eq", "denser_relaxation"])
-@pytest.mark.parametrize("strategy", ["frac", "dual"])
+@pytest.mark.parametrize("strategy", ["frac", "dual", "frac_dual", "dual_frac", "frac_redcost",
+                                      "redcost_frac"])
 def test_cabi_search_matches_oracle_on_other_shapes(P, maker, strategy):
     """The same node-for-node agreement on covering sub-LPs (fixed columns, >=-rows), mixed
     senses with free continuous columns, and a denser relaxation (the row filter of the
     C++ search, which skips rows whose slack covers every range, must not change a decision)."""
     lp = maker()
     r = O.solve(lp, O.Params(tol=1e-4, iter_limit=20000))
-    sid = {"frac": F.FRAC, "dual": F.DUAL}[strategy]
+    sid = STRATEGY_IDS[strategy]
     for draw_seed in (1, 7):
         st, dom, nodes, backtracks = F.fp_search(lp, r.x, r.y, lp.is_int, sid, draw_seed)
         x, res = P.fp_run(lp, r.x, r.y, strategy=strategy, seed=draw_seed, final_lp=False)
@@ -202,7 +245,9 @@ def test_cabi_rejects_bad_arguments(P):
     with pytest.raises(P.PdlpError, match="need y_lp"):
         P.fp_run(lp, x, None, strategy="dual", final_lp=False)  # Dual needs y
     with pytest.raises(P.PdlpError, match="unknown var_strategy"):
-        P.fp_run(lp, x, y, strategy=7, final_lp=False)
+        P.fp_run(lp, x, y, strategy=8, final_lp=False)
+    with pytest.raises(P.PdlpError, match="need y_lp"):
+        P.fp_run(lp, x, None, strategy="frac_redcost", final_lp=False)
     with pytest.raises(P.PdlpError, match="nrefs >= 1"):
         P.fp_run_refs(lp, [], y, final_lp=False)
 

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import lpgen
+import test_gpu_pdlp as T
 from oracle import pdlp_oracle as O
 from oracle import reference_lp as R
 
@@ -18,23 +19,25 @@ def P():
     return P
 
 
+MIXED_KEYS = ["mip_relaxation(1)", "set_cover(7,m=2000,n=8000)", "energy_system(hours=24)",
+              "random_sparse_lp(11,300,500)", "skewed_lp()", "mip_relaxation(2,m=60,n=90)"]
+
+
 def mixed_lps():
-    import test_gpu_pdlp as T
     return [lpgen.mip_relaxation(1), lpgen.set_cover(7, m=2000, n=8000), lpgen.energy_system(hours=24),
-            lpgen.random_sparse_lp(11, 300, 500), T.skewed_lp(), lpgen.mip_relaxation(2, m=60, n=90)]
+            lpgen.random_sparse_lp(11, 300, 500), lpgen.skewed_lp(), lpgen.mip_relaxation(2, m=60, n=90)]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_mixed_batch_reaches_tolerance(P, prec):
     lps = mixed_lps()
     xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision=prec))
-    for lp, x, y, r in zip(lps, xs, ys, res):
+    for lp, key, x, y, r in zip(lps, MIXED_KEYS, xs, ys, res):
         assert r["status"] == P.PDLP_OPTIMAL, (lp.name, r)
         k = O.kkt_original(lp, x, y)
         assert k.rel_kkt <= 1.01e-4, (lp.name, k)
         assert r["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
-        obj, _, _, _ = R.highs(lp)
-        assert abs(r["primal_obj"] - obj) / (1 + abs(obj)) <= 5e-4, lp.name
+        assert T.obj_err(r["primal_obj"], key) <= T.OBJ_TOL, lp.name
     assert len({r["iters"] for r in res}) > 1  # the LPs stop independently
 
 
@@ -55,13 +58,15 @@ def test_fp64_batch_matches_oracle_per_lp(P, K):
 def test_batch_of_fixed_cover_subproblems(P):
     """Covering sub-LPs with 10-50 % of the columns fixed to 0/1 (as fix-and-propagate
     leaves them), float32 iterates on the pattern matrix."""
-    lps = [lpgen.set_cover_fixed(4000 + k, int(m)) for k, m in
-           enumerate(np.random.default_rng(0).integers(2000, 6001, size=12))]
-    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="bf16"))
-    for lp, x, y, r in zip(lps, xs, ys, res):
-        assert r["status"] == P.PDLP_OPTIMAL and r["precision_used"] == 3
-        assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4
-        assert np.all(x >= lp.l) and np.all(x <= lp.u)
+    sizes = [int(m) for m in np.random.default_rng(0).integers(2000, 6001, size=12)]
+    lps = [lpgen.set_cover_fixed(4000 + k, m) for k, m in enumerate(sizes)]
+    for tiles in (0, 1):
+        xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="bf16", tiles=tiles))
+        for k, (lp, x, y, r) in enumerate(zip(lps, xs, ys, res)):
+            assert r["status"] == P.PDLP_OPTIMAL and r["precision_used"] == 3 and r["tiles"] == tiles
+            assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4
+            assert np.all(x >= lp.l) and np.all(x <= lp.u)
+            assert T.obj_err(r["primal_obj"], f"set_cover_fixed({4000 + k},{sizes[k]})") <= T.OBJ_TOL
 
 
 def test_batch_rejects_an_invalid_member(P):

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import lpgen
+import test_gpu_pdlp as T
 from oracle import pdlp_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -41,13 +42,15 @@ short_rows_lp = lpgen.short_rows_lp
 
 
 INSTANCES = {
-    "mip_relaxation_200x400": (lambda: lpgen.mip_relaxation(1), "fp32"),
-    "set_cover_2000x8000_pattern": (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16"),
-    "mip_relaxation_bf16": (lambda: lpgen.mip_relaxation(3), "bf16"),
-    "energy_system_48h": (lambda: lpgen.energy_system(hours=48), "fp32"),
-    "random_free_eq_300x500": (lambda: lpgen.random_sparse_lp(11, 300, 500), "fp32"),
-    "long_rows_6500x3000": (lambda: long_rows_lp(), "fp32"),
-    "short_rows_3000x40000": (lambda: short_rows_lp(), "bf16"),
+    "mip_relaxation_200x400": (lambda: lpgen.mip_relaxation(1), "fp32", "mip_relaxation(1)"),
+    "set_cover_2000x8000_pattern": (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16",
+                                    "set_cover(7,m=2000,n=8000)"),
+    "mip_relaxation_bf16": (lambda: lpgen.mip_relaxation(3), "bf16", "mip_relaxation(3)"),
+    "energy_system_48h": (lambda: lpgen.energy_system(hours=48), "fp32", "energy_system(hours=48)"),
+    "random_free_eq_300x500": (lambda: lpgen.random_sparse_lp(11, 300, 500), "fp32",
+                               "random_sparse_lp(11,300,500)"),
+    "long_rows_6500x3000": (lambda: long_rows_lp(), "fp32", "long_rows_lp()"),
+    "short_rows_3000x40000": (lambda: short_rows_lp(), "bf16", "short_rows_lp()"),
 }
 _cache = {}
 
@@ -89,6 +92,7 @@ def test_tile_solve_reaches_tolerance(P, name):
     k = O.kkt_original(lp, x, y)
     assert k.rel_kkt <= 1.01e-4, k
     assert r["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
+    assert T.obj_err(r["primal_obj"], INSTANCES[name][2]) <= T.OBJ_TOL
 
 
 def test_tiles_are_deterministic(P):
