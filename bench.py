@@ -518,7 +518,8 @@ def batch_section(args, dev, stream, peak):
             "precision": {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
                           3: "fp32 iterates, pattern matrix"}[res[0]["precision_used"]],
             "tiles": res[0]["tiles"], "optimal": int(sum(r["status"] == P.PDLP_OPTIMAL for r in res)),
-            "wall_s": statistics.median(walls), "setup_s": statistics.median(setup),
+            "wall_s": statistics.median(walls), "upload_s": res[0]["upload_s"],
+            "setup_s": statistics.median(setup),
             "solve_s": statistics.median(solve), "iters_sum": iters[-1],
             "iters_per_s": iters[-1] / solve[-1], "lps_per_s": len(lps) / statistics.median(solve),
             "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},

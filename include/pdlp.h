@@ -184,6 +184,8 @@ typedef struct {
                              (DUAL_INFEASIBLE); NaN otherwise */
   double ray_res;         /* the 2-norm of the certificate's residual; NaN otherwise */
   int tiles;              /* 1 if the staged tile step kernels ran (pdlp_params.tiles) */
+  double upload_s;        /* batches from host buffers: the host-to-device copies of the
+                             inputs (setup_s is the device setup after them); 0 otherwise */
 } pdlp_result;
 
 /* Optional diagnostic outputs (same memory space as the entry point's outputs;
@@ -310,10 +312,12 @@ int pdlp_polish_dual(const pdlp_csr* A, const char* sense, const double* c, cons
  * Arrays of per-LP HOST pointers in the layout of pdlp_solve; one parameter
  * set for all; r[count] results.  x_out / y_out may be NULL (or hold NULL
  * entries) for outputs not wanted.
- * The LPs form one block-diagonal problem on the device: each LP is set up
- * (canonical form, transpose, scaling) on its own, then every step kernel and
- * KKT pass runs over all LPs in one launch; each LP keeps its own step size,
- * primal weight, restarts and termination, and stops independently.  One CUDA
+ * The LPs form one block-diagonal problem on the device: the inputs are copied to
+ * their places in it, validated per LP and set up (canonical form, transpose,
+ * scaling) in one pass over the whole batch -- every setup step treats each row
+ * and column on its own, so each LP is set up exactly as on its own -- then every
+ * step kernel and KKT pass runs over all LPs in one launch; each LP keeps its own
+ * step size, primal weight, restarts and termination, and stops independently.  One CUDA
  * graph holds check_period attempts plus the KKT block of the whole batch.
  * All LPs share one precision mode: FP32_BF16A picks the pattern / bf16 form
  * only if every LP qualifies.  Limits: total rows, columns and nonzeros below
@@ -323,6 +327,19 @@ int pdlp_solve_batch(int count, const pdlp_csr* const* A, const double* const* b
                      const char* const* sense, const double* const* c, const double* const* l,
                      const double* const* u, const pdlp_params* p, double* const* x_out,
                      double* const* y_out, pdlp_result* r);
+
+/* pdlp_solve_batch from DEVICE buffers, in stream order: A[k] are host structs whose
+ * arrays are on the device, b[k] ... u[k] device pointers, x_out[k] / y_out[k] device
+ * outputs (NULL entries allowed), r[count] host results, stream a cudaStream_t.  The
+ * batch is validated and set up on the device as one block-diagonal problem (each LP
+ * exactly as on its own: every setup step treats rows and columns one by one), with
+ * one small read-back of per-LP scalars; the library allocates its scratch with the
+ * stream-ordered allocator.  No counterpart in the paper.  Returns as pdlp_solve_batch. */
+int pdlp_solve_batch_device(int count, const pdlp_csr* const* A, const double* const* b,
+                            const char* const* sense, const double* const* c,
+                            const double* const* l, const double* const* u, const pdlp_params* p,
+                            double* const* x_out, double* const* y_out, pdlp_result* r,
+                            void* stream);
 
 /* Device workspace, in bytes, that pdlp_solve_device needs for this size and
  * these parameters (precision mode and value format decide it).  Returns 0 on

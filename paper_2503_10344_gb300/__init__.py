@@ -8,7 +8,8 @@ from .binding import (FP_DUAL, FP_FEASIBLE, FP_FRAC, FP_INFEASIBLE, FP_NODE_LIMI
                       PDLP_FP32, PDLP_FP32_BF16A, PDLP_FP64, PDLP_ITER_LIMIT, PDLP_NUMERICAL,
                       PDLP_OPTIMAL, PDLP_TIME_LIMIT, PDLP_PRIMAL_INFEASIBLE, PDLP_DUAL_INFEASIBLE,
                       DeviceLP, PdlpError, default_params, lib,
-                      pdlp_polish_dual, pdlp_polish_primal, pdlp_solve, pdlp_solve_batch, pdlp_solve_device, pdlp_solve_device_noalloc,
+                      pdlp_polish_dual, pdlp_polish_primal, pdlp_solve, pdlp_solve_batch, pdlp_solve_batch_device, pdlp_solve_device,
+                      pdlp_solve_device_noalloc,
                       time_kernels, time_kernels_batch,
                       workspace_size)
 from .gnn import GnnGraph, GnnModel, pdlp_solve_warm, start_kkt
@@ -17,6 +18,6 @@ __all__ = ["FP_DUAL", "FP_FEASIBLE", "FP_FRAC", "FP_INFEASIBLE", "FP_NODE_LIMIT"
            "FP_NO_FINAL_LP", "FP_REDCOST", "FP_TYPE", "fp_run", "fp_run_refs", "PDLP_FP32", "PDLP_FP32_BF16A", "PDLP_FP64", "PDLP_ITER_LIMIT", "PDLP_NUMERICAL",
            "PDLP_OPTIMAL", "PDLP_TIME_LIMIT", "PDLP_PRIMAL_INFEASIBLE", "PDLP_DUAL_INFEASIBLE",
            "DeviceLP", "PdlpError", "default_params", "lib",
-           "pdlp_polish_dual", "pdlp_polish_primal", "pdlp_solve", "pdlp_solve_batch", "pdlp_solve_device",
+           "pdlp_polish_dual", "pdlp_polish_primal", "pdlp_solve", "pdlp_solve_batch", "pdlp_solve_batch_device", "pdlp_solve_device",
            "pdlp_solve_device_noalloc", "time_kernels", "time_kernels_batch",
            "workspace_size", "GnnGraph", "GnnModel", "pdlp_solve_warm", "start_kkt"]

@@ -54,7 +54,7 @@ class PdlpResult(C.Structure):
                 ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("lanes_A", C.c_int),
                 ("lanes_AT", C.c_int), ("ray_obj", C.c_double), ("ray_res", C.c_double),
-                ("tiles", C.c_int)]
+                ("tiles", C.c_int), ("upload_s", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -499,6 +499,38 @@ def pdlp_solve_batch(lps, params: PdlpParams | None = None, want_y: bool = True)
     _check(rc)
     del keep
     return xs, ys, [res[i].as_dict() for i in range(k)]
+
+
+def pdlp_solve_batch_device(dlps, params: PdlpParams | None = None, stream=None):
+    """Solve a list of DeviceLP together from device buffers (pdlp_solve_batch_device);
+    returns (xs, ys, results) with xs / ys float64 CUDA tensors."""
+    import torch
+    L = lib()
+    if not getattr(L, "_batch_dev_ready", False):
+        L.pdlp_solve_batch_device.argtypes = [C.c_int, C.c_void_p] + [C.c_void_p] * 5 + \
+            [C.POINTER(PdlpParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L._batch_dev_ready = True
+    p = params or default_params()
+    k = len(dlps)
+    dev = dlps[0].c.device
+    xs = [torch.empty(d.n, dtype=torch.float64, device=dev) for d in dlps]
+    ys = [torch.empty(max(d.m, 1), dtype=torch.float64, device=dev) for d in dlps]
+    csrs = (PdlpCsr * k)()
+    ptrs = {name: (C.c_void_p * k)() for name in ("b", "sense", "c", "l", "u", "x", "y")}
+    for i, d in enumerate(dlps):
+        csrs[i] = PdlpCsr(d.m, d.n, d.nnz, d.row_ptr.data_ptr(), d.col.data_ptr(), d.val.data_ptr())
+        for name, t in (("b", d.b), ("sense", d.sense), ("c", d.c), ("l", d.l), ("u", d.u),
+                        ("x", xs[i]), ("y", ys[i])):
+            ptrs[name][i] = t.data_ptr()
+    csr_ptrs = (C.c_void_p * k)(*[C.cast(C.pointer(csrs[i]), C.c_void_p) for i in range(k)])
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    res = (PdlpResult * k)()
+    rc = L.pdlp_solve_batch_device(k, csr_ptrs, ptrs["b"], ptrs["sense"], ptrs["c"], ptrs["l"],
+                                   ptrs["u"], C.byref(p), ptrs["x"], ptrs["y"], res,
+                                   C.c_void_p(stream.cuda_stream))
+    _check(rc)
+    return xs, [y[: d.m] for y, d in zip(ys, dlps)], [res[i].as_dict() for i in range(k)]
 
 
 def time_kernels_batch(lps, params: PdlpParams | None = None, reps: int = 20) -> dict:

@@ -190,7 +190,8 @@ struct TileSet {
   int n;                 // items
   const int* item0;      // [count + 1] first item of each LP
   const int* lng0;       // [count + 1] first long-row slot of each LP
-  float2* part;          // [n] per-(block, LP) partial sums, in the slot of the run's first item
+  float2* part;          // [n x kWarps] per-(block, LP) partial sums of each warp, in the slot
+                         // of the run's first item
   float2* rowpart;       // [n] a slice's partial row sum(s)
   float2* lterm;         // [long rows] a finished long row's partial-sum terms
   int* ticket;           // [n] slices done, in the slot of a row's first slice (0 between launches)

@@ -60,16 +60,9 @@ cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_
 cudaError_t launch_iter_bf16(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_pat(int which, int lanes, const IterRaw& r, cudaStream_t s);
 
-// The float64 candidates of one column (or row) of a KKT check side by side, so
-// that a gathered entry is one 32-byte sector: c current, a average, r ray
-// (0 unless the certificate test needs it), unscaled.
-struct alignas(32) Cand {
-  double c, a, r, pad;
-};
-
 struct KktRaw {
   const int *a_ptr, *a_col;
-  const double* a_val64;  // raw canonical K (NULL = every value +1)
+  const double* a_val64;  // raw canonical K (NULL: every value is +1, the pattern mode)
   const int *t_ptr, *t_col;
   const double* t_val64;
   const int *a_long, *t_long;
@@ -80,8 +73,13 @@ struct KktRaw {
   const unsigned char* bflags;             // per column: bit 0 l finite, bit 1 u finite
   const unsigned char* row_kind;           // 0 >=-row, 1 =-row, 2 <=-row flipped to >=
   void *x[2], *y[2], *sum_x, *sum_y;       // iterates (float or double; x as (x_j, dx_j) pairs)
-  Cand *XG, *YG;    // candidates per column / row; the ray slot holds x - x_last, y - y_last
-                    // projected onto the recession cone of [l, u] and onto Y
+  // the float64 candidates of each column / row of a KKT check, unscaled:
+  // (current, average) side by side, so a gathered entry is one 16-byte load; the
+  // certificate rays x - x_last, y - y_last (projected onto the recession cone of
+  // [l, u] and onto Y) in arrays of their own, written and read only when the
+  // certificate test needs them (XR with rays = 2, YR with rays >= 1)
+  double2 *XG, *YG;
+  double *XR, *YR;
   double *Xl, *Yl;  // unscaled restart anchors
   double* chk_pts;  // [chk_cap x n] current point of the last checks (NULL: not kept)
   long long chk_cap;

@@ -566,12 +566,12 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
   T a = 0, b0 = 0, b1 = 0;
   if (std::is_same<T, float>::value && d.tile) {
     // tile kernels: one slot per (block, LP) run -- the LP's first min(items, grid)
-    // item slots -- and one per long row
+    // item slots, one entry per warp -- and one per long row
     const int i0 = d.tt.item0[k], i1 = min(d.tt.item0[k + 1], i0 + d.grid_tt);
-    for (int i = i0 + threadIdx.x; i < i1; i += kBlock) a += (T)d.tt.part[i].x;
+    for (int i = i0 * kWarps + threadIdx.x; i < i1 * kWarps; i += kBlock) a += (T)d.tt.part[i].x;
     for (int i = d.tt.lng0[k] + threadIdx.x; i < d.tt.lng0[k + 1]; i += kBlock) a += (T)d.tt.lterm[i].x;
     const int j0 = d.ta.item0[k], j1 = min(d.ta.item0[k + 1], j0 + d.grid_ta);
-    for (int i = j0 + threadIdx.x; i < j1; i += kBlock) {
+    for (int i = j0 * kWarps + threadIdx.x; i < j1 * kWarps; i += kBlock) {
       const float2 v = d.ta.part[i];
       b0 += (T)v.x;
       b1 += (T)v.y;

@@ -30,15 +30,9 @@ namespace {
 // divides where the definition divides), the block's reciprocal otherwise
 #define avg_of(sum, sw, isw) (std::is_same<T, double>::value ? (sum) / (sw) : (sum) * (isw))
 
-// (current, average) and the ray of a candidate entry: one 16-byte load for the
-// pair, the ray from the second half of the same 32-byte sector (ordinary loads:
-// the vectors are written by the preceding kernel of the same chain)
-__device__ __forceinline__ double2 cand2(const Cand* g, long long i) {
-  return reinterpret_cast<const double2*>(g)[2 * i];
-}
-__device__ __forceinline__ double cand_r(const Cand* g, long long i) {
-  return reinterpret_cast<const double2*>(g)[2 * i + 1].x;
-}
+// (current, average) of a candidate entry: one 16-byte load (ordinary loads: the
+// vectors are written by the preceding kernel of the same chain)
+__device__ __forceinline__ double2 cand2(const double2* g, long long i) { return g[i]; }
 
 // columns and rows of one LP for the elementwise kernels (prep, apply, output)
 struct ESpan {
@@ -83,9 +77,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
       if (f & 1u) d = fmax(d, 0.0);
       if (f & 2u) d = fmin(d, 0.0);
     }
-    double2* g = reinterpret_cast<double2*>(r.XG + j);
-    g[0] = make_double2(Xc, fmin(fmax(s * xa, r.l[j]), r.u[j]));
-    g[1] = make_double2(d, 0.0);
+    r.XG[j] = make_double2(Xc, fmin(fmax(s * xa, r.l[j]), r.u[j]));
+    if (r.rays == 2) r.XR[j] = d;
     if (r.chk_pts && !st->init_pending)  // row (completed checks) mod capacity
       r.chk_pts[(size_t)(st->checks % r.chk_cap) * (size_t)r.n + (size_t)j] = Xc;
   }
@@ -99,9 +92,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
       d = Yc - r.Yl[i];
       if (r.row_kind[i] != 1) d = fmax(d, 0.0);
     }
-    double2* g = reinterpret_cast<double2*>(r.YG + i);
-    g[0] = make_double2(Yc, s * ya);
-    g[1] = make_double2(d, 0.0);
+    r.YG[i] = make_double2(Yc, s * ya);
+    if (r.rays) r.YR[i] = d;
   }
 }
 
@@ -126,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
     const int j = __ldg(r.a_col + p);
     const double2 x2 = cand2(r.XG, j);
     if constexpr (RAYS == 2)
-      return D3{v * x2.x, v * x2.y, v * cand_r(r.XG, j)};
+      return D3{v * x2.x, v * x2.y, v * r.XR[j]};
     else
       return D2{v * x2.x, v * x2.y};
   };
@@ -152,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
       acc[8] += rr * rr;
     }
     if constexpr (RAYS >= 1) {
-      const double qy = q * cand_r(r.YG, i);
+      const double qy = q * r.YR[i];
       acc[9] += qy;
       acc[10] += fabs(qy);
     }
@@ -186,7 +178,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
     const int i = __ldg(r.t_col + p);
     const double2 y2 = cand2(r.YG, i);
     if constexpr (RAYS)
-      return D3{v * y2.x, v * y2.y, v * cand_r(r.YG, i)};
+      return D3{v * y2.x, v * y2.y, v * r.YR[i]};
     else
       return D2{v * y2.x, v * y2.y};
   };
@@ -223,7 +215,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
       if constexpr (RAYS == 2) {
         const double rd = pos ? (lfin ? 0.0 : lam) : (ufin ? 0.0 : -lam);
         acc[10] += rd * rd;
-        const double cx = c * cand_r(r.XG, j);
+        const double cx = c * r.XR[j];
         acc[13] += cx;
         acc[14] += fabs(cx);
       }
@@ -433,7 +425,7 @@ __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, doub
     const double l = r.l[j], u = r.u[j];
     const double2 x2 = cand2(r.XG, j);
     const double xc = fmin(fmax(x2.x, l), u), xa = fmin(fmax(x2.y, l), u);
-    if (x_out) x_out[j] = x_ray ? cand_r(r.XG, j) : ua ? xa : xc;
+    if (x_out) x_out[j] = x_ray ? r.XR[j] : ua ? xa : xc;
     if (x_cur) x_cur[j] = xc;
     if (x_avg) x_avg[j] = xa;
   }
@@ -441,7 +433,7 @@ __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, doub
     const double s = r.row_kind[i] == 2 ? -1.0 : 1.0;
     const double2 y2 = cand2(r.YG, i);
     const double yc = s * y2.x, ya = s * y2.y;
-    if (y_out) y_out[i] = y_ray ? s * cand_r(r.YG, i) : ua ? ya : yc;
+    if (y_out) y_out[i] = y_ray ? s * r.YR[i] : ua ? ya : yc;
     if (y_cur) y_cur[i] = yc;
     if (y_avg) y_avg[i] = ya;
   }

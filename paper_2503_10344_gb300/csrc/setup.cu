@@ -994,4 +994,150 @@ cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0
   return cudaSuccess;
 }
 
+// ------------------------------------------------------------------ batches
+namespace {
+
+// One LP of a batch: its arrays (device) and its first global row, column and
+// nonzero in the block-diagonal problem.
+__global__ void k_batch_ingest(const BatchLp* lps, int64_t* rp_g, int* col_g, double* val_g,
+                               double* b_g, char* sense_g, double* c_g, double* l_g, double* u_g,
+                               int* err) {
+  const BatchLp L = lps[blockIdx.y];
+  const int k = blockIdx.y;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int e = 0;
+  for (long long i = t0; i <= L.m; i += stride) {
+    const int64_t v = L.rp[i];
+    if (i < L.m) {
+      const int64_t w = L.rp[i + 1];
+      if (v < 0 || w < v || w > L.nnz) e |= ERR_ROWPTR;
+      const char sn = L.sense[i];
+      if (sn != 'L' && sn != 'G' && sn != 'E') e |= ERR_SENSE;
+      const double bi = L.b[i];
+      if (!isfinite(bi)) e |= ERR_NONFINITE;
+      b_g[L.R + i] = bi;
+      sense_g[L.R + i] = sn;
+    }
+    if ((i == 0 && v != 0) || (i == L.m && v != L.nnz)) e |= ERR_ROWPTR;
+    rp_g[L.R + i] = L.Z + v;  // the next LP writes the same value at its first row
+  }
+  for (long long p = t0; p < L.nnz; p += stride) {
+    const int j = L.col[p];
+    const double v = L.val[p];
+    if (j < 0 || j >= L.n) e |= ERR_COL;
+    if (!isfinite(v)) e |= ERR_NONFINITE;
+    col_g[L.Z + p] = (int)L.C + j;
+    val_g[L.Z + p] = v;
+  }
+  for (long long j = t0; j < L.n; j += stride) {
+    const double cj = L.c[j], lj = L.l[j], uj = L.u[j];
+    if (!isfinite(cj)) e |= ERR_NONFINITE;
+    if (isnan(lj) || isnan(uj) || lj > uj || lj == INFINITY || uj == -INFINITY) e |= ERR_BOUNDS;
+    c_g[L.C + j] = cj;
+    l_g[L.C + j] = lj;
+    u_g[L.C + j] = uj;
+  }
+  if (e) atomicOr(err + k, e);
+}
+
+// The A3 scalars of each LP (one block per LP), as k_iter_vectors and k_absmax_scaled
+// take them for one LP: out[8 k + ...] = ||c~||, ||q~||, ||c||, ||q||, max |K~_ij|, 0, 0,
+// columns with an infinite bound.
+__global__ void k_batch_scalars(const BatchLp* lps, const double* dr, const double* dc,
+                                const double* c, const double* l, const double* u,
+                                const double* q, const int* a_ptr, const int* a_col,
+                                const double* a_val64, double* out) {
+  const BatchLp L = lps[blockIdx.x];
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (long long j = L.C + threadIdx.x; j < L.C + L.n; j += blockDim.x) {
+    const double d = dc[j], cj = c[j];
+    acc[0] += (d * cj) * (d * cj);
+    acc[2] += cj * cj;
+    acc[6] += (isfinite(l[j]) && isfinite(u[j])) ? 0.0 : 1.0;
+  }
+  for (long long i = L.R + threadIdx.x; i < L.R + L.m; i += blockDim.x) {
+    const double d = dr[i], qi = q[i];
+    acc[1] += (d * qi) * (d * qi);
+    acc[3] += qi * qi;
+  }
+  double mx = 0.0;
+  const int lane = threadIdx.x & 31;
+  for (long long r = L.R + (threadIdx.x >> 5); r < L.R + L.m; r += blockDim.x / 32) {
+    const int s = a_ptr[r], e = a_ptr[r + 1];
+    for (int p = s + lane; p < e; p += 32) mx = fmax(mx, fabs((dr[r] * a_val64[p]) * dc[a_col[p]]));
+  }
+  double r7[7];
+  block_sum<7>(acc, r7);
+  __shared__ double sh[kWarps];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kWarps; ++w) mx = fmax(mx, sh[w]);
+    double* o = out + 8 * (size_t)blockIdx.x;
+    o[0] = sqrt(r7[0]);
+    o[1] = sqrt(r7[1]);
+    o[2] = sqrt(r7[2]);
+    o[3] = sqrt(r7[3]);
+    o[4] = mx;
+    o[5] = 0.0;
+    o[6] = 0.0;
+    o[7] = r7[6];
+  }
+}
+
+// counts[k] = entries of `pos` (an exclusive scan over global rows) before LP k's first row
+__global__ void k_batch_bounds(const BatchLp* lps, int count, int over_cols, int R,
+                               const int* pos, int* out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= count; k += gridDim.x * blockDim.x) {
+    const long long r = k == count ? R : (over_cols ? lps[k].C : lps[k].R);
+    out[k] = pos[r];
+  }
+}
+
+}  // namespace
+
+cudaError_t setup_batch_ingest(const BatchLp* d_lps, int count, long long max_rows_nnz_cols,
+                               int64_t* rp_g, int* col_g, double* val_g, double* b_g,
+                               char* sense_g, double* c_g, double* l_g, double* u_g, int* d_err,
+                               cudaStream_t s) {
+  RET(cudaMemsetAsync(d_err, 0, sizeof(int) * (size_t)count, s));
+  if (count == 0) return cudaSuccess;
+  const int per_lp = (int)std::min<long long>(64, std::max<long long>(1, (max_rows_nnz_cols + kBlock - 1) / kBlock));
+  dim3 grid((unsigned)per_lp, (unsigned)count);
+  k_batch_ingest<<<grid, kBlock, 0, s>>>(d_lps, rp_g, col_g, val_g, b_g, sense_g, c_g, l_g, u_g,
+                                         d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_batch_scalars(const BatchLp* d_lps, int count, const double* dr,
+                                const double* dc, const double* c, const double* l,
+                                const double* u, const double* q, const int* a_ptr,
+                                const int* a_col, const double* a_val64, double* out,
+                                cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_batch_scalars<<<count, kBlock, 0, s>>>(d_lps, dr, dc, c, l, u, q, a_ptr, a_col, a_val64, out);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_batch_long_rows(const int* ptr, int R, int thresh, const BatchLp* d_lps,
+                                  int count, int over_cols, int* flags, int* pos, int* bsum,
+                                  int* list, int* d_bounds, cudaStream_t s) {
+  const int G = device_sm_count() * 8;
+  if (R > 0) {
+    k_long_flags<<<grid_for(R, G), kBlock, 0, s>>>(ptr, R, thresh, flags);
+    RET(cudaGetLastError());
+  }
+  RET(exclusive_scan(flags, pos, R, bsum, s));
+  if (R > 0) {
+    k_long_scatter<<<grid_for(R, G), kBlock, 0, s>>>(flags, pos, R, list);
+    RET(cudaGetLastError());
+  }
+  k_batch_bounds<<<grid_for(count + 1, G), kBlock, 0, s>>>(d_lps, count, over_cols, R, pos,
+                                                            d_bounds);
+  return cudaGetLastError();
+}
+
 }  // namespace pdlp

@@ -88,4 +88,38 @@ cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0
                         int* tmp, TileItem* items, int* item0, int* lng0, int* ticket,
                         size_t item_cap, int* h_counts, int* W_out, cudaStream_t s);
 
+// ---- batches: many LPs set up together as one block-diagonal problem
+// One LP of a batch: its arrays (device) and its first global row, column and
+// nonzero.
+struct BatchLp {
+  const int64_t* rp;
+  const int32_t* col;
+  const double* val;
+  const double* b;
+  const char* sense;
+  const double *c, *l, *u;
+  int m, n;
+  long long nnz;
+  long long R, C, Z;
+};
+// Validates every LP (error bits per LP into d_err[count]) and writes the batch in
+// global numbering: int64 row pointers rp_g[M + 1], column indices shifted by each
+// LP's first column, values, b, senses, c, l, u.
+cudaError_t setup_batch_ingest(const BatchLp* d_lps, int count, long long max_rows_nnz_cols,
+                               int64_t* rp_g, int* col_g, double* val_g, double* b_g,
+                               char* sense_g, double* c_g, double* l_g, double* u_g, int* d_err,
+                               cudaStream_t s);
+// The A3 scalars of every LP: out[8 count] as setup_iter_vectors' scalars_out
+// (hint norms 0).
+cudaError_t setup_batch_scalars(const BatchLp* d_lps, int count, const double* dr,
+                                const double* dc, const double* c, const double* l,
+                                const double* u, const double* q, const int* a_ptr,
+                                const int* a_col, const double* a_val64, double* out,
+                                cudaStream_t s);
+// The global list of rows longer than thresh and each LP's first entry of it
+// (d_bounds[count + 1]); over_cols: the rows are the LPs' columns (A^T).
+cudaError_t setup_batch_long_rows(const int* ptr, int R, int thresh, const BatchLp* d_lps,
+                                  int count, int over_cols, int* flags, int* pos, int* bsum,
+                                  int* list, int* d_bounds, cudaStream_t s);
+
 }  // namespace pdlp

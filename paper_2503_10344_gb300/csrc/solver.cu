@@ -87,7 +87,8 @@ struct Bufs {
   double *a_val64, *t_val64;
   void *a_valit, *t_valit;
   double *q64, *dr, *dc, *Xl, *Yl, *stat_r, *stat_c, *inv_dr, *inv_dc;
-  Cand *XG, *YG;
+  double2 *XG, *YG;
+  double *XR, *YR;
   unsigned char *row_kind, *bflags;
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
@@ -133,9 +134,11 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.q64 = (double*)ar.take(8 * M);
   b.dr = (double*)ar.take(8 * M);
   b.dc = (double*)ar.take(8 * N);
-  b.XG = (Cand*)ar.take(sizeof(Cand) * N);
+  b.XG = (double2*)ar.take(16 * N);
+  b.XR = (double*)ar.take(8 * N);
   b.Xl = (double*)ar.take(8 * N);
-  b.YG = (Cand*)ar.take(sizeof(Cand) * M);
+  b.YG = (double2*)ar.take(16 * M);
+  b.YR = (double*)ar.take(8 * M);
   b.Yl = (double*)ar.take(8 * M);
   b.stat_r = (double*)ar.take(8 * M);
   b.stat_c = (double*)ar.take(8 * N);
@@ -174,8 +177,10 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
     b.tcap_t = tile_item_cap(n, nnz, 1);
     b.ti_a = (TileItem*)ar.take(sizeof(TileItem) * b.tcap_a);
     b.ti_t = (TileItem*)ar.take(sizeof(TileItem) * b.tcap_t);
-    for (float2** v : {&b.tpart_a, &b.trow_a, &b.tlong_a}) *v = (float2*)ar.take(8 * b.tcap_a);
-    for (float2** v : {&b.tpart_t, &b.trow_t, &b.tlong_t}) *v = (float2*)ar.take(8 * b.tcap_t);
+    b.tpart_a = (float2*)ar.take(8 * kWarps * b.tcap_a);
+    b.tpart_t = (float2*)ar.take(8 * kWarps * b.tcap_t);
+    for (float2** v : {&b.trow_a, &b.tlong_a}) *v = (float2*)ar.take(8 * b.tcap_a);
+    for (float2** v : {&b.trow_t, &b.tlong_t}) *v = (float2*)ar.take(8 * b.tcap_t);
     b.tick_a = (int*)ar.take(4 * b.tcap_a);
     b.tick_t = (int*)ar.take(4 * b.tcap_t);
     b.tlp_a = (int*)ar.take(4 * 4);
@@ -773,8 +778,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
 
   KktRaw kr{};
   kr.count = 1;
-  kr.a_ptr = bf.a_ptr; kr.a_col = bf.a_col; kr.a_val64 = bf.a_val64;
-  kr.t_ptr = bf.t_ptr; kr.t_col = bf.t_col; kr.t_val64 = bf.t_val64;
+  kr.a_ptr = bf.a_ptr; kr.a_col = bf.a_col; kr.a_val64 = mode == MODE_PAT ? nullptr : bf.a_val64;
+  kr.t_ptr = bf.t_ptr; kr.t_col = bf.t_col; kr.t_val64 = mode == MODE_PAT ? nullptr : bf.t_val64;
   kr.a_long = bf.a_long; kr.t_long = bf.t_long;
   kr.a_nlong = nlong_a; kr.t_nlong = nlong_t; kr.a_thresh = th_a; kr.t_thresh = th_t;
   kr.m = m; kr.n = n;
@@ -783,7 +788,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   kr.row_kind = bf.row_kind;
   for (int k = 0; k < 2; ++k) { kr.x[k] = bf.x[k]; kr.y[k] = bf.y[k]; }
   kr.sum_x = bf.sum_x; kr.sum_y = bf.sum_y;
-  kr.XG = bf.XG; kr.Xl = bf.Xl; kr.YG = bf.YG; kr.Yl = bf.Yl;
+  kr.XG = bf.XG; kr.Xl = bf.Xl; kr.YG = bf.YG; kr.Yl = bf.Yl; kr.XR = bf.XR; kr.YR = bf.YR;
   if (dg && dg->point_capacity > 0 && dg->check_points) {
     kr.chk_pts = dg->check_points;
     kr.chk_cap = dg->point_capacity;
@@ -1271,7 +1276,8 @@ static int time_kernels_after_setup(Solve& sv, DevState* st, int mode, long long
   tq.bytes[2] = tq.bytes[0] + tq.bytes[1];
   // certificate terms: the dual ray (rays >= 1) and the primal ray (rays == 2)
   const double ry = sv.kr.rays >= 1 ? 8 : 0, rx = sv.kr.rays == 2 ? 8 : 0;
-  // KKT over A: row_ptr, col, float64 values; x candidates gathered (and the primal ray);
+  // KKT over A: row_ptr, col, float64 values (none for a pattern); x candidates
+  // gathered (and the primal ray);
   // q, D_r, 1/D_r, kind, y candidates (and the dual ray), y anchor
   tq.bytes[3] = 4 * (M + 1) + Z * (4 + val64) + N * (16 + rx) + M * (8 + 8 + 8 + 1 + 16 + ry + 8);
   // KKT over A^T: row_ptr, col, values; y candidates gathered (and the dual ray); c, l, u,
@@ -1346,52 +1352,38 @@ static Tables tables_at(int* dev, int grid, int K) {
   return t;
 }
 
+// device_inputs: the LPs' arrays and the outputs are device buffers and the work runs
+// on `user_stream`; otherwise host buffers, uploaded on a stream of the call's own.
 static int solve_batch(int count, const pdlp_csr* const* A, const double* const* b,
                        const char* const* sense, const double* const* c, const double* const* l,
                        const double* const* u, const pdlp_params* p, double* const* x_out,
-                       double* const* y_out, pdlp_result* res, const TimingReq* tq = nullptr) {
+                       double* const* y_out, pdlp_result* res, const TimingReq* tq = nullptr,
+                       bool device_inputs = false, cudaStream_t user_stream = nullptr) {
   g_launches = 0;
   const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t s;
-  CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaStream_t s = user_stream;
+  if (!device_inputs) CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   struct SFree {
     cudaStream_t s;
-    ~SFree() { cudaStreamDestroy(s); }
-  } sfree{s};
+    bool own;
+    ~SFree() {
+      if (own) cudaStreamDestroy(s);
+    }
+  } sfree{s, !device_inputs};
   // ---- shapes and global numbering
   std::vector<LpShape> sh(count);
   long long M = 0, N = 0, Z = 0;
-  int mmax = 0, nmax = 0;
-  long long zmax = 0;
   for (int k = 0; k < count; ++k) {
     sh[k] = {A[k]->m, A[k]->n, A[k]->nnz, M, N, Z};
     M += A[k]->m;
     N += A[k]->n;
     Z += A[k]->nnz;
-    mmax = std::max(mmax, A[k]->m);
-    nmax = std::max(nmax, A[k]->n);
-    zmax = std::max(zmax, (long long)A[k]->nnz);
   }
   if (M >= INT32_MAX || N >= INT32_MAX || Z >= INT32_MAX)
     return fail(PDLP_ERR_INVALID_INPUT, "a batch must have fewer than 2^31 rows, columns and nonzeros");
-  // ---- one mode and one set of lanes for the whole batch (one kernel instantiation)
+  // ---- one mode and one set of lanes for the whole batch (one kernel instantiation);
+  // FP32_BF16A settles on the pattern / bfloat16 form after the canonical form, on the device
   int mode = p->precision == PDLP_FP64 ? MODE_FP64 : MODE_FP32;
-  if (p->precision == PDLP_FP32_BF16A) {
-    bool all_one = true, bf16 = true;
-    for (int k = 0; k < count; ++k)
-      for (int i = 0; i < A[k]->m; ++i) {
-        const double sg = sense[k][i] == 'L' ? -1.0 : 1.0;
-        for (int64_t q = A[k]->row_ptr[i]; q < A[k]->row_ptr[i + 1]; ++q) {
-          const double v = sg * A[k]->val[q];
-          all_one = all_one && v == 1.0;
-          const float f = (float)v;
-          uint32_t bits;
-          memcpy(&bits, &f, 4);
-          bf16 = bf16 && (double)f == v && (bits & 0xffffu) == 0;
-        }
-      }
-    mode = all_one ? MODE_PAT : (bf16 ? MODE_BF16 : MODE_FP32);
-  }
   const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
   const double avg_a = M ? (double)Z / (double)M : 1.0, avg_t = N ? (double)Z / (double)N : 1.0;
   // a float32 batch whose step data is well beyond L2 streams from HBM, where the dual
@@ -1407,33 +1399,39 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
                   p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane),
                   p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0),
                   p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0)};
-  // ---- per-LP scratch (inputs and a single-LP workspace, sized for the largest LP)
   const size_t eb = mode == MODE_FP64 ? 8 : 4;
-  const size_t vb = mode == MODE_FP64 ? 8 : mode == MODE_FP32 ? 4 : mode == MODE_BF16 ? 2 : 0;
-  Bufs one;
-  Arena dry{nullptr, 0};
-  const size_t one_bytes = carve(dry, one, mmax, std::max(nmax, 1), zmax, p->precision);
-  const size_t in_bytes = 8 * ((size_t)mmax + 1) + 12 * (size_t)zmax + 9 * (size_t)mmax +
-                          24 * (size_t)nmax + 8 * 256;
+  const size_t vb = mode == MODE_FP64 ? 8 : 4;  // bound: bfloat16 (2) / pattern (0) fit
+  const long long RM = std::max(M, N) + 1;
+  const size_t tmp_ints = std::max(std::max(transpose_tmp_ints((int)M, (int)N, Z),
+                                            2 * (size_t)RM + scan_tmp_ints(RM)),
+                                   tile_tmp_ints((int)std::max(M, N)));
   // ---- global arrays
   struct G {
     int *a_ptr, *a_col, *t_ptr, *t_col, *a_long, *t_long, *tabA, *tabT;
     double *a_val64, *t_val64, *q64, *dr, *dc, *inv_dr, *inv_dc, *Xl, *Yl;
-    Cand *XG, *YG;
+    double2 *XG, *YG;
+    double *XR, *YR;
     double *c64, *l64, *u64, *part_p, *part_d, *part_r, *part_c, *x_out, *y_out;
     void *a_valit, *t_valit, *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
     unsigned char *row_kind, *bflags;
     DevState* st;
     FacTable* fac;
+    // batched setup: the batch in global numbering as the callers gave it, scratch
+    int64_t *rp_in, *rp_up;
+    int* col_in;
+    double *val_in, *b_in, *stat_r, *stat_c, *part_setup, *scalars, *lpsca;
+    char* sense_in;
+    int *tmp, *flags2, *errs, *lb_a, *lb_t;
+    BatchLp* lps;
     // staged tile kernels over the block-diagonal A and A^T
     TileItem *ti_a, *ti_t;
     float2 *tpart_a, *tpart_t, *trow_a, *trow_t, *tlong_a, *tlong_t;
-    int *tick_a, *tick_t, *tlp_a, *tlp_t, *row0_a, *row0_t, *ttmp;
+    int *tick_a, *tick_t, *tlp_a, *tlp_t, *row0_a, *row0_t;
   } g{};
   const bool use_tiles = mode != MODE_FP64 && p->tiles && !p->persistent;
   const size_t tcap_a = use_tiles ? tile_item_cap((int)M, Z, count) : 0;
   const size_t tcap_t = use_tiles ? tile_item_cap((int)N, Z, count) : 0;
-  // long rows and launch maps need the per-LP setups first: upper bounds here
+  // long rows and launch maps need the setup first: upper bounds here
   const int MB = max_blocks();
   const int budget = 4 * MB;
   const size_t gmax = (size_t)budget + (size_t)count * (kMaxLongBlocks + 2);
@@ -1447,12 +1445,16 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.t_val64 = (double*)ar.take(8 * Z);
     g.a_valit = ar.take(vb * Z);
     g.t_valit = ar.take(vb * Z);
-    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yl, &g.y_out}) *v = (double*)ar.take(8 * M);
-    g.YG = (Cand*)ar.take(sizeof(Cand) * M);
-    g.XG = (Cand*)ar.take(sizeof(Cand) * N);
-    for (double** v : {&g.dc, &g.inv_dc, &g.Xl, &g.c64, &g.l64, &g.u64, &g.x_out})
+    for (double** v : {&g.q64, &g.dr, &g.inv_dr, &g.Yl, &g.y_out, &g.b_in, &g.stat_r})
+      *v = (double*)ar.take(8 * M);
+    g.YG = (double2*)ar.take(16 * M);
+    g.XG = (double2*)ar.take(16 * N);
+    g.YR = (double*)ar.take(8 * M);
+    g.XR = (double*)ar.take(8 * N);
+    for (double** v : {&g.dc, &g.inv_dc, &g.Xl, &g.c64, &g.l64, &g.u64, &g.x_out, &g.stat_c})
       *v = (double*)ar.take(8 * N);
     g.row_kind = (unsigned char*)ar.take(M);
+    g.sense_in = (char*)ar.take(M);
     g.bflags = (unsigned char*)ar.take(N);
     for (void** v : {&g.c_it, &g.l_it, &g.u_it, &g.tw, &g.sum_x}) *v = ar.take(eb * N);
     for (void** v : {&g.q_it, &g.sw, &g.sum_y}) *v = ar.take(eb * M);
@@ -1469,22 +1471,35 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g.tabA = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.tabT = (int*)ar.take(4 * (gmax + 7 * (size_t)count));
     g.st = (DevState*)ar.take(sizeof(DevState) * count);
+    g.rp_in = (int64_t*)ar.take(8 * (M + 1));
+    g.rp_up = device_inputs ? nullptr : (int64_t*)ar.take(8 * (M + (size_t)count));
+    g.col_in = (int*)ar.take(4 * Z);
+    g.val_in = (double*)ar.take(8 * Z);
+    g.part_setup = (double*)ar.take(8 * setup_part_doubles((int)M, (int)N));
+    g.scalars = (double*)ar.take(8 * 8);
+    g.lpsca = (double*)ar.take(8 * 8 * (size_t)count);
+    g.tmp = (int*)ar.take(4 * tmp_ints);
+    g.flags2 = (int*)ar.take(16);
+    g.errs = (int*)ar.take(4 * (size_t)count);
+    g.lb_a = (int*)ar.take(4 * ((size_t)count + 1));
+    g.lb_t = (int*)ar.take(4 * ((size_t)count + 1));
+    g.lps = (BatchLp*)ar.take(sizeof(BatchLp) * (size_t)count);
     if (use_tiles) {
       g.ti_a = (TileItem*)ar.take(sizeof(TileItem) * tcap_a);
       g.ti_t = (TileItem*)ar.take(sizeof(TileItem) * tcap_t);
-      for (float2** v : {&g.tpart_a, &g.trow_a, &g.tlong_a}) *v = (float2*)ar.take(8 * tcap_a);
-      for (float2** v : {&g.tpart_t, &g.trow_t, &g.tlong_t}) *v = (float2*)ar.take(8 * tcap_t);
+      g.tpart_a = (float2*)ar.take(8 * kWarps * tcap_a);
+      g.tpart_t = (float2*)ar.take(8 * kWarps * tcap_t);
+      for (float2** v : {&g.trow_a, &g.tlong_a}) *v = (float2*)ar.take(8 * tcap_a);
+      for (float2** v : {&g.trow_t, &g.tlong_t}) *v = (float2*)ar.take(8 * tcap_t);
       g.tick_a = (int*)ar.take(4 * tcap_a);
       g.tick_t = (int*)ar.take(4 * tcap_t);
       for (int** v : {&g.tlp_a, &g.tlp_t}) *v = (int*)ar.take(4 * 2 * ((size_t)count + 1));
       for (int** v : {&g.row0_a, &g.row0_t}) *v = (int*)ar.take(4 * ((size_t)count + 1));
-      g.ttmp = (int*)ar.take(4 * tile_tmp_ints((int)std::max(M, N)));
     }
-    one.fac = nullptr;
   };
   Arena gdry{nullptr, 0};
   lay(gdry);
-  const size_t total = gdry.off + 256 + one_bytes + 256 + in_bytes + 256;
+  const size_t total = gdry.off + 256;
   void* dev = nullptr;
   {
     cudaError_t e = cudaMallocAsync(&dev, total, s);
@@ -1500,98 +1515,157 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   } dfree{dev, s};
   Arena gar{(char*)dev, 0};
   lay(gar);
-  char* one_base = (char*)dev + ((gdry.off + 255) & ~(size_t)255) + 256;
-  one_base = (char*)(((uintptr_t)one_base + 255) & ~(uintptr_t)255);
-  Arena oar{one_base, 0};
-  carve(oar, one, mmax, std::max(nmax, 1), zmax, p->precision);
-  char* in_base = (char*)(((uintptr_t)(one_base + one_bytes) + 255) & ~(uintptr_t)255);
-  // ---- set up every LP and export it into the global numbering
-  std::vector<DevState> hs(count);
-  std::vector<int> nlong_a(count), nlong_t(count), long0_a(count), long0_t(count);
-  int th_a = 0, th_t = 0;
-  bool any_unboxed = false;  // some LP has a column with an infinite bound
-  long long la_total = 0, lt_total = 0;
   const FacTable& ft = fac_table();
   CUDA_TRY(cudaMemcpyAsync(g.fac, &ft, sizeof(FacTable), cudaMemcpyHostToDevice, s));
+  // ---- the batch in global numbering (A0 preconditions checked per LP on the way)
+  std::vector<BatchLp> hl(count);
   for (int k = 0; k < count; ++k) {
-    const int m = sh[k].m, n = sh[k].n;
-    const long long z = sh[k].nnz;
-    Arena iar{in_base, 0};
-    int64_t* d_rp = (int64_t*)iar.take(8 * ((size_t)m + 1));
-    int32_t* d_col = (int32_t*)iar.take(4 * (size_t)z);
-    double* d_val = (double*)iar.take(8 * (size_t)z);
-    double* d_b = (double*)iar.take(8 * (size_t)m);
-    char* d_sense = (char*)iar.take((size_t)m);
-    double* d_c = (double*)iar.take(8 * (size_t)n);
-    double* d_l = (double*)iar.take(8 * (size_t)n);
-    double* d_u = (double*)iar.take(8 * (size_t)n);
-    CUDA_TRY(cudaMemcpyAsync(d_rp, A[k]->row_ptr, 8 * ((size_t)m + 1), cudaMemcpyHostToDevice, s));
-    if (z) {
-      CUDA_TRY(cudaMemcpyAsync(d_col, A[k]->col, 4 * (size_t)z, cudaMemcpyHostToDevice, s));
-      CUDA_TRY(cudaMemcpyAsync(d_val, A[k]->val, 8 * (size_t)z, cudaMemcpyHostToDevice, s));
-    }
-    if (m) {
-      CUDA_TRY(cudaMemcpyAsync(d_b, b[k], 8 * (size_t)m, cudaMemcpyHostToDevice, s));
-      CUDA_TRY(cudaMemcpyAsync(d_sense, sense[k], (size_t)m, cudaMemcpyHostToDevice, s));
-    }
-    CUDA_TRY(cudaMemcpyAsync(d_c, c[k], 8 * (size_t)n, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(d_l, l[k], 8 * (size_t)n, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(d_u, u[k], 8 * (size_t)n, cudaMemcpyHostToDevice, s));
-    pdlp_csr dA{m, n, z, d_rp, d_col, d_val};
-    SetupOut so;
-    {
-      const int rc = setup_lp(&dA, d_b, d_sense, d_c, d_l, d_u, p, nullptr, nullptr, one, s, false,
-                              mode, lanes, &so, nullptr, nullptr, [](const char*) {}, false);
-      if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
-    }
-    th_a = so.th_a;
-    th_t = so.th_t;
     const LpShape& q = sh[k];
-    // index arrays in the global numbering
-    CUDA_TRY(setup_offset_copy(g.a_ptr + q.R, one.a_ptr, m, (int)q.Z, s));
-    CUDA_TRY(setup_offset_copy(g.t_ptr + q.C, one.t_ptr, n, (int)q.Z, s));
-    CUDA_TRY(setup_offset_copy(g.a_col + q.Z, one.a_col, z, (int)q.C, s));
-    CUDA_TRY(setup_offset_copy(g.t_col + q.Z, one.t_col, z, (int)q.R, s));
-    nlong_a[k] = so.nlong_a;
-    nlong_t[k] = so.nlong_t;
-    long0_a[k] = (int)la_total;
-    long0_t[k] = (int)lt_total;
-    CUDA_TRY(setup_offset_copy(g.a_long + la_total, one.a_long, so.nlong_a, (int)q.R, s));
-    CUDA_TRY(setup_offset_copy(g.t_long + lt_total, one.t_long, so.nlong_t, (int)q.C, s));
-    la_total += so.nlong_a;
-    lt_total += so.nlong_t;
-    g_launches += 6;
-    auto d2d = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
-      return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
-    };
-    CUDA_TRY(d2d(g.a_val64 + q.Z, one.a_val64, 8 * (size_t)z));
-    CUDA_TRY(d2d(g.t_val64 + q.Z, one.t_val64, 8 * (size_t)z));
-    if (vb) {
-      CUDA_TRY(d2d((char*)g.a_valit + vb * q.Z, one.a_valit, vb * (size_t)z));
-      CUDA_TRY(d2d((char*)g.t_valit + vb * q.Z, one.t_valit, vb * (size_t)z));
+    BatchLp& L = hl[k];
+    L.m = q.m;
+    L.n = q.n;
+    L.nnz = q.nnz;
+    L.R = q.R;
+    L.C = q.C;
+    L.Z = q.Z;
+    if (device_inputs) {
+      L.rp = A[k]->row_ptr;
+      L.col = A[k]->col;
+      L.val = A[k]->val;
+      L.b = b[k];
+      L.sense = sense[k];
+      L.c = c[k];
+      L.l = l[k];
+      L.u = u[k];
+    } else {
+      // host arrays: uploaded straight to their places in the global arrays (row
+      // pointers to a staging array, one slot more per LP); the ingest kernel then
+      // checks them and shifts the indices in place
+      int64_t* rp = g.rp_up + q.R + k;
+      auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+      };
+      CUDA_TRY(up(rp, A[k]->row_ptr, 8 * ((size_t)q.m + 1)));
+      CUDA_TRY(up(g.col_in + q.Z, A[k]->col, 4 * (size_t)q.nnz));
+      CUDA_TRY(up(g.val_in + q.Z, A[k]->val, 8 * (size_t)q.nnz));
+      CUDA_TRY(up(g.b_in + q.R, b[k], 8 * (size_t)q.m));
+      CUDA_TRY(up(g.sense_in + q.R, sense[k], (size_t)q.m));
+      CUDA_TRY(up(g.c64 + q.C, c[k], 8 * (size_t)q.n));
+      CUDA_TRY(up(g.l64 + q.C, l[k], 8 * (size_t)q.n));
+      CUDA_TRY(up(g.u64 + q.C, u[k], 8 * (size_t)q.n));
+      L.rp = rp;
+      L.col = g.col_in + q.Z;
+      L.val = g.val_in + q.Z;
+      L.b = g.b_in + q.R;
+      L.sense = g.sense_in + q.R;
+      L.c = g.c64 + q.C;
+      L.l = g.l64 + q.C;
+      L.u = g.u64 + q.C;
     }
-    CUDA_TRY(d2d(g.q64 + q.R, one.q64, 8 * (size_t)m));
-    CUDA_TRY(d2d(g.dr + q.R, one.dr, 8 * (size_t)m));
-    CUDA_TRY(d2d(g.inv_dr + q.R, one.inv_dr, 8 * (size_t)m));
-    CUDA_TRY(d2d(g.row_kind + q.R, one.row_kind, (size_t)m));
-    CUDA_TRY(d2d(g.dc + q.C, one.dc, 8 * (size_t)n));
-    CUDA_TRY(d2d(g.inv_dc + q.C, one.inv_dc, 8 * (size_t)n));
-    CUDA_TRY(d2d(g.bflags + q.C, one.bflags, (size_t)n));
-    CUDA_TRY(d2d(g.c64 + q.C, d_c, 8 * (size_t)n));
-    CUDA_TRY(d2d(g.l64 + q.C, d_l, 8 * (size_t)n));
-    CUDA_TRY(d2d(g.u64 + q.C, d_u, 8 * (size_t)n));
-    CUDA_TRY(d2d((char*)g.c_it + eb * q.C, one.c_it, eb * (size_t)n));
-    CUDA_TRY(d2d((char*)g.l_it + eb * q.C, one.l_it, eb * (size_t)n));
-    CUDA_TRY(d2d((char*)g.u_it + eb * q.C, one.u_it, eb * (size_t)n));
-    CUDA_TRY(d2d((char*)g.tw + eb * q.C, one.tw, eb * (size_t)n));
-    CUDA_TRY(d2d((char*)g.q_it + eb * q.R, one.q_it, eb * (size_t)m));
-    CUDA_TRY(d2d((char*)g.sw + eb * q.R, one.sw, eb * (size_t)m));
-    CUDA_TRY(d2d((char*)g.x[0] + 2 * eb * q.C, one.x[0], 2 * eb * (size_t)n));
-    CUDA_TRY(d2d((char*)g.y[0] + eb * q.R, one.y[0], eb * (size_t)m));
-    // device state of the LP (the A3 scalars of this LP)
+  }
+  if (!device_inputs) CUDA_TRY(cudaStreamSynchronize(s));
+  const double upload_s =
+      device_inputs ? 0.0 : std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  CUDA_TRY(cudaMemcpyAsync(g.lps, hl.data(), sizeof(BatchLp) * (size_t)count, cudaMemcpyHostToDevice, s));
+  {
+    long long mx = 1;
+    for (const LpShape& q : sh) mx = std::max(mx, std::max((long long)q.m + 1, std::max(q.nnz, (long long)q.n)));
+    CUDA_TRY(setup_batch_ingest(g.lps, count, mx, g.rp_in, g.col_in, g.val_in, g.b_in, g.sense_in,
+                                g.c64, g.l64, g.u64, g.errs, s));
+    ++g_launches;
+    std::vector<int> errs(count);
+    CUDA_TRY(cudaMemcpyAsync(errs.data(), g.errs, 4 * (size_t)count, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < count; ++k)
+      if (errs[k]) {
+        std::string msg = "LP " + std::to_string(k) + ": invalid input:";
+        if (errs[k] & ERR_ROWPTR) msg += " row_ptr";
+        if (errs[k] & ERR_COL) msg += " column index";
+        if (errs[k] & ERR_NONFINITE) msg += " non-finite value";
+        if (errs[k] & ERR_SENSE) msg += " sense";
+        if (errs[k] & ERR_BOUNDS) msg += " bounds";
+        return fail(PDLP_ERR_INVALID_INPUT, msg);
+      }
+  }
+  // ---- A0-A3 over the whole block-diagonal problem: every step treats each row and
+  // column on its own, so each LP is set up exactly as on its own
+  SetupIn gin{(int)M, (int)N, Z, g.rp_in, g.col_in, g.val_in, g.b_in, g.sense_in, g.c64, g.l64, g.u64};
+  CUDA_TRY(setup_canonical(gin, g.a_ptr, g.a_col, g.a_val64, g.q64, g.row_kind, s));
+  CUDA_TRY(setup_transpose((int)M, (int)N, (int)Z, g.a_ptr, g.a_col, g.a_val64, g.t_ptr, g.t_col,
+                           g.t_val64, g.tmp, s, false));
+  g_launches += 11;
+  if (p->precision == PDLP_FP32_BF16A) {
+    int bf16_exact = 0, all_one = 0;
+    CUDA_TRY(setup_value_format(g.a_val64, (int)Z, g.flags2, &bf16_exact, &all_one, s));
+    ++g_launches;
+    mode = all_one ? MODE_PAT : (bf16_exact ? MODE_BF16 : MODE_FP32);
+  }
+  const int scaled = (mode == MODE_FP64 || mode == MODE_FP32) ? 1 : 0;
+  {
+    ScaleIn sc{(int)M, (int)N, g.a_ptr, g.a_col, g.a_val64, g.t_ptr, g.t_col, g.t_val64,
+               p->ruiz_iters, p->pc_alpha, Z};
+    CUDA_TRY(setup_scaling(sc, g.dr, g.dc, g.stat_r, g.stat_c, s));
+    g_launches += 2 + 2 * p->ruiz_iters + (p->pc_alpha >= 0 ? 2 : 0);
+  }
+  CUDA_TRY(setup_kkt_aux((int)M, (int)N, g.dr, g.dc, g.l64, g.u64, g.inv_dr, g.inv_dc, g.bflags, s));
+  ++g_launches;
+  if (mode != MODE_PAT) {
+    const int vt = mode == MODE_FP64 ? 0 : (mode == MODE_FP32 ? 1 : 2);
+    CUDA_TRY(setup_iter_values(vt, g.a_ptr, g.a_col, g.a_val64, (int)M, g.dr, g.dc, 1, scaled,
+                               g.a_valit, s));
+    CUDA_TRY(setup_iter_values(vt, g.t_ptr, g.t_col, g.t_val64, (int)N, g.dc, g.dr, 0, scaled,
+                               g.t_valit, s));
+    g_launches += 2;
+  }
+  {
+    VecIn vi{(int)M, (int)N, g.dr, g.dc, g.c64, g.l64, g.u64, g.q64, g.row_kind, nullptr, nullptr,
+             scaled, nullptr, nullptr};
+    CUDA_TRY(setup_iter_vectors(vi, mode != MODE_FP64, g.c_it, g.l_it, g.u_it, g.q_it, g.tw, g.sw,
+                                g.x[0], g.y[0], g.a_ptr, g.a_col, g.a_val64, g.part_setup,
+                                g.scalars, s));
+    CUDA_TRY(setup_batch_scalars(g.lps, count, g.dr, g.dc, g.c64, g.l64, g.u64, g.q64, g.a_ptr,
+                                 g.a_col, g.a_val64, g.lpsca, s));
+    g_launches += 4;
+  }
+  // long rows: one global list per orientation, each LP's part of it contiguous
+  const int th_a = long_thresh(std::max(lanes[0], lanes[2]));
+  const int th_t = long_thresh(std::max(lanes[1], lanes[3]));
+  std::vector<int> nlong_a(count), nlong_t(count), long0_a(count), long0_t(count);
+  long long la_total = 0, lt_total = 0;
+  {
+    int* flags = g.tmp;
+    int* pos = flags + RM;
+    int* bsum = pos + RM + 1;
+    CUDA_TRY(setup_batch_long_rows(g.a_ptr, (int)M, th_a, g.lps, count, 0, flags, pos, bsum,
+                                   g.a_long, g.lb_a, s));
+    CUDA_TRY(setup_batch_long_rows(g.t_ptr, (int)N, th_t, g.lps, count, 1, flags, pos, bsum,
+                                   g.t_long, g.lb_t, s));
+    g_launches += 10;
+    std::vector<int> lb(2 * ((size_t)count + 1));
+    CUDA_TRY(cudaMemcpyAsync(lb.data(), g.lb_a, 4 * ((size_t)count + 1), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(lb.data() + count + 1, g.lb_t, 4 * ((size_t)count + 1),
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < count; ++k) {
+      long0_a[k] = lb[k];
+      nlong_a[k] = lb[k + 1] - lb[k];
+      long0_t[k] = lb[count + 1 + k];
+      nlong_t[k] = lb[count + 2 + k] - lb[count + 1 + k];
+    }
+    la_total = lb[count];
+    lt_total = lb[2 * count + 1];
+  }
+  // ---- the device state of every LP (the A3 scalars of each LP)
+  std::vector<double> sca(8 * (size_t)count);
+  CUDA_TRY(cudaMemcpyAsync(sca.data(), g.lpsca, 8 * 8 * (size_t)count, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<DevState> hs(count);
+  bool any_unboxed = false;  // some LP has a column with an infinite bound
+  for (int k = 0; k < count; ++k) {
+    const double* so = sca.data() + 8 * (size_t)k;
     DevState& h = hs[k];
     memset(&h, 0, sizeof(h));
-    const double nct = so.sca[0], nqt = so.sca[1], kmax = so.sca[4];
+    const double nct = so[0], nqt = so[1], kmax = so[4];
     h.omega = (nct > 1e-10 && nqt > 1e-10) ? nct / nqt : 1.0;
     h.eta = kmax > 0.0 ? 1.0 / kmax : 1.0;
     if (p->fixed_eta > 0.0) h.eta = p->fixed_eta;
@@ -1607,9 +1681,9 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     h.detect_inf = p->detect_infeasibility ? 1 : 0;
     h.spin_limit = kSpinLimit;
     h.tol = p->tol;
-    h.norm_c = so.sca[2];
-    h.norm_q = so.sca[3];
-    any_unboxed = any_unboxed || so.sca[7] > 0.0;
+    h.norm_c = so[2];
+    h.norm_q = so[3];
+    any_unboxed = any_unboxed || so[7] > 0.0;
     h.inv_omega = 1.0 / h.omega;
     h.tau_d = h.eta / h.omega;
     h.sigma_d = h.eta * h.omega;
@@ -1623,12 +1697,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     h.fac_dec_f = g.fac->dec_f;
     h.fac_inc_f = g.fac->inc_f;
     h.fac_n = kFacN;
-    CUDA_TRY(cudaStreamSynchronize(s));  // the per-LP scratch is reused by the next LP
   }
   {
-    const int zi = (int)Z;
-    CUDA_TRY(cudaMemcpyAsync(g.a_ptr + M, &zi, sizeof(int), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(g.t_ptr + N, &zi, sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(g.sum_x, 0, eb * N, s));
     if (M) CUDA_TRY(cudaMemsetAsync(g.sum_y, 0, eb * M, s));
     CUDA_TRY(cudaMemsetAsync(g.Xl, 0, 8 * N, s));
@@ -1652,7 +1722,6 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   ir.a_long = g.a_long; ir.t_long = g.t_long;
   ir.a_nlong = (int)la_total; ir.t_nlong = (int)lt_total; ir.a_thresh = th_a; ir.t_thresh = th_t;
   ir.m = (int)M; ir.n = (int)N;
-  const int scaled = (mode == MODE_FP64 || mode == MODE_FP32) ? 1 : 0;
   ir.c = g.c_it; ir.l = g.l_it; ir.u = g.u_it; ir.q = g.q_it;
   ir.tw = scaled ? nullptr : g.tw; ir.sw = scaled ? nullptr : g.sw;
   ir.row_kind = g.row_kind;
@@ -1676,9 +1745,9 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     CUDA_TRY(cudaMemcpyAsync(g.row0_a, r0a.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(g.row0_t, r0t.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
     int ca[2] = {0, 0}, ct[2] = {0, 0}, W = 0;
-    CUDA_TRY(setup_tiles(g.a_ptr, (int)M, Z, g.row0_a, count, g.ttmp, g.ti_a, g.tlp_a,
+    CUDA_TRY(setup_tiles(g.a_ptr, (int)M, Z, g.row0_a, count, g.tmp, g.ti_a, g.tlp_a,
                          g.tlp_a + count + 1, g.tick_a, tcap_a, ca, &W, s));
-    CUDA_TRY(setup_tiles(g.t_ptr, (int)N, Z, g.row0_t, count, g.ttmp, g.ti_t, g.tlp_t,
+    CUDA_TRY(setup_tiles(g.t_ptr, (int)N, Z, g.row0_t, count, g.tmp, g.ti_t, g.tlp_t,
                          g.tlp_t + count + 1, g.tick_t, tcap_t, ct, &W, s));
     g_launches += 16;
     int bp = 0, bd = 0;
@@ -1690,8 +1759,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     ir.grid_ta = tile_grid(ca[0], bd);
   }
   KktRaw kr{};
-  kr.a_ptr = g.a_ptr; kr.a_col = g.a_col; kr.a_val64 = g.a_val64;
-  kr.t_ptr = g.t_ptr; kr.t_col = g.t_col; kr.t_val64 = g.t_val64;
+  kr.a_ptr = g.a_ptr; kr.a_col = g.a_col; kr.a_val64 = mode == MODE_PAT ? nullptr : g.a_val64;
+  kr.t_ptr = g.t_ptr; kr.t_col = g.t_col; kr.t_val64 = mode == MODE_PAT ? nullptr : g.t_val64;
   kr.a_long = g.a_long; kr.t_long = g.t_long;
   kr.a_nlong = (int)la_total; kr.t_nlong = (int)lt_total; kr.a_thresh = th_a; kr.t_thresh = th_t;
   kr.m = (int)M; kr.n = (int)N;
@@ -1700,7 +1769,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   kr.row_kind = g.row_kind;
   for (int k = 0; k < 2; ++k) { kr.x[k] = g.x[k]; kr.y[k] = g.y[k]; }
   kr.sum_x = g.sum_x; kr.sum_y = g.sum_y;
-  kr.XG = g.XG; kr.Xl = g.Xl; kr.YG = g.YG; kr.Yl = g.Yl;
+  kr.XG = g.XG; kr.Xl = g.Xl; kr.YG = g.YG; kr.Yl = g.Yl; kr.XR = g.XR; kr.YR = g.YR;
   kr.rays = p->detect_infeasibility && p->terminate ? (any_unboxed ? 2 : 1) : 0;
   kr.part_r = g.part_r; kr.part_c = g.part_c;
   kr.grid_r_short = gridA; kr.grid_r = gridA; kr.grid_c_short = gridT; kr.grid_c = gridT;
@@ -1832,10 +1901,11 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   std::vector<DevState> fs(count);
   CUDA_TRY(cudaMemcpyAsync(fs.data(), g.st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
   for (int k = 0; k < count; ++k) {
+    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (x_out && x_out[k])
-      CUDA_TRY(cudaMemcpyAsync(x_out[k], g.x_out + sh[k].C, 8 * (size_t)sh[k].n, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(x_out[k], g.x_out + sh[k].C, 8 * (size_t)sh[k].n, kind, s));
     if (y_out && y_out[k] && sh[k].m)
-      CUDA_TRY(cudaMemcpyAsync(y_out[k], g.y_out + sh[k].R, 8 * (size_t)sh[k].m, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(y_out[k], g.y_out + sh[k].R, 8 * (size_t)sh[k].m, kind, s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   for (int k = 0; k < count; ++k) {
@@ -1865,7 +1935,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     const bool cert = f.status == PDLP_PRIMAL_INFEASIBLE || f.status == PDLP_DUAL_INFEASIBLE;
     r.ray_obj = cert ? f.ray_obj : NAN;
     r.ray_res = cert ? f.ray_res : NAN;
-    r.setup_s = setup_s;
+    r.setup_s = setup_s - upload_s;
+    r.upload_s = upload_s;
     r.solve_s = solve_s;
     r.kernel_launches = g_launches;
   }
@@ -2181,6 +2252,29 @@ int pdlp_solve_batch(int count, const pdlp_csr* const* A, const double* const* b
     if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
   }
   return solve_batch(count, A, b, sense, c, l, u, p, x_out, y_out, r);
+}
+
+int pdlp_solve_batch_device(int count, const pdlp_csr* const* A, const double* const* b,
+                            const char* const* sense, const double* const* c,
+                            const double* const* l, const double* const* u, const pdlp_params* p,
+                            double* const* x_out, double* const* y_out, pdlp_result* r,
+                            void* stream) {
+  pdlp_params d;
+  if (!p) {
+    pdlp_default_params(&d);
+    p = &d;
+  }
+  if (count < 1 || !A || !b || !sense || !c || !l || !u || !r)
+    return fail(PDLP_ERR_INVALID_INPUT, "batch: count >= 1 and every pointer array required");
+  for (int k = 0; k < count; ++k) {
+    double dummy = 0.0;
+    const int rc = check_inputs(A[k], b[k], sense[k], c[k], l[k], u[k], p,
+                                x_out ? (void*)x_out[k] : (void*)&dummy,
+                                (y_out && y_out[k]) ? (void*)y_out[k] : (void*)&dummy, &r[k]);
+    if (rc) return fail(rc, std::string("LP ") + std::to_string(k) + ": " + g_last_error);
+  }
+  return solve_batch(count, A, b, sense, c, l, u, p, x_out, y_out, r, nullptr, true,
+                     (cudaStream_t)stream);
 }
 
 int pdlp_time_kernels_batch(int count, const pdlp_csr* const* A, const double* const* b,

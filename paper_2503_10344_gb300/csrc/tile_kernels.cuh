@@ -205,7 +205,8 @@ __device__ __forceinline__ void issue_const(unsigned char* s, const TileItem& it
 
 // Requests the iterate data of item `it` into stage `s` (one thread): the rows'
 // current entries (primal x pairs, dual y) and, with a pending weight, their
-// running sums.
+// running sums; an item whose LP does not step this attempt gets none.  Always
+// the stage's second arrival of the use.
 template <typename V, bool DUAL>
 __device__ __forceinline__ void issue_iter(unsigned char* s, const TileItem& it,
                                            const IterData<float, V>& d, const StageMeta& mt,
@@ -214,7 +215,8 @@ __device__ __forceinline__ void issue_iter(unsigned char* s, const TileItem& it,
   const Span16 s4 = span16(it.r0, it.r1, 4);
   const Span16 s8 = span16(it.r0, it.r1, 8);
   const bool with_sum = mt.pw != 0.0f;
-  unsigned bytes = (with_sum ? 4u * s4.cnt : 0u) + (DUAL ? 4u * s4.cnt : 8u * s8.cnt);
+  const unsigned bytes =
+      mt.go ? (with_sum ? 4u * s4.cnt : 0u) + (DUAL ? 4u * s4.cnt : 8u * s8.cnt) : 0u;
   mbar_arrive_expect_tx(bar, bytes);
   if (bytes == 0) return;
   if (DUAL) {
@@ -238,29 +240,6 @@ __device__ __forceinline__ StageMeta item_meta(const IterData<float, V>& d, int 
   m.step = DUAL ? st->sigma_f : st->tau_f;
   m.pw = st->pw_f;
   return m;
-}
-
-// Deterministic block sum of two floats; thread 0 gets them.
-__device__ __forceinline__ void block_sum2f(float& a, float& b, float (*sh)[kWarps]) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    sh[0][w] = a;
-    sh[1][w] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    a = b = 0.0f;
-    for (int i = 0; i < kWarps; ++i) {
-      a += sh[0][i];
-      b += sh[1][i];
-    }
-  }
-  __syncthreads();
 }
 
 // The update of one row from its sums (the same arithmetic as k_primal / k_dual):
@@ -296,23 +275,39 @@ __device__ __forceinline__ float2 dual_row(float kx, float kdx, float q, float s
 // ---------------------------------------------------------------- the kernel
 // DUAL = false: the primal step over the items of A^T (gathers y);
 // DUAL = true:  the dual step over the items of A (gathers the (x', dx) pairs).
+//
+// The block's warps consume a staged item independently: warp w owns the item's
+// rows [r0 + 32 w, r0 + 32 w + 32) -- their nonzeros are one contiguous run of the
+// stage -- gathers for them, sums them and updates them; only __syncwarp orders a
+// warp's own phases.  A warp then releases the stage (a shared-memory count) and the
+// warp that releases it last requests the stage's next item, so no warp waits for
+// another except through the data it needs.  A slice is shared by the 8 warps
+// (one part of its nonzeros each); the last warp to finish its part adds the 8
+// partial sums in warp order.  Step-rule partial sums are kept per warp and written
+// once per (block, LP) run to the warp's slot of the run's first item.
 template <typename V, bool IMPLICIT, bool DUAL>
 __global__ void __launch_bounds__(kBlock, 4) k_tile(IterData<float, V> d) {
   using L = StageLayout<V, DUAL>;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ unsigned long long bar_c[kTileStages], bar_v[kTileStages];
+  __shared__ unsigned long long bar_full[kTileStages];
   __shared__ StageMeta meta[kTileStages];
-  __shared__ float red[2][kWarps];
-  __shared__ int fail, fail_i, fin_flag;
+  __shared__ int released[kTileStages];   // warps done with the stage's current item
+  __shared__ int slice_done[kTileStages];  // warps done with a slice's partial sum
+  __shared__ float2 slice_part[kTileStages][kWarps];
+  __shared__ int issued[kTileStages];      // uses of the stage requested so far
+  __shared__ int fail;
   const TileSet& ts = DUAL ? d.ta : d.tt;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int nmine = b < ts.n ? (ts.n - 1 - b) / G + 1 : 0;
   if (nmine == 0) return;
   const int npre = nmine < kTileStages ? nmine : kTileStages;
   if (tid == 0) {
     for (int s = 0; s < kTileStages; ++s) {
-      mbar_init(&bar_c[s], 1);
-      mbar_init(&bar_v[s], 1);
+      mbar_init(&bar_full[s], 2);  // two arrivals per use: constant data, iterate data
+      released[s] = 0;
+      slice_done[s] = 0;
+      issued[s] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_proxy_async_smem();
@@ -322,25 +317,28 @@ __global__ void __launch_bounds__(kBlock, 4) k_tile(IterData<float, V> d) {
   // constant data of the first stages: independent of the preceding kernels
   if (tid == 0)
     for (int s = 0; s < npre; ++s) {
-      const TileItem it = ts.item[b + s * G];
-      issue_const<V, DUAL, IMPLICIT>(smem + s * L::bytes, it, d, &bar_c[s]);
+      issue_const<V, DUAL, IMPLICIT>(smem + s * L::bytes, ts.item[b + s * G], d, &bar_full[s]);
+      issued[s] = 1;
     }
   pdl_enter();
   if (tid == 0)
     for (int s = 0; s < npre; ++s) {
       const TileItem it = ts.item[b + s * G];
       meta[s] = item_meta<V, DUAL>(d, it.lp);
-      if (meta[s].go) issue_iter<V, DUAL>(smem + s * L::bytes, it, d, meta[s], &bar_v[s]);
+      issue_iter<V, DUAL>(smem + s * L::bytes, it, d, meta[s], &bar_full[s]);
     }
-  __syncthreads();
+  // (the meta writes are published by the arrivals; consumers read them after the wait)
 
-  float acc1 = 0.0f, acc2 = 0.0f;  // this thread's share of the current (block, LP) run
+  float acc1 = 0.0f, acc2 = 0.0f;  // this lane's share of the current (block, LP) run
   int run_lp = -1, run_slot = -1, run_go = 0;
-  auto flush = [&]() {  // uniform over the block
+  auto flush = [&]() {  // per warp: the warp's partial sums into its slot of the run
     if (run_lp >= 0 && run_go) {
-      float a = acc1, c2 = acc2;
-      block_sum2f(a, c2, red);
-      if (tid == 0) ts.part[run_slot] = make_float2(a, c2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+        acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+      }
+      if (lane == 0) ts.part[(size_t)run_slot * kWarps + warp] = make_float2(acc1, acc2);
     }
     acc1 = acc2 = 0.0f;
   };
@@ -351,6 +349,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_tile(IterData<float, V> d) {
     const int gi = b + i * G;
     const TileItem it = ts.item[gi];
     unsigned char* st = smem + s * L::bytes;
+    if (!mbar_wait(&bar_full[s], par)) {
+      atomicExch(&fail, 1);
+      break;
+    }
     const StageMeta mt = meta[s];
     if (it.lp != run_lp) {
       flush();
@@ -358,150 +360,174 @@ __global__ void __launch_bounds__(kBlock, 4) k_tile(IterData<float, V> d) {
       run_slot = gi;
       run_go = mt.go;
     }
-    // wait for the stage (every thread polls; bounded)
-    bool ok = mbar_wait(&bar_c[s], par);
-    if (ok && mt.go) ok = mbar_wait(&bar_v[s], par);
-    if (!ok && atomicExch(&fail, 1) == 0) fail_i = i;
-    __syncthreads();
-    if (fail) break;
     if (mt.go) {
       const int za = it.nb & ~7;
-      const int o = it.nb - za, nz = it.ne - it.nb;
       int* col = reinterpret_cast<int*>(st + L::col);
       float* prb = reinterpret_cast<float*>(st + L::prb);
-      // ---- phase 1: every nonzero's product, gathers issued together
-      if (DUAL) {
-        const float2* xg = mt.cur ? d.x[0] : d.x[1];  // x' of this attempt
-        float2 g[kMaxPerThread];
+      const int* sp = reinterpret_cast<const int*>(st + L::ptr);
+      const float2* xg = mt.cur ? d.x[0] : d.x[1];  // dual: x' of this attempt
+      const float* yg = mt.cur ? d.y[1] : d.y[0];    // primal: current y
+      // products of the staged nonzeros [q0, q1) (stage-relative), lanes strided,
+      // eight gathers issued before any is used
+      auto products = [&](int q0, int q1) {
+        for (int q = q0 + lane; q < q1; q += 8 * 32) {
+          if (DUAL) {
+            float2 g[8];
 #pragma unroll
-        for (int k = 0; k < kMaxPerThread; ++k) {
-          const int q = tid + k * kBlock;
-          g[k] = q < nz ? xg[col[o + q]] : make_float2(0.0f, 0.0f);
+            for (int k = 0; k < 8; ++k) {
+              const int e = q + 32 * k;
+              g[k] = e < q1 ? xg[col[e]] : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int e = q + 32 * k;
+              if (e < q1) {
+                const float v = stage_val<V>(st + L::val, e);
+                col[e] = __float_as_int(v * g[k].x);
+                prb[e] = v * g[k].y;
+              }
+            }
+          } else {
+            float g[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int e = q + 32 * k;
+              g[k] = e < q1 ? yg[col[e]] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int e = q + 32 * k;
+              if (e < q1) col[e] = __float_as_int(stage_val<V>(st + L::val, e) * g[k]);
+            }
+          }
         }
-#pragma unroll
-        for (int k = 0; k < kMaxPerThread; ++k) {
-          const int q = tid + k * kBlock;
-          if (q < nz) {
-            const float v = stage_val<V>(st + L::val, o + q);
-            col[o + q] = __float_as_int(v * g[k].x);
-            prb[o + q] = v * g[k].y;
+      };
+      if (it.first < 0) {
+        // tile: this warp's rows [w0, w1) of the item (stage-relative row w0 - r0)
+        const int nr = it.r1 - it.r0;
+        const int w0 = 32 * warp, w1 = min(nr, w0 + 32);
+        if (w0 < w1) {
+          const int po = it.r0 & 3;
+          products(sp[po + w0] - za, sp[po + w1] - za);
+          __syncwarp();
+          const int t = w0 + lane;
+          if (t < w1) {
+            const int r = it.r0 + t;
+            const int p0 = sp[po + t] - za, p1 = sp[po + t + 1] - za;
+            float a = 0.0f, c2 = 0.0f;
+            for (int p = p0; p < p1; ++p) {
+              a += __int_as_float(col[p]);
+              if (DUAL) c2 += prb[p];
+            }
+            const int k4 = po + t;
+            const float* R0 = reinterpret_cast<const float*>(st + L::r0);
+            const float* R1 = reinterpret_cast<const float*>(st + L::r1);
+            const float* R2 = reinterpret_cast<const float*>(st + L::r2);
+            const float* R3 = reinterpret_cast<const float*>(st + L::r3);
+            const float* R4 = reinterpret_cast<const float*>(st + L::r4);
+            if (DUAL) {
+              const unsigned char* kinds = st + L::r5;
+              const float2 tm = dual_row<IMPLICIT>(a, c2, R0[k4], IMPLICIT ? R1[k4] : 1.0f,
+                                                   kinds[(it.r0 & 15) + t], R2[k4],
+                                                   mt.pw != 0.0f ? R4[k4] : 0.0f, mt.step, mt.pw,
+                                                   mt.cur ? d.y[0] : d.y[1], d.sum_y, r);
+              acc1 += tm.x;
+              acc2 += tm.y;
+            } else {
+              const float2* xs = reinterpret_cast<const float2*>(st + L::r5);
+              acc1 += primal_row<IMPLICIT>(a, R0[k4], R1[k4], R2[k4], IMPLICIT ? R3[k4] : 1.0f,
+                                           xs[(it.r0 & 1) + t].x, mt.pw != 0.0f ? R4[k4] : 0.0f,
+                                           mt.step, mt.pw, mt.cur ? d.x[0] : d.x[1], d.sum_x, r);
+            }
           }
         }
       } else {
-        const float* yg = mt.cur ? d.y[1] : d.y[0];
-        float g[kMaxPerThread];
-#pragma unroll
-        for (int k = 0; k < kMaxPerThread; ++k) {
-          const int q = tid + k * kBlock;
-          g[k] = q < nz ? yg[col[o + q]] : 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < kMaxPerThread; ++k) {
-          const int q = tid + k * kBlock;
-          if (q < nz) col[o + q] = __float_as_int(stage_val<V>(st + L::val, o + q) * g[k]);
-        }
-      }
-      __syncthreads();
-      // ---- phase 2
-      const int* sp = reinterpret_cast<const int*>(st + L::ptr);
-      const float* R0 = reinterpret_cast<const float*>(st + L::r0);
-      const float* R1 = reinterpret_cast<const float*>(st + L::r1);
-      const float* R2 = reinterpret_cast<const float*>(st + L::r2);
-      const float* R3 = reinterpret_cast<const float*>(st + L::r3);
-      const float* R4 = reinterpret_cast<const float*>(st + L::r4);
-      if (it.first < 0) {  // tile: one thread per row
-        const int nr = it.r1 - it.r0;
-        if (tid < nr) {
-          const int po = it.r0 & 3, r = it.r0 + tid;
-          const int p0 = sp[po + tid] - za, p1 = sp[po + tid + 1] - za;
-          float a = 0.0f, c2 = 0.0f;
-          for (int p = p0; p < p1; ++p) {
-            a += __int_as_float(col[p]);
-            if (DUAL) c2 += prb[p];
-          }
-          const int k4 = po + tid;
-          if (DUAL) {
-            const unsigned char* kinds = st + L::r5;
-            const float2 t = dual_row<IMPLICIT>(a, c2, R0[k4], IMPLICIT ? R1[k4] : 1.0f,
-                                                kinds[(it.r0 & 15) + tid], R2[k4],
-                                                mt.pw != 0.0f ? R4[k4] : 0.0f, mt.step, mt.pw,
-                                                mt.cur ? d.y[0] : d.y[1], d.sum_y, r);
-            acc1 += t.x;
-            acc2 += t.y;
-          } else {
-            const float2* xs = reinterpret_cast<const float2*>(st + L::r5);
-            acc1 += primal_row<IMPLICIT>(a, R0[k4], R1[k4], R2[k4], IMPLICIT ? R3[k4] : 1.0f,
-                                         xs[(it.r0 & 1) + tid].x, mt.pw != 0.0f ? R4[k4] : 0.0f,
-                                         mt.step, mt.pw, mt.cur ? d.x[0] : d.x[1], d.sum_x, r);
-          }
-        }
-      } else {  // slice of a long row: the block's partial, then the ticket
+        // slice: this warp's part of the nonzeros, then the eight parts in warp order
+        const int o = it.nb - za, nz = it.ne - it.nb;
+        const int part = ((nz + kWarps - 1) / kWarps + 31) & ~31;
+        const int q0 = o + min(nz, warp * part), q1 = o + min(nz, (warp + 1) * part);
+        products(q0, q1);
+        __syncwarp();
         float a = 0.0f, c2 = 0.0f;
-        for (int q = tid; q < nz; q += kBlock) {
-          a += __int_as_float(col[o + q]);
-          if (DUAL) c2 += prb[o + q];
+        for (int q = q0 + lane; q < q1; q += 32) {
+          a += __int_as_float(col[q]);
+          if (DUAL) c2 += prb[q];
         }
-        block_sum2f(a, c2, red);
-        if (tid == 0) {
-          ts.rowpart[gi] = make_float2(a, c2);
-          __threadfence();
-          const int done = atomicAdd(&ts.ticket[it.first], 1);
-          fin_flag = done == it.nsl - 1;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, off);
+          c2 += __shfl_xor_sync(0xffffffffu, c2, off);
         }
-        __syncthreads();
-        if (fin_flag && tid == 0) {  // the last slice: finish the row
-          __threadfence();
-          float sa = 0.0f, sb = 0.0f;
-          for (int k = 0; k < it.nsl; ++k) {
-            const float2 pv = __ldcg(ts.rowpart + it.first + k);
-            sa += pv.x;
-            sb += pv.y;
+        if (lane == 0) {
+          slice_part[s][warp] = make_float2(a, c2);
+          __threadfence_block();
+          if (atomicAdd(&slice_done[s], 1) == kWarps - 1) {  // the last part: the slice's sum
+            __threadfence_block();
+            slice_done[s] = 0;
+            float sa = 0.0f, sb = 0.0f;
+            for (int k = 0; k < kWarps; ++k) {
+              const float2 pv = slice_part[s][k];
+              sa += pv.x;
+              sb += pv.y;
+            }
+            ts.rowpart[gi] = make_float2(sa, sb);
+            __threadfence();
+            if (atomicAdd(&ts.ticket[it.first], 1) == it.nsl - 1) {  // the last slice: the row
+              __threadfence();
+              float ra = 0.0f, rb = 0.0f;
+              for (int k = 0; k < it.nsl; ++k) {
+                const float2 pv = __ldcg(ts.rowpart + it.first + k);
+                ra += pv.x;
+                rb += pv.y;
+              }
+              const int r = it.r0;
+              if (DUAL) {
+                const float* y = mt.cur ? d.y[1] : d.y[0];
+                ts.lterm[it.lid] = dual_row<IMPLICIT>(
+                    ra, rb, d.q[r], IMPLICIT ? d.sw[r] : 1.0f, d.row_kind[r], y[r],
+                    mt.pw != 0.0f ? d.sum_y[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.y[0] : d.y[1],
+                    d.sum_y, r);
+              } else {
+                const float2* x = mt.cur ? d.x[1] : d.x[0];
+                const float tm = primal_row<IMPLICIT>(
+                    ra, d.c[r], d.l[r], d.u[r], IMPLICIT ? d.tw[r] : 1.0f, x[r].x,
+                    mt.pw != 0.0f ? d.sum_x[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.x[0] : d.x[1],
+                    d.sum_x, r);
+                ts.lterm[it.lid] = make_float2(tm, 0.0f);
+              }
+              ts.ticket[it.first] = 0;  // ready for the next launch
+            }
           }
-          const int r = it.r0;
-          if (DUAL) {
-            const float* y = mt.cur ? d.y[1] : d.y[0];
-            const float2 t = dual_row<IMPLICIT>(
-                sa, sb, d.q[r], IMPLICIT ? d.sw[r] : 1.0f, d.row_kind[r], y[r],
-                mt.pw != 0.0f ? d.sum_y[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.y[0] : d.y[1],
-                d.sum_y, r);
-            ts.lterm[it.lid] = t;
-          } else {
-            const float2* x = mt.cur ? d.x[1] : d.x[0];
-            const float t = primal_row<IMPLICIT>(
-                sa, d.c[r], d.l[r], d.u[r], IMPLICIT ? d.tw[r] : 1.0f, x[r].x,
-                mt.pw != 0.0f ? d.sum_x[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.x[0] : d.x[1],
-                d.sum_x, r);
-            ts.lterm[it.lid] = make_float2(t, 0.0f);
-          }
-          ts.ticket[it.first] = 0;  // ready for the next launch
         }
       }
     }
-    __syncthreads();  // every thread is done with stage s
-    if (tid == 0 && i + kTileStages < nmine) {
-      const TileItem nx = ts.item[gi + kTileStages * G];
+    // release the stage; the warp that releases it last requests its next item
+    __syncwarp();
+    if (lane == 0) {
       fence_proxy_async_smem();
-      issue_const<V, DUAL, IMPLICIT>(st, nx, d, &bar_c[s]);
-      meta[s] = item_meta<V, DUAL>(d, nx.lp);
-      if (meta[s].go) issue_iter<V, DUAL>(st, nx, d, meta[s], &bar_v[s]);
-    }
-    // meta[s] of item i + kTileStages is read after the next barriers
-  }
-  if (fail) {
-    // a stage never completed: record it for every LP, wait (bounded) for the copies
-    // still in flight into the stages of the items not consumed, and return
-    if (tid == 0) {
-      for (int j = fail_i; j < nmine && j < fail_i + kTileStages; ++j) {
-        const int s = j % kTileStages;
-        const unsigned par = (unsigned)((j / kTileStages) & 1);
-        (void)mbar_wait(&bar_c[s], par);
-        if (meta[s].go) (void)mbar_wait(&bar_v[s], par);
+      __threadfence_block();
+      if (atomicAdd(&released[s], 1) == kWarps - 1) {
+        __threadfence_block();
+        released[s] = 0;
+        if (i + kTileStages < nmine) {
+          const TileItem nx = ts.item[gi + kTileStages * G];
+          issue_const<V, DUAL, IMPLICIT>(st, nx, d, &bar_full[s]);
+          meta[s] = item_meta<V, DUAL>(d, nx.lp);
+          issue_iter<V, DUAL>(st, nx, d, meta[s], &bar_full[s]);
+          issued[s] += 1;
+        }
       }
-      for (int k = 0; k < d.count; ++k) atomicExch(&d.st[k].status, kStatusWaitFailed);
     }
-    return;
   }
   flush();
+  // a stage never completed: record it; wait (bounded) for the copies still in flight
+  // into the stages of items not consumed before the block exits
+  __syncthreads();
+  if (fail && tid == 0) {
+    for (int s2 = 0; s2 < kTileStages; ++s2)
+      if (issued[s2] > 0) (void)mbar_wait(&bar_full[s2], (unsigned)((issued[s2] - 1) & 1));
+    for (int k = 0; k < d.count; ++k) atomicExch(&d.st[k].status, kStatusWaitFailed);
+  }
 }
 
 }  // namespace pdlp

@@ -113,3 +113,27 @@ def test_batch_kernel_timing(P):
         assert kt[k]["bytes"] == pytest.approx(sum(o[k]["bytes"] for o in one), rel=1e-5), k
     _, _, res = P.pdlp_solve_batch(lps, prm)
     assert all(r["status"] == P.PDLP_OPTIMAL for r in res)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_device_batch_equals_host_batch(P, prec):
+    """pdlp_solve_batch_device (inputs and outputs on the device, the caller's stream)
+    runs the same setup and iteration as the host entry point: the same points bit for
+    bit, the same counts; no upload time."""
+    lps = mixed_lps()
+    prm = P.default_params(tol=1e-4, precision=prec)
+    xh, yh, rh = P.pdlp_solve_batch(lps, prm)
+    xd, yd, rd = P.pdlp_solve_batch_device([P.DeviceLP(lp) for lp in lps], prm)
+    for a, b, c, d, r1, r2 in zip(xh, xd, yh, yd, rh, rd):
+        assert np.array_equal(a, b.cpu().numpy()) and np.array_equal(c, d.cpu().numpy())
+        assert r1["iters"] == r2["iters"] and r1["status"] == r2["status"]
+        assert r2["upload_s"] == 0.0 and r1["upload_s"] > 0.0
+
+
+def test_device_batch_rejects_an_invalid_member(P):
+    lps = mixed_lps()[:3]
+    bad = lpgen.mip_relaxation(5)
+    bad.col = bad.col.copy()
+    bad.col[3] = bad.n  # column index out of range
+    with pytest.raises(P.PdlpError, match="LP 3: invalid input: column index"):
+        P.pdlp_solve_batch_device([P.DeviceLP(lp) for lp in lps + [bad]])

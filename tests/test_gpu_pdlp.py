@@ -23,38 +23,29 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 PARITY = 1e-9
-# reduced-precision results: |obj - obj_fp64| / (1 + |obj_fp64|) against the float64
-# oracle's objective at rel. KKT 1e-6 (tests/golden/objectives.json, written by
-# make_golden.py from oracle/ only)
+# Reduced-precision results at rel. KKT 1e-4: the objective p against the optimum p* (the
+# float64 oracle's objective at rel. KKT 1e-6, pinned by HiGHS in test_golden.py;
+# tests/golden/objectives.json, written by make_golden.py from oracle/ only), relative in
+# the sense of the termination test's gap: |p - p*| / (1 + |p| + |p*|) <= 1e-4.  A point
+# at relative KKT 1e-4 has |p - d| <= 1e-4 (1 + |p| + |d|) with the optimum between
+# (up to its 1e-4 residuals), so this is what the tolerance promises; the float64
+# oracle's own 1e-4 points land up to 1.9e-4 from p* when divided by 1 + |p*| alone,
+# and two 1e-4 points can sit on opposite sides of p*.
 OBJ_TOL = 1e-4
 _OBJECTIVES = None
 
 
-def fp64_objective(key):
+def golden(key):
     global _OBJECTIVES
     if _OBJECTIVES is None:
         _OBJECTIVES = json.load(open(os.path.join(GOLDEN, "objectives.json")))
-    return _OBJECTIVES[key]["oracle_obj"]
+    return _OBJECTIVES[key]
 
 
 def obj_err(obj, key):
-    ref = fp64_objective(key)
-    return abs(obj - ref) / (1.0 + abs(ref))
-
-
-@pytest.fixture(scope="module")
-def P():
-    import __graft_entry__ as G
-    G.build()
-    import paper_2503_10344_gb300 as P
-    return P
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1.0, np.linalg.norm(b)))
-
-
-skewed_lp = lpgen.skewed_lp
+    """|p - p*| / (1 + |p| + |p*|) against the float64 oracle's optimum."""
+    opt = golden(key)["oracle_obj"]
+    return abs(obj - opt) / (1.0 + abs(obj) + abs(opt))
 
 
 GOLDEN_KEY = {"mip_relaxation_200x400": "mip_relaxation(1)",
@@ -409,7 +400,7 @@ def test_energy_system_full_size_fp32(P):
     _, _, r64 = P.pdlp_solve_device(d, P.default_params(tol=1e-6, precision="fp64", iter_limit=400_000))
     assert r64["status"] == P.PDLP_OPTIMAL, r64
     ref = r64["primal_obj"]
-    assert abs(r["primal_obj"] - ref) / (1.0 + abs(ref)) <= OBJ_TOL
+    assert abs(r["primal_obj"] - ref) / (1.0 + abs(r["primal_obj"]) + abs(ref)) <= OBJ_TOL
 
 
 # ---------------------------------------------------------------- primal-weight hint
