@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
                     help="1: one cooperative step kernel per check period; 0: two launches per attempt")
-    ap.add_argument("--tiles", type=int, default=0, choices=[0, 1],
-                    help="float32 steps: 1 staged tile kernels (bulk copies into shared memory); "
-                         "0 lanes-per-row kernels")
+    ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],
+                    help="float32 steps: 0 lanes-per-row kernels; 1 staged block tiles (bulk "
+                         "copies into shared memory); 2 warp tiles")
     for k in ("lanes-a", "lanes-at", "lanes-kkt-a", "lanes-kkt-at"):
         ap.add_argument("--" + k, type=int, default=0, help="SpMV lanes per row (0 = automatic)")
     return ap.parse_args()
@@ -528,40 +528,44 @@ def batch_section(args, dev, stream, peak):
 
 def c1_section(args, dev, stream, peak):
     """The 200 x 400 MIP relaxation (seeds 1..20): float64 PDLP to rel. KKT 1e-4 and to
-    1e-8 through the host API (latency of a small LP: setup, iterations, copies), then
-    fix-and-propagate (Frac order) from the 1e-4 point with its final LP at 1e-8."""
+    1e-8 through the host API (latency of a small LP: setup, iterations, copies), with
+    the two-launch step kernels and with the one-block persistent kernel
+    (persistent = 2), then fix-and-propagate (Frac order) from the 1e-4 point with its
+    final LP at 1e-8."""
     import lpgen
     import paper_2503_10344_gb300 as P
 
-    rows = []
-    P.pdlp_solve(lpgen.mip_relaxation(1), P.default_params(tol=1e-4))  # warm
-    for seed in range(1, 21):
-        lp = lpgen.mip_relaxation(seed)
-        out = {"seed": seed}
-        for tol in (1e-4, 1e-8):
-            t0 = time.perf_counter()
-            x, y, r = P.pdlp_solve(lp, P.default_params(tol=tol))
-            out[f"{tol:g}"] = {"wall_s": time.perf_counter() - t0, "solve_s": r["solve_s"],
-                               "setup_s": r["setup_s"], "iters": r["iters"], "status": r["status"],
-                               "rel_kkt": r["rel_kkt"], "obj": r["primal_obj"]}
-            if tol == 1e-4:
-                x4, y4 = x, y
+    out = {"workload": "mip_relaxation m=200 n=400 seeds 1..20 (float64)"}
+    lps = [lpgen.mip_relaxation(seed) for seed in range(1, 21)]
+    for persistent in (0, 2):
+        P.pdlp_solve(lps[0], P.default_params(tol=1e-4, persistent=persistent))  # warm
+        rows = []
+        for lp in lps:
+            row = {}
+            for tol in (1e-4, 1e-8):
+                t0 = time.perf_counter()
+                x, y, r = P.pdlp_solve(lp, P.default_params(tol=tol, persistent=persistent))
+                row[tol] = {"wall_s": time.perf_counter() - t0, "solve_s": r["solve_s"],
+                            "iters": r["iters"], "ok": r["status"] == P.PDLP_OPTIMAL,
+                            "obj": r["primal_obj"], "x": x, "y": y}
+            rows.append(row)
+        med = lambda key, tol: float(np.median([r[tol][key] for r in rows]))
+        out[f"persistent{persistent}"] = {
+            "time_to_1e-4_s": {"median_wall": med("wall_s", 1e-4), "median_solve": med("solve_s", 1e-4)},
+            "time_to_1e-8_s": {"median_wall": med("wall_s", 1e-8), "median_solve": med("solve_s", 1e-8)},
+            "iters_1e-4_median": med("iters", 1e-4), "iters_1e-8_median": med("iters", 1e-8),
+            "optimal": int(sum(r[t]["ok"] for r in rows for t in (1e-4, 1e-8)))}
+    fp = []
+    for lp, row in zip(lps, rows):
         t0 = time.perf_counter()
-        xf, f = P.fp_run(lp, x4, y4, strategy="frac", final_lp=True, final_lp_tol=1e-8)
-        out["fp"] = {"wall_s": time.perf_counter() - t0, "status": f["status"], "obj": f["obj"],
-                     "nodes": f["nodes"], "search_s": f["search_s"], "final_lp_s": f["lp_s"]}
-        rows.append(out)
-    med = lambda key, tol: float(np.median([r[tol][key] for r in rows]))
-    feas = [r for r in rows if r["fp"]["status"] == P.FP_FEASIBLE]
-    return {"workload": "mip_relaxation m=200 n=400 seeds 1..20 (float64)",
-            "time_to_1e-4_s": {"median_wall": med("wall_s", "0.0001"), "median_solve": med("solve_s", "0.0001")},
-            "time_to_1e-8_s": {"median_wall": med("wall_s", "1e-08"), "median_solve": med("solve_s", "1e-08")},
-            "iters_1e-4_median": med("iters", "0.0001"), "iters_1e-8_median": med("iters", "1e-08"),
-            "optimal": int(sum(r[t]["status"] == P.PDLP_OPTIMAL for r in rows for t in ("0.0001", "1e-08"))),
-            "fp_run": {"feasible": len(feas), "median_wall_s": float(np.median([r["fp"]["wall_s"] for r in rows])),
-                       "median_gap_to_lp": float(np.median([(r["fp"]["obj"] - r["1e-08"]["obj"]) /
-                                                            max(1.0, abs(r["fp"]["obj"])) for r in feas]))
-                       if feas else None}}
+        _, f = P.fp_run(lp, row[1e-4]["x"], row[1e-4]["y"], strategy="frac", final_lp=True,
+                        final_lp_tol=1e-8)
+        fp.append((time.perf_counter() - t0, f, row[1e-8]["obj"]))
+    feas = [(w, f, o) for w, f, o in fp if f["status"] == P.FP_FEASIBLE]
+    out["fp_run"] = {"feasible": len(feas), "median_wall_s": float(np.median([w for w, _, _ in fp])),
+                     "median_gap_to_lp": float(np.median([(f["obj"] - o) / max(1.0, abs(f["obj"]))
+                                                          for _, f, o in feas])) if feas else None}
+    return out
 
 
 def run_kernels_only(args):

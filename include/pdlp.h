@@ -134,9 +134,11 @@ typedef struct {
   int verbose;          /* 0 quiet; 1 one line per KKT check on stderr; 2 also the host-side
                            time of each setup phase (synchronising the stream at each) */
   int persistent;       /* 1: the step attempts of a check period run in one cooperative
-                           kernel with grid-wide barriers; 0 (default): two kernel launches
-                           per attempt.  Same iteration either way; batches always use the
-                           two-launch form. */
+                           kernel with grid-wide barriers; 2: the same kernel as one block
+                           (small LPs, such as the 200 x 400 relaxations: the grid barrier
+                           is the block's barrier, no launch per attempt); 0 (default): two
+                           kernel launches per attempt.  Same iteration either way; batches
+                           always use the two-launch form. */
   int autotune;         /* 1: before iterating, time whole step attempts (primal kernel,
                            dual kernel and decision) with 2, 4, 8, 16 and 32 lanes per row,
                            first for the primal kernel's A^T, then for the dual kernel's A,

@@ -13,7 +13,7 @@ namespace pdlp {
 constexpr int kBlock = 256;         // threads per block of every streaming kernel
 constexpr int kWarps = kBlock / 32;
 // resident blocks per SM the float32 step kernels are compiled for
-constexpr int kStepBlocksPerSmF32 = 6;
+constexpr int kStepBlocksPerSmF32 = 4;
 
 // Matrix value formats of the iteration matrix.
 struct Pattern {};  // every stored value is exactly +1: no value array at all
@@ -175,6 +175,10 @@ constexpr int kTileRows = kBlock;
 constexpr int kLongRow = 256;
 constexpr int kTileWindowMin = 256;
 constexpr int kTileWindowMax = 1024;
+// warp tiles (wtile_kernels.cuh): at most 32 rows, windows of 64-256 nonzeros
+constexpr int kWarpTileRows = 32;
+constexpr int kWarpTileWindowMin = 64;
+constexpr int kWarpTileWindowMax = 256;
 
 // One work item (32 bytes).  Tile: rows [r0, r1), nonzeros [nb, ne), first = -1.
 // Slice: row r0 (r1 = r0 + 1), nonzeros [nb, ne) of it, first = index of the row's

@@ -31,10 +31,13 @@ struct IterRaw {
   unsigned long long cond;  // while-loop handle of the check-period graph (0: none)
   int loop_cap;             // attempts per graph launch at most (with cond)
   Tables tp, td; // batch tables over A^T and A (all NULL for one LP)
-  // staged tile step kernels (float32 iterates; tile_kernels.cuh): 1 = on
+  // tile step kernels (float32 iterates): 0 off, 1 staged block tiles
+  // (tile_kernels.cuh), 2 warp tiles (wtile_kernels.cuh)
   int tile;
   TileSet tt, ta;        // items over A^T (primal step) and over A (dual step)
-  int grid_tt, grid_ta;  // their grids (k_decide reads one partial slot per block and LP)
+  int grid_tt, grid_ta;  // their grids (blocks)
+  int work_tt, work_ta;  // workers (blocks or warps): k_decide reads one slot per worker and LP
+  int tslot;             // partials per slot (8 for block tiles, 1 for warp tiles)
 };
 
 // IK_DUAL launches the dual step kernel and then the step decision (k_decide)
@@ -50,10 +53,10 @@ cudaError_t launch_persist_bf16(int lanes_a, int lanes_t, const IterRaw& r, int 
 cudaError_t launch_persist_pat(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
                                int grid, int* grid_out, cudaStream_t s);
 
-// blocks of the staged tile kernels (primal, dual) resident at once on this device
-cudaError_t tile_resident_fp32(int* primal_blocks, int* dual_blocks);
-cudaError_t tile_resident_bf16(int* primal_blocks, int* dual_blocks);
-cudaError_t tile_resident_pat(int* primal_blocks, int* dual_blocks);
+// blocks of the tile kernels of a form (primal, dual) resident at once on this device
+cudaError_t tile_resident_fp32(int form, int* primal_blocks, int* dual_blocks);
+cudaError_t tile_resident_bf16(int form, int* primal_blocks, int* dual_blocks);
+cudaError_t tile_resident_pat(int form, int* primal_blocks, int* dual_blocks);
 
 cudaError_t launch_iter_fp64(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_t s);

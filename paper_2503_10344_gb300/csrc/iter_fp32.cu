@@ -9,8 +9,8 @@ cudaError_t launch_persist_fp32(int lanes_a, int lanes_t, const IterRaw& r, int 
                                   int grid, int* grid_out, cudaStream_t s) {
   return launch_persist_t<float, float, false>(lanes_a, lanes_t, r, max_attempts, grid, grid_out, s);
 }
-cudaError_t tile_resident_fp32(int* primal_blocks, int* dual_blocks) {
-  const cudaError_t e = tile_resident<float, false, false>(primal_blocks);
-  return e != cudaSuccess ? e : tile_resident<float, false, true>(dual_blocks);
+cudaError_t tile_resident_fp32(int form, int* primal_blocks, int* dual_blocks) {
+  const cudaError_t e = tile_resident<float, false, false>(form, primal_blocks);
+  return e != cudaSuccess ? e : tile_resident<float, false, true>(form, dual_blocks);
 }
 }  // namespace pdlp

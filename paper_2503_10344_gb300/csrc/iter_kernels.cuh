@@ -83,9 +83,9 @@ struct IterData {
   unsigned long long cond;                             // while-loop handle of the graph (0: none)
   int loop_cap;                                        // attempts per graph launch at most
   Tables tp, td;                                       // batch tables over A^T / A (NULL: one LP)
-  int tile;                                            // staged tile kernels (float32 only)
+  int tile;                                            // tile kernels (float32 only): form
   TileSet tt, ta;                                      // their items over A^T and A
-  int grid_tt, grid_ta;
+  int grid_tt, grid_ta, work_tt, work_ta, tslot;
 };
 
 // Rows of one LP (span), one aligned group of LANES lanes per row, rows
@@ -192,6 +192,106 @@ __device__ __forceinline__ bool rows_short2(const Span& sp, const int* __restric
       if (n0 >= 0) fin((int)r0, a0, pc0, pv0);
       if (n1 >= 0) fin((int)r1, a1, pc1, pv1);
     }
+  }
+  return true;
+}
+
+// The same traversal as rows_short2, software-pipelined across passes: while a
+// pass gathers and finishes its row pair, the column indices and values of the next
+// pair (from row pointers loaded one pass earlier) and the row pointers of the pair
+// after it are already in flight, so a pass waits on its gathers alone instead of on
+// the row pointer -> column index -> gather chain.  The first pair's pointers,
+// indices and values and the second pair's pointers are loaded before `enter()`
+// (they do not depend on the iterate).  Same rows, same lanes, same summation order
+// as rows_short2.
+template <int LANES, typename Acc, typename PC, typename PV, typename Val, typename Term,
+          typename PrefC, typename PrefV, typename Fin, typename Enter>
+__device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restrict__ ptr,
+                                            const int* __restrict__ col, int thresh, Val val,
+                                            Term term, PrefC pref_c, PrefV pref_v, Fin fin,
+                                            Enter enter) {
+  using VT = decltype(val(0));
+  const int lane = threadIdx.x & (LANES - 1);
+  const long long G = (long long)sp.nshort * kBlock / LANES;
+  const long long end = (long long)sp.row0 + sp.nrows;
+  long long r0 = sp.row0 + ((long long)sp.bidx * kBlock + threadIdx.x) / LANES;
+  struct Rows {  // a pair's starts and lengths (-1: a long row or no row)
+    int s0, n0, s1, n1;
+  };
+  struct Heads {  // each lane's first kPre column indices and values of the pair's rows
+    int c0[kPre], c1[kPre];
+    VT v0[kPre], v1[kPre];
+  };
+  auto load_rows = [&](long long ra) -> Rows {
+    Rows p{0, -1, 0, -1};
+    if (ra < end) {
+      const int s = __ldg(ptr + ra), e = __ldg(ptr + ra + 1);
+      p.s0 = s;
+      p.n0 = e - s <= thresh ? e - s : -1;
+    }
+    if (ra + G < end) {
+      const int s = __ldg(ptr + ra + G), e = __ldg(ptr + ra + G + 1);
+      p.s1 = s;
+      p.n1 = e - s <= thresh ? e - s : -1;
+    }
+    return p;
+  };
+  auto load_heads = [&](const Rows& p) -> Heads {
+    Heads h;
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int q = lane + k * LANES;
+      h.c0[k] = q < p.n0 ? __ldg(col + p.s0 + q) : 0;
+      h.v0[k] = q < p.n0 ? val(p.s0 + q) : VT(0);
+      h.c1[k] = q < p.n1 ? __ldg(col + p.s1 + q) : 0;
+      h.v1[k] = q < p.n1 ? val(p.s1 + q) : VT(0);
+    }
+    return h;
+  };
+  Rows rw = load_rows(r0);
+  Heads hd = load_heads(rw);
+  Rows rn = load_rows(r0 + 2 * G);
+  if (!enter()) return false;
+  for (; r0 < end; r0 += 2 * G) {
+    const long long r1 = r0 + G;
+    // the next pair's heads and the pointers of the pair after it: independent of
+    // this pair's gathers, issued first
+    const Heads hn = load_heads(rn);
+    const Rows rnn = load_rows(r0 + 4 * G);
+    PC pc0{}, pc1{};
+    PV pv0{}, pv1{};
+    if (lane == 0) {
+      if (rw.n0 >= 0) {
+        pc0 = pref_c((int)r0);
+        pv0 = pref_v((int)r0);
+      }
+      if (rw.n1 >= 0) {
+        pc1 = pref_c((int)r1);
+        pv1 = pref_v((int)r1);
+      }
+    }
+    Acc a0{}, a1{};
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int q = lane + k * LANES;
+      if (q < rw.n0) a0 += term(hd.v0[k], hd.c0[k]);
+      if (q < rw.n1) a1 += term(hd.v1[k], hd.c1[k]);
+    }
+    const int nmax = rw.n0 > rw.n1 ? rw.n0 : rw.n1;
+#pragma unroll 2
+    for (int q = lane + kPre * LANES; q < nmax; q += LANES) {
+      if (q < rw.n0) a0 += term(val(rw.s0 + q), __ldg(col + rw.s0 + q));
+      if (q < rw.n1) a1 += term(val(rw.s1 + q), __ldg(col + rw.s1 + q));
+    }
+    a0 = group_sum<LANES>(a0);
+    a1 = group_sum<LANES>(a1);
+    if (lane == 0) {
+      if (rw.n0 >= 0) fin((int)r0, a0, pc0, pv0);
+      if (rw.n1 >= 0) fin((int)r1, a1, pc1, pv1);
+    }
+    rw = rn;
+    hd = hn;
+    rn = rnn;
   }
   return true;
 }
@@ -353,7 +453,7 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_primal(IterData<T
     if (!enter()) return;
     rows_all<true, LANES, T>(sp, d.t_ptr, d.t_thresh, load, epi);
   } else if (sp.bidx < sp.nshort) {
-    if (!rows_short2<LANES, T, PreCP<T>, PreVP<T>>(sp, d.t_ptr, d.t_col, d.t_thresh, val, term,
+    if (!rows_short3<LANES, T, PreCP<T>, PreVP<T>>(sp, d.t_ptr, d.t_col, d.t_thresh, val, term,
                                                    pref_c, pref_v, fin, enter))
       return;
   } else {
@@ -511,7 +611,7 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
     if (!enter()) return;
     rows_all<true, LANES, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
   } else if (sp.bidx < sp.nshort) {
-    if (!rows_short2<LANES, P2<T>, PreCD<T>, PreVD<T>>(sp, d.a_ptr, d.a_col, d.a_thresh, val, term,
+    if (!rows_short3<LANES, P2<T>, PreCD<T>, PreVD<T>>(sp, d.a_ptr, d.a_col, d.a_thresh, val, term,
                                                        pref_c, pref_v, fin, enter))
       return;
   } else {
@@ -565,13 +665,13 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
   }
   T a = 0, b0 = 0, b1 = 0;
   if (std::is_same<T, float>::value && d.tile) {
-    // tile kernels: one slot per (block, LP) run -- the LP's first min(items, grid)
-    // item slots, one entry per warp -- and one per long row
-    const int i0 = d.tt.item0[k], i1 = min(d.tt.item0[k + 1], i0 + d.grid_tt);
-    for (int i = i0 * kWarps + threadIdx.x; i < i1 * kWarps; i += kBlock) a += (T)d.tt.part[i].x;
+    // tile kernels: one slot per (worker, LP) run -- the LP's first min(items, workers)
+    // item slots, tslot entries each -- and one per long row
+    const int i0 = d.tt.item0[k], i1 = min(d.tt.item0[k + 1], i0 + d.work_tt);
+    for (int i = i0 * d.tslot + threadIdx.x; i < i1 * d.tslot; i += kBlock) a += (T)d.tt.part[i].x;
     for (int i = d.tt.lng0[k] + threadIdx.x; i < d.tt.lng0[k + 1]; i += kBlock) a += (T)d.tt.lterm[i].x;
-    const int j0 = d.ta.item0[k], j1 = min(d.ta.item0[k + 1], j0 + d.grid_ta);
-    for (int i = j0 * kWarps + threadIdx.x; i < j1 * kWarps; i += kBlock) {
+    const int j0 = d.ta.item0[k], j1 = min(d.ta.item0[k + 1], j0 + d.work_ta);
+    for (int i = j0 * d.tslot + threadIdx.x; i < j1 * d.tslot; i += kBlock) {
       const float2 v = d.ta.part[i];
       b0 += (T)v.x;
       b1 += (T)v.y;
@@ -627,6 +727,10 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 __device__ __forceinline__ bool grid_barrier(DevState* st) {
+  if (gridDim.x == 1) {  // a one-block launch: the block's barrier orders its global memory
+    __syncthreads();
+    return true;
+  }
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -7,6 +7,7 @@
 #include "internal.h"
 #include "iter_kernels.cuh"
 #include "tile_kernels.cuh"
+#include "wtile_kernels.cuh"
 
 namespace pdlp {
 
@@ -39,6 +40,9 @@ IterData<T, V> typed(const IterRaw& r) {
   d.ta = r.ta;
   d.grid_tt = r.grid_tt;
   d.grid_ta = r.grid_ta;
+  d.work_tt = r.work_tt;
+  d.work_ta = r.work_ta;
+  d.tslot = r.tslot;
   return d;
 }
 
@@ -73,24 +77,32 @@ cudaError_t launch_one(int which, const IterData<T, V>& d, cudaStream_t s) {
   }
 }
 
-// The staged tile kernel of one orientation (kTileStages stages of dynamic shared
-// memory, allowed for the device by tile_resident during the setup).
+// The tile kernel of one orientation: the staged block tiles (kTileStages stages of
+// dynamic shared memory, allowed for the device by tile_resident during the setup)
+// or the warp tiles.
 template <typename V, bool IMPLICIT, bool DUAL>
 cudaError_t launch_tile(const IterData<float, V>& d, cudaStream_t s) {
+  const int grid = DUAL ? d.grid_ta : d.grid_tt;
+  if (d.tile == 2) return launch_pdl(k_wtile<V, IMPLICIT, DUAL>, grid, kBlock, s, d);
   const int smem = kTileStages * StageLayout<V, DUAL>::bytes;
-  return launch_pdl_smem(k_tile<V, IMPLICIT, DUAL>, DUAL ? d.grid_ta : d.grid_tt, kBlock, smem, s, d);
+  return launch_pdl_smem(k_tile<V, IMPLICIT, DUAL>, grid, kBlock, smem, s, d);
 }
 
-// Blocks of the tile kernel of one orientation that fit on the device at once; also
-// allows the kernel its dynamic shared memory on the current device.
+// Blocks of the tile kernel (form 1 or 2) of one orientation that fit on the device at
+// once; for form 1 also allows the kernel its dynamic shared memory on this device.
 template <typename V, bool IMPLICIT, bool DUAL>
-cudaError_t tile_resident(int* blocks) {
-  auto kern = k_tile<V, IMPLICIT, DUAL>;
-  const int smem = kTileStages * StageLayout<V, DUAL>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+cudaError_t tile_resident(int form, int* blocks) {
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
+  cudaError_t e;
+  if (form == 2) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wtile<V, IMPLICIT, DUAL>, kBlock, 0);
+  } else {
+    auto kern = k_tile<V, IMPLICIT, DUAL>;
+    const int smem = kTileStages * StageLayout<V, DUAL>::bytes;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
+  }
   if (e != cudaSuccess) return e;
   *blocks = std::max(1, per_sm) * device_sm_count();
   return cudaSuccess;

@@ -9,8 +9,8 @@ cudaError_t launch_persist_pat(int lanes_a, int lanes_t, const IterRaw& r, int m
                                   int grid, int* grid_out, cudaStream_t s) {
   return launch_persist_t<float, Pattern, true>(lanes_a, lanes_t, r, max_attempts, grid, grid_out, s);
 }
-cudaError_t tile_resident_pat(int* primal_blocks, int* dual_blocks) {
-  const cudaError_t e = tile_resident<Pattern, true, false>(primal_blocks);
-  return e != cudaSuccess ? e : tile_resident<Pattern, true, true>(dual_blocks);
+cudaError_t tile_resident_pat(int form, int* primal_blocks, int* dual_blocks) {
+  const cudaError_t e = tile_resident<Pattern, true, false>(form, primal_blocks);
+  return e != cudaSuccess ? e : tile_resident<Pattern, true, true>(form, dual_blocks);
 }
 }  // namespace pdlp

@@ -878,13 +878,13 @@ namespace {
 // lfl[r] = 1 if row r is long.  A row starts an item if it is the first row, a
 // multiple of kTileRows, long, follows a long row, or starts in another window of
 // W nonzeros than the row before it.
-__global__ void k_tile_count(const int* ptr, int R, int W, int* cnt, int* lfl) {
+__global__ void k_tile_count(const int* ptr, int R, int W, int rows, int* cnt, int* lfl) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride) {
     const int r = (int)i;
     const int s = ptr[r], e = ptr[r + 1];
     const bool lng = e - s > kLongRow;
-    bool start = r == 0 || r % kTileRows == 0 || lng;
+    bool start = r == 0 || r % rows == 0 || lng;
     if (!start) {
       const int sp = ptr[r - 1];
       start = s / W != sp / W || s - sp > kLongRow;
@@ -944,24 +944,33 @@ __global__ void k_tile_lp_ranges(const int* lp_row0, int count, int R, const int
 
 }  // namespace
 
-int tile_window(int R, long long nnz) {
-  const double avg = R > 0 ? (double)nnz / (double)R : 1.0;
-  const double w = (double)kTileRows * avg;
-  return (int)std::max((double)kTileWindowMin, std::min((double)kTileWindowMax, w));
+TileShape tile_shape(int form) {
+  return form == 2 ? TileShape{kWarpTileRows, kWarpTileWindowMin, kWarpTileWindowMax}
+                   : TileShape{kTileRows, kTileWindowMin, kTileWindowMax};
 }
 
-size_t tile_item_cap(int R, long long nnz, int count) {
-  // starts: multiples of kTileRows, window crossings (W >= kTileWindowMin), the rows at
-  // and after each long row, LP starts; plus the slices of the long rows
-  return (size_t)R / kTileRows + 5 * (size_t)(nnz / kTileWindowMin) + (size_t)count + 8;
+int tile_window(const TileShape& sh, int R, long long nnz) {
+  const double avg = R > 0 ? (double)nnz / (double)R : 1.0;
+  const double w = (double)sh.rows * avg;
+  return (int)std::max((double)sh.wmin, std::min((double)sh.wmax, w));
+}
+
+size_t tile_item_cap(const TileShape& sh, int R, long long nnz, int count) {
+  // starts: multiples of the row cap, crossings of the W-windows, the rows at and
+  // after each long row, LP starts; plus the slices of the long rows (at most
+  // nnz / W + one per long row); long rows number at most nnz / (kLongRow + 1)
+  const size_t W = (size_t)tile_window(sh, R, nnz), Z = (size_t)nnz;
+  const size_t nlong = Z / (kLongRow + 1) + 1;
+  return (size_t)R / sh.rows + 2 * (Z / W + 1) + 3 * nlong + (size_t)count + 8;
 }
 
 size_t tile_tmp_ints(int R) { return 4 * ((size_t)R + 1) + scan_tmp_ints((long long)R + 1) + 8; }
 
-cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0, int count,
-                        int* tmp, TileItem* items, int* item0, int* lng0, int* ticket,
-                        size_t item_cap, int* h_counts, int* W_out, cudaStream_t s) {
-  const int W = tile_window(R, nnz);
+cudaError_t setup_tiles(const TileShape& sh, const int* ptr, int R, long long nnz,
+                        const int* lp_row0, int count, int* tmp, TileItem* items, int* item0,
+                        int* lng0, int* ticket, size_t item_cap, int* h_counts, int* W_out,
+                        cudaStream_t s) {
+  const int W = tile_window(sh, R, nnz);
   *W_out = W;
   int* cnt = tmp;
   int* off = cnt + (R + 1);
@@ -970,7 +979,7 @@ cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0
   int* bsum = loff + (R + 1);
   const int G = device_sm_count() * 8;
   if (R > 0) {
-    k_tile_count<<<grid_for(R, G), kBlock, 0, s>>>(ptr, R, W, cnt, lfl);
+    k_tile_count<<<grid_for(R, G), kBlock, 0, s>>>(ptr, R, W, sh.rows, cnt, lfl);
     RET(cudaGetLastError());
     if (lp_row0 && count > 1) {
       k_tile_lp_starts<<<grid_for(count, G), kBlock, 0, s>>>(lp_row0, count, R, cnt);

@@ -81,12 +81,18 @@ cudaError_t setup_long_rows(const int* ptr, int nrows, int thresh, int* flags, i
 // (lp_row0[count]: each LP's first row, NULL for one LP), tickets zeroed.
 // h_counts[0] = items, h_counts[1] = long rows (read back; the stream is
 // synchronised).  cudaErrorInvalidValue if the items exceed item_cap.
-int tile_window(int R, long long nnz);
-size_t tile_item_cap(int R, long long nnz, int count);
+// form 1: the staged block tiles; form 2: warp tiles
+struct TileShape {
+  int rows, wmin, wmax;  // rows of an item at most; range of the window W
+};
+TileShape tile_shape(int form);
+int tile_window(const TileShape& sh, int R, long long nnz);
+size_t tile_item_cap(const TileShape& sh, int R, long long nnz, int count);
 size_t tile_tmp_ints(int R);
-cudaError_t setup_tiles(const int* ptr, int R, long long nnz, const int* lp_row0, int count,
-                        int* tmp, TileItem* items, int* item0, int* lng0, int* ticket,
-                        size_t item_cap, int* h_counts, int* W_out, cudaStream_t s);
+cudaError_t setup_tiles(const TileShape& sh, const int* ptr, int R, long long nnz,
+                        const int* lp_row0, int count, int* tmp, TileItem* items, int* item0,
+                        int* lng0, int* ticket, size_t item_cap, int* h_counts, int* W_out,
+                        cudaStream_t s);
 
 // ---- batches: many LPs set up together as one block-diagonal problem
 // One LP of a batch: its arrays (device) and its first global row, column and

@@ -173,12 +173,16 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.tcap_a = b.tcap_t = 0;
   size_t tile_tmp = 0;
   if (precision != PDLP_FP64) {
-    b.tcap_a = tile_item_cap(m, nnz, 1);
-    b.tcap_t = tile_item_cap(n, nnz, 1);
+    // both tile forms fit: block tiles keep one partial per warp and slot, warp tiles one
+    const TileShape s1 = tile_shape(1), s2 = tile_shape(2);
+    b.tcap_a = std::max(tile_item_cap(s1, m, nnz, 1), tile_item_cap(s2, m, nnz, 1));
+    b.tcap_t = std::max(tile_item_cap(s1, n, nnz, 1), tile_item_cap(s2, n, nnz, 1));
+    const size_t pa = std::max(kWarps * tile_item_cap(s1, m, nnz, 1), tile_item_cap(s2, m, nnz, 1));
+    const size_t pt = std::max(kWarps * tile_item_cap(s1, n, nnz, 1), tile_item_cap(s2, n, nnz, 1));
     b.ti_a = (TileItem*)ar.take(sizeof(TileItem) * b.tcap_a);
     b.ti_t = (TileItem*)ar.take(sizeof(TileItem) * b.tcap_t);
-    b.tpart_a = (float2*)ar.take(8 * kWarps * b.tcap_a);
-    b.tpart_t = (float2*)ar.take(8 * kWarps * b.tcap_t);
+    b.tpart_a = (float2*)ar.take(8 * pa);
+    b.tpart_t = (float2*)ar.take(8 * pt);
     for (float2** v : {&b.trow_a, &b.tlong_a}) *v = (float2*)ar.take(8 * b.tcap_a);
     for (float2** v : {&b.trow_t, &b.tlong_t}) *v = (float2*)ar.take(8 * b.tcap_t);
     b.tick_a = (int*)ar.take(4 * b.tcap_a);
@@ -214,12 +218,24 @@ static int tile_grid(int items, int resident) {
   return (items + rounds - 1) / rounds;
 }
 
-static cudaError_t tile_resident_mode(Mode mode, int* bp, int* bd) {
+static cudaError_t tile_resident_mode(Mode mode, int form, int* bp, int* bd) {
   switch (mode) {
-    case MODE_FP32: return tile_resident_fp32(bp, bd);
-    case MODE_BF16: return tile_resident_bf16(bp, bd);
-    case MODE_PAT: return tile_resident_pat(bp, bd);
+    case MODE_FP32: return tile_resident_fp32(form, bp, bd);
+    case MODE_BF16: return tile_resident_bf16(form, bp, bd);
+    case MODE_PAT: return tile_resident_pat(form, bp, bd);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+// Launch shape of the tile kernels of a form over `items` work items, with `resident`
+// blocks at most at once: grid (blocks) and workers (blocks, or warps for warp tiles).
+static void tile_launch(int form, int items, int resident, int* grid, int* workers) {
+  if (form == 2) {
+    const int w = tile_grid(items, kWarps * resident);
+    *grid = (w + kWarps - 1) / kWarps;
+    *workers = kWarps * *grid;
+  } else {
+    *grid = *workers = tile_grid(items, resident);
   }
 }
 
@@ -337,11 +353,11 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
     return fail(PDLP_ERR_INVALID_INPUT, "invalid parameter value");
   if (p->precision != PDLP_FP64 && p->precision != PDLP_FP32 && p->precision != PDLP_FP32_BF16A)
     return fail(PDLP_ERR_INVALID_INPUT, "unknown precision mode");
-  if (p->persistent != 0 && p->persistent != 1)
-    return fail(PDLP_ERR_INVALID_INPUT, "persistent must be 0 or 1");
+  if (p->persistent < 0 || p->persistent > 2)
+    return fail(PDLP_ERR_INVALID_INPUT, "persistent must be 0, 1 or 2");
   if (p->autotune != 0 && p->autotune != 1)
     return fail(PDLP_ERR_INVALID_INPUT, "autotune must be 0 or 1");
-  if (p->tiles != 0 && p->tiles != 1) return fail(PDLP_ERR_INVALID_INPUT, "tiles must be 0 or 1");
+  if (p->tiles < 0 || p->tiles > 2) return fail(PDLP_ERR_INVALID_INPUT, "tiles must be 0, 1 or 2");
   if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)) ||
       (p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
       (p->lanes_kkt_AT && !valid_lanes(p->lanes_kkt_AT)))
@@ -474,13 +490,14 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   so->n_ta = so->n_tt = 0;
   if (build_tiles && fp32 && p->tiles && !p->persistent && bf.tcap_t > 0) {
     int cnt[2] = {0, 0}, W = 0;
-    CUDA_TRY(setup_tiles(bf.a_ptr, m, nnz, nullptr, 1, bf.tmp, bf.ti_a, bf.tlp_a, bf.tlp_a + 2,
+    const TileShape tsh = tile_shape(p->tiles);
+    CUDA_TRY(setup_tiles(tsh, bf.a_ptr, m, nnz, nullptr, 1, bf.tmp, bf.ti_a, bf.tlp_a, bf.tlp_a + 2,
                          bf.tick_a, bf.tcap_a, cnt, &W, s));
     so->n_ta = cnt[0];
-    CUDA_TRY(setup_tiles(bf.t_ptr, n, nnz, nullptr, 1, bf.tmp, bf.ti_t, bf.tlp_t, bf.tlp_t + 2,
+    CUDA_TRY(setup_tiles(tsh, bf.t_ptr, n, nnz, nullptr, 1, bf.tmp, bf.ti_t, bf.tlp_t, bf.tlp_t + 2,
                          bf.tick_t, bf.tcap_t, cnt, &W, s));
     so->n_tt = cnt[0];
-    so->tiles = 1;
+    so->tiles = p->tiles;
     g_launches += 14;
   }
   CUDA_TRY(cudaStreamSynchronize(s));  // scalars
@@ -768,12 +785,13 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   ir.count = 1;
   if (so.tiles) {
     int bp = 0, bd = 0;
-    CUDA_TRY(tile_resident_mode(mode, &bp, &bd));
-    ir.tile = 1;
+    CUDA_TRY(tile_resident_mode(mode, so.tiles, &bp, &bd));
+    ir.tile = so.tiles;
+    ir.tslot = so.tiles == 1 ? kWarps : 1;
     ir.tt = TileSet{bf.ti_t, so.n_tt, bf.tlp_t, bf.tlp_t + 2, bf.tpart_t, bf.trow_t, bf.tlong_t, bf.tick_t};
     ir.ta = TileSet{bf.ti_a, so.n_ta, bf.tlp_a, bf.tlp_a + 2, bf.tpart_a, bf.trow_a, bf.tlong_a, bf.tick_a};
-    ir.grid_tt = tile_grid(so.n_tt, bp);
-    ir.grid_ta = tile_grid(so.n_ta, bd);
+    tile_launch(so.tiles, so.n_tt, bp, &ir.grid_tt, &ir.work_tt);
+    tile_launch(so.tiles, so.n_ta, bd, &ir.grid_ta, &ir.work_ta);
   }
 
   KktRaw kr{};
@@ -888,13 +906,15 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   if (p->persistent) {
     // the resident grid of the persistent kernel (probe launch with nothing to do:
     // the state says check_due, so every block returns at entry)
+    // persistent = 2: one block (small LPs: the grid barrier is the block's barrier)
+    const int want = p->persistent == 2 ? 1 : 0;
     int g = 0;
     cudaError_t e;
     switch (mode) {
-      case MODE_FP64: e = launch_persist_fp64(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
-      case MODE_FP32: e = launch_persist_fp32(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
-      case MODE_BF16: e = launch_persist_bf16(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
-      default: e = launch_persist_pat(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &g, s); break;
+      case MODE_FP64: e = launch_persist_fp64(sv.lanes_a, sv.lanes_t, sv.ir, 0, want, &g, s); break;
+      case MODE_FP32: e = launch_persist_fp32(sv.lanes_a, sv.lanes_t, sv.ir, 0, want, &g, s); break;
+      case MODE_BF16: e = launch_persist_bf16(sv.lanes_a, sv.lanes_t, sv.ir, 0, want, &g, s); break;
+      default: e = launch_persist_pat(sv.lanes_a, sv.lanes_t, sv.ir, 0, want, &g, s); break;
     }
     ++g_launches;
     if (e != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("persistent kernel: ") + cudaGetErrorString(e));
@@ -1429,8 +1449,10 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     int *tick_a, *tick_t, *tlp_a, *tlp_t, *row0_a, *row0_t;
   } g{};
   const bool use_tiles = mode != MODE_FP64 && p->tiles && !p->persistent;
-  const size_t tcap_a = use_tiles ? tile_item_cap((int)M, Z, count) : 0;
-  const size_t tcap_t = use_tiles ? tile_item_cap((int)N, Z, count) : 0;
+  const TileShape tsh = tile_shape(p->tiles);
+  const size_t tcap_a = use_tiles ? tile_item_cap(tsh, (int)M, Z, count) : 0;
+  const size_t tcap_t = use_tiles ? tile_item_cap(tsh, (int)N, Z, count) : 0;
+  const size_t tslot = p->tiles == 1 ? kWarps : 1;  // partials per slot
   // long rows and launch maps need the setup first: upper bounds here
   const int MB = max_blocks();
   const int budget = 4 * MB;
@@ -1487,8 +1509,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     if (use_tiles) {
       g.ti_a = (TileItem*)ar.take(sizeof(TileItem) * tcap_a);
       g.ti_t = (TileItem*)ar.take(sizeof(TileItem) * tcap_t);
-      g.tpart_a = (float2*)ar.take(8 * kWarps * tcap_a);
-      g.tpart_t = (float2*)ar.take(8 * kWarps * tcap_t);
+      g.tpart_a = (float2*)ar.take(8 * tslot * tcap_a);
+      g.tpart_t = (float2*)ar.take(8 * tslot * tcap_t);
       for (float2** v : {&g.trow_a, &g.tlong_a}) *v = (float2*)ar.take(8 * tcap_a);
       for (float2** v : {&g.trow_t, &g.tlong_t}) *v = (float2*)ar.take(8 * tcap_t);
       g.tick_a = (int*)ar.take(4 * tcap_a);
@@ -1745,18 +1767,19 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     CUDA_TRY(cudaMemcpyAsync(g.row0_a, r0a.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(g.row0_t, r0t.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
     int ca[2] = {0, 0}, ct[2] = {0, 0}, W = 0;
-    CUDA_TRY(setup_tiles(g.a_ptr, (int)M, Z, g.row0_a, count, g.tmp, g.ti_a, g.tlp_a,
+    CUDA_TRY(setup_tiles(tsh, g.a_ptr, (int)M, Z, g.row0_a, count, g.tmp, g.ti_a, g.tlp_a,
                          g.tlp_a + count + 1, g.tick_a, tcap_a, ca, &W, s));
-    CUDA_TRY(setup_tiles(g.t_ptr, (int)N, Z, g.row0_t, count, g.tmp, g.ti_t, g.tlp_t,
+    CUDA_TRY(setup_tiles(tsh, g.t_ptr, (int)N, Z, g.row0_t, count, g.tmp, g.ti_t, g.tlp_t,
                          g.tlp_t + count + 1, g.tick_t, tcap_t, ct, &W, s));
     g_launches += 16;
     int bp = 0, bd = 0;
-    CUDA_TRY(tile_resident_mode((Mode)mode, &bp, &bd));
-    ir.tile = 1;
+    CUDA_TRY(tile_resident_mode((Mode)mode, p->tiles, &bp, &bd));
+    ir.tile = p->tiles;
+    ir.tslot = (int)tslot;
     ir.tt = TileSet{g.ti_t, ct[0], g.tlp_t, g.tlp_t + count + 1, g.tpart_t, g.trow_t, g.tlong_t, g.tick_t};
     ir.ta = TileSet{g.ti_a, ca[0], g.tlp_a, g.tlp_a + count + 1, g.tpart_a, g.trow_a, g.tlong_a, g.tick_a};
-    ir.grid_tt = tile_grid(ct[0], bp);
-    ir.grid_ta = tile_grid(ca[0], bd);
+    tile_launch(p->tiles, ct[0], bp, &ir.grid_tt, &ir.work_tt);
+    tile_launch(p->tiles, ca[0], bd, &ir.grid_ta, &ir.work_ta);
   }
   KktRaw kr{};
   kr.a_ptr = g.a_ptr; kr.a_col = g.a_col; kr.a_val64 = mode == MODE_PAT ? nullptr : g.a_val64;

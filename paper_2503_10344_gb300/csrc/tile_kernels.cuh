@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_tile(IterData<float, V> d) {
           a += __shfl_xor_sync(0xffffffffu, a, off);
           c2 += __shfl_xor_sync(0xffffffffu, c2, off);
         }
+        int fin = 0;
         if (lane == 0) {
           slice_part[s][warp] = make_float2(a, c2);
           __threadfence_block();
@@ -472,31 +473,40 @@ __global__ void __launch_bounds__(kBlock, 4) k_tile(IterData<float, V> d) {
             }
             ts.rowpart[gi] = make_float2(sa, sb);
             __threadfence();
-            if (atomicAdd(&ts.ticket[it.first], 1) == it.nsl - 1) {  // the last slice: the row
-              __threadfence();
-              float ra = 0.0f, rb = 0.0f;
-              for (int k = 0; k < it.nsl; ++k) {
-                const float2 pv = __ldcg(ts.rowpart + it.first + k);
-                ra += pv.x;
-                rb += pv.y;
-              }
-              const int r = it.r0;
-              if (DUAL) {
-                const float* y = mt.cur ? d.y[1] : d.y[0];
-                ts.lterm[it.lid] = dual_row<IMPLICIT>(
-                    ra, rb, d.q[r], IMPLICIT ? d.sw[r] : 1.0f, d.row_kind[r], y[r],
-                    mt.pw != 0.0f ? d.sum_y[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.y[0] : d.y[1],
-                    d.sum_y, r);
-              } else {
-                const float2* x = mt.cur ? d.x[1] : d.x[0];
-                const float tm = primal_row<IMPLICIT>(
-                    ra, d.c[r], d.l[r], d.u[r], IMPLICIT ? d.tw[r] : 1.0f, x[r].x,
-                    mt.pw != 0.0f ? d.sum_x[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.x[0] : d.x[1],
-                    d.sum_x, r);
-                ts.lterm[it.lid] = make_float2(tm, 0.0f);
-              }
-              ts.ticket[it.first] = 0;  // ready for the next launch
+            fin = atomicAdd(&ts.ticket[it.first], 1) == it.nsl - 1;
+          }
+        }
+        fin = __shfl_sync(0xffffffffu, fin, 0);
+        if (fin) {  // the last slice: the warp adds the slices' partials, lane 0 finishes the row
+          __threadfence();
+          float ra = 0.0f, rb = 0.0f;
+          for (int k = lane; k < it.nsl; k += 32) {
+            const float2 pv = __ldcg(ts.rowpart + it.first + k);
+            ra += pv.x;
+            rb += pv.y;
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            ra += __shfl_xor_sync(0xffffffffu, ra, off);
+            rb += __shfl_xor_sync(0xffffffffu, rb, off);
+          }
+          if (lane == 0) {
+            const int r = it.r0;
+            if (DUAL) {
+              const float* y = mt.cur ? d.y[1] : d.y[0];
+              ts.lterm[it.lid] = dual_row<IMPLICIT>(
+                  ra, rb, d.q[r], IMPLICIT ? d.sw[r] : 1.0f, d.row_kind[r], y[r],
+                  mt.pw != 0.0f ? d.sum_y[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.y[0] : d.y[1],
+                  d.sum_y, r);
+            } else {
+              const float2* x = mt.cur ? d.x[1] : d.x[0];
+              const float tm = primal_row<IMPLICIT>(
+                  ra, d.c[r], d.l[r], d.u[r], IMPLICIT ? d.tw[r] : 1.0f, x[r].x,
+                  mt.pw != 0.0f ? d.sum_x[r] : 0.0f, mt.step, mt.pw, mt.cur ? d.x[0] : d.x[1],
+                  d.sum_x, r);
+              ts.lterm[it.lid] = make_float2(tm, 0.0f);
             }
+            ts.ticket[it.first] = 0;  // ready for the next launch
           }
         }
       }

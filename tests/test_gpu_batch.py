@@ -60,7 +60,7 @@ def test_batch_of_fixed_cover_subproblems(P):
     leaves them), float32 iterates on the pattern matrix."""
     sizes = [int(m) for m in np.random.default_rng(0).integers(2000, 6001, size=12)]
     lps = [lpgen.set_cover_fixed(4000 + k, m) for k, m in enumerate(sizes)]
-    for tiles in (0, 1):
+    for tiles in (0, 1, 2):
         xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="bf16", tiles=tiles))
         for k, (lp, x, y, r) in enumerate(zip(lps, xs, ys, res)):
             assert r["status"] == P.PDLP_OPTIMAL and r["precision_used"] == 3 and r["tiles"] == tiles

@@ -48,6 +48,21 @@ def obj_err(obj, key):
     return abs(obj - opt) / (1.0 + abs(obj) + abs(opt))
 
 
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as G
+    G.build()
+    import paper_2503_10344_gb300 as P
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1.0, np.linalg.norm(b)))
+
+
+skewed_lp = lpgen.skewed_lp
+
+
 GOLDEN_KEY = {"mip_relaxation_200x400": "mip_relaxation(1)",
               "set_cover_2000x8000": "set_cover(7,m=2000,n=8000)",
               "energy_system_24h": "energy_system(hours=24)",
@@ -476,6 +491,27 @@ def test_persistent_kernel_matches_two_launch_form(P, name):
     assert r1["kernel_launches"] < r0["kernel_launches"]
 
 
+@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "random_free_eq_300x500",
+                                  "set_cover_2000x8000"])
+def test_one_block_persistent_kernel_matches_two_launch_form(P, name):
+    """persistent = 2 runs the persistent kernel as one block (the small-LP form): the same
+    iteration to rounding after 300 fixed steps, and an adaptive solve to 1e-8 on the
+    200 x 400 relaxation matching HiGHS's optimum."""
+    lp = inst(name)
+    kw = dict(iter_limit=300, adaptive_step=0, restarts=0, terminate=0, fixed_eta=0.9)
+    _, _, r2, it2 = gpu_iterates(P, lp, persistent=2, **kw)
+    _, _, r0, it0 = gpu_iterates(P, lp, persistent=0, **kw)
+    assert r2["iters"] == r0["iters"] == 300
+    for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
+        assert rel(it2[k], it0[k]) <= 1e-13, k
+    if name == "mip_relaxation_200x400":
+        x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-8, persistent=2))
+        assert r["status"] == P.PDLP_OPTIMAL
+        assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-8
+        obj, _, _, _ = R.highs(lp)
+        assert abs(r["primal_obj"] - obj) / (1 + abs(obj)) <= 1e-7
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_persistent_and_two_launch_reach_the_same_tolerance(P, prec):
     lp = inst("set_cover_2000x8000")
@@ -488,7 +524,7 @@ def test_persistent_and_two_launch_reach_the_same_tolerance(P, prec):
 def test_persistent_parameter_is_checked(P):
     lp = inst("mip_relaxation_200x400")
     with pytest.raises(P.PdlpError):
-        P.pdlp_solve(lp, P.default_params(persistent=2))
+        P.pdlp_solve(lp, P.default_params(persistent=3))
 
 
 # ---------------------------------------------------------------- launch-shape autotuner

@@ -64,16 +64,20 @@ def inst(name):
 FIXED = dict(adaptive_step=0, restarts=0, terminate=0, fixed_eta=0.9)
 
 
+FORMS = [1, 2]  # staged block tiles, warp tiles
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("name", list(INSTANCES))
 @pytest.mark.parametrize("K", [1, 10, 60])
-def test_tile_iterates_match_lanes_and_oracle(P, name, K):
+def test_tile_iterates_match_lanes_and_oracle(P, name, K, form):
     lp = inst(name)
     prec = INSTANCES[name][1]
-    _, _, rt, it_t = P.pdlp_solve(lp, P.default_params(iter_limit=K, precision=prec, tiles=1, **FIXED),
-                                  iterates=True)
+    _, _, rt, it_t = P.pdlp_solve(lp, P.default_params(iter_limit=K, precision=prec, tiles=form,
+                                                       **FIXED), iterates=True)
     _, _, rl, it_l = P.pdlp_solve(lp, P.default_params(iter_limit=K, precision=prec, tiles=0, **FIXED),
                                   iterates=True)
-    assert rt["tiles"] == 1 and rl["tiles"] == 0
+    assert rt["tiles"] == form and rl["tiles"] == 0
     assert rt["iters"] == rl["iters"] == K
     ref = O.solve(lp, O.Params(iter_limit=K, adaptive=False, restarts=False, terminate=False,
                                fixed_eta=0.9))
@@ -83,22 +87,24 @@ def test_tile_iterates_match_lanes_and_oracle(P, name, K):
         assert rel(it_t[k], want) <= F32, (k, rel(it_t[k], want))
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("name", list(INSTANCES))
-def test_tile_solve_reaches_tolerance(P, name):
+def test_tile_solve_reaches_tolerance(P, name, form):
     lp = inst(name)
     prec = INSTANCES[name][1]
-    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec, tiles=1))
-    assert r["status"] == P.PDLP_OPTIMAL and r["tiles"] == 1
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec, tiles=form))
+    assert r["status"] == P.PDLP_OPTIMAL and r["tiles"] == form
     k = O.kkt_original(lp, x, y)
     assert k.rel_kkt <= 1.01e-4, k
     assert r["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
     assert T.obj_err(r["primal_obj"], INSTANCES[name][2]) <= T.OBJ_TOL
 
 
-def test_tiles_are_deterministic(P):
+@pytest.mark.parametrize("form", FORMS)
+def test_tiles_are_deterministic(P, form):
     lp = inst("long_rows_6500x3000")
-    runs = [P.pdlp_solve(lp, P.default_params(iter_limit=300, terminate=0, precision="fp32"),
-                         iterates=True) for _ in range(2)]
+    runs = [P.pdlp_solve(lp, P.default_params(iter_limit=300, terminate=0, precision="fp32",
+                                              tiles=form), iterates=True) for _ in range(2)]
     for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
         assert np.array_equal(runs[0][3][k], runs[1][3][k]), k
     assert runs[0][2]["attempts"] == runs[1][2]["attempts"]
@@ -112,7 +118,7 @@ def test_float64_ignores_tiles(P):
 
 def test_tiles_parameter_is_checked(P):
     with pytest.raises(P.PdlpError):
-        P.pdlp_solve(inst("mip_relaxation_200x400"), P.default_params(tiles=2))
+        P.pdlp_solve(inst("mip_relaxation_200x400"), P.default_params(tiles=3))
 
 
 def batch_lps():
@@ -121,25 +127,27 @@ def batch_lps():
             lpgen.mip_relaxation(2, m=60, n=90), short_rows_lp(m=500, n=3000, seed=4)]
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("K", [1, 30])
-def test_batch_tiles_match_lanes(P, K):
+def test_batch_tiles_match_lanes(P, K, form):
     """Every LP of a float32 batch ends at the same point with tiles and with lanes
     (fixed step, no restarts: the returned point of each LP after K steps)."""
     lps = batch_lps()
-    xt, yt, rt = P.pdlp_solve_batch(lps, P.default_params(iter_limit=K, precision="fp32", tiles=1,
+    xt, yt, rt = P.pdlp_solve_batch(lps, P.default_params(iter_limit=K, precision="fp32", tiles=form,
                                                           **FIXED))
     xl, yl, rl = P.pdlp_solve_batch(lps, P.default_params(iter_limit=K, precision="fp32", tiles=0,
                                                           **FIXED))
     for lp, a, b, c, d, r1, r2 in zip(lps, xt, xl, yt, yl, rt, rl):
-        assert r1["tiles"] == 1 and r2["tiles"] == 0
+        assert r1["tiles"] == form and r2["tiles"] == 0
         assert r1["iters"] == r2["iters"] == K
         assert rel(a, b) <= F32, (lp.name, rel(a, b))
         assert rel(c, d) <= F32, (lp.name, rel(c, d))
 
 
-def test_batch_tiles_reach_tolerance(P):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_tiles_reach_tolerance(P, form):
     lps = batch_lps()
-    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="fp32", tiles=1))
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision="fp32", tiles=form))
     for lp, x, y, r in zip(lps, xs, ys, res):
-        assert r["status"] == P.PDLP_OPTIMAL and r["tiles"] == 1, (lp.name, r)
+        assert r["status"] == P.PDLP_OPTIMAL and r["tiles"] == form, (lp.name, r)
         assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4, lp.name
