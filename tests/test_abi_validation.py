@@ -42,8 +42,9 @@ def _rejected(P, call, needle):
     ("ruiz_iters", -2, "invalid parameter value"),
     ("time_limit_s", 0.0, "invalid parameter value"),
     ("precision", 7, "unknown precision mode"),
-    ("persistent", 2, "persistent must be 0 or 1"),
+    ("persistent", 3, "persistent must be 0, 1 or 2"),
     ("autotune", -1, "autotune must be 0 or 1"),
+    ("tiles", 3, "tiles must be 0, 1 or 2"),
     ("lanes_A", 3, "lanes must be"),
     ("lanes_kkt_AT", 64, "lanes must be"),
 ])
