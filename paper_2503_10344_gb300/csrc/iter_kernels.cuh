@@ -108,102 +108,24 @@ __device__ __forceinline__ void rows_short(const Span& sp, const int* __restrict
   }
 }
 
-// Two rows per group and pass, rows g and g + G of the grid's G groups, their
-// loads interleaved in one loop (twice the loads in flight of one row at a
-// time).  The first row pair's row pointers and each lane's first kPre column
-// indices and values do not depend on the iterate: they are loaded BEFORE
-// `enter()` waits for the preceding kernel (programmatic dependent launch), so
-// after the wait a row costs its vector gathers; the epilogue operands
-// (`pref_c` constant, `pref_v` iterate) are issued alongside the gathers.  `enter()` returns false when the state says the kernel has
-// nothing to do (uniform over the block).  `val(p)` is the stored value at
-// position p, `term(v, j)` the row-sum term of value v and gathered entry j,
-// `fin(r, acc, pc, pv)` finishes a row.  Rows longer than `thresh` are skipped
-// (long-row blocks own them).
+// Two rows per group and pass, rows g and g + G of the grid's G groups, their loads
+// interleaved (twice the loads in flight of one row at a time), software-pipelined
+// across passes: while a pass gathers and finishes its row pair, each lane's first
+// kPre column indices and values of the next pair's rows (from row pointers loaded
+// one pass earlier) and the row pointers of the pair after it are already in
+// flight, so a pass waits on its gathers alone instead of on the row pointer ->
+// column index -> gather chain; entries beyond kPre per lane follow in a dependent
+// loop.  The first pair's pointers, indices and values and the second pair's
+// pointers are loaded BEFORE `enter()` waits for the preceding kernel (they do not
+// depend on the iterate).  The epilogue operands (`pref_c` constant, `pref_v`
+// iterate) are issued alongside the gathers.  `enter()` returns false when the state
+// says the kernel has nothing to do (uniform over the block).  `val(p)` is the
+// stored value at position p, `term(v, j)` the row-sum term of value v and gathered
+// entry j, `fin(r, acc, pc, pv)` finishes a row.  Rows longer than `thresh` are
+// skipped (long-row blocks own them).  (A prefetch depth of 4 measured slower:
+// register spills at the 64 registers of four blocks per SM.)
 constexpr int kPre = 2;
 
-template <int LANES, typename Acc, typename PC, typename PV, typename Val, typename Term,
-          typename PrefC, typename PrefV, typename Fin, typename Enter>
-__device__ __forceinline__ bool rows_short2(const Span& sp, const int* __restrict__ ptr,
-                                            const int* __restrict__ col, int thresh, Val val,
-                                            Term term, PrefC pref_c, PrefV pref_v, Fin fin,
-                                            Enter enter) {
-  using VT = decltype(val(0));
-  const int lane = threadIdx.x & (LANES - 1);
-  const long long G = (long long)sp.nshort * kBlock / LANES;
-  const long long end = (long long)sp.row0 + sp.nrows;
-  long long r0 = sp.row0 + ((long long)sp.bidx * kBlock + threadIdx.x) / LANES;
-  int s0 = 0, s1 = 0, n0 = 0, n1 = 0;
-  int c0[kPre], c1[kPre];
-  VT v0[kPre], v1[kPre];
-  PC pc0{}, pc1{};
-  auto fetch = [&](long long ra) {
-    const long long rb = ra + G;
-    s0 = __ldg(ptr + ra);
-    const int e0 = __ldg(ptr + ra + 1);
-    s1 = 0;
-    int e1 = 0;
-    if (rb < end) {
-      s1 = __ldg(ptr + rb);
-      e1 = __ldg(ptr + rb + 1);
-    }
-    n0 = e0 - s0 <= thresh ? e0 - s0 : -1;  // -1: a long row, not ours (uniform in the group)
-    n1 = rb < end ? (e1 - s1 <= thresh ? e1 - s1 : -1) : -1;
-#pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      const int q = lane + k * LANES;
-      c0[k] = q < n0 ? __ldg(col + s0 + q) : 0;
-      v0[k] = q < n0 ? val(s0 + q) : VT(0);
-      c1[k] = q < n1 ? __ldg(col + s1 + q) : 0;
-      v1[k] = q < n1 ? val(s1 + q) : VT(0);
-    }
-  };
-  if (r0 < end) fetch(r0);
-  if (!enter()) return false;
-  for (bool first = true; r0 < end; r0 += 2 * G, first = false) {
-    if (!first) fetch(r0);
-    const long long r1 = r0 + G;
-    PV pv0{}, pv1{};
-    if (lane == 0) {  // independent of the gathers below: issued together with them
-      if (n0 >= 0) {
-        pc0 = pref_c((int)r0);
-        pv0 = pref_v((int)r0);
-      }
-      if (n1 >= 0) {
-        pc1 = pref_c((int)r1);
-        pv1 = pref_v((int)r1);
-      }
-    }
-    Acc a0{}, a1{};
-#pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      const int q = lane + k * LANES;
-      if (q < n0) a0 += term(v0[k], c0[k]);
-      if (q < n1) a1 += term(v1[k], c1[k]);
-    }
-    const int nmax = n0 > n1 ? n0 : n1;
-#pragma unroll 2
-    for (int q = lane + kPre * LANES; q < nmax; q += LANES) {
-      if (q < n0) a0 += term(val(s0 + q), __ldg(col + s0 + q));
-      if (q < n1) a1 += term(val(s1 + q), __ldg(col + s1 + q));
-    }
-    a0 = group_sum<LANES>(a0);
-    a1 = group_sum<LANES>(a1);
-    if (lane == 0) {
-      if (n0 >= 0) fin((int)r0, a0, pc0, pv0);
-      if (n1 >= 0) fin((int)r1, a1, pc1, pv1);
-    }
-  }
-  return true;
-}
-
-// The same traversal as rows_short2, software-pipelined across passes: while a
-// pass gathers and finishes its row pair, the column indices and values of the next
-// pair (from row pointers loaded one pass earlier) and the row pointers of the pair
-// after it are already in flight, so a pass waits on its gathers alone instead of on
-// the row pointer -> column index -> gather chain.  The first pair's pointers,
-// indices and values and the second pair's pointers are loaded before `enter()`
-// (they do not depend on the iterate).  Same rows, same lanes, same summation order
-// as rows_short2.
 template <int LANES, typename Acc, typename PC, typename PV, typename Val, typename Term,
           typename PrefC, typename PrefV, typename Fin, typename Enter>
 __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restrict__ ptr,
