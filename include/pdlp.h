@@ -127,10 +127,15 @@ typedef struct {
   double fixed_eta;     /* > 0 overrides the initial step size eta0 */
   double fixed_omega;   /* > 0 overrides the initial primal weight omega0 */
   int terminate;        /* 1 (default): stop at tol; 0: run to iter_limit */
-  int lanes_A;          /* SpMV lanes per row of A in the step kernels (0 = automatic; 2,4,8,16,32) */
-  int lanes_AT;         /* SpMV lanes per row of A^T in the step kernels (0 = automatic) */
-  int lanes_kkt_A;      /* lanes per row of A in the float64 KKT pass (0 = automatic) */
-  int lanes_kkt_AT;     /* lanes per row of A^T in the float64 KKT pass (0 = automatic) */
+  int lanes_A;          /* SpMV lanes per row of A in the step kernels (0 = automatic:
+                           float32 iterates with persistent = 0 take 1 when an average
+                           row has at most 8 entries; 1, 2, 4, 8, 16, 32; 1 -- each
+                           thread sums and finishes whole rows -- only with
+                           persistent = 0) */
+  int lanes_AT;         /* SpMV lanes per row of A^T in the step kernels (as lanes_A) */
+  int lanes_kkt_A;      /* lanes per row of A in the float64 KKT pass (0 = automatic;
+                           2, 4, 8, 16, 32) */
+  int lanes_kkt_AT;     /* lanes per row of A^T in the float64 KKT pass (as lanes_kkt_A) */
   int verbose;          /* 0 quiet; 1 one line per KKT check on stderr; 2 also the host-side
                            time of each setup phase (synchronising the stream at each) */
   int persistent;       /* 1: the step attempts of a check period run in one cooperative
@@ -140,7 +145,8 @@ typedef struct {
                            kernel launches per attempt.  Same iteration either way; batches
                            always use the two-launch form. */
   int autotune;         /* 1: before iterating, time whole step attempts (primal kernel,
-                           dual kernel and decision) with 2, 4, 8, 16 and 32 lanes per row,
+                           dual kernel and decision) with 1 (float32 iterates and
+                           persistent = 0 only), 2, 4, 8, 16 and 32 lanes per row,
                            first for the primal kernel's A^T, then for the dual kernel's A,
                            on this LP without moving the iterate, and keep the fastest;
                            cached per (device, precision mode, m, n, nnz) for the process.
@@ -160,10 +166,13 @@ typedef struct {
                            work items of at most 256 rows and 1280 nonzeros (rows longer
                            than 256 entries in slices) into shared memory with bulk copies,
                            gathers from the staged indices and sums each row in storage
-                           order; 0 (default) uses the lanes-per-row kernels (lanes_A,
-                           lanes_AT).
+                           order; 2 runs the warp-tile kernels -- every warp owns work
+                           items of at most 32 rows and 64-256 nonzeros (longer rows in
+                           slices) and works through them without block-wide
+                           synchronisation; 0 (default) uses the lanes-per-row kernels
+                           (lanes_A, lanes_AT).
                            Same iteration either way; float32 sums differ in rounding.
-                           Ignored in float64 and with persistent = 1. */
+                           Ignored in float64 and with persistent != 0. */
 } pdlp_params;
 
 typedef struct {

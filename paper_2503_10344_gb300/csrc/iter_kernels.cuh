@@ -123,8 +123,12 @@ __device__ __forceinline__ void rows_short(const Span& sp, const int* __restrict
 // stored value at position p, `term(v, j)` the row-sum term of value v and gathered
 // entry j, `fin(r, acc, pc, pv)` finishes a row.  Rows longer than `thresh` are
 // skipped (long-row blocks own them).  (A prefetch depth of 4 measured slower:
-// register spills at the 64 registers of four blocks per SM.)
+// register spills at the 64 registers of four blocks per SM.)  With one lane per row
+// every thread finishes its own rows (no idle lanes in the epilogue, consecutive rows
+// on consecutive lanes) and prefetches kPre1 entries of each.
 constexpr int kPre = 2;
+constexpr int kPre1 = 3;
+template <int LANES> struct PreDepth { static constexpr int value = LANES == 1 ? kPre1 : kPre; };
 
 template <int LANES, typename Acc, typename PC, typename PV, typename Val, typename Term,
           typename PrefC, typename PrefV, typename Fin, typename Enter>
@@ -133,6 +137,7 @@ __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restric
                                             Term term, PrefC pref_c, PrefV pref_v, Fin fin,
                                             Enter enter) {
   using VT = decltype(val(0));
+  constexpr int KP = PreDepth<LANES>::value;
   const int lane = threadIdx.x & (LANES - 1);
   const long long G = (long long)sp.nshort * kBlock / LANES;
   const long long end = (long long)sp.row0 + sp.nrows;
@@ -140,9 +145,9 @@ __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restric
   struct Rows {  // a pair's starts and lengths (-1: a long row or no row)
     int s0, n0, s1, n1;
   };
-  struct Heads {  // each lane's first kPre column indices and values of the pair's rows
-    int c0[kPre], c1[kPre];
-    VT v0[kPre], v1[kPre];
+  struct Heads {  // each lane's first KP column indices and values of the pair's rows
+    int c0[KP], c1[KP];
+    VT v0[KP], v1[KP];
   };
   auto load_rows = [&](long long ra) -> Rows {
     Rows p{0, -1, 0, -1};
@@ -161,7 +166,7 @@ __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restric
   auto load_heads = [&](const Rows& p) -> Heads {
     Heads h;
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
+    for (int k = 0; k < KP; ++k) {
       const int q = lane + k * LANES;
       h.c0[k] = q < p.n0 ? __ldg(col + p.s0 + q) : 0;
       h.v0[k] = q < p.n0 ? val(p.s0 + q) : VT(0);
@@ -194,14 +199,14 @@ __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restric
     }
     Acc a0{}, a1{};
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
+    for (int k = 0; k < KP; ++k) {
       const int q = lane + k * LANES;
       if (q < rw.n0) a0 += term(hd.v0[k], hd.c0[k]);
       if (q < rw.n1) a1 += term(hd.v1[k], hd.c1[k]);
     }
     const int nmax = rw.n0 > rw.n1 ? rw.n0 : rw.n1;
 #pragma unroll 2
-    for (int q = lane + kPre * LANES; q < nmax; q += LANES) {
+    for (int q = lane + KP * LANES; q < nmax; q += LANES) {
       if (q < rw.n0) a0 += term(val(rw.s0 + q), __ldg(col + rw.s0 + q));
       if (q < rw.n1) a1 += term(val(rw.s1 + q), __ldg(col + rw.s1 + q));
     }
@@ -297,10 +302,10 @@ __device__ __forceinline__ void rows_all(const Span& sp, const int* ptr, int thr
 }
 
 // ---------------------------------------------------------------- A4: primal
-// resident blocks per SM the float32 step kernels are compiled for (register
-// budget 42): the float32 solve of the 50k x 200k covering LP needs 782 blocks
-// for one pass, six per SM keep them all resident; the float64 kernels keep
-// their registers (a tighter budget spills)
+// resident blocks per SM the float32 step kernels are compiled for (kStepBlocksPerSmF32,
+// a 64-register budget: the pipelined traversal holds two passes of row pointers and one
+// of column indices and values per lane); the float64 kernels keep their registers (a
+// tighter budget spills)
 template <typename T> struct StepOcc { static constexpr int value = kStepBlocksPerSmF32; };
 template <> struct StepOcc<double> { static constexpr int value = 1; };
 

@@ -121,6 +121,7 @@ cudaError_t launch_iter_t(int which, int lanes, const IterRaw& r, cudaStream_t s
     }
   }
   switch (lanes) {
+    case 1: return launch_one<1, T, V, IMPLICIT>(which, d, s);
     case 2: return launch_one<2, T, V, IMPLICIT>(which, d, s);
     case 4: return launch_one<4, T, V, IMPLICIT>(which, d, s);
     case 8: return launch_one<8, T, V, IMPLICIT>(which, d, s);

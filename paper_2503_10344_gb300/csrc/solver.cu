@@ -205,9 +205,29 @@ static int auto_lanes(double avg_len, double per_lane) {
   return l;
 }
 
-static int long_thresh(int lanes) { return std::max(1024, 128 * lanes); }
+// Lanes per row of a float32 step kernel: one lane per row (every thread sums and
+// finishes whole rows: no idle lanes in the epilogue, consecutive rows on consecutive
+// lanes) when an average row has at most kOneLaneAvg entries and the two-launch kernels
+// run (`one_ok`), else auto_lanes.  Measured on GB300 with float32 iterates: the energy
+// system (2.10M x 2.45M, 3.75 / 3.2 entries per row of A / A^T) 96.8 -> 75.6 us per
+// attempt; the primal kernel of the 256 covering sub-LPs (6.5 entries per column)
+// 527 -> 449 us, of the 50k x 200k covering LP 20.7 -> 19.9 us per attempt; over the
+// covering rows (26 entries) one lane per row is 1.4-4x slower.
+constexpr double kOneLaneAvg = 8.0;
+static int step_lanes(double avg_len, double per_lane, bool one_ok) {
+  return one_ok && avg_len <= kOneLaneAvg ? 1 : auto_lanes(avg_len, per_lane);
+}
+
+// Rows longer than this go to the long-row blocks (one block per row).  With one lane
+// per row a thread walks its rows' entries one after another, so the cut-off is low.
+static int long_thresh(int step_lanes, int kkt_lanes) {
+  return step_lanes == 1 ? 64 : std::max(1024, 128 * std::max(step_lanes, kkt_lanes));
+}
 
 static bool valid_lanes(int l) { return l == 2 || l == 4 || l == 8 || l == 16 || l == 32; }
+// the two-launch step kernels also take one lane per row (the persistent kernel and the
+// KKT passes do not)
+static bool valid_step_lanes(int l) { return l == 1 || valid_lanes(l); }
 
 // Grid of a staged tile kernel over `items` work items with at most `resident`
 // blocks at once: every block gets the same number of items, give or take one
@@ -358,10 +378,13 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
   if (p->autotune != 0 && p->autotune != 1)
     return fail(PDLP_ERR_INVALID_INPUT, "autotune must be 0 or 1");
   if (p->tiles < 0 || p->tiles > 2) return fail(PDLP_ERR_INVALID_INPUT, "tiles must be 0, 1 or 2");
-  if ((p->lanes_A && !valid_lanes(p->lanes_A)) || (p->lanes_AT && !valid_lanes(p->lanes_AT)) ||
-      (p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
+  if ((p->lanes_A && !valid_step_lanes(p->lanes_A)) || (p->lanes_AT && !valid_step_lanes(p->lanes_AT)))
+    return fail(PDLP_ERR_INVALID_INPUT, "step lanes must be 0, 1, 2, 4, 8, 16 or 32");
+  if ((p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
       (p->lanes_kkt_AT && !valid_lanes(p->lanes_kkt_AT)))
-    return fail(PDLP_ERR_INVALID_INPUT, "lanes must be 0, 2, 4, 8, 16 or 32");
+    return fail(PDLP_ERR_INVALID_INPUT, "KKT lanes must be 0, 2, 4, 8, 16 or 32");
+  if (p->persistent && (p->lanes_A == 1 || p->lanes_AT == 1))
+    return fail(PDLP_ERR_INVALID_INPUT, "one lane per row needs persistent = 0");
   return PDLP_OK;
 }
 
@@ -463,8 +486,9 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
   // ---- launch shapes and long rows
   const double avg_a = m ? (double)nnz / m : 1.0, avg_t = (double)nnz / n;
   const double per_lane = mode == MODE_FP64 ? 8.0 : 4.0;
-  int lanes_a = p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane);
-  int lanes_t = p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane);
+  const bool one_ok = mode != MODE_FP64 && !p->persistent;
+  int lanes_a = p->lanes_A ? p->lanes_A : step_lanes(avg_a, per_lane, one_ok);
+  int lanes_t = p->lanes_AT ? p->lanes_AT : step_lanes(avg_t, per_lane, one_ok);
   int lanes_ka = p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0);
   int lanes_kt = p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0);
   if (forced_lanes) {
@@ -473,8 +497,8 @@ static int setup_lp(const pdlp_csr* A, const double* b, const char* sense, const
     lanes_ka = forced_lanes[2];
     lanes_kt = forced_lanes[3];
   }
-  const int th_a = long_thresh(std::max(lanes_a, lanes_ka));
-  const int th_t = long_thresh(std::max(lanes_t, lanes_kt));
+  const int th_a = long_thresh(lanes_a, lanes_ka);
+  const int th_t = long_thresh(lanes_t, lanes_kt);
   int nlong_a = 0, nlong_t = 0;
   {
     const size_t R = (size_t)std::max(m, n) + 1;
@@ -568,8 +592,10 @@ constexpr int kTuneReps = 16;
 struct TuneKey {
   int dev, mode, count;
   long long m, n, nnz;
+  bool one_lane;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, mode, count, m, n, nnz) < std::tie(o.dev, o.mode, o.count, o.m, o.n, o.nnz);
+    return std::tie(dev, mode, count, m, n, nnz, one_lane) <
+           std::tie(o.dev, o.mode, o.count, o.m, o.n, o.nnz, o.one_lane);
   }
 };
 static std::mutex g_tune_mu;
@@ -579,11 +605,11 @@ static std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 // the launch shapes (grids, batch maps); set_dry(on) switches the state(s)
 // between dry mode (check_due 0, dry 1) and ready (check_due 1, dry 0).
 template <typename SetGrids, typename SetDry>
-static int autotune_lanes(Solve& sv, int count, bool tune_t, bool tune_a, SetGrids set_grids,
-                          SetDry set_dry) {
+static int autotune_lanes(Solve& sv, int count, bool tune_t, bool tune_a, bool one_lane,
+                          SetGrids set_grids, SetDry set_dry) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  const TuneKey key{dev, (int)sv.mode, count, sv.m, sv.n, sv.nnz};
+  const TuneKey key{dev, (int)sv.mode, count, sv.m, sv.n, sv.nnz, one_lane};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -646,12 +672,14 @@ static int autotune_lanes(Solve& sv, int count, bool tune_t, bool tune_a, SetGri
     g_launches += 2LL * 3 * kTuneReps;
     return PDLP_OK;
   };
-  static const int cand[5] = {2, 4, 8, 16, 32};
+  // one lane per row only for float32 iterates and the two-launch kernels
+  static const int cand[6] = {1, 2, 4, 8, 16, 32};
   for (int which : {IK_PRIMAL, IK_DUAL}) {
     if ((which == IK_PRIMAL && !tune_t) || (which == IK_DUAL && !tune_a)) continue;
     double best = INFINITY;
     int best_l = which == IK_PRIMAL ? sv.lanes_t : sv.lanes_a;
     for (int L : cand) {
+      if (L == 1 && !one_lane) continue;
       if (which == IK_PRIMAL) sv.lanes_t = L; else sv.lanes_a = L;
       if ((rc = set_grids(sv.lanes_t, sv.lanes_a)) != PDLP_OK) return rc;
       double ms = 0.0;
@@ -748,8 +776,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   // float32 step kernels: one group of lanes per two rows, rows grid-strided;
   // float64 kernels (float64 steps, KKT passes): warp tiles of 32 rows
   const bool tiled = mode == MODE_FP64;
-  // float32 step kernels: at most one wave of resident blocks (six per SM) including the
-  // long-row blocks, the short rows grid-strided; a second partial wave would trail
+  // float32 step kernels: at most one wave of resident blocks (kStepBlocksPerSmF32 per
+  // SM) including the long-row blocks, the short rows grid-strided; a second partial
+  // wave would trail
   const int lt_blk = std::min(nlong_t, kMaxLongBlocks), la_blk = std::min(nlong_a, kMaxLongBlocks);
   const int wave = kStepBlocksPerSmF32 * device_sm_count();
   const int MBp = std::max(device_sm_count(), wave - lt_blk);
@@ -900,7 +929,9 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       CUDA_TRY(cudaMemcpyAsync(&bf.st->dry, &v[on][1], sizeof(int), cudaMemcpyHostToDevice, s));
       return PDLP_OK;
     };
-    const int rc = autotune_lanes(sv, 1, !p->lanes_AT, !p->lanes_A, set_grids, set_dry);
+    const bool one_lane_ok = !tiled && !p->persistent;
+    const int rc = autotune_lanes(sv, 1, !p->lanes_AT, !p->lanes_A, one_lane_ok, set_grids,
+                                  set_dry);
     if (rc) return rc;
   }
   if (p->persistent) {
@@ -1415,8 +1446,9 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   const double step_bytes = 2.0 * (double)Z * 8.0 + 40.0 * (double)(M + N);
   const double per_lane_a =
       mode != MODE_FP64 && step_bytes > 256e6 ? 4.0 * per_lane : per_lane;
-  int lanes[4] = {p->lanes_A ? p->lanes_A : auto_lanes(avg_a, per_lane_a),
-                  p->lanes_AT ? p->lanes_AT : auto_lanes(avg_t, per_lane),
+  const bool one_ok = mode != MODE_FP64;  // batches always use the two-launch kernels
+  int lanes[4] = {p->lanes_A ? p->lanes_A : step_lanes(avg_a, per_lane_a, one_ok),
+                  p->lanes_AT ? p->lanes_AT : step_lanes(avg_t, per_lane, one_ok),
                   p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0),
                   p->lanes_kkt_AT ? p->lanes_kkt_AT : auto_lanes(avg_t, 8.0)};
   const size_t eb = mode == MODE_FP64 ? 8 : 4;
@@ -1650,8 +1682,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     g_launches += 4;
   }
   // long rows: one global list per orientation, each LP's part of it contiguous
-  const int th_a = long_thresh(std::max(lanes[0], lanes[2]));
-  const int th_t = long_thresh(std::max(lanes[1], lanes[3]));
+  const int th_a = long_thresh(lanes[0], lanes[2]);
+  const int th_t = long_thresh(lanes[1], lanes[3]);
   std::vector<int> nlong_a(count), nlong_t(count), long0_a(count), long0_t(count);
   long long la_total = 0, lt_total = 0;
   {
@@ -1836,7 +1868,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
       CUDA_TRY(cudaStreamSynchronize(s));
       return PDLP_OK;
     };
-    const int rc = autotune_lanes(sv, count, !p->lanes_AT, !p->lanes_A, set_grids, set_dry);
+    const int rc = autotune_lanes(sv, count, !p->lanes_AT, !p->lanes_A, mode != MODE_FP64, set_grids,
+                                  set_dry);
     if (rc) return rc;
     lanes[0] = sv.lanes_a;
     lanes[1] = sv.lanes_t;

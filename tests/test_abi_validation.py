@@ -45,11 +45,20 @@ def _rejected(P, call, needle):
     ("persistent", 3, "persistent must be 0, 1 or 2"),
     ("autotune", -1, "autotune must be 0 or 1"),
     ("tiles", 3, "tiles must be 0, 1 or 2"),
-    ("lanes_A", 3, "lanes must be"),
-    ("lanes_kkt_AT", 64, "lanes must be"),
+    ("lanes_A", 3, "step lanes must be"),
+    ("lanes_AT", 64, "step lanes must be"),
+    ("lanes_kkt_AT", 64, "KKT lanes must be"),
+    ("lanes_kkt_A", 1, "KKT lanes must be"),  # one lane per row: step kernels only
 ])
 def test_solve_rejects_invalid_parameters(P, lp, field, value, needle):
     _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(**{field: value})), needle)
+
+
+@pytest.mark.parametrize("persistent", [1, 2])
+@pytest.mark.parametrize("field", ["lanes_A", "lanes_AT"])
+def test_one_lane_per_row_needs_the_two_launch_form(P, lp, persistent, field):
+    _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(persistent=persistent, **{field: 1})),
+              "one lane per row needs persistent = 0")
 
 
 def test_solve_rejects_a_params_struct_of_another_size(P, lp):

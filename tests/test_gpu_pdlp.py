@@ -173,9 +173,59 @@ def test_adaptive_restarted_steps_by_replay(P, name):
     check_replay(P, inst(name), 150)
 
 
-@pytest.mark.parametrize("lanes", [(2, 2), (32, 32), (4, 16)])
+@pytest.mark.parametrize("lanes", [(2, 2), (32, 32), (4, 16), (1, 1), (1, 8)])
 def test_lanes_do_not_change_iterates(P, lanes):
     check_replay(P, inst("set_cover_2000x8000"), 150, lanes_A=lanes[0], lanes_AT=lanes[1])
+
+
+# float32 iterates against float64 after at most 60 fixed steps: a few hundred float32
+# roundings of relative size 6e-8 each
+F32 = 2e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("lanes", [(1, 1), (1, 4), (8, 1)])
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_one_lane_per_row_float32_iterates(P, name, lanes, prec):
+    """One lane per row (every thread sums and finishes whole rows, three entries of
+    each prefetched): after 60 fixed steps the float32 iterates agree with the float64
+    oracle's and with the two-lane kernels' to float32 rounding."""
+    lp = inst(name)
+    fixed = dict(iter_limit=60, adaptive_step=0, restarts=0, terminate=0, fixed_eta=0.9,
+                 precision=prec)
+    _, _, r1, it1 = gpu_iterates(P, lp, lanes_A=lanes[0], lanes_AT=lanes[1], **fixed)
+    _, _, r2, it2 = gpu_iterates(P, lp, lanes_A=2, lanes_AT=2, **fixed)
+    assert (r1["lanes_A"], r1["lanes_AT"]) == lanes
+    ref = O.solve(lp, O.Params(iter_limit=60, adaptive=False, restarts=False, terminate=False,
+                               fixed_eta=0.9))
+    for k, want in (("x_cur", ref.x_cur), ("y_cur", ref.y_cur), ("x_avg", ref.x_avg),
+                    ("y_avg", ref.y_avg)):
+        assert rel(it1[k], it2[k]) <= F32, (k, rel(it1[k], it2[k]))
+        assert rel(it1[k], want) <= F32, (k, rel(it1[k], want))
+
+
+def test_size_heuristic_lanes(P):
+    """Without autotune: float32 two-launch kernels take one lane per row where an average
+    row has at most 8 entries (covering columns: 6.5; energy rows and columns: 3.75 / 3.2),
+    the covering rows (26 entries) 8 lanes; the persistent kernel and float64 never one."""
+    kw = dict(iter_limit=5, terminate=0)
+    sc, en = inst("set_cover_2000x8000"), inst("energy_system_24h")
+    _, _, r = P.pdlp_solve(sc, P.default_params(precision="bf16", **kw))
+    assert (r["lanes_A"], r["lanes_AT"]) == (8, 1)
+    _, _, r = P.pdlp_solve(en, P.default_params(precision="fp32", **kw))
+    assert (r["lanes_A"], r["lanes_AT"]) == (1, 1)
+    for prm in (dict(precision="fp32", persistent=1), dict(precision="fp64")):
+        _, _, r = P.pdlp_solve(en, P.default_params(**prm, **kw))
+        assert min(r["lanes_A"], r["lanes_AT"]) >= 2, prm
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_one_lane_per_row_reaches_tolerance(P, name):
+    lp = inst(name)
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision="fp32", lanes_A=1, lanes_AT=1))
+    assert r["status"] == P.PDLP_OPTIMAL and r["lanes_A"] == r["lanes_AT"] == 1
+    assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4
+    assert obj_err(r["primal_obj"], GOLDEN_KEY[name]) <= OBJ_TOL
 
 
 def one_ulp_copy(lp, seed=0):
