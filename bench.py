@@ -150,16 +150,18 @@ class ClockSampler:
                 "reasons": reasons}
 
 
-def ncu_traffic(kernel: str, precision: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, if one exists for
-    this kernel version and precision (profiles/dram_traffic.txt), else None."""
+def ncu_traffic(kernel: str, precision: str, workload: str = "set_cover"):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu capture, if
+    one exists for this kernel version and precision (profiles/dram_traffic.txt), else
+    None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         f = line.split()
-        if len(f) == 3 and not line.startswith("#") and f[0] == kernel and f[1] == precision:
-            return float(f[2])
+        if (len(f) == 4 and not line.startswith("#") and f[0] == workload and f[1] == kernel
+                and f[2] == precision):
+            return float(f[3])
     return None
 
 
@@ -408,15 +410,18 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------------ other workloads
-def kernel_roofline(kt, peak, peak_source):
+def kernel_roofline(kt, peak, peak_source, workload=None, precision=None):
     """Roofline of the step kernels from pdlp_time_kernels: the dominant of the primal
-    step and the dual half-step, with every timed kernel's bytes, time and GB/s."""
+    step and the dual half-step, with every timed kernel's bytes, time and GB/s; the
+    dominant kernel's DRAM bytes per launch from the committed ncu capture of `workload`
+    (None where there is none)."""
     kern = {k: {"us": 1e3 * v["ms"], "bytes": v["bytes"], "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
                 "frac": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peak}
             for k, v in kt.items() if v["ms"] > 0}
     dom = max(("primal_step", "dual_step"), key=lambda k: kt[k]["ms"])
+    traffic = ncu_traffic(dom, precision, workload) if workload else None
     return {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": kern[dom]["frac"], "traffic": None, "peak_source": peak_source, "kernels": kern}
+            "frac": kern[dom]["frac"], "traffic": traffic, "peak_source": peak_source, "kernels": kern}
 
 
 def _peak():
@@ -473,7 +478,7 @@ def energy_section(args, dev, stream, peak):
                      "rel_kkt": res64["rel_kkt"], "primal_obj": obj64},
             "obj_rel_diff_vs_fp64": abs(res["primal_obj"] - obj64) / (1.0 + abs(obj64)),
             "speedup_vs_fp64_time_to_tol": ms64 / ms,
-            "roofline": kernel_roofline(kt, pk, src), "clocks": clk.summary()}
+            "roofline": kernel_roofline(kt, pk, src, "energy", "fp32"), "clocks": clk.summary()}
 
 
 def _batch_lps(count):
