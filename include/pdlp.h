@@ -139,11 +139,12 @@ typedef struct {
   int verbose;          /* 0 quiet; 1 one line per KKT check on stderr; 2 also the host-side
                            time of each setup phase (synchronising the stream at each) */
   int persistent;       /* 1: the step attempts of a check period run in one cooperative
-                           kernel with grid-wide barriers; 2: the same kernel as one block
-                           (small LPs, such as the 200 x 400 relaxations: the grid barrier
-                           is the block's barrier, no launch per attempt); 0 (default): two
-                           kernel launches per attempt.  Same iteration either way; batches
-                           always use the two-launch form. */
+                           kernel with grid-wide barriers; 2: one block per check period
+                           (small LPs, such as the 200 x 400 relaxations: no launch per
+                           attempt), which copies the LP into shared memory when it fits
+                           and otherwise runs the cooperative kernel as one block; 0
+                           (default): two kernel launches per attempt.  Same iteration
+                           either way; batches always use the two-launch form. */
   int autotune;         /* 1: before iterating, time whole step attempts (primal kernel,
                            dual kernel and decision) with 1 (float32 iterates and
                            persistent = 0 only), 2, 4, 8, 16 and 32 lanes per row,
@@ -194,9 +195,16 @@ typedef struct {
   double ray_obj;         /* certificate statuses: d^ (PRIMAL_INFEASIBLE) or c^T x^
                              (DUAL_INFEASIBLE); NaN otherwise */
   double ray_res;         /* the 2-norm of the certificate's residual; NaN otherwise */
-  int tiles;              /* 1 if the staged tile step kernels ran (pdlp_params.tiles) */
+  int tiles;              /* the tile step kernels that ran (pdlp_params.tiles): 0 none,
+                             1 staged block tiles, 2 warp tiles */
   double upload_s;        /* batches from host buffers: the host-to-device copies of the
                              inputs (setup_s is the device setup after them); 0 otherwise */
+  int persistent_form;    /* how the step attempts ran: 0 two launches per attempt,
+                             1 one cooperative kernel per check period, 2 one block per
+                             check period stepping from global memory, 3 one block with
+                             the LP held in shared memory (persistent = 2 when the matrix,
+                             vectors and iterates fit: 73 KB for a 200 x 400 relaxation
+                             with 1,600 nonzeros in float64) */
 } pdlp_result;
 
 /* Optional diagnostic outputs (same memory space as the entry point's outputs;

@@ -54,7 +54,7 @@ class PdlpResult(C.Structure):
                 ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("lanes_A", C.c_int),
                 ("lanes_AT", C.c_int), ("ray_obj", C.c_double), ("ray_res", C.c_double),
-                ("tiles", C.c_int), ("upload_s", C.c_double)]
+                ("tiles", C.c_int), ("upload_s", C.c_double), ("persistent_form", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

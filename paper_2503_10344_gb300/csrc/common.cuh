@@ -14,6 +14,9 @@ constexpr int kBlock = 256;         // threads per block of every streaming kern
 constexpr int kWarps = kBlock / 32;
 // resident blocks per SM the float32 step kernels are compiled for
 constexpr int kStepBlocksPerSmF32 = 4;
+// static shared memory the one-block shared-memory step kernel keeps for itself (its
+// copy of the state and the block reductions), subtracted from the device's opt-in limit
+constexpr int kSmemStatic = 2048;
 
 // Matrix value formats of the iteration matrix.
 struct Pattern {};  // every stored value is exactly +1: no value array at all

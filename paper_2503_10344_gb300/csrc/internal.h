@@ -13,6 +13,49 @@ namespace pdlp {
 
 enum Mode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_BF16 = 2, MODE_PAT = 3 };
 
+// Byte offsets of the one-block shared-memory step kernel's copy of an LP
+// (smem_kernels.cuh; 16-byte aligned, -1: absent); bytes = 0: the kernel is not used.
+struct SmemLayout {
+  int t_ptr, t_col, t_val, a_ptr, a_col, a_val;
+  int c, l, u, tw, q, sw, kind, x0, x1, y0, y1, sx, sy;
+  int bytes;
+};
+
+// Shared memory the kernel needs for an LP of m rows, n columns and nnz nonzeros with
+// iterate elements of `it` bytes; `vals`: the values are stored (not a 0/1 pattern);
+// `implicit`: the per-element step weights tw / sw are kept.  bytes saturates at 2^30.
+inline SmemLayout smem_layout(long long m, long long n, long long nnz, int it, bool vals,
+                              bool implicit) {
+  SmemLayout L;
+  long long o = 0;
+  auto take = [&o](long long b) -> int {
+    const long long r = o;
+    o += (b + 15) / 16 * 16;
+    return (int)(r < (1LL << 30) ? r : (1LL << 30));
+  };
+  L.t_ptr = take(4 * (n + 1));
+  L.t_col = take(4 * nnz);
+  L.t_val = vals ? take(it * nnz) : -1;
+  L.a_ptr = take(4 * (m + 1));
+  L.a_col = take(4 * nnz);
+  L.a_val = vals ? take(it * nnz) : -1;
+  L.c = take(it * n);
+  L.l = take(it * n);
+  L.u = take(it * n);
+  L.tw = implicit ? take(it * n) : -1;
+  L.q = take(it * m);
+  L.sw = implicit ? take(it * m) : -1;
+  L.kind = take(m);
+  L.x0 = take(2 * it * n);
+  L.x1 = take(2 * it * n);
+  L.y0 = take(it * m);
+  L.y1 = take(it * m);
+  L.sx = take(it * n);
+  L.sy = take(it * m);
+  L.bytes = (int)(o < (1LL << 30) ? o : (1LL << 30));
+  return L;
+}
+
 struct IterRaw {
   const int *a_ptr, *a_col;
   const void* a_val;
@@ -38,6 +81,9 @@ struct IterRaw {
   int grid_tt, grid_ta;  // their grids (blocks)
   int work_tt, work_ta;  // workers (blocks or warps): k_decide reads one slot per worker and LP
   int tslot;             // partials per slot (8 for block tiles, 1 for warp tiles)
+  // one-block persistent form (persistent = 2): smem.bytes > 0 runs k_smem, the LP held in
+  // that much shared memory; 0 runs the one-block k_persist from global memory
+  SmemLayout smem;
 };
 
 // IK_DUAL launches the dual step kernel and then the step decision (k_decide)

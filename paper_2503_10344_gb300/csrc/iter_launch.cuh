@@ -7,6 +7,7 @@
 #include "internal.h"
 #include "iter_kernels.cuh"
 #include "tile_kernels.cuh"
+#include "smem_kernels.cuh"
 #include "wtile_kernels.cuh"
 
 namespace pdlp {
@@ -176,6 +177,26 @@ template <typename T, typename V, bool IMPLICIT>
 cudaError_t launch_persist_t(int lanes_a, int lanes_t, const IterRaw& r, int max_attempts,
                              int grid, int* grid_out, cudaStream_t s) {
   const IterData<T, V> d = typed<T, V>(r);
+  if (grid == 1 && r.smem.bytes > 0) {
+    // one block with the LP in shared memory (allowed its dynamic shared memory once
+    // per device, at the setup's probe launch, outside any capture)
+    auto kern = k_smem<T, V, IMPLICIT>;
+    static int allowed_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (allowed_dev != dev) {
+      int optin = 0;
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - kSmemStatic);
+      if (e != cudaSuccess) return e;
+      allowed_dev = dev;
+    }
+    if (grid_out) *grid_out = 1;
+    kern<<<1, kBlock, r.smem.bytes, s>>>(d, r.smem, max_attempts);
+    return cudaGetLastError();
+  }
   switch (lanes_a) {
     case 2: return launch_persist_la<2, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);
     case 4: return launch_persist_la<4, T, V, IMPLICIT>(lanes_t, d, max_attempts, grid, grid_out, s);

@@ -939,6 +939,16 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     // the state says check_due, so every block returns at entry)
     // persistent = 2: one block (small LPs: the grid barrier is the block's barrier)
     const int want = p->persistent == 2 ? 1 : 0;
+    if (p->persistent == 2) {
+      // the one block holds the LP in shared memory when it fits (the 200 x 400
+      // relaxations take 73 KB in float64), else it steps from global memory
+      int dev = 0, optin = 0;
+      CUDA_TRY(cudaGetDevice(&dev));
+      CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      const SmemLayout L = smem_layout(m, n, nnz, mode == MODE_FP64 ? 8 : 4, mode != MODE_PAT,
+                                       mode == MODE_BF16 || mode == MODE_PAT);
+      if (L.bytes <= optin - kSmemStatic) sv.ir.smem = L;
+    }
     int g = 0;
     cudaError_t e;
     switch (mode) {
@@ -1180,6 +1190,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   r->lanes_A = sv.lanes_a;
   r->lanes_AT = sv.lanes_t;
   r->tiles = sv.ir.tile;
+  r->persistent_form = p->persistent == 0 ? 0 : p->persistent == 1 ? 1 : sv.ir.smem.bytes > 0 ? 3 : 2;
   r->iters = fs.iters;
   r->attempts = fs.attempts;
   r->restarts = fs.restarts;

@@ -552,6 +552,9 @@ def test_one_block_persistent_kernel_matches_two_launch_form(P, name):
     _, _, r2, it2 = gpu_iterates(P, lp, persistent=2, **kw)
     _, _, r0, it0 = gpu_iterates(P, lp, persistent=0, **kw)
     assert r2["iters"] == r0["iters"] == 300
+    # the two small LPs fit in shared memory (73 / 224 KB in float64), the covering LP not
+    assert r2["persistent_form"] == (2 if name == "set_cover_2000x8000" else 3)
+    assert r0["persistent_form"] == 0
     for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
         assert rel(it2[k], it0[k]) <= 1e-13, k
     if name == "mip_relaxation_200x400":
@@ -560,6 +563,58 @@ def test_one_block_persistent_kernel_matches_two_launch_form(P, name):
         assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-8
         obj, _, _, _ = R.highs(lp)
         assert abs(r["primal_obj"] - obj) / (1 + abs(obj)) <= 1e-7
+
+
+@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "random_free_eq_300x500"])
+def test_shared_memory_kernel_by_replay(P, name):
+    """The one-block kernel with the LP in shared memory (persistent = 2): 300 adaptive,
+    restarted steps with replayed step sizes match the oracle (iterates to 1e-9, every
+    accept and restart the rule applied to the oracle's numbers)."""
+    _, _, r = P.pdlp_solve(inst(name), P.default_params(iter_limit=5, terminate=0, persistent=2))
+    assert r["persistent_form"] == 3
+    check_replay(P, inst(name), 300, persistent=2)
+
+
+def test_shared_memory_kernel_empty_rows_and_columns(P):
+    lp = lpgen.random_sparse_lp(5, 60, 80)
+    _, _, r = P.pdlp_solve(lp, P.default_params(iter_limit=5, terminate=0, persistent=2))
+    assert r["persistent_form"] == 3
+    check_replay(P, lp, 300, persistent=2)
+
+
+def small_cover():
+    return lpgen.set_cover(7, m=300, n=1200)  # a 0/1 pattern that fits in shared memory
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "random_free_eq_300x500", "cover_300x1200"])
+def test_shared_memory_kernel_float32(P, name, prec):
+    """Float32 iterates in the shared-memory kernel (float32 values, bfloat16 values, the
+    0/1 pattern): after 60 fixed steps they agree with the two-launch kernels' and the
+    float64 oracle's to float32 rounding; solved to 1e-4 the point passes the oracle's
+    float64 KKT and its objective is within 1e-4 of the optimum."""
+    lp = small_cover() if name == "cover_300x1200" else inst(name)
+    fixed = dict(iter_limit=60, adaptive_step=0, restarts=0, terminate=0, fixed_eta=0.9,
+                 precision=prec)
+    _, _, r2, it2 = gpu_iterates(P, lp, persistent=2, **fixed)
+    _, _, r0, it0 = gpu_iterates(P, lp, persistent=0, **fixed)
+    assert r2["persistent_form"] == 3 and r2["iters"] == 60
+    ref = O.solve(lp, O.Params(iter_limit=60, adaptive=False, restarts=False, terminate=False,
+                               fixed_eta=0.9))
+    for k, want in (("x_cur", ref.x_cur), ("y_cur", ref.y_cur), ("x_avg", ref.x_avg),
+                    ("y_avg", ref.y_avg)):
+        assert rel(it2[k], it0[k]) <= F32, (k, rel(it2[k], it0[k]))
+        assert rel(it2[k], want) <= F32, (k, rel(it2[k], want))
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec, persistent=2))
+    assert r["status"] == P.PDLP_OPTIMAL and r["persistent_form"] == 3
+    assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-4
+    if name == "cover_300x1200":
+        if prec == "bf16":
+            assert r["precision_used"] == P.PDLP_USED_PATTERN
+        opt, _, _, _ = R.highs(lp)
+        assert abs(r["primal_obj"] - opt) / (1 + abs(r["primal_obj"]) + abs(opt)) <= OBJ_TOL
+    else:
+        assert obj_err(r["primal_obj"], GOLDEN_KEY[name]) <= OBJ_TOL
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
