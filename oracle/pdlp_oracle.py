@@ -19,6 +19,15 @@ reading is marked "reading" where it is used below:
       y_i >= 0 on inequality rows and y_i free on equality rows.
   A2  Ruiz equilibration (10 passes, inf-norm) then Pock-Chambolle (alpha = 1)
       diagonal scaling, K~ = D_r K D_c.
+  A2b optional bound-objective rescaling (one of the algorithmic variants of
+      PDLP; off by default): after A2 the objective is divided by
+      gamma = 1 + ||c~||_2 and the right-hand side and the variable bounds by
+      beta = 1 + ||q~||_2, so PDHG runs on (K~, q~/beta, c~/gamma, l~/beta,
+      u~/beta) and a point (x', y') of that problem is x = beta D_c x',
+      y = gamma D_r y' in the original units (reading: the factors are the
+      scaled norms plus one, both bounds and b share beta).  Everything in
+      A3-A10 is taken in the rescaled space; A8, A11 and A12 measure the
+      unscaled point as before.
   A3  x0 = proj_[l~,u~](0), y0 = 0, omega0 = ||c~|| / ||q~|| (if both > 1e-10,
       else 1), eta0 = 1 / max|K~_ij|.  With a primal-weight hint (x_h, y_h),
       omega0 = ||y~_h|| / ||x~_h|| of the hint projected and scaled like a
@@ -217,6 +226,7 @@ class Params:
     restarts: bool = True           # A9/A10
     fixed_eta: float | None = None  # overrides eta0 (fixed-step mode)
     fixed_omega: float | None = None  # overrides omega0
+    bound_objective_rescaling: bool = False  # A2b
     terminate: bool = True          # stop at tol (False: run to iter_limit)
     beta_suff: float = 0.2
     beta_nec: float = 0.8
@@ -317,6 +327,17 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
     qt = dr * q
     lt = lp.l / dc
     ut = lp.u / dc
+    if p.bound_objective_rescaling:
+        # A2b: gamma, beta from the scaled norms; the rescaled problem's point maps
+        # back through D_c beta and D_r gamma (unscaling below uses dc, dr so folded)
+        gamma = 1.0 + float(np.linalg.norm(ct))
+        beta = 1.0 + float(np.linalg.norm(qt))
+        ct = ct / gamma
+        qt = qt / beta
+        lt = lt / beta
+        ut = ut / beta
+        dc = dc * beta
+        dr = dr * gamma
     # A3
     if x0 is None:
         x = proj_box(np.zeros(lp.n), lt, ut)

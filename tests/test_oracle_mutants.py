@@ -88,6 +88,13 @@ MUTANTS = [
      "ddx = float(np.linalg.norm(dc * (cand_x - x_last)))\n"
      "                    ddy = float(np.linalg.norm(dr * (cand_y - y_last)))",
      ["test_primal_weight_distances_are_taken_in_scaled_space_by_hand"]),
+    ("rescaled variable bounds divided by gamma instead of beta",
+     "lt = lt / beta\n        ut = ut / beta", "lt = lt / gamma\n        ut = ut / gamma",
+     ["test_bound_objective_rescaling_is_the_same_pdhg_without_restarts"]),
+    ("rescaled dual point not multiplied back by gamma", "dr = dr * gamma", "dr = dr",
+     ["test_bound_objective_rescaling_one_step_by_hand"]),
+    ("objective rescaled by beta", "ct = ct / gamma", "ct = ct / beta",
+     ["test_bound_objective_rescaling_one_step_by_hand"]),
 ]
 
 
@@ -97,6 +104,8 @@ def _pin_args(name):
         return {"seed": 1}
     if name == "test_scaling_b_and_c_by_powers_of_two_scales_the_iterates_exactly":
         return {"maker": lambda: lpgen.mip_relaxation(1)}
+    if name == "test_bound_objective_rescaling_is_the_same_pdhg_without_restarts":
+        return {"maker": lambda: lpgen.mip_relaxation(2)}
     return {}
 
 

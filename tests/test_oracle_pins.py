@@ -492,3 +492,63 @@ def test_primal_weight_distances_are_taken_in_scaled_space_by_hand():
     assert r.check_trace[0][1] == pytest.approx(math.sqrt(0.5), rel=1e-15)
     np.testing.assert_allclose(r.x_cur, [0.25, s2 / 16.0], rtol=1e-14, atol=0)
     np.testing.assert_allclose(r.y_cur, [0.0, (0.25 + s2 / 2.0) / 4.0], rtol=1e-14, atol=0)
+
+
+# ---------------------------------------------------------------- A2b rescaling
+def test_bound_objective_rescaling_one_step_by_hand():
+    """A2b on min -3 x0 + 4 x1 s.t. x0 >= 1, x1 >= 0, x in [0, 10]^2 with K = I (no Ruiz,
+    no Pock-Chambolle, so D = I): gamma = 1 + ||c|| = 6, beta = 1 + ||q|| = 2, the
+    rescaled data c' = (-1/2, 2/3), q' = (1/2, 0), u' = 5, omega0' = ||c'|| / ||q'||
+    = (5/6) / (1/2) = 5/3.  One step with eta = 1/2 from 0:
+      x'1 = proj(0 - (0.5 / (5/3)) c') = proj(-0.3 c') = (0.15, 0),
+      y'1 = proj_Y(0 + 0.5 (5/3) (q' - 2 x'1)) = (5/6)(0.2, 0) = (1/6, 0);
+    unscaled x = beta x' = (0.3, 0), y = gamma y' = (1, 0) -- the unrescaled step with
+    omega0 = ||c|| / ||q|| = 5 from 0 gives the same point."""
+    lp = _lp_from_dense([[1.0, 0.0], [0.0, 1.0]], [1.0, 0.0], "GG", [-3.0, 4.0], [0.0, 0.0],
+                        [10.0, 10.0])
+    kw = dict(iter_limit=1, adaptive=False, fixed_eta=0.5, **NOSCALE)
+    r = O.solve(lp, O.Params(bound_objective_rescaling=True, **kw))
+    np.testing.assert_allclose(r.x_cur, [0.3, 0.0], rtol=1e-15, atol=0)
+    np.testing.assert_allclose(r.y_cur, [1.0, 0.0], rtol=1e-15, atol=0)
+    assert r.omega == pytest.approx(5.0 / 3.0, rel=1e-15)
+    r0 = O.solve(lp, O.Params(**kw))
+    np.testing.assert_allclose(r0.x_cur, r.x_cur, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(r0.y_cur, r.y_cur, rtol=1e-15, atol=0)
+    assert r0.omega == pytest.approx(5.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("maker", [lambda: lpgen.mip_relaxation(2),
+                                   lambda: lpgen.random_sparse_lp(3, 40, 60)])
+def test_bound_objective_rescaling_is_the_same_pdhg_without_restarts(maker):
+    """A2b changes the PDHG iteration only through the restart metric: with (x', y') =
+    (x~ / beta, y~ / gamma) the step, the step bound eta_bar and the omega0 rule map onto
+    the unrescaled ones with omega' = omega beta / gamma.  So with restarts off the
+    adaptive runs take the same attempts and accept decisions and reach the same unscaled
+    iterates (to the rounding the adaptive step amplifies), and the reported weights differ
+    by beta / gamma exactly as the scaled norms give it."""
+    lp = maker()
+    kw = dict(iter_limit=60, restarts=False, terminate=False)
+    r1 = O.solve(lp, O.Params(bound_objective_rescaling=True, **kw))
+    r0 = O.solve(lp, O.Params(**kw))
+    assert r1.iters == r0.iters == 60 and r1.attempts == r0.attempts
+    assert [a[2] for a in r1.attempt_trace] == [a[2] for a in r0.attempt_trace]
+    for a, b in ((r1.x_cur, r0.x_cur), (r1.y_cur, r0.y_cur), (r1.x_avg, r0.x_avg),
+                 (r1.y_avg, r0.y_avg)):
+        assert np.linalg.norm(a - b) <= 1e-9 * max(1.0, np.linalg.norm(b))
+    k, q, _, _ = O.canonicalize(lp)
+    dr, dc = O.ruiz_pock_chambolle(k)
+    gamma = 1.0 + np.linalg.norm(dc * lp.c)
+    beta = 1.0 + np.linalg.norm(dr * q)
+    assert r1.omega == pytest.approx(r0.omega * beta / gamma, rel=1e-12)
+    np.testing.assert_allclose([a[0] for a in r1.attempt_trace], [a[0] for a in r0.attempt_trace],
+                               rtol=1e-9)
+
+
+def test_bound_objective_rescaling_with_restarts_reaches_the_optimum():
+    """With restarts the rescaled run is its own iteration (the restart metric weighs
+    its gap term by 1 / (beta gamma)); it must still reach HiGHS's optimum."""
+    lp = lpgen.mip_relaxation(1)
+    r = O.solve(lp, O.Params(tol=1e-6, bound_objective_rescaling=True))
+    assert r.status == O.STATUS_OPTIMAL and r.kkt.rel_kkt <= 1e-6
+    obj, _, _, _ = R.highs(lp)
+    assert abs(float(lp.c @ r.x) - obj) / (1 + abs(obj)) <= 1e-5
