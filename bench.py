@@ -50,12 +50,15 @@ def parse():
     ap.add_argument("--kernels-only", action="store_true",
                     help="only time the fused kernels (pdlp_time_kernels) and print them")
     ap.add_argument("--reps", type=int, default=200)
-    ap.add_argument("--workload", default="set_cover", choices=["set_cover", "batch", "energy", "fp"],
+    ap.add_argument("--workload", default="set_cover",
+                    choices=["set_cover", "batch", "energy", "fp", "c1"],
                     help="batch: 256 uneven covering sub-LPs (m in [2000, 40000], n = 4m, "
-                         "10-50 %% of the columns fixed), solved together by pdlp_solve_batch")
+                         "10-50 %% of the columns fixed), solved together by pdlp_solve_batch; "
+                         "c1 (with --kernels-only): the 200 x 400 MIP relaxation")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
-                    help="1: one cooperative step kernel per check period; 0: two launches per attempt")
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2],
+                    help="1: one cooperative step kernel per check period; 2: one block per check "
+                         "period (the LP in shared memory when it fits); 0: two launches per attempt")
     ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],
                     help="float32 steps: 0 lanes-per-row kernels; 1 staged block tiles (bulk "
                          "copies into shared memory); 2 warp tiles")
@@ -589,6 +592,9 @@ def run_kernels_only(args):
         if args.workload == "energy":
             lp = lpgen.energy_system()
             prec = "fp32" if args.precision == "bf16" else args.precision
+        elif args.workload == "c1":
+            lp = lpgen.mip_relaxation(1)  # the 200 x 400 relaxation, float64 unless asked
+            prec = "fp64" if args.precision == "bf16" else args.precision
         else:
             lp = lpgen.set_cover(2025)
             prec = args.precision
@@ -807,6 +813,8 @@ if __name__ == "__main__":
         run_energy(a)
     elif a.workload == "batch" and a.impl == "gpu":
         run_batch(a)
+    elif a.workload == "c1" and a.impl == "gpu":
+        sys.exit("--workload c1 runs with --kernels-only (its solves are the default line's c1 section)")
     elif a.impl == "reference":
         run_reference(a)
     else:

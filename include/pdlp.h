@@ -174,6 +174,14 @@ typedef struct {
                            (lanes_A, lanes_AT).
                            Same iteration either way; float32 sums differ in rounding.
                            Ignored in float64 and with persistent != 0. */
+  int bound_objective_rescaling; /* 1: after the Ruiz / Pock-Chambolle scaling divide the
+                           objective by gamma = 1 + ||c~||_2 and the right-hand side and
+                           the variable bounds by beta = 1 + ||q~||_2 (one of PDLP's
+                           algorithmic variants; the paper is silent).  Without restarts
+                           it is the same iteration (x~ = beta x', y~ = gamma y',
+                           omega' = omega beta / gamma); the restart metric then weighs its
+                           gap term by 1 / (beta gamma).  0 (default): off.  Single LPs
+                           only: a batch with 1 is rejected. */
 } pdlp_params;
 
 typedef struct {

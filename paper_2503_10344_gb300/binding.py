@@ -42,7 +42,7 @@ class PdlpParams(C.Structure):
                 ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int),
                 ("persistent", C.c_int), ("autotune", C.c_int),
                 ("detect_infeasibility", C.c_int), ("debug_skip_barrier", C.c_int),
-                ("tiles", C.c_int)]
+                ("tiles", C.c_int), ("bound_objective_rescaling", C.c_int)]
 
 
 class PdlpResult(C.Structure):

@@ -137,6 +137,10 @@ struct KktRaw {
              // boxed, so the primal ray is 0), 2 both
   int grid_r_short, grid_r, grid_c_short, grid_c, grid_e;
   int scaled;  // iterates are in scaled space (explicit K~)
+  // iterates in unscaled space (scaled = 0): the factors that carry them to the original
+  // units, beta and gamma of the bound-objective rescaling (1 without it); in scaled space
+  // the factors are folded into dc and dr
+  double ux, uy;
   int fp32;    // iterate element type is float
   DevState* st;  // [count]
   int count;     // LPs in the batch (1 for a single LP)

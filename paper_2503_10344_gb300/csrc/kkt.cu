@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
   for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
     const double xc = (double)x[j].x;
     const double xa = sw > 0.0 ? avg_of((double)sx[j] + pw * xc, sw, isw) : xc;
-    const double s = r.scaled ? r.dc[j] : 1.0;
+    const double s = r.scaled ? r.dc[j] : r.ux;
     // unscaled candidates, clipped to [l, u] so the KKT measured here is the
     // KKT of exactly the point the solver returns (A11)
     const double Xc = fmin(fmax(s * xc, r.l[j]), r.u[j]);
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_prep(KktRaw r) {
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
     const double yc = (double)y[i];
     const double ya = sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc;
-    const double s = r.scaled ? r.dr[i] : 1.0;
+    const double s = r.scaled ? r.dr[i] : r.uy;
     const double Yc = s * yc;
     double d = 0.0;
     if (r.rays) {

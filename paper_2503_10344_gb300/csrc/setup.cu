@@ -559,6 +559,33 @@ __global__ void k_finish_scalars(const double* vpart, int nv, const double* mpar
   }
 }
 
+// Bound-objective rescaling (optional, after A2/A3's vectors): the iteration-space
+// objective divided by gamma, the right-hand side, the bounds and the start x by beta,
+// the start y by gamma; the factors that carry an iteration-space point back to the
+// original units (D_c, D_r of the KKT passes and the output) take beta and gamma in,
+// and their inverses (the scaled distances of the primal-weight update) 1 / beta and
+// 1 / gamma.  The step weights and the iteration matrix were formed before and keep
+// the plain D_r, D_c.
+template <typename T>
+__global__ void k_rescale(int m, int n, double beta, double gamma, T* c, T* l, T* u, T* q, T* x0,
+                          T* y0, double* dr, double* dc, double* inv_dr, double* inv_dc) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    c[j] = (T)((double)c[j] / gamma);
+    l[j] = (T)((double)l[j] / beta);
+    u[j] = (T)((double)u[j] / beta);
+    x0[2 * j] = (T)((double)x0[2 * j] / beta);
+    dc[j] = dc[j] * beta;
+    inv_dc[j] = 1.0 / dc[j];
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    q[i] = (T)((double)q[i] / beta);
+    y0[i] = (T)((double)y0[i] / gamma);
+    dr[i] = dr[i] * gamma;
+    inv_dr[i] = 1.0 / dr[i];
+  }
+}
+
 // float64 auxiliaries of the KKT passes: 1 / D_r, 1 / D_c and, per column, bit 0
 // = lower bound finite, bit 1 = upper bound finite (integer tests instead of
 // float64 compares in the per-column epilogue)
@@ -836,6 +863,20 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
 size_t setup_part_doubles(int m, int n) {
   const int G = device_sm_count() * 8;
   return (size_t)G * 7 + (size_t)G + 16;
+}
+
+cudaError_t setup_rescale(int m, int n, int fp32, double beta, double gamma, void* c, void* l,
+                          void* u, void* q, void* x0, void* y0, double* dr, double* dc,
+                          double* inv_dr, double* inv_dc, cudaStream_t s) {
+  const int g = grid_for(std::max(m, n), device_sm_count() * 8);
+  if (fp32)
+    k_rescale<float><<<g, kBlock, 0, s>>>(m, n, beta, gamma, (float*)c, (float*)l, (float*)u,
+                                          (float*)q, (float*)x0, (float*)y0, dr, dc, inv_dr, inv_dc);
+  else
+    k_rescale<double><<<g, kBlock, 0, s>>>(m, n, beta, gamma, (double*)c, (double*)l, (double*)u,
+                                           (double*)q, (double*)x0, (double*)y0, dr, dc, inv_dr,
+                                           inv_dc);
+  return cudaGetLastError();
 }
 
 cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,

@@ -69,6 +69,12 @@ size_t scan_tmp_ints(long long N);
 // dst[i] = src[i] + offset (index arrays moved into a batch's global numbering)
 cudaError_t setup_offset_copy(int* dst, const int* src, long long count, int offset,
                               cudaStream_t s);
+// Bound-objective rescaling of the iteration vectors and the start point, with the
+// factors beta (right-hand side, bounds, x) and gamma (objective, y) folded into the
+// KKT passes' D_r, D_c and their inverses (k_rescale in setup.cu).
+cudaError_t setup_rescale(int m, int n, int fp32, double beta, double gamma, void* c, void* l,
+                          void* u, void* q, void* x0, void* y0, double* dr, double* dc,
+                          double* inv_dr, double* inv_dc, cudaStream_t s);
 cudaError_t setup_kkt_aux(int m, int n, const double* dr, const double* dc, const double* l,
                           const double* u, double* inv_dr, double* inv_dc, unsigned char* bflags,
                           cudaStream_t s);

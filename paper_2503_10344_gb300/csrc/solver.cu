@@ -378,6 +378,8 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
   if (p->autotune != 0 && p->autotune != 1)
     return fail(PDLP_ERR_INVALID_INPUT, "autotune must be 0 or 1");
   if (p->tiles < 0 || p->tiles > 2) return fail(PDLP_ERR_INVALID_INPUT, "tiles must be 0, 1 or 2");
+  if (p->bound_objective_rescaling != 0 && p->bound_objective_rescaling != 1)
+    return fail(PDLP_ERR_INVALID_INPUT, "bound_objective_rescaling must be 0 or 1");
   if ((p->lanes_A && !valid_step_lanes(p->lanes_A)) || (p->lanes_AT && !valid_step_lanes(p->lanes_AT)))
     return fail(PDLP_ERR_INVALID_INPUT, "step lanes must be 0, 1, 2, 4, 8, 16 or 32");
   if ((p->lanes_kkt_A && !valid_lanes(p->lanes_kkt_A)) ||
@@ -850,13 +852,27 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
 
   // ---- A3: initial state
   CUDA_TRY(cudaStreamSynchronize(s));  // scalars
+  // optional bound-objective rescaling: the objective by gamma = 1 + ||c~||, the
+  // right-hand side and the bounds by beta = 1 + ||q~||; every scaled norm below is
+  // taken in the rescaled problem
+  double beta = 1.0, gamma = 1.0;
+  if (p->bound_objective_rescaling) {
+    gamma = 1.0 + sca[0];
+    beta = 1.0 + sca[1];
+    CUDA_TRY(setup_rescale(m, n, fp32, beta, gamma, bf.c_it, bf.l_it, bf.u_it, bf.q_it, bf.x[0],
+                           bf.y[0], bf.dr, bf.dc, bf.inv_dr, bf.inv_dc, s));
+    ++g_launches;
+  }
+  kr.ux = scaled ? 1.0 : beta;
+  kr.uy = scaled ? 1.0 : gamma;
   DevState hs;
   memset(&hs, 0, sizeof(hs));
-  const double nct = sca[0], nqt = sca[1], kmax = sca[4];
+  const double nct = sca[0] / gamma, nqt = sca[1] / beta, kmax = sca[4];
   hs.omega = (nct > 1e-10 && nqt > 1e-10) ? nct / nqt : 1.0;
   // a primal-weight hint replaces the ||c~|| / ||q~|| estimate by the ratio of the
   // hint's own scaled norms (the balance the weight is meant to strike)
-  if ((hx || hy) && sca[5] > 1e-10 && sca[6] > 1e-10) hs.omega = sca[6] / sca[5];
+  const double nxh = sca[5] / beta, nyh = sca[6] / gamma;
+  if ((hx || hy) && nxh > 1e-10 && nyh > 1e-10) hs.omega = nyh / nxh;
   hs.eta = kmax > 0.0 ? 1.0 / kmax : 1.0;
   if (p->fixed_eta > 0.0) hs.eta = p->fixed_eta;
   if (p->fixed_omega > 0.0) hs.omega = p->fixed_omega;
@@ -1421,6 +1437,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
                        const double* const* u, const pdlp_params* p, double* const* x_out,
                        double* const* y_out, pdlp_result* res, const TimingReq* tq = nullptr,
                        bool device_inputs = false, cudaStream_t user_stream = nullptr) {
+  if (p->bound_objective_rescaling)
+    return fail(PDLP_ERR_INVALID_INPUT, "bound_objective_rescaling is for single LPs, not batches");
   g_launches = 0;
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = user_stream;
@@ -1841,6 +1859,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   kr.grid_r_short = gridA; kr.grid_r = gridA; kr.grid_c_short = gridT; kr.grid_c = gridT;
   kr.grid_e = gridT;
   kr.scaled = scaled; kr.fp32 = mode != MODE_FP64;
+  kr.ux = kr.uy = 1.0;  // batches: no bound-objective rescaling
   kr.st = g.st;
   kr.count = count;
   kr.tr = tA;
@@ -2049,6 +2068,7 @@ int pdlp_default_params(pdlp_params* p) {
   p->autotune = 0;
   p->detect_infeasibility = 1;
   p->tiles = 0;
+  p->bound_objective_rescaling = 0;
   return PDLP_OK;
 }
 

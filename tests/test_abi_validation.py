@@ -128,3 +128,8 @@ def test_polishing_needs_its_start_point(P, lp):
 def test_batch_rejects_an_empty_batch_and_names_a_bad_lp(P, lp):
     _rejected(P, lambda: P.pdlp_solve_batch([]), "count >= 1")
     _rejected(P, lambda: P.pdlp_solve_batch([lp, lp], P.default_params(tol=-1.0)), "LP 0")
+
+
+def test_bound_objective_rescaling_parameter_is_checked(P, lp):
+    _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(bound_objective_rescaling=2)),
+              "bound_objective_rescaling must be 0 or 1")

@@ -468,6 +468,56 @@ def test_energy_system_full_size_fp32(P):
     assert abs(r["primal_obj"] - ref) / (1.0 + abs(r["primal_obj"]) + abs(ref)) <= OBJ_TOL
 
 
+# ---------------------------------------------------------------- bound-objective rescaling
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("K", [1, 10, 100])
+def test_bound_objective_rescaling_fixed_step_matches_oracle(P, name, K):
+    """With bound_objective_rescaling the float64 iterates (unscaled: x = beta D_c x',
+    y = gamma D_r y') follow the oracle's A2b run to 1e-9, restarts and primal-weight
+    updates included (fixed step)."""
+    lp = inst(name)
+    _, _, res, its = gpu_iterates(P, lp, iter_limit=K, adaptive_step=0, fixed_eta=0.9,
+                                  terminate=0, bound_objective_rescaling=1)
+    ref = O.solve(lp, O.Params(iter_limit=K, adaptive=False, fixed_eta=0.9, terminate=False,
+                               bound_objective_rescaling=True))
+    assert res["iters"] == ref.iters == K
+    assert_iterate_parity(its, ref)
+    assert res["omega"] == pytest.approx(ref.omega, rel=1e-9)
+
+
+@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "energy_system_24h", "skewed_6000x3000"])
+def test_bound_objective_rescaling_by_replay(P, name):
+    """Adaptive steps and KKT restarts in the rescaled space, replayed against the oracle:
+    every accept and restart decision is the rule on the oracle's numbers."""
+    lp = inst(name)
+    _, _, res, dg = P.pdlp_solve(lp, P.default_params(iter_limit=150, terminate=0,
+                                                      bound_objective_rescaling=1), trace=8 * 150 + 64)
+    ref = O.solve(lp, O.Params(iter_limit=150, terminate=False, bound_objective_rescaling=True,
+                               replay_eta=dg["eta"], replay_accepted=dg["accepted"]))
+    assert res["iters"] == ref.iters and res["attempts"] == ref.attempts
+    assert list(dg["restart"]) == [c[0] for c in ref.check_trace]
+    np.testing.assert_allclose(dg["omega"], [c[1] for c in ref.check_trace], rtol=1e-9)
+    assert_iterate_parity(dg, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "set_cover_2000x8000", "energy_system_24h"])
+def test_bound_objective_rescaling_float32_reaches_tolerance(P, name, prec):
+    lp = inst(name)
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-4, precision=prec, bound_objective_rescaling=1))
+    assert r["status"] == P.PDLP_OPTIMAL
+    k = O.kkt_original(lp, x, y)
+    assert k.rel_kkt <= 1.01e-4
+    assert r["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
+    assert obj_err(r["primal_obj"], GOLDEN_KEY[name]) <= OBJ_TOL
+
+
+def test_bound_objective_rescaling_is_rejected_for_batches(P):
+    with pytest.raises(P.PdlpError, match="single LPs"):
+        P.pdlp_solve_batch([inst("mip_relaxation_200x400")] * 2,
+                           P.default_params(bound_objective_rescaling=1))
+
+
 # ---------------------------------------------------------------- primal-weight hint
 def seeded_hint(lp, seed):
     rng = np.random.default_rng(seed)
