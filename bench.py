@@ -519,8 +519,16 @@ def batch_section(args, dev, stream, peak):
             solve.append(res[0]["solve_s"])
             iters.append(sum(r["iters"] for r in res))
     it = np.array([r["iters"] for r in res])
+    # the same batch with one cooperative kernel per check period (persistent = 1)
+    prm1 = P.default_params(tol=1e-4, precision="bf16", persistent=1)
+    P.pdlp_solve_batch(lps, prm1, want_y=False)  # warm
+    _, _, res1 = P.pdlp_solve_batch(lps, prm1, want_y=False)
     kt = P.time_kernels_batch(lps, prm, reps=20)
     pk, src = _peak()
+    persistent = {"solve_s": res1[0]["solve_s"], "iters_sum": int(sum(r["iters"] for r in res1)),
+                  "optimal": int(sum(r["status"] == P.PDLP_OPTIMAL for r in res1)),
+                  "kernel_launches": int(res1[0]["kernel_launches"]),
+                  "kernel_launches_two_launch_form": int(res[0]["kernel_launches"])}
     return {"workload": f"batch of {len(lps)} set-cover sub-LPs, sum m={sum(l.m for l in lps)}, "
                         f"sum n={sum(l.n for l in lps)}, nnz={sum(l.nnz for l in lps)}, tol=1e-4",
             "precision": {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
@@ -531,6 +539,7 @@ def batch_section(args, dev, stream, peak):
             "solve_s": statistics.median(solve), "iters_sum": iters[-1],
             "iters_per_s": iters[-1] / solve[-1], "lps_per_s": len(lps) / statistics.median(solve),
             "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+            "persistent": persistent,
             "roofline": kernel_roofline(kt, pk, src), "clocks": clk.summary()}
 
 

@@ -144,7 +144,9 @@ typedef struct {
                            attempt), which copies the LP into shared memory when it fits
                            and otherwise runs the cooperative kernel as one block; 0
                            (default): two kernel launches per attempt.  Same iteration
-                           either way; batches always use the two-launch form. */
+                           either way.  Batches: 1 runs one cooperative kernel per check
+                           period over every LP of the batch (three grid barriers per
+                           attempt); 2 is rejected. */
   int autotune;         /* 1: before iterating, time whole step attempts (primal kernel,
                            dual kernel and decision) with 1 (float32 iterates and
                            persistent = 0 only), 2, 4, 8, 16 and 32 lanes per row,

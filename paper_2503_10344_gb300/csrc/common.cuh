@@ -136,6 +136,23 @@ struct Span {
   int nlist;
 };
 
+// The span of virtual block `vb` of a batch's launch map (the persistent batch kernel
+// walks the map's blocks with a resident grid).
+__device__ __forceinline__ Span span_of(const Tables& t, int vb, const int* list1) {
+  Span s;
+  const int k = t.blk_lp[vb];
+  s.lp = k;
+  s.row0 = t.row0[k];
+  s.nrows = t.nrows[k];
+  s.part0 = t.blk0[k];
+  s.bidx = vb - s.part0;
+  s.nshort = t.nshort[k];
+  s.nblk = t.nblk[k];
+  s.list = list1 + t.long0[k];
+  s.nlist = t.nlong[k];
+  return s;
+}
+
 __device__ __forceinline__ Span make_span(const Tables& t, int nrows1, int nshort1,
                                           const int* list1, int nlist1) {
   Span s;

@@ -691,9 +691,162 @@ __device__ __forceinline__ bool grid_barrier(DevState* st) {
   return ok != 0;
 }
 
+// The persistent kernel over a batch (persistent = 1 with count > 1): the resident grid
+// walks the two launch maps' virtual blocks (block b takes b, b + G, ...; each virtual
+// block belongs to one LP and keeps its rows and its partial-sum slot, as in the
+// two-launch form), with three grid barriers per attempt: after the primal phase, after
+// the dual phase, and after the decisions, which block b takes for the LPs b, b + G, ...
+// from the LP's slots in order.  Each LP steps until its own check falls due or it
+// stops; the launch ends when no LP steps any more or after `max_attempts`.  State,
+// partial sums and every vector entry another block wrote are read through L2.
+template <typename T>
+struct StepView {
+  int go, cur;
+  T tau, sigma, pw;
+};
+template <typename T>
+__device__ __forceinline__ StepView<T> step_view(const DevState* st) {
+  StepView<T> v;
+  v.go = __ldcg(&st->status) == 0 && __ldcg(&st->check_due) == 0;
+  v.cur = __ldcg(&st->cur);
+  if constexpr (std::is_same<T, float>::value) {
+    v.tau = __ldcg(&st->tau_f);
+    v.sigma = __ldcg(&st->sigma_f);
+    v.pw = __ldcg(&st->pw_f);
+  } else {
+    v.tau = __ldcg(&st->tau_d);
+    v.sigma = __ldcg(&st->sigma_d);
+    v.pw = __ldcg(&st->pending_w);
+  }
+  return v;
+}
+
+template <int LA, int LT, typename T, typename V, bool IMPLICIT>
+__device__ __forceinline__ void persist_batch(const IterData<T, V>& d, int max_attempts) {
+  constexpr bool TILED = std::is_same<T, double>::value;
+  DevState* gst = d.st;  // LP 0's state also holds the grid barrier's words
+  const int G = gridDim.x, b = blockIdx.x;
+  __shared__ StepView<T> vsh;
+  __shared__ DevState ls;
+  __shared__ T fac[2];
+  __shared__ int go_any;
+  for (int att = 0; att < max_attempts; ++att) {
+    // ---- A4: primal phase over the virtual blocks of the A^T map
+    for (int vb = b; vb < d.grid_p; vb += G) {
+      const Span sp = span_of(d.tp, vb, d.t_long);
+      if (threadIdx.x == 0) vsh = step_view<T>(d.st + sp.lp);
+      __syncthreads();
+      const StepView<T> v = vsh;
+      __syncthreads();
+      if (!v.go) continue;
+      const vec2_t<T>* x = v.cur ? d.x[1] : d.x[0];
+      vec2_t<T>* xn = v.cur ? d.x[0] : d.x[1];
+      const T* y = v.cur ? d.y[1] : d.y[0];
+      T dx2 = 0;
+      auto load = [&](int p) -> T {
+        return Ld<T, V>::get(d.t_val, p) * __ldcg(y + __ldg(d.t_col + p));
+      };
+      auto epi = [&](int j, T aty) {
+        const T xo = __ldcg(x + j).x;
+        const T g = __ldg(d.c + j) - aty;
+        const T step = IMPLICIT ? v.tau * __ldg(d.tw + j) : v.tau;
+        const T xv = clampv(xo - step * g, __ldg(d.l + j), __ldg(d.u + j));
+        const T dd = xv - xo;
+        vec2_t<T> o;
+        o.x = xv;
+        o.y = dd;
+        xn[j] = o;
+        if (v.pw != (T)0) d.sum_x[j] = __ldcg(d.sum_x + j) + v.pw * xo;
+        dx2 += IMPLICIT ? dd * dd / __ldg(d.tw + j) : dd * dd;
+      };
+      rows_all<TILED, LT, T>(sp, d.t_ptr, d.t_thresh, load, epi);
+      const T s = block_sum1<T>(dx2);
+      if (threadIdx.x == 0) d.part_p[vb] = s;
+    }
+    if (!grid_barrier(gst)) return;
+    // ---- A5: dual phase over the virtual blocks of the A map
+    for (int vb = b; vb < d.grid_d; vb += G) {
+      const Span sp = span_of(d.td, vb, d.a_long);
+      if (threadIdx.x == 0) vsh = step_view<T>(d.st + sp.lp);
+      __syncthreads();
+      const StepView<T> v = vsh;
+      __syncthreads();
+      if (!v.go) continue;
+      const vec2_t<T>* xn = v.cur ? d.x[0] : d.x[1];
+      const T* y = v.cur ? d.y[1] : d.y[0];
+      T* yn = v.cur ? d.y[0] : d.y[1];
+      T dy2 = 0, dkd = 0;
+      auto load = [&](int p) -> P2<T> {
+        const T val = Ld<T, V>::get(d.a_val, p);
+        const vec2_t<T> xv = __ldcg(xn + __ldg(d.a_col + p));
+        return P2<T>{val * xv.x, val * xv.y};
+      };
+      auto epi = [&](int i, P2<T> acc) {
+        const T yo = __ldcg(y + i);
+        const T step = IMPLICIT ? v.sigma * __ldg(d.sw + i) : v.sigma;
+        T yv = yo + step * (__ldg(d.q + i) - (acc.a + acc.b));
+        if (__ldg(d.row_kind + i) != 1) yv = maxv(yv, (T)0);
+        yn[i] = yv;
+        if (v.pw != (T)0) d.sum_y[i] = __ldcg(d.sum_y + i) + v.pw * yo;
+        const T dd = yv - yo;
+        dy2 += IMPLICIT ? dd * dd / __ldg(d.sw + i) : dd * dd;
+        dkd += dd * acc.b;
+      };
+      rows_all<TILED, LA, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
+      const T s0 = block_sum1<T>(dy2);
+      const T s1 = block_sum1<T>(dkd);
+      if (threadIdx.x == 0) {
+        d.part_d[vb] = s0;
+        d.part_d[d.grid_d + vb] = s1;
+      }
+    }
+    if (!grid_barrier(gst)) return;
+    // ---- A6: the decisions, block b for the LPs b, b + G, ...
+    for (int k = b; k < d.count; k += G) {
+      if (threadIdx.x < 32) {
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(d.st + k);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ls);
+        for (int w = threadIdx.x; w < (int)(sizeof(DevState) / 8); w += 32) dst[w] = __ldcg(src + w);
+        __syncwarp();
+        if (threadIdx.x == 0) step_factors(&ls, ls.attempts + 1, &fac[0], &fac[1]);
+      }
+      __syncthreads();
+      if (ls.status == 0 && !ls.check_due && !ls.dry) {
+        const int p0 = d.tp.blk0[k], pn = d.tp.nblk[k], q0 = d.td.blk0[k], qn = d.td.nblk[k];
+        T a = 0, b0 = 0, b1 = 0;
+        for (int i = threadIdx.x; i < pn; i += kBlock) a += __ldcg(d.part_p + p0 + i);
+        for (int i = threadIdx.x; i < qn; i += kBlock) {
+          b0 += __ldcg(d.part_d + q0 + i);
+          b1 += __ldcg(d.part_d + d.grid_d + q0 + i);
+        }
+        block_sum3<T>(a, b0, b1);
+        if (threadIdx.x == 0) {
+          decide_step<T>(&ls, a, b0, b1, fac[0], fac[1]);
+          store_step_state(d.st + k, ls);
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(gst)) return;
+    // ---- does any LP still step?  (every block reads the same states)
+    int mine = 0;
+    for (int k = threadIdx.x; k < d.count; k += kBlock)
+      mine |= __ldcg(&d.st[k].status) == 0 && __ldcg(&d.st[k].check_due) == 0;
+    if (threadIdx.x == 0) go_any = 0;
+    __syncthreads();
+    if (mine) go_any = 1;
+    __syncthreads();
+    if (!go_any) break;
+  }
+}
+
 template <int LA, int LT, typename T, typename V, bool IMPLICIT>
 __global__ void __launch_bounds__(kBlock) k_persist(IterData<T, V> d, int max_attempts) {
   constexpr bool TILED = std::is_same<T, double>::value;
+  if (d.tp.blk_lp != nullptr) {  // a batch
+    persist_batch<LA, LT, T, V, IMPLICIT>(d, max_attempts);
+    return;
+  }
   DevState* gst = d.st;
   __shared__ DevState ls;
   __shared__ int stop;

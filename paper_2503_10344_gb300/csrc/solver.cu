@@ -1439,6 +1439,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
                        bool device_inputs = false, cudaStream_t user_stream = nullptr) {
   if (p->bound_objective_rescaling)
     return fail(PDLP_ERR_INVALID_INPUT, "bound_objective_rescaling is for single LPs, not batches");
+  if (p->persistent == 2)
+    return fail(PDLP_ERR_INVALID_INPUT, "persistent = 2 (one block) is for single LPs, not batches");
   g_launches = 0;
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = user_stream;
@@ -1475,7 +1477,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   const double step_bytes = 2.0 * (double)Z * 8.0 + 40.0 * (double)(M + N);
   const double per_lane_a =
       mode != MODE_FP64 && step_bytes > 256e6 ? 4.0 * per_lane : per_lane;
-  const bool one_ok = mode != MODE_FP64;  // batches always use the two-launch kernels
+  // one lane per row: float32 and the two-launch kernels only
+  const bool one_ok = mode != MODE_FP64 && !p->persistent;
   int lanes[4] = {p->lanes_A ? p->lanes_A : step_lanes(avg_a, per_lane_a, one_ok),
                   p->lanes_AT ? p->lanes_AT : step_lanes(avg_t, per_lane, one_ok),
                   p->lanes_kkt_A ? p->lanes_kkt_A : auto_lanes(avg_a, 8.0),
@@ -1898,13 +1901,28 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
       CUDA_TRY(cudaStreamSynchronize(s));
       return PDLP_OK;
     };
-    const int rc = autotune_lanes(sv, count, !p->lanes_AT, !p->lanes_A, mode != MODE_FP64, set_grids,
+    const int rc = autotune_lanes(sv, count, !p->lanes_AT, !p->lanes_A, one_ok, set_grids,
                                   set_dry);
     if (rc) return rc;
     lanes[0] = sv.lanes_a;
     lanes[1] = sv.lanes_t;
     ir = sv.ir;  // the output kernels below use these copies
     kr = sv.kr;
+  }
+  if (p->persistent == 1) {
+    // one cooperative kernel per check period walks both launch maps with the resident
+    // grid (probe launch with no attempt to run: the states say check_due)
+    int gp = 0;
+    cudaError_t e;
+    switch (mode) {
+      case MODE_FP64: e = launch_persist_fp64(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &gp, s); break;
+      case MODE_FP32: e = launch_persist_fp32(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &gp, s); break;
+      case MODE_BF16: e = launch_persist_bf16(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &gp, s); break;
+      default: e = launch_persist_pat(sv.lanes_a, sv.lanes_t, sv.ir, 0, 0, &gp, s); break;
+    }
+    ++g_launches;
+    if (e != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("persistent kernel: ") + cudaGetErrorString(e));
+    sv.persist_grid = gp;
   }
   CUDA_TRY(sv.kkt_block());  // initial KKT of every LP
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -2004,6 +2022,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
     r.lanes_A = lanes[0];
     r.lanes_AT = lanes[1];
     r.tiles = ir.tile;
+    r.persistent_form = sv.persist_grid > 0 ? 1 : 0;
     r.iters = f.iters;
     r.attempts = f.attempts;
     r.restarts = f.restarts;

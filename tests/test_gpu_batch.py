@@ -137,3 +137,65 @@ def test_device_batch_rejects_an_invalid_member(P):
     bad.col[3] = bad.n  # column index out of range
     with pytest.raises(P.PdlpError, match="LP 3: invalid input: column index"):
         P.pdlp_solve_batch_device([P.DeviceLP(lp) for lp in lps + [bad]])
+
+
+# ---------------------------------------------------------------- persistent batch
+@pytest.mark.parametrize("K", [1, 10, 60])
+def test_persistent_batch_float64_equals_two_launch_form(P, K):
+    """persistent = 1 over a batch: one cooperative kernel per check period walks both
+    launch maps with the resident grid, three grid barriers per attempt.  Each virtual
+    block keeps its rows and partial-sum slot and each LP's decision adds its slots in
+    order, so float64 runs equal the two-launch form bit for bit (fixed step, K steps;
+    adaptive steps with restarts below)."""
+    lps = mixed_lps()
+    kw = dict(iter_limit=K, terminate=0, adaptive_step=0, fixed_eta=0.9)
+    x1, y1, r1 = P.pdlp_solve_batch(lps, P.default_params(persistent=1, **kw))
+    x0, y0, r0 = P.pdlp_solve_batch(lps, P.default_params(persistent=0, **kw))
+    for a, b, c, d, ra, rb in zip(x1, x0, y1, y0, r1, r0):
+        assert ra["persistent_form"] == 1 and rb["persistent_form"] == 0
+        assert ra["iters"] == rb["iters"] == K
+        assert np.array_equal(a, b) and np.array_equal(c, d)
+
+
+def test_persistent_batch_adaptive_matches_oracle_per_lp(P):
+    lps = mixed_lps()
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(iter_limit=60, terminate=0, persistent=1))
+    for lp, x, y, r in zip(lps, xs, ys, res):
+        ref = O.solve(lp, O.Params(iter_limit=60, terminate=False))
+        assert r["iters"] == ref.iters == 60 and r["attempts"] == ref.attempts
+        for got, want in ((x, ref.x), (y, ref.y)):
+            assert np.linalg.norm(got - want) <= 1e-9 * max(1.0, np.linalg.norm(want)), lp.name
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_persistent_batch_reaches_tolerance(P, prec):
+    """Every LP stops on its own (its check due, then optimal) while the others keep
+    stepping inside the same launch; fewer kernel launches than two per attempt."""
+    lps = mixed_lps()
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision=prec, persistent=1))
+    _, _, res0 = P.pdlp_solve_batch(lps, P.default_params(tol=1e-4, precision=prec))
+    for lp, key, x, y, r in zip(lps, MIXED_KEYS, xs, ys, res):
+        assert r["status"] == P.PDLP_OPTIMAL and r["persistent_form"] == 1, (lp.name, r)
+        k = O.kkt_original(lp, x, y)
+        assert k.rel_kkt <= 1.01e-4, (lp.name, k)
+        assert T.obj_err(r["primal_obj"], key) <= T.OBJ_TOL, lp.name
+    assert len({r["iters"] for r in res}) > 1
+    assert res[0]["kernel_launches"] < res0[0]["kernel_launches"]
+
+
+def test_persistent_batch_float32_iterates(P):
+    """Float32 persistent and two-launch batch runs differ only in how rows are grouped
+    into partial sums (the persistent kernel walks rows with the plain traversal): after
+    30 fixed steps every LP's point agrees to float32 rounding."""
+    lps = mixed_lps()
+    kw = dict(iter_limit=30, terminate=0, adaptive_step=0, restarts=0, fixed_eta=0.9, precision="fp32")
+    x1, y1, _ = P.pdlp_solve_batch(lps, P.default_params(persistent=1, **kw))
+    x0, y0, _ = P.pdlp_solve_batch(lps, P.default_params(persistent=0, lanes_A=2, lanes_AT=2, **kw))
+    for lp, a, b, c, d in zip(lps, x1, x0, y1, y0):
+        assert np.linalg.norm(a - b) <= 2e-5 * max(1.0, np.linalg.norm(b)), lp.name
+        assert np.linalg.norm(c - d) <= 2e-5 * max(1.0, np.linalg.norm(d)), lp.name
+
+
+def test_persistent_two_is_rejected_for_batches(P):
+    with pytest.raises(P.PdlpError, match="single LPs"):
+        P.pdlp_solve_batch(mixed_lps()[:2], P.default_params(persistent=2))
