@@ -128,10 +128,15 @@ __device__ __forceinline__ void rows_short(const Span& sp, const int* __restrict
 // on consecutive lanes) and prefetches kPre1 entries of each.
 constexpr int kPre = 2;
 constexpr int kPre1 = 3;
+// one lane per row in the dual kernel: the entries past the first kPre1 are loaded kChunk1
+// at a time before their gathers (the energy model's 175,200 balance rows of 13-21 entries
+// come first in row order and make the first pass long: dual half-step 42.8 -> 41.1 us;
+// in the primal kernel the chunk's registers delayed the next pass's prefetch instead)
+constexpr int kChunk1 = 4;
 template <int LANES> struct PreDepth { static constexpr int value = LANES == 1 ? kPre1 : kPre; };
 
-template <int LANES, typename Acc, typename PC, typename PV, typename Val, typename Term,
-          typename PrefC, typename PrefV, typename Fin, typename Enter>
+template <int LANES, typename Acc, typename PC, typename PV, bool CHUNK_TAIL = false, typename Val,
+          typename Term, typename PrefC, typename PrefV, typename Fin, typename Enter>
 __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restrict__ ptr,
                                             const int* __restrict__ col, int thresh, Val val,
                                             Term term, PrefC pref_c, PrefV pref_v, Fin fin,
@@ -205,10 +210,34 @@ __device__ __forceinline__ bool rows_short3(const Span& sp, const int* __restric
       if (q < rw.n1) a1 += term(hd.v1[k], hd.c1[k]);
     }
     const int nmax = rw.n0 > rw.n1 ? rw.n0 : rw.n1;
+    if constexpr (LANES == 1 && CHUNK_TAIL) {
+      // a thread walks the rest of its two rows alone: kChunk1 indices and values of
+      // each issued together, then their gathers (the same order of the sums; with more
+      // lanes per row the chunks measured slower: covering LP dual 11.7 -> 12.0 us, batch
+      // dual 595 -> 617 us)
+      for (int q0 = KP; q0 < nmax; q0 += kChunk1) {
+        int c0[kChunk1], c1[kChunk1];
+        VT v0[kChunk1], v1[kChunk1];
+#pragma unroll
+        for (int k = 0; k < kChunk1; ++k) {
+          const int q = q0 + k;
+          c0[k] = q < rw.n0 ? __ldg(col + rw.s0 + q) : -1;
+          v0[k] = q < rw.n0 ? val(rw.s0 + q) : VT(0);
+          c1[k] = q < rw.n1 ? __ldg(col + rw.s1 + q) : -1;
+          v1[k] = q < rw.n1 ? val(rw.s1 + q) : VT(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kChunk1; ++k) {
+          if (c0[k] >= 0) a0 += term(v0[k], c0[k]);
+          if (c1[k] >= 0) a1 += term(v1[k], c1[k]);
+        }
+      }
+    } else {
 #pragma unroll 2
-    for (int q = lane + KP * LANES; q < nmax; q += LANES) {
-      if (q < rw.n0) a0 += term(val(rw.s0 + q), __ldg(col + rw.s0 + q));
-      if (q < rw.n1) a1 += term(val(rw.s1 + q), __ldg(col + rw.s1 + q));
+      for (int q = lane + KP * LANES; q < nmax; q += LANES) {
+        if (q < rw.n0) a0 += term(val(rw.s0 + q), __ldg(col + rw.s0 + q));
+        if (q < rw.n1) a1 += term(val(rw.s1 + q), __ldg(col + rw.s1 + q));
+      }
     }
     a0 = group_sum<LANES>(a0);
     a1 = group_sum<LANES>(a1);
@@ -538,8 +567,8 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
     if (!enter()) return;
     rows_all<true, LANES, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
   } else if (sp.bidx < sp.nshort) {
-    if (!rows_short3<LANES, P2<T>, PreCD<T>, PreVD<T>>(sp, d.a_ptr, d.a_col, d.a_thresh, val, term,
-                                                       pref_c, pref_v, fin, enter))
+    if (!rows_short3<LANES, P2<T>, PreCD<T>, PreVD<T>, true>(sp, d.a_ptr, d.a_col, d.a_thresh, val,
+                                                             term, pref_c, pref_v, fin, enter))
       return;
   } else {
     if (!enter()) return;
