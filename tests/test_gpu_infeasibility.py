@@ -105,6 +105,35 @@ def test_batch_mixes_certificates_and_optima(P, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_persistent_batch_mixes_certificates_and_optima(P, prec):
+    """The persistent kernel over a batch (persistent = 1): an LP that stops on a
+    certificate leaves the launch's other LPs stepping."""
+    names = ["contradiction1", "relaxation1", "dead_cover", "box", "hand"]
+    lps = [lpgen.mip_relaxation(1)] + [inst(k) for k in names] + [lpgen.set_cover(7, m=2000, n=8000)]
+    kinds = ["opt"] + [CASES[k][0] for k in names] + ["opt"]
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-6, iter_limit=20000, precision=prec,
+                                                           persistent=1))
+    for lp, kind, x, y, r in zip(lps, kinds, xs, ys, res):
+        assert r["persistent_form"] == 1
+        if kind == "opt":
+            assert r["status"] == P.PDLP_OPTIMAL, (lp.name, r)
+            assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-6
+        else:
+            check_certificate(P, lp, kind, x, y, r)
+
+
+@pytest.mark.parametrize("name", FP32_CASES)
+def test_shared_memory_kernel_certificates(P, name):
+    """The one-block kernel with the LP in shared memory (persistent = 2) ends an
+    infeasible or unbounded small LP on the oracle's status with a valid ray."""
+    kind, _ = CASES[name]
+    lp = inst(name)
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-8, iter_limit=20000, persistent=2))
+    assert r["persistent_form"] == 3
+    check_certificate(P, lp, kind, x, y, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_switching_the_test_off_changes_nothing_on_feasible_lps(P, prec):
     lp = lpgen.random_sparse_lp(11, 300, 500)
     on = P.pdlp_solve(lp, P.default_params(tol=1e-6, precision=prec))

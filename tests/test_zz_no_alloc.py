@@ -55,19 +55,24 @@ def long_column_lp(m=6000, n=3000, seed=5):
                      np.zeros(n), np.ones(n), np.zeros(n, np.uint8), "long_columns")
 
 
-CASES = [(lambda: lpgen.mip_relaxation(1), "fp64", 0),
-         (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16", 0),
-         (lambda: long_column_lp(), "fp32", 0),
-         (lambda: lpgen.mip_relaxation(2), "fp64", 1),
-         (lambda: lpgen.set_cover(8, m=2000, n=8000), "fp32", 1)]
+CASES = [(lambda: lpgen.mip_relaxation(1), "fp64", 0, 0),
+         (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16", 0, 0),
+         (lambda: long_column_lp(), "fp32", 0, 0),
+         (lambda: lpgen.mip_relaxation(2), "fp64", 1, 0),
+         (lambda: lpgen.set_cover(8, m=2000, n=8000), "fp32", 1, 0),
+         # one block with the LP in shared memory; bound-objective rescaling
+         (lambda: lpgen.mip_relaxation(3), "fp64", 2, 0),
+         (lambda: lpgen.mip_relaxation(4), "fp64", 0, 1),
+         (lambda: lpgen.set_cover(9, m=2000, n=8000), "bf16", 0, 1)]
 
 
-@pytest.mark.parametrize("maker,prec,persistent", CASES)
-def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec, persistent):
+@pytest.mark.parametrize("maker,prec,persistent,rescale", CASES)
+def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec, persistent, rescale):
     import torch
     lp = maker()
     d = P.DeviceLP(lp)
-    prm = P.default_params(tol=1e-6, precision=prec, persistent=persistent)
+    prm = P.default_params(tol=1e-6, precision=prec, persistent=persistent,
+                           bound_objective_rescaling=rescale)
     assert P.workspace_size(lp.m, lp.n, lp.nnz, prm) <= P.binding.NOALLOC_BYTES
     xr, yr, rr = P.pdlp_solve_device(d, prm)
     xr, yr = xr.cpu().numpy(), yr.cpu().numpy()
@@ -83,13 +88,15 @@ def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec, pers
         assert r["rel_kkt"] == pytest.approx(rr["rel_kkt"], rel=PARITY)
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_noalloc_call_leaves_device_memory_unchanged(P, persistent):
     """The property the entry point exists for: after a first call (which may load
     the library's module, and with it the static array), a call changes neither the
     memory PyTorch has allocated nor the device's free memory."""
     import torch
-    lp = lpgen.set_cover(9, m=2000, n=8000)
+    # persistent = 2 on an LP that fits in shared memory (the kernel's dynamic shared
+    # memory is no device allocation)
+    lp = lpgen.mip_relaxation(1) if persistent == 2 else lpgen.set_cover(9, m=2000, n=8000)
     d = P.DeviceLP(lp)
     prm = P.default_params(tol=1e-4, precision="fp32", persistent=persistent)
     xo = torch.empty(lp.n, dtype=torch.float64, device="cuda")
