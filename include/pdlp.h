@@ -213,7 +213,7 @@ typedef struct {
                              1 one cooperative kernel per check period, 2 one block per
                              check period stepping from global memory, 3 one block with
                              the LP held in shared memory (persistent = 2 when the matrix,
-                             vectors and iterates fit: 73 KB for a 200 x 400 relaxation
+                             vectors and iterates fit: 76 KB for a 200 x 400 relaxation
                              with 1,600 nonzeros in float64) */
 } pdlp_result;
 

@@ -16,7 +16,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kStepBlocksPerSmF32 = 4;
 // static shared memory the one-block shared-memory step kernel keeps for itself (its
 // copy of the state and the block reductions), subtracted from the device's opt-in limit
-constexpr int kSmemStatic = 2048;
+constexpr int kSmemStatic = 8192;
 
 // Matrix value formats of the iteration matrix.
 struct Pattern {};  // every stored value is exactly +1: no value array at all

@@ -18,6 +18,7 @@ enum Mode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_BF16 = 2, MODE_PAT = 3 };
 struct SmemLayout {
   int t_ptr, t_col, t_val, a_ptr, a_col, a_val;
   int c, l, u, tw, q, sw, kind, x0, x1, y0, y1, sx, sy;
+  int ot, oa;  // the columns and the rows in the order the threads take them
   int bytes;
 };
 
@@ -52,6 +53,8 @@ inline SmemLayout smem_layout(long long m, long long n, long long nnz, int it, b
   L.y1 = take(it * m);
   L.sx = take(it * n);
   L.sy = take(it * m);
+  L.ot = take(4 * n);
+  L.oa = take(4 * m);
   L.bytes = (int)(o < (1LL << 30) ? o : (1LL << 30));
   return L;
 }

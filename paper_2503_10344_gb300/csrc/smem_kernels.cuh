@@ -13,7 +13,11 @@
 //   dual:   y' = proj_Y(y + sigma (q - K(2x' - x))) from the (x', x' - x) pairs, one
 //           thread per row of A; ||y' - y||^2 and (y' - y)^T K (x' - x);
 //   decision (A6) by thread 0 on the block's copy of the state,
-// with a block barrier between the phases.  At exit the iterate buffers and running
+// with a block barrier between the phases.  The threads take the rows longest first
+// (a stable order by length, built at entry), so the 32 rows of a warp have nearly equal
+// lengths: a float64 warp instruction holds the SM's float64 pipe ~16 cycles whatever
+// its active lanes, and a warp's sum loop runs as long as its longest row.  At exit the
+// iterate buffers and running
 // sums go back to global memory (where the KKT block reads them) with the state.  The
 // same iteration as the two-launch kernels; the partial sums are added in another
 // order, so float64 iterates agree with theirs to rounding.
@@ -30,6 +34,7 @@ __global__ void __launch_bounds__(kBlock) k_smem(IterData<T, V> d, SmemLayout L,
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ DevState ls;
   __shared__ int stop;
+  __shared__ T red[3][kBlock];
   DevState* gst = d.st;
   if (threadIdx.x == 0) {
     ls = *gst;
@@ -55,10 +60,28 @@ __global__ void __launch_bounds__(kBlock) k_smem(IterData<T, V> d, SmemLayout L,
   T* ys[2] = {(T*)(sm + L.y0), (T*)(sm + L.y1)};
   T* sx = (T*)(sm + L.sx);
   T* sy = (T*)(sm + L.sy);
+  int* ot = (int*)(sm + L.ot);
+  int* oa = (int*)(sm + L.oa);
   // ---- copy in (iterates with ordinary loads: the KKT block of the same graph wrote them)
   const int nnz = __ldg(d.t_ptr + n);
   for (int i = tid; i <= n; i += kBlock) tp[i] = __ldg(d.t_ptr + i);
   for (int i = tid; i <= m; i += kBlock) ap[i] = __ldg(d.a_ptr + i);
+  __syncthreads();
+  // rows by descending length, ties by index: a row's place is the number of rows before
+  // it in that order (every thread compares its rows with all the others)
+  auto order = [&](const int* ptr, int rows, int* ord) {
+    for (int r = tid; r < rows; r += kBlock) {
+      const int len = ptr[r + 1] - ptr[r];
+      int pos = 0;
+      for (int k = 0; k < rows; ++k) {
+        const int lk = ptr[k + 1] - ptr[k];
+        pos += (lk > len) || (lk == len && k < r);
+      }
+      ord[pos] = r;
+    }
+  };
+  order(tp, n, ot);
+  order(ap, m, oa);
   for (int p = tid; p < nnz; p += kBlock) {
     tc[p] = __ldg(d.t_col + p);
     ac[p] = __ldg(d.a_col + p);
@@ -95,7 +118,8 @@ __global__ void __launch_bounds__(kBlock) k_smem(IterData<T, V> d, SmemLayout L,
     // ---- A4: primal step, one thread per column
     const T tau = StepT<T>::tau(&ls);
     T dx2 = 0;
-    for (int j = tid; j < n; j += kBlock) {
+    for (int t = tid; t < n; t += kBlock) {
+      const int j = ot[t];
       T aty = 0;
       for (int p = tp[j]; p < tp[j + 1]; ++p) aty += (VALS ? tv[p] : (T)1) * y[tc[p]];
       const T xo = x[j].x;
@@ -109,11 +133,12 @@ __global__ void __launch_bounds__(kBlock) k_smem(IterData<T, V> d, SmemLayout L,
       if (pw != (T)0) sx[j] += pw * xo;  // A7: add the iterate whose weight is pending
       dx2 += IMPLICIT ? dd * dd / tw[j] : dd * dd;
     }
-    const T sdx = block_sum1<T>(dx2);  // its barriers also order xn before the dual phase
+    __syncthreads();  // xn complete before the dual phase gathers it
     // ---- A5: dual step, one thread per row
     const T sigma = StepT<T>::sigma(&ls);
     T dy2 = 0, dkd = 0;
-    for (int i = tid; i < m; i += kBlock) {
+    for (int t = tid; t < m; t += kBlock) {
+      const int i = oa[t];
       T kx = 0, kd = 0;  // (K x')_i, (K dx)_i
       for (int p = ap[i]; p < ap[i + 1]; ++p) {
         const T v = VALS ? av[p] : (T)1;
@@ -131,15 +156,34 @@ __global__ void __launch_bounds__(kBlock) k_smem(IterData<T, V> d, SmemLayout L,
       dy2 += IMPLICIT ? dd * dd / sw[i] : dd * dd;
       dkd += dd * kd;
     }
-    T a = sdx, b0 = dy2, b1 = dkd;
-    // thread 0's a is the primal sum already; the others contribute 0 to it
-    if (tid != 0) a = 0;
-    block_sum3<T>(a, b0, b1);
-    // ---- A6: the decision
-    if (tid == 0) {
-      T fd, fi;
-      step_factors(&ls, ls.attempts + 1, &fd, &fi);
-      decide_step<T>(&ls, a, b0, b1, fd, fi);
+    // the three sums by one warp: every thread's values through shared memory, eight
+    // additions per lane, then five shuffle levels (a float64 warp instruction holds the
+    // pipe as long with one active lane as with 32, so one warp reducing costs an eighth
+    // of eight warps shuffling)
+    red[0][tid] = dx2;
+    red[1][tid] = dy2;
+    red[2][tid] = dkd;
+    __syncthreads();
+    if (tid < 32) {
+      T a = 0, b0 = 0, b1 = 0;
+#pragma unroll
+      for (int i = tid; i < kBlock; i += 32) {
+        a += red[0][i];
+        b0 += red[1][i];
+        b1 += red[2][i];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+      }
+      // ---- A6: the decision
+      if (tid == 0) {
+        T fd, fi;
+        step_factors(&ls, ls.attempts + 1, &fd, &fi);
+        decide_step<T>(&ls, a, b0, b1, fd, fi);
+      }
     }
     __syncthreads();
     if (ls.status != 0 || ls.check_due) break;

@@ -957,7 +957,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     const int want = p->persistent == 2 ? 1 : 0;
     if (p->persistent == 2) {
       // the one block holds the LP in shared memory when it fits (the 200 x 400
-      // relaxations take 73 KB in float64), else it steps from global memory
+      // relaxations take 76 KB in float64), else it steps from global memory
       int dev = 0, optin = 0;
       CUDA_TRY(cudaGetDevice(&dev));
       CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));

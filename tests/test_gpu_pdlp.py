@@ -602,8 +602,9 @@ def test_one_block_persistent_kernel_matches_two_launch_form(P, name):
     _, _, r2, it2 = gpu_iterates(P, lp, persistent=2, **kw)
     _, _, r0, it0 = gpu_iterates(P, lp, persistent=0, **kw)
     assert r2["iters"] == r0["iters"] == 300
-    # the two small LPs fit in shared memory (73 / 224 KB in float64), the covering LP not
-    assert r2["persistent_form"] == (2 if name == "set_cover_2000x8000" else 3)
+    # the 200 x 400 relaxation fits in shared memory (76 KB in float64), the other two
+    # do not (227 KB, 1.9 MB) and step from global memory
+    assert r2["persistent_form"] == (3 if name == "mip_relaxation_200x400" else 2)
     assert r0["persistent_form"] == 0
     for k in ("x_cur", "y_cur", "x_avg", "y_avg"):
         assert rel(it2[k], it0[k]) <= 1e-13, k
@@ -615,14 +616,20 @@ def test_one_block_persistent_kernel_matches_two_launch_form(P, name):
         assert abs(r["primal_obj"] - obj) / (1 + abs(obj)) <= 1e-7
 
 
-@pytest.mark.parametrize("name", ["mip_relaxation_200x400", "random_free_eq_300x500"])
+SMALL = {"mip_relaxation_200x400": lambda: inst("mip_relaxation_200x400"),
+         # 30 equality rows, free and one-sided columns; 102 KB in float64
+         "random_free_eq_200x300": lambda: lpgen.random_sparse_lp(11, 200, 300)}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
 def test_shared_memory_kernel_by_replay(P, name):
     """The one-block kernel with the LP in shared memory (persistent = 2): 300 adaptive,
     restarted steps with replayed step sizes match the oracle (iterates to 1e-9, every
     accept and restart the rule applied to the oracle's numbers)."""
-    _, _, r = P.pdlp_solve(inst(name), P.default_params(iter_limit=5, terminate=0, persistent=2))
+    lp = SMALL[name]()
+    _, _, r = P.pdlp_solve(lp, P.default_params(iter_limit=5, terminate=0, persistent=2))
     assert r["persistent_form"] == 3
-    check_replay(P, inst(name), 300, persistent=2)
+    check_replay(P, lp, 300, persistent=2)
 
 
 def test_shared_memory_kernel_empty_rows_and_columns(P):
