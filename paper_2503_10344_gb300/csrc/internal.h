@@ -87,6 +87,7 @@ struct IterRaw {
   // one-block persistent form (persistent = 2): smem.bytes > 0 runs k_smem, the LP held in
   // that much shared memory; 0 runs the one-block k_persist from global memory
   SmemLayout smem;
+  const int *ord_t, *ord_a;  // its order of the columns and rows (longest first)
 };
 
 // IK_DUAL launches the dual step kernel and then the step decision (k_decide)

@@ -86,6 +86,7 @@ struct IterData {
   int tile;                                            // tile kernels (float32 only): form
   TileSet tt, ta;                                      // their items over A^T and A
   int grid_tt, grid_ta, work_tt, work_ta, tslot;
+  const int *ord_t, *ord_a;                            // one-block kernel: rows longest first
 };
 
 // Rows of one LP (span), one aligned group of LANES lanes per row, rows

@@ -44,6 +44,8 @@ IterData<T, V> typed(const IterRaw& r) {
   d.work_tt = r.work_tt;
   d.work_ta = r.work_ta;
   d.tslot = r.tslot;
+  d.ord_t = r.ord_t;
+  d.ord_a = r.ord_a;
   return d;
 }
 

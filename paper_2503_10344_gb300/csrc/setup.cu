@@ -586,6 +586,21 @@ __global__ void k_rescale(int m, int n, double beta, double gamma, T* c, T* l, T
   }
 }
 
+// rows by descending length, ties by index: a row's place is the number of rows before it
+// in that order (every thread compares its row with all the others)
+__global__ void k_len_order(const int* ptr, int rows, int* ord) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+    const int len = ptr[r + 1] - ptr[r];
+    int pos = 0;
+    for (int k = 0; k < rows; ++k) {
+      const int lk = ptr[k + 1] - ptr[k];
+      pos += (lk > len) || (lk == len && k < r);
+    }
+    ord[pos] = (int)r;
+  }
+}
+
 // float64 auxiliaries of the KKT passes: 1 / D_r, 1 / D_c and, per column, bit 0
 // = lower bound finite, bit 1 = upper bound finite (integer tests instead of
 // float64 compares in the per-column epilogue)
@@ -863,6 +878,11 @@ cudaError_t setup_iter_vectors(const VecIn& v, int fp32, void* c, void* l, void*
 size_t setup_part_doubles(int m, int n) {
   const int G = device_sm_count() * 8;
   return (size_t)G * 7 + (size_t)G + 16;
+}
+
+cudaError_t setup_len_order(const int* ptr, int rows, int* ord, cudaStream_t s) {
+  k_len_order<<<grid_for(rows, device_sm_count() * 8), kBlock, 0, s>>>(ptr, rows, ord);
+  return cudaGetLastError();
 }
 
 cudaError_t setup_rescale(int m, int n, int fp32, double beta, double gamma, void* c, void* l,

@@ -69,6 +69,9 @@ size_t scan_tmp_ints(long long N);
 // dst[i] = src[i] + offset (index arrays moved into a batch's global numbering)
 cudaError_t setup_offset_copy(int* dst, const int* src, long long count, int offset,
                               cudaStream_t s);
+// The rows of a CSR matrix by descending length, ties by index (ord[place] = row).
+cudaError_t setup_len_order(const int* ptr, int rows, int* ord, cudaStream_t s);
+
 // Bound-objective rescaling of the iteration vectors and the start point, with the
 // factors beta (right-hand side, bounds, x) and gamma (objective, y) folded into the
 // KKT passes' D_r, D_c and their inverses (k_rescale in setup.cu).

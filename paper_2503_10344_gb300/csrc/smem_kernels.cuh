@@ -13,14 +13,14 @@
 //   dual:   y' = proj_Y(y + sigma (q - K(2x' - x))) from the (x', x' - x) pairs, one
 //           thread per row of A; ||y' - y||^2 and (y' - y)^T K (x' - x);
 //   decision (A6) by thread 0 on the block's copy of the state,
-// with a block barrier between the phases.  The threads take the rows longest first
-// (a stable order by length, built at entry), so the 32 rows of a warp have nearly equal
-// lengths: a float64 warp instruction holds the SM's float64 pipe ~16 cycles whatever
-// its active lanes, and a warp's sum loop runs as long as its longest row.  At exit the
-// iterate buffers and running
-// sums go back to global memory (where the KKT block reads them) with the state.  The
-// same iteration as the two-launch kernels; the partial sums are added in another
-// order, so float64 iterates agree with theirs to rounding.
+// with a block barrier between the phases.  The threads take the rows longest first (a
+// stable order by length, built once per solve at setup), so the 32 rows of a warp have
+// nearly equal lengths: a float64 warp instruction holds the SM's float64 pipe ~16
+// cycles whatever its active lanes, and a warp's sum loop runs as long as its longest
+// row.  At exit the iterate buffers and running sums go back to global memory (where
+// the KKT block reads them) with the state.  The same iteration as the two-launch
+// kernels; the partial sums are added in another order, so float64 iterates agree with
+// theirs to rounding.
 #pragma once
 
 #include "internal.h"
@@ -66,22 +66,9 @@ __global__ void __launch_bounds__(kBlock) k_smem(IterData<T, V> d, SmemLayout L,
   const int nnz = __ldg(d.t_ptr + n);
   for (int i = tid; i <= n; i += kBlock) tp[i] = __ldg(d.t_ptr + i);
   for (int i = tid; i <= m; i += kBlock) ap[i] = __ldg(d.a_ptr + i);
-  __syncthreads();
-  // rows by descending length, ties by index: a row's place is the number of rows before
-  // it in that order (every thread compares its rows with all the others)
-  auto order = [&](const int* ptr, int rows, int* ord) {
-    for (int r = tid; r < rows; r += kBlock) {
-      const int len = ptr[r + 1] - ptr[r];
-      int pos = 0;
-      for (int k = 0; k < rows; ++k) {
-        const int lk = ptr[k + 1] - ptr[k];
-        pos += (lk > len) || (lk == len && k < r);
-      }
-      ord[pos] = r;
-    }
-  };
-  order(tp, n, ot);
-  order(ap, m, oa);
+  // the order the threads take the columns and rows in (longest first, built at setup)
+  for (int i = tid; i < n; i += kBlock) ot[i] = __ldg(d.ord_t + i);
+  for (int i = tid; i < m; i += kBlock) oa[i] = __ldg(d.ord_a + i);
   for (int p = tid; p < nnz; p += kBlock) {
     tc[p] = __ldg(d.t_col + p);
     ac[p] = __ldg(d.a_col + p);

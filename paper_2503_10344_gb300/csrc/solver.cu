@@ -93,6 +93,7 @@ struct Bufs {
   void *c_it, *l_it, *u_it, *q_it, *tw, *sw, *x[2], *y[2], *sum_x, *sum_y;
   double *part_p, *part_d, *part_r, *part_c, *part_setup, *scalars;
   int *a_long, *t_long, *tmp, *flags2;
+  int *ord_t, *ord_a;  // columns / rows longest first (the shared-memory one-block kernel)
   DevState* st;
   // staged tile kernels (float32 iterates): items over A (dual step) and A^T (primal)
   TileItem *ti_a, *ti_t;
@@ -146,6 +147,8 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
   b.inv_dr = (double*)ar.take(8 * M);
   b.inv_dc = (double*)ar.take(8 * N);
   b.bflags = (unsigned char*)ar.take(N);
+  b.ord_t = (int*)ar.take(4 * N);
+  b.ord_a = (int*)ar.take(4 * M);
   b.c_it = ar.take(eb * N);
   b.l_it = ar.take(eb * N);
   b.u_it = ar.take(eb * N);
@@ -963,7 +966,16 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
       CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
       const SmemLayout L = smem_layout(m, n, nnz, mode == MODE_FP64 ? 8 : 4, mode != MODE_PAT,
                                        mode == MODE_BF16 || mode == MODE_PAT);
-      if (L.bytes <= optin - kSmemStatic) sv.ir.smem = L;
+      if (L.bytes <= optin - kSmemStatic) {
+        sv.ir.smem = L;
+        // the order in which the block's threads take the columns and rows (longest
+        // first), once per solve
+        CUDA_TRY(setup_len_order(bf.t_ptr, n, bf.ord_t, s));
+        if (m) CUDA_TRY(setup_len_order(bf.a_ptr, m, bf.ord_a, s));
+        g_launches += m ? 2 : 1;
+        sv.ir.ord_t = bf.ord_t;
+        sv.ir.ord_a = bf.ord_a;
+      }
     }
     int g = 0;
     cudaError_t e;
