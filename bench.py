@@ -51,7 +51,7 @@ def parse():
                     help="only time the fused kernels (pdlp_time_kernels) and print them")
     ap.add_argument("--reps", type=int, default=200)
     ap.add_argument("--workload", default="set_cover",
-                    choices=["set_cover", "batch", "energy", "fp", "c1"],
+                    choices=["set_cover", "batch", "energy", "fp", "c1", "variants"],
                     help="batch: 256 uneven covering sub-LPs (m in [2000, 40000], n = 4m, "
                          "10-50 %% of the columns fixed), solved together by pdlp_solve_batch; "
                          "c1 (with --kernels-only): the 200 x 400 MIP relaxation")
@@ -467,6 +467,9 @@ def energy_section(args, dev, stream, peak):
     with ClockSampler(dev.index) as clk:
         ms, res = solves(prm, 2, 1)
     ms64, res64 = solves(P.default_params(tol=1e-4, precision="fp64", iter_limit=200_000), 1, 0)
+    # the bound-objective rescaling variant on the same instance (not the default iteration)
+    msr, resr = solves(P.default_params(tol=1e-4, precision="fp32", iter_limit=200_000,
+                                        bound_objective_rescaling=1), 1, 0)
     kt = P.time_kernels(d, prm, reps=50, stream=stream)
     pk, src = _peak()
     obj64 = res64["primal_obj"]
@@ -481,6 +484,9 @@ def energy_section(args, dev, stream, peak):
                      "rel_kkt": res64["rel_kkt"], "primal_obj": obj64},
             "obj_rel_diff_vs_fp64": abs(res["primal_obj"] - obj64) / (1.0 + abs(obj64)),
             "speedup_vs_fp64_time_to_tol": ms64 / ms,
+            "bound_objective_rescaling": {"time_to_tol_s": msr / 1e3, "iters": resr["iters"],
+                                          "status": resr["status"], "rel_kkt": resr["rel_kkt"],
+                                          "primal_obj": resr["primal_obj"]},
             "roofline": kernel_roofline(kt, pk, src, "energy", "fp32"), "clocks": clk.summary()}
 
 
@@ -708,6 +714,40 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def run_variants(args):
+    """Bound-objective rescaling (pdlp_params.bound_objective_rescaling) against the default
+    iteration on the same instances and precision modes: iterations and iteration-phase
+    time to rel. KKT 1e-4 (float32 / pattern on the covering LPs and the energy system,
+    float64 on the 200 x 400 relaxations)."""
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    import lpgen
+    import paper_2503_10344_gb300 as P
+
+    cases = [("set_cover m=50000 n=200000", lpgen.set_cover(2025), "bf16"),
+             ("set_cover m=5000 n=20000", lpgen.set_cover(3, m=5000, n=20000), "bf16"),
+             ("energy_system 720 h", lpgen.energy_system(hours=720), "fp32")]
+    cases += [(f"mip_relaxation seed {k}", lpgen.mip_relaxation(k), "fp64") for k in range(1, 6)]
+    rows = []
+    for name, lp, prec in cases:
+        d = P.DeviceLP(lp)
+        row = {"instance": name, "precision": prec}
+        for resc in (0, 1):
+            prm = P.default_params(tol=1e-4, precision=prec, bound_objective_rescaling=resc,
+                                   iter_limit=200_000)
+            P.pdlp_solve_device(d, prm)  # warm
+            torch.cuda.synchronize()
+            _, _, r = P.pdlp_solve_device(d, prm)
+            row["rescaled" if resc else "default"] = {
+                "status": r["status"], "iters": r["iters"], "restarts": r["restarts"],
+                "solve_s": r["solve_s"], "rel_kkt": r["rel_kkt"], "primal_obj": r["primal_obj"]}
+        rows.append(row)
+    print(json.dumps({"workload": "bound-objective rescaling against the default iteration",
+                      "tol": 1e-4, "runs": rows}), flush=True)
+
+
 def run_energy(args):
     """The energy-system LP (8760 h x 20 regions x 6 technologies, 2.1M rows, 2.45M
     columns, 7.9M nonzeros) to rel. KKT 1e-4 with float32 iterates: the workload whose
@@ -811,7 +851,7 @@ def single_gpu_rank(args) -> bool:
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "gpu" and (a.kernels_only or a.workload in ("energy", "fp")) \
+    if a.impl == "gpu" and (a.kernels_only or a.workload in ("energy", "fp", "variants")) \
             and not single_gpu_rank(a):
         sys.exit(0)
     if a.kernels_only and a.impl == "gpu":
@@ -822,6 +862,8 @@ if __name__ == "__main__":
         run_energy(a)
     elif a.workload == "batch" and a.impl == "gpu":
         run_batch(a)
+    elif a.workload == "variants" and a.impl == "gpu":
+        run_variants(a)
     elif a.workload == "c1" and a.impl == "gpu":
         sys.exit("--workload c1 runs with --kernels-only (its solves are the default line's c1 section)")
     elif a.impl == "reference":
