@@ -535,6 +535,15 @@ def batch_section(args, dev, stream, peak):
                   "optimal": int(sum(r["status"] == P.PDLP_OPTIMAL for r in res1)),
                   "kernel_launches": int(res1[0]["kernel_launches"]),
                   "kernel_launches_two_launch_form": int(res[0]["kernel_launches"])}
+    # the launch shapes picked by the autotuner (timed step attempts, cached per shape) instead
+    # of the size heuristic
+    prma = P.default_params(tol=1e-4, precision="bf16", autotune=1)
+    P.pdlp_solve_batch(lps, prma, want_y=False)  # tunes and caches
+    _, _, resa = P.pdlp_solve_batch(lps, prma, want_y=False)
+    autotuned = {"solve_s": resa[0]["solve_s"], "iters_sum": int(sum(r["iters"] for r in resa)),
+                 "optimal": int(sum(r["status"] == P.PDLP_OPTIMAL for r in resa)),
+                 "lanes_A": int(resa[0]["lanes_A"]), "lanes_AT": int(resa[0]["lanes_AT"]),
+                 "heuristic_lanes": [int(res[0]["lanes_A"]), int(res[0]["lanes_AT"])]}
     return {"workload": f"batch of {len(lps)} set-cover sub-LPs, sum m={sum(l.m for l in lps)}, "
                         f"sum n={sum(l.n for l in lps)}, nnz={sum(l.nnz for l in lps)}, tol=1e-4",
             "precision": {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
@@ -545,7 +554,7 @@ def batch_section(args, dev, stream, peak):
             "solve_s": statistics.median(solve), "iters_sum": iters[-1],
             "iters_per_s": iters[-1] / solve[-1], "lps_per_s": len(lps) / statistics.median(solve),
             "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
-            "persistent": persistent,
+            "persistent": persistent, "autotuned": autotuned,
             "roofline": kernel_roofline(kt, pk, src), "clocks": clk.summary()}
 
 
