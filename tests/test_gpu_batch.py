@@ -199,3 +199,24 @@ def test_persistent_batch_float32_iterates(P):
 def test_persistent_two_is_rejected_for_batches(P):
     with pytest.raises(P.PdlpError, match="single LPs"):
         P.pdlp_solve_batch(mixed_lps()[:2], P.default_params(persistent=2))
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batch_with_degenerate_members(P, persistent):
+    """A batch holding an LP without rows, a 1 x 1 LP and LPs of ordinary size: every member
+    ends optimal with its own answer, in both batch forms."""
+    n = 5
+    norows = lpgen._lp(0, n, np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), np.zeros(0),
+                       np.zeros(0, np.uint8), np.array([1.0, -2.0, 0.0, 3.0, -0.5]),
+                       np.array([-1.0, 0.0, 0.5, -3.0, 2.0]), np.array([1.0, 2.0, 1.0, 5.0, 7.0]),
+                       np.zeros(n, np.uint8), "norows")
+    one = lpgen._lp(1, 1, np.zeros(1, np.int64), np.zeros(1, np.int64), np.array([2.0]),
+                    np.array([1.0]), np.array([lpgen.SENSE_GE], np.uint8), np.array([1.0]),
+                    np.array([0.0]), np.array([3.0]), np.zeros(1, np.uint8), "one")
+    lps = [lpgen.mip_relaxation(1), norows, one, lpgen.set_cover(7, m=2000, n=8000)]
+    xs, ys, res = P.pdlp_solve_batch(lps, P.default_params(tol=1e-6, persistent=persistent))
+    assert all(r["status"] == P.PDLP_OPTIMAL for r in res), [r["status"] for r in res]
+    np.testing.assert_allclose(xs[1], [-1.0, 2.0, 0.5, -3.0, 7.0], atol=1e-6)
+    assert xs[2][0] == pytest.approx(0.5, abs=1e-6) and ys[2][0] == pytest.approx(0.5, abs=1e-6)
+    for lp, x, y in ((lps[0], xs[0], ys[0]), (lps[3], xs[3], ys[3])):
+        assert O.kkt_original(lp, x, y).rel_kkt <= 1.01e-6

@@ -334,6 +334,41 @@ def test_no_rows_closed_form(P):
     np.testing.assert_array_equal(x, [-1.0, 2.0, 0.5, -3.0, 7.0])
 
 
+def no_rows_lp():
+    n = 5
+    c = np.array([1.0, -2.0, 0.0, 3.0, -0.5])
+    l = np.array([-1.0, 0.0, 0.5, -3.0, 2.0])
+    u = np.array([1.0, 2.0, 1.0, 5.0, 7.0])
+    return lpgen._lp(0, n, np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0), np.zeros(0),
+                     np.zeros(0, np.uint8), c, l, u, np.zeros(n, np.uint8), "norows")
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(precision="bf16"),
+                                dict(precision="fp32", lanes_A=1, lanes_AT=1),
+                                dict(persistent=2), dict(precision="fp32", persistent=2),
+                                dict(persistent=1), dict(bound_objective_rescaling=1),
+                                dict(precision="fp32", tiles=1), dict(precision="fp32", tiles=2)],
+                         ids=lambda kw: ",".join(f"{k}={v}" for k, v in kw.items()))
+def test_no_rows_in_every_form(P, kw):
+    """An LP without rows (the optimum is each column at the bound its cost points to) in
+    every precision, lanes, persistent, tile and rescaling form."""
+    x, y, res = P.pdlp_solve(no_rows_lp(), P.default_params(tol=1e-6, **kw))
+    assert res["status"] == P.PDLP_OPTIMAL, res
+    np.testing.assert_allclose(x, [-1.0, 2.0, 0.5, -3.0, 7.0], rtol=1e-6, atol=1e-6)
+
+
+def test_one_by_one_lp_in_every_form(P):
+    """min x s.t. 2x >= 1, x in [0, 3]: x* = 1/2, y* = 1/2."""
+    lp = lpgen._lp(1, 1, np.zeros(1, np.int64), np.zeros(1, np.int64), np.array([2.0]),
+                   np.array([1.0]), np.array([lpgen.SENSE_GE], np.uint8), np.array([1.0]),
+                   np.array([0.0]), np.array([3.0]), np.zeros(1, np.uint8), "one")
+    for kw in (dict(), dict(precision="fp32"), dict(persistent=2), dict(persistent=1),
+               dict(precision="fp32", lanes_A=1, lanes_AT=1), dict(bound_objective_rescaling=1)):
+        x, y, res = P.pdlp_solve(lp, P.default_params(tol=1e-7, **kw))
+        assert res["status"] == P.PDLP_OPTIMAL, (kw, res)
+        assert x[0] == pytest.approx(0.5, abs=1e-6) and y[0] == pytest.approx(0.5, abs=1e-6), kw
+
+
 def test_empty_rows_and_columns(P):
     lp = lpgen.random_sparse_lp(5, 60, 80)  # has empty rows and columns
     assert np.any(np.diff(lp.row_ptr) == 0)
