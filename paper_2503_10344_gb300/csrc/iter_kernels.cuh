@@ -670,11 +670,15 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
 // records the decision trace and writes the state back at exit.  Rows keep
 // their owner thread across attempts, so a row's own iterate entries are read
 // back by the thread that wrote them; entries gathered from other blocks' rows
-// (y in the primal phase, the (x', dx) pairs in the dual phase) and the
-// partial sums are read through L2 (ld.global.cg), never through the
-// non-coherent L1 path.  Partial sums alternate between two buffers by attempt
-// parity, so a block still reducing attempt k never sees attempt k + 1's
-// values.  Every barrier wait is bounded: a block that gives up flags the
+// (y in the primal phase, the (x', dx) pairs in the dual phase) are read with
+// ordinary loads, which each grid barrier orders after the writes (thread 0's
+// acquire load of the barrier generation, after the writers' fence and arrival,
+// then a block barrier); the partial sums are read through L2 (ld.global.cg);
+// nothing the kernel writes goes through the non-coherent read-only path.  The
+// float32 phases use the pipelined row traversal of the two-launch kernels.
+// Partial sums alternate between two buffers by attempt parity, so a block
+// still reducing attempt k never sees attempt k + 1's values.  Every barrier
+// wait is bounded: a block that gives up flags the
 // state (kStatusWaitFailed) and returns, and so do the others.
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -727,8 +731,12 @@ __device__ __forceinline__ bool grid_barrier(DevState* st) {
 // two-launch form), with three grid barriers per attempt: after the primal phase, after
 // the dual phase, and after the decisions, which block b takes for the LPs b, b + G, ...
 // from the LP's slots in order.  Each LP steps until its own check falls due or it
-// stops; the launch ends when no LP steps any more or after `max_attempts`.  State,
-// partial sums and every vector entry another block wrote are read through L2.
+// stops; the launch ends when no LP steps any more or after `max_attempts`.  The state
+// and the partial sums are read through L2; vector entries other blocks wrote in an earlier
+// phase are read with ordinary loads: each grid barrier ends with thread 0's acquire load of
+// the barrier generation (after the writers' fence and arrival) and a block barrier, which
+// orders them after those writes.  The float32 phases use the same pipelined row traversal
+// as the two-launch kernels.
 template <typename T>
 struct StepView {
   int go, cur;
@@ -773,23 +781,36 @@ __device__ __forceinline__ void persist_batch(const IterData<T, V>& d, int max_a
       vec2_t<T>* xn = v.cur ? d.x[0] : d.x[1];
       const T* y = v.cur ? d.y[1] : d.y[0];
       T dx2 = 0;
-      auto load = [&](int p) -> T {
-        return Ld<T, V>::get(d.t_val, p) * __ldcg(y + __ldg(d.t_col + p));
+      auto val = [&](int p) -> T { return Ld<T, V>::get(d.t_val, p); };
+      auto term = [&](T a, int i) -> T { return a * y[i]; };
+      auto load = [&](int p) -> T { return term(val(p), __ldg(d.t_col + p)); };
+      auto pref_c = [&](int j) -> PreCP<T> {
+        return PreCP<T>{__ldg(d.c + j), __ldg(d.l + j), __ldg(d.u + j),
+                        IMPLICIT ? __ldg(d.tw + j) : (T)1};
       };
-      auto epi = [&](int j, T aty) {
-        const T xo = __ldcg(x + j).x;
-        const T g = __ldg(d.c + j) - aty;
-        const T step = IMPLICIT ? v.tau * __ldg(d.tw + j) : v.tau;
-        const T xv = clampv(xo - step * g, __ldg(d.l + j), __ldg(d.u + j));
-        const T dd = xv - xo;
+      auto pref_v = [&](int j) -> PreVP<T> {
+        return PreVP<T>{x[j].x, v.pw != (T)0 ? d.sum_x[j] : (T)0};
+      };
+      auto fin = [&](int j, T aty, const PreCP<T>& c, const PreVP<T>& pv) {
+        const T step = IMPLICIT ? v.tau * c.tw : v.tau;
+        const T xv = clampv(pv.xo - step * (c.c - aty), c.l, c.u);
+        const T dd = xv - pv.xo;
         vec2_t<T> o;
         o.x = xv;
         o.y = dd;
         xn[j] = o;
-        if (v.pw != (T)0) d.sum_x[j] = __ldcg(d.sum_x + j) + v.pw * xo;
-        dx2 += IMPLICIT ? dd * dd / __ldg(d.tw + j) : dd * dd;
+        if (v.pw != (T)0) d.sum_x[j] = pv.sx + v.pw * pv.xo;
+        dx2 += IMPLICIT ? dd * dd / c.tw : dd * dd;
       };
-      rows_all<TILED, LT, T>(sp, d.t_ptr, d.t_thresh, load, epi);
+      auto epi = [&](int j, T aty) { fin(j, aty, pref_c(j), pref_v(j)); };
+      if constexpr (TILED) {
+        rows_all<true, LT, T>(sp, d.t_ptr, d.t_thresh, load, epi);
+      } else if (sp.bidx < sp.nshort) {
+        rows_short3<LT, T, PreCP<T>, PreVP<T>>(sp, d.t_ptr, d.t_col, d.t_thresh, val, term, pref_c,
+                                               pref_v, fin, [] { return true; });
+      } else {
+        rows_long<T>(sp, d.t_ptr, load, epi);
+      }
       const T s = block_sum1<T>(dx2);
       if (threadIdx.x == 0) d.part_p[vb] = s;
     }
@@ -806,23 +827,37 @@ __device__ __forceinline__ void persist_batch(const IterData<T, V>& d, int max_a
       const T* y = v.cur ? d.y[1] : d.y[0];
       T* yn = v.cur ? d.y[0] : d.y[1];
       T dy2 = 0, dkd = 0;
-      auto load = [&](int p) -> P2<T> {
-        const T val = Ld<T, V>::get(d.a_val, p);
-        const vec2_t<T> xv = __ldcg(xn + __ldg(d.a_col + p));
-        return P2<T>{val * xv.x, val * xv.y};
+      auto val = [&](int p) -> T { return Ld<T, V>::get(d.a_val, p); };
+      auto term = [&](T a, int j) -> P2<T> {
+        const vec2_t<T> xv = xn[j];
+        return P2<T>{a * xv.x, a * xv.y};
       };
-      auto epi = [&](int i, P2<T> acc) {
-        const T yo = __ldcg(y + i);
-        const T step = IMPLICIT ? v.sigma * __ldg(d.sw + i) : v.sigma;
-        T yv = yo + step * (__ldg(d.q + i) - (acc.a + acc.b));
-        if (__ldg(d.row_kind + i) != 1) yv = maxv(yv, (T)0);
+      auto load = [&](int p) -> P2<T> { return term(val(p), __ldg(d.a_col + p)); };
+      auto pref_c = [&](int i) -> PreCD<T> {
+        return PreCD<T>{__ldg(d.q + i), IMPLICIT ? __ldg(d.sw + i) : (T)1, (int)__ldg(d.row_kind + i)};
+      };
+      auto pref_v = [&](int i) -> PreVD<T> {
+        return PreVD<T>{y[i], v.pw != (T)0 ? d.sum_y[i] : (T)0};
+      };
+      auto fin = [&](int i, P2<T> acc, const PreCD<T>& c, const PreVD<T>& pv) {
+        const T step = IMPLICIT ? v.sigma * c.sw : v.sigma;
+        T yv = pv.yo + step * (c.q - (acc.a + acc.b));
+        if (c.kind != 1) yv = maxv(yv, (T)0);
         yn[i] = yv;
-        if (v.pw != (T)0) d.sum_y[i] = __ldcg(d.sum_y + i) + v.pw * yo;
-        const T dd = yv - yo;
-        dy2 += IMPLICIT ? dd * dd / __ldg(d.sw + i) : dd * dd;
+        if (v.pw != (T)0) d.sum_y[i] = pv.sy + v.pw * pv.yo;
+        const T dd = yv - pv.yo;
+        dy2 += IMPLICIT ? dd * dd / c.sw : dd * dd;
         dkd += dd * acc.b;
       };
-      rows_all<TILED, LA, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
+      auto epi = [&](int i, P2<T> acc) { fin(i, acc, pref_c(i), pref_v(i)); };
+      if constexpr (TILED) {
+        rows_all<true, LA, P2<T>>(sp, d.a_ptr, d.a_thresh, load, epi);
+      } else if (sp.bidx < sp.nshort) {
+        rows_short3<LA, P2<T>, PreCD<T>, PreVD<T>>(sp, d.a_ptr, d.a_col, d.a_thresh, val, term,
+                                                   pref_c, pref_v, fin, [] { return true; });
+      } else {
+        rows_long<P2<T>>(sp, d.a_ptr, load, epi);
+      }
       const T s0 = block_sum1<T>(dy2);
       const T s1 = block_sum1<T>(dkd);
       if (threadIdx.x == 0) {
@@ -906,26 +941,33 @@ __global__ void __launch_bounds__(kBlock) k_persist(IterData<T, V> d, int max_at
       const T* y = cur ? d.y[1] : d.y[0];
       const T tau = StepT<T>::tau(&ls);
       T dx2 = 0;
-      auto load = [&](int p) -> T {
-        return Ld<T, V>::get(d.t_val, p) * __ldcg(y + __ldg(d.t_col + p));
+      auto val = [&](int p) -> T { return Ld<T, V>::get(d.t_val, p); };
+      auto term = [&](T a, int i) -> T { return a * y[i]; };
+      auto load = [&](int p) -> T { return term(val(p), __ldg(d.t_col + p)); };
+      auto pref_c = [&](int j) -> PreCP<T> {
+        return PreCP<T>{__ldg(d.c + j), __ldg(d.l + j), __ldg(d.u + j),
+                        IMPLICIT ? __ldg(d.tw + j) : (T)1};
       };
-      auto epi = [&](int j, T aty) {
-        const T xo = __ldcg(x + j).x;
-        const T g = __ldg(d.c + j) - aty;
-        const T step = IMPLICIT ? tau * __ldg(d.tw + j) : tau;
-        const T xv = clampv(xo - step * g, __ldg(d.l + j), __ldg(d.u + j));
-        const T dd = xv - xo;
+      auto pref_v = [&](int j) -> PreVP<T> {
+        return PreVP<T>{x[j].x, pw != (T)0 ? d.sum_x[j] : (T)0};
+      };
+      auto fin = [&](int j, T aty, const PreCP<T>& c, const PreVP<T>& pv) {
+        const T step = IMPLICIT ? tau * c.tw : tau;
+        const T xv = clampv(pv.xo - step * (c.c - aty), c.l, c.u);
+        const T dd = xv - pv.xo;
         vec2_t<T> o;
         o.x = xv;
         o.y = dd;
         xn[j] = o;
-        if (pw != (T)0) d.sum_x[j] = __ldcg(d.sum_x + j) + pw * xo;
-        dx2 += IMPLICIT ? dd * dd / __ldg(d.tw + j) : dd * dd;
+        if (pw != (T)0) d.sum_x[j] = pv.sx + pw * pv.xo;
+        dx2 += IMPLICIT ? dd * dd / c.tw : dd * dd;
       };
+      auto epi = [&](int j, T aty) { fin(j, aty, pref_c(j), pref_v(j)); };
       if constexpr (TILED)
         rows_tiled<LT, T>(sp_p, d.t_ptr, d.t_thresh, load, epi);
       else
-        rows_short<LT, T>(sp_p, d.t_ptr, d.t_thresh, load, epi);
+        rows_short3<LT, T, PreCP<T>, PreVP<T>>(sp_p, d.t_ptr, d.t_col, d.t_thresh, val, term,
+                                               pref_c, pref_v, fin, [] { return true; });
       rows_long<T>(sp_pl, d.t_ptr, load, epi);
       const T s = block_sum1<T>(dx2);
       if (threadIdx.x == 0) pp[par * G + b] = s;
@@ -938,27 +980,34 @@ __global__ void __launch_bounds__(kBlock) k_persist(IterData<T, V> d, int max_at
       T* yn = cur ? d.y[0] : d.y[1];
       const T sigma = StepT<T>::sigma(&ls);
       T dy2 = 0, dkd = 0;
-      auto load = [&](int p) -> P2<T> {
-        const T v = Ld<T, V>::get(d.a_val, p);
-        const vec2_t<T> xv = __ldcg(xn + __ldg(d.a_col + p));
-        return P2<T>{v * xv.x, v * xv.y};
+      auto val = [&](int p) -> T { return Ld<T, V>::get(d.a_val, p); };
+      auto term = [&](T a, int j) -> P2<T> {
+        const vec2_t<T> xv = xn[j];
+        return P2<T>{a * xv.x, a * xv.y};
       };
-      auto epi = [&](int i, P2<T> acc) {
-        const T kxbar = acc.a + acc.b;
-        const T yo = __ldcg(y + i);
-        const T step = IMPLICIT ? sigma * __ldg(d.sw + i) : sigma;
-        T v = yo + step * (__ldg(d.q + i) - kxbar);
-        if (__ldg(d.row_kind + i) != 1) v = maxv(v, (T)0);
-        yn[i] = v;
-        if (pw != (T)0) d.sum_y[i] = __ldcg(d.sum_y + i) + pw * yo;
-        const T dd = v - yo;
-        dy2 += IMPLICIT ? dd * dd / __ldg(d.sw + i) : dd * dd;
+      auto load = [&](int p) -> P2<T> { return term(val(p), __ldg(d.a_col + p)); };
+      auto pref_c = [&](int i) -> PreCD<T> {
+        return PreCD<T>{__ldg(d.q + i), IMPLICIT ? __ldg(d.sw + i) : (T)1, (int)__ldg(d.row_kind + i)};
+      };
+      auto pref_v = [&](int i) -> PreVD<T> {
+        return PreVD<T>{y[i], pw != (T)0 ? d.sum_y[i] : (T)0};
+      };
+      auto fin = [&](int i, P2<T> acc, const PreCD<T>& c, const PreVD<T>& pv) {
+        const T step = IMPLICIT ? sigma * c.sw : sigma;
+        T yv = pv.yo + step * (c.q - (acc.a + acc.b));
+        if (c.kind != 1) yv = maxv(yv, (T)0);
+        yn[i] = yv;
+        if (pw != (T)0) d.sum_y[i] = pv.sy + pw * pv.yo;
+        const T dd = yv - pv.yo;
+        dy2 += IMPLICIT ? dd * dd / c.sw : dd * dd;
         dkd += dd * acc.b;
       };
+      auto epi = [&](int i, P2<T> acc) { fin(i, acc, pref_c(i), pref_v(i)); };
       if constexpr (TILED)
         rows_tiled<LA, P2<T>>(sp_d, d.a_ptr, d.a_thresh, load, epi);
       else
-        rows_short<LA, P2<T>>(sp_d, d.a_ptr, d.a_thresh, load, epi);
+        rows_short3<LA, P2<T>, PreCD<T>, PreVD<T>>(sp_d, d.a_ptr, d.a_col, d.a_thresh, val, term,
+                                                   pref_c, pref_v, fin, [] { return true; });
       rows_long<P2<T>>(sp_dl, d.a_ptr, load, epi);
       const T s0 = block_sum1<T>(dy2);
       const T s1 = block_sum1<T>(dkd);
