@@ -67,6 +67,26 @@ reading is marked "reading" where it is used below:
       passing.  The primal test is taken first.  The certificate is returned
       in place of the dual (primal infeasible) or primal (dual infeasible)
       output.
+  A14 optional reflected restarted Halpern PDHG (one of the algorithmic
+      variants of PDLP; off by default; every detail is a reading, the paper
+      runs PDLP as a black box): a constant step eta = 0.998 / L, where L is
+      the power-iteration estimate of ||K~||_2 (64 passes of
+      v <- K~^T K~ v / ||K~^T K~ v|| from v = 1/sqrt(n), L = the square root of
+      the last norm); no step-size search and no averages.  Each step maps the
+      Halpern iterate z^k = (x^k, y^k) through the PDHG operator T (A4/A5 with
+      tau = eta/omega, sigma = eta*omega) and mixes
+        z^{k+1} = (k+1)/(k+2) ((1+rho) T(z^k) - rho z^k) + 1/(k+2) z^a,
+      rho the reflection coefficient (1: reflected), z^a the anchor (the start,
+      then the last restart point), k the steps since the last restart.  The
+      candidate the checks (A8, A11, A12) evaluate and the solver returns is
+      the latest T(z^k).  Restarts compare the fixed-point residual of the
+      latest step, r = ||z^k - T(z^k)||_P with ||(dx, dy)||_P^2 =
+      (omega/eta) ||dx||^2 + ||dy||^2 / (omega eta) - 2 dy^T K~ dx, with r_0,
+      the residual of the epoch's first step, by the beta_suff / beta_nec /
+      beta_art rules of A9 (r in place of KKT_omega; "no progress" = r above
+      the previous check's r); a restart takes the candidate as the new
+      anchor and iterate (k = 0) after the A10 primal-weight update from the
+      candidate's scaled distance to the previous anchor.
   A13 primal feasibility polishing (``polish_primal``): the same iteration on
       the LP with its objective replaced by 0, from (x, 0).  Dual feasibility
       polishing (``polish_dual``): the same iteration on the LP with b = 0 and
@@ -227,6 +247,10 @@ class Params:
     fixed_eta: float | None = None  # overrides eta0 (fixed-step mode)
     fixed_omega: float | None = None  # overrides omega0
     bound_objective_rescaling: bool = False  # A2b
+    halpern: bool = False           # A14: reflected restarted Halpern PDHG
+    halpern_reflection: float = 1.0  # A14: rho
+    halpern_eta_scale: float = 0.998  # A14: eta = scale / L
+    power_iters: int = 64           # A14: passes of the power iteration for L
     terminate: bool = True          # stop at tol (False: run to iter_limit)
     beta_suff: float = 0.2
     beta_nec: float = 0.8
@@ -264,6 +288,9 @@ class Result:
     check_trace: list = field(default_factory=list)    # (restart kind, omega after) per check
     rays: list = field(default_factory=list)           # Rays of every check (A12)
     check_points: list = field(default_factory=list)   # unscaled current x of the last checks
+    x_halpern: np.ndarray | None = None  # A14: the Halpern iterate z^k, unscaled (not clipped)
+    y_halpern: np.ndarray | None = None
+    spectral_norm: float | None = None   # A14: L, the estimate of ||K~||_2
 
 
 @dataclass
@@ -285,6 +312,25 @@ class Rays:
     def dual_infeasible(self, eps, kappa=1e-9):
         p = -self.primal_ray_obj
         return p > 0 and p > kappa * self.primal_ray_abs and self.primal_ray_res <= eps * p
+
+
+def power_norm(kt, iters=64) -> float:
+    """A14: L = sqrt(||K~^T K~ v||) after ``iters`` passes of the power iteration
+    v <- K~^T K~ v / ||K~^T K~ v|| from v = 1/sqrt(n) (0 for an empty K~ or when a
+    pass gives the zero vector).  For a unit v, ||K~^T K~ v|| <= ||K~||_2^2, so L
+    never exceeds ||K~||_2."""
+    n = kt.shape[1]
+    if n == 0 or kt.nnz == 0:
+        return 0.0
+    v = np.full(n, 1.0 / math.sqrt(n))
+    s = 0.0
+    for _ in range(iters):
+        w = kt.T @ (kt @ v)
+        s = float(np.linalg.norm(w))
+        if s == 0.0:
+            return 0.0
+        v = w / s
+    return math.sqrt(s)
 
 
 def recession_proj(dx, l, u):
@@ -357,6 +403,11 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
             omega = nyh / nxh
     kmax = float(abs(kt).max()) if kt.nnz else 0.0
     eta = 1.0 / kmax if kmax > 0 else 1.0
+    spectral = None
+    if p.halpern:
+        # A14: a constant step from the power-iteration estimate of ||K~||_2
+        spectral = power_norm(kt, p.power_iters)
+        eta = p.halpern_eta_scale / spectral if spectral > 0 else 1.0
     if p.fixed_eta is not None:
         eta = p.fixed_eta
     if p.fixed_omega is not None:
@@ -398,41 +449,71 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
     def unscaled_point(xs, ys):
         return proj_box(dc * xs, lp.l, lp.u), dr * ys
 
+    # A14 state: the Halpern iterate, its anchor, the steps since the last restart,
+    # the residuals of the epoch's first step, of the latest step and of the last check
+    xh, yh = x.copy(), y.copy()
+    xa0, ya0 = x.copy(), y.copy()
+    h_k = 0
+    h_r0 = h_res = h_prev = math.inf
+
     while it < p.iter_limit:
         attempts += 1
-        if p.replay_eta is not None:
-            eta = float(p.replay_eta[attempts - 1])
-        # A4: primal step
-        x_new = proj_box(x - (eta / omega) * (ct - ktt @ y), lt, ut)
-        # A5: dual step with extrapolation 2x' - x
-        y_new = proj_dual(y + eta * omega * (qt - kt @ (2.0 * x_new - x)), is_eq)
-        eta_used = eta
-        # A6: the step-size bound of this attempt
-        dx = x_new - x
-        dy = y_new - y
-        denom = 2.0 * abs(float(dy @ (kt @ dx)))
-        num = omega * float(dx @ dx) + float(dy @ dy) / omega
-        eta_bar = num / denom if denom > 0 else math.inf
-        accept = True
-        if p.adaptive:
-            eta_next = min((1.0 - (attempts + 1) ** -0.3) * eta_bar,
-                           (1.0 + (attempts + 1) ** -0.6) * eta)
-            accept = not (eta > eta_bar)
-        if p.replay_accepted is not None:
-            accept = bool(p.replay_accepted[attempts - 1])
-        attempt_trace.append((eta_used, eta_bar, accept))
-        if not accept:
-            trace.append(("reject", attempts, eta, eta_bar))
-            eta = eta_next
-            continue
-        if p.adaptive:
-            eta = eta_next
-        # accept; A7 running sums weighted by the step that produced the iterate
-        x, y = x_new, y_new
-        sum_x += eta_used * x
-        sum_y += eta_used * y
-        sum_w += eta_used
-        it += 1
+        if p.halpern:
+            # A14: the PDHG operator at the Halpern iterate (A4, A5 with the constant step)
+            x_new = proj_box(xh - (eta / omega) * (ct - ktt @ yh), lt, ut)
+            y_new = proj_dual(yh + eta * omega * (qt - kt @ (2.0 * x_new - xh)), is_eq)
+            dx = x_new - xh
+            dy = y_new - yh
+            # fixed-point residual ||z^k - T(z^k)||_P
+            r2 = (omega / eta * float(dx @ dx) + float(dy @ dy) / (omega * eta)
+                  - 2.0 * float(dy @ (kt @ dx)))
+            h_res = math.sqrt(max(r2, 0.0))
+            if h_k == 0:
+                h_r0 = h_res
+            # the reflected Halpern mix with the anchor
+            lam = (h_k + 1.0) / (h_k + 2.0)
+            rho = p.halpern_reflection
+            xh = lam * ((1.0 + rho) * x_new - rho * xh) + (1.0 - lam) * xa0
+            yh = lam * ((1.0 + rho) * y_new - rho * yh) + (1.0 - lam) * ya0
+            h_k += 1
+            attempt_trace.append((eta, h_res, True))
+            # the candidate: no averages (sum_w stays 0, so average() is the candidate)
+            x, y = x_new, y_new
+            it += 1
+        else:
+            if p.replay_eta is not None:
+                eta = float(p.replay_eta[attempts - 1])
+            # A4: primal step
+            x_new = proj_box(x - (eta / omega) * (ct - ktt @ y), lt, ut)
+            # A5: dual step with extrapolation 2x' - x
+            y_new = proj_dual(y + eta * omega * (qt - kt @ (2.0 * x_new - x)), is_eq)
+            eta_used = eta
+            # A6: the step-size bound of this attempt
+            dx = x_new - x
+            dy = y_new - y
+            denom = 2.0 * abs(float(dy @ (kt @ dx)))
+            num = omega * float(dx @ dx) + float(dy @ dy) / omega
+            eta_bar = num / denom if denom > 0 else math.inf
+            accept = True
+            if p.adaptive:
+                eta_next = min((1.0 - (attempts + 1) ** -0.3) * eta_bar,
+                               (1.0 + (attempts + 1) ** -0.6) * eta)
+                accept = not (eta > eta_bar)
+            if p.replay_accepted is not None:
+                accept = bool(p.replay_accepted[attempts - 1])
+            attempt_trace.append((eta_used, eta_bar, accept))
+            if not accept:
+                trace.append(("reject", attempts, eta, eta_bar))
+                eta = eta_next
+                continue
+            if p.adaptive:
+                eta = eta_next
+            # accept; A7 running sums weighted by the step that produced the iterate
+            x, y = x_new, y_new
+            sum_x += eta_used * x
+            sum_y += eta_used * y
+            sum_w += eta_used
+            it += 1
         last = it >= p.iter_limit
         if it % p.check_period == 0 or last:
             # A8
@@ -473,7 +554,30 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                 check_trace.append((0, omega))
                 break
             kind = 0
-            if p.restarts:
+            if p.restarts and p.halpern:
+                # A14: the A9 rules on the fixed-point residual
+                do_restart = (h_res <= p.beta_suff * h_r0
+                              or (h_res <= p.beta_nec * h_r0 and h_res > h_prev)
+                              or (it - last_restart_it) >= p.beta_art * it)
+                if do_restart:
+                    # A10 from the candidate's distance to the previous anchor
+                    ddx = float(np.linalg.norm(x - x_last))
+                    ddy = float(np.linalg.norm(y - y_last))
+                    if ddx > 1e-10 and ddy > 1e-10:
+                        omega = math.exp(p.omega_smooth * math.log(ddy / ddx)
+                                         + (1.0 - p.omega_smooth) * math.log(omega))
+                    x_last, y_last = x.copy(), y.copy()
+                    xh, yh = x.copy(), y.copy()
+                    xa0, ya0 = x.copy(), y.copy()
+                    h_k = 0
+                    h_prev = math.inf
+                    last_restart_it = it
+                    restarts += 1
+                    kind = 1
+                    trace.append(("restart", it, False, omega))
+                else:
+                    h_prev = h_res
+            elif p.restarts:
                 # A9
                 sc = scaled_kkt(x, y)
                 sa = scaled_kkt(xa, ya)
@@ -531,7 +635,9 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                   x_out, y_out, chosen_kkt,
                   unscale_x(x), unscale_y(y), unscale_x(xa), unscale_y(ya),
                   eta, omega, chosen_avg, time.perf_counter() - t0, trace, attempt_trace,
-                  check_trace, rays, check_points)
+                  check_trace, rays, check_points,
+                  dc * xh if p.halpern else None,
+                  s * (dr * yh) if p.halpern else None, spectral)
 
 
 # ---------------------------------------------------------------- A13 ------

@@ -95,6 +95,24 @@ MUTANTS = [
      ["test_bound_objective_rescaling_one_step_by_hand"]),
     ("objective rescaled by beta", "ct = ct / gamma", "ct = ct / beta",
      ["test_bound_objective_rescaling_one_step_by_hand"]),
+    ("Halpern weight k/(k+1) instead of (k+1)/(k+2)", "lam = (h_k + 1.0) / (h_k + 2.0)",
+     "lam = (h_k + 0.0) / (h_k + 1.0)", ["test_halpern_steps_by_hand"]),
+    ("Halpern reflection added instead of subtracted", "- rho * yh", "+ rho * yh",
+     ["test_halpern_steps_by_hand"]),
+    ("Halpern anchor kept at a restart",
+     "xa0, ya0 = x.copy(), y.copy()\n                    h_k = 0", "h_k = 0",
+     ["test_halpern_sufficient_decay_restart_by_hand"]),
+    ("fixed-point residual with the cross term's sign flipped",
+     "- 2.0 * float(dy @ (kt @ dx)))", "+ 2.0 * float(dy @ (kt @ dx)))",
+     ["test_halpern_steps_by_hand"]),
+    ("power iteration on K~ instead of K~^T K~", "w = kt.T @ (kt @ v)", "w = kt @ v",
+     ["test_power_iteration_closed_forms"]),
+    ("epoch residual r_0 replaced at every step",
+     "if h_k == 0:\n                h_r0 = h_res", "h_r0 = h_res",
+     ["test_halpern_necessary_decay_restart_by_hand"]),
+    ("Halpern candidate taken at the mixed iterate instead of T(z)",
+     "x, y = x_new, y_new\n            it += 1", "x, y = xh.copy(), yh.copy()\n            it += 1",
+     ["test_halpern_steps_by_hand"]),
 ]
 
 

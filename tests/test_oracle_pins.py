@@ -552,3 +552,133 @@ def test_bound_objective_rescaling_with_restarts_reaches_the_optimum():
     assert r.status == O.STATUS_OPTIMAL and r.kkt.rel_kkt <= 1e-6
     obj, _, _, _ = R.highs(lp)
     assert abs(float(lp.c @ r.x) - obj) / (1 + abs(obj)) <= 1e-5
+
+
+# ---------------------------------------------------------------- A14 Halpern
+def _one_by_one():
+    # min x  s.t.  x >= 1,  0 <= x (optimum x* = 1, y* = 1)
+    return _lp_from_dense([[1.0]], [1.0], "G", [1.0], [0.0], [np.inf])
+
+
+HALP = dict(ruiz_iters=0, pc_alpha=None, halpern=True, fixed_eta=0.5, fixed_omega=1.0,
+            terminate=False)
+
+
+def test_halpern_steps_by_hand():
+    """Four reflected Halpern steps (rho = 1) on min x, x >= 1, eta = 0.5, omega = 1
+    (tau = sigma = 0.5), from z^0 = (0, 0) = the anchor:
+      k=0: T = (max(0 - 0.5*1, 0), 0 + 0.5*(1 - 0)) = (0, 0.5);  z1 = 1/2 (2T - z0) + 1/2 z0 = (0, 0.5)
+      k=1: T = (max(0 - 0.5*0.5, 0), 0.5 + 0.5) = (0, 1);         z2 = 2/3 (0, 1.5) = (0, 1)
+      k=2: T = (0, 1.5);                                           z3 = 3/4 (0, 2) = (0, 1.5)
+      k=3: T = (0 + 0.5*0.5, 1.5 + 0.5*(1 - 0.5)) = (0.25, 1.75); z4 = 4/5 (0.5, 2) = (0.4, 1.6)
+    Residuals ||z - T(z)||_P^2 = 2 dx^2 + 2 dy^2 - 2 dy dx: 0.5, 0.5, 0.5, then
+    2/16 + 2/16 - 2/16 = 0.125."""
+    r = O.solve(_one_by_one(), O.Params(iter_limit=4, restarts=False, **HALP))
+    assert r.iters == 4 and r.attempts == 4
+    np.testing.assert_allclose(r.x_cur, [0.25], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r.y_cur, [1.75], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r.x_halpern, [0.4], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r.y_halpern, [1.6], rtol=0, atol=1e-15)
+    np.testing.assert_allclose([t[1] for t in r.attempt_trace],
+                               [math.sqrt(0.5)] * 3 + [math.sqrt(0.125)], rtol=1e-15)
+    # no averages: the average candidate is the latest T(z^k)
+    np.testing.assert_allclose(r.x_avg, r.x_cur, rtol=0, atol=0)
+
+
+def test_plain_halpern_steps_by_hand():
+    """rho = 0 (no reflection) on the same LP: z1 = 1/2 T(z0) = (0, 0.25);
+    T(z1) = (max(0 - 0.5*(1 - 0.25), 0), 0.25 + 0.5) = (0, 0.75), z2 = 2/3 (0, 0.75) = (0, 0.5)."""
+    r = O.solve(_one_by_one(), O.Params(iter_limit=2, restarts=False, halpern_reflection=0.0,
+                                        **HALP))
+    np.testing.assert_allclose(r.y_cur, [0.75], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r.y_halpern, [0.5], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r.x_halpern, [0.0], rtol=0, atol=1e-15)
+
+
+def test_halpern_necessary_decay_restart_by_hand():
+    """Checks after every step, the artificial rule out of reach (beta_art = 10).
+    Residuals of the steps above: r = 0.7071 (r_0), 0.7071, 0.7071, 0.3536; step 5 from
+    z4 = (0.4, 1.6): T = (0.4 + 0.5*0.6, 1.6 + 0.5*(1 - 1.0)) = (0.7, 1.6), r^2 = 2*0.09 = 0.18,
+    r = 0.4243 <= 0.8 r_0 and above the previous check's 0.3536: a restart to (0.7, 1.6), with
+    omega = exp(0.5 ln(1.6 / 0.7)) (distances from the anchor (0, 0)).  The sixth check is the
+    iteration limit."""
+    r = O.solve(_one_by_one(), O.Params(iter_limit=6, check_period=1, beta_art=10.0, **HALP))
+    kinds = [k for k, _ in r.check_trace]
+    assert kinds == [0, 0, 0, 0, 1, 0] and r.restarts == 1
+    assert r.check_trace[4][1] == pytest.approx(math.sqrt(1.6 / 0.7), rel=1e-14)
+
+
+def test_halpern_sufficient_decay_restart_by_hand():
+    """beta_suff = 0.6: step 4's r = 0.3536 <= 0.6 * 0.7071 restarts to T(z3) = (0.25, 1.75);
+    omega = exp(0.5 ln(1.75 / 0.25)) = sqrt(7).  Then, from the new anchor with
+    tau = 0.5/sqrt(7), sigma = 0.5 sqrt(7), the first step of the epoch sets r_0 afresh."""
+    r = O.solve(_one_by_one(), O.Params(iter_limit=5, check_period=1, beta_art=10.0,
+                                        beta_suff=0.6, **HALP))
+    assert [k for k, _ in r.check_trace][:4] == [0, 0, 0, 1]
+    assert r.check_trace[3][1] == pytest.approx(math.sqrt(7.0), rel=1e-14)
+    # step 5 starts from the anchor (0.25, 1.75): x' = 0.25 + tau*0.75, and with k = 0
+    # z5 = 1/2 (2 T - z) + 1/2 z = T
+    tau = 0.5 / math.sqrt(7.0)
+    sigma = 0.5 * math.sqrt(7.0)
+    xt = 0.25 + tau * 0.75
+    yt = 1.75 + sigma * (1.0 - (2.0 * xt - 0.25))
+    np.testing.assert_allclose(r.x_cur, [xt], rtol=1e-14)
+    np.testing.assert_allclose(r.y_cur, [yt], rtol=1e-14)
+    np.testing.assert_allclose(r.x_halpern, [xt], rtol=1e-14)
+    np.testing.assert_allclose(r.y_halpern, [yt], rtol=1e-14)
+
+
+def test_halpern_first_check_restarts_artificially():
+    """check_period 2: at the first check (iteration 2) 2 - 0 >= 0.36 * 2 restarts to
+    T(z1) = (0, 1) with omega unchanged (no primal distance); at iteration 4 the
+    artificial rule (4 - 2 >= 1.44) restarts again, to T(z'1) where the epoch's first step
+    T(0, 1) = (0, 1.5) and z'1 = 1/2 (2 (0, 1.5) - (0, 1)) + 1/2 (0, 1) = (0, 1.5), then
+    T(z'1) = (0.25, 1.75): omega = exp(0.5 ln(0.75 / 0.25)) = sqrt(3)."""
+    r = O.solve(_one_by_one(), O.Params(iter_limit=6, check_period=2, **HALP))
+    assert [k for k, _ in r.check_trace] == [1, 1, 0]
+    assert r.check_trace[0][1] == 1.0
+    assert r.check_trace[1][1] == pytest.approx(math.sqrt(3.0), rel=1e-14)
+
+
+def _diag_lp(d):
+    n = len(d)
+    return _lp_from_dense(np.diag(d), np.ones(n), "G" * n, np.ones(n), np.zeros(n),
+                          np.full(n, np.inf))
+
+
+def test_power_iteration_closed_forms():
+    """||diag(2, 1)||_2 = 2 and ||u v^T||_2 = ||u|| ||v|| (rank one: exact after one
+    pass); the power estimate never exceeds the true norm (LAPACK's 2-norm as the
+    independent check) and the Halpern step is 0.998 / L."""
+    import scipy.sparse as sps
+    assert O.power_norm(sps.csr_matrix(np.diag([2.0, 1.0]))) == pytest.approx(2.0, rel=1e-14)
+    u = np.array([1.0, 2.0, 2.0])
+    v = np.array([3.0, 4.0])
+    assert O.power_norm(sps.csr_matrix(np.outer(u, v))) == pytest.approx(15.0, rel=1e-14)
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        a = sps.random(30, 20, density=0.2, random_state=rng, format="csr")
+        true = np.linalg.norm(a.toarray(), 2)
+        est = O.power_norm(a)
+        assert est <= true * (1 + 1e-12) and est >= 0.9 * true
+    r = O.solve(_diag_lp([2.0, 1.0]), O.Params(iter_limit=1, ruiz_iters=0, pc_alpha=None,
+                                               halpern=True, terminate=False))
+    assert r.spectral_norm == pytest.approx(2.0, rel=1e-14)
+    assert r.eta == pytest.approx(0.998 / 2.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_halpern_tiny_lp_matches_vertex_enumeration(seed):
+    lp = lpgen.tiny_lp(seed, m=5 + seed % 2, n=4 + seed % 2, eq_rows=seed % 2)
+    best, _ = R.vertex_enumeration(lp)
+    r = O.solve(lp, O.Params(tol=1e-9, iter_limit=400_000, halpern=True))
+    assert r.status == O.STATUS_OPTIMAL
+    assert r.kkt.primal_obj == pytest.approx(best, rel=1e-6, abs=1e-6)
+
+
+def test_halpern_mip_relaxation_matches_highs():
+    lp = lpgen.mip_relaxation(2)
+    obj, _, _, _ = R.highs(lp)
+    r = O.solve(lp, O.Params(tol=1e-8, halpern=True))
+    assert r.status == O.STATUS_OPTIMAL
+    assert abs(r.kkt.primal_obj - obj) / (1 + abs(obj)) < 1e-7
