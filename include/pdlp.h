@@ -184,6 +184,24 @@ typedef struct {
                            omega' = omega beta / gamma); the restart metric then weighs its
                            gap term by 1 / (beta gamma).  0 (default): off.  Single LPs
                            only: a batch with 1 is rejected. */
+  int halpern;          /* 1: reflected restarted Halpern PDHG (one of PDLP's algorithmic
+                           variants; the paper is silent): a constant step
+                           eta = 0.998 / L, L the power-iteration estimate of ||K~||_2
+                           (64 passes of v <- K~^T K~ v / ||K~^T K~ v|| from
+                           v = 1/sqrt(n); fixed_eta > 0 overrides); each step maps the
+                           Halpern iterate z through the PDHG operator T and takes
+                           z' = (k+1)/(k+2) ((1+rho) T(z) - rho z) + 1/(k+2) z_a, z_a the
+                           anchor (the start, then the last restart point), k the steps
+                           since the last restart; no averages; the checks evaluate and
+                           the solver returns the latest T(z); restarts apply the KKT
+                           restart thresholds (0.2, 0.8, 0.36) to the fixed-point residual
+                           ||z - T(z)||_P against the epoch's first, and move the anchor
+                           and the iterate to T(z).  The decision trace records the
+                           residual in place of eta_bar.  0 (default): off.  Single LPs
+                           with persistent = 0 and tiles = 0 only; adaptive_step is
+                           ignored. */
+  double halpern_reflection; /* rho of the Halpern variant, in [0, 1]: 1 (default)
+                           reflected, 0 plain Halpern */
 } pdlp_params;
 
 typedef struct {
@@ -215,6 +233,8 @@ typedef struct {
                              the LP held in shared memory (persistent = 2 when the matrix,
                              vectors and iterates fit: 76 KB for a 200 x 400 relaxation
                              with 1,600 nonzeros in float64) */
+  double spectral_norm;   /* halpern = 1: L, the power-iteration estimate of ||K~||_2 the
+                             step size came from; 0 otherwise */
 } pdlp_result;
 
 /* Optional diagnostic outputs (same memory space as the entry point's outputs;

@@ -42,7 +42,8 @@ class PdlpParams(C.Structure):
                 ("lanes_kkt_A", C.c_int), ("lanes_kkt_AT", C.c_int), ("verbose", C.c_int),
                 ("persistent", C.c_int), ("autotune", C.c_int),
                 ("detect_infeasibility", C.c_int), ("debug_skip_barrier", C.c_int),
-                ("tiles", C.c_int), ("bound_objective_rescaling", C.c_int)]
+                ("tiles", C.c_int), ("bound_objective_rescaling", C.c_int),
+                ("halpern", C.c_int), ("halpern_reflection", C.c_double)]
 
 
 class PdlpResult(C.Structure):
@@ -54,7 +55,8 @@ class PdlpResult(C.Structure):
                 ("eta", C.c_double), ("omega", C.c_double), ("used_average", C.c_int),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("lanes_A", C.c_int),
                 ("lanes_AT", C.c_int), ("ray_obj", C.c_double), ("ray_res", C.c_double),
-                ("tiles", C.c_int), ("upload_s", C.c_double), ("persistent_form", C.c_int)]
+                ("tiles", C.c_int), ("upload_s", C.c_double), ("persistent_form", C.c_int),
+                ("spectral_norm", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

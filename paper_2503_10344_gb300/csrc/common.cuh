@@ -102,7 +102,35 @@ struct DevState {
   int bar_err;
   int bar_skip;          // fault-handling tests: block 0 skips its barrier arrivals
   long long spin_limit;  // polls of one barrier wait before it gives up
+  // reflected restarted Halpern PDHG (halpern = 1; pdlp_params.halpern): a step maps the
+  // Halpern iterate z through the PDHG operator T and mixes z' = ha T(z) + hb z + hc z_a
+  // (z_a the anchor); the coefficients of the next step in both precisions, the steps
+  // since the last restart (h_k), the reflection rho, the fixed-point residuals of the
+  // latest step and of the epoch's first step (prev_cand holds the last check's)
+  int halpern, h_pad;
+  long long h_k;
+  double h_rho, h_res, h_r0;
+  double ha_d, hb_d, hc_d;
+  float ha_f, hb_f, hc_f, hf_pad;
 };
+
+// Halpern variant: passes of the power iteration for ||K~||_2 and the step size's
+// fraction of 1 / ||K~||_2
+constexpr int kPowerIters = 64;
+constexpr double kHalpernEtaScale = 0.998;
+
+// Halpern coefficients of step k = h_k since the last restart:
+// lambda = (k + 1) / (k + 2), ha = lambda (1 + rho), hb = -lambda rho, hc = 1 - lambda
+__host__ __device__ inline void halpern_coeffs(DevState* st) {
+  const double k = (double)st->h_k;
+  const double lam = (k + 1.0) / (k + 2.0);
+  st->ha_d = lam * (1.0 + st->h_rho);
+  st->hb_d = -lam * st->h_rho;
+  st->hc_d = 1.0 - lam;
+  st->ha_f = (float)st->ha_d;
+  st->hb_f = (float)st->hb_d;
+  st->hc_f = (float)st->hc_d;
+}
 
 // status value of a persistent step kernel whose bounded barrier wait gave up
 constexpr int kStatusWaitFailed = 99;

@@ -88,6 +88,9 @@ struct IterRaw {
   // that much shared memory; 0 runs the one-block k_persist from global memory
   SmemLayout smem;
   const int *ord_t, *ord_a;  // its order of the columns and rows (longest first)
+  // Halpern variant (pdlp_params.halpern): its iterate and anchor (iterate type; NULL off)
+  void *hx, *hy;
+  const void *hax, *hay;
 };
 
 // IK_DUAL launches the dual step kernel and then the step decision (k_decide)
@@ -112,6 +115,11 @@ cudaError_t launch_iter_fp64(int which, int lanes, const IterRaw& r, cudaStream_
 cudaError_t launch_iter_fp32(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_bf16(int which, int lanes, const IterRaw& r, cudaStream_t s);
 cudaError_t launch_iter_pat(int which, int lanes, const IterRaw& r, cudaStream_t s);
+// the Halpern variant's step kernels (two launches per attempt only)
+cudaError_t launch_iter_fp64_h(int which, int lanes, const IterRaw& r, cudaStream_t s);
+cudaError_t launch_iter_fp32_h(int which, int lanes, const IterRaw& r, cudaStream_t s);
+cudaError_t launch_iter_bf16_h(int which, int lanes, const IterRaw& r, cudaStream_t s);
+cudaError_t launch_iter_pat_h(int which, int lanes, const IterRaw& r, cudaStream_t s);
 
 struct KktRaw {
   const int *a_ptr, *a_col;
@@ -134,6 +142,9 @@ struct KktRaw {
   double2 *XG, *YG;
   double *XR, *YR;
   double *Xl, *Yl;  // unscaled restart anchors
+  // Halpern variant: its iterate and anchor (iterate type), reset to the candidate at a
+  // restart (NULL off)
+  void *hx, *hy, *hax, *hay;
   double* chk_pts;  // [chk_cap x n] current point of the last checks (NULL: not kept)
   long long chk_cap;
   double *part_r, *part_c;                 // kPartR / kPartC partial rows of grid_r / grid_c

@@ -55,11 +55,17 @@ template <> struct StepT<float> {
   static __device__ __forceinline__ float tau(const DevState* s) { return s->tau_f; }
   static __device__ __forceinline__ float sigma(const DevState* s) { return s->sigma_f; }
   static __device__ __forceinline__ float pw(const DevState* s) { return s->pw_f; }
+  static __device__ __forceinline__ float ha(const DevState* s) { return s->ha_f; }
+  static __device__ __forceinline__ float hb(const DevState* s) { return s->hb_f; }
+  static __device__ __forceinline__ float hc(const DevState* s) { return s->hc_f; }
 };
 template <> struct StepT<double> {
   static __device__ __forceinline__ double tau(const DevState* s) { return s->tau_d; }
   static __device__ __forceinline__ double sigma(const DevState* s) { return s->sigma_d; }
   static __device__ __forceinline__ double pw(const DevState* s) { return s->pending_w; }
+  static __device__ __forceinline__ double ha(const DevState* s) { return s->ha_d; }
+  static __device__ __forceinline__ double hb(const DevState* s) { return s->hb_d; }
+  static __device__ __forceinline__ double hc(const DevState* s) { return s->hc_d; }
 };
 
 template <typename T, typename V>
@@ -87,6 +93,9 @@ struct IterData {
   TileSet tt, ta;                                      // their items over A^T and A
   int grid_tt, grid_ta, work_tt, work_ta, tslot;
   const int *ord_t, *ord_a;                            // one-block kernel: rows longest first
+  // Halpern variant (H kernels): the iterate z = (hx, hy) the step starts from, updated in
+  // place by the row's owner, and the anchor (hax, hay)
+  T* hx; T* hy; const T* hax; const T* hay;
 };
 
 // Rows of one LP (span), one aligned group of LANES lanes per row, rows
@@ -363,7 +372,12 @@ struct PreVD {  // dual row i: y_i, running sum
 // (weak, L1-cacheable) loads after the dependent-launch wait, whose guarantee
 // covers them; never through the non-coherent read-only path (__ldg), which
 // assumes data that no grid in flight writes.
-template <int LANES, typename T, typename V, bool IMPLICIT>
+//
+// H (the Halpern variant, pdlp_params.halpern): the step starts from the Halpern iterate
+// (hx, hy) instead of the current buffers, writes T(z) as usual (the (x', dx) pairs and
+// y' in the next buffers: the candidate the checks evaluate), and each row's owner
+// replaces its entry of the Halpern iterate by ha T(z) + hb z + hc z_a; no averages.
+template <int LANES, typename T, typename V, bool IMPLICIT, bool H = false>
 __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_primal(IterData<T, V> d) {
   constexpr bool TILED = std::is_same<T, double>::value;
   const Span sp = make_span(d.tp, d.n, d.grid_p_short, d.t_long, d.t_nlong);
@@ -371,16 +385,22 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_primal(IterData<T
   const vec2_t<T>* x = nullptr;
   vec2_t<T>* xn = nullptr;
   const T* y = nullptr;
-  T tau = 0, pw = 0;
+  T tau = 0, pw = 0, ha = 0, hb = 0, hc = 0;
   auto enter = [&]() -> bool {
     pdl_enter();
     if (st->status != 0 || st->check_due) return false;
     const int cur = st->cur;
     x = cur ? d.x[1] : d.x[0];
     xn = cur ? d.x[0] : d.x[1];
-    y = cur ? d.y[1] : d.y[0];
+    y = H ? d.hy : cur ? d.y[1] : d.y[0];
     tau = StepT<T>::tau(st);
-    pw = StepT<T>::pw(st);
+    if constexpr (H) {
+      ha = StepT<T>::ha(st);
+      hb = StepT<T>::hb(st);
+      hc = StepT<T>::hc(st);
+    } else {
+      pw = StepT<T>::pw(st);
+    }
     return true;
   };
   T dx2 = 0;
@@ -391,6 +411,7 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_primal(IterData<T
     return PreCP<T>{__ldg(d.c + j), __ldg(d.l + j), __ldg(d.u + j), IMPLICIT ? __ldg(d.tw + j) : (T)1};
   };
   auto pref_v = [&](int j) -> PreVP<T> {
+    if constexpr (H) return PreVP<T>{d.hx[j], d.hax[j]};  // the iterate and its anchor
     return PreVP<T>{x[j].x, pw != (T)0 ? d.sum_x[j] : (T)0};
   };
   auto fin = [&](int j, T aty, const PreCP<T>& c, const PreVP<T>& v) {
@@ -402,7 +423,10 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_primal(IterData<T
     o.x = xv;
     o.y = dd;
     xn[j] = o;
-    if (pw != (T)0) d.sum_x[j] = v.sx + pw * v.xo;  // A7: add the iterate whose weight is pending
+    if constexpr (H)
+      d.hx[j] = ha * xv + hb * v.xo + hc * v.sx;  // the reflected Halpern mix
+    else if (pw != (T)0)
+      d.sum_x[j] = v.sx + pw * v.xo;  // A7: add the iterate whose weight is pending
     dx2 += IMPLICIT ? dd * dd / c.tw : dd * dd;
   };
   auto epi = [&](int j, T aty) { fin(j, aty, pref_c(j), pref_v(j)); };
@@ -499,6 +523,40 @@ __device__ __forceinline__ void decide_step(DevState* st, T dx2, T dy2, T dkd, T
   }
 }
 
+// The Halpern variant's decision: every step is taken at the constant step size; the
+// fixed-point residual r = ||z - T(z)||_P of this step, ||(dx, dy)||_P^2 =
+// (omega / eta) ||dx||^2 + ||dy||^2 / (omega eta) - 2 dy^T K dx (scaled norms), is
+// recorded for the restart rules (the epoch's first step also sets r_0) and in the
+// decision trace (as eta_bar); then the Halpern coefficients of the next step.
+template <typename T>
+__device__ __forceinline__ void decide_halpern(DevState* st, T dx2, T dy2, T dkd) {
+  constexpr bool F64 = std::is_same<T, double>::value;
+  st->attempts += 1;
+  if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(dkd)) {
+    st->status = 4;  // PDLP_NUMERICAL
+    return;
+  }
+  const T eta = F64 ? (T)st->eta : (T)st->eta_f;
+  const T om = F64 ? (T)st->omega : (T)st->omega_f;
+  const T iom = F64 ? (T)st->inv_omega : (T)st->inv_omega_f;
+  const T r2 = F64 ? om / eta * dx2 + dy2 / (om * eta) - (T)2 * dkd
+                   : (om * dx2 + dy2 * iom) / eta - (T)2 * dkd;
+  const double r = sqrt(fmax((double)r2, 0.0));
+  st->h_res = r;
+  if (st->h_k == 0) st->h_r0 = r;
+  const long long t = st->attempts - 1;
+  if (t < st->tr_cap) {
+    st->tr_eta[t] = (double)eta;
+    st->tr_eta_bar[t] = r;
+    st->tr_accepted[t] = 1;
+  }
+  st->cur ^= 1;  // the current buffers hold T(z): the candidate of the checks
+  st->iters += 1;
+  if (st->iters % st->period == 0 || st->iters >= st->iter_limit) st->check_due = 1;
+  st->h_k += 1;
+  halpern_coeffs(st);
+}
+
 // fields of the state a step decision changes (the barrier words are not copied)
 __device__ __forceinline__ void store_step_state(DevState* g, const DevState& l) {
   g->status = l.status;
@@ -515,10 +573,19 @@ __device__ __forceinline__ void store_step_state(DevState* g, const DevState& l)
   g->sigma_f = l.sigma_f;
   g->pw_f = l.pw_f;
   g->eta_f = l.eta_f;
+  g->h_k = l.h_k;
+  g->h_res = l.h_res;
+  g->h_r0 = l.h_r0;
+  g->ha_d = l.ha_d;
+  g->hb_d = l.hb_d;
+  g->hc_d = l.hc_d;
+  g->ha_f = l.ha_f;
+  g->hb_f = l.hb_f;
+  g->hc_f = l.hc_f;
 }
 
 // ---------------------------------------------------------------- A5 + A6: dual
-template <int LANES, typename T, typename V, bool IMPLICIT>
+template <int LANES, typename T, typename V, bool IMPLICIT, bool H = false>
 __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, V> d) {
   constexpr bool TILED = std::is_same<T, double>::value;
   const Span sp = make_span(d.td, d.m, d.grid_d_short, d.a_long, d.a_nlong);
@@ -526,7 +593,7 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
   const vec2_t<T>* xn = nullptr;
   const T* y = nullptr;
   T* yn = nullptr;
-  T sigma = 0, pw = 0;
+  T sigma = 0, pw = 0, ha = 0, hb = 0, hc = 0;
   auto enter = [&]() -> bool {
     pdl_enter();
     if (st->status != 0 || st->check_due) return false;
@@ -535,7 +602,13 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
     y = cur ? d.y[1] : d.y[0];
     yn = cur ? d.y[0] : d.y[1];
     sigma = StepT<T>::sigma(st);
-    pw = StepT<T>::pw(st);
+    if constexpr (H) {
+      ha = StepT<T>::ha(st);
+      hb = StepT<T>::hb(st);
+      hc = StepT<T>::hc(st);
+    } else {
+      pw = StepT<T>::pw(st);
+    }
     return true;
   };
   T dy2 = 0, dkd = 0;
@@ -550,6 +623,7 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
     return PreCD<T>{__ldg(d.q + i), IMPLICIT ? __ldg(d.sw + i) : (T)1, (int)__ldg(d.row_kind + i)};
   };
   auto pref_v = [&](int i) -> PreVD<T> {
+    if constexpr (H) return PreVD<T>{d.hy[i], d.hay[i]};  // the iterate and its anchor
     return PreVD<T>{y[i], pw != (T)0 ? d.sum_y[i] : (T)0};
   };
   auto fin = [&](int i, P2<T> acc, const PreCD<T>& c, const PreVD<T>& v) {
@@ -558,7 +632,10 @@ __global__ void __launch_bounds__(kBlock, StepOcc<T>::value) k_dual(IterData<T, 
     T yv = v.yo + step * (c.q - kxbar);
     if (c.kind != 1) yv = maxv(yv, (T)0);
     yn[i] = yv;
-    if (pw != (T)0) d.sum_y[i] = v.sy + pw * v.yo;
+    if constexpr (H)
+      d.hy[i] = ha * yv + hb * v.yo + hc * v.sy;  // the reflected Halpern mix
+    else if (pw != (T)0)
+      d.sum_y[i] = v.sy + pw * v.yo;
     const T dd = yv - v.yo;
     dy2 += IMPLICIT ? dd * dd / c.sw : dd * dd;
     dkd += dd * acc.b;
@@ -647,7 +724,10 @@ __global__ void __launch_bounds__(kBlock) k_decide(IterData<T, V> d) {
   }
   block_sum3<T>(a, b0, b1);
   if (threadIdx.x == 0) {
-    decide_step<T>(&ls, a, b0, b1, fac[0], fac[1]);
+    if (ls.halpern)
+      decide_halpern<T>(&ls, a, b0, b1);
+    else
+      decide_step<T>(&ls, a, b0, b1, fac[0], fac[1]);
     store_step_state(st, ls);
     if (d.cond && k == 0) {
       // one LP in a graph with a while loop: keep stepping until a KKT check falls

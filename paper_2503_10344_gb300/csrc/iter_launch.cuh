@@ -46,6 +46,10 @@ IterData<T, V> typed(const IterRaw& r) {
   d.tslot = r.tslot;
   d.ord_t = r.ord_t;
   d.ord_a = r.ord_a;
+  d.hx = (T*)r.hx;
+  d.hy = (T*)r.hy;
+  d.hax = (const T*)r.hax;
+  d.hay = (const T*)r.hay;
   return d;
 }
 
@@ -63,16 +67,16 @@ cudaError_t prefer_l1(K kernel) {
   return e;
 }
 
-template <int LANES, typename T, typename V, bool IMPLICIT>
+template <int LANES, typename T, typename V, bool IMPLICIT, bool H>
 cudaError_t launch_one(int which, const IterData<T, V>& d, cudaStream_t s) {
   if (which == IK_PRIMAL) {
-    const cudaError_t e = prefer_l1(k_primal<LANES, T, V, IMPLICIT>);
+    const cudaError_t e = prefer_l1(k_primal<LANES, T, V, IMPLICIT, H>);
     if (e != cudaSuccess) return e;
   }
   switch (which) {
-    case IK_PRIMAL: return launch_pdl(k_primal<LANES, T, V, IMPLICIT>, d.grid_p, kBlock, s, d);
+    case IK_PRIMAL: return launch_pdl(k_primal<LANES, T, V, IMPLICIT, H>, d.grid_p, kBlock, s, d);
     case IK_DUAL: {  // the dual step, then the step decision of every LP
-      const cudaError_t e = launch_pdl(k_dual<LANES, T, V, IMPLICIT>, d.grid_d, kBlock, s, d);
+      const cudaError_t e = launch_pdl(k_dual<LANES, T, V, IMPLICIT, H>, d.grid_d, kBlock, s, d);
       if (e != cudaSuccess) return e;
       return launch_pdl(k_decide<T, V>, d.count, kBlock, s, d);
     }
@@ -111,10 +115,11 @@ cudaError_t tile_resident(int form, int* blocks) {
   return cudaSuccess;
 }
 
-template <typename T, typename V, bool IMPLICIT>
+// H: the Halpern variant's step kernels (the tile forms have none)
+template <typename T, typename V, bool IMPLICIT, bool H = false>
 cudaError_t launch_iter_t(int which, int lanes, const IterRaw& r, cudaStream_t s) {
   const IterData<T, V> d = typed<T, V>(r);
-  if constexpr (std::is_same<T, float>::value) {
+  if constexpr (std::is_same<T, float>::value && !H) {
     if (r.tile) {
       if (which == IK_PRIMAL) return launch_tile<V, IMPLICIT, false>(d, s);
       if (which != IK_DUAL) return cudaErrorInvalidValue;
@@ -124,12 +129,12 @@ cudaError_t launch_iter_t(int which, int lanes, const IterRaw& r, cudaStream_t s
     }
   }
   switch (lanes) {
-    case 1: return launch_one<1, T, V, IMPLICIT>(which, d, s);
-    case 2: return launch_one<2, T, V, IMPLICIT>(which, d, s);
-    case 4: return launch_one<4, T, V, IMPLICIT>(which, d, s);
-    case 8: return launch_one<8, T, V, IMPLICIT>(which, d, s);
-    case 16: return launch_one<16, T, V, IMPLICIT>(which, d, s);
-    case 32: return launch_one<32, T, V, IMPLICIT>(which, d, s);
+    case 1: return launch_one<1, T, V, IMPLICIT, H>(which, d, s);
+    case 2: return launch_one<2, T, V, IMPLICIT, H>(which, d, s);
+    case 4: return launch_one<4, T, V, IMPLICIT, H>(which, d, s);
+    case 8: return launch_one<8, T, V, IMPLICIT, H>(which, d, s);
+    case 16: return launch_one<16, T, V, IMPLICIT, H>(which, d, s);
+    case 32: return launch_one<32, T, V, IMPLICIT, H>(which, d, s);
     default: return cudaErrorInvalidValue;
   }
 }

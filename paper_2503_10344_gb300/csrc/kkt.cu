@@ -310,7 +310,34 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
     st->status = 3;  // PDLP_TIME_LIMIT
   }
   st->restart_kind = 0;
-  if (st->status == 0 && st->restarts_on && st->iters % st->period == 0) {
+  if (st->status == 0 && st->restarts_on && st->iters % st->period == 0 && st->halpern) {
+    // Halpern variant: the A9 rules on the fixed-point residual of the latest step
+    // against the epoch's first (prev_cand: the residual at the previous check)
+    const double rr = st->h_res, r0 = st->h_r0;
+    const bool do_restart = rr <= 0.2 * r0 || (rr <= 0.8 * r0 && rr > st->prev_cand) ||
+                            (double)(st->iters - st->last_restart_it) >= 0.36 * (double)st->iters;
+    if (!do_restart) {
+      st->prev_cand = rr;
+    } else {
+      // A10 from the candidate's scaled distance to the previous anchor
+      const double om = st->omega;
+      const double ddx = sqrt(pc[8]), ddy = sqrt(pr[6]);
+      if (ddx > 1e-10 && ddy > 1e-10) {
+        st->omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(om));
+        st->inv_omega = 1.0 / st->omega;
+        st->omega_f = (float)st->omega;
+        st->inv_omega_f = (float)st->inv_omega;
+        st->tau_d = st->eta / st->omega;
+        st->sigma_d = st->eta * st->omega;
+        st->tau_f = st->eta_f * st->inv_omega_f;
+        st->sigma_f = st->eta_f * st->omega_f;
+      }
+      st->prev_cand = INFINITY;
+      st->last_restart_it = st->iters;
+      st->restarts += 1;
+      st->restart_kind = 1;
+    }
+  } else if (st->status == 0 && st->restarts_on && st->iters % st->period == 0) {
     // A9: KKT restart on the scaled KKT_omega
     const double om = st->omega;
     const double mc = kkt_omega(om, pr[2], pc[2], gap2[0]);
@@ -372,7 +399,18 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
   __syncthreads();
   const double isw = inv_sh;
   const long long stride = (long long)es.nblk * kBlock;
+  // Halpern variant: the candidate T(z) (the current buffers) becomes the iterate and
+  // the anchor
+  T* hx = (T*)r.hx;
+  T* hy = (T*)r.hy;
+  T* hax = (T*)r.hax;
+  T* hay = (T*)r.hay;
   for (long long j = es.c0 + (long long)es.bidx * kBlock + threadIdx.x; j < es.c0 + es.nc; j += stride) {
+    if (hx) {
+      const T xc = x[j].x;
+      hx[j] = xc;
+      hax[j] = xc;
+    }
     if (kind == 2) {
       const double xc = (double)x[j].x;
       vec2_t<T> v;
@@ -383,9 +421,14 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
     } else {
       r.Xl[j] = cand2(r.XG, j).x;
     }
-    sx[j] = (T)0;
+    if (!hx) sx[j] = (T)0;  // (the Halpern iterate lives where the sums would)
   }
   for (long long i = es.r0 + (long long)es.bidx * kBlock + threadIdx.x; i < es.r0 + es.nr; i += stride) {
+    if (hy) {
+      const T yc = y[i];
+      hy[i] = yc;
+      hay[i] = yc;
+    }
     if (kind == 2) {
       const double yc = (double)y[i];
       y[i] = (T)(sw > 0.0 ? avg_of((double)sy[i] + pw * yc, sw, isw) : yc);
@@ -393,7 +436,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_apply(KktRaw r) {
     } else {
       r.Yl[i] = cand2(r.YG, i).x;
     }
-    sy[i] = (T)0;
+    if (!hy) sy[i] = (T)0;
   }
 }
 
@@ -407,6 +450,10 @@ __global__ void k_kkt_end(KktRaw r) {
     st->sum_w = 0.0;
     st->pending_w = 0.0;
     st->pw_f = 0.0f;
+    if (st->halpern) {  // a new epoch: k = 0
+      st->h_k = 0;
+      halpern_coeffs(st);
+    }
   }
   st->restart_kind = 0;
   st->check_due = 0;

@@ -880,6 +880,94 @@ size_t setup_part_doubles(int m, int n) {
   return (size_t)G * 7 + (size_t)G + 16;
 }
 
+// ---- Halpern variant: the power iteration for L ~ ||K~||_2, K~ = D_r K D_c
+// (K the canonical matrix; val NULL: every entry +1).  v = w / s is the unit vector of
+// the previous pass (w = 1/sqrt(n), s = 1 at the start); a pass forms u = K~ v and
+// w = K~^T u, s = ||w||; after the last pass L = sqrt(s).  A zero s leaves v = 0.
+__global__ void k_pow_start(double* w, int n, double* s) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const double v = 1.0 / sqrt((double)n);
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) w[j] = v;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s = 1.0;
+}
+
+// one warp per row of the matrix (ptr, col, val): out_r = fo_r sum_p K_rp fi_c(p) in_c(p) / s
+// (s NULL: no division), fo, fi the row and column scalings; with part != NULL also each
+// block's sum of out_r^2
+__global__ void __launch_bounds__(kBlock) k_pow_pass(const int* ptr, const int* col,
+                                                      const double* val, int rows,
+                                                      const double* fo, const double* fi,
+                                                      const double* in, const double* s,
+                                                      double* out, double* part) {
+  __shared__ double red[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double sv = s ? *s : 1.0;
+  const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+  double sq = 0.0;
+  const long long W = (long long)gridDim.x * kWarps;
+  for (long long r = (long long)blockIdx.x * kWarps + warp; r < rows; r += W) {
+    double acc = 0.0;
+    for (int p = ptr[r] + lane; p < ptr[r + 1]; p += 32) {
+      const int c = col[p];
+      acc += (val ? val[p] : 1.0) * fi[c] * (in[c] * inv);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const double v = fo[r] * acc;
+    if (lane == 0) {
+      out[r] = v;
+      sq += v * v;
+    }
+  }
+  if (part == nullptr) return;
+  if (lane == 0) red[warp] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kWarps; ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+// s = sqrt(sum of nb partials), added in slot order (one block)
+__global__ void __launch_bounds__(kBlock) k_pow_norm(const double* part, int nb, double* s) {
+  __shared__ double red[kBlock];
+  double t = 0.0;
+  for (int k = threadIdx.x; k < nb; k += kBlock) t += part[k];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = kBlock / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *s = sqrt(red[0]);
+}
+
+cudaError_t setup_power_norm(const int* a_ptr, const int* a_col, const double* a_val, int m,
+                             const int* t_ptr, const int* t_col, const double* t_val, int n,
+                             const double* dr, const double* dc, int iters, double* u, double* w,
+                             double* part, int part_cap, double* s_dev, double* L,
+                             long long* launches, cudaStream_t s) {
+  *L = 0.0;
+  const int G = std::max(1, std::min(part_cap, device_sm_count() * 8));
+  const int gr = std::max(1, std::min(G, (m + kWarps - 1) / kWarps));
+  const int gc = std::max(1, std::min(G, (n + kWarps - 1) / kWarps));
+  k_pow_start<<<grid_for(n, G), kBlock, 0, s>>>(w, n, s_dev);
+  *launches += 1;
+  for (int it = 0; it < iters; ++it) {
+    k_pow_pass<<<gr, kBlock, 0, s>>>(a_ptr, a_col, a_val, m, dr, dc, w, s_dev, u, nullptr);
+    k_pow_pass<<<gc, kBlock, 0, s>>>(t_ptr, t_col, t_val, n, dc, dr, u, nullptr, w, part);
+    k_pow_norm<<<1, kBlock, 0, s>>>(part, gc, s_dev);
+    *launches += 3;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double sv = 0.0;
+  e = cudaMemcpyAsync(&sv, s_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *L = sqrt(sv);
+  return e;
+}
+
 cudaError_t setup_len_order(const int* ptr, int rows, int* ord, cudaStream_t s) {
   k_len_order<<<grid_for(rows, device_sm_count() * 8), kBlock, 0, s>>>(ptr, rows, ord);
   return cudaGetLastError();

@@ -304,6 +304,14 @@ struct Solve {
   cudaError_t iter(int which) {
     g_launches += which == IK_DUAL ? 2 : 1;  // the dual step is followed by the decision
     const int lanes = which == IK_PRIMAL ? lanes_t : lanes_a;
+    if (ir.hx) {  // the Halpern variant
+      switch (mode) {
+        case MODE_FP64: return launch_iter_fp64_h(which, lanes, ir, s);
+        case MODE_FP32: return launch_iter_fp32_h(which, lanes, ir, s);
+        case MODE_BF16: return launch_iter_bf16_h(which, lanes, ir, s);
+        default: return launch_iter_pat_h(which, lanes, ir, s);
+      }
+    }
     switch (mode) {
       case MODE_FP64: return launch_iter_fp64(which, lanes, ir, s);
       case MODE_FP32: return launch_iter_fp32(which, lanes, ir, s);
@@ -390,6 +398,11 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
     return fail(PDLP_ERR_INVALID_INPUT, "KKT lanes must be 0, 2, 4, 8, 16 or 32");
   if (p->persistent && (p->lanes_A == 1 || p->lanes_AT == 1))
     return fail(PDLP_ERR_INVALID_INPUT, "one lane per row needs persistent = 0");
+  if (p->halpern != 0 && p->halpern != 1) return fail(PDLP_ERR_INVALID_INPUT, "halpern must be 0 or 1");
+  if (p->halpern && !(p->halpern_reflection >= 0.0 && p->halpern_reflection <= 1.0))
+    return fail(PDLP_ERR_INVALID_INPUT, "halpern_reflection must lie in [0, 1]");
+  if (p->halpern && (p->persistent || p->tiles))
+    return fail(PDLP_ERR_INVALID_INPUT, "halpern runs with persistent = 0 and tiles = 0 only");
   return PDLP_OK;
 }
 
@@ -852,9 +865,29 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   kr.grid_e = ge;
   kr.scaled = scaled; kr.fp32 = fp32;
   kr.st = bf.st;
+  if (p->halpern) {
+    // the Halpern iterate lives in the running-sum buffers (no averages in this variant)
+    // and its anchor in the scaling statistics' (used only by the setup); the initial
+    // KKT block sets both to the start
+    ir.hx = kr.hx = bf.sum_x;
+    ir.hy = kr.hy = bf.sum_y;
+    ir.hax = kr.hax = bf.stat_c;
+    ir.hay = kr.hay = bf.stat_r;
+  }
 
   // ---- A3: initial state
   CUDA_TRY(cudaStreamSynchronize(s));  // scalars
+  // Halpern variant: the constant step from the power-iteration estimate of ||K~||_2,
+  // taken before any rescaling touches D_r and D_c (the KKT candidate buffers and
+  // partials, not yet in use, are its scratch)
+  double spectral = 0.0;
+  if (p->halpern) {
+    const int part_cap = kPartC * (max_blocks() + kMaxLongBlocks);
+    CUDA_TRY(setup_power_norm(bf.a_ptr, bf.a_col, mode == MODE_PAT ? nullptr : bf.a_val64, m,
+                              bf.t_ptr, bf.t_col, mode == MODE_PAT ? nullptr : bf.t_val64, n,
+                              bf.dr, bf.dc, kPowerIters, (double*)bf.YG, (double*)bf.XG,
+                              bf.part_c, part_cap, bf.part_r, &spectral, &g_launches, s));
+  }
   // optional bound-objective rescaling: the objective by gamma = 1 + ||c~||, the
   // right-hand side and the bounds by beta = 1 + ||q~||; every scaled norm below is
   // taken in the rescaled problem
@@ -879,12 +912,22 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   hs.eta = kmax > 0.0 ? 1.0 / kmax : 1.0;
   if (p->fixed_eta > 0.0) hs.eta = p->fixed_eta;
   if (p->fixed_omega > 0.0) hs.omega = p->fixed_omega;
+  if (p->halpern) {
+    // a constant step, every step taken; the first epoch's coefficients (k = 0)
+    hs.halpern = 1;
+    hs.h_rho = p->halpern_reflection;
+    hs.eta = spectral > 0.0 ? kHalpernEtaScale / spectral : 1.0;
+    if (p->fixed_eta > 0.0) hs.eta = p->fixed_eta;
+    hs.h_k = 0;
+    hs.h_res = hs.h_r0 = INFINITY;
+    halpern_coeffs(&hs);
+  }
   hs.check_due = 1;
   hs.init_pending = 1;
   hs.prev_cand = INFINITY;
   hs.iter_limit = p->iter_limit;
   hs.period = p->check_period;
-  hs.adaptive = p->adaptive_step ? 1 : 0;
+  hs.adaptive = p->adaptive_step && !p->halpern ? 1 : 0;
   hs.restarts_on = p->restarts ? 1 : 0;
   hs.terminate = p->terminate ? 1 : 0;
   hs.detect_inf = p->detect_infeasibility ? 1 : 0;
@@ -1219,6 +1262,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   r->lanes_AT = sv.lanes_t;
   r->tiles = sv.ir.tile;
   r->persistent_form = p->persistent == 0 ? 0 : p->persistent == 1 ? 1 : sv.ir.smem.bytes > 0 ? 3 : 2;
+  r->spectral_norm = spectral;
   r->iters = fs.iters;
   r->attempts = fs.attempts;
   r->restarts = fs.restarts;
@@ -1451,6 +1495,7 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
                        bool device_inputs = false, cudaStream_t user_stream = nullptr) {
   if (p->bound_objective_rescaling)
     return fail(PDLP_ERR_INVALID_INPUT, "bound_objective_rescaling is for single LPs, not batches");
+  if (p->halpern) return fail(PDLP_ERR_INVALID_INPUT, "halpern is for single LPs, not batches");
   if (p->persistent == 2)
     return fail(PDLP_ERR_INVALID_INPUT, "persistent = 2 (one block) is for single LPs, not batches");
   g_launches = 0;
@@ -2100,6 +2145,8 @@ int pdlp_default_params(pdlp_params* p) {
   p->detect_infeasibility = 1;
   p->tiles = 0;
   p->bound_objective_rescaling = 0;
+  p->halpern = 0;
+  p->halpern_reflection = 1.0;
   return PDLP_OK;
 }
 

@@ -133,3 +133,16 @@ def test_batch_rejects_an_empty_batch_and_names_a_bad_lp(P, lp):
 def test_bound_objective_rescaling_parameter_is_checked(P, lp):
     _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(bound_objective_rescaling=2)),
               "bound_objective_rescaling must be 0 or 1")
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(halpern=2), "halpern must be 0 or 1"),
+    (dict(halpern=1, halpern_reflection=1.5), "halpern_reflection must lie in [0, 1]"),
+    (dict(halpern=1, halpern_reflection=-0.1), "halpern_reflection must lie in [0, 1]"),
+    (dict(halpern=1, halpern_reflection=float("nan")), "halpern_reflection must lie in [0, 1]"),
+    (dict(halpern=1, persistent=1), "halpern runs with persistent = 0 and tiles = 0 only"),
+    (dict(halpern=1, persistent=2), "halpern runs with persistent = 0 and tiles = 0 only"),
+    (dict(halpern=1, tiles=1, precision=1), "halpern runs with persistent = 0 and tiles = 0 only"),
+])
+def test_halpern_parameters_are_checked(P, lp, kw, needle):
+    _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(**kw)), needle)
