@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],
                     help="float32 steps: 0 lanes-per-row kernels; 1 staged block tiles (bulk "
                          "copies into shared memory); 2 warp tiles")
+    ap.add_argument("--halpern", type=int, default=0, choices=[0, 1],
+                    help="1: the reflected restarted Halpern PDHG variant (single LPs)")
     for k in ("lanes-a", "lanes-at", "lanes-kkt-a", "lanes-kkt-at"):
         ap.add_argument("--" + k, type=int, default=0, help="SpMV lanes per row (0 = automatic)")
     return ap.parse_args()
@@ -69,7 +71,8 @@ def parse():
 
 def lane_params(args) -> dict:
     return {"lanes_A": args.lanes_a, "lanes_AT": args.lanes_at, "lanes_kkt_A": args.lanes_kkt_a,
-            "lanes_kkt_AT": args.lanes_kkt_at, "persistent": args.persistent, "tiles": args.tiles}
+            "lanes_kkt_AT": args.lanes_kkt_at, "persistent": args.persistent, "tiles": args.tiles,
+            "halpern": args.halpern}
 
 
 def dist_env():
@@ -724,10 +727,11 @@ def run_batch(args):
 
 
 def run_variants(args):
-    """Bound-objective rescaling (pdlp_params.bound_objective_rescaling) against the default
-    iteration on the same instances and precision modes: iterations and iteration-phase
-    time to rel. KKT 1e-4 (float32 / pattern on the covering LPs and the energy system,
-    float64 on the 200 x 400 relaxations)."""
+    """The algorithmic variants against the default iteration on the same instances and
+    precision modes: bound-objective rescaling (pdlp_params.bound_objective_rescaling) and
+    the reflected restarted Halpern PDHG (pdlp_params.halpern); iterations and
+    iteration-phase time to rel. KKT 1e-4 (float32 / pattern on the covering LPs and the
+    energy system, float64 on the 200 x 400 relaxations)."""
     import torch
 
     import __graft_entry__ as G
@@ -743,17 +747,19 @@ def run_variants(args):
     for name, lp, prec in cases:
         d = P.DeviceLP(lp)
         row = {"instance": name, "precision": prec}
-        for resc in (0, 1):
-            prm = P.default_params(tol=1e-4, precision=prec, bound_objective_rescaling=resc,
-                                   iter_limit=200_000)
+        for key, kw in (("default", {}), ("rescaled", {"bound_objective_rescaling": 1}),
+                        ("halpern", {"halpern": 1})):
+            prm = P.default_params(tol=1e-4, precision=prec, iter_limit=200_000, **kw)
             P.pdlp_solve_device(d, prm)  # warm
             torch.cuda.synchronize()
             _, _, r = P.pdlp_solve_device(d, prm)
-            row["rescaled" if resc else "default"] = {
+            row[key] = {
                 "status": r["status"], "iters": r["iters"], "restarts": r["restarts"],
-                "solve_s": r["solve_s"], "rel_kkt": r["rel_kkt"], "primal_obj": r["primal_obj"]}
+                "solve_s": r["solve_s"], "setup_s": r["setup_s"], "rel_kkt": r["rel_kkt"],
+                "primal_obj": r["primal_obj"]}
         rows.append(row)
-    print(json.dumps({"workload": "bound-objective rescaling against the default iteration",
+    print(json.dumps({"workload": "bound-objective rescaling and reflected restarted Halpern "
+                                  "PDHG against the default iteration",
                       "tol": 1e-4, "runs": rows}), flush=True)
 
 
@@ -802,8 +808,10 @@ def run_energy(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"energy system 8760h x 20 regions x 6 techs, m={lp.m}, n={lp.n}, "
-                                   f"nnz={lp.nnz}, tol=1e-4", "precision": prec},
+                                   f"nnz={lp.nnz}, tol=1e-4", "precision": prec,
+                       "halpern": args.halpern},
             "time_to_tol_s": sum(ms) / 1e3 / args.steps, "iters_per_solve": iters / args.steps,
+            "primal_obj": res["primal_obj"], "restarts": res["restarts"],
             "status": res["status"], "rel_kkt": res["rel_kkt"], "setup_ms": 1e3 * res["setup_s"],
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
                          "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": None,

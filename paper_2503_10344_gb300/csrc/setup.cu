@@ -891,41 +891,82 @@ __global__ void k_pow_start(double* w, int n, double* s) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *s = 1.0;
 }
 
-// one warp per row of the matrix (ptr, col, val): out_r = fo_r sum_p K_rp fi_c(p) in_c(p) / s
-// (s NULL: no division), fo, fi the row and column scalings; with part != NULL also each
-// block's sum of out_r^2
+// A pass over the matrix (ptr, col, val): out_r = fo_r sum_p K_rp fi_c(p) in_c(p) / s
+// (s NULL: no division), fo, fi the row and column scalings.  Rows of at most `thresh`
+// entries by groups of kPowLanes lanes, rows grid-strided (longer rows: k_pow_long); with
+// part != NULL also each block's sum of out_r^2 into part[block].
+constexpr int kPowLanes = 4;
+__device__ __forceinline__ double pow_inv(const double* s) {
+  const double sv = s ? *s : 1.0;
+  return sv > 0.0 ? 1.0 / sv : 0.0;
+}
+__device__ __forceinline__ void pow_block_part(double sq, double* part) {
+  __shared__ double red[kBlock];
+  red[threadIdx.x] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kBlock; k += kPowLanes) t += red[k];  // the groups' first lanes
+    part[blockIdx.x] = t;
+  }
+}
 __global__ void __launch_bounds__(kBlock) k_pow_pass(const int* ptr, const int* col,
-                                                      const double* val, int rows,
+                                                      const double* val, int rows, int thresh,
                                                       const double* fo, const double* fi,
                                                       const double* in, const double* s,
                                                       double* out, double* part) {
-  __shared__ double red[kWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double sv = s ? *s : 1.0;
-  const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+  const int gl = threadIdx.x & (kPowLanes - 1);
+  const double inv = pow_inv(s);
   double sq = 0.0;
-  const long long W = (long long)gridDim.x * kWarps;
-  for (long long r = (long long)blockIdx.x * kWarps + warp; r < rows; r += W) {
+  const long long G = (long long)gridDim.x * (kBlock / kPowLanes);
+  for (long long r = ((long long)blockIdx.x * kBlock + threadIdx.x) / kPowLanes; r < rows; r += G) {
+    const int b0 = ptr[r], e0 = ptr[r + 1];
+    if (e0 - b0 > thresh) continue;  // uniform within the group
     double acc = 0.0;
-    for (int p = ptr[r] + lane; p < ptr[r + 1]; p += 32) {
+    for (int p = b0 + gl; p < e0; p += kPowLanes) {
       const int c = col[p];
       acc += (val ? val[p] : 1.0) * fi[c] * (in[c] * inv);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    const double v = fo[r] * acc;
-    if (lane == 0) {
+    acc = group_sum<kPowLanes>(acc);
+    if (gl == 0) {
+      const double v = fo[r] * acc;
       out[r] = v;
       sq += v * v;
     }
   }
-  if (part == nullptr) return;
-  if (lane == 0) red[warp] = sq;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < kWarps; ++k) t += red[k];
-    part[blockIdx.x] = t;
+  if (part) pow_block_part(gl == 0 ? sq : 0.0, part);
+}
+// the rows longer than `thresh` (list[nlist]), one block per row, grid-strided over the list
+__global__ void __launch_bounds__(kBlock) k_pow_long(const int* ptr, const int* col,
+                                                      const double* val, const int* list,
+                                                      int nlist, const double* fo,
+                                                      const double* fi, const double* in,
+                                                      const double* s, double* out,
+                                                      double* part) {
+  __shared__ double red[kBlock];
+  const double inv = pow_inv(s);
+  double sq = 0.0;
+  for (int k = blockIdx.x; k < nlist; k += gridDim.x) {
+    const int r = list[k];
+    double acc = 0.0;
+    for (int p = ptr[r] + threadIdx.x; p < ptr[r + 1]; p += kBlock) {
+      const int c = col[p];
+      acc += (val ? val[p] : 1.0) * fi[c] * (in[c] * inv);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kBlock / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double v = fo[r] * red[0];
+      out[r] = v;
+      sq += v * v;
+    }
+    __syncthreads();
   }
+  if (part && threadIdx.x == 0) part[blockIdx.x] = sq;
 }
 
 // s = sqrt(sum of nb partials), added in slot order (one block)
@@ -942,22 +983,29 @@ __global__ void __launch_bounds__(kBlock) k_pow_norm(const double* part, int nb,
   if (threadIdx.x == 0) *s = sqrt(red[0]);
 }
 
-cudaError_t setup_power_norm(const int* a_ptr, const int* a_col, const double* a_val, int m,
-                             const int* t_ptr, const int* t_col, const double* t_val, int n,
-                             const double* dr, const double* dc, int iters, double* u, double* w,
-                             double* part, int part_cap, double* s_dev, double* L,
-                             long long* launches, cudaStream_t s) {
+cudaError_t setup_power_norm(const PowIn& q, int iters, double* u, double* w, double* part,
+                             int part_cap, double* s_dev, double* L, long long* launches,
+                             cudaStream_t s) {
   *L = 0.0;
-  const int G = std::max(1, std::min(part_cap, device_sm_count() * 8));
-  const int gr = std::max(1, std::min(G, (m + kWarps - 1) / kWarps));
-  const int gc = std::max(1, std::min(G, (n + kWarps - 1) / kWarps));
-  k_pow_start<<<grid_for(n, G), kBlock, 0, s>>>(w, n, s_dev);
+  const int G = std::max(1, std::min(part_cap / 2, device_sm_count() * 8));
+  const int per = kBlock / kPowLanes;
+  const int gr = std::max(1, std::min(G, (q.m + per - 1) / per));
+  const int gc = std::max(1, std::min(G, (q.n + per - 1) / per));
+  const int lr = std::min(q.a_nlong, G), lc = std::min(q.t_nlong, G);
+  k_pow_start<<<grid_for(q.n, G), kBlock, 0, s>>>(w, q.n, s_dev);
   *launches += 1;
   for (int it = 0; it < iters; ++it) {
-    k_pow_pass<<<gr, kBlock, 0, s>>>(a_ptr, a_col, a_val, m, dr, dc, w, s_dev, u, nullptr);
-    k_pow_pass<<<gc, kBlock, 0, s>>>(t_ptr, t_col, t_val, n, dc, dr, u, nullptr, w, part);
-    k_pow_norm<<<1, kBlock, 0, s>>>(part, gc, s_dev);
-    *launches += 3;
+    // u = K~ v over the rows of A, then w = K~^T u over the rows of A^T with ||w||^2
+    k_pow_pass<<<gr, kBlock, 0, s>>>(q.a_ptr, q.a_col, q.a_val, q.m, q.a_thresh, q.dr, q.dc, w,
+                                     s_dev, u, nullptr);
+    if (lr) k_pow_long<<<lr, kBlock, 0, s>>>(q.a_ptr, q.a_col, q.a_val, q.a_long, q.a_nlong, q.dr,
+                                             q.dc, w, s_dev, u, nullptr);
+    k_pow_pass<<<gc, kBlock, 0, s>>>(q.t_ptr, q.t_col, q.t_val, q.n, q.t_thresh, q.dc, q.dr, u,
+                                     nullptr, w, part);
+    if (lc) k_pow_long<<<lc, kBlock, 0, s>>>(q.t_ptr, q.t_col, q.t_val, q.t_long, q.t_nlong, q.dc,
+                                             q.dr, u, nullptr, w, part + gc);
+    k_pow_norm<<<1, kBlock, 0, s>>>(part, gc + lc, s_dev);
+    *launches += 3 + (lr ? 1 : 0) + (lc ? 1 : 0);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

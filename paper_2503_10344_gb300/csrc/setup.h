@@ -71,15 +71,25 @@ cudaError_t setup_offset_copy(int* dst, const int* src, long long count, int off
                               cudaStream_t s);
 // The rows of a CSR matrix by descending length, ties by index (ord[place] = row).
 cudaError_t setup_len_order(const int* ptr, int rows, int* ord, cudaStream_t s);
-// Halpern variant: *L = the power-iteration estimate of ||D_r K D_c||_2 after `iters`
-// passes (A and A^T in CSR, values NULL: every entry +1) from v = 1/sqrt(n); u[m], w[n],
-// part[part_cap] and s_dev[1] are scratch; synchronises the stream to read the result;
-// *launches grows by the kernels launched.
-cudaError_t setup_power_norm(const int* a_ptr, const int* a_col, const double* a_val, int m,
-                             const int* t_ptr, const int* t_col, const double* t_val, int n,
-                             const double* dr, const double* dc, int iters, double* u, double* w,
-                             double* part, int part_cap, double* s_dev, double* L,
-                             long long* launches, cudaStream_t s);
+// Halpern variant: the matrix of the power iteration, A and A^T in CSR (values NULL:
+// every entry +1) with their long-row lists (rows longer than the thresholds, one block
+// each) and the scalings D_r, D_c.
+struct PowIn {
+  const int *a_ptr, *a_col;
+  const double* a_val;
+  const int *t_ptr, *t_col;
+  const double* t_val;
+  const int *a_long, *t_long;
+  int a_nlong, t_nlong, a_thresh, t_thresh;
+  int m, n;
+  const double *dr, *dc;
+};
+// *L = the power-iteration estimate of ||D_r K D_c||_2 after `iters` passes from
+// v = 1/sqrt(n); u[m], w[n], part[part_cap] and s_dev[1] are scratch; synchronises the
+// stream to read the result; *launches grows by the kernels launched.
+cudaError_t setup_power_norm(const PowIn& q, int iters, double* u, double* w, double* part,
+                             int part_cap, double* s_dev, double* L, long long* launches,
+                             cudaStream_t s);
 
 // Bound-objective rescaling of the iteration vectors and the start point, with the
 // factors beta (right-hand side, bounds, x) and gamma (objective, y) folded into the

@@ -883,10 +883,11 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   double spectral = 0.0;
   if (p->halpern) {
     const int part_cap = kPartC * (max_blocks() + kMaxLongBlocks);
-    CUDA_TRY(setup_power_norm(bf.a_ptr, bf.a_col, mode == MODE_PAT ? nullptr : bf.a_val64, m,
-                              bf.t_ptr, bf.t_col, mode == MODE_PAT ? nullptr : bf.t_val64, n,
-                              bf.dr, bf.dc, kPowerIters, (double*)bf.YG, (double*)bf.XG,
-                              bf.part_c, part_cap, bf.part_r, &spectral, &g_launches, s));
+    PowIn pq{bf.a_ptr, bf.a_col, mode == MODE_PAT ? nullptr : bf.a_val64,
+             bf.t_ptr, bf.t_col, mode == MODE_PAT ? nullptr : bf.t_val64,
+             bf.a_long, bf.t_long, nlong_a, nlong_t, th_a, th_t, m, n, bf.dr, bf.dc};
+    CUDA_TRY(setup_power_norm(pq, kPowerIters, (double*)bf.YG, (double*)bf.XG, bf.part_c,
+                              part_cap, bf.part_r, &spectral, &g_launches, s));
   }
   // optional bound-objective rescaling: the objective by gamma = 1 + ||c~||, the
   // right-hand side and the bounds by beta = 1 + ||q~||; every scaled norm below is
