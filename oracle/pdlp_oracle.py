@@ -44,6 +44,26 @@ reading is marked "reading" where it is used below:
       and the average iterate on the unscaled data (Part I below).
   A9  KKT restart (beta_suff 0.2, beta_nec 0.8, beta_art 0.36) on the scaled
       KKT_omega = sqrt(omega ||r_p~||^2 + ||r_d~||^2 / omega + gap^2).
+  A9b optional normalized-duality-gap restarts (the restart metric of the
+      original PDLP; off by default; every detail is a reading): the same
+      three rules with rho(r; z) in place of KKT_omega, where for a candidate
+      z (current or average, scaled) r = ||z - z_last||_omega,
+      ||(x, y)||_omega^2 = omega ||x||^2 + ||y||^2 / omega, and
+        rho(r; z) = max{ L(x, y^) - L(x^, y) : z^ in X x Y,
+                         ||z^ - z||_omega <= r } / r
+      (0 when r = 0) with L(x, y) = c~^T x - y^T K~ x + q~^T y, i.e. the
+      maximum of g^T (z^ - z), g = (K~^T y - c~, q~ - K~ x), over the
+      trust region.  Its maximiser is z^(t) = (proj_X(x + t g_x / omega),
+      proj_Y(y + t omega g_y)) with t the largest step whose distance
+      d(t) = ||z^(t) - z||_omega is at most r (d is nondecreasing and
+      d(t) <= t N, N^2 = ||g_x||^2 / omega + omega ||g_y||^2).  t is found
+      by bisection from t0 = r / N: the smallest k in 0..63 with
+      d(t0 2^k) >= r (bisection over k, 6 steps; t = t0 2^63 if none), then
+      44 halvings of [t0 2^(k-1), t0 2^k], t the final lower end.  The
+      candidate is the one with the smaller rho (tie: current); the restart
+      point's rho (the one that triggered it, with the radius that brought it
+      there) is the reference of the next epoch; before the first restart the
+      reference is +inf.
   A10 primal weight omega <- exp(0.5 ln(dy/dx) + 0.5 ln omega) on restart.
   A11 stop when min(relKKT(current), relKKT(average)) <= tol; unscale.
   A12 infeasibility certificates (PDLP's test on iterate differences; the
@@ -247,6 +267,7 @@ class Params:
     fixed_eta: float | None = None  # overrides eta0 (fixed-step mode)
     fixed_omega: float | None = None  # overrides omega0
     bound_objective_rescaling: bool = False  # A2b
+    restart_metric: str = "kkt"     # A9 "kkt" | A9b "ndg" (normalized duality gap)
     halpern: bool = False           # A14: reflected restarted Halpern PDHG
     halpern_reflection: float = 1.0  # A14: rho
     halpern_eta_scale: float = 0.998  # A14: eta = scale / L
@@ -331,6 +352,64 @@ def power_norm(kt, iters=64) -> float:
             return 0.0
         v = w / s
     return math.sqrt(s)
+
+
+NDG_K_STEPS = 6
+NDG_HALVINGS = 44
+
+
+def trust_region_gap(gx, gy, x, y, lt, ut, is_eq, omega, r):
+    """A9b: max g^T (z^ - z) over z^ in X x Y with ||z^ - z||_omega <= r, by the
+    bisection on t of the module docstring.  Returns (value, t)."""
+    if r <= 0.0:
+        return 0.0, 0.0
+    nn = math.sqrt(float(gx @ gx) / omega + omega * float(gy @ gy))
+    if nn == 0.0:
+        return 0.0, 0.0
+
+    def step(t):
+        return proj_box(x + (t / omega) * gx, lt, ut) - x, proj_dual(y + (t * omega) * gy, is_eq) - y
+
+    def dist(t):
+        dx, dy = step(t)
+        return math.sqrt(omega * float(dx @ dx) + float(dy @ dy) / omega)
+
+    t0 = r / nn
+    if dist(t0 * 2.0 ** 63) < r:
+        t = t0 * 2.0 ** 63
+    else:
+        lo, hi = -1, 63            # d(t0 2^lo) < r <= d(t0 2^hi) (lo = -1: below k = 0)
+        for _ in range(NDG_K_STEPS):
+            mid = (lo + hi) // 2
+            if mid == lo:
+                break
+            if dist(t0 * 2.0 ** mid) >= r:
+                hi = mid
+            else:
+                lo = mid
+        a, b = t0 * 2.0 ** (hi - 1), t0 * 2.0 ** hi
+        for _ in range(NDG_HALVINGS):
+            mid = 0.5 * (a + b)
+            if dist(mid) >= r:
+                b = mid
+            else:
+                a = mid
+        t = a
+    dx, dy = step(t)
+    return float(gx @ dx) + float(gy @ dy), t
+
+
+def normalized_gap(kt, ktt, ct, qt, lt, ut, is_eq, omega, xs, ys, x_last, y_last):
+    """A9b: rho(r; z) for the scaled candidate z = (xs, ys), r its omega-distance from
+    the last restart point (0 when r = 0)."""
+    dx, dy = xs - x_last, ys - y_last
+    r = math.sqrt(omega * float(dx @ dx) + float(dy @ dy) / omega)
+    if r == 0.0:
+        return 0.0
+    gx = ktt @ ys - ct
+    gy = qt - kt @ xs
+    val, _ = trust_region_gap(gx, gy, xs, ys, lt, ut, is_eq, omega, r)
+    return val / r
 
 
 def recession_proj(dx, l, u):
@@ -429,6 +508,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
     x_last, y_last = x.copy(), y.copy()
     kkt_last = scaled_kkt(x, y)          # "last restart" KKT starts at z0
     kkt_prev_cand = math.inf
+    ndg_last = math.inf                  # A9b: rho of the last restart point
     last_restart_it = 0
     status = STATUS_ITER_LIMIT
     trace = []
@@ -581,12 +661,20 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                 # A9
                 sc = scaled_kkt(x, y)
                 sa = scaled_kkt(xa, ya)
-                mc, ma = sc.kkt_omega(omega), sa.kkt_omega(omega)
+                if p.restart_metric == "ndg":
+                    # A9b: the normalized duality gaps at the candidates' own radii
+                    mc = normalized_gap(kt, ktt, ct, qt, lt, ut, is_eq, omega, x, y,
+                                        x_last, y_last)
+                    ma = normalized_gap(kt, ktt, ct, qt, lt, ut, is_eq, omega, xa, ya,
+                                        x_last, y_last)
+                    m_last = ndg_last
+                else:
+                    mc, ma = sc.kkt_omega(omega), sa.kkt_omega(omega)
+                    m_last = kkt_last.kkt_omega(omega)
                 use_avg = ma < mc
                 cand_x, cand_y = (xa, ya) if use_avg else (x, y)
                 cand_k = sa if use_avg else sc
                 m_cand = ma if use_avg else mc
-                m_last = kkt_last.kkt_omega(omega)
                 do_restart = (m_cand <= p.beta_suff * m_last
                               or (m_cand <= p.beta_nec * m_last and m_cand > kkt_prev_cand)
                               or (it - last_restart_it) >= p.beta_art * it)
@@ -600,6 +688,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None) -> Result:
                     x, y = cand_x.copy(), cand_y.copy()
                     x_last, y_last = x.copy(), y.copy()
                     kkt_last = cand_k
+                    ndg_last = m_cand
                     kkt_prev_cand = math.inf
                     last_restart_it = it
                     sum_x[:] = 0.0

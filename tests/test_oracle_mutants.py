@@ -110,6 +110,18 @@ MUTANTS = [
     ("epoch residual r_0 replaced at every step",
      "if h_k == 0:\n                h_r0 = h_res", "h_r0 = h_res",
      ["test_halpern_necessary_decay_restart_by_hand"]),
+    ("trust-region step of y scaled by 1/omega", "proj_dual(y + (t * omega) * gy, is_eq)",
+     "proj_dual(y + (t / omega) * gy, is_eq)", ["test_trust_region_gap_closed_forms"]),
+    ("gap gradient g_x with the wrong sign", "gx = ktt @ ys - ct", "gx = ct - ktt @ ys",
+     ["test_normalized_gap_by_hand"]),
+    ("gap not divided by the radius", "return val / r", "return val",
+     ["test_normalized_gap_by_hand"]),
+    ("reference gap not moved at a restart", "ndg_last = m_cand\n", "\n",
+     ["test_ndg_restart_sequence_differs_from_kkt_and_restarts_less_on_a_relaxation"]),
+    ("gap radius without the primal weight",
+     "r = math.sqrt(omega * float(dx @ dx) + float(dy @ dy) / omega)\n    if r == 0.0:",
+     "r = math.sqrt(float(dx @ dx) + float(dy @ dy))\n    if r == 0.0:",
+     ["test_normalized_gap_by_hand"]),
     ("Halpern candidate taken at the mixed iterate instead of T(z)",
      "x, y = x_new, y_new\n            it += 1", "x, y = xh.copy(), yh.copy()\n            it += 1",
      ["test_halpern_steps_by_hand"]),

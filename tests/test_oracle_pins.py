@@ -682,3 +682,113 @@ def test_halpern_mip_relaxation_matches_highs():
     r = O.solve(lp, O.Params(tol=1e-8, halpern=True))
     assert r.status == O.STATUS_OPTIMAL
     assert abs(r.kkt.primal_obj - obj) / (1 + abs(obj)) < 1e-7
+
+
+# ---------------------------------------------------------------- A9b normalized duality gap
+def _tr(gx, gy, x, y, lt, ut, is_eq, omega, r):
+    f = lambda v: np.asarray(v, dtype=float)
+    return O.trust_region_gap(f(gx), f(gy), f(x), f(y), f(lt), f(ut), np.asarray(is_eq, bool),
+                              omega, r)[0]
+
+
+def test_trust_region_gap_closed_forms():
+    """Without active bounds the maximum of g^T d over ||d||_omega <= r is r times the dual
+    norm sqrt(||g_x||^2 / omega + omega ||g_y||^2); a box that caps every direction inside
+    the ball gives the box maximum; on [0, 1]^2 with g = (3, 4), omega = 1: r = 1 -> 5
+    (interior), r = 1.3 -> b = 1, a = sqrt(1.69 - 1): 3 sqrt(0.69) + 4."""
+    inf = np.inf
+    v = _tr([1.0, -2.0], [0.5], [0.3, 0.1], [0.2], [-inf, -inf], [inf, inf], [True], 2.5, 0.7)
+    assert v == pytest.approx(0.7 * math.sqrt((1 + 4) / 2.5 + 2.5 * 0.25), rel=1e-12)
+    assert _tr([2.0], [], [0.0], [], [0.0], [1.0], [], 1.0, 5.0) == pytest.approx(2.0, rel=1e-12)
+    assert _tr([3.0, 4.0], [], [0.0, 0.0], [], [0.0, 0.0], [1.0, 1.0], [], 1.0, 1.0) == \
+        pytest.approx(5.0, rel=1e-12)
+    assert _tr([3.0, 4.0], [], [0.0, 0.0], [], [0.0, 0.0], [1.0, 1.0], [], 1.0, 1.3) == \
+        pytest.approx(3.0 * math.sqrt(0.69) + 4.0, rel=1e-12)
+    # an inequality row's dual cannot go below 0: y = 0.5, g_y = -2 moves y to 0 at most
+    assert _tr([], [-2.0], [], [0.5], [], [], [False], 1.0, 3.0) == pytest.approx(1.0, rel=1e-12)
+    assert _tr([1.0], [2.0], [0.0], [0.0], [0.0], [1.0], [False], 1.0, 0.0) == 0.0
+
+
+def test_trust_region_gap_matches_an_independent_solver():
+    """Random boxes, cones, omega != 1: the bisection's maximum against SLSQP's on the
+    same problem (maximise g^T d subject to the bounds and the omega-ball)."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(11)
+    for trial in range(12):
+        n, m = 3, 2
+        omega = float(rng.uniform(0.3, 3.0))
+        x = rng.uniform(-1, 1, n)
+        lt = x - rng.uniform(0.0, 0.6, n)
+        ut = x + rng.uniform(0.0, 0.6, n)
+        lt[0], ut[1] = -np.inf, np.inf
+        is_eq = np.array([trial % 2 == 0, False])
+        y = np.where(is_eq, rng.normal(size=m), rng.uniform(0, 0.5, m))
+        gx, gy = rng.normal(size=n), rng.normal(size=m)
+        r = float(rng.uniform(0.2, 1.5))
+        got = _tr(gx, gy, x, y, lt, ut, is_eq, omega, r)
+        z0 = np.concatenate([x, y])
+        lo = np.concatenate([lt, np.where(is_eq, -np.inf, 0.0)])
+        hi = np.concatenate([ut, np.full(m, np.inf)])
+        g = np.concatenate([gx, gy])
+        w = np.concatenate([np.full(n, omega), np.full(m, 1.0 / omega)])
+        cons = [{"type": "ineq", "fun": lambda z: r * r - float(w @ (z - z0) ** 2)}]
+        bnds = [(None if not np.isfinite(a) else a, None if not np.isfinite(b) else b)
+                for a, b in zip(lo, hi)]
+        res = minimize(lambda z: -float(g @ (z - z0)), z0, jac=lambda z: -g, bounds=bnds,
+                       constraints=cons, method="SLSQP", options={"ftol": 1e-12, "maxiter": 1000})
+        zs = res.x
+        # SLSQP's point is feasible (to 1e-9) and no better than the bisection's maximum
+        assert float(w @ (zs - z0) ** 2) <= r * r * (1 + 1e-9)
+        assert np.all(zs >= lo - 1e-9) and np.all(zs <= hi + 1e-9)
+        assert got == pytest.approx(-res.fun, rel=1e-6, abs=1e-9)
+
+
+def test_normalized_gap_by_hand():
+    """min x s.t. x >= 1 (K = 1, q = 1, c = 1), omega = 1, from the restart point (0, 1):
+    the current point (0.25, 1.75) is r = sqrt(0.625) away with g = (y - c, q - x) =
+    (0.75, 0.75); nothing binds, so rho = ||g|| = 0.75 sqrt(2).  The point (0.125, 1.625):
+    g = (0.625, 0.875), rho = sqrt(0.625^2 + 0.875^2).  With omega = 4 the gradient norm
+    is sqrt(g_x^2 / 4 + 4 g_y^2).  At the restart point itself r = 0: rho = 0."""
+    import scipy.sparse as sps
+    kt = sps.csr_matrix(np.array([[1.0]]))
+    args = (kt, kt.T.tocsr(), np.array([1.0]), np.array([1.0]), np.array([0.0]),
+            np.array([np.inf]), np.array([False]))
+    g = lambda om, xs, ys: O.normalized_gap(*args, om, np.array([xs]), np.array([ys]),
+                                            np.array([0.0]), np.array([1.0]))
+    assert g(1.0, 0.25, 1.75) == pytest.approx(0.75 * math.sqrt(2.0), rel=1e-12)
+    assert g(1.0, 0.125, 1.625) == pytest.approx(math.hypot(0.625, 0.875), rel=1e-12)
+    assert g(4.0, 0.25, 1.75) == pytest.approx(math.sqrt(0.75 ** 2 / 4 + 4 * 0.75 ** 2), rel=1e-12)
+    assert g(1.0, 0.0, 1.0) == 0.0
+    # omega = 4 with x <= 0.3 binding: r^2 = 4 (0.25)^2 + (0.75)^2 / 4 = 0.390625; x moves
+    # 0.1875 t and stops at 0.3 (dx = 0.05), y moves 3 t; the ball then gives
+    # 4 (0.05)^2 + (3 t)^2 / 4 = r^2, and rho = 0.75 (0.05 + 3 t) / r
+    args_b = args[:5] + (np.array([0.3]),) + args[6:]
+    rho = O.normalized_gap(*args_b, 4.0, np.array([0.25]), np.array([1.75]), np.array([0.0]),
+                           np.array([1.0]))
+    r = math.sqrt(0.390625)
+    t = math.sqrt((0.390625 - 4 * 0.05 ** 2) * 4 / 9)
+    assert rho == pytest.approx(0.75 * (0.05 + 3 * t) / r, rel=1e-12)
+
+
+def test_ndg_restarts_reach_the_optimum():
+    for seed in range(3):
+        lp = lpgen.tiny_lp(seed, m=5 + seed % 2, n=4 + seed % 2, eq_rows=seed % 2)
+        best, _ = R.vertex_enumeration(lp)
+        r = O.solve(lp, O.Params(tol=1e-9, iter_limit=400_000, restart_metric="ndg"))
+        assert r.status == O.STATUS_OPTIMAL
+        assert r.kkt.primal_obj == pytest.approx(best, rel=1e-6, abs=1e-6)
+    lp = lpgen.mip_relaxation(1)
+    obj, _, _, _ = R.highs(lp)
+    r = O.solve(lp, O.Params(tol=1e-8, restart_metric="ndg"))
+    assert r.status == O.STATUS_OPTIMAL
+    assert abs(r.kkt.primal_obj - obj) / (1 + abs(obj)) < 1e-7
+
+
+def test_ndg_restart_sequence_differs_from_kkt_and_restarts_less_on_a_relaxation():
+    """On the 200 x 400 relaxation (seed 1) the gap metric restarts at different checks
+    than KKT_omega (3 against 4 restarts to 1e-4, 384 against 640 iterations)."""
+    lp = lpgen.mip_relaxation(1)
+    a = O.solve(lp, O.Params(tol=1e-4))
+    b = O.solve(lp, O.Params(tol=1e-4, restart_metric="ndg"))
+    assert [k for k, _ in a.check_trace] != [k for k, _ in b.check_trace]
+    assert (a.iters, a.restarts) == (640, 4) and (b.iters, b.restarts) == (384, 3)
