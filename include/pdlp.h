@@ -202,6 +202,18 @@ typedef struct {
                            ignored. */
   double halpern_reflection; /* rho of the Halpern variant, in [0, 1]: 1 (default)
                            reflected, 0 plain Halpern */
+  int restart_metric;   /* 0 (default): KKT restarts on the scaled KKT_omega; 1: the
+                           normalized duality gap of the original PDLP (one of its
+                           algorithmic variants; the paper is silent): for the current and
+                           the average point z, r = ||z - z_last||_omega (omega-weighted,
+                           scaled), rho = the maximum of the Lagrangian gap
+                           L(x, y^) - L(x^, y) over the points of X x Y within r of z,
+                           divided by r (by bisection on the step of the projected
+                           gradient path: 6 steps on its exponent, 44 halvings); the
+                           candidate with the smaller rho, the same three thresholds,
+                           and the restart point's rho as the next reference.  Adds 53
+                           small launches per KKT check.  Single LPs without halpern and
+                           bound_objective_rescaling only. */
 } pdlp_params;
 
 typedef struct {

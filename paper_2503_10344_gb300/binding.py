@@ -43,7 +43,8 @@ class PdlpParams(C.Structure):
                 ("persistent", C.c_int), ("autotune", C.c_int),
                 ("detect_infeasibility", C.c_int), ("debug_skip_barrier", C.c_int),
                 ("tiles", C.c_int), ("bound_objective_rescaling", C.c_int),
-                ("halpern", C.c_int), ("halpern_reflection", C.c_double)]
+                ("halpern", C.c_int), ("halpern_reflection", C.c_double),
+                ("restart_metric", C.c_int)]
 
 
 class PdlpResult(C.Structure):

@@ -107,11 +107,31 @@ struct DevState {
   // (z_a the anchor); the coefficients of the next step in both precisions, the steps
   // since the last restart (h_k), the reflection rho, the fixed-point residuals of the
   // latest step and of the epoch's first step (prev_cand holds the last check's)
-  int halpern, h_pad;
+  int halpern, restart_metric;  // restart_metric: 0 KKT_omega, 1 normalized duality gap
+  double ndg_last;              // normalized duality gap of the last restart point (A9b)
   long long h_k;
   double h_rho, h_res, h_r0;
   double ha_d, hb_d, hc_d;
   float ha_f, hb_f, hc_f, hf_pad;
+};
+
+// Normalized-duality-gap restarts (restart_metric = 1): the trust-region maximum of the
+// gap at each candidate, by bisection on the step t of z^(t) = proj(z + t M^-1 g):
+// one launch of k_ndg_eval per stage -- 0 the radius r and the dual norm N, 1 the test
+// of t0 2^63 (t0 = r / N), 2..7 the bisection over the exponent k of t0 2^k, 8..51 the
+// halvings of [t0 2^(k-1), t0 2^k], 52 the gap at the final lower end.
+constexpr int kNdgKSteps = 6;
+constexpr int kNdgHalvings = 44;
+constexpr int kNdgStages = 3 + kNdgKSteps + kNdgHalvings;
+struct NdgCand {
+  double r, nrm, t0, a, b, trial, rho;
+  int lo, hi, mid, fixed;  // fixed: t stays t0 2^63 (the region's far end is inside the ball)
+  int done, pad;           // done: rho is final (r = 0 or N = 0: rho = 0)
+};
+struct NdgState {
+  NdgCand c[2];  // current, average
+  int stage;
+  unsigned ticket;  // blocks of the running launch that have added their partials
 };
 
 // Halpern variant: passes of the power iteration for ||K~||_2 and the step size's

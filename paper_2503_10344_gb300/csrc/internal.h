@@ -145,6 +145,12 @@ struct KktRaw {
   // Halpern variant: its iterate and anchor (iterate type), reset to the candidate at a
   // restart (NULL off)
   void *hx, *hy, *hax, *hay;
+  // normalized-duality-gap restarts (NULL off): the scaled gap gradients premultiplied by
+  // D_c (columns) and D_r (rows) for (current, average), written by the KKT passes; the
+  // bisection state; 4 partials per block of k_ndg_eval (grid_e blocks)
+  double2 *ndg_gx, *ndg_gy;
+  NdgState* ndg;
+  double* ndg_part;
   double* chk_pts;  // [chk_cap x n] current point of the last checks (NULL: not kept)
   long long chk_cap;
   double *part_r, *part_c;                 // kPartR / kPartC partial rows of grid_r / grid_c
@@ -167,7 +173,8 @@ struct KktRaw {
 constexpr int kPartR = 11;
 constexpr int kPartC = 15;
 
-enum KktKernel { KK_PREP = 0, KK_ROWS = 1, KK_COLS = 2, KK_FINAL = 3, KK_APPLY = 4, KK_END = 5 };
+enum KktKernel { KK_PREP = 0, KK_ROWS = 1, KK_COLS = 2, KK_FINAL = 3, KK_APPLY = 4, KK_END = 5,
+                 KK_NDG = 6 };
 cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s);
 // Final outputs in the caller's convention: x clipped to [l,u], y sign-flipped
 // back on <=-rows.  Any pointer may be NULL.

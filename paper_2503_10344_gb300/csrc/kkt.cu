@@ -128,6 +128,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(KktRaw r) {
     const double kx[2] = {ax.a, ax.b};
     const double2 y2 = cand2(r.YG, i);
     const double yv[2] = {y2.x, y2.y};
+    // A9b: D_r times the scaled gap gradient q~ - K~ x~ = D_r (q - K x) of both candidates
+    if (r.ndg_gy) r.ndg_gy[i] = make_double2(dr * (dr * (q - kx[0])), dr * (dr * (q - kx[1])));
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       double rp = q - kx[k];
@@ -190,6 +192,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
     const double kty[2] = {aty.a, aty.b};
     const double2 x2 = cand2(r.XG, j);
     const double xv[2] = {x2.x, x2.y};
+    // A9b: D_c times the scaled gap gradient K~^T y~ - c~ = D_c (K^T y - c)
+    if (r.ndg_gx) r.ndg_gx[j] = make_double2(dc * (dc * (kty[0] - c)), dc * (dc * (kty[1] - c)));
     // lambda+ = lam, lambda- = 0 when lam > 0, else lambda+ = 0, lambda- = -lam: each
     // term below keeps only its nonzero part (the same values; the sign test is an
     // integer compare, so the float64 pipe does the arithmetic only)
@@ -234,6 +238,144 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(KktRaw r) {
 __device__ __forceinline__ bool inf_certificate(double obj, double mag, double res) {
   constexpr double eps_inf = 1e-8, kappa = 1e-9;
   return obj > 0.0 && obj > kappa * mag && res <= eps_inf * obj;
+}
+
+// A9b: one stage of the normalized duality gaps of both candidates (current, average)
+// at a check, in scaled space through the unscaled candidates X = D_c x~, Y = D_r y~:
+// for the trial steps t of the two candidates every block adds, over its columns and
+// rows, the squared omega-distance of z^(t) = (proj_[l,u](X + (t / omega) D_c g~_x),
+// proj_Y(Y + t omega D_r g~_y)) from z and the gap g~^T (z~^(t) - z~) (stage 0: the
+// squared radius from the last restart point and the squared dual norm N^2 =
+// ||g~_x||^2 / omega + omega ||g~_y||^2); the last block to finish adds the blocks'
+// partials in slot order and advances both candidates' bisection.  One LP.
+__device__ void ndg_advance(NdgState* g, const double* sum) {
+  const int stage = g->stage;
+  for (int c = 0; c < 2; ++c) {
+    NdgCand& k = g->c[c];
+    if (stage == 0) {
+      k.done = 0;
+      k.fixed = 0;
+      k.r = sqrt(sum[c]);
+      k.nrm = sqrt(sum[2 + c]);
+      k.rho = 0.0;
+      if (k.r == 0.0 || k.nrm == 0.0) {
+        k.done = 1;
+        continue;
+      }
+      k.t0 = k.r / k.nrm;
+      k.trial = ldexp(k.t0, 63);
+      continue;
+    }
+    if (k.done) continue;
+    const double d = sqrt(sum[c]);
+    if (stage == 1) {
+      if (d < k.r) {
+        k.fixed = 1;  // the far end t0 2^63 is inside the ball: t stays there
+      } else {
+        k.lo = -1;
+        k.hi = 63;
+        k.mid = (k.lo + k.hi) >> 1;
+        k.trial = ldexp(k.t0, k.mid);
+      }
+    } else if (stage < 2 + kNdgKSteps) {
+      if (k.fixed) continue;
+      if (d >= k.r) k.hi = k.mid; else k.lo = k.mid;
+      if (stage == 1 + kNdgKSteps) {
+        k.a = ldexp(k.t0, k.hi - 1);
+        k.b = ldexp(k.t0, k.hi);
+        k.trial = 0.5 * (k.a + k.b);
+      } else {
+        k.mid = (k.lo + k.hi) >> 1;  // floor, also for lo = -1
+        k.trial = ldexp(k.t0, k.mid);
+      }
+    } else if (stage < 2 + kNdgKSteps + kNdgHalvings) {
+      if (k.fixed) continue;
+      if (d >= k.r) k.b = k.trial; else k.a = k.trial;
+      k.trial = stage == 1 + kNdgKSteps + kNdgHalvings ? k.a : 0.5 * (k.a + k.b);
+    } else {
+      k.rho = sum[2 + c] / k.r;  // the gap at the final step over the radius
+      k.done = 1;
+    }
+  }
+  g->stage = stage + 1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
+  pdl_enter();
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0 || st->init_pending) return;
+  NdgState* g = r.ndg;
+  const int stage = g->stage;  // the same in every block: written by an earlier launch
+  if (stage >= kNdgStages) return;
+  const double om = st->omega, iom = st->inv_omega;
+  const double s0 = g->c[0].trial, s1 = g->c[1].trial;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * kBlock;
+  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+    const double2 X = r.XG[j], D = r.ndg_gx[j];
+    const double idc = r.inv_dc[j];
+    if (stage == 0) {
+      const double xl = r.Xl[j];
+      const double d0 = (X.x - xl) * idc, d1 = (X.y - xl) * idc;
+      acc[0] += om * d0 * d0;
+      acc[1] += om * d1 * d1;
+      const double g0 = D.x * idc, g1 = D.y * idc;
+      acc[2] += g0 * g0 * iom;
+      acc[3] += g1 * g1 * iom;
+    } else {
+      const double l = r.l[j], u = r.u[j];
+      const double d0 = (fmin(fmax(X.x + (s0 * iom) * D.x, l), u) - X.x) * idc;
+      const double d1 = (fmin(fmax(X.y + (s1 * iom) * D.y, l), u) - X.y) * idc;
+      acc[0] += om * d0 * d0;
+      acc[1] += om * d1 * d1;
+      acc[2] += (D.x * idc) * d0;
+      acc[3] += (D.y * idc) * d1;
+    }
+  }
+  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+    const double2 Y = r.YG[i], E = r.ndg_gy[i];
+    const double idr = r.inv_dr[i];
+    if (stage == 0) {
+      const double yl = r.Yl[i];
+      const double d0 = (Y.x - yl) * idr, d1 = (Y.y - yl) * idr;
+      acc[0] += d0 * d0 * iom;
+      acc[1] += d1 * d1 * iom;
+      const double g0 = E.x * idr, g1 = E.y * idr;
+      acc[2] += om * g0 * g0;
+      acc[3] += om * g1 * g1;
+    } else {
+      const bool eq = r.row_kind[i] == 1;
+      double y0 = Y.x + (s0 * om) * E.x, y1 = Y.y + (s1 * om) * E.y;
+      if (!eq) {
+        y0 = fmax(y0, 0.0);
+        y1 = fmax(y1, 0.0);
+      }
+      const double d0 = (y0 - Y.x) * idr, d1 = (y1 - Y.y) * idr;
+      acc[0] += d0 * d0 * iom;
+      acc[1] += d1 * d1 * iom;
+      acc[2] += (E.x * idr) * d0;
+      acc[3] += (E.y * idr) * d1;
+    }
+  }
+  double out[4];
+  block_sum_rs<4>(acc, out);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) r.ndg_part[(size_t)k * gridDim.x + blockIdx.x] = out[k];
+    __threadfence();
+    last = atomicAdd(&g->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double sum[4];
+  for (int k = 0; k < 4; ++k) {
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(r.ndg_part + (size_t)k * gridDim.x + b);
+    sum[k] = t;
+  }
+  g->ticket = 0;
+  ndg_advance(g, sum);
 }
 
 __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
@@ -338,13 +480,14 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
       st->restart_kind = 1;
     }
   } else if (st->status == 0 && st->restarts_on && st->iters % st->period == 0) {
-    // A9: KKT restart on the scaled KKT_omega
+    // A9: KKT restart on the scaled KKT_omega (A9b: on the normalized duality gap)
     const double om = st->omega;
-    const double mc = kkt_omega(om, pr[2], pc[2], gap2[0]);
-    const double ma = kkt_omega(om, pr[3], pc[3], gap2[1]);
+    const bool ndg = st->restart_metric == 1 && r.ndg != nullptr;
+    const double mc = ndg ? r.ndg->c[0].rho : kkt_omega(om, pr[2], pc[2], gap2[0]);
+    const double ma = ndg ? r.ndg->c[1].rho : kkt_omega(om, pr[3], pc[3], gap2[1]);
     const int ua = ma < mc;
     const double mcand = ua ? ma : mc;
-    const double mlast = kkt_omega(om, st->last_rp2, st->last_rd2, st->last_gap2);
+    const double mlast = ndg ? st->ndg_last : kkt_omega(om, st->last_rp2, st->last_rd2, st->last_gap2);
     const bool do_restart = mcand <= 0.2 * mlast ||
                             (mcand <= 0.8 * mlast && mcand > st->prev_cand) ||
                             (double)(st->iters - st->last_restart_it) >= 0.36 * (double)st->iters;
@@ -367,6 +510,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
       st->last_rp2 = pr[2 + ua];
       st->last_rd2 = pc[2 + ua];
       st->last_gap2 = gap2[ua];
+      st->ndg_last = mcand;
       st->prev_cand = INFINITY;
       st->last_restart_it = st->iters;
       st->restarts += 1;
@@ -457,6 +601,7 @@ __global__ void k_kkt_end(KktRaw r) {
   }
   st->restart_kind = 0;
   st->check_due = 0;
+  if (r.ndg && k == 0) r.ndg->stage = 0;  // the next check's gaps start from stage 0
 }
 
 __global__ void __launch_bounds__(kBlock) k_output(KktRaw r, double* x_out, double* y_out,
@@ -531,6 +676,8 @@ cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cud
       return launch_pdl(k_kkt_apply<double>, egrid(r), kBlock, s, r);
     case KK_END:
       return launch_pdl(k_kkt_end, (r.count + kBlock - 1) / kBlock, kBlock, s, r);
+    case KK_NDG:
+      return launch_pdl(k_ndg_eval, r.grid_e, kBlock, s, r);
     default: return cudaErrorInvalidValue;
   }
 }

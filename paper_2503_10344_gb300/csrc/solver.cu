@@ -100,6 +100,9 @@ struct Bufs {
   float2 *tpart_a, *tpart_t, *trow_a, *trow_t, *tlong_a, *tlong_t;
   int *tick_a, *tick_t, *tlp_a, *tlp_t;  // tickets; [item0[0..count], lng0[0..count]]
   size_t tcap_a, tcap_t;
+  double2 *ndg_gx, *ndg_gy;  // normalized-duality-gap restarts (NULL off)
+  NdgState* ndg;
+  double* ndg_part;
 };
 
 constexpr int kMaxLongBlocks = 1024;
@@ -118,7 +121,8 @@ static void elem_sizes(int precision, size_t* it_bytes, size_t* val_bytes) {
   }
 }
 
-static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precision) {
+static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precision,
+                    bool ndg = false) {
   size_t eb, vb;
   elem_sizes(precision, &eb, &vb);
   const size_t G = (size_t)max_blocks() + kMaxLongBlocks;
@@ -195,6 +199,11 @@ static size_t carve(Arena& ar, Bufs& b, int m, int n, long long nnz, int precisi
     tile_tmp = tile_tmp_ints(std::max(m, n));
   }
   b.tmp = (int*)ar.take(4 * std::max(tmp_ints, tile_tmp));
+  // normalized-duality-gap restarts: gradients of both candidates, bisection state, partials
+  b.ndg_gx = ndg ? (double2*)ar.take(16 * N) : nullptr;
+  b.ndg_gy = ndg ? (double2*)ar.take(16 * M) : nullptr;
+  b.ndg = ndg ? (NdgState*)ar.take(sizeof(NdgState)) : nullptr;
+  b.ndg_part = ndg ? (double*)ar.take(8 * 4 * G) : nullptr;
   return ar.off + 256;
 }
 
@@ -319,10 +328,22 @@ struct Solve {
       default: return launch_iter_pat(which, lanes, ir, s);
     }
   }
+  // normalized-duality-gap restarts: the stages of both candidates' gaps, after the
+  // passes (which write the gradients) and before the restart decision
+  cudaError_t ndg_stages() {
+    if (kr.ndg == nullptr) return cudaSuccess;
+    g_launches += kNdgStages;
+    for (int k = 0; k < kNdgStages; ++k) {
+      const cudaError_t e = launch_kkt(KK_NDG, lanes_ka, lanes_kt, kr, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   cudaError_t kkt_block() {
     cudaError_t e;
     if (s2 == nullptr) {
       for (int k : {KK_PREP, KK_ROWS, KK_COLS, KK_FINAL, KK_APPLY, KK_END}) {
+        if (k == KK_FINAL && (e = ndg_stages()) != cudaSuccess) return e;
         ++g_launches;
         if ((e = launch_kkt(k, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
       }
@@ -336,6 +357,7 @@ struct Solve {
     if ((e = cudaEventRecord(ev_join, s2)) != cudaSuccess) return e;
     if ((e = launch_kkt(KK_ROWS, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, ev_join, 0)) != cudaSuccess) return e;
+    if ((e = ndg_stages()) != cudaSuccess) return e;
     for (int k : {KK_FINAL, KK_APPLY, KK_END})
       if ((e = launch_kkt(k, lanes_ka, lanes_kt, kr, s)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -403,6 +425,11 @@ static int check_inputs(const pdlp_csr* A, const void* b, const void* sense, con
     return fail(PDLP_ERR_INVALID_INPUT, "halpern_reflection must lie in [0, 1]");
   if (p->halpern && (p->persistent || p->tiles))
     return fail(PDLP_ERR_INVALID_INPUT, "halpern runs with persistent = 0 and tiles = 0 only");
+  if (p->restart_metric != 0 && p->restart_metric != 1)
+    return fail(PDLP_ERR_INVALID_INPUT, "restart_metric must be 0 or 1");
+  if (p->restart_metric == 1 && (p->halpern || p->bound_objective_rescaling))
+    return fail(PDLP_ERR_INVALID_INPUT,
+                "restart_metric = 1 runs without halpern and bound_objective_rescaling");
   return PDLP_OK;
 }
 
@@ -729,7 +756,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   memset(r, 0, sizeof(*r));
   Bufs bf;
   Arena dry{nullptr, 0};
-  const size_t need = carve(dry, bf, m, n, nnz, p->precision);
+  const size_t need = carve(dry, bf, m, n, nnz, p->precision, p->restart_metric == 1);
   void* own_ws = nullptr;
   if (!workspace) {
     cudaError_t e = cudaMallocAsync(&own_ws, need, s);
@@ -746,7 +773,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
     }
   } freer{own_ws, s};
   Arena ar{(char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255), 0};
-  carve(ar, bf, m, n, nnz, p->precision);
+  carve(ar, bf, m, n, nnz, p->precision, p->restart_metric == 1);
 
   // no_alloc: nothing below creates a CUDA object or allocates memory (no events,
   // graphs, streams or pinned buffers); phases are timed with host clocks
@@ -865,6 +892,12 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   kr.grid_e = ge;
   kr.scaled = scaled; kr.fp32 = fp32;
   kr.st = bf.st;
+  if (p->restart_metric == 1) {
+    kr.ndg_gx = bf.ndg_gx;
+    kr.ndg_gy = bf.ndg_gy;
+    kr.ndg = bf.ndg;
+    kr.ndg_part = bf.ndg_part;
+  }
   if (p->halpern) {
     // the Halpern iterate lives in the running-sum buffers (no averages in this variant)
     // and its anchor in the scaling statistics' (used only by the setup); the initial
@@ -926,6 +959,8 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   hs.check_due = 1;
   hs.init_pending = 1;
   hs.prev_cand = INFINITY;
+  hs.restart_metric = p->restart_metric;
+  hs.ndg_last = INFINITY;
   hs.iter_limit = p->iter_limit;
   hs.period = p->check_period;
   hs.adaptive = p->adaptive_step && !p->halpern ? 1 : 0;
@@ -972,6 +1007,7 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   if (m) CUDA_TRY(cudaMemsetAsync(bf.sum_y, 0, eb * m, s));
   CUDA_TRY(cudaMemsetAsync(bf.Xl, 0, 8 * (size_t)n, s));
   if (m) CUDA_TRY(cudaMemsetAsync(bf.Yl, 0, 8 * (size_t)m, s));
+  if (bf.ndg) CUDA_TRY(cudaMemsetAsync(bf.ndg, 0, sizeof(NdgState), s));
 
   Solve sv{m, n, nnz, mode, lanes_a, lanes_t, lanes_ka, lanes_kt, ir, kr, s, 0};
   // the autotuner creates a stream, events and graphs: never without allocation; the
@@ -1497,6 +1533,8 @@ static int solve_batch(int count, const pdlp_csr* const* A, const double* const*
   if (p->bound_objective_rescaling)
     return fail(PDLP_ERR_INVALID_INPUT, "bound_objective_rescaling is for single LPs, not batches");
   if (p->halpern) return fail(PDLP_ERR_INVALID_INPUT, "halpern is for single LPs, not batches");
+  if (p->restart_metric)
+    return fail(PDLP_ERR_INVALID_INPUT, "restart_metric = 1 is for single LPs, not batches");
   if (p->persistent == 2)
     return fail(PDLP_ERR_INVALID_INPUT, "persistent = 2 (one block) is for single LPs, not batches");
   g_launches = 0;
@@ -2148,6 +2186,7 @@ int pdlp_default_params(pdlp_params* p) {
   p->bound_objective_rescaling = 0;
   p->halpern = 0;
   p->halpern_reflection = 1.0;
+  p->restart_metric = 0;
   return PDLP_OK;
 }
 
@@ -2160,7 +2199,7 @@ size_t pdlp_workspace_size(int32_t m, int32_t n, int64_t nnz, const pdlp_params*
   }
   Bufs b;
   Arena ar{nullptr, 0};
-  return carve(ar, b, m, n, nnz, p->precision);
+  return carve(ar, b, m, n, nnz, p->precision, p->restart_metric == 1);
 }
 
 int pdlp_solve_device(const pdlp_csr* A, const double* b, const char* sense, const double* c,

@@ -146,3 +146,12 @@ def test_bound_objective_rescaling_parameter_is_checked(P, lp):
 ])
 def test_halpern_parameters_are_checked(P, lp, kw, needle):
     _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(**kw)), needle)
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(restart_metric=2), "restart_metric must be 0 or 1"),
+    (dict(restart_metric=1, halpern=1), "restart_metric = 1 runs without halpern"),
+    (dict(restart_metric=1, bound_objective_rescaling=1), "restart_metric = 1 runs without halpern"),
+])
+def test_restart_metric_parameter_is_checked(P, lp, kw, needle):
+    _rejected(P, lambda: P.pdlp_solve(lp, P.default_params(**kw)), needle)
