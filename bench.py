@@ -64,6 +64,8 @@ def parse():
                          "copies into shared memory); 2 warp tiles")
     ap.add_argument("--halpern", type=int, default=0, choices=[0, 1],
                     help="1: the reflected restarted Halpern PDHG variant (single LPs)")
+    ap.add_argument("--restart-metric", type=int, default=0, choices=[0, 1],
+                    help="1: normalized-duality-gap restarts (single LPs)")
     for k in ("lanes-a", "lanes-at", "lanes-kkt-a", "lanes-kkt-at"):
         ap.add_argument("--" + k, type=int, default=0, help="SpMV lanes per row (0 = automatic)")
     return ap.parse_args()
@@ -72,7 +74,7 @@ def parse():
 def lane_params(args) -> dict:
     return {"lanes_A": args.lanes_a, "lanes_AT": args.lanes_at, "lanes_kkt_A": args.lanes_kkt_a,
             "lanes_kkt_AT": args.lanes_kkt_at, "persistent": args.persistent, "tiles": args.tiles,
-            "halpern": args.halpern}
+            "halpern": args.halpern, "restart_metric": args.restart_metric}
 
 
 def dist_env():
@@ -728,8 +730,9 @@ def run_batch(args):
 
 def run_variants(args):
     """The algorithmic variants against the default iteration on the same instances and
-    precision modes: bound-objective rescaling (pdlp_params.bound_objective_rescaling) and
-    the reflected restarted Halpern PDHG (pdlp_params.halpern); iterations and
+    precision modes: bound-objective rescaling (pdlp_params.bound_objective_rescaling), the
+    reflected restarted Halpern PDHG (pdlp_params.halpern) and normalized-duality-gap
+    restarts (pdlp_params.restart_metric = 1); iterations and
     iteration-phase time to rel. KKT 1e-4 (float32 / pattern on the covering LPs and the
     energy system, float64 on the 200 x 400 relaxations)."""
     import torch
@@ -748,7 +751,7 @@ def run_variants(args):
         d = P.DeviceLP(lp)
         row = {"instance": name, "precision": prec}
         for key, kw in (("default", {}), ("rescaled", {"bound_objective_rescaling": 1}),
-                        ("halpern", {"halpern": 1})):
+                        ("halpern", {"halpern": 1}), ("ndg_restarts", {"restart_metric": 1})):
             prm = P.default_params(tol=1e-4, precision=prec, iter_limit=200_000, **kw)
             P.pdlp_solve_device(d, prm)  # warm
             torch.cuda.synchronize()
@@ -758,8 +761,9 @@ def run_variants(args):
                 "solve_s": r["solve_s"], "setup_s": r["setup_s"], "rel_kkt": r["rel_kkt"],
                 "primal_obj": r["primal_obj"]}
         rows.append(row)
-    print(json.dumps({"workload": "bound-objective rescaling and reflected restarted Halpern "
-                                  "PDHG against the default iteration",
+    print(json.dumps({"workload": "bound-objective rescaling, reflected restarted Halpern "
+                                  "PDHG and normalized-duality-gap restarts against the default "
+                                  "iteration",
                       "tol": 1e-4, "runs": rows}), flush=True)
 
 
@@ -809,7 +813,7 @@ def run_energy(args):
             "data": "synthetic",
             "config": {"workload": f"energy system 8760h x 20 regions x 6 techs, m={lp.m}, n={lp.n}, "
                                    f"nnz={lp.nnz}, tol=1e-4", "precision": prec,
-                       "halpern": args.halpern},
+                       "halpern": args.halpern, "restart_metric": args.restart_metric},
             "time_to_tol_s": sum(ms) / 1e3 / args.steps, "iters_per_solve": iters / args.steps,
             "primal_obj": res["primal_obj"], "restarts": res["restarts"],
             "status": res["status"], "rel_kkt": res["rel_kkt"], "setup_ms": 1e3 * res["setup_s"],

@@ -366,14 +366,17 @@ __global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
     last = atomicAdd(&g->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
+  // the last block: every thread adds a strided share of the partials (read through L2),
+  // then the block's fixed-order reduction
   __threadfence();
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kBlock)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += __ldcg(r.ndg_part + (size_t)k * gridDim.x + b);
   double sum[4];
-  for (int k = 0; k < 4; ++k) {
-    double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(r.ndg_part + (size_t)k * gridDim.x + b);
-    sum[k] = t;
-  }
+  block_sum_rs<4>(v, sum);
+  if (threadIdx.x != 0) return;
   g->ticket = 0;
   ndg_advance(g, sum);
 }
