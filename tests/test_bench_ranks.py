@@ -128,14 +128,14 @@ def test_all_core_oracle_sample_times_replicas_started_together():
 def test_roofline_traffic_comes_from_the_committed_capture():
     """bench.py reads the DRAM bytes per launch of its roofline kernel from the committed
     ncu summary, and reports none for a kernel or precision that was not captured."""
-    assert bench.ncu_traffic("dual_step", "bf16") == 7_759_744
-    assert bench.ncu_traffic("primal_step", "bf16") == 11_004_928
-    assert bench.ncu_traffic("dual_step", "fp32", "energy") == 116_404_352
+    assert bench.ncu_traffic("dual_step", "bf16") == 7_759_360
+    assert bench.ncu_traffic("primal_step", "bf16") == 11_005_056
+    assert bench.ncu_traffic("dual_step", "fp32", "energy") == 116_110_080
     assert bench.ncu_traffic("dual_step", "fp64") is None
     assert bench.ncu_traffic("persistent_attempt", "bf16") is None
     assert bench.ncu_traffic("dual_step", "bf16", "batch") is None
     kt = {"primal_step": {"ms": 0.033, "bytes": 169598404.0},
           "dual_step": {"ms": 0.042, "bytes": 135255364.0}}
     roof = bench.kernel_roofline(kt, 6794.5, "measured", "energy", "fp32")
-    assert roof["kernel"] == "dual_step" and roof["traffic"] == 116_404_352
+    assert roof["kernel"] == "dual_step" and roof["traffic"] == 116_110_080
     assert bench.kernel_roofline(kt, 6794.5, "measured")["traffic"] is None
