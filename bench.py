@@ -192,6 +192,42 @@ print(json.dumps({{"iters": r.iters, "seconds": dt, "status": r.status, "rel_kkt
 """
 
 
+CPU_WORKLOAD_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import lpgen
+from oracle import pdlp_oracle as O
+lps = {maker}
+setup = total = 0.0
+its = 0
+for lp in lps:
+    t = time.perf_counter()
+    O.solve(lp, O.Params(iter_limit=0, terminate=False))
+    setup += time.perf_counter() - t
+    t = time.perf_counter()
+    r = O.solve(lp, O.Params(iter_limit={iters}, terminate=False))
+    total += time.perf_counter() - t
+    its += r.iters
+print(json.dumps({{"iters": its, "setup_s": setup, "total_s": total, "lps": len(lps)}}))
+"""
+
+
+def cpu_oracle_workload(maker: str, iters: int, what: str) -> dict:
+    """The float64 oracle, as it stands, on a bounded sample of another workload, one core:
+    each LP of `maker` solved once with no iteration (its setup: canonical form, scaling,
+    the check at the start) and once for `iters` iterations; iterations per second of the
+    difference."""
+    code = CPU_WORKLOAD_SNIPPET.format(root=ROOT, maker=maker, iters=iters)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         env=_oracle_env(), check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    run_s = d["total_s"] - d["setup_s"]
+    return {"value": d["iters"] / run_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "setup_s": d["setup_s"] / d["lps"],
+            "sample": f"{iters} iterations of the float64 oracle on {what} "
+                      f"({d['iters']} in all, {run_s:.1f} s after {d['setup_s']:.1f} s of setup)"}
+
+
 def _oracle_env():
     return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
 
@@ -384,6 +420,17 @@ def run_gpu(args):
                 extra[key] = fn(args, dev, stream, peak)
             except Exception as e:  # reported, never silently replaced
                 extra[key] = {"error": str(e)[:300]}
+        if not args.no_cpu_baseline:
+            # the oracle beside the two workloads that stream from HBM, on bounded samples
+            for key, maker, iters, what in (
+                    ("energy", "[lpgen.energy_system()]", 16, "the energy system"),
+                    ("batch", "lpgen.set_cover_batch(count=8)", 64,
+                     "each of the first 8 sub-LPs of the batch")):
+                if key in extra and "error" not in extra[key]:
+                    try:
+                        extra[key]["cpu_baseline"] = cpu_oracle_workload(maker, iters, what)
+                    except Exception as e:
+                        extra[key]["cpu_baseline"] = {"error": str(e)[:200]}
     if rank == 0:
         prec_used = {0: "fp64", 1: "fp32", 2: "fp32 iterates, bf16 matrix",
                      3: "fp32 iterates, pattern matrix"}[res["precision_used"]]
