@@ -51,7 +51,7 @@ def parse():
                     help="only time the fused kernels (pdlp_time_kernels) and print them")
     ap.add_argument("--reps", type=int, default=200)
     ap.add_argument("--workload", default="set_cover",
-                    choices=["set_cover", "batch", "energy", "fp", "c1", "variants"],
+                    choices=["set_cover", "batch", "energy", "fp", "c1", "variants", "warmstart"],
                     help="batch: 256 uneven covering sub-LPs (m in [2000, 40000], n = 4m, "
                          "10-50 %% of the columns fixed), solved together by pdlp_solve_batch; "
                          "c1 (with --kernels-only): the 200 x 400 MIP relaxation")
@@ -415,7 +415,8 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and ws == 1 and not args.no_extra:
         # the other workloads, one GPU each (replicas only under torchrun: rank 0 alone)
-        for key, fn in (("c1", c1_section), ("energy", energy_section), ("batch", batch_section)):
+        for key, fn in (("c1", c1_section), ("energy", energy_section), ("batch", batch_section),
+                        ("c5", c5_section)):
             try:
                 extra[key] = fn(args, dev, stream, peak)
             except Exception as e:  # reported, never silently replaced
@@ -608,6 +609,21 @@ def batch_section(args, dev, stream, peak):
             "iters_per_lp": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
             "persistent": persistent, "autotuned": autotuned,
             "roofline": kernel_roofline(kt, pk, src), "clocks": clk.summary()}
+
+
+def c5_section(args, dev, stream, peak, train=160, test=20, mmin=5_000, mmax=20_000,
+               epochs=12):
+    """The learned warm start at a reduced scale (the full one: ``--workload warmstart``):
+    covering LPs with m ~ U[mmin, mmax], n = 4m; float64 PDLP labels at 1e-6, the network
+    trained on the GPU, then every held-out LP solved cold and warm to 1e-4 (bfloat16 /
+    pattern iterates); iterations and times (geometric means), fallback rate."""
+    from paper_2503_10344_gb300 import warmstart as W
+    res = W.run(train, test, mmin, mmax, epochs, 4, 1e-3, log=lambda *a: None)
+    s = res["summary"]
+    return {"workload": f"learned warm start: {train} training + {test} held-out covering LPs, "
+                        f"m ~ U[{mmin}, {mmax}], n = 4m, {epochs} epochs (reduced scale)",
+            "generate_s": res["generate_s"], "label_s": res["label_s"], "train_s": res["train_s"],
+            "loss_first": res["loss_first"], "loss_last": res["loss_last"], **s}
 
 
 def c1_section(args, dev, stream, peak):
@@ -814,6 +830,18 @@ def run_variants(args):
                       "tol": 1e-4, "runs": rows}), flush=True)
 
 
+def run_warmstart(args):
+    """The learned warm start at full scale: 2,000 training covering LPs and 100 held-out
+    ones, m ~ U[5,000, 50,000], n = 4m, 30 epochs; one JSON line with the summary."""
+    import __graft_entry__ as G
+    G.build()
+    from paper_2503_10344_gb300 import warmstart as W
+    res = W.run(2000, 100, 5_000, 50_000, 30, 4, 1e-3, log=lambda *a: None)
+    res.pop("per_lp", None)
+    res.pop("losses", None)
+    print(json.dumps({"workload": "learned warm start, full scale", **res}), flush=True)
+
+
 def run_energy(args):
     """The energy-system LP (8760 h x 20 regions x 6 technologies, 2.1M rows, 2.45M
     columns, 7.9M nonzeros) to rel. KKT 1e-4 with float32 iterates: the workload whose
@@ -919,7 +947,8 @@ def single_gpu_rank(args) -> bool:
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "gpu" and (a.kernels_only or a.workload in ("energy", "fp", "variants")) \
+    if a.impl == "gpu" and (a.kernels_only or a.workload in ("energy", "fp", "variants",
+                                                              "warmstart")) \
             and not single_gpu_rank(a):
         sys.exit(0)
     if a.kernels_only and a.impl == "gpu":
@@ -932,6 +961,8 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "variants" and a.impl == "gpu":
         run_variants(a)
+    elif a.workload == "warmstart" and a.impl == "gpu":
+        run_warmstart(a)
     elif a.workload == "c1" and a.impl == "gpu":
         sys.exit("--workload c1 runs with --kernels-only (its solves are the default line's c1 section)")
     elif a.impl == "reference":
