@@ -835,8 +835,12 @@ static int solve_device(const pdlp_csr* A, const double* b, const char* sense, c
   const int gp = gp_short + std::min(nlong_t, kMaxLongBlocks);
   const int gd = gd_short + std::min(nlong_a, kMaxLongBlocks);
   const int ge = grid_for(std::max(m, n), MB);
-  // KKT passes: at most two blocks per SM keeps the one-block final reduction short
-  const int KB = 2 * device_sm_count();
+  // KKT passes: up to six blocks per SM.  The passes over A and A^T run side by side on
+  // two graph branches; measured per KKT block (prep, both passes, final, apply, end):
+  // two blocks per SM 687 / 130 us on the energy system / covering LP, three 642 / 107,
+  // four 615 / 109, six 615 / 100, eight 620 / 101 (the final reduction's longer partial
+  // lists cost less than the passes gain from more warps in flight)
+  const int KB = 6 * device_sm_count();
   const int gr_short = grid_for(((long long)std::max(m, 1) + 31) / 32 * 32, KB);
   const int gc_short = grid_for(((long long)n + 31) / 32 * 32, KB);
   const int gr = gr_short + std::min(nlong_a, kMaxLongBlocks);
