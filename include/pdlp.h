@@ -403,8 +403,9 @@ int pdlp_solve_batch_device(int count, const pdlp_csr* const* A, const double* c
                             void* stream);
 
 /* Device workspace, in bytes, that pdlp_solve_device needs for this size and
- * these parameters (precision mode and value format decide it).  Returns 0 on
- * invalid sizes.  The bound holds for every value pattern. */
+ * these parameters (the precision mode decides it, and restart_metric = 1 adds
+ * 16 (m + n) bytes for the gap gradients).  Returns 0 on invalid sizes.  The bound
+ * holds for every value pattern. */
 size_t pdlp_workspace_size(int32_t m, int32_t n, int64_t nnz, const pdlp_params* p);
 
 /* Solve eq. (1) from DEVICE buffers, in stream order.
