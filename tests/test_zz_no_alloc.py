@@ -55,24 +55,27 @@ def long_column_lp(m=6000, n=3000, seed=5):
                      np.zeros(n), np.ones(n), np.zeros(n, np.uint8), "long_columns")
 
 
-CASES = [(lambda: lpgen.mip_relaxation(1), "fp64", 0, 0),
-         (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16", 0, 0),
-         (lambda: long_column_lp(), "fp32", 0, 0),
-         (lambda: lpgen.mip_relaxation(2), "fp64", 1, 0),
-         (lambda: lpgen.set_cover(8, m=2000, n=8000), "fp32", 1, 0),
-         # one block with the LP in shared memory; bound-objective rescaling
-         (lambda: lpgen.mip_relaxation(3), "fp64", 2, 0),
-         (lambda: lpgen.mip_relaxation(4), "fp64", 0, 1),
-         (lambda: lpgen.set_cover(9, m=2000, n=8000), "bf16", 0, 1)]
+CASES = [(lambda: lpgen.mip_relaxation(1), "fp64", 0, {}),
+         (lambda: lpgen.set_cover(7, m=2000, n=8000), "bf16", 0, {}),
+         (lambda: long_column_lp(), "fp32", 0, {}),
+         (lambda: lpgen.mip_relaxation(2), "fp64", 1, {}),
+         (lambda: lpgen.set_cover(8, m=2000, n=8000), "fp32", 1, {}),
+         # one block with the LP in shared memory; the algorithmic variants
+         (lambda: lpgen.mip_relaxation(3), "fp64", 2, {}),
+         (lambda: lpgen.mip_relaxation(4), "fp64", 0, {"bound_objective_rescaling": 1}),
+         (lambda: lpgen.set_cover(9, m=2000, n=8000), "bf16", 0, {"bound_objective_rescaling": 1}),
+         (lambda: lpgen.mip_relaxation(5), "fp64", 0, {"halpern": 1}),
+         (lambda: lpgen.set_cover(10, m=2000, n=8000), "fp32", 0, {"halpern": 1}),
+         (lambda: lpgen.mip_relaxation(6), "fp64", 0, {"restart_metric": 1}),
+         (lambda: lpgen.set_cover(11, m=2000, n=8000), "bf16", 1, {"restart_metric": 1})]
 
 
-@pytest.mark.parametrize("maker,prec,persistent,rescale", CASES)
-def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec, persistent, rescale):
+@pytest.mark.parametrize("maker,prec,persistent,variant", CASES)
+def test_noalloc_matches_solve_device_on_two_calls_in_a_row(P, maker, prec, persistent, variant):
     import torch
     lp = maker()
     d = P.DeviceLP(lp)
-    prm = P.default_params(tol=1e-6, precision=prec, persistent=persistent,
-                           bound_objective_rescaling=rescale)
+    prm = P.default_params(tol=1e-6, precision=prec, persistent=persistent, **variant)
     assert P.workspace_size(lp.m, lp.n, lp.nnz, prm) <= P.binding.NOALLOC_BYTES
     xr, yr, rr = P.pdlp_solve_device(d, prm)
     xr, yr = xr.cpu().numpy(), yr.cpu().numpy()
