@@ -123,6 +123,8 @@ struct DevState {
 constexpr int kNdgKSteps = 6;
 constexpr int kNdgHalvings = 44;
 constexpr int kNdgStages = 3 + kNdgKSteps + kNdgHalvings;
+// LPs with at most this many columns and rows run every stage in one block (one launch)
+constexpr int kNdgOneBlock = 4096;
 struct NdgCand {
   double r, nrm, t0, a, b, trial, rho;
   int lo, hi, mid, fixed;  // fixed: t stays t0 2^63 (the region's far end is inside the ball)

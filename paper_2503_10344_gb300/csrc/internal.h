@@ -174,7 +174,7 @@ constexpr int kPartR = 11;
 constexpr int kPartC = 15;
 
 enum KktKernel { KK_PREP = 0, KK_ROWS = 1, KK_COLS = 2, KK_FINAL = 3, KK_APPLY = 4, KK_END = 5,
-                 KK_NDG = 6 };
+                 KK_NDG = 6, KK_NDG_BLOCK = 7 };
 cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cudaStream_t s);
 // Final outputs in the caller's convention: x clipped to [l,u], y sign-flipped
 // back on <=-rows.  Any pointer may be NULL.

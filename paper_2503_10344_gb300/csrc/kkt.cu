@@ -300,18 +300,13 @@ __device__ void ndg_advance(NdgState* g, const double* sum) {
   g->stage = stage + 1;
 }
 
-__global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
-  pdl_enter();
-  DevState* st = r.st;
-  if (!st->check_due || st->status != 0 || st->init_pending) return;
-  NdgState* g = r.ndg;
-  const int stage = g->stage;  // the same in every block: written by an earlier launch
-  if (stage >= kNdgStages) return;
-  const double om = st->omega, iom = st->inv_omega;
-  const double s0 = g->c[0].trial, s1 = g->c[1].trial;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const long long stride = (long long)gridDim.x * kBlock;
-  for (long long j = (long long)blockIdx.x * kBlock + threadIdx.x; j < r.n; j += stride) {
+// one stage's partials of this thread over its columns and rows (strided by `stride`
+// from `first`): stage 0 the squared radii and dual norms, later the squared distances
+// and the gaps at the trial steps s0, s1
+__device__ __forceinline__ void ndg_stage_sums(const KktRaw& r, int stage, double om, double iom,
+                                               double s0, double s1, long long first,
+                                               long long stride, double (&acc)[4]) {
+  for (long long j = first; j < r.n; j += stride) {
     const double2 X = r.XG[j], D = r.ndg_gx[j];
     const double idc = r.inv_dc[j];
     if (stage == 0) {
@@ -332,7 +327,7 @@ __global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
       acc[3] += (D.y * idc) * d1;
     }
   }
-  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < r.m; i += stride) {
+  for (long long i = first; i < r.m; i += stride) {
     const double2 Y = r.YG[i], E = r.ndg_gy[i];
     const double idr = r.inv_dr[i];
     if (stage == 0) {
@@ -357,6 +352,19 @@ __global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
       acc[3] += (E.y * idr) * d1;
     }
   }
+}
+
+__global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
+  pdl_enter();
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0 || st->init_pending) return;
+  NdgState* g = r.ndg;
+  const int stage = g->stage;  // the same in every block: written by an earlier launch
+  if (stage >= kNdgStages) return;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  ndg_stage_sums(r, stage, st->omega, st->inv_omega, g->c[0].trial, g->c[1].trial,
+                 (long long)blockIdx.x * kBlock + threadIdx.x, (long long)gridDim.x * kBlock,
+                 acc);
   double out[4];
   block_sum_rs<4>(acc, out);
   __shared__ int last;
@@ -379,6 +387,25 @@ __global__ void __launch_bounds__(kBlock) k_ndg_eval(KktRaw r) {
   if (threadIdx.x != 0) return;
   g->ticket = 0;
   ndg_advance(g, sum);
+}
+
+// All the stages in one block (small LPs: n + m <= kNdgOneBlock), the block's reduction
+// in place of the last-block hand-over; the same partial sums in the same order per
+// thread, added in another order than k_ndg_eval's.
+__global__ void __launch_bounds__(kBlock) k_ndg_block(KktRaw r) {
+  pdl_enter();
+  DevState* st = r.st;
+  if (!st->check_due || st->status != 0 || st->init_pending) return;
+  NdgState* g = r.ndg;
+  const double om = st->omega, iom = st->inv_omega;
+  for (int stage = 0; stage < kNdgStages; ++stage) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    ndg_stage_sums(r, stage, om, iom, g->c[0].trial, g->c[1].trial, threadIdx.x, kBlock, acc);
+    double sum[4];
+    block_sum_rs<4>(acc, sum);  // ends with a block barrier
+    if (threadIdx.x == 0) ndg_advance(g, sum);
+    __syncthreads();  // the next trial steps, written by thread 0
+  }
 }
 
 __global__ void __launch_bounds__(kBlock) k_kkt_final(KktRaw r) {
@@ -681,6 +708,8 @@ cudaError_t launch_kkt(int which, int lanes_r, int lanes_c, const KktRaw& r, cud
       return launch_pdl(k_kkt_end, (r.count + kBlock - 1) / kBlock, kBlock, s, r);
     case KK_NDG:
       return launch_pdl(k_ndg_eval, r.grid_e, kBlock, s, r);
+    case KK_NDG_BLOCK:
+      return launch_pdl(k_ndg_block, 1, kBlock, s, r);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -332,6 +332,10 @@ struct Solve {
   // passes (which write the gradients) and before the restart decision
   cudaError_t ndg_stages() {
     if (kr.ndg == nullptr) return cudaSuccess;
+    if ((long long)kr.m + kr.n <= kNdgOneBlock) {  // a small LP: every stage in one block
+      ++g_launches;
+      return launch_kkt(KK_NDG_BLOCK, lanes_ka, lanes_kt, kr, s);
+    }
     g_launches += kNdgStages;
     for (int k = 0; k < kNdgStages; ++k) {
       const cudaError_t e = launch_kkt(KK_NDG, lanes_ka, lanes_kt, kr, s);
