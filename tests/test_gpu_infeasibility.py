@@ -175,3 +175,24 @@ def test_full_size_cover_with_a_dead_row(P):
     margin = float(lp.b @ y) - float(np.maximum(g, 0) @ lp.u - np.maximum(-g, 0) @ lp.l)
     assert margin > 0
     assert r["ray_obj"] == pytest.approx(margin, rel=1e-6)
+
+
+VARIANTS = {"halpern": ({"halpern": 1}, {"halpern": True}),
+            "ndg_restarts": ({"restart_metric": 1}, {"restart_metric": "ndg"})}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("name", list(CASES))
+def test_variants_find_the_oracles_certificates(P, name, variant):
+    """The algorithmic variants (Halpern PDHG, normalized-duality-gap restarts) end every
+    infeasible or unbounded LP on the status the oracle reaches with the same variant, at
+    the same check where float64 parity holds (short runs), with a valid ray."""
+    kind, _ = CASES[name]
+    lp = inst(name)
+    gkw, okw = VARIANTS[variant]
+    ref = O.solve(lp, O.Params(tol=1e-8, iter_limit=20000, **okw))
+    x, y, r = P.pdlp_solve(lp, P.default_params(tol=1e-8, iter_limit=20000, **gkw))
+    assert r["status"] == ref.status
+    check_certificate(P, lp, kind, x, y, r)
+    if ref.iters <= 256:
+        assert r["iters"] == ref.iters
