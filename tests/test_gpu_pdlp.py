@@ -347,11 +347,14 @@ def no_rows_lp():
                                 dict(precision="fp32", lanes_A=1, lanes_AT=1),
                                 dict(persistent=2), dict(precision="fp32", persistent=2),
                                 dict(persistent=1), dict(bound_objective_rescaling=1),
-                                dict(precision="fp32", tiles=1), dict(precision="fp32", tiles=2)],
+                                dict(precision="fp32", tiles=1), dict(precision="fp32", tiles=2),
+                                dict(halpern=1), dict(precision="fp32", halpern=1),
+                                dict(restart_metric=1), dict(precision="bf16", restart_metric=1)],
                          ids=lambda kw: ",".join(f"{k}={v}" for k, v in kw.items()))
 def test_no_rows_in_every_form(P, kw):
     """An LP without rows (the optimum is each column at the bound its cost points to) in
-    every precision, lanes, persistent, tile and rescaling form."""
+    every precision, lanes, persistent, tile and rescaling form and with the Halpern
+    variant and normalized-duality-gap restarts."""
     x, y, res = P.pdlp_solve(no_rows_lp(), P.default_params(tol=1e-6, **kw))
     assert res["status"] == P.PDLP_OPTIMAL, res
     np.testing.assert_allclose(x, [-1.0, 2.0, 0.5, -3.0, 7.0], rtol=1e-6, atol=1e-6)
@@ -363,7 +366,8 @@ def test_one_by_one_lp_in_every_form(P):
                    np.array([1.0]), np.array([lpgen.SENSE_GE], np.uint8), np.array([1.0]),
                    np.array([0.0]), np.array([3.0]), np.zeros(1, np.uint8), "one")
     for kw in (dict(), dict(precision="fp32"), dict(persistent=2), dict(persistent=1),
-               dict(precision="fp32", lanes_A=1, lanes_AT=1), dict(bound_objective_rescaling=1)):
+               dict(precision="fp32", lanes_A=1, lanes_AT=1), dict(bound_objective_rescaling=1),
+               dict(halpern=1), dict(restart_metric=1), dict(precision="fp32", halpern=1)):
         x, y, res = P.pdlp_solve(lp, P.default_params(tol=1e-7, **kw))
         assert res["status"] == P.PDLP_OPTIMAL, (kw, res)
         assert x[0] == pytest.approx(0.5, abs=1e-6) and y[0] == pytest.approx(0.5, abs=1e-6), kw
