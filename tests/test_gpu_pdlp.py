@@ -278,7 +278,7 @@ def test_solve_reaches_tolerance(P, name, prec):
     tol = 1e-4
     x, y, res = P.pdlp_solve(lp, P.default_params(tol=tol, precision=prec))
     assert res["status"] == P.PDLP_OPTIMAL, res
-    k = O.kkt_original(lp, x, y)  # float64 judge on the returned point
+    k = O.kkt_original(lp, x, y)  # float64 KKT of the returned point
     assert k.rel_kkt <= tol * 1.01, (k, res)
     assert res["rel_kkt"] == pytest.approx(k.rel_kkt, rel=1e-6, abs=1e-12)
     assert obj_err(res["primal_obj"], GOLDEN_KEY[name]) <= OBJ_TOL
