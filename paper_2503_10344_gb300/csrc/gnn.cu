@@ -815,11 +815,23 @@ struct LpDev {
   double *b = nullptr, *c = nullptr, *l = nullptr, *u = nullptr;
   char* sense = nullptr;
   unsigned char* kind = nullptr;
+  // every array above lives in one allocation (one cudaMalloc and one cudaFree per LP, not
+  // one each), followed by `extra` bytes the caller asked build_lp_dev for
+  void* arena = nullptr;
+  unsigned char* extra = nullptr;
   void release() {
-    void* ps[] = {ptr64, a_ptr, a_col, t_ptr, t_col, a_val, t_val, b, c, l, u, sense, kind};
-    for (void* p : ps)
-      if (p) cudaFree(p);
+    if (arena) cudaFree(arena);
     *this = LpDev{};
+  }
+};
+
+// byte offsets of consecutive arrays, each 256-byte aligned
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
   }
 };
 
@@ -837,25 +849,37 @@ int check_host_lp(const pdlp_csr* A, const double* b, const char* sense, const d
 
 // Copies a host LP to the device, validates it there and builds int32 CSR of A and A^T.
 int build_lp_dev(const pdlp_csr* A, const double* b, const char* sense, const double* c,
-                 const double* l, const double* u, cudaStream_t s, LpDev* d) {
+                 const double* l, const double* u, cudaStream_t s, LpDev* d,
+                 size_t extra_bytes = 0) {
   RTRY(check_host_lp(A, b, sense, c, l, u));
   const int m = A->m, n = A->n, nnz = (int)A->nnz;
+  const size_t M = (size_t)m, N = (size_t)n, Z = (size_t)nnz;
   d->m = m;
   d->n = n;
   d->nnz = nnz;
-  GTRY(dalloc(&d->ptr64, (size_t)m + 1));
-  GTRY(dalloc(&d->a_ptr, (size_t)m + 1));
-  GTRY(dalloc(&d->a_col, nnz));
-  GTRY(dalloc(&d->a_val, nnz));
-  GTRY(dalloc(&d->t_ptr, (size_t)n + 1));
-  GTRY(dalloc(&d->t_col, nnz));
-  GTRY(dalloc(&d->t_val, nnz));
-  GTRY(dalloc(&d->b, m));
-  GTRY(dalloc(&d->c, n));
-  GTRY(dalloc(&d->l, n));
-  GTRY(dalloc(&d->u, n));
-  GTRY(dalloc(&d->sense, m));
-  GTRY(dalloc(&d->kind, m));
+  Carve cv;
+  const size_t o_ptr64 = cv.take(8 * (M + 1)), o_aptr = cv.take(4 * (M + 1));
+  const size_t o_acol = cv.take(4 * Z), o_aval = cv.take(8 * Z);
+  const size_t o_tptr = cv.take(4 * (N + 1)), o_tcol = cv.take(4 * Z), o_tval = cv.take(8 * Z);
+  const size_t o_b = cv.take(8 * M), o_c = cv.take(8 * N), o_l = cv.take(8 * N), o_u = cv.take(8 * N);
+  const size_t o_sense = cv.take(M), o_kind = cv.take(M), o_err = cv.take(sizeof(int));
+  const size_t o_extra = cv.take(extra_bytes);
+  GTRY(cudaMalloc(&d->arena, cv.off));
+  unsigned char* base = (unsigned char*)d->arena;
+  d->ptr64 = (int64_t*)(base + o_ptr64);
+  d->a_ptr = (int*)(base + o_aptr);
+  d->a_col = (int*)(base + o_acol);
+  d->a_val = (double*)(base + o_aval);
+  d->t_ptr = (int*)(base + o_tptr);
+  d->t_col = (int*)(base + o_tcol);
+  d->t_val = (double*)(base + o_tval);
+  d->b = (double*)(base + o_b);
+  d->c = (double*)(base + o_c);
+  d->l = (double*)(base + o_l);
+  d->u = (double*)(base + o_u);
+  d->sense = (char*)(base + o_sense);
+  d->kind = base + o_kind;
+  d->extra = extra_bytes ? base + o_extra : nullptr;
   GTRY(cudaMemcpyAsync(d->ptr64, A->row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
   if (nnz > 0) {
     GTRY(cudaMemcpyAsync(d->a_col, A->col, sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
@@ -876,15 +900,13 @@ int build_lp_dev(const pdlp_csr* A, const double* b, const char* sense, const do
   for (int i = 0; i < m; ++i)
     if (A->row_ptr[i + 1] < A->row_ptr[i])
       return gfail(PDLP_ERR_INVALID_INPUT, "row_ptr decreases at row " + std::to_string(i));
-  int* d_err = nullptr;
-  GTRY(dalloc(&d_err, 1));
+  int* d_err = (int*)(base + o_err);
   pdlp::SetupIn in{m, n, (long long)nnz, d->ptr64, d->a_col, d->a_val, d->b, d->sense,
                    d->c, d->l, d->u};
   cudaError_t e = pdlp::setup_validate(in, d_err, s);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_err);
   GTRY(e);
   if (herr) {
     std::string why;
@@ -1363,23 +1385,28 @@ int gnn_graph_create(gnn_model* md, const pdlp_csr* A, const double* b, const ch
   gnn_graph* g = new gnn_graph();
   g->owner = md;
   cudaStream_t s = md->s;
-  int rc = build_lp_dev(A, b, sense, c, l, u, s, &g->d);
+  // the graph's own arrays and the feature pass's scratch share the LP's allocation
+  const size_t M = A ? (size_t)std::max(A->m, 0) : 0, N = A ? (size_t)std::max(A->n, 0) : 0;
+  Carve cv;
+  const size_t o_idr = cv.take(4 * M), o_idc = cv.take(4 * N);
+  const size_t o_fv = cv.take(4 * N * GNN_VAR_FEATURES), o_fc = cv.take(4 * M * GNN_CON_FEATURES);
+  const size_t o_nr = cv.take(8 * M), o_nc = cv.take(8 * N), o_mx = cv.take(6 * 8);
+  int rc = build_lp_dev(A, b, sense, c, l, u, s, &g->d, cv.off);
   if (rc != PDLP_OK) {
     gnn_graph_free(g);
     return rc;
   }
   const int m = g->d.m, n = g->d.n;
-  double *nr = nullptr, *nc = nullptr;
-  unsigned long long* mx = nullptr;
+  unsigned char* ex = g->d.extra;
+  g->inv_deg_r = (float*)(ex + o_idr);
+  g->inv_deg_c = (float*)(ex + o_idc);
+  g->fv = (float*)(ex + o_fv);
+  g->fc = (float*)(ex + o_fc);
+  double* nr = (double*)(ex + o_nr);
+  double* nc = (double*)(ex + o_nc);
+  unsigned long long* mx = (unsigned long long*)(ex + o_mx);
   unsigned long long hmx[6] = {};
-  cudaError_t e = dalloc(&g->inv_deg_r, m);
-  if (e == cudaSuccess) e = dalloc(&g->inv_deg_c, n);
-  if (e == cudaSuccess) e = dalloc(&g->fv, (size_t)n * GNN_VAR_FEATURES);
-  if (e == cudaSuccess) e = dalloc(&g->fc, (size_t)m * GNN_CON_FEATURES);
-  if (e == cudaSuccess) e = dalloc(&nr, m);
-  if (e == cudaSuccess) e = dalloc(&nc, n);
-  if (e == cudaSuccess) e = dalloc(&mx, 6);
-  if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, 6 * sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(mx, 0, 6 * sizeof(unsigned long long), s);
   const int G = sm_count() * 8;
   if (e == cudaSuccess && m > 0) {
     k_gnn_stats<<<grid_rows(m, NB, G), NB, 0, s>>>(m, g->d.a_ptr, g->d.a_val, g->d.b, nr,
@@ -1401,9 +1428,6 @@ int gnn_graph_create(gnn_model* md, const pdlp_csr* A, const double* b, const ch
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (nr) cudaFree(nr);
-  if (nc) cudaFree(nc);
-  if (mx) cudaFree(mx);
   if (e != cudaSuccess) {
     gnn_graph_free(g);
     return gfail(e == cudaErrorMemoryAllocation ? PDLP_ERR_OOM : PDLP_ERR_CUDA, cudaGetErrorString(e));
@@ -1457,9 +1481,10 @@ int gnn_graph_features(const gnn_graph* g, float* fv, float* fc) {
 
 int gnn_graph_free(gnn_graph* g) {
   if (!g) return PDLP_OK;
-  // cudaFree waits for the device; the owner is not touched (it may be gone)
+  // cudaFree waits for the device; the owner is not touched (it may be gone).  The degree
+  // and feature arrays live in the LP's allocation; the labels have their own.
   g->d.release();
-  void* ps[] = {g->inv_deg_r, g->inv_deg_c, g->fv, g->fc, g->x_star, g->y_star};
+  void* ps[] = {g->x_star, g->y_star};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete g;
@@ -1628,17 +1653,27 @@ int pdlp_solve_warm(gnn_model* md, const pdlp_csr* A, const double* b, const cha
   cudaStream_t s = md->s;
   const int n = g->d.n, m = g->d.m;
   double *xc = nullptr, *yc = nullptr, *part = nullptr, *kk = nullptr, *xo = nullptr, *yo = nullptr;
+  double* buf = nullptr;  // the six scratch vectors in one allocation
   double hk[8] = {};
   int rc = forward(md, g, true, false, false);
   cudaError_t e = cudaSuccess;
   if (rc == PDLP_OK) {
-    e = dalloc(&xc, n);
-    if (e == cudaSuccess) e = dalloc(&yc, m);
-    if (e == cudaSuccess) e = dalloc(&part, start_kkt_part_doubles());
-    if (e == cudaSuccess) e = dalloc(&kk, 8);
-    if (e == cudaSuccess) e = dalloc(&xo, n);
-    if (e == cudaSuccess) e = dalloc(&yo, m);
-    if (e != cudaSuccess) rc = gfail(PDLP_ERR_OOM, cudaGetErrorString(e));
+    Carve cv;
+    const size_t o_xc = cv.take(8 * (size_t)n), o_yc = cv.take(8 * (size_t)m);
+    const size_t o_part = cv.take(8 * start_kkt_part_doubles()), o_kk = cv.take(8 * 8);
+    const size_t o_xo = cv.take(8 * (size_t)n), o_yo = cv.take(8 * (size_t)m);
+    e = cudaMalloc((void**)&buf, cv.off);
+    if (e == cudaSuccess) {
+      unsigned char* p0 = (unsigned char*)buf;
+      xc = (double*)(p0 + o_xc);
+      yc = (double*)(p0 + o_yc);
+      part = (double*)(p0 + o_part);
+      kk = (double*)(p0 + o_kk);
+      xo = (double*)(p0 + o_xo);
+      yo = (double*)(p0 + o_yo);
+    } else {
+      rc = gfail(PDLP_ERR_OOM, cudaGetErrorString(e));
+    }
   }
   if (rc == PDLP_OK) rc = start_kkt(g->d, md->xpred, md->ypred, 0, part, kk, s);
   if (rc == PDLP_OK) rc = start_kkt(g->d, xc, yc, 1, part, kk + 4, s);
@@ -1671,8 +1706,7 @@ int pdlp_solve_warm(gnn_model* md, const pdlp_csr* A, const double* b, const cha
     info->predict_s = predict_s;
   }
   cudaStreamSynchronize(s);
-  for (void* q : {(void*)xc, (void*)yc, (void*)part, (void*)kk, (void*)xo, (void*)yo})
-    if (q) cudaFree(q);
+  if (buf) cudaFree(buf);
   gnn_graph_free(g);
   return rc;
 }
